@@ -1,0 +1,243 @@
+"""FP64 CPU oracle for the 3DGS rasterization hot path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package. The CUDA library never does, and this package
+never imports the CUDA library: the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, OpenMP over
+independent outputs); this module compiles it with gcc on first use and marshals
+numpy arrays. Every function follows the paper's section 3.2 (Eqs. 1-3) and
+Algorithm 1 under the readings listed at the top of ``oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.c"
+_LIB_PATH = _HERE / "liboracle.so"
+_lib = None
+
+DEFAULT_OPTS = dict(tile=16, dilation=0.3, alpha_min=1.0 / 255.0, alpha_max=0.99,
+                    t_stop=1e-4, q_max=9.0)
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.c into liboracle.so beside it (gcc -O2 -fopenmp)."""
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".so.{os.getpid()}.tmp")
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                               "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = C.CDLL(str(_LIB_PATH))
+        _lib.orc_duplicate.restype = C.c_int64
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
+def opts_array(opts=None):
+    """[tile, dilation, alpha_min, alpha_max, t_stop, q_max] as float64.
+
+    The thresholds are rounded to float32 first, so that the oracle compares
+    against exactly the values the CUDA library receives.
+    """
+    o = dict(DEFAULT_OPTS)
+    if opts:
+        o.update(opts)
+    vals = [o["tile"], o["dilation"], o["alpha_min"], o["alpha_max"], o["t_stop"], o["q_max"]]
+    return np.array([float(np.float32(v)) for v in vals], np.float64)
+
+
+def cam_array(cam):
+    """Camera -> 17 float64 values made from its float32 parameters."""
+    return cam.as_array().astype(np.float64)
+
+
+def num_threads() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def preprocess(scene, cam, opts=None):
+    """Per-Gaussian projection, conic, extent, tile rectangle and colour (Eq. 1).
+
+    Returns a dict of numpy arrays: valid [N] int32, uv [N,2], conic [N,3]
+    (a, b, c with q = a dx^2 + 2 b dx dy + c dy^2), S [N,3] (s00, s01, s11),
+    opacity [N], rgb [N,3], z [N], zkey [N] float32, radius [N], rect [N,4]
+    (x0, y0, x1, y1 in tiles, upper bounds exclusive).
+    """
+    n = scene["means"].shape[0]
+    out = dict(valid=np.zeros(n, np.int32), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
+               S=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)), z=np.zeros(n),
+               zkey=np.zeros(n, np.float32), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32))
+    arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    rc = _L().orc_preprocess(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]),
+                             _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
+                             *[_p(out[k]) for k in ("valid", "uv", "conic", "S", "opacity", "rgb",
+                                                    "z", "zkey", "radius", "rect")])
+    if rc != 0:
+        raise ValueError("oracle preprocess rejected its arguments")
+    return out
+
+
+def render_pixels(prep, px, py, bg=(0.0, 0.0, 0.0), opts=None):
+    """Brute-force definition at the given pixels: every valid splat is a candidate.
+
+    Returns dict rgb [P,3], alpha [P], T [P], n_contrib [P], ambiguous [P].
+    """
+    n = prep["valid"].shape[0]
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    P = px.shape[0]
+    out = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), T=np.zeros(P),
+               n_contrib=np.zeros(P, np.int32), ambiguous=np.zeros(P, np.int32))
+    _L().orc_render_pixels(C.c_int64(n), _p(prep["valid"]), _p(prep["uv"]), _p(prep["conic"]),
+                           _p(prep["opacity"]), _p(prep["rgb"]), _p(prep["zkey"]), C.c_int64(P),
+                           _p(px), _p(py), _p(_f64(bg)), _p(opts_array(opts)),
+                           _p(out["rgb"]), _p(out["alpha"]), _p(out["T"]), _p(out["n_contrib"]),
+                           _p(out["ambiguous"]))
+    return out
+
+
+def render_bruteforce(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None):
+    """Whole image by the brute-force definition; rgb returned planar [3,H,W]."""
+    ys, xs = np.mgrid[0:H, 0:W]
+    r = render_pixels(prep, xs.ravel(), ys.ravel(), bg, opts)
+    return dict(rgb=r["rgb"].T.reshape(3, H, W).copy(), alpha=r["alpha"].reshape(H, W),
+                T=r["T"].reshape(H, W), n_contrib=r["n_contrib"].reshape(H, W),
+                ambiguous=r["ambiguous"].reshape(H, W))
+
+
+def render_tiled(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
+    """Tile-binned render (same result as the brute force; faster on big scenes).
+
+    tile_mask: optional uint8 [tiles_y * tiles_x]; only those tiles are computed
+    (other pixels are NaN in rgb/alpha/T and -1 in n_contrib/ambiguous).
+    """
+    n = prep["valid"].shape[0]
+    out = dict(rgb=np.full((3, H, W), np.nan), alpha=np.full((H, W), np.nan),
+               T=np.full((H, W), np.nan), n_contrib=np.full((H, W), -1, np.int32),
+               ambiguous=np.full((H, W), -1, np.int32))
+    mask_p = None
+    if tile_mask is not None:
+        tile_mask = np.ascontiguousarray(tile_mask, np.uint8)
+        mask_p = _p(tile_mask)
+    rc = _L().orc_render_tiled(C.c_int64(n), _p(prep["valid"]), _p(prep["uv"]), _p(prep["conic"]),
+                               _p(prep["opacity"]), _p(prep["rgb"]), _p(prep["zkey"]), _p(prep["rect"]),
+                               C.c_int(W), C.c_int(H), _p(_f64(bg)), _p(opts_array(opts)), mask_p,
+                               _p(out["rgb"]), _p(out["alpha"]), _p(out["T"]), _p(out["n_contrib"]),
+                               _p(out["ambiguous"]))
+    if rc != 0:
+        raise MemoryError("oracle tile binning failed")
+    return out
+
+
+def render(scene, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
+    """Preprocess + tile-binned render of one view."""
+    prep = preprocess(scene, cam, opts)
+    return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask), prep
+
+
+def duplicate(prep, tiles_x, cap=None):
+    """Keys (tile << 32 | float bits of zkey) and vals (Gaussian index), index-major."""
+    n = prep["valid"].shape[0]
+    rect = prep["rect"]
+    counts = np.where(prep["valid"] != 0, (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]), 0)
+    m_total = int(counts.sum())
+    cap = m_total if cap is None else cap
+    keys = np.zeros(max(cap, 1), np.uint64)
+    vals = np.zeros(max(cap, 1), np.uint32)
+    m = _L().orc_duplicate(C.c_int64(n), _p(prep["valid"]), _p(rect), _p(prep["zkey"]),
+                           C.c_int(tiles_x), _p(keys), _p(vals), C.c_int64(cap))
+    if m < 0:
+        raise OverflowError("more keys than capacity")
+    return keys[:m], vals[:m]
+
+
+def duplicate_raw(valid, rect, zkey, tiles_x):
+    """Same as duplicate() from explicit arrays (valid [N], rect [N,4], zkey [N])."""
+    return duplicate(dict(valid=np.ascontiguousarray(valid, np.int32),
+                          rect=np.ascontiguousarray(rect, np.int32),
+                          zkey=np.ascontiguousarray(zkey, np.float32)), tiles_x)
+
+
+def stable_sort_pairs(keys, vals):
+    keys = np.ascontiguousarray(keys, np.uint64)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    m = keys.shape[0]
+    ok = np.zeros(max(m, 1), np.uint64)
+    ov = np.zeros(max(m, 1), np.uint32)
+    _L().orc_stable_sort_pairs(C.c_int64(m), _p(keys), _p(vals), _p(ok), _p(ov))
+    return ok[:m], ov[:m]
+
+
+def tile_ranges(sorted_keys, ntiles):
+    sorted_keys = np.ascontiguousarray(sorted_keys, np.uint64)
+    r = np.zeros((ntiles, 2), np.uint32)
+    _L().orc_tile_ranges(C.c_int64(sorted_keys.shape[0]), _p(sorted_keys), C.c_int64(ntiles), _p(r))
+    return r
+
+
+def sh_eval(deg, direction):
+    """Real SH basis values Y_k, k < (deg+1)^2, at a unit direction (x, y, z)."""
+    Y = np.zeros(16)
+    x, y, z = (float(v) for v in direction)
+    _L().orc_sh_eval(C.c_int(deg), C.c_double(x), C.c_double(y), C.c_double(z), _p(Y))
+    return Y[: (deg + 1) ** 2].copy()
+
+
+def covariance(log_scales, quats):
+    """Sigma = R diag(exp(log_s))^2 R^T per Gaussian, [N,3,3]."""
+    ls = _f64(np.atleast_2d(log_scales))
+    q = _f64(np.atleast_2d(quats))
+    n = ls.shape[0]
+    out = np.zeros((n, 9))
+    _L().orc_covariance(C.c_int64(n), _p(ls), _p(q), _p(out))
+    return out.reshape(n, 3, 3)
+
+
+def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False):
+    """FP64 gradient of L = sum(gC * rgb) + sum(gA * alpha) w.r.t. all Gaussian inputs.
+
+    gC: [3,H,W], gA: [H,W]. Returns dict means [N,3], log_scales [N,3], quats [N,4],
+    opacity_logits [N], sh [N,K,3] (and g2 [N,9] screen-space gradients if asked).
+    """
+    n = scene["means"].shape[0]
+    K = (scene["sh_degree"] + 1) ** 2
+    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
+    g2 = np.zeros((n, 9))
+    arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    rc = _L().orc_adjoint(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]),
+                          _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
+                          _p(_f64(bg)), _p(_f64(gC)), _p(_f64(gA)),
+                          *[_p(out[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")],
+                          _p(g2))
+    if rc != 0:
+        raise ValueError("oracle adjoint failed")
+    if return_g2:
+        out["g2"] = g2
+    return out
