@@ -287,16 +287,15 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     out->uv[2 * i + 1] = v;
 
     int T_ = op->tile;
-    int x0 = (int)floor((u - rad - 1.0) / T_), x1 = (int)floor((u + rad + 1.0) / T_) + 1;
-    int y0 = (int)floor((v - rad - 1.0) / T_), y1 = (int)floor((v + rad + 1.0) / T_) + 1;
-    if (x0 < 0) x0 = 0; if (x0 > tiles_x) x0 = tiles_x;
-    if (x1 < 0) x1 = 0; if (x1 > tiles_x) x1 = tiles_x;
-    if (y0 < 0) y0 = 0; if (y0 > tiles_y) y0 = tiles_y;
-    if (y1 < 0) y1 = 0; if (y1 > tiles_y) y1 = tiles_y;
+    /* clamp in floating point before converting: u, v may be far off screen */
+    double fx0 = floor((u - rad - 1.0) / T_), fx1 = floor((u + rad + 1.0) / T_) + 1.0;
+    double fy0 = floor((v - rad - 1.0) / T_), fy1 = floor((v + rad + 1.0) / T_) + 1.0;
+    int x0 = (int)fmin((double)tiles_x, fmax(0.0, fx0)), x1 = (int)fmin((double)tiles_x, fmax(0.0, fx1));
+    int y0 = (int)fmin((double)tiles_y, fmax(0.0, fy0)), y1 = (int)fmin((double)tiles_y, fmax(0.0, fy1));
     out->radius[i] = rad;
     out->rect[4 * i + 0] = x0; out->rect[4 * i + 1] = y0;
     out->rect[4 * i + 2] = x1; out->rect[4 * i + 3] = y1;
-    if ((x1 - x0) * (y1 - y0) <= 0) return;
+    if (x1 <= x0 || y1 <= y0) return;
 
     /* colour */
     double cc[3];
@@ -351,9 +350,12 @@ static int cmp_ord(const void* a, const void* b) {
 }
 
 /* Ambiguity margins: a decision taken within these of its threshold may go the
- * other way in float32 arithmetic (kappa = 8 safety factor). */
-#define AMB_Q_REL     (8.0 * 1e-5)
-#define AMB_ALPHA_REL (8.0 * 1e-5)
+ * other way in float32 arithmetic. The float32 renderer evaluates q and alpha to
+ * ~1e-6 relative (float-float pixel centres, whitened splat shape) and the
+ * transmittance product to ~1e-5 relative after ~100 splats; each margin is a
+ * safety factor of 8 above that. */
+#define AMB_Q_REL     (8.0 * 1e-6)
+#define AMB_ALPHA_REL (8.0 * 1e-6)
 #define AMB_T_REL     (8.0 * 1e-5)
 
 typedef struct {
