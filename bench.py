@@ -1,0 +1,426 @@
+"""Benchmark of the B300 3DGS rasterizer; prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload 1m|6m|fwdbwd|small]
+
+A step is one pass of the whole hot path over one frame: preprocess, key
+duplication, radix sort, tile ranges and compositing of one view (fwdbwd: plus
+the adjoint). The default workload is 1M Gaussians with SH degree 3 seen from a
+32-camera orbit at 1920x1080 (steps cycle through the views); the attribute
+arrays (236 MB) exceed the 126 MB L2, so no flush is needed between steps.
+
+value      frame time in ms (whole job: max-over-ranks time / frames of all ranks),
+           inputs resident in HBM, CUDA events on the launching stream.
+e2e        the same through the C ABI with host buffers: every step copies the
+           scene from pinned host memory, renders, and reads the image back.
+roofline   the stage that dominates the frame, against the measured HBM copy
+           bandwidth (MEASURED_PEAKS.json), algorithmic bytes per launch over the
+           CUDA-event launch time.
+cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same
+           frame (a stride of its tiles), scaled to a frame.
+--impl reference   times that oracle alone as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "1080p frame ms at 1M/6M Gaussians SH3; fwd+bwd ms; sort keys/s vs HBM peak"
+STAGES = ["clear", "preprocess", "duplicate", "sort_histogram", "sort_passes", "ranges", "composite"]
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6400.0, source="fallback")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# workloads
+# ------------------------------------------------------------------------------------------
+
+def load_workload(name):
+    from paper_2512_08478_b300 import synth
+    if name == "1m":
+        sc, cams = synth.workload_1m(views=32)
+        desc = dict(workload="1M Gaussians SH3, 64-component mixture, 32-view orbit r=15, 1920x1080, 50 deg vfov",
+                    n_gaussians=1_000_000, sh_degree=3, width=1920, height=1080, views=32, tile=16)
+        return sc, cams, desc, None
+    if name == "6m":
+        sc, extras, cams = synth.workload_dynamic()
+        desc = dict(workload="6M Gaussians SH3, dynamic (moving means, pulsing opacity), 1920x1080 slow orbit",
+                    n_gaussians=6_000_000, sh_degree=3, width=1920, height=1080, frames=120, tile=16)
+        return sc, cams, desc, extras
+    if name == "fwdbwd":
+        sc, target, cams = synth.workload_fwdbwd()
+        desc = dict(workload="500k Gaussians SH3, 800x800, L2 loss vs perturbed target, forward + backward",
+                    n_gaussians=500_000, sh_degree=3, width=800, height=800, views=len(cams), tile=16)
+        return sc, cams, desc, target
+    if name == "small":
+        sc, cams = synth.workload_small()
+        desc = dict(workload="10k Gaussians SH0, 256x256, one camera", n_gaussians=10_000, sh_degree=0,
+                    width=256, height=256, views=1, tile=16)
+        return sc, cams, desc, None
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"], samples=0)
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_2512_08478_b300 as vis
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    sc_np, cams, desc, extra = load_workload(args.workload)
+    W, H = desc["width"], desc["height"]
+    sc = vis.Scene.from_numpy(sc_np)
+    n = sc.n
+    cap = 16 * n + (1 << 20)
+    ws = vis.Workspace(n, W, H, key_capacity=cap)
+    rgb = torch.empty((3, H, W), device="cuda")
+    alpha = torch.empty((H, W), device="cuda")
+    stream = torch.cuda.current_stream()
+    fwdbwd = args.workload == "fwdbwd"
+    if fwdbwd:
+        tgt = vis.Scene.from_numpy(extra)
+        tgt_rgb = torch.empty_like(rgb)
+        tgt_a = torch.empty_like(alpha)
+        grads = {k: torch.empty_like(sc.tensors[k]) for k in vis.FIELDS}
+        d_alpha = torch.zeros_like(alpha)
+        d_rgb = torch.empty_like(rgb)
+    cam_objs = [vis.make_camera(c) for c in cams]
+    view0 = rank * args.steps
+
+    def frame(i):
+        c = cam_objs[(view0 + i) % len(cam_objs)]
+        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        if fwdbwd:
+            torch.sub(rgb, tgt_rgb, out=d_rgb)
+            d_rgb.mul_(2.0 / rgb.numel())
+            vis.vis_render_backward(sc.handle, c, W, H, (0.0, 0.0, 0.0), d_rgb, d_alpha, ws.buf, grads)
+
+    if fwdbwd:   # target image of view 0 (fixed), rendered once outside the timing
+        vis.vis_render(tgt.handle, cam_objs[0], W, H, (0.0, 0.0, 0.0), tgt_rgb, tgt_a, ws.buf)
+        vis.vis_check(ws.buf)
+
+    for i in range(args.warmup):
+        frame(i)
+    num_keys = vis.vis_check(ws.buf)
+
+    # ---- device-timed region ----
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    keys_seen = []
+    with ClockSampler(local) as clk:
+        vis.lib().vis_profile_begin()
+        ev0.record(stream)
+        for i in range(args.steps):
+            frame(i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    import ctypes as C
+    stage = (C.c_double * 7)()
+    ns, nr, npass = C.c_int(), C.c_int(), C.c_int()
+    vis._ok(vis.lib().vis_profile_end(stage, 7, C.byref(ns), C.byref(nr), C.byref(npass)))
+    vis.vis_check(ws.buf)
+    t_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    frames_total = args.steps * world
+    value = t_ms / frames_total
+    stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
+    passes = npass.value
+
+    # keys per frame averaged over the views used
+    mlist = []
+    for i in range(min(args.steps, len(cam_objs))):
+        c = cam_objs[(view0 + i) % len(cam_objs)]
+        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        mlist.append(vis.vis_check(ws.buf))
+    M = float(np.mean(mlist))
+
+    # ---- roofline of the dominant stage ----
+    peaks = _peaks()
+    dom = max(("preprocess", "sort_passes", "composite", "duplicate"), key=lambda s: stage_ms[s])
+    sh_k = (desc["sh_degree"] + 1) ** 2
+    bytes_pre = n * (12 + 12 + 16 + 4 + 12 * sh_k) + n * (48 + 4 + 8 + 4)
+    if dom == "sort_passes":
+        launch_ms = stage_ms["sort_passes"] / passes
+        algo = 24.0 * M
+        unit_note = "24 B per key per digit pass (8 B key + 4 B value, read and written)"
+    elif dom == "preprocess":
+        launch_ms = stage_ms["preprocess"]
+        algo = float(bytes_pre)
+        unit_note = "attributes read + splat record, depth, rect, count written per Gaussian"
+    else:
+        launch_ms = stage_ms[dom]
+        algo = M * (4 + 48) + W * H * (16 + 8)
+        unit_note = "per key: value + gathered 48 B record; per pixel: rgb, alpha, T, last written"
+    achieved = algo / (launch_ms * 1e-3) / 1e9
+    traffic = _committed_traffic(dom, M, n)
+    roof = dict(kernel=dom, bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=round(achieved / peaks["hbm_gbs"], 4), traffic=traffic,
+                peak_source=peaks["source"], algorithmic_bytes_per_launch=int(algo), launch_ms=round(launch_ms, 4),
+                bytes_model=unit_note)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist)
+
+    line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(desc, l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
+                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                clocks=clk.summary(), e2e=e2e,
+                gpu_launches=int(args.steps * (6 + passes + (2 if fwdbwd else 0))),
+                roofline=roof,
+                stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                keys_per_frame=int(M), sort_passes=passes,
+                sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]) * 1e3, 1),
+                gaussians_per_s=round(n / value * 1e3, 1))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _committed_traffic(kernel, M, n):
+    """DRAM bytes per launch from a committed ncu capture (profiles/traffic.json), scaled
+    to this launch by keys (sort, composite) or Gaussians (preprocess); None if absent."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text()).get(kernel)
+    if not d:
+        return None
+    if "bytes_per_key" in d:
+        return int(d["bytes_per_key"] * M)
+    if "bytes_per_gaussian" in d:
+        return int(d["bytes_per_gaussian"] * n)
+    return None
+
+
+def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist):
+    """Every step: H2D of the scene from pinned memory, render, D2H of rgb + alpha."""
+    host = {k: torch.from_numpy(sc_np[k]).pin_memory() for k in vis.FIELDS}
+    dev = {k: torch.empty(host[k].shape, dtype=torch.float32, device="cuda") for k in vis.FIELDS}
+    sc = vis.Scene(**dev, sh_degree=sc_np["sh_degree"])
+    ws = vis.Workspace(sc.n, W, H, key_capacity=cap)
+    rgb = torch.empty((3, H, W), device="cuda")
+    alpha = torch.empty((H, W), device="cuda")
+    out_rgb = torch.empty((3, H, W)).pin_memory()
+    out_a = torch.empty((H, W)).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = (out_rgb.numel() + out_a.numel()) * 4
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        for k in vis.FIELDS:
+            dev[k].copy_(host[k], non_blocking=True)
+        vis.vis_render(sc.handle, cam_objs[i % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        out_rgb.copy_(rgb, non_blocking=True)
+        out_a.copy_(alpha, non_blocking=True)
+
+    for i in range(max(2, args.warmup)):
+        step(i)
+    vis.vis_check(ws.buf)
+    steps = max(4, args.steps // 2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vis.vis_check(ws.buf)
+    t = e0.elapsed_time(e1)
+    world = 1
+    if dist:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        world = dist.get_world_size()
+    return dict(value=round(t / (steps * world), 4), unit="ms/frame", h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(d2h), steps=steps)
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ------------------------------------------------------------------------------------------
+
+def _oracle_frame(oracle, sc_np, cam, stride):
+    """Oracle preprocess of all Gaussians + composite of every `stride`-th tile;
+    returns seconds scaled to one whole frame."""
+    tiles_x, tiles_y = (cam.W + 15) // 16, (cam.H + 15) // 16
+    mask = np.zeros(tiles_x * tiles_y, np.uint8)
+    mask[::stride] = 1
+    t0 = time.perf_counter()
+    prep = oracle.preprocess(sc_np, cam)
+    t1 = time.perf_counter()
+    oracle.render_tiled(prep, cam.W, cam.H, tile_mask=mask)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) * (tiles_x * tiles_y) / mask.sum()
+
+
+def _stride_for(workload):
+    return {"1m": 8, "6m": 16, "fwdbwd": 8, "small": 1}.get(workload, 8)
+
+
+def cpu_baseline(workload, sc_np, cams, desc, budget_s=20.0):
+    import oracle
+    stride = _stride_for(workload)
+    frames, t_acc, t_start = 0, 0.0, time.perf_counter()
+    while True:
+        t_acc += _oracle_frame(oracle, sc_np, cams[frames % len(cams)], stride)
+        frames += 1
+        if time.perf_counter() - t_start > budget_s * 0.5 or frames >= 3:
+            break
+    return dict(value=round(t_acc / frames * 1e3, 1), unit="ms/frame", cores=oracle.num_threads(), kind="oracle",
+                sample=f"{frames} view(s): FP64 preprocess of all {desc['n_gaussians']} Gaussians + composite of "
+                       f"every {stride}th 16x16 tile, tile time scaled by {stride}")
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sc_np, cams, desc, _ = load_workload(args.workload)
+    stride = _stride_for(args.workload)
+    for i in range(args.warmup):
+        _oracle_frame(oracle, sc_np, cams[i % len(cams)], stride * 4)
+    t0 = time.perf_counter()
+    acc = 0.0
+    for i in range(args.steps):
+        acc += _oracle_frame(oracle, sc_np, cams[i % len(cams)], stride)
+    wall = time.perf_counter() - t0
+    value = acc / args.steps * 1e3
+    cores = oracle.num_threads()
+    sample = (f"per step: FP64 preprocess of all {desc['n_gaussians']} Gaussians + composite of every "
+              f"{stride}th 16x16 tile, tile time scaled by {stride}")
+    line = dict(impl="reference", metric=METRIC, value=round(value, 1), unit="ms/frame", n_gpus=world,
+                steps=args.steps, warmup=args.warmup, ms_per_step=round(wall / args.steps * 1e3, 1),
+                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(desc), cpu_baseline=dict(value=round(value, 1), unit="ms/frame", cores=cores,
+                                                     kind="oracle", sample=sample),
+                e2e=dict(value=round(value, 1), unit="ms/frame", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * vis.h -- C ABI of the B300 (sm_103a) 3D Gaussian Splatting rasterizer.
+ *
+ * The library renders N 3D Gaussians to an image: preprocess (EWA projection,
+ * spherical-harmonics colour, 3-sigma extent and tile overlap), duplication of
+ * one (tile, depth) key per touched tile, a stable LSD radix sort of those keys,
+ * per-tile ranges, and front-to-back alpha compositing; plus the adjoint of all of
+ * it and a batched many-asset, many-camera form. The math is the paper's
+ * definition of 3DGS (section 3.2): Eq. 1 (x_i = Pi(mu_i), S_i = J_i Sigma_i J_i^T),
+ * Eq. 2 (w_i(x) = alpha_i exp(-1/2 (x-x_i)^T S_i^-1 (x-x_i))) and Eq. 3 (front-to-back
+ * compositing in depth order), with the per-frame preprocess / GPU sort / draw
+ * structure of Algorithm 1.
+ *
+ * Conventions (all calls):
+ *  - Every pointer argument named as device memory must be a CUDA device pointer
+ *    on the current device, 16-byte aligned, C-contiguous. Host pointers are
+ *    named as such.
+ *  - The caller owns all memory: inputs, outputs and the workspace. No call
+ *    allocates device memory. A scene handle borrows the caller's attribute
+ *    arrays (zero copy); they must outlive the handle and may be rewritten
+ *    between frames.
+ *  - Work is enqueued on the given stream and returns without synchronising,
+ *    except vis_check(), which synchronises the stream.
+ *  - Every call returns a vis_status; no exception or abort crosses the ABI.
+ *    On failure, vis_last_error() returns a thread-local message.
+ *  - Errors found on the device (key capacity exceeded, a bounded spin wait that
+ *    ran out) are recorded in the workspace and returned by vis_check().
+ */
+#ifndef VIS_H
+#define VIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VIS_API __attribute__((visibility("default")))
+#else
+#define VIS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VIS_OK = 0,
+    VIS_ERR_INVALID_ARG = 1,   /* rejected on the host; nothing was enqueued */
+    VIS_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    VIS_ERR_CAPACITY = 3,      /* more (tile, Gaussian) keys than the workspace holds */
+    VIS_ERR_TIMEOUT = 4,       /* a bounded device spin wait gave up; outputs are invalid */
+    VIS_ERR_UNSUPPORTED = 5
+} vis_status;
+
+/* Opaque scene handle: borrowed attribute pointers plus the SH degree. */
+typedef struct vis_scene* vis_scene_t;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).
+ * A world point X maps to camera space as p = R X + t (R row-major), and to pixel
+ * coordinates (fx p.x/p.z + cx, fy p.y/p.z + cy). Pixel (x, y) covers
+ * [x, x+1) x [y, y+1); its centre is (x + 0.5, y + 0.5). Gaussians with
+ * p.z <= near_z are culled (Algorithm 1, frustum cull). */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_z;
+} vis_camera;
+
+/* Render options. Pass NULL for the defaults, or fill with vis_default_opts().
+ *  tile        tile edge in pixels: 8, 16 or 32 (default 16)
+ *  digit_bits  radix digit width of the sort: 8 (default 8)
+ *  dilation    low-pass term added to the diagonal of S (px^2, default 0.3)
+ *  alpha_min   splats with alpha < alpha_min are skipped; Gaussians whose opacity
+ *              is below it are culled (default 1/255)
+ *  alpha_max   alpha is clamped to alpha_max (default 0.99)
+ *  t_stop      compositing stops before the first splat that would bring the
+ *              transmittance below t_stop (default 1e-4)
+ * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
+typedef struct {
+    int tile;
+    int digit_bits;
+    float dilation;
+    float alpha_min;
+    float alpha_max;
+    float t_stop;
+} vis_render_opts;
+
+VIS_API void vis_default_opts(vis_render_opts* opts);
+
+/* Workspace layout (byte offsets from the workspace base), as used by
+ * vis_render / vis_render_backward for a given (n, W, H, opts, ws_bytes).
+ * Exposed so that callers can inspect intermediate stages. */
+typedef struct {
+    size_t total_bytes;      /* bytes the layout needs (<= ws_bytes) */
+    int64_t key_capacity;    /* max (tile, Gaussian) keys the workspace holds */
+    int tiles_x, tiles_y;
+    int sort_passes;         /* radix passes over the key bits in use */
+    int sorted_buffer;       /* 0 or 1: which key/val buffer holds the sorted result */
+    size_t off_ctrl;         /* vis_ctrl, device-written status */
+    size_t off_rec;          /* float4[n][3] splat records: (u,v,u_lo,v_lo), (f1,f2), (opacity,rgb) */
+    size_t off_depth;        /* float[n] view depth (the sort key's low word) */
+    size_t off_rect;         /* uint2[n] tile rect: x0 | x1<<16, y0 | y1<<16 (upper bounds exclusive) */
+    size_t off_touched;      /* uint32[n] tiles touched (0 if culled) */
+    size_t off_keys[2];      /* uint64[cap] (tile << 32) | float bits of depth */
+    size_t off_vals[2];      /* uint32[cap] Gaussian index */
+    size_t off_ranges;       /* uint2[tiles] [start, end) into the sorted keys */
+    size_t off_tfinal;       /* float[H*W] final transmittance */
+    size_t off_last;         /* int32[H*W] 1 + position, in the sorted key list, of the last composited splat (0 if none) */
+    size_t off_g2;           /* float[n][9] screen-space gradients (backward scratch) */
+} vis_ws_layout;
+
+/* Device-written status block at workspace offset off_ctrl (= 0). */
+typedef struct {
+    uint32_t num_keys;       /* keys produced by the last render (may exceed capacity) */
+    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout */
+    uint32_t reserved[62];
+} vis_ctrl;
+
+/* Borrow a scene (section 3.2: mean, scale, rotation quaternion, opacity, SH colour).
+ *  means          device float[n][3]
+ *  log_scales     device float[n][3]   s = exp(log_s)
+ *  quats          device float[n][4]   (w, x, y, z); normalised by the renderer
+ *  opacity_logits device float[n]      opacity = sigmoid(logit)
+ *  sh             device float[n][K][3], K = (sh_degree+1)^2, coefficient k = l*l+l+m
+ *  sh_degree      0..3
+ *  n              1 .. 2^31-1
+ * Errors: VIS_ERR_INVALID_ARG for null/misaligned pointers or bad sizes. */
+VIS_API vis_status vis_scene_upload(const float* means, const float* log_scales, const float* quats,
+                            const float* opacity_logits, const float* sh, int sh_degree,
+                            int64_t n, vis_scene_t* out);
+VIS_API void vis_scene_destroy(vis_scene_t scene);
+
+/* Bytes of workspace vis_render needs for n Gaussians at W x H holding up to
+ * key_capacity (tile, Gaussian) keys (one per tile a splat's rectangle touches). */
+VIS_API vis_status vis_workspace_size(int64_t n, int W, int H, int64_t key_capacity,
+                              const vis_render_opts* opts, size_t* bytes);
+
+/* Layout of a workspace of ws_bytes for (n, W, H, opts); key_capacity is the
+ * largest that fits. VIS_ERR_INVALID_ARG if ws_bytes cannot hold even one key. */
+VIS_API vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes,
+                                const vis_render_opts* opts, vis_ws_layout* out);
+
+/* Forward render of one view (section 3.2 Eqs. 1-3; Algorithm 1 per-frame path).
+ *  bg         host float[3] background colour
+ *  out_rgb    device float[3][H][W] (planar)
+ *  out_alpha  device float[H][W] = 1 - final transmittance
+ *  ws         device workspace of ws_bytes (>= vis_workspace_size for the keys produced);
+ *             it keeps the intermediates that vis_render_backward reads
+ *  stream     cudaStream_t (NULL = legacy default stream)
+ * Device-side errors are reported by vis_check(). */
+VIS_API vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                      float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
+                      const vis_render_opts* opts, void* stream);
+
+/* Synchronise `stream`, read the status block of `ws`, and return VIS_OK,
+ * VIS_ERR_CAPACITY or VIS_ERR_TIMEOUT. num_keys (host, may be NULL) receives the
+ * number of keys the last render produced (the capacity a retry needs). */
+VIS_API vis_status vis_check(const void* ws, void* stream, int64_t* num_keys);
+
+/* Adjoint of vis_render (section 3.2: the splatting formulation is differentiable
+ * in all Gaussian parameters). Must follow a vis_render with the same scene
+ * contents, camera, size, bg, opts and workspace.
+ *  d_rgb, d_alpha   device float[3][H][W], float[H][W]: dL/d out_rgb, dL/d out_alpha
+ *  d_means .. d_sh  device outputs shaped like the scene arrays; overwritten
+ * Decision sets (culling, the 3-sigma cut, the alpha_min skip, the early stop)
+ * are held fixed; the alpha_max clamp and the colour clamp at 0 pass no gradient. */
+VIS_API vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, int H,
+                               const float bg[3], const float* d_rgb, const float* d_alpha,
+                               void* ws, size_t ws_bytes, const vis_render_opts* opts,
+                               float* d_means, float* d_log_scales, float* d_quats,
+                               float* d_opacity_logits, float* d_sh, void* stream);
+
+/* Stable LSD radix sort of (key, value) pairs on the device: the sort stage of the
+ * renderer (Algorithm 1, "Radix Sort"; section 3.4, GPU sorting) exposed on its own.
+ *  keys_in, vals_in    device uint64[m], uint32[m] (not modified)
+ *  keys_out, vals_out  device uint64[m], uint32[m]
+ *  key_bits            only bits [0, key_bits) take part (1..64); higher bits must be 0
+ *  ws                  device workspace of vis_sort_workspace_size(m, key_bits) bytes
+ * Equal keys keep their input order. */
+VIS_API vis_status vis_sort_workspace_size(int64_t m, int key_bits, size_t* bytes);
+VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                          uint32_t* vals_out, int64_t m, int key_bits, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* Per-stage timing of vis_render (tracing; the paper times its frame by stages,
+ * Table 1 "Sort" vs "Prep.+Draw"). Between vis_profile_begin and vis_profile_end,
+ * every vis_render records CUDA events on its stream between its stages, for up
+ * to 1024 renders. vis_profile_end synchronises those events and returns, per
+ * stage, the summed milliseconds over the recorded renders, in this order:
+ *   0 clear, 1 preprocess, 2 scan + key duplication, 3 sort histogram,
+ *   4 sort digit passes (all of them), 5 tile ranges, 6 composite.
+ *  stage_ms   host double[max_stages]
+ *  n_stages   host out: number of stages written (7)
+ *  n_renders  host out: renders summed
+ *  n_passes   host out: radix passes per render (of the last render)
+ * Profiling is per process and not thread safe. */
+VIS_API vis_status vis_profile_begin(void);
+VIS_API vis_status vis_profile_end(double* stage_ms, int max_stages, int* n_stages, int* n_renders,
+                                   int* n_passes);
+
+/* Thread-local description of the last error (empty string if none). */
+VIS_API const char* vis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VIS_H */

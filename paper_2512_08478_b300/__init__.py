@@ -1,0 +1,333 @@
+"""B300-native 3D Gaussian Splatting rasterizer (sm_103a CUDA behind a C ABI).
+
+This module is a thin ctypes binding over ``libvis.so`` (see include/vis.h): it
+marshals torch tensors to device pointers and the current CUDA stream; every step
+of the render runs in the library's kernels. There is no CPU path: if the
+library is missing or no CUDA device is present, calls raise.
+
+Entry points with the C names: vis_scene_upload, vis_workspace_size,
+vis_workspace_layout, vis_render, vis_check, vis_render_backward,
+vis_sort_workspace_size, vis_sort_pairs, vis_default_opts, vis_last_error.
+Convenience layer: ``Scene``, ``Workspace``, ``render`` (differentiable through
+``torch.autograd``) and ``sort_pairs``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libvis.so"
+_lib = None
+
+VIS_OK, VIS_ERR_INVALID_ARG, VIS_ERR_CUDA, VIS_ERR_CAPACITY, VIS_ERR_TIMEOUT, VIS_ERR_UNSUPPORTED = range(6)
+_STATUS = {0: "VIS_OK", 1: "VIS_ERR_INVALID_ARG", 2: "VIS_ERR_CUDA", 3: "VIS_ERR_CAPACITY",
+           4: "VIS_ERR_TIMEOUT", 5: "VIS_ERR_UNSUPPORTED"}
+
+
+class VisError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vis_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("near_z", C.c_float)]
+
+
+class vis_render_opts(C.Structure):
+    _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
+
+
+class vis_ws_layout(C.Structure):
+    _fields_ = [("total_bytes", C.c_size_t), ("key_capacity", C.c_int64), ("tiles_x", C.c_int),
+                ("tiles_y", C.c_int), ("sort_passes", C.c_int), ("sorted_buffer", C.c_int),
+                ("off_ctrl", C.c_size_t), ("off_rec", C.c_size_t), ("off_depth", C.c_size_t),
+                ("off_rect", C.c_size_t), ("off_touched", C.c_size_t), ("off_keys", C.c_size_t * 2),
+                ("off_vals", C.c_size_t * 2), ("off_ranges", C.c_size_t), ("off_tfinal", C.c_size_t),
+                ("off_last", C.c_size_t), ("off_g2", C.c_size_t)]
+
+
+_P = C.c_void_p
+
+
+def lib():
+    """Load libvis.so (built in-tree by paper_2512_08478_b300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2512_08478_b300.build`")
+        L = C.CDLL(str(LIB_PATH))
+        sig = {
+            "vis_default_opts": (None, [C.POINTER(vis_render_opts)]),
+            "vis_last_error": (C.c_char_p, []),
+            "vis_scene_upload": (C.c_int, [_P, _P, _P, _P, _P, C.c_int, C.c_int64, C.POINTER(_P)]),
+            "vis_scene_destroy": (None, [_P]),
+            "vis_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.c_int, C.c_int64,
+                                             C.POINTER(vis_render_opts), C.POINTER(C.c_size_t)]),
+            "vis_workspace_layout": (C.c_int, [C.c_int64, C.c_int, C.c_int, C.c_size_t,
+                                               C.POINTER(vis_render_opts), C.POINTER(vis_ws_layout)]),
+            "vis_render": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int, C.POINTER(C.c_float),
+                                     _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts), _P]),
+            "vis_check": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
+            "vis_render_backward": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int,
+                                              C.POINTER(C.c_float), _P, _P, _P, C.c_size_t,
+                                              C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
+            "vis_sort_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
+            "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ok(status):
+    if status != VIS_OK:
+        raise VisError(status, lib().vis_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return _P(t.data_ptr())
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+def make_camera(cam) -> vis_camera:
+    """From a synth.Camera (or anything with R, t, fx, fy, cx, cy, near)."""
+    c = vis_camera()
+    R = [float(v) for v in cam.R.reshape(-1)]
+    t = [float(v) for v in cam.t.reshape(-1)]
+    c.R[:] = R
+    c.t[:] = t
+    c.fx, c.fy, c.cx, c.cy, c.near_z = (float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy),
+                                        float(cam.near))
+    return c
+
+
+def make_opts(**kw) -> vis_render_opts:
+    o = vis_render_opts()
+    lib().vis_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _opts_ref(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, dict):
+        opts = make_opts(**opts)
+    return C.byref(opts)
+
+
+def _bg(bg):
+    return (C.c_float * 3)(*[float(v) for v in bg])
+
+
+# ----------------------------------------------------------------------------------
+# C-named entry points (argument marshalling only)
+# ----------------------------------------------------------------------------------
+
+def vis_scene_upload(means, log_scales, quats, opacity_logits, sh, sh_degree):
+    h = _P()
+    _ok(lib().vis_scene_upload(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity_logits), _ptr(sh),
+                               int(sh_degree), int(means.shape[0]), C.byref(h)))
+    return h
+
+
+def vis_workspace_size(n, W, H, key_capacity, opts=None):
+    b = C.c_size_t()
+    _ok(lib().vis_workspace_size(int(n), int(W), int(H), int(key_capacity), _opts_ref(opts), C.byref(b)))
+    return b.value
+
+
+def vis_workspace_layout(n, W, H, ws_bytes, opts=None) -> vis_ws_layout:
+    L = vis_ws_layout()
+    _ok(lib().vis_workspace_layout(int(n), int(W), int(H), int(ws_bytes), _opts_ref(opts), C.byref(L)))
+    return L
+
+
+def vis_render(scene_handle, cam, W, H, bg, out_rgb, out_alpha, ws, opts=None, stream=None):
+    c = cam if isinstance(cam, vis_camera) else make_camera(cam)
+    _ok(lib().vis_render(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(out_rgb), _ptr(out_alpha),
+                         _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts), _stream(stream)))
+
+
+def vis_check(ws, stream=None):
+    """Synchronise the stream; return the key count, raise VisError on a device error."""
+    m = C.c_int64()
+    st = lib().vis_check(_ptr(ws), _stream(stream), C.byref(m))
+    if st != VIS_OK:
+        err = VisError(st, lib().vis_last_error().decode())
+        err.num_keys = m.value
+        raise err
+    return m.value
+
+
+def vis_render_backward(scene_handle, cam, W, H, bg, d_rgb, d_alpha, ws, grads, opts=None, stream=None):
+    c = cam if isinstance(cam, vis_camera) else make_camera(cam)
+    _ok(lib().vis_render_backward(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(d_rgb), _ptr(d_alpha),
+                                  _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts),
+                                  *[_ptr(grads[k]) for k in ("means", "log_scales", "quats",
+                                                             "opacity_logits", "sh")], _stream(stream)))
+
+
+def vis_sort_workspace_size(m, key_bits):
+    b = C.c_size_t()
+    _ok(lib().vis_sort_workspace_size(int(m), int(key_bits), C.byref(b)))
+    return b.value
+
+
+def vis_sort_pairs(keys_in, vals_in, keys_out, vals_out, key_bits, ws, stream=None):
+    _ok(lib().vis_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), int(keys_in.numel()),
+                             int(key_bits), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def vis_last_error():
+    return lib().vis_last_error().decode()
+
+
+# ----------------------------------------------------------------------------------
+# Convenience layer
+# ----------------------------------------------------------------------------------
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+class Scene:
+    """Borrowed device tensors of one Gaussian asset plus its C handle.
+
+    The tensors must stay alive and unmoved while the Scene is used; they may be
+    rewritten in place between frames.
+    """
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh, sh_degree):
+        torch = _torch()
+        t = dict(means=means, log_scales=log_scales, quats=quats, opacity_logits=opacity_logits, sh=sh)
+        for k, v in t.items():
+            if not (v.is_cuda and v.dtype == torch.float32 and v.is_contiguous()):
+                raise ValueError(f"{k} must be a contiguous float32 CUDA tensor")
+        self.tensors = t
+        self.sh_degree = int(sh_degree)
+        self.n = int(means.shape[0])
+        self.handle = vis_scene_upload(means, log_scales, quats, opacity_logits, sh, sh_degree)
+
+    @classmethod
+    def from_numpy(cls, scene, device="cuda"):
+        torch = _torch()
+        ts = {k: torch.from_numpy(scene[k]).to(device).contiguous() for k in FIELDS}
+        return cls(**ts, sh_degree=scene["sh_degree"])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.vis_scene_destroy(h)
+            self.handle = None
+
+
+class Workspace:
+    """A caller-owned device workspace, grown on a capacity error."""
+
+    def __init__(self, n, W, H, key_capacity=None, opts=None, device="cuda"):
+        self.n, self.W, self.H, self.opts = n, W, H, opts
+        cap = key_capacity if key_capacity is not None else max(1 << 16, 4 * n)
+        self._alloc(cap, device)
+
+    def _alloc(self, cap, device="cuda"):
+        torch = _torch()
+        nbytes = vis_workspace_size(self.n, self.W, self.H, cap, self.opts)
+        self.buf = torch.empty((nbytes + 15) // 16 * 16, dtype=torch.uint8, device=device)
+        self.key_capacity = cap
+
+    def grow(self, needed):
+        self._alloc(int(needed * 1.25) + 1024, self.buf.device)
+
+    def layout(self) -> vis_ws_layout:
+        return vis_workspace_layout(self.n, self.W, self.H, self.buf.numel(), self.opts)
+
+
+def _render_checked(scene, cam, W, H, bg, ws, opts, stream=None):
+    torch = _torch()
+    out_rgb = torch.empty((3, H, W), dtype=torch.float32, device=ws.buf.device)
+    out_alpha = torch.empty((H, W), dtype=torch.float32, device=ws.buf.device)
+    for _ in range(2):
+        vis_render(scene.handle, cam, W, H, bg, out_rgb, out_alpha, ws.buf, opts, stream)
+        try:
+            vis_check(ws.buf, stream)
+            return out_rgb, out_alpha
+        except VisError as e:
+            if e.status != VIS_ERR_CAPACITY:
+                raise
+            ws.grow(e.num_keys)
+    raise VisError(VIS_ERR_CAPACITY, "workspace growth did not converge")
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class RenderFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, scene, cam, W, H, bg, ws, opts, means, log_scales, quats, opacity_logits, sh):
+            rgb, alpha = _render_checked(scene, cam, W, H, bg, ws, opts)
+            ctx.scene, ctx.cam, ctx.W, ctx.H, ctx.bg, ctx.ws, ctx.opts = scene, cam, W, H, bg, ws, opts
+            return rgb, alpha
+
+        @staticmethod
+        def backward(ctx, d_rgb, d_alpha):
+            sc = ctx.scene
+            d_rgb = (d_rgb if d_rgb is not None else torch.zeros((3, ctx.H, ctx.W), device=ctx.ws.buf.device))
+            d_alpha = (d_alpha if d_alpha is not None else torch.zeros((ctx.H, ctx.W), device=ctx.ws.buf.device))
+            d_rgb = d_rgb.contiguous().float()
+            d_alpha = d_alpha.contiguous().float()
+            grads = {k: torch.empty_like(sc.tensors[k]) for k in FIELDS}
+            vis_render_backward(sc.handle, ctx.cam, ctx.W, ctx.H, ctx.bg, d_rgb, d_alpha, ctx.ws.buf, grads,
+                                ctx.opts)
+            return (None, None, None, None, None, None, None, grads["means"], grads["log_scales"],
+                    grads["quats"], grads["opacity_logits"], grads["sh"])
+
+    return RenderFn
+
+
+_RENDER_FN = None
+
+
+def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = None, opts=None):
+    """Render one view; differentiable w.r.t. the scene tensors (if they require grad).
+
+    Returns (rgb [3,H,W], alpha [H,W]). The workspace keeps the forward's
+    intermediates for the backward; do not reuse it for another render before
+    calling backward.
+    """
+    global _RENDER_FN
+    if _RENDER_FN is None:
+        _RENDER_FN = _make_autograd()
+    if ws is None:
+        ws = Workspace(scene.n, W, H, opts=opts)
+    t = scene.tensors
+    return _RENDER_FN.apply(scene, cam, W, H, tuple(bg), ws, opts, t["means"], t["log_scales"], t["quats"],
+                            t["opacity_logits"], t["sh"])
+
+
+def sort_pairs(keys, vals, key_bits=64):
+    """Stable device sort of uint64 keys (int64 tensor) with uint32 values (int32 tensor)."""
+    torch = _torch()
+    m = keys.numel()
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    ws = torch.empty(max(16, vis_sort_workspace_size(m, key_bits)), dtype=torch.uint8, device=keys.device)
+    vis_sort_pairs(keys, vals, ko, vo, key_bits, ws)
+    return ko, vo

@@ -1,0 +1,465 @@
+// C ABI of libvis (declared in include/vis.h): argument validation, workspace
+// layout, and the per-frame launch sequence of Algorithm 1 re-planned for one GPU:
+//   clear status/histograms -> preprocess -> scan + duplicate keys -> radix sort
+//   -> tile ranges -> composite            (vis_render)
+//   composite adjoint -> preprocess adjoint (vis_render_backward)
+// Nothing here allocates device memory; every launch goes on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "vis_internal.cuh"
+
+struct vis_scene {
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* logits;
+    const float* sh;
+    int deg;
+    int64_t n;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vis_status fail(vis_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+vis_status cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return fail(VIS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return VIS_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+vis_render_opts resolve_opts(const vis_render_opts* o) {
+    vis_render_opts r;
+    vis_default_opts(&r);
+    if (o) r = *o;
+    if (r.tile == 0) r.tile = 16;
+    if (r.digit_bits == 0) r.digit_bits = vis::kRadixBits;
+    return r;
+}
+
+vis_status check_opts(const vis_render_opts& o) {
+    if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
+    if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
+    if (!(o.dilation >= 0.f) || !std::isfinite(o.dilation)) return fail(VIS_ERR_INVALID_ARG, "dilation must be finite and >= 0");
+    if (!(o.alpha_min > 0.f && o.alpha_min < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_min must be in (0, 1)");
+    if (!(o.alpha_max > 0.f && o.alpha_max < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_max must be in (0, 1)");
+    if (!(o.t_stop >= 0.f && o.t_stop < 1.f)) return fail(VIS_ERR_INVALID_ARG, "t_stop must be in [0, 1)");
+    return VIS_OK;
+}
+
+vis_status check_size(int64_t n, int W, int H) {
+    if (n < 1 || n > 0x7fffffffLL) return fail(VIS_ERR_INVALID_ARG, "n must be in [1, 2^31-1] (got %lld)", (long long)n);
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return fail(VIS_ERR_INVALID_ARG, "W, H must be in [1, 16384] (got %d x %d)", W, H);
+    return VIS_OK;
+}
+
+vis_status check_camera(const vis_camera* c) {
+    if (!c) return fail(VIS_ERR_INVALID_ARG, "camera is null");
+    const float* f = reinterpret_cast<const float*>(c);
+    for (int k = 0; k < 17; ++k)
+        if (!std::isfinite(f[k])) return fail(VIS_ERR_INVALID_ARG, "camera has a non-finite value");
+    if (!(c->fx > 0.f && c->fy > 0.f)) return fail(VIS_ERR_INVALID_ARG, "fx, fy must be > 0");
+    if (!(c->near_z > 0.f)) return fail(VIS_ERR_INVALID_ARG, "near_z must be > 0");
+    return VIS_OK;
+}
+
+// Preprocess parameters for one view (camera centre and guard limits in double).
+vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int H, const vis::Layout& L,
+                            const vis_render_opts& o) {
+    vis::PrepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.means = s->means; p.log_scales = s->log_scales; p.quats = s->quats; p.logits = s->logits; p.sh = s->sh;
+    p.deg = s->deg; p.n = (int)s->n;
+    for (int k = 0; k < 9; ++k) p.R[k] = c->R[k];
+    for (int k = 0; k < 3; ++k) p.t[k] = c->t[k];
+    p.fx = c->fx; p.fy = c->fy; p.cx = c->cx; p.cy = c->cy; p.near_z = c->near_z;
+    for (int j = 0; j < 3; ++j) {
+        double a = 0;
+        for (int r = 0; r < 3; ++r) a -= (double)c->R[3 * r + j] * (double)c->t[r];
+        p.cam_pos[j] = (float)a;
+    }
+    p.limx = (float)(1.3 * (W / (2.0 * c->fx)));
+    p.limy = (float)(1.3 * (H / (2.0 * c->fy)));
+    p.W = W; p.H = H; p.tile = L.tile; p.tiles_x = L.tiles_x; p.tiles_y = L.tiles_y;
+    p.dilation = o.dilation; p.alpha_min = o.alpha_min;
+    vis::sh_constants(p.shc);
+    return p;
+}
+
+// ---- per-stage profiling (vis_profile_begin / vis_profile_end) ----
+constexpr int kProfStages = 7;
+constexpr int kProfRing = 1024;
+struct Profiler {
+    bool on = false;
+    int count = 0;
+    int passes = 0;
+    cudaEvent_t ev[kProfRing][kProfStages + 1];
+    bool created = false;
+};
+Profiler g_prof;
+
+// Record event `k` (0 = start, k = end of stage k-1) of the current render.
+void prof_mark(int k, cudaStream_t stream) {
+    if (!g_prof.on || g_prof.count >= kProfRing) return;
+    cudaEventRecord(g_prof.ev[g_prof.count][k], stream);
+}
+
+}  // namespace
+
+namespace vis {
+
+// K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!); the real SH polynomials in (x, y, z)
+// on the unit sphere (Condon-Shortley phase) are products of these with
+// (-1)^m d^m P_l/dz^m and Re/Im (x + i y)^m, so the constants below are:
+//   [0] K_1^0             [1] sqrt2 K_1^1
+//   [2] K_2^0 / 2         [3] 3 sqrt2 K_2^1     [4] 3 sqrt2 K_2^2
+//   [5] K_3^0 / 2         [6] 3/2 sqrt2 K_3^1   [7] 15 sqrt2 K_3^2   [8] 15 sqrt2 K_3^3
+//   [9] K_0^0
+void sh_constants(float out[12]) {
+    auto fact = [](int n) { double f = 1; for (int k = 2; k <= n; ++k) f *= k; return f; };
+    const double pi = 3.14159265358979323846;
+    auto K = [&](int l, int m) { return std::sqrt((2.0 * l + 1.0) / (4.0 * pi) * fact(l - m) / fact(l + m)); };
+    const double r2 = std::sqrt(2.0);
+    out[0] = (float)K(1, 0);
+    out[1] = (float)(r2 * K(1, 1));
+    out[2] = (float)(K(2, 0) / 2.0);
+    out[3] = (float)(3.0 * r2 * K(2, 1));
+    out[4] = (float)(3.0 * r2 * K(2, 2));
+    out[5] = (float)(K(3, 0) / 2.0);
+    out[6] = (float)(1.5 * r2 * K(3, 1));
+    out[7] = (float)(15.0 * r2 * K(3, 2));
+    out[8] = (float)(15.0 * r2 * K(3, 3));
+    out[9] = (float)K(0, 0);
+    out[10] = out[11] = 0.f;
+}
+
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap) {
+    Layout L;
+    L.n = n; L.W = W; L.H = H; L.tile = tile;
+    L.tiles_x = (W + tile - 1) / tile;
+    L.tiles_y = (H + tile - 1) / tile;
+    L.ntiles = (int64_t)L.tiles_x * L.tiles_y;
+    L.tile_bits = ceil_log2(L.ntiles);
+    L.key_bits = 32 + L.tile_bits;
+    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
+    L.cap = cap;
+    L.prep_blocks = (n + kPrepThreads - 1) / kPrepThreads;
+    L.sort_parts = (cap + kSortPartition - 1) / kSortPartition;
+    L.sorted_buffer = L.passes & 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    // cleared every frame: status block, histograms, look-back words, tile ranges
+    L.zero_begin = off;
+    L.off_ctrl = take(sizeof(Ctrl));
+    L.off_hist = take(sizeof(uint32_t) * kMaxPasses * kRadix);
+    L.off_lookback = take(sizeof(uint32_t) * (size_t)L.passes * L.sort_parts * kRadix);
+    L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
+    L.zero_end = off;
+    L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
+    L.off_depth = take(sizeof(float) * (size_t)n);
+    L.off_rect = take(sizeof(uint2) * (size_t)n);
+    L.off_touched = take(sizeof(uint32_t) * (size_t)n);
+    L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_keys[0] = take(sizeof(uint64_t) * (size_t)cap);
+    L.off_keys[1] = take(sizeof(uint64_t) * (size_t)cap);
+    L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
+    L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
+    L.off_tfinal = take(sizeof(float) * (size_t)W * H);
+    L.off_last = take(sizeof(int32_t) * (size_t)W * H);
+    L.off_g2 = take(sizeof(float) * 9 * (size_t)n);
+    L.total = off;
+    return L;
+}
+
+int64_t capacity_for(int64_t n, int W, int H, int tile, size_t ws_bytes) {
+    if (make_layout(n, W, H, tile, 1).total > ws_bytes) return 0;
+    int64_t lo = 1, hi = kMaxKeys;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (make_layout(n, W, H, tile, mid).total <= ws_bytes) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace vis
+
+extern "C" {
+
+void vis_default_opts(vis_render_opts* o) {
+    if (!o) return;
+    o->tile = 16;
+    o->digit_bits = vis::kRadixBits;
+    o->dilation = 0.3f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->t_stop = 1e-4f;
+}
+
+const char* vis_last_error(void) { return g_err.c_str(); }
+
+vis_status vis_scene_upload(const float* means, const float* log_scales, const float* quats,
+                            const float* opacity_logits, const float* sh, int sh_degree, int64_t n,
+                            vis_scene_t* out) {
+    if (!out) return fail(VIS_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (sh_degree < 0 || sh_degree > 3) return fail(VIS_ERR_INVALID_ARG, "sh_degree must be 0..3 (got %d)", sh_degree);
+    if (n < 1 || n > 0x7fffffffLL) return fail(VIS_ERR_INVALID_ARG, "n must be in [1, 2^31-1] (got %lld)", (long long)n);
+    const void* ptrs[5] = {means, log_scales, quats, opacity_logits, sh};
+    const char* names[5] = {"means", "log_scales", "quats", "opacity_logits", "sh"};
+    for (int k = 0; k < 5; ++k) {
+        if (!ptrs[k]) return fail(VIS_ERR_INVALID_ARG, "%s is null", names[k]);
+        if (!aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "%s is not 16-byte aligned", names[k]);
+    }
+    vis_scene* s = new (std::nothrow) vis_scene;
+    if (!s) return fail(VIS_ERR_INVALID_ARG, "out of host memory");
+    s->means = means; s->log_scales = log_scales; s->quats = quats; s->logits = opacity_logits; s->sh = sh;
+    s->deg = sh_degree; s->n = n;
+    *out = s;
+    g_err.clear();
+    return VIS_OK;
+}
+
+void vis_scene_destroy(vis_scene_t s) { delete s; }
+
+vis_status vis_workspace_size(int64_t n, int W, int H, int64_t key_capacity, const vis_render_opts* opts,
+                              size_t* bytes) {
+    if (!bytes) return fail(VIS_ERR_INVALID_ARG, "bytes is null");
+    vis_status st = check_size(n, W, H);
+    if (st) return st;
+    const vis_render_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    if (key_capacity < 1 || key_capacity > (int64_t)vis::kMaxKeys)
+        return fail(VIS_ERR_INVALID_ARG, "key_capacity must be in [1, 2^30-1]");
+    *bytes = vis::make_layout(n, W, H, o.tile, key_capacity).total;
+    return VIS_OK;
+}
+
+vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const vis_render_opts* opts,
+                                vis_ws_layout* out) {
+    if (!out) return fail(VIS_ERR_INVALID_ARG, "out is null");
+    vis_status st = check_size(n, W, H);
+    if (st) return st;
+    const vis_render_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    const int64_t cap = vis::capacity_for(n, W, H, o.tile, ws_bytes);
+    if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
+    const vis::Layout L = vis::make_layout(n, W, H, o.tile, cap);
+    out->total_bytes = L.total;
+    out->key_capacity = L.cap;
+    out->tiles_x = L.tiles_x; out->tiles_y = L.tiles_y;
+    out->sort_passes = L.passes; out->sorted_buffer = L.sorted_buffer;
+    out->off_ctrl = L.off_ctrl; out->off_rec = L.off_rec; out->off_depth = L.off_depth;
+    out->off_rect = L.off_rect; out->off_touched = L.off_touched;
+    out->off_keys[0] = L.off_keys[0]; out->off_keys[1] = L.off_keys[1];
+    out->off_vals[0] = L.off_vals[0]; out->off_vals[1] = L.off_vals[1];
+    out->off_ranges = L.off_ranges; out->off_tfinal = L.off_tfinal; out->off_last = L.off_last;
+    out->off_g2 = L.off_g2;
+    return VIS_OK;
+}
+
+static vis_status prepare(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], void* ws,
+                          size_t ws_bytes, const vis_render_opts* opts, vis_render_opts* o, vis::Layout* L) {
+    if (!scene) return fail(VIS_ERR_INVALID_ARG, "scene is null");
+    vis_status st = check_size(scene->n, W, H);
+    if (st) return st;
+    if ((st = check_camera(cam))) return st;
+    if (!bg) return fail(VIS_ERR_INVALID_ARG, "bg is null");
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(bg[k])) return fail(VIS_ERR_INVALID_ARG, "bg is not finite");
+    *o = resolve_opts(opts);
+    if ((st = check_opts(*o))) return st;
+    if (!ws || !aligned16(ws)) return fail(VIS_ERR_INVALID_ARG, "workspace is null or not 16-byte aligned");
+    const int64_t cap = vis::capacity_for(scene->n, W, H, o->tile, ws_bytes);
+    if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
+    *L = vis::make_layout(scene->n, W, H, o->tile, cap);
+    return VIS_OK;
+}
+
+vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], float* out_rgb,
+                      float* out_alpha, void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
+    vis_render_opts o;
+    vis::Layout L;
+    vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
+    if (st) return st;
+    if (!out_rgb || !out_alpha || !aligned16(out_rgb) || !aligned16(out_alpha))
+        return fail(VIS_ERR_INVALID_ARG, "out_rgb / out_alpha null or not 16-byte aligned");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    char* w = static_cast<char*>(ws);
+    const vis::PrepParams p = make_params(scene, cam, W, H, L, o);
+    prof_mark(0, stream);
+    if ((st = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, stream), "clear workspace")))
+        return st;
+    prof_mark(1, stream);
+    vis::launch_preprocess(p, L, w, stream);
+    prof_mark(2, stream);
+    vis::launch_scan_and_duplicate(L, w, scene->n, stream);
+    prof_mark(3, stream);
+    vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark : nullptr, 4);
+    prof_mark(5, stream);
+    vis::launch_ranges(L, w, stream);
+    prof_mark(6, stream);
+    vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, out_rgb, out_alpha, stream);
+    prof_mark(7, stream);
+    if (g_prof.on && g_prof.count < kProfRing) { ++g_prof.count; g_prof.passes = L.passes; }
+    if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
+    if (!ws) return fail(VIS_ERR_INVALID_ARG, "workspace is null");
+    vis::Ctrl c;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    vis_status st = cuda_check(cudaStreamSynchronize(stream), "synchronize");
+    if (st) return st;
+    if ((st = cuda_check(cudaMemcpy(&c, ws, sizeof(c), cudaMemcpyDeviceToHost), "read status"))) return st;
+    if (num_keys) *num_keys = c.num_keys;
+    if (c.error & vis::kErrCapacity)
+        return fail(VIS_ERR_CAPACITY, "%u keys exceed the workspace capacity", c.num_keys);
+    if (c.error & vis::kErrTimeout) return fail(VIS_ERR_TIMEOUT, "a device spin wait timed out");
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                               const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
+                               const vis_render_opts* opts, float* d_means, float* d_log_scales, float* d_quats,
+                               float* d_opacity_logits, float* d_sh, void* stream_) {
+    vis_render_opts o;
+    vis::Layout L;
+    vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
+    if (st) return st;
+    const void* ptrs[7] = {d_rgb, d_alpha, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+    for (int k = 0; k < 7; ++k)
+        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "gradient buffer %d null or misaligned", k);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    const vis::PrepParams p = make_params(scene, cam, W, H, L, o);
+    vis::launch_backward(p, L, static_cast<char*>(ws), bg, o.alpha_min, o.alpha_max, o.t_stop, d_rgb, d_alpha,
+                         d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, stream);
+    if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_profile_begin(void) {
+    if (!g_prof.created) {
+        for (int r = 0; r < kProfRing; ++r)
+            for (int k = 0; k <= kProfStages; ++k) {
+                vis_status st = cuda_check(cudaEventCreate(&g_prof.ev[r][k]), "create profiling events");
+                if (st) return st;
+            }
+        g_prof.created = true;
+    }
+    g_prof.on = true;
+    g_prof.count = 0;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_profile_end(double* stage_ms, int max_stages, int* n_stages, int* n_renders, int* n_passes) {
+    if (!g_prof.on) return fail(VIS_ERR_INVALID_ARG, "profiling was not begun");
+    g_prof.on = false;
+    const int n = g_prof.count < kProfStages ? g_prof.count : kProfStages;
+    (void)n;
+    double sum[kProfStages] = {0};
+    for (int r = 0; r < g_prof.count; ++r) {
+        vis_status st = cuda_check(cudaEventSynchronize(g_prof.ev[r][kProfStages]), "profiling sync");
+        if (st) return st;
+        for (int k = 0; k < kProfStages; ++k) {
+            float ms = 0.f;
+            if ((st = cuda_check(cudaEventElapsedTime(&ms, g_prof.ev[r][k], g_prof.ev[r][k + 1]), "elapsed")))
+                return st;
+            sum[k] += ms;
+        }
+    }
+    const int w = max_stages < kProfStages ? max_stages : kProfStages;
+    for (int k = 0; k < w && stage_ms; ++k) stage_ms[k] = sum[k];
+    if (n_stages) *n_stages = w;
+    if (n_renders) *n_renders = g_prof.count;
+    if (n_passes) *n_passes = g_prof.passes;
+    g_err.clear();
+    return VIS_OK;
+}
+
+// Standalone sort workspace: status block, histograms, look-back words, one
+// ping-pong key/value buffer.
+static size_t sort_ws_layout(int64_t m, int passes, size_t* off_hist, size_t* off_lb, size_t* off_k, size_t* off_v,
+                             int64_t* parts) {
+    *parts = (m + vis::kSortPartition - 1) / vis::kSortPartition;
+    size_t off = align_up(sizeof(vis::Ctrl), 256);
+    *off_hist = off; off = align_up(off + sizeof(uint32_t) * vis::kMaxPasses * vis::kRadix, 256);
+    *off_lb = off; off = align_up(off + sizeof(uint32_t) * (size_t)passes * (*parts) * vis::kRadix, 256);
+    const size_t zero_end = off;
+    *off_k = off; off = align_up(off + sizeof(uint64_t) * (size_t)m, 256);
+    *off_v = off; off = align_up(off + sizeof(uint32_t) * (size_t)m, 256);
+    (void)zero_end;
+    return off;
+}
+
+vis_status vis_sort_workspace_size(int64_t m, int key_bits, size_t* bytes) {
+    if (!bytes) return fail(VIS_ERR_INVALID_ARG, "bytes is null");
+    if (m < 0 || m > (int64_t)vis::kMaxKeys) return fail(VIS_ERR_INVALID_ARG, "m must be in [0, 2^30-1]");
+    if (key_bits < 1 || key_bits > 64) return fail(VIS_ERR_INVALID_ARG, "key_bits must be in [1, 64]");
+    const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
+    size_t a, b, c, d;
+    int64_t parts;
+    *bytes = sort_ws_layout(m, passes, &a, &b, &c, &d, &parts);
+    return VIS_OK;
+}
+
+vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
+                          int64_t m, int key_bits, void* ws, size_t ws_bytes, void* stream_) {
+    size_t need = 0;
+    vis_status st = vis_sort_workspace_size(m, key_bits, &need);
+    if (st) return st;
+    if (!ws || !aligned16(ws) || ws_bytes < need)
+        return fail(VIS_ERR_INVALID_ARG, "sort workspace null, misaligned or smaller than %zu bytes", need);
+    if (m == 0) { g_err.clear(); return VIS_OK; }
+    const void* ptrs[4] = {keys_in, vals_in, keys_out, vals_out};
+    for (int k = 0; k < 4; ++k)
+        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "sort buffer %d null or misaligned", k);
+    if ((const void*)keys_in == (const void*)keys_out || (const void*)vals_in == (const void*)vals_out)
+        return fail(VIS_ERR_INVALID_ARG, "sort input and output must not alias");
+    const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
+    size_t off_hist, off_lb, off_k, off_v;
+    int64_t parts;
+    sort_ws_layout(m, passes, &off_hist, &off_lb, &off_k, &off_v, &parts);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    char* w = static_cast<char*>(ws);
+    vis::Ctrl* ctrl = reinterpret_cast<vis::Ctrl*>(w);
+    if ((st = cuda_check(cudaMemsetAsync(w, 0, off_k, stream), "clear sort workspace"))) return st;
+    vis::launch_set_u32(&ctrl->num_keys, (uint32_t)m, stream);
+    vis::launch_sort_generic(keys_in, vals_in, keys_out, vals_out, reinterpret_cast<uint64_t*>(w + off_k),
+                             reinterpret_cast<uint32_t*>(w + off_v), m, &ctrl->num_keys, passes,
+                             reinterpret_cast<uint32_t*>(w + off_hist), reinterpret_cast<uint32_t*>(w + off_lb),
+                             parts, ctrl, stream);
+    if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
+    g_err.clear();
+    return VIS_OK;
+}
+
+}  // extern "C"

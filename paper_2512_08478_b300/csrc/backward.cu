@@ -1,0 +1,349 @@
+// K7 -- adjoint of the render (section 3.2: the splatting formulation is
+// differentiable in every Gaussian parameter).
+//
+// K7a composite_backward_kernel: one CTA per tile, one thread per pixel, walking
+// the tile's sorted range back to front in shared-memory chunks, starting from the
+// final transmittance and the last contributor the forward stored. Per-splat
+// alphas are recomputed (with the forward's exact arithmetic, so every skip and cut
+// decision is the same) rather than stored; T before each splat is recovered as
+// T / (1 - alpha). With S the colour behind a splat, normalised by the
+// transmittance after it (S <- rgb a + (1 - a) S walking backwards):
+//   dC/drgb = a T,  dC/da = T (rgb - S) - T_final bg / (1 - a),  dA/da = T_final / (1 - a).
+// The nine screen-space gradients of a splat (u, v, conic a/b/c, opacity, rgb) are
+// summed over the warp with shuffles and added to global memory by one lane.
+//
+// K7b preprocess_backward_kernel: one thread per Gaussian chains those through
+// conic = S^-1, S = A A^T + dil I with A = J W R_q diag(s), the projection, the
+// quaternion normalisation, exp, sigmoid and the SH basis.
+#include "splat_eval.cuh"
+
+namespace vis {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(TILE * TILE)
+composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                          const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0,
+                          float bg1, float bg2, float alpha_min, float alpha_max,
+                          const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
+                          const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
+                          float* __restrict__ g2) {
+    constexpr int NT = TILE * TILE;
+    constexpr int CH = NT < 256 ? NT : 256;   // splats staged per chunk
+    __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
+    __shared__ uint32_t s_g[CH];
+    const int tile = blockIdx.x;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
+    const bool inside = px < W && py < H;
+    const size_t pix = (size_t)py * W + px;
+    const size_t HW = (size_t)H * W;
+    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const uint2 r = ranges[tile];
+    const int lane = threadIdx.x & 31;
+
+    float T = 1.f, TN = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gA = 0.f;
+    int32_t last = 0;
+    if (inside) {
+        TN = t_final[pix];
+        T = TN;
+        last = last_in[pix];
+        gC0 = d_rgb[pix]; gC1 = d_rgb[HW + pix]; gC2 = d_rgb[2 * HW + pix];
+        gA = d_alpha[pix];
+    }
+    // terms constant along the walk
+    const float bgdot = bg0 * gC0 + bg1 * gC1 + bg2 * gC2;
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+
+    // block-wide maximum of `last` bounds the walk
+    __shared__ int32_t s_max_last;
+    if (threadIdx.x == 0) s_max_last = 0;
+    __syncthreads();
+    atomicMax(&s_max_last, last);
+    __syncthreads();
+    const uint32_t end = (uint32_t)max((int32_t)r.x, s_max_last);
+
+    for (int64_t top = end; top > (int64_t)r.x; top -= CH) {
+        const int64_t lo = max((int64_t)r.x, top - CH);
+        const int cnt = (int)(top - lo);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const uint32_t g = vals[lo + threadIdx.x];
+            s_g[threadIdx.x] = g;
+            s_a[threadIdx.x] = rec[3 * (size_t)g + 0];
+            s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
+            s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
+        }
+        __syncthreads();
+        for (int k = cnt - 1; k >= 0; --k) {
+            const int64_t pos = lo + k;   // sorted position of this splat
+            float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool contrib = false;
+            if (inside && pos < (int64_t)last) {
+                const float4 a = s_a[k], b = s_b[k];
+                const PairEval e = eval_pair(pcx, pcy, a, b);
+                if (e.q <= 9.f) {
+                    const float4 c = s_c[k];
+                    const float G = gauss_of_q(e.q);
+                    const float raw = __fmul_rn(c.x, G);
+                    const float alpha = fminf(alpha_max, raw);
+                    if (alpha >= alpha_min) {
+                        contrib = true;
+                        const float om = __fsub_rn(1.f, alpha);
+                        const float inv_om = 1.f / om;
+                        T = T * inv_om;                      // T before this splat
+                        const float w = alpha * T;
+                        g[6] = gC0 * w; g[7] = gC1 * w; g[8] = gC2 * w;
+                        float ga = T * ((c.y - S0) * gC0 + (c.z - S1) * gC1 + (c.w - S2) * gC2);
+                        ga += (gA - bgdot) * TN * inv_om;
+                        S0 = c.y * alpha + om * S0;
+                        S1 = c.z * alpha + om * S1;
+                        S2 = c.w * alpha + om * S2;
+                        if (raw <= alpha_max) {   // clamp inactive
+                            g[5] = ga * G;
+                            const float gq = -0.5f * ga * c.x * G;
+                            // dq/dd = 2 (f1 p1 + f2 p2); d = pixel - (u, v)
+                            const float qdx = b.x * e.p1 + b.z * e.p2;
+                            const float qdy = b.y * e.p1 + b.w * e.p2;
+                            g[0] = -2.f * gq * qdx;
+                            g[1] = -2.f * gq * qdy;
+                            g[2] = gq * e.dx * e.dx;
+                            g[3] = 2.f * gq * e.dx * e.dy;
+                            g[4] = gq * e.dy * e.dy;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int f = 0; f < 9; ++f) g[f] = warp_sum(g[f]);
+                if (lane == 0) {
+                    float* dst = g2 + 9 * (size_t)s_g[k];
+#pragma unroll
+                    for (int f = 0; f < 9; ++f)
+                        if (g[f] != 0.f) atomicAdd(dst + f, g[f]);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uint32_t* __restrict__ touched,
+                           float* __restrict__ d_means, float* __restrict__ d_log_scales,
+                           float* __restrict__ d_quats, float* __restrict__ d_logits, float* __restrict__ d_sh) {
+    const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    if (i >= p.n) return;
+    const int K = (p.deg + 1) * (p.deg + 1);
+    float* dsh = d_sh + (size_t)i * K * 3;
+    if (touched[i] == 0) {
+        for (int k = 0; k < 3; ++k) { d_means[3 * i + k] = 0.f; d_log_scales[3 * i + k] = 0.f; }
+        for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = 0.f;
+        d_logits[i] = 0.f;
+        for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.f;
+        return;
+    }
+    float gg[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) gg[f] = g2[9 * (size_t)i + f];
+    const float mx = p.means[3 * i], my = p.means[3 * i + 1], mz = p.means[3 * i + 2];
+
+    // ---- colour: rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5) ----
+    float vx = mx - p.cam_pos[0], vy = my - p.cam_pos[1], vz = mz - p.cam_pos[2];
+    const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float x = vx * vinv, y = vy * vinv, z = vz * vinv;
+    const float* c = p.shc;
+    float Y[16], Yx[16], Yy[16], Yz[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { Y[k] = 0.f; Yx[k] = 0.f; Yy[k] = 0.f; Yz[k] = 0.f; }
+    Y[0] = c[9];
+    if (p.deg >= 1) {
+        Y[1] = -c[1] * y; Yy[1] = -c[1];
+        Y[2] = c[0] * z;  Yz[2] = c[0];
+        Y[3] = -c[1] * x; Yx[3] = -c[1];
+    }
+    if (p.deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 2.f * c[4] * x * y;       Yx[4] = 2.f * c[4] * y;  Yy[4] = 2.f * c[4] * x;
+        Y[5] = -c[3] * y * z;            Yy[5] = -c[3] * z;       Yz[5] = -c[3] * y;
+        Y[6] = c[2] * (3.f * zz - 1.f);  Yz[6] = 6.f * c[2] * z;
+        Y[7] = -c[3] * x * z;            Yx[7] = -c[3] * z;       Yz[7] = -c[3] * x;
+        Y[8] = c[4] * (xx - yy);         Yx[8] = 2.f * c[4] * x;  Yy[8] = -2.f * c[4] * y;
+        if (p.deg >= 3) {
+            Y[9] = -c[8] * (3.f * xx * y - yy * y);
+            Yx[9] = -6.f * c[8] * x * y;     Yy[9] = -c[8] * (3.f * xx - 3.f * yy);
+            Y[10] = 2.f * c[7] * x * y * z;
+            Yx[10] = 2.f * c[7] * y * z;     Yy[10] = 2.f * c[7] * x * z;  Yz[10] = 2.f * c[7] * x * y;
+            Y[11] = -c[6] * (5.f * zz - 1.f) * y;
+            Yy[11] = -c[6] * (5.f * zz - 1.f); Yz[11] = -10.f * c[6] * z * y;
+            Y[12] = c[5] * (5.f * zz * z - 3.f * z);
+            Yz[12] = c[5] * (15.f * zz - 3.f);
+            Y[13] = -c[6] * (5.f * zz - 1.f) * x;
+            Yx[13] = -c[6] * (5.f * zz - 1.f); Yz[13] = -10.f * c[6] * z * x;
+            Y[14] = c[7] * z * (xx - yy);
+            Yx[14] = 2.f * c[7] * x * z;     Yy[14] = -2.f * c[7] * y * z;  Yz[14] = c[7] * (xx - yy);
+            Y[15] = -c[8] * (xx * x - 3.f * x * yy);
+            Yx[15] = -c[8] * (3.f * xx - 3.f * yy); Yy[15] = 6.f * c[8] * x * y;
+        }
+    }
+    const float* shi = p.sh + (size_t)i * K * 3;
+    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+        float col = 0.5f;
+        for (int k = 0; k < K; ++k) col += shi[3 * k + ch] * Y[k];
+        const float gch = (col < 0.f) ? 0.f : gg[6 + ch];
+        for (int k = 0; k < K; ++k) {
+            dsh[3 * k + ch] = gch * Y[k];
+            const float s = shi[3 * k + ch] * gch;
+            gdx += s * Yx[k]; gdy += s * Yy[k]; gdz += s * Yz[k];
+        }
+    }
+    const float dd = gdx * x + gdy * y + gdz * z;
+    float gmx = (gdx - x * dd) * vinv, gmy = (gdy - y * dd) * vinv, gmz = (gdz - z * dd) * vinv;
+
+    // ---- opacity ----
+    const float opac = 1.f / (1.f + __expf(-p.logits[i]));
+    d_logits[i] = gg[5] * opac * (1.f - opac);
+
+    // ---- camera-space position (float is enough for gradients) ----
+    float pc[3];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr) pc[rr] = p.R[3 * rr] * mx + p.R[3 * rr + 1] * my + p.R[3 * rr + 2] * mz + p.t[rr];
+    const float zc = pc[2], zi = 1.f / zc;
+    const float rx = pc[0] * zi, ry = pc[1] * zi;
+    float gp0 = gg[0] * p.fx * zi, gp1 = gg[1] * p.fy * zi;
+    float gp2 = -(gg[0] * p.fx * rx + gg[1] * p.fy * ry) * zi;
+
+    // ---- recompute A = J W M and S ----
+    const float4 q4 = *reinterpret_cast<const float4*>(p.quats + 4 * (size_t)i);
+    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const bool qdeg = qn2 < 1e-24f;
+    const float qinv = qdeg ? 0.f : rsqrtf(qn2);
+    const float qw = qdeg ? 1.f : q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+    const float Rq[9] = {
+        1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+        2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+        2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    const float sk[3] = {__expf(p.log_scales[3 * i]), __expf(p.log_scales[3 * i + 1]),
+                         __expf(p.log_scales[3 * i + 2])};
+    const bool clx = rx > p.limx || rx < -p.limx, cly = ry > p.limy || ry < -p.limy;
+    const float txc = fminf(p.limx, fmaxf(-p.limx, rx)), tyc = fminf(p.limy, fmaxf(-p.limy, ry));
+    const float J00 = p.fx * zi, J02 = -p.fx * txc * zi, J11 = p.fy * zi, J12 = -p.fy * tyc * zi;
+    float Tm[2][3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+        Tm[0][cc] = J00 * p.R[cc] + J02 * p.R[6 + cc];
+        Tm[1][cc] = J11 * p.R[3 + cc] + J12 * p.R[6 + cc];
+    }
+    float M[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[a][k] = Rq[3 * a + k] * sk[k];
+    float A[2][3];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) A[rr][k] = Tm[rr][0] * M[0][k] + Tm[rr][1] * M[1][k] + Tm[rr][2] * M[2][k];
+    const float s00 = A[0][0] * A[0][0] + A[0][1] * A[0][1] + A[0][2] * A[0][2] + p.dilation;
+    const float s11 = A[1][0] * A[1][0] + A[1][1] * A[1][1] + A[1][2] * A[1][2] + p.dilation;
+    const float s01 = A[0][0] * A[1][0] + A[0][1] * A[1][1] + A[0][2] * A[1][2];
+    const float det = s00 * s11 - s01 * s01;
+    const float idet = 1.f / det;
+    const float Qa = s11 * idet, Qb = -s01 * idet, Qc = s00 * idet;
+
+    // ---- conic -> S: G_S = -Q Gbar Q, Gbar = [[ga, gb/2], [gb/2, gc]] ----
+    const float Gb00 = gg[2], Gb01 = 0.5f * gg[3], Gb11 = gg[4];
+    const float QG00 = Qa * Gb00 + Qb * Gb01, QG01 = Qa * Gb01 + Qb * Gb11;
+    const float QG10 = Qb * Gb00 + Qc * Gb01, QG11 = Qb * Gb01 + Qc * Gb11;
+    const float GS00 = -(QG00 * Qa + QG01 * Qb);
+    const float GS01 = -(QG00 * Qb + QG01 * Qc);
+    const float GS11 = -(QG10 * Qb + QG11 * Qc);
+    // ---- S = A A^T + dil I: dL/dA = 2 G_S A ----
+    float gA_[2][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        gA_[0][k] = 2.f * (GS00 * A[0][k] + GS01 * A[1][k]);
+        gA_[1][k] = 2.f * (GS01 * A[0][k] + GS11 * A[1][k]);
+    }
+    // ---- A = T M: dL/dT = dL/dA M^T, dL/dM = T^T dL/dA ----
+    float gT[2][3], gM[3][3];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gT[rr][a] = gA_[rr][0] * M[a][0] + gA_[rr][1] * M[a][1] + gA_[rr][2] * M[a][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gM[a][k] = Tm[0][a] * gA_[0][k] + Tm[1][a] * gA_[1][k];
+    // ---- T = J W: dL/dJ = dL/dT W^T (only J00, J02, J11, J12 are non-zero) ----
+    const float gJ00 = gT[0][0] * p.R[0] + gT[0][1] * p.R[1] + gT[0][2] * p.R[2];
+    const float gJ02 = gT[0][0] * p.R[6] + gT[0][1] * p.R[7] + gT[0][2] * p.R[8];
+    const float gJ11 = gT[1][0] * p.R[3] + gT[1][1] * p.R[4] + gT[1][2] * p.R[5];
+    const float gJ12 = gT[1][0] * p.R[6] + gT[1][1] * p.R[7] + gT[1][2] * p.R[8];
+    const float zi2 = zi * zi;
+    gp2 += -gJ00 * p.fx * zi2 - gJ11 * p.fy * zi2 + gJ02 * p.fx * txc * zi2 + gJ12 * p.fy * tyc * zi2;
+    if (!clx) { gp0 += -gJ02 * p.fx * zi2; gp2 += gJ02 * p.fx * rx * zi2; }
+    if (!cly) { gp1 += -gJ12 * p.fy * zi2; gp2 += gJ12 * p.fy * ry * zi2; }
+    // ---- p = R mu + t ----
+    gmx += p.R[0] * gp0 + p.R[3] * gp1 + p.R[6] * gp2;
+    gmy += p.R[1] * gp0 + p.R[4] * gp1 + p.R[7] * gp2;
+    gmz += p.R[2] * gp0 + p.R[5] * gp1 + p.R[8] * gp2;
+    d_means[3 * i] = gmx; d_means[3 * i + 1] = gmy; d_means[3 * i + 2] = gmz;
+    // ---- M = Rq diag(s) ----
+    float gR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gs = gM[0][k] * Rq[k] + gM[1][k] * Rq[3 + k] + gM[2][k] * Rq[6 + k];
+        d_log_scales[3 * i + k] = gs * sk[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gR[3 * a + k] = gM[a][k] * sk[k];
+    }
+    // ---- Rq(qhat) -> qhat -> q ----
+    float gw = -2.f * qz * gR[1] + 2.f * qy * gR[2] + 2.f * qz * gR[3] - 2.f * qx * gR[5] - 2.f * qy * gR[6] + 2.f * qx * gR[7];
+    float gx = 2.f * qy * gR[1] + 2.f * qz * gR[2] + 2.f * qy * gR[3] - 4.f * qx * gR[4] - 2.f * qw * gR[5] + 2.f * qz * gR[6] + 2.f * qw * gR[7] - 4.f * qx * gR[8];
+    float gy = -4.f * qy * gR[0] + 2.f * qx * gR[1] + 2.f * qw * gR[2] + 2.f * qx * gR[3] + 2.f * qz * gR[5] - 2.f * qw * gR[6] + 2.f * qz * gR[7] - 4.f * qy * gR[8];
+    float gz = -4.f * qz * gR[0] - 2.f * qw * gR[1] + 2.f * qx * gR[2] + 2.f * qw * gR[3] - 4.f * qz * gR[4] + 2.f * qy * gR[5] + 2.f * qx * gR[6] + 2.f * qy * gR[7];
+    if (qdeg) { gw = gx = gy = gz = 0.f; }
+    const float dq = gw * qw + gx * qx + gy * qy + gz * qz;
+    d_quats[4 * i + 0] = (gw - qw * dq) * qinv;
+    d_quats[4 * i + 1] = (gx - qx * dq) * qinv;
+    d_quats[4 * i + 2] = (gy - qy * dq) * qinv;
+    d_quats[4 * i + 3] = (gz - qz * dq) * qinv;
+}
+
+void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3], float alpha_min,
+                     float alpha_max, float t_stop, const float* d_rgb, const float* d_alpha, float* d_means,
+                     float* d_log_scales, float* d_quats, float* d_logits, float* d_sh, cudaStream_t stream) {
+    (void)t_stop;
+    float* g2 = reinterpret_cast<float*>(ws + L.off_g2);
+    cudaMemsetAsync(g2, 0, sizeof(float) * 9 * (size_t)L.n, stream);
+    const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
+    const uint32_t* vals = reinterpret_cast<const uint32_t*>(ws + L.off_vals[L.sorted_buffer]);
+    const float4* rec = reinterpret_cast<const float4*>(ws + L.off_rec);
+    const float* tfin = reinterpret_cast<const float*>(ws + L.off_tfinal);
+    const int32_t* last = reinterpret_cast<const int32_t*>(ws + L.off_last);
+    const int blocks = (int)L.ntiles;
+#define VIS_LAUNCH_BWD(TS)                                                                                 \
+    composite_backward_kernel<TS><<<blocks, TS * TS, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, \
+                                                                  bg[0], bg[1], bg[2], alpha_min,         \
+                                                                  alpha_max, tfin, last, d_rgb, d_alpha,  \
+                                                                  g2)
+    if (blocks > 0) {
+        if (L.tile == 8) VIS_LAUNCH_BWD(8);
+        else if (L.tile == 32) VIS_LAUNCH_BWD(32);
+        else VIS_LAUNCH_BWD(16);
+    }
+#undef VIS_LAUNCH_BWD
+    if (p.n > 0)
+        preprocess_backward_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
+            p, g2, reinterpret_cast<const uint32_t*>(ws + L.off_touched), d_means, d_log_scales, d_quats,
+            d_logits, d_sh);
+}
+
+}  // namespace vis

@@ -1,0 +1,144 @@
+// K2 -- tile-key duplication, and K4 -- per-tile ranges.
+//
+// Algorithm 1 appends every surviving splat with an atomic counter, which makes
+// the order (and so the tie order of the sort) run-dependent. Here the offsets are
+// an exclusive prefix sum of the tiles-touched counts in Gaussian-index order, so
+// the key list -- and the sorted result -- is deterministic:
+//   1. scan_block_sums: one CTA scans the per-block sums written by the preprocess
+//      and stores the total key count M in the status block (capacity checked);
+//   2. duplicate_kernel: each block rescans its 256 counts (warp shuffles), then
+//      every warp emits its Gaussians' keys cooperatively, lane j writing key j of
+//      the warp's contiguous output run, so stores are coalesced whatever the
+//      per-Gaussian counts. key = (tile id << 32) | float bits of the view depth,
+//      val = Gaussian index; tiles in row-major order within each rectangle.
+//   3. ranges_kernel: [start, end) of every tile in the sorted keys.
+#include "vis_internal.cuh"
+
+namespace vis {
+
+__global__ void __launch_bounds__(1024)
+scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
+                Ctrl* ctrl, int64_t cap) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nblocks; base += 1024) {
+        const int64_t b = base + threadIdx.x;
+        uint32_t v = (b < nblocks) ? bsum[b] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warp_tot[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            warp_tot[lane] = wi - w;   // exclusive warp offsets
+        }
+        __syncthreads();
+        const unsigned long long c = carry;
+        const unsigned long long excl = c + warp_tot[warp] + (incl - v);
+        if (b < nblocks) boff[b] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long total = carry;
+        ctrl->num_keys = (uint32_t)min(total, (unsigned long long)0xffffffffu);
+        if (total > (unsigned long long)cap) atomicOr(&ctrl->error, kErrCapacity);
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+duplicate_kernel(const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
+                 const float* __restrict__ depth, const uint32_t* __restrict__ boff, int64_t n,
+                 int tiles_x, const Ctrl* __restrict__ ctrl, uint64_t* __restrict__ keys,
+                 uint32_t* __restrict__ vals) {
+    if (ctrl->error & kErrCapacity) return;   // nothing fits: leave the buffers alone
+    __shared__ uint32_t s_start[kPrepThreads];   // exclusive offset within the warp's run
+    __shared__ uint32_t warp_tot[kPrepThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const uint32_t cnt = (i < n) ? touched[i] : 0u;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    s_start[threadIdx.x] = incl - cnt;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t warp_base = boff[blockIdx.x];
+    for (int w = 0; w < warp; ++w) warp_base += warp_tot[w];
+    const uint32_t run = warp_tot[warp];
+    const int g0 = warp * 32;   // first Gaussian (block-local) of this warp
+    for (uint32_t j = lane; j < run; j += 32) {
+        // owner: the last g of the warp with s_start[g] <= j; a Gaussian with a zero
+        // count shares its start with the next one, so the last such g owns key j
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_start[g0 + mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int64_t gi = (int64_t)blockIdx.x * kPrepThreads + g0 + lo;
+        const uint2 r = rect[gi];
+        const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu;
+        const uint32_t w = x1 - x0;
+        const uint32_t k = j - s_start[g0 + lo];
+        const uint32_t tx = x0 + k % w, ty = y0 + k / w;
+        const uint64_t tile = (uint64_t)ty * (uint64_t)tiles_x + tx;
+        const uint32_t zb = __float_as_uint(depth[gi]);
+        keys[warp_base + j] = (tile << 32) | zb;
+        vals[warp_base + j] = (uint32_t)gi;
+    }
+}
+
+void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_t stream) {
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    const uint32_t* bsum = reinterpret_cast<const uint32_t*>(ws + L.off_bsum);
+    uint32_t* boff = reinterpret_cast<uint32_t*>(ws + L.off_boff);
+    scan_block_sums<<<1, 1024, 0, stream>>>(bsum, boff, L.prep_blocks, ctrl, L.cap);
+    if (n <= 0) return;
+    duplicate_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
+        reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint2*>(ws + L.off_rect),
+        reinterpret_cast<const float*>(ws + L.off_depth), boff, n, L.tiles_x, ctrl,
+        reinterpret_cast<uint64_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
+}
+
+__global__ void ranges_kernel(const uint64_t* __restrict__ keys, const Ctrl* __restrict__ ctrl,
+                              int64_t cap, uint2* __restrict__ ranges) {
+    if (ctrl->error) return;
+    const int64_t m = min((int64_t)ctrl->num_keys, cap);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(keys[j] >> 32);
+        if (j == 0 || (uint32_t)(keys[j - 1] >> 32) != t) ranges[t].x = (uint32_t)j;
+        if (j == m - 1 || (uint32_t)(keys[j + 1] >> 32) != t) ranges[t].y = (uint32_t)(j + 1);
+    }
+}
+
+void launch_ranges(const Layout& L, char* ws, cudaStream_t stream) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (L.cap + 255) / 256;
+    const int64_t lim = (int64_t)sms * 8;
+    const int blocks = (int)(want < 1 ? 1 : (want < lim ? want : lim));
+    ranges_kernel<<<blocks, 256, 0, stream>>>(
+        reinterpret_cast<const uint64_t*>(ws + L.off_keys[L.sorted_buffer]),
+        reinterpret_cast<const Ctrl*>(ws + L.off_ctrl), L.cap, reinterpret_cast<uint2*>(ws + L.off_ranges));
+}
+
+}  // namespace vis

@@ -1,0 +1,212 @@
+// K1 -- per-Gaussian preprocess (section 3.2 Eq. 1; Algorithm 1, Preprocess).
+//
+// One thread per Gaussian. Reads the caller's fp32 SoA attributes once and writes
+// a 48-byte splat record, the view depth, the tile rectangle and the number of
+// tiles touched; each block also writes the sum of its tiles-touched counts for
+// the key-offset scan.
+//
+// Numerics. The camera transform and the perspective division are carried in
+// float-float (error-free transforms) so that the pixel centre (u, v) is exact to
+// ~1e-7 px even 1000 px from the principal point. The 2D covariance is formed as
+// S = A A^T + dil I with A = J W R_q diag(s); its determinant as
+// |A_0 x A_1|^2 + dil tr(A A^T) + dil^2 (no cancellation), and the splat is stored
+// in whitened form: q = (d.f1)^2 + (d.f2)^2 with f_k = e_k / sqrt(lambda_k), the
+// eigenpairs of S. This equals d^T S^-1 d of Eq. 2 and stays well conditioned for
+// needle-shaped splats, where the conic form (a, b, c) loses digits.
+#include "vis_internal.cuh"
+
+namespace vis {
+
+__global__ void __launch_bounds__(kPrepThreads)
+preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
+                  uint2* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
+                  uint32_t* __restrict__ block_sums) {
+    const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    uint32_t touched = 0;
+    if (i < p.n) {
+        // --- camera-space position in float-float: p = R mu + t ---
+        const float mx = __ldg(p.means + 3 * i + 0);
+        const float my = __ldg(p.means + 3 * i + 1);
+        const float mz = __ldg(p.means + 3 * i + 2);
+        float2 pc[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            float2 acc = make_float2(p.t[r], 0.f);
+            acc = ff_add(acc, two_prod(p.R[3 * r + 0], mx));
+            acc = ff_add(acc, two_prod(p.R[3 * r + 1], my));
+            acc = ff_add(acc, two_prod(p.R[3 * r + 2], mz));
+            pc[r] = acc;
+        }
+        const float z = pc[2].x;
+        const float logit = __ldg(p.logits + i);
+        const float opac = 1.f / (1.f + __expf(-logit));
+        depth_out[i] = z;
+        bool ok = (z > p.near_z) && (opac >= p.alpha_min);
+        uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        if (ok) {
+            // --- pixel centre u = fx x/z + cx (float-float) ---
+            const float2 rx = ff_div(pc[0], pc[2]);
+            const float2 ry = ff_div(pc[1], pc[2]);
+            float2 u, v;
+            {
+                float2 a = two_prod(p.fx, rx.x);
+                a.y = __fmaf_rn(p.fx, rx.y, a.y);
+                float2 s = two_sum(a.x, p.cx);
+                u = fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+                float2 b = two_prod(p.fy, ry.x);
+                b.y = __fmaf_rn(p.fy, ry.y, b.y);
+                float2 s2 = two_sum(b.x, p.cy);
+                v = fast_two_sum(s2.x, __fadd_rn(s2.y, b.y));
+            }
+            // --- covariance factor M = R_q diag(s) ---
+            const float4 q4 = __ldg(reinterpret_cast<const float4*>(p.quats) + i);
+            float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+            const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+            if (qn2 < 1e-24f) { qw = 1.f; qx = qy = qz = 0.f; }
+            else { const float inv = rsqrtf(qn2); qw *= inv; qx *= inv; qy *= inv; qz *= inv; }
+            const float Rq[9] = {
+                1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+            const float s0 = __expf(__ldg(p.log_scales + 3 * i + 0));
+            const float s1 = __expf(__ldg(p.log_scales + 3 * i + 1));
+            const float s2 = __expf(__ldg(p.log_scales + 3 * i + 2));
+            // --- EWA Jacobian at the camera-space mean, with the x/z, y/z guard ---
+            const float zi = 1.f / z;
+            const float tx = fminf(p.limx, fmaxf(-p.limx, rx.x));
+            const float ty = fminf(p.limy, fmaxf(-p.limy, ry.x));
+            const float J00 = p.fx * zi, J02 = -p.fx * tx * zi;
+            const float J11 = p.fy * zi, J12 = -p.fy * ty * zi;
+            // T = J W (2x3), W = camera rotation
+            float T0[3], T1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T0[c] = J00 * p.R[c] + J02 * p.R[6 + c];
+                T1[c] = J11 * p.R[3 + c] + J12 * p.R[6 + c];
+            }
+            // A = T M: rows A0, A1 (3 each); M[:, k] = Rq[:, k] s_k
+            float A0[3], A1[3];
+            const float sk[3] = {s0, s1, s2};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float m0 = Rq[0 + k] * sk[k], m1 = Rq[3 + k] * sk[k], m2 = Rq[6 + k] * sk[k];
+                A0[k] = T0[0] * m0 + T0[1] * m1 + T0[2] * m2;
+                A1[k] = T1[0] * m0 + T1[1] * m1 + T1[2] * m2;
+            }
+            const float a00 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+            const float a11 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+            const float a01 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+            const float c0 = diff_of_products(A0[1], A1[2], A0[2], A1[1]);
+            const float c1 = diff_of_products(A0[2], A1[0], A0[0], A1[2]);
+            const float c2 = diff_of_products(A0[0], A1[1], A0[1], A1[0]);
+            const float dil = p.dilation;
+            const float s00 = a00 + dil, s11 = a11 + dil, s01 = a01;
+            const float det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (a00 + a11) + dil * dil;
+            if (det > 0.f) {
+                const float m = 0.5f * (s00 + s11);
+                const float h = 0.5f * (s00 - s11);
+                const float disc = h * h + s01 * s01;
+                const float rt = sqrtf(disc);
+                const float lam1 = m + rt;                 // largest eigenvalue
+                const float lam2 = det / lam1;             // smallest, without cancellation
+                float ex, ey;
+                if (h >= 0.f) { ex = h + rt; ey = s01; } else { ex = s01; ey = rt - h; }
+                const float en2 = ex * ex + ey * ey;
+                if (en2 > 0.f) { const float inv = rsqrtf(en2); ex *= inv; ey *= inv; }
+                else { ex = 1.f; ey = 0.f; }
+                const float i1 = rsqrtf(lam1), i2 = rsqrtf(lam2);
+                const float lam_ext = m + sqrtf(fmaxf(0.1f, disc));
+                const float radius = ceilf(3.f * sqrtf(lam_ext));
+                const float T = (float)p.tile;
+                const float ftx = (float)p.tiles_x, fty = (float)p.tiles_y;
+                // clamp in float before converting (u may be far off screen)
+                const int ix0 = (int)fminf(ftx, fmaxf(0.f, floorf((u.x - radius - 1.f) / T)));
+                const int ix1 = (int)fminf(ftx, fmaxf(0.f, floorf((u.x + radius + 1.f) / T) + 1.f));
+                const int iy0 = (int)fminf(fty, fmaxf(0.f, floorf((v.x - radius - 1.f) / T)));
+                const int iy1 = (int)fminf(fty, fmaxf(0.f, floorf((v.x + radius + 1.f) / T) + 1.f));
+                touched = (ix1 > ix0 && iy1 > iy0) ? (uint32_t)((ix1 - ix0) * (iy1 - iy0)) : 0u;
+                if (touched > 0) {
+                    x0 = ix0; x1 = ix1; y0 = iy0; y1 = iy1;
+                    // --- colour from SH at dir = normalize(mu - camera centre) ---
+                    float dx = mx - p.cam_pos[0], dy = my - p.cam_pos[1], dz = mz - p.cam_pos[2];
+                    const float dinv = rsqrtf(dx * dx + dy * dy + dz * dz);
+                    dx *= dinv; dy *= dinv; dz *= dinv;
+                    const int K = (p.deg + 1) * (p.deg + 1);
+                    float Y[16];
+                    Y[0] = p.shc[9];
+                    if (p.deg >= 1) {
+                        Y[1] = -p.shc[1] * dy; Y[2] = p.shc[0] * dz; Y[3] = -p.shc[1] * dx;
+                    }
+                    if (p.deg >= 2) {
+                        const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+                        Y[4] = 2.f * p.shc[4] * dx * dy;
+                        Y[5] = -p.shc[3] * dy * dz;
+                        Y[6] = p.shc[2] * (3.f * zz - 1.f);
+                        Y[7] = -p.shc[3] * dx * dz;
+                        Y[8] = p.shc[4] * (xx - yy);
+                        if (p.deg >= 3) {
+                            Y[9] = -p.shc[8] * (3.f * xx * dy - yy * dy);
+                            Y[10] = 2.f * p.shc[7] * dx * dy * dz;
+                            Y[11] = -p.shc[6] * (5.f * zz - 1.f) * dy;
+                            Y[12] = p.shc[5] * (5.f * zz * dz - 3.f * dz);
+                            Y[13] = -p.shc[6] * (5.f * zz - 1.f) * dx;
+                            Y[14] = p.shc[7] * dz * (xx - yy);
+                            Y[15] = -p.shc[8] * (xx * dx - 3.f * dx * yy);
+                        }
+                    }
+                    float col[3] = {0.5f, 0.5f, 0.5f};
+                    const float* shi = p.sh + (size_t)i * K * 3;
+                    if (p.deg == 3) {
+                        const float4* s4 = reinterpret_cast<const float4*>(shi);
+                        float buf[48];
+#pragma unroll
+                        for (int k = 0; k < 12; ++k) {
+                            const float4 w = __ldg(s4 + k);
+                            buf[4 * k] = w.x; buf[4 * k + 1] = w.y; buf[4 * k + 2] = w.z; buf[4 * k + 3] = w.w;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            col[0] += buf[3 * k] * Y[k]; col[1] += buf[3 * k + 1] * Y[k]; col[2] += buf[3 * k + 2] * Y[k];
+                        }
+                    } else {
+                        for (int k = 0; k < K; ++k) {
+                            col[0] += __ldg(shi + 3 * k) * Y[k];
+                            col[1] += __ldg(shi + 3 * k + 1) * Y[k];
+                            col[2] += __ldg(shi + 3 * k + 2) * Y[k];
+                        }
+                    }
+                    rec[3 * (size_t)i + 0] = make_float4(u.x, v.x, u.y, v.y);
+                    rec[3 * (size_t)i + 1] = make_float4(ex * i1, ey * i1, -ey * i2, ex * i2);
+                    rec[3 * (size_t)i + 2] = make_float4(opac, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f),
+                                                         fmaxf(col[2], 0.f));
+                }
+            }
+        }
+        rect_out[i] = make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
+        touched_out[i] = touched;
+    }
+    // block sum of tiles touched (for the offset scan)
+    __shared__ uint32_t warp_sums[kPrepThreads / 32];
+    uint32_t s = touched;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kPrepThreads / 32; ++w) tot += warp_sums[w];
+        block_sums[blockIdx.x] = tot;
+    }
+}
+
+void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream) {
+    if (p.n <= 0) return;
+    const int blocks = (int)L.prep_blocks;
+    preprocess_kernel<<<blocks, kPrepThreads, 0, stream>>>(
+        p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
+        reinterpret_cast<uint2*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
+        reinterpret_cast<uint32_t*>(ws + L.off_bsum));
+}
+
+}  // namespace vis

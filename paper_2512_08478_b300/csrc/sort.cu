@@ -1,0 +1,270 @@
+// K3 -- stable LSD radix sort of (key, value) pairs, onesweep style.
+//
+// Algorithm 1 sorts the splats on the GPU with a radix sort (section 3.4, "GPU
+// sorting and rasterization"); here the keys are 64-bit (tile id << 32 | float bits
+// of the view depth) with the Gaussian index as payload, so one stable sort yields
+// the (tile, depth, index) order the compositor walks.
+//
+//  - sort_histogram: one read of all keys builds the digit histograms of every
+//    pass at once (shared-memory counters, one global atomic per bin per CTA).
+//  - sort_pass (one launch per 8-bit digit): a CTA takes the next partition of
+//    4096 keys from an atomic ticket (so partitions start in order and the
+//    look-back below always makes progress), ranks its keys stably per warp with
+//    __match_any_sync, publishes its per-digit counts, and resolves its global
+//    offsets by decoupled look-back over the preceding partitions' published
+//    counts. The keys are then reordered by digit in shared memory and written out
+//    in runs, so global stores are coalesced within each digit run.
+//  - Spin waits on a predecessor are bounded (kSpinLimit polls); on expiry the
+//    CTA records kErrTimeout, publishes anyway so nobody waits on it, and writes
+//    nothing out of range (every destination is checked against the key count).
+#include "vis_internal.cuh"
+
+namespace vis {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+
+__global__ void __launch_bounds__(256)
+sort_histogram(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap,
+               int passes, uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
+    __shared__ uint32_t sh[kMaxPasses * kRadix];
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    if (*error) return;
+    const int64_t m = min((int64_t)*num_keys, cap);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint64_t k = keys[j];
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sh[p * kRadix + (uint32_t)((k >> (kRadixBits * p)) & (kRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// exclusive scan of one value per thread over a 256-thread block; returns total in *tot
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* s_warp, uint32_t* tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t x = s_warp[w];
+        if (w < warp) woff += x;
+        all += x;
+    }
+    __syncthreads();
+    if (tot) *tot = all;
+    return woff + incl - v;
+}
+
+static_assert(kSortThreads == kRadix, "one digit per thread");
+
+struct SortSmem {
+    uint64_t keys[kSortPartition];
+    uint32_t vals[kSortPartition];
+    uint32_t whist[kSortThreads / 32][kRadix];
+    uint32_t digit_off[kRadix];
+    uint32_t local_start[kRadix];
+    uint32_t scan_tmp[8];
+    uint32_t part;
+    uint32_t bad;
+};
+
+__global__ void __launch_bounds__(kSortThreads)
+sort_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+          uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+          const uint32_t* __restrict__ num_keys, int64_t cap, int shift,
+          const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
+          uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (ld_relaxed(error) & kErrCapacity) return;
+    const int64_t m = min((int64_t)*num_keys, cap);
+    if (tid == 0) {
+        S.part = atomicAdd(part_counter, 1u);
+        S.bad = 0;
+    }
+    for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t part = S.part;
+    const int64_t base = (int64_t)part * kSortPartition;
+    if (base >= m) return;
+
+    // ---- load (warp-striped: warp w owns keys [w*512, (w+1)*512) of the partition) ----
+    uint64_t key[kSortKeysPerThread];
+    uint32_t val[kSortKeysPerThread];
+    const int64_t wbase = base + (int64_t)warp * (32 * kSortKeysPerThread);
+#pragma unroll
+    for (int k = 0; k < kSortKeysPerThread; ++k) {
+        const int64_t idx = wbase + k * 32 + lane;
+        if (idx < m) { key[k] = keys_in[idx]; val[k] = vals_in[idx]; }
+        else { key[k] = 0; val[k] = 0; }
+    }
+
+    // ---- stable per-warp ranking ----
+    uint32_t rank[kSortKeysPerThread];
+    uint32_t* wh = S.whist[warp];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kSortKeysPerThread; ++k) {
+        const bool valid = (wbase + k * 32 + lane) < m;
+        const uint32_t d = (uint32_t)(key[k] >> shift) & (kRadix - 1);
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (kRadix + lane));
+        uint32_t before = 0;
+        if (valid) before = wh[d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wh[d] = before + __popc(peers);
+        __syncwarp();
+        rank[k] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // ---- per-digit totals and warp offsets; publish the partition aggregate ----
+    const uint32_t d = tid;   // one digit per thread (256 threads, 256 digits)
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t c = S.whist[w][d];
+        S.whist[w][d] = cnt;
+        cnt += c;
+    }
+    uint32_t* lb = lookback + (size_t)part * kRadix;
+    st_relaxed(&lb[d], (part == 0 ? kFlagInc : kFlagAgg) | cnt);
+    const uint32_t local_start = block_exclusive_scan_256(cnt, S.scan_tmp, nullptr);
+    const uint32_t gstart = block_exclusive_scan_256(hist_pass[d], S.scan_tmp, nullptr);
+
+    // ---- decoupled look-back ----
+    uint32_t prefix = 0;
+    if (part > 0) {
+        int64_t q = (int64_t)part - 1;
+        bool timed_out = false;
+        while (true) {
+            uint32_t v = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
+            uint32_t spins = 0;
+            while ((v & ~kCountMask) == 0) {
+                if (++spins > kSpinLimit) { timed_out = true; break; }
+                if (spins > 8) __nanosleep(32);
+                v = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
+            }
+            if (timed_out) break;
+            prefix += v & kCountMask;
+            if ((v & ~kCountMask) == kFlagInc || q == 0) break;
+            --q;
+        }
+        st_relaxed(&lb[d], kFlagInc | ((prefix + cnt) & kCountMask));
+        if (timed_out) {
+            atomicOr(error, kErrTimeout);
+            S.bad = 1;
+        }
+    }
+    S.local_start[d] = local_start;
+    S.digit_off[d] = gstart + prefix - local_start;
+    __syncthreads();
+
+    // ---- reorder by digit in shared memory ----
+#pragma unroll
+    for (int k = 0; k < kSortKeysPerThread; ++k) {
+        if ((wbase + k * 32 + lane) < m) {
+            const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
+            const uint32_t pos = S.local_start[dk] + wh[dk] + rank[k];
+            S.keys[pos] = key[k];
+            S.vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    if (S.bad) return;
+
+    // ---- write out in digit runs ----
+    const int n_in = (int)((m - base) < kSortPartition ? (m - base) : kSortPartition);
+    for (int i = tid; i < n_in; i += kSortThreads) {
+        const uint64_t kk = S.keys[i];
+        const uint32_t dk = (uint32_t)(kk >> shift) & (kRadix - 1);
+        const uint32_t dest = S.digit_off[dk] + (uint32_t)i;   // modular: digit_off may wrap
+        if ((int64_t)dest < m) {
+            keys_out[dest] = kk;
+            vals_out[dest] = S.vals[i];
+        }
+    }
+}
+
+__global__ void set_u32_kernel(uint32_t* ptr, uint32_t value) { *ptr = value; }
+
+void launch_set_u32(uint32_t* ptr, uint32_t value, cudaStream_t stream) {
+    set_u32_kernel<<<1, 1, 0, stream>>>(ptr, value);
+}
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+void launch_sort_generic(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_a,
+                         uint32_t* vals_a, uint64_t* keys_b, uint32_t* vals_b, int64_t cap,
+                         const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                         uint32_t* lookback, int64_t parts, Ctrl* ctrl, cudaStream_t stream,
+                         StageMark mark, int mark_index) {
+    if (cap <= 0 || passes <= 0) return;
+    static bool attr_done = false;   // per process; the attribute is per function
+    const size_t smem = sizeof(SortSmem);
+    if (!attr_done) {
+        cudaFuncSetAttribute(sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done = true;
+    }
+    const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
+    const int hist_blocks = (int)(hb < hlim ? hb : hlim);
+    sort_histogram<<<hist_blocks, 256, 0, stream>>>(keys_in, num_keys_dev, cap, passes, hist, &ctrl->error);
+    if (mark) mark(mark_index, stream);
+    const uint64_t* src_k = keys_in;
+    const uint32_t* src_v = vals_in;
+    for (int p = 0; p < passes; ++p) {
+        const bool to_a = ((passes - 1 - p) % 2) == 0;
+        uint64_t* dk = to_a ? keys_a : keys_b;
+        uint32_t* dv = to_a ? vals_a : vals_b;
+        sort_pass<<<(int)parts, kSortThreads, smem, stream>>>(
+            src_k, src_v, dk, dv, num_keys_dev, cap, kRadixBits * p, hist + p * kRadix,
+            lookback + (size_t)p * parts * kRadix, &ctrl->part_counter[p], &ctrl->error);
+        src_k = dk;
+        src_v = dv;
+    }
+}
+
+void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);
+    uint64_t* k1 = reinterpret_cast<uint64_t*>(ws + L.off_keys[1]);
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
+    uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    // the result lands in buffer (passes & 1); see Layout::sorted_buffer
+    uint64_t* ka = (L.passes & 1) ? k1 : k0;
+    uint32_t* va = (L.passes & 1) ? v1 : v0;
+    uint64_t* kb = (L.passes & 1) ? k0 : k1;
+    uint32_t* vb = (L.passes & 1) ? v0 : v1;
+    launch_sort_generic(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, L.passes,
+                        reinterpret_cast<uint32_t*>(ws + L.off_hist),
+                        reinterpret_cast<uint32_t*>(ws + L.off_lookback), L.sort_parts, ctrl, stream, mark,
+                        mark_index);
+}
+
+}  // namespace vis

@@ -1,0 +1,152 @@
+// Internal declarations shared by the CUDA translation units of libvis.
+// Nothing here is part of the C ABI (see include/vis.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vis.h"
+
+namespace vis {
+
+constexpr int kPrepThreads = 256;        // Gaussians per preprocess / duplicate block
+constexpr int kSortThreads = 256;        // threads per radix-sort CTA
+constexpr int kSortKeysPerThread = 16;   // keys per thread per partition
+constexpr int kSortPartition = kSortThreads * kSortKeysPerThread;   // 4096 keys
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
+constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit counts
+
+// ctrl->error bits
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// Look-back spin limit, in polls (each poll ~ a few hundred ns with the backoff);
+// far beyond any legitimate wait, it only bounds a wait that can never end.
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+struct Layout {
+    int64_t n = 0;
+    int W = 0, H = 0, tile = 16;
+    int tiles_x = 0, tiles_y = 0;
+    int64_t ntiles = 0;
+    int tile_bits = 0, key_bits = 0, passes = 0;
+    int64_t cap = 0;
+    int64_t prep_blocks = 0;
+    int64_t sort_parts = 0;
+    size_t off_ctrl = 0, off_rec = 0, off_depth = 0, off_rect = 0, off_touched = 0;
+    size_t off_bsum = 0, off_boff = 0;
+    size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
+    size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
+    size_t off_tfinal = 0, off_last = 0, off_g2 = 0;
+    size_t zero_begin = 0, zero_end = 0;   // region cleared before every render
+    size_t total = 0;
+    int sorted_buffer = 0;
+};
+
+// Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`.
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap);
+// Largest capacity whose layout fits ws_bytes (0 if none).
+int64_t capacity_for(int64_t n, int W, int H, int tile, size_t ws_bytes);
+
+struct Ctrl {
+    uint32_t num_keys;
+    uint32_t error;
+    uint32_t part_counter[kMaxPasses];
+    uint32_t reserved[54];
+};
+static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
+
+// Per-view preprocess parameters (passed by value).
+struct PrepParams {
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* logits;
+    const float* sh;
+    int deg;
+    int n;
+    float R[9], t[3];
+    float fx, fy, cx, cy, near_z;
+    float cam_pos[3];
+    float limx, limy;
+    int W, H, tile, tiles_x, tiles_y;
+    float dilation, alpha_min;
+    float shc[12];           // SH polynomial constants, see sh_constants()
+};
+
+// SH polynomial constants from the normalisation K_l^m (computed in double).
+void sh_constants(float out[12]);
+
+// ---------------------------------------------------------------------------
+// Error-free transforms and float-float arithmetic (Dekker / Knuth), used to
+// carry the camera transform and perspective division beyond float precision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {   // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return make_float2(p, e);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    return fast_two_sum(s.x, e);
+}
+// a.hi/a.lo divided by b.hi/b.lo
+__device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
+    float q = __fdiv_rn(a.x, b.x);
+    float r = __fmaf_rn(-q, b.x, a.x);          // exact remainder of a.x - q b.x
+    r = __fadd_rn(r, __fsub_rn(a.y, __fmul_rn(q, b.y)));
+    float ql = __fdiv_rn(r, b.x);
+    return fast_two_sum(q, ql);
+}
+
+// Kahan's accurate a*b - c*d
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    float w = __fmul_rn(c, d);
+    float e = __fmaf_rn(-c, d, w);
+    float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+// Launchers (host side, enqueue on `stream`).
+void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream);
+void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_t stream);
+// Sorts keys[0] -> keys[L.sorted_buffer] over L.passes digit passes. If `mark` is
+// given it is called with (mark_index, stream) after the histogram, i.e. between
+// the histogram and the first digit pass.
+typedef void (*StageMark)(int, cudaStream_t);
+void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark = nullptr, int mark_index = 0);
+void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
+void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
+                      float alpha_max, float t_stop, float* out_rgb, float* out_alpha,
+                      cudaStream_t stream);
+void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3],
+                     float alpha_min, float alpha_max, float t_stop, const float* d_rgb,
+                     const float* d_alpha, float* d_means, float* d_log_scales, float* d_quats,
+                     float* d_logits, float* d_sh, cudaStream_t stream);
+
+// Standalone sort: generic buffers. `lookback` must hold passes * parts * kRadix words,
+// `hist` passes * kRadix words and `ctrl` one Ctrl, all zeroed by the caller.
+void launch_sort_generic(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_a,
+                         uint32_t* vals_a, uint64_t* keys_b, uint32_t* vals_b, int64_t cap,
+                         const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                         uint32_t* lookback, int64_t parts, Ctrl* ctrl, cudaStream_t stream,
+                         StageMark mark = nullptr, int mark_index = 0);
+
+// *ptr = value, enqueued on the stream (no host synchronisation).
+void launch_set_u32(uint32_t* ptr, uint32_t value, cudaStream_t stream);
+
+}  // namespace vis

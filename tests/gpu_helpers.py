@@ -1,0 +1,70 @@
+"""Shared helpers for the GPU tests (device buffers <-> numpy, workspace views)."""
+import numpy as np
+
+import paper_2512_08478_b300 as vis
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def ws_view(ws, off, count, dtype):
+    """numpy copy of `count` items of `dtype` at byte offset `off` of a workspace."""
+    t = torch()
+    itemsize = np.dtype(dtype).itemsize
+    raw = ws.buf[off: off + count * itemsize].cpu().numpy()
+    return raw.view(dtype).copy()
+
+
+def render_gpu(scene_np, cam, bg=(0.0, 0.0, 0.0), opts=None, key_capacity=None):
+    """Render through the C ABI; returns (rgb [3,H,W] np, alpha np, Scene, Workspace)."""
+    sc = vis.Scene.from_numpy(scene_np)
+    ws = vis.Workspace(sc.n, cam.W, cam.H, key_capacity=key_capacity, opts=opts)
+    rgb, alpha = vis._render_checked(sc, cam, cam.W, cam.H, bg, ws, opts)
+    return rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), sc, ws
+
+
+def gpu_stage_outputs(sc, ws):
+    """Preprocess and sort intermediates from the workspace of the last render."""
+    L = ws.layout()
+    n = sc.n
+    rec = ws_view(ws, L.off_rec, 12 * n, np.float32).reshape(n, 3, 4)
+    touched = ws_view(ws, L.off_touched, n, np.uint32)
+    rect_p = ws_view(ws, L.off_rect, 2 * n, np.uint32).reshape(n, 2)
+    depth = ws_view(ws, L.off_depth, n, np.float32)
+    ctrl = ws_view(ws, L.off_ctrl, 64, np.uint32)
+    m = int(ctrl[0])
+    keys = ws_view(ws, L.off_keys[L.sorted_buffer], m, np.uint64)
+    vals = ws_view(ws, L.off_vals[L.sorted_buffer], m, np.uint32)
+    ntiles = L.tiles_x * L.tiles_y
+    ranges = ws_view(ws, L.off_ranges, 2 * ntiles, np.uint32).reshape(ntiles, 2)
+    rect = np.stack([rect_p[:, 0] & 0xFFFF, rect_p[:, 1] & 0xFFFF, rect_p[:, 0] >> 16, rect_p[:, 1] >> 16], 1)
+    a, b, c = rec[:, 0], rec[:, 1], rec[:, 2]
+    u = a[:, 0].astype(np.float64) + a[:, 2]
+    v = a[:, 1].astype(np.float64) + a[:, 3]
+    f1 = b[:, 0:2].astype(np.float64)
+    f2 = b[:, 2:4].astype(np.float64)
+    Q = f1[:, :, None] * f1[:, None, :] + f2[:, :, None] * f2[:, None, :]
+    return dict(valid=(touched > 0).astype(np.int32), touched=touched, rect=rect.astype(np.int32),
+                zkey=depth, uv=np.stack([u, v], 1), conic=np.stack([Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]], 1),
+                opacity=c[:, 0].astype(np.float64), rgb=c[:, 1:4].astype(np.float64), keys=keys, vals=vals,
+                ranges=ranges, m=m, layout=L)
+
+
+def image_parity(gpu_rgb, gpu_alpha, ref, max_abs=2e-4, mean_abs=1e-5, max_ambiguous_frac=5e-3):
+    """The parity bar: max-abs on unambiguous pixels, mean-abs on all, per channel."""
+    amb = ref["ambiguous"] != 0
+    ok = ~amb
+    frac = amb.mean()
+    d = np.abs(gpu_rgb - ref["rgb"])
+    da = np.abs(gpu_alpha - ref["alpha"])
+    worst = max(d[:, ok].max(initial=0.0), da[ok].max(initial=0.0))
+    print(f"parity: max-abs {worst:.3g} (unambiguous), mean-abs {d.mean():.3g}, ambiguous {amb.sum()} "
+          f"({frac:.2e}), max-abs incl. ambiguous {d.max(initial=0.0):.3g}")
+    assert frac <= max_ambiguous_frac, f"ambiguous fraction {frac}"
+    assert worst <= max_abs, f"max-abs {worst} on unambiguous pixels"
+    for ch in range(3):
+        assert d[ch].mean() <= mean_abs, f"channel {ch} mean-abs {d[ch].mean()}"
+    assert da.mean() <= mean_abs, f"alpha mean-abs {da.mean()}"
+    return dict(max_abs=float(worst), mean_abs=float(d.mean()), ambiguous=int(amb.sum()))

@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/vis.h declares, and rejects bad arguments before any device work."""
+import re
+from pathlib import Path
+
+import pytest
+
+import paper_2512_08478_b300 as vis
+from paper_2512_08478_b300 import build
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return vis.lib()
+
+
+def test_every_declared_function_is_exported(L):
+    header = (ROOT / "include" / "vis.h").read_text()
+    names = re.findall(r"^VIS_API [^(]*?\b(vis_\w+)\s*\(", header, flags=re.M)
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_workspace_queries_and_validation(L):
+    b = vis.vis_workspace_size(10_000, 256, 256, 100_000)
+    lay = vis.vis_workspace_layout(10_000, 256, 256, b)
+    assert lay.key_capacity == 100_000 and lay.total_bytes <= b
+    assert lay.tiles_x == 16 and lay.sort_passes == 5          # 32 depth bits + 8 tile bits
+    lay32 = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(tile=16))
+    assert lay32.sort_passes == 6                                # 8160 tiles -> 13 bits
+    offs = [lay.off_ctrl, lay.off_rec, lay.off_depth, lay.off_rect, lay.off_touched, lay.off_keys[0],
+            lay.off_keys[1], lay.off_vals[0], lay.off_vals[1], lay.off_ranges, lay.off_tfinal, lay.off_last,
+            lay.off_g2]
+    assert all(o % 256 == 0 for o in offs) and len(set(offs)) == len(offs)
+    for bad in (dict(n=0), dict(W=0), dict(H=20000), dict(key_capacity=0), dict(key_capacity=1 << 31)):
+        a = dict(n=10, W=8, H=8, key_capacity=10)
+        a.update(bad)
+        with pytest.raises(vis.VisError) as e:
+            vis.vis_workspace_size(**a)
+        assert e.value.status == vis.VIS_ERR_INVALID_ARG
+    with pytest.raises(vis.VisError):
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(tile=12))
+    with pytest.raises(vis.VisError) as e:
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(digit_bits=4))
+    assert e.value.status == vis.VIS_ERR_UNSUPPORTED
+    with pytest.raises(vis.VisError):
+        vis.vis_workspace_layout(10, 8, 8, 100)        # too small for even one key
+    assert vis.vis_sort_workspace_size(0, 45) > 0
+    with pytest.raises(vis.VisError):
+        vis.vis_sort_workspace_size(10, 65)
+
+
+def test_scene_upload_rejects_null_and_bad_degree(L):
+    import ctypes as C
+    h = C.c_void_p()
+    st = L.vis_scene_upload(None, None, None, None, None, 0, 10, C.byref(h))
+    assert st == vis.VIS_ERR_INVALID_ARG and "null" in vis.vis_last_error()
+    p = C.c_void_p(1 << 20)   # never dereferenced: upload only records pointers
+    st = L.vis_scene_upload(p, p, p, p, p, 4, 10, C.byref(h))
+    assert st == vis.VIS_ERR_INVALID_ARG and "sh_degree" in vis.vis_last_error()
+    st = L.vis_scene_upload(p, p, C.c_void_p((1 << 20) + 4), p, p, 0, 10, C.byref(h))
+    assert st == vis.VIS_ERR_INVALID_ARG and "aligned" in vis.vis_last_error()
+    st = L.vis_scene_upload(p, p, p, p, p, 3, 10, C.byref(h))
+    assert st == vis.VIS_OK
+    L.vis_scene_destroy(h)
