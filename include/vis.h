@@ -182,6 +182,29 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
                           uint32_t* vals_out, int64_t m, int key_bits, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* The same sort for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a library convenience). Some callers may not call cudaMalloc
+ * where they sort -- a real-time loop with a fixed memory budget, a plug-in whose
+ * host application owns all device allocations, code that must not risk the device
+ * synchronisation an allocation can cause -- so they cannot pass the workspace
+ * vis_sort_pairs needs. This entry point allocates nothing: its scratch is a fixed
+ * array of VIS_SORT_NOALLOC_SCRATCH_BYTES (about 14 MiB) of static device memory
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits. The caller still passes the inputs and outputs, as for
+ * vis_sort_pairs (same layout, alignment and stability).
+ *  m          0 .. VIS_SORT_NOALLOC_MAX_KEYS; larger m returns VIS_ERR_INVALID_ARG
+ *  key_bits   1..64
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture. Every call shares the one array (it is cleared where needed
+ * at the start of each call), so calls whose GPU work overlaps -- on different
+ * streams, or from different threads -- race and must be serialised by the caller. */
+#define VIS_SORT_NOALLOC_MAX_KEYS (1 << 20)
+#define VIS_SORT_NOALLOC_SCRATCH_BYTES 14688512
+VIS_API vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
+                                          uint64_t* keys_out, uint32_t* vals_out, int64_t m,
+                                          int key_bits, void* stream);
+
 /* Per-stage timing of vis_render (tracing; the paper times its frame by stages,
  * Table 1 "Sort" vs "Prep.+Draw"). Between vis_profile_begin and vis_profile_end,
  * every vis_render records CUDA events on its stream between its stages, for up

@@ -77,6 +77,10 @@ def lib():
                                               C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
             "vis_sort_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
+            "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
+            "vis_profile_begin": (C.c_int, []),
+            "vis_profile_end": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -195,6 +199,12 @@ def vis_sort_workspace_size(m, key_bits):
 def vis_sort_pairs(keys_in, vals_in, keys_out, vals_out, key_bits, ws, stream=None):
     _ok(lib().vis_sort_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), int(keys_in.numel()),
                              int(key_bits), _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def vis_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, key_bits, stream=None):
+    """Same sort with the library's static device scratch (no workspace; m <= 2^20)."""
+    _ok(lib().vis_sort_pairs_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                     int(keys_in.numel()), int(key_bits), _stream(stream)))
 
 
 def vis_last_error():

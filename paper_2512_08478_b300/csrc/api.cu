@@ -131,6 +131,8 @@ void prof_mark(int k, cudaStream_t stream) {
 
 namespace vis {
 
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 // K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!); the real SH polynomials in (x, y, z)
 // on the unit sphere (Condon-Shortley phase) are products of these with
 // (-1)^m d^m P_l/dz^m and Re/Im (x + i y)^m, so the constants below are:

@@ -146,6 +146,9 @@ void launch_sort_generic(const uint64_t* keys_in, const uint32_t* vals_in, uint6
                          uint32_t* lookback, int64_t parts, Ctrl* ctrl, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0);
 
+// Sets the thread-local message returned by vis_last_error().
+void set_last_error(const char* msg);
+
 // *ptr = value, enqueued on the stream (no host synchronisation).
 void launch_set_u32(uint32_t* ptr, uint32_t value, cudaStream_t stream);
 
