@@ -37,8 +37,13 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
+kDP = 4   # depth passes of sort_mode 1
 METRIC = "1080p frame ms at 1M/6M Gaussians SH3; fwd+bwd ms; sort keys/s vs HBM peak"
 STAGES = ["clear", "preprocess", "duplicate", "sort_histogram", "sort_passes", "ranges", "composite"]
+# sort_mode 1 (depth first): "duplicate" = compaction + depth sort + emission in depth order,
+# "sort_histogram"/"sort_passes" = the stable sort by tile id of 4-byte keys
+STAGES_DF = ["clear", "preprocess", "depth_sort_and_emit", "tile_sort_histogram", "tile_sort_passes", "ranges",
+             "composite"]
 
 
 def _peaks():
@@ -162,7 +167,8 @@ def run_ours(args):
     sc = vis.Scene.from_numpy(sc_np)
     n = sc.n
     cap = 16 * n + (1 << 20)
-    ws = vis.Workspace(n, W, H, key_capacity=cap)
+    opts = vis.make_opts(sort_mode=args.sort_mode)
+    ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
     stream = torch.cuda.current_stream()
@@ -179,14 +185,14 @@ def run_ours(args):
 
     def frame(i):
         c = cam_objs[(view0 + i) % len(cam_objs)]
-        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         if fwdbwd:
             torch.sub(rgb, tgt_rgb, out=d_rgb)
             d_rgb.mul_(2.0 / rgb.numel())
-            vis.vis_render_backward(sc.handle, c, W, H, (0.0, 0.0, 0.0), d_rgb, d_alpha, ws.buf, grads)
+            vis.vis_render_backward(sc.handle, c, W, H, (0.0, 0.0, 0.0), d_rgb, d_alpha, ws.buf, grads, opts)
 
     if fwdbwd:   # target image of view 0 (fixed), rendered once outside the timing
-        vis.vis_render(tgt.handle, cam_objs[0], W, H, (0.0, 0.0, 0.0), tgt_rgb, tgt_a, ws.buf)
+        vis.vis_render(tgt.handle, cam_objs[0], W, H, (0.0, 0.0, 0.0), tgt_rgb, tgt_a, ws.buf, opts)
         vis.vis_check(ws.buf)
 
     for i in range(args.warmup):
@@ -220,25 +226,28 @@ def run_ours(args):
     frames_total = args.steps * world
     value = t_ms / frames_total
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
+    names = STAGES_DF if args.sort_mode == 1 else STAGES
     passes = npass.value
 
     # keys per frame averaged over the views used
     mlist = []
     for i in range(min(args.steps, len(cam_objs))):
         c = cam_objs[(view0 + i) % len(cam_objs)]
-        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         mlist.append(vis.vis_check(ws.buf))
     M = float(np.mean(mlist))
 
     # ---- roofline of the dominant stage ----
     peaks = _peaks()
-    dom = max(("preprocess", "sort_passes", "composite", "duplicate"), key=lambda s: stage_ms[s])
+    dom = max(("preprocess", "sort_passes", "composite"), key=lambda s: stage_ms[s])
     sh_k = (desc["sh_degree"] + 1) ** 2
     bytes_pre = n * (12 + 12 + 16 + 4 + 12 * sh_k) + n * (48 + 4 + 8 + 4)
     if dom == "sort_passes":
         launch_ms = stage_ms["sort_passes"] / passes
-        algo = 24.0 * M
-        unit_note = "24 B per key per digit pass (8 B key + 4 B value, read and written)"
+        per_key = 24.0 if args.sort_mode == 0 else 16.0
+        algo = per_key * M
+        unit_note = (f"{int(per_key)} B per key per digit pass ({'8' if args.sort_mode == 0 else '4'} B key + "
+                     f"4 B value, read and written)")
     elif dom == "preprocess":
         launch_ms = stage_ms["preprocess"]
         algo = float(bytes_pre)
@@ -249,23 +258,25 @@ def run_ours(args):
         unit_note = "per key: value + gathered 48 B record; per pixel: rgb, alpha, T, last written"
     achieved = algo / (launch_ms * 1e-3) / 1e9
     traffic = _committed_traffic(dom, M, n)
-    roof = dict(kernel=dom, bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+    roof = dict(kernel=names[STAGES.index(dom)], bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
                 frac=round(achieved / peaks["hbm_gbs"], 4), traffic=traffic,
                 peak_source=peaks["source"], algorithmic_bytes_per_launch=int(algo), launch_ms=round(launch_ms, 4),
                 bytes_model=unit_note)
 
     # ---- end to end through the C ABI with host buffers ----
-    e2e = run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist)
+    e2e = run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts)
 
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(desc, l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
+                config=dict(desc, sort_mode=args.sort_mode,
+                            l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk.summary(), e2e=e2e,
-                gpu_launches=int(args.steps * (6 + passes + (2 if fwdbwd else 0))),
+                gpu_launches=int(args.steps * ((6 + passes) if args.sort_mode == 0 else (11 + kDP + passes))
+                                 + (2 * args.steps if fwdbwd else 0)),
                 roofline=roof,
-                stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
                 keys_per_frame=int(M), sort_passes=passes,
                 sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]) * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
@@ -293,12 +304,12 @@ def _committed_traffic(kernel, M, n):
     return None
 
 
-def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist):
+def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts):
     """Every step: H2D of the scene from pinned memory, render, D2H of rgb + alpha."""
     host = {k: torch.from_numpy(sc_np[k]).pin_memory() for k in vis.FIELDS}
     dev = {k: torch.empty(host[k].shape, dtype=torch.float32, device="cuda") for k in vis.FIELDS}
     sc = vis.Scene(**dev, sh_degree=sc_np["sh_degree"])
-    ws = vis.Workspace(sc.n, W, H, key_capacity=cap)
+    ws = vis.Workspace(sc.n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
     out_rgb = torch.empty((3, H, W)).pin_memory()
@@ -310,7 +321,7 @@ def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist):
     def step(i):
         for k in vis.FIELDS:
             dev[k].copy_(host[k], non_blocking=True)
-        vis.vis_render(sc.handle, cam_objs[i % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf)
+        vis.vis_render(sc.handle, cam_objs[i % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         out_rgb.copy_(rgb, non_blocking=True)
         out_a.copy_(alpha, non_blocking=True)
 
@@ -412,6 +423,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--sort-mode", type=int, default=1, choices=[0, 1],
+                    help="0: one sort of 64-bit (tile, depth) keys; 1: depth-first sort then tile sort")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -75,6 +75,12 @@ typedef struct {
  *  alpha_max   alpha is clamped to alpha_max (default 0.99)
  *  t_stop      compositing stops before the first splat that would bring the
  *              transmittance below t_stop (default 1e-4)
+ *  sort_mode   how the (tile, depth, index) order is produced (Algorithm 1, "Radix Sort"):
+ *              0 = one LSD sort of 64-bit (tile << 32 | depth) keys;
+ *              1 = depth first (default): the surviving splats are sorted once by
+ *                  32-bit depth (as in the paper), their tile copies are emitted in that
+ *                  order and stably sorted by tile id alone. Both give the same order
+ *                  bit for bit; 1 moves about a quarter of the bytes.
  * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
 typedef struct {
     int tile;
@@ -83,6 +89,7 @@ typedef struct {
     float alpha_min;
     float alpha_max;
     float t_stop;
+    int sort_mode;
 } vis_render_opts;
 
 VIS_API void vis_default_opts(vis_render_opts* opts);
@@ -101,12 +108,14 @@ typedef struct {
     size_t off_depth;        /* float[n] view depth (the sort key's low word) */
     size_t off_rect;         /* uint2[n] tile rect: x0 | x1<<16, y0 | y1<<16 (upper bounds exclusive) */
     size_t off_touched;      /* uint32[n] tiles touched (0 if culled) */
-    size_t off_keys[2];      /* uint64[cap] (tile << 32) | float bits of depth */
+    size_t off_keys[2];      /* key_bytes x cap: sort keys (see key_bytes) */
     size_t off_vals[2];      /* uint32[cap] Gaussian index */
     size_t off_ranges;       /* uint2[tiles] [start, end) into the sorted keys */
     size_t off_tfinal;       /* float[H*W] final transmittance */
     size_t off_last;         /* int32[H*W] 1 + position, in the sorted key list, of the last composited splat (0 if none) */
     size_t off_g2;           /* float[n][9] screen-space gradients (backward scratch) */
+    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1) */
+    int sort_mode;
 } vis_ws_layout;
 
 /* Device-written status block at workspace offset off_ctrl (= 0). */
@@ -188,7 +197,7 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
  * host application owns all device allocations, code that must not risk the device
  * synchronisation an allocation can cause -- so they cannot pass the workspace
  * vis_sort_pairs needs. This entry point allocates nothing: its scratch is a fixed
- * array of VIS_SORT_NOALLOC_SCRATCH_BYTES (about 14 MiB) of static device memory
+ * array of VIS_SORT_NOALLOC_SCRATCH_BYTES (about 16 MiB) of static device memory
  * inside the library, which every GPU that loads the library holds until the
  * process exits. The caller still passes the inputs and outputs, as for
  * vis_sort_pairs (same layout, alignment and stability).
@@ -200,7 +209,7 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
  * at the start of each call), so calls whose GPU work overlaps -- on different
  * streams, or from different threads -- race and must be serialised by the caller. */
 #define VIS_SORT_NOALLOC_MAX_KEYS (1 << 20)
-#define VIS_SORT_NOALLOC_SCRATCH_BYTES 14688512
+#define VIS_SORT_NOALLOC_SCRATCH_BYTES 16785664
 VIS_API vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
                                           uint64_t* keys_out, uint32_t* vals_out, int64_t m,
                                           int key_bits, void* stream);

@@ -38,7 +38,8 @@ class vis_camera(C.Structure):
 
 class vis_render_opts(C.Structure):
     _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
-                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float)]
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
+                ("sort_mode", C.c_int)]
 
 
 class vis_ws_layout(C.Structure):
@@ -47,7 +48,8 @@ class vis_ws_layout(C.Structure):
                 ("off_ctrl", C.c_size_t), ("off_rec", C.c_size_t), ("off_depth", C.c_size_t),
                 ("off_rect", C.c_size_t), ("off_touched", C.c_size_t), ("off_keys", C.c_size_t * 2),
                 ("off_vals", C.c_size_t * 2), ("off_ranges", C.c_size_t), ("off_tfinal", C.c_size_t),
-                ("off_last", C.c_size_t), ("off_g2", C.c_size_t)]
+                ("off_last", C.c_size_t), ("off_g2", C.c_size_t), ("key_bytes", C.c_int),
+                ("sort_mode", C.c_int)]
 
 
 _P = C.c_void_p

@@ -63,6 +63,8 @@ vis_render_opts resolve_opts(const vis_render_opts* o) {
 vis_status check_opts(const vis_render_opts& o) {
     if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
     if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
+    if (o.sort_mode != vis::kSortTileDepth && o.sort_mode != vis::kSortDepthFirst)
+        return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0 or 1 (got %d)", o.sort_mode);
     if (!(o.dilation >= 0.f) || !std::isfinite(o.dilation)) return fail(VIS_ERR_INVALID_ARG, "dilation must be finite and >= 0");
     if (!(o.alpha_min > 0.f && o.alpha_min < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_min must be in (0, 1)");
     if (!(o.alpha_max > 0.f && o.alpha_max < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_max must be in (0, 1)");
@@ -158,26 +160,30 @@ void sh_constants(float out[12]) {
     out[10] = out[11] = 0.f;
 }
 
-Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap) {
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     Layout L;
+    L.mode = mode;
     L.n = n; L.W = W; L.H = H; L.tile = tile;
     L.tiles_x = (W + tile - 1) / tile;
     L.tiles_y = (H + tile - 1) / tile;
     L.ntiles = (int64_t)L.tiles_x * L.tiles_y;
     L.tile_bits = ceil_log2(L.ntiles);
-    L.key_bits = 32 + L.tile_bits;
-    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
     L.cap = cap;
     L.prep_blocks = (n + kPrepThreads - 1) / kPrepThreads;
-    L.sort_parts = (cap + kSortPartition - 1) / kSortPartition;
+    const bool df = mode == kSortDepthFirst;
+    L.key_bits = df ? L.tile_bits : 32 + L.tile_bits;
+    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
+    L.key_bytes = df ? 4 : 8;
+    L.sort_parts = df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap);
     L.sorted_buffer = L.passes & 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     // cleared every frame: status block, histograms, look-back words, tile ranges
     L.zero_begin = off;
     L.off_ctrl = take(sizeof(Ctrl));
-    L.off_hist = take(sizeof(uint32_t) * kMaxPasses * kRadix);
-    L.off_lookback = take(sizeof(uint32_t) * (size_t)L.passes * L.sort_parts * kRadix);
+    L.off_hist = take(sizeof(uint32_t) * 2 * kMaxPasses * kRadix);
+    L.lookback_words_depth = df ? (size_t)kDepthPasses * sort_parts<uint32_t>(n) * kRadix : 0;
+    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * kRadix));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     L.zero_end = off;
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
@@ -186,8 +192,14 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap) {
     L.off_touched = take(sizeof(uint32_t) * (size_t)n);
     L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    L.off_keys[0] = take(sizeof(uint64_t) * (size_t)cap);
-    L.off_keys[1] = take(sizeof(uint64_t) * (size_t)cap);
+    if (df) {
+        L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+        L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+        for (int b = 0; b < 2; ++b) L.off_dkeys[b] = take(sizeof(uint32_t) * (size_t)n);
+        for (int b = 0; b < 2; ++b) L.off_dvals[b] = take(sizeof(uint32_t) * (size_t)n);
+    }
+    L.off_keys[0] = take((size_t)L.key_bytes * (size_t)cap);
+    L.off_keys[1] = take((size_t)L.key_bytes * (size_t)cap);
     L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
     L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
     L.off_tfinal = take(sizeof(float) * (size_t)W * H);
@@ -197,12 +209,12 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap) {
     return L;
 }
 
-int64_t capacity_for(int64_t n, int W, int H, int tile, size_t ws_bytes) {
-    if (make_layout(n, W, H, tile, 1).total > ws_bytes) return 0;
+int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes) {
+    if (make_layout(n, W, H, tile, 1, mode).total > ws_bytes) return 0;
     int64_t lo = 1, hi = kMaxKeys;
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
-        if (make_layout(n, W, H, tile, mid).total <= ws_bytes) lo = mid; else hi = mid - 1;
+        if (make_layout(n, W, H, tile, mid, mode).total <= ws_bytes) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -219,6 +231,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->alpha_min = 1.0f / 255.0f;
     o->alpha_max = 0.99f;
     o->t_stop = 1e-4f;
+    o->sort_mode = vis::kSortDepthFirst;
 }
 
 const char* vis_last_error(void) { return g_err.c_str(); }
@@ -256,7 +269,7 @@ vis_status vis_workspace_size(int64_t n, int W, int H, int64_t key_capacity, con
     if ((st = check_opts(o))) return st;
     if (key_capacity < 1 || key_capacity > (int64_t)vis::kMaxKeys)
         return fail(VIS_ERR_INVALID_ARG, "key_capacity must be in [1, 2^30-1]");
-    *bytes = vis::make_layout(n, W, H, o.tile, key_capacity).total;
+    *bytes = vis::make_layout(n, W, H, o.tile, key_capacity, o.sort_mode).total;
     return VIS_OK;
 }
 
@@ -267,9 +280,9 @@ vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const 
     if (st) return st;
     const vis_render_opts o = resolve_opts(opts);
     if ((st = check_opts(o))) return st;
-    const int64_t cap = vis::capacity_for(n, W, H, o.tile, ws_bytes);
+    const int64_t cap = vis::capacity_for(n, W, H, o.tile, o.sort_mode, ws_bytes);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
-    const vis::Layout L = vis::make_layout(n, W, H, o.tile, cap);
+    const vis::Layout L = vis::make_layout(n, W, H, o.tile, cap, o.sort_mode);
     out->total_bytes = L.total;
     out->key_capacity = L.cap;
     out->tiles_x = L.tiles_x; out->tiles_y = L.tiles_y;
@@ -280,6 +293,8 @@ vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const 
     out->off_vals[0] = L.off_vals[0]; out->off_vals[1] = L.off_vals[1];
     out->off_ranges = L.off_ranges; out->off_tfinal = L.off_tfinal; out->off_last = L.off_last;
     out->off_g2 = L.off_g2;
+    out->key_bytes = L.key_bytes;
+    out->sort_mode = L.mode;
     return VIS_OK;
 }
 
@@ -295,9 +310,9 @@ static vis_status prepare(vis_scene_t scene, const vis_camera* cam, int W, int H
     *o = resolve_opts(opts);
     if ((st = check_opts(*o))) return st;
     if (!ws || !aligned16(ws)) return fail(VIS_ERR_INVALID_ARG, "workspace is null or not 16-byte aligned");
-    const int64_t cap = vis::capacity_for(scene->n, W, H, o->tile, ws_bytes);
+    const int64_t cap = vis::capacity_for(scene->n, W, H, o->tile, o->sort_mode, ws_bytes);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
-    *L = vis::make_layout(scene->n, W, H, o->tile, cap);
+    *L = vis::make_layout(scene->n, W, H, o->tile, cap, o->sort_mode);
     return VIS_OK;
 }
 
@@ -318,11 +333,17 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     prof_mark(1, stream);
     vis::launch_preprocess(p, L, w, stream);
     prof_mark(2, stream);
-    vis::launch_scan_and_duplicate(L, w, scene->n, stream);
-    prof_mark(3, stream);
-    vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark : nullptr, 4);
-    prof_mark(5, stream);
-    vis::launch_ranges(L, w, stream);
+    if (L.mode == vis::kSortDepthFirst) {
+        vis::launch_depth_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
+        prof_mark(5, stream);
+        vis::launch_ranges32(L, w, stream);
+    } else {
+        vis::launch_scan_and_duplicate(L, w, scene->n, stream);
+        prof_mark(3, stream);
+        vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark : nullptr, 4);
+        prof_mark(5, stream);
+        vis::launch_ranges(L, w, stream);
+    }
     prof_mark(6, stream);
     vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, out_rgb, out_alpha, stream);
     prof_mark(7, stream);
@@ -411,7 +432,7 @@ vis_status vis_profile_end(double* stage_ms, int max_stages, int* n_stages, int*
 // ping-pong key/value buffer.
 static size_t sort_ws_layout(int64_t m, int passes, size_t* off_hist, size_t* off_lb, size_t* off_k, size_t* off_v,
                              int64_t* parts) {
-    *parts = (m + vis::kSortPartition - 1) / vis::kSortPartition;
+    *parts = vis::sort_parts<uint64_t>(m);
     size_t off = align_up(sizeof(vis::Ctrl), 256);
     *off_hist = off; off = align_up(off + sizeof(uint32_t) * vis::kMaxPasses * vis::kRadix, 256);
     *off_lb = off; off = align_up(off + sizeof(uint32_t) * (size_t)passes * (*parts) * vis::kRadix, 256);
@@ -455,10 +476,10 @@ vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
     vis::Ctrl* ctrl = reinterpret_cast<vis::Ctrl*>(w);
     if ((st = cuda_check(cudaMemsetAsync(w, 0, off_k, stream), "clear sort workspace"))) return st;
     vis::launch_set_u32(&ctrl->num_keys, (uint32_t)m, stream);
-    vis::launch_sort_generic(keys_in, vals_in, keys_out, vals_out, reinterpret_cast<uint64_t*>(w + off_k),
-                             reinterpret_cast<uint32_t*>(w + off_v), m, &ctrl->num_keys, passes,
-                             reinterpret_cast<uint32_t*>(w + off_hist), reinterpret_cast<uint32_t*>(w + off_lb),
-                             parts, ctrl, stream);
+    vis::launch_sort_generic<uint64_t>(keys_in, vals_in, keys_out, vals_out, reinterpret_cast<uint64_t*>(w + off_k),
+                                       reinterpret_cast<uint32_t*>(w + off_v), m, &ctrl->num_keys, passes,
+                                       reinterpret_cast<uint32_t*>(w + off_hist), reinterpret_cast<uint32_t*>(w + off_lb),
+                                       ctrl->part_counter, &ctrl->error, stream);
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;

@@ -1,0 +1,196 @@
+// Depth-first ordering of the splats: the sort of Algorithm 1 ("Radix Sort" over the
+// depths of the surviving splats, section 3.4), followed by a stable bucketing of
+// their tile copies by tile.
+//
+//   1. compact_visible: surviving Gaussians (tiles touched > 0), in index order, as
+//      (float bits of depth, index) pairs; the count goes to the status block.
+//   2. a stable radix sort of those pairs by the 32-bit depth key (4 passes of 8 bits;
+//      equal depths keep index order);
+//   3. depth_touch_sums / scan / emit_tiles: every sorted splat emits one (tile id,
+//      index) pair per tile of its rectangle, in depth order (same deterministic
+//      warp-cooperative emission as the index-order duplication);
+//   4. a stable radix sort of those pairs by the tile id alone (ceil(tile bits / 8)
+//      passes of 32-bit keys);
+//   5. ranges_kernel32: [start, end) of every tile.
+// Stability makes the final order (tile, depth, index) -- identical to sorting the
+// 64-bit (tile << 32 | depth) keys -- while the sort moves 4-byte keys, and only the
+// N surviving splats (not the M tile copies) take part in the four depth passes.
+#include "vis_internal.cuh"
+
+namespace vis {
+
+// exclusive warp scan helper
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block sums of `flag(i)` over blocks of kPrepThreads, for i < n.
+__global__ void __launch_bounds__(kPrepThreads)
+visible_block_sums(const uint32_t* __restrict__ touched, int64_t n, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t ws[kPrepThreads / 32];
+    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const uint32_t f = (i < n && touched[i] > 0) ? 1u : 0u;
+    const uint32_t b = __popc(__ballot_sync(0xffffffffu, f));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kPrepThreads / 32; ++w) t += ws[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ depth, int64_t n,
+                const uint32_t* __restrict__ boff, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals) {
+    __shared__ uint32_t ws[kPrepThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    const bool f = i < n && touched[i] > 0;
+    const uint32_t bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[warp] = __popc(bal);
+    __syncthreads();
+    uint32_t off = boff[blockIdx.x];
+    for (int w = 0; w < warp; ++w) off += ws[w];
+    if (f) {
+        const uint32_t o = off + __popc(bal & ((1u << lane) - 1u));
+        dkeys[o] = __float_as_uint(depth[i]);   // z > near > 0: bit order = numeric order
+        dvals[o] = (uint32_t)i;
+    }
+}
+
+// Block sums of tiles touched, in depth order.
+__global__ void __launch_bounds__(kPrepThreads)
+depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched,
+                 const uint32_t* __restrict__ num_visible, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t ws[kPrepThreads / 32];
+    const int64_t nv = *num_visible;
+    const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    uint32_t c = (j < nv) ? touched[dvals[j]] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kPrepThreads / 32; ++w) t += ws[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+emit_tiles(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
+           const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
+           const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    if (ctrl->error & kErrCapacity) return;
+    __shared__ uint32_t s_start[kPrepThreads];
+    __shared__ uint32_t s_g[kPrepThreads];
+    __shared__ uint32_t warp_tot[kPrepThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nv = *num_visible;
+    const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
+    uint32_t g = 0, cnt = 0;
+    if (j < nv) { g = dvals[j]; cnt = touched[g]; }
+    const uint32_t incl = warp_incl_scan(cnt, lane);
+    s_start[threadIdx.x] = incl - cnt;
+    s_g[threadIdx.x] = g;
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t warp_base = boff[blockIdx.x];
+    for (int w = 0; w < warp; ++w) warp_base += warp_tot[w];
+    const uint32_t run = warp_tot[warp];
+    const int g0 = warp * 32;
+    for (uint32_t q = lane; q < run; q += 32) {
+        // owner: the last slot of the warp whose start is <= q (zero counts share starts)
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_start[g0 + mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t gi = s_g[g0 + lo];
+        const uint2 r = rect[gi];
+        const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu;
+        const uint32_t w = x1 - x0;
+        const uint32_t k = q - s_start[g0 + lo];
+        keys[warp_base + q] = (y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w);
+        vals[warp_base + q] = gi;
+    }
+}
+
+__global__ void ranges_kernel32(const uint32_t* __restrict__ keys, const Ctrl* __restrict__ ctrl, int64_t cap,
+                                uint2* __restrict__ ranges) {
+    if (ctrl->error) return;
+    const int64_t m = min((int64_t)ctrl->num_keys, cap);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[j];
+        if (j == 0 || keys[j - 1] != t) ranges[t].x = (uint32_t)j;
+        if (j == m - 1 || keys[j + 1] != t) ranges[t].y = (uint32_t)(j + 1);
+    }
+}
+
+static int sms() {
+    int dev = 0, s = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    return s;
+}
+
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
+    const int blocks_n = (int)L.prep_blocks;
+    uint32_t* bvis = reinterpret_cast<uint32_t*>(ws + L.off_bsum);
+    uint32_t* bvis_off = reinterpret_cast<uint32_t*>(ws + L.off_boff);
+    uint32_t* dk0 = reinterpret_cast<uint32_t*>(ws + L.off_dkeys[0]);
+    uint32_t* dk1 = reinterpret_cast<uint32_t*>(ws + L.off_dkeys[1]);
+    uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[0]);
+    uint32_t* dv1 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[1]);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
+    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
+
+    // 1. compaction of the surviving splats, in index order
+    visible_block_sums<<<blocks_n, kPrepThreads, 0, stream>>>(touched, L.n, bvis);
+    launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0, stream);
+    compact_visible<<<blocks_n, kPrepThreads, 0, stream>>>(touched, reinterpret_cast<const float*>(ws + L.off_depth),
+                                                           L.n, bvis_off, dk0, dv0);
+    // 2. sort by depth (4 passes; the result lands in buffer 0)
+    launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
+                                  ctrl->part_counter, &ctrl->error, stream);
+    // 3. tile copies in depth order
+    uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
+    uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
+    depth_touch_sums<<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, &ctrl->num_visible, bsum2);
+    launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
+    uint32_t* k0 = reinterpret_cast<uint32_t*>(ws + L.off_keys[0]);
+    uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
+    uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
+    emit_tiles<<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect),
+                                                      &ctrl->num_visible, boff2, L.tiles_x, ctrl, k0, v0);
+    if (mark) mark(mark_index, stream);
+    // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer
+    const int tp = L.passes;
+    uint32_t* ka = L.sorted_buffer ? k1 : k0;
+    uint32_t* va = L.sorted_buffer ? v1 : v0;
+    uint32_t* kb = L.sorted_buffer ? k0 : k1;
+    uint32_t* vb = L.sorted_buffer ? v0 : v1;
+    launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp, hist + kMaxPasses * kRadix,
+                                  lb + L.lookback_words_depth, ctrl->part_counter + kMaxPasses, &ctrl->error, stream,
+                                  mark, mark_index + 1);
+    (void)sms;
+}
+
+void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream) {
+    const int64_t want = (L.cap + 255) / 256, lim = (int64_t)sms() * 8;
+    const int blocks = (int)(want < 1 ? 1 : (want < lim ? want : lim));
+    ranges_kernel32<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint32_t*>(ws + L.off_keys[L.sorted_buffer]),
+                                                reinterpret_cast<const Ctrl*>(ws + L.off_ctrl), L.cap,
+                                                reinterpret_cast<uint2*>(ws + L.off_ranges));
+}
+
+}  // namespace vis

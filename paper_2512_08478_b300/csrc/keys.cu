@@ -16,9 +16,11 @@
 
 namespace vis {
 
+// Exclusive scan of per-block sums; the total goes to *total, and if `error` is given
+// a total above `cap` sets kErrCapacity there.
 __global__ void __launch_bounds__(1024)
 scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
-                Ctrl* ctrl, int64_t cap) {
+                uint32_t* total_out, uint32_t* error, int64_t cap) {
     __shared__ uint32_t warp_tot[32];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
@@ -55,9 +57,14 @@ scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, 
     }
     if (threadIdx.x == 0) {
         const unsigned long long total = carry;
-        ctrl->num_keys = (uint32_t)min(total, (unsigned long long)0xffffffffu);
-        if (total > (unsigned long long)cap) atomicOr(&ctrl->error, kErrCapacity);
+        *total_out = (uint32_t)min(total, (unsigned long long)0xffffffffu);
+        if (error && total > (unsigned long long)cap) atomicOr(error, kErrCapacity);
     }
+}
+
+void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
+                      int64_t cap, cudaStream_t stream) {
+    scan_block_sums<<<1, 1024, 0, stream>>>(bsum, boff, nblocks, total, error, cap);
 }
 
 __global__ void __launch_bounds__(kPrepThreads)
@@ -109,7 +116,7 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* bsum = reinterpret_cast<const uint32_t*>(ws + L.off_bsum);
     uint32_t* boff = reinterpret_cast<uint32_t*>(ws + L.off_boff);
-    scan_block_sums<<<1, 1024, 0, stream>>>(bsum, boff, L.prep_blocks, ctrl, L.cap);
+    launch_scan_sums(bsum, boff, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
     if (n <= 0) return;
     duplicate_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
         reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint2*>(ws + L.off_rect),

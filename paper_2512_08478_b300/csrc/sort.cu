@@ -8,7 +8,7 @@
 //  - sort_histogram: one read of all keys builds the digit histograms of every
 //    pass at once (shared-memory counters, one global atomic per bin per CTA).
 //  - sort_pass (one launch per 8-bit digit): a CTA takes the next partition of
-//    4096 keys from an atomic ticket (so partitions start in order and the
+//    2048 64-bit or 4096 32-bit keys from an atomic ticket (so partitions start in order and the
 //    look-back below always makes progress), ranks its keys stably per warp with
 //    __match_any_sync, publishes its per-digit counts, and resolves its global
 //    offsets by decoupled look-back over the preceding partitions' published
@@ -25,9 +25,10 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 
+template <typename K>
 __global__ void __launch_bounds__(256)
-sort_histogram(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap,
-               int passes, uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
+sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap, int passes,
+               uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -35,7 +36,7 @@ sort_histogram(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n
     const int64_t m = min((int64_t)*num_keys, cap);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
-        const uint64_t k = keys[j];
+        const K k = keys[j];
         for (int p = 0; p < passes; ++p)
             atomicAdd(&sh[p * kRadix + (uint32_t)((k >> (kRadixBits * p)) & (kRadix - 1))], 1u);
     }
@@ -78,9 +79,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_
 
 static_assert(kSortThreads == kRadix, "one digit per thread");
 
+template <typename K>
 struct SortSmem {
-    uint64_t keys[kSortPartition];
-    uint32_t vals[kSortPartition];
+    static constexpr int KPT = SortKPT<K>::value;
+    K keys[kSortThreads * KPT];
+    uint32_t vals[kSortThreads * KPT];
     uint32_t whist[kSortThreads / 32][kRadix];
     uint32_t digit_off[kRadix];
     uint32_t local_start[kRadix];
@@ -89,14 +92,18 @@ struct SortSmem {
     uint32_t bad;
 };
 
-__global__ void __launch_bounds__(kSortThreads)
-sort_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-          uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+// Three CTAs of 256 threads per SM: at most 85 registers per thread.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads, 3)
+sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+          K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
           const uint32_t* __restrict__ num_keys, int64_t cap, int shift,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
+    constexpr int KPT = SortKPT<K>::value;
+    constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+    SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_relaxed(error) & kErrCapacity) return;
     const int64_t m = min((int64_t)*num_keys, cap);
@@ -107,26 +114,26 @@ sort_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ val
     for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t part = S.part;
-    const int64_t base = (int64_t)part * kSortPartition;
+    const int64_t base = (int64_t)part * PART;
     if (base >= m) return;
 
     // ---- load (warp-striped: warp w owns keys [w*512, (w+1)*512) of the partition) ----
-    uint64_t key[kSortKeysPerThread];
-    uint32_t val[kSortKeysPerThread];
-    const int64_t wbase = base + (int64_t)warp * (32 * kSortKeysPerThread);
+    K key[KPT];
+    uint32_t val[KPT];
+    const int64_t wbase = base + (int64_t)warp * (32 * KPT);
 #pragma unroll
-    for (int k = 0; k < kSortKeysPerThread; ++k) {
+    for (int k = 0; k < KPT; ++k) {
         const int64_t idx = wbase + k * 32 + lane;
         if (idx < m) { key[k] = keys_in[idx]; val[k] = vals_in[idx]; }
         else { key[k] = 0; val[k] = 0; }
     }
 
     // ---- stable per-warp ranking ----
-    uint32_t rank[kSortKeysPerThread];
+    uint32_t rank[KPT];
     uint32_t* wh = S.whist[warp];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int k = 0; k < kSortKeysPerThread; ++k) {
+    for (int k = 0; k < KPT; ++k) {
         const bool valid = (wbase + k * 32 + lane) < m;
         const uint32_t d = (uint32_t)(key[k] >> shift) & (kRadix - 1);
         const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (kRadix + lane));
@@ -183,7 +190,7 @@ sort_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ val
 
     // ---- reorder by digit in shared memory ----
 #pragma unroll
-    for (int k = 0; k < kSortKeysPerThread; ++k) {
+    for (int k = 0; k < KPT; ++k) {
         if ((wbase + k * 32 + lane) < m) {
             const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
             const uint32_t pos = S.local_start[dk] + wh[dk] + rank[k];
@@ -195,9 +202,9 @@ sort_pass(const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ val
     if (S.bad) return;
 
     // ---- write out in digit runs ----
-    const int n_in = (int)((m - base) < kSortPartition ? (m - base) : kSortPartition);
+    const int n_in = (int)((m - base) < PART ? (m - base) : PART);
     for (int i = tid; i < n_in; i += kSortThreads) {
-        const uint64_t kk = S.keys[i];
+        const K kk = S.keys[i];
         const uint32_t dk = (uint32_t)(kk >> shift) & (kRadix - 1);
         const uint32_t dest = S.digit_off[dk] + (uint32_t)i;   // modular: digit_off may wrap
         if ((int64_t)dest < m) {
@@ -220,35 +227,43 @@ static int sm_count() {
     return sms;
 }
 
-void launch_sort_generic(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_a,
-                         uint32_t* vals_a, uint64_t* keys_b, uint32_t* vals_b, int64_t cap,
-                         const uint32_t* num_keys_dev, int passes, uint32_t* hist,
-                         uint32_t* lookback, int64_t parts, Ctrl* ctrl, cudaStream_t stream,
+template <typename K>
+void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
+                         uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                         uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark, int mark_index) {
     if (cap <= 0 || passes <= 0) return;
     static bool attr_done = false;   // per process; the attribute is per function
-    const size_t smem = sizeof(SortSmem);
+    const size_t smem = sizeof(SortSmem<K>);
     if (!attr_done) {
-        cudaFuncSetAttribute(sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
+    const int64_t parts = sort_parts<K>(cap);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
-    sort_histogram<<<hist_blocks, 256, 0, stream>>>(keys_in, num_keys_dev, cap, passes, hist, &ctrl->error);
+    sort_histogram<K><<<hist_blocks, 256, 0, stream>>>(keys_in, num_keys_dev, cap, passes, hist, error);
     if (mark) mark(mark_index, stream);
-    const uint64_t* src_k = keys_in;
+    const K* src_k = keys_in;
     const uint32_t* src_v = vals_in;
     for (int p = 0; p < passes; ++p) {
         const bool to_a = ((passes - 1 - p) % 2) == 0;
-        uint64_t* dk = to_a ? keys_a : keys_b;
+        K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
-        sort_pass<<<(int)parts, kSortThreads, smem, stream>>>(
+        sort_pass<K><<<(int)parts, kSortThreads, smem, stream>>>(
             src_k, src_v, dk, dv, num_keys_dev, cap, kRadixBits * p, hist + p * kRadix,
-            lookback + (size_t)p * parts * kRadix, &ctrl->part_counter[p], &ctrl->error);
+            lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
         src_k = dk;
         src_v = dv;
     }
 }
+
+template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
+                                            uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int);
+template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                            uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);
@@ -261,10 +276,10 @@ void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark,
     uint32_t* va = (L.passes & 1) ? v1 : v0;
     uint64_t* kb = (L.passes & 1) ? k0 : k1;
     uint32_t* vb = (L.passes & 1) ? v0 : v1;
-    launch_sort_generic(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, L.passes,
-                        reinterpret_cast<uint32_t*>(ws + L.off_hist),
-                        reinterpret_cast<uint32_t*>(ws + L.off_lookback), L.sort_parts, ctrl, stream, mark,
-                        mark_index);
+    launch_sort_generic<uint64_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, L.passes,
+                                  reinterpret_cast<uint32_t*>(ws + L.off_hist),
+                                  reinterpret_cast<uint32_t*>(ws + L.off_lookback), ctrl->part_counter,
+                                  &ctrl->error, stream, mark, mark_index);
 }
 
 }  // namespace vis

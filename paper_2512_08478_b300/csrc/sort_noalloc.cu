@@ -23,7 +23,7 @@
 namespace {
 
 constexpr int64_t kMaxKeys = VIS_SORT_NOALLOC_MAX_KEYS;
-constexpr int64_t kMaxParts = (kMaxKeys + vis::kSortPartition - 1) / vis::kSortPartition;
+constexpr int64_t kMaxParts = vis::sort_parts<uint64_t>(kMaxKeys);
 constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffHist = 256;
 constexpr size_t kOffLookback = kOffHist + sizeof(uint32_t) * vis::kMaxPasses * vis::kRadix;
@@ -97,11 +97,11 @@ extern "C" vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint
     vis::Ctrl* ctrl = reinterpret_cast<vis::Ctrl*>(w + kOffCtrl);
     vis::launch_set_u32(&ctrl->num_keys, (uint32_t)m, stream);
     const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
-    const int64_t parts = (m + vis::kSortPartition - 1) / vis::kSortPartition;
-    vis::launch_sort_generic(keys_in, vals_in, keys_out, vals_out, reinterpret_cast<uint64_t*>(w + kOffKeys),
-                             reinterpret_cast<uint32_t*>(w + kOffVals), m, &ctrl->num_keys, passes,
-                             reinterpret_cast<uint32_t*>(w + kOffHist), reinterpret_cast<uint32_t*>(w + kOffLookback),
-                             parts, ctrl, stream);
+    vis::launch_sort_generic<uint64_t>(keys_in, vals_in, keys_out, vals_out,
+                                       reinterpret_cast<uint64_t*>(w + kOffKeys), reinterpret_cast<uint32_t*>(w + kOffVals),
+                                       m, &ctrl->num_keys, passes, reinterpret_cast<uint32_t*>(w + kOffHist),
+                                       reinterpret_cast<uint32_t*>(w + kOffLookback), ctrl->part_counter, &ctrl->error,
+                                       stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
     vis::set_last_error("");

@@ -11,11 +11,18 @@ namespace vis {
 
 constexpr int kPrepThreads = 256;        // Gaussians per preprocess / duplicate block
 constexpr int kSortThreads = 256;        // threads per radix-sort CTA
-constexpr int kSortKeysPerThread = 16;   // keys per thread per partition
-constexpr int kSortPartition = kSortThreads * kSortKeysPerThread;   // 4096 keys
+// keys per thread per partition, by key width (8 for 64-bit keys keeps three CTAs per SM)
+template <typename K> struct SortKPT;
+template <> struct SortKPT<uint64_t> { static constexpr int value = 8; };
+template <> struct SortKPT<uint32_t> { static constexpr int value = 16; };
+template <typename K> constexpr int64_t sort_partition() { return (int64_t)kSortThreads * SortKPT<K>::value; }
+template <typename K> constexpr int64_t sort_parts(int64_t cap) {
+    return (cap + sort_partition<K>() - 1) / sort_partition<K>();
+}
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
+constexpr int kDepthPasses = 4;          // 8-bit passes over the float bits of a positive depth
 constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit counts
 
 // ctrl->error bits
@@ -26,7 +33,12 @@ constexpr uint32_t kErrTimeout = 2u;
 // far beyond any legitimate wait, it only bounds a wait that can never end.
 constexpr uint32_t kSpinLimit = 1u << 22;
 
+// Sort modes (vis_render_opts.sort_mode)
+constexpr int kSortTileDepth = 0;   // one sort of 64-bit (tile << 32 | depth) keys
+constexpr int kSortDepthFirst = 1;  // depth sort of the surviving splats, then a tile sort
+
 struct Layout {
+    int mode = kSortTileDepth;
     int64_t n = 0;
     int W = 0, H = 0, tile = 16;
     int tiles_x = 0, tiles_y = 0;
@@ -40,21 +52,26 @@ struct Layout {
     size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
     size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
     size_t off_tfinal = 0, off_last = 0, off_g2 = 0;
+    // depth-first mode only
+    size_t off_dkeys[2] = {0, 0}, off_dvals[2] = {0, 0}, off_bsum2 = 0, off_boff2 = 0;
+    size_t lookback_words_depth = 0;
+    int key_bytes = 8;
     size_t zero_begin = 0, zero_end = 0;   // region cleared before every render
     size_t total = 0;
     int sorted_buffer = 0;
 };
 
-// Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`.
-Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap);
+// Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`, sort mode.
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode);
 // Largest capacity whose layout fits ws_bytes (0 if none).
-int64_t capacity_for(int64_t n, int W, int H, int tile, size_t ws_bytes);
+int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes);
 
 struct Ctrl {
     uint32_t num_keys;
     uint32_t error;
-    uint32_t part_counter[kMaxPasses];
-    uint32_t reserved[54];
+    uint32_t part_counter[2 * kMaxPasses];   // partition tickets of up to two sorts per render
+    uint32_t num_visible;                    // Gaussians that survive culling (depth-first sort)
+    uint32_t reserved[45];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
 
@@ -130,6 +147,12 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
 typedef void (*StageMark)(int, cudaStream_t);
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark = nullptr, int mark_index = 0);
 void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
+void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
+                      int64_t cap, cudaStream_t stream);
+// Depth-first mode: compaction, depth sort, emission (then mark(3)), tile sort (mark(4)
+// after its histogram). Ranges for its 32-bit tile keys:
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
+void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, float* out_rgb, float* out_alpha,
                       cudaStream_t stream);
@@ -138,12 +161,15 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
                      const float* d_alpha, float* d_means, float* d_log_scales, float* d_quats,
                      float* d_logits, float* d_sh, cudaStream_t stream);
 
-// Standalone sort: generic buffers. `lookback` must hold passes * parts * kRadix words,
-// `hist` passes * kRadix words and `ctrl` one Ctrl, all zeroed by the caller.
-void launch_sort_generic(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_a,
-                         uint32_t* vals_a, uint64_t* keys_b, uint32_t* vals_b, int64_t cap,
-                         const uint32_t* num_keys_dev, int passes, uint32_t* hist,
-                         uint32_t* lookback, int64_t parts, Ctrl* ctrl, cudaStream_t stream,
+// Stable LSD radix sort of (K key, uint32 value) pairs over `passes` 8-bit digits.
+// Reads keys_in/vals_in, ping-pongs between the a and b buffers and leaves the result in a.
+// `lookback` must hold passes * sort_parts<K>(cap) * kRadix words, `hist` passes * kRadix
+// words and `part_counters` passes words, all zeroed; the key count is read from
+// num_keys_dev (<= cap). If `mark` is given it is called after the histogram.
+template <typename K>
+void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
+                         uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                         uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0);
 
 // Sets the thread-local message returned by vis_last_error().

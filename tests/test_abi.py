@@ -29,7 +29,7 @@ def test_workspace_queries_and_validation(L):
     b = vis.vis_workspace_size(10_000, 256, 256, 100_000)
     lay = vis.vis_workspace_layout(10_000, 256, 256, b)
     assert lay.key_capacity == 100_000 and lay.total_bytes <= b
-    assert lay.tiles_x == 16 and lay.sort_passes == 5          # 32 depth bits + 8 tile bits
+    assert lay.tiles_x == 16 and lay.sort_passes == 5 and lay.key_bytes == 8   # 32 depth + 8 tile bits
     lay32 = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(tile=16))
     assert lay32.sort_passes == 6                                # 8160 tiles -> 13 bits
     offs = [lay.off_ctrl, lay.off_rec, lay.off_depth, lay.off_rect, lay.off_touched, lay.off_keys[0],
@@ -49,6 +49,11 @@ def test_workspace_queries_and_validation(L):
     assert e.value.status == vis.VIS_ERR_UNSUPPORTED
     with pytest.raises(vis.VisError):
         vis.vis_workspace_layout(10, 8, 8, 100)        # too small for even one key
+    df = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=1))
+    assert df.key_bytes == 4 and df.sort_mode == 1 and df.sort_passes == 2   # 13 tile bits
+    assert vis.vis_workspace_size(10_000, 256, 256, 100_000, vis.make_opts(sort_mode=1)) < b
+    with pytest.raises(vis.VisError):
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=2))
     assert vis.vis_sort_workspace_size(0, 45) > 0
     with pytest.raises(vis.VisError):
         vis.vis_sort_workspace_size(10, 65)

@@ -1,0 +1,85 @@
+"""Depth-first sort mode (sort_mode = 1): depth sort of the surviving splats, then a
+stable tile sort of their copies. It must give the same (tile, depth, index) order as
+the 64-bit (tile, depth) key sort -- hence the same values, ranges and image, bit for
+bit -- and pass the same oracle parity."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2512_08478_b300 as vis
+from paper_2512_08478_b300 import synth
+from gpu_helpers import image_parity, render_gpu, ws_view
+
+pytestmark = pytest.mark.gpu
+
+
+def _sorted_vals_and_ranges(sc, ws):
+    L = ws.layout()
+    m = int(ws_view(ws, L.off_ctrl, 1, np.uint32)[0])
+    vals = ws_view(ws, L.off_vals[L.sorted_buffer], m, np.uint32)
+    nt = L.tiles_x * L.tiles_y
+    ranges = ws_view(ws, L.off_ranges, 2 * nt, np.uint32).reshape(nt, 2)
+    return vals, ranges, L
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_depth_first_equals_tile_depth_sort(tile):
+    sc = synth.mixture_scene(20000, 31, sh_degree=2, ball_radius=3.0, comp_std=0.5, log_scale_mean=-3.2)
+    cam = synth.look_at((1.0, 2.0, 9.0), (0, 0, 0), 301, 187, 55.0)
+    a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=0))
+    b_rgb, b_alpha, sb, wb = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1))
+    va, ra, La = _sorted_vals_and_ranges(sa, wa)
+    vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
+    assert La.key_bytes == 8 and Lb.key_bytes == 4 and Lb.sort_mode == 1
+    assert np.array_equal(va, vb)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
+
+
+def test_depth_first_small_workload_parity():
+    sc, cams = synth.workload_small()
+    rgb, alpha, _, _ = render_gpu(sc, cams[0], opts=vis.make_opts(sort_mode=1))
+    ref, _ = oracle.render(sc, cams[0])
+    image_parity(rgb, alpha, ref)
+
+
+def test_depth_first_all_culled_and_single_tile():
+    sc, cams = synth.workload_small()
+    dead = dict(sc, opacity_logits=np.full_like(sc["opacity_logits"], -30.0))
+    rgb, alpha, _, ws = render_gpu(dead, cams[0], (0.5, 0.5, 0.5), vis.make_opts(sort_mode=1))
+    assert np.all(alpha == 0.0) and vis.vis_check(ws.buf) == 0
+    cam = synth.look_at((0, 0, 4), (0, 0, 0), 12, 10, 60.0)   # one tile
+    rgb, alpha, _, _ = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=1))
+    ref, _ = oracle.render(sc, cam)
+    image_parity(rgb, alpha, ref)
+
+
+def test_depth_first_gradients_match_oracle():
+    import torch
+    sc, cam = synth.fd_scene()
+    rng = np.random.default_rng(8)
+    gC = rng.standard_normal((3, cam.H, cam.W))
+    gA = rng.standard_normal((cam.H, cam.W))
+    opts = vis.make_opts(sort_mode=1)
+    _, _, s, ws = render_gpu(sc, cam, (0, 0, 0), opts)
+    grads = {k: torch.empty_like(s.tensors[k]) for k in vis.FIELDS}
+    vis.vis_render_backward(s.handle, cam, cam.W, cam.H, (0, 0, 0),
+                            torch.from_numpy(gC.astype(np.float32)).cuda(),
+                            torch.from_numpy(gA.astype(np.float32)).cuda(), ws.buf, grads, opts)
+    ref = oracle.adjoint(sc, cam, gC, gA)
+    for k in vis.FIELDS:
+        a = grads[k].cpu().numpy().astype(np.float64).ravel()
+        b = ref[k].ravel()
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), k
+
+
+def test_depth_first_capacity_error_then_retry():
+    sc_np, cams = synth.workload_small()
+    cam = cams[0]
+    opts = vis.make_opts(sort_mode=1)
+    s = vis.Scene.from_numpy(sc_np)
+    ws = vis.Workspace(s.n, cam.W, cam.H, key_capacity=100, opts=opts)
+    rgb, alpha = vis._render_checked(s, cam, cam.W, cam.H, (0, 0, 0), ws, opts)
+    assert ws.key_capacity > 100
+    ref, _ = oracle.render(sc_np, cam)
+    image_parity(rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), ref)
