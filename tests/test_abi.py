@@ -26,11 +26,12 @@ def test_every_declared_function_is_exported(L):
 
 
 def test_workspace_queries_and_validation(L):
-    b = vis.vis_workspace_size(10_000, 256, 256, 100_000)
-    lay = vis.vis_workspace_layout(10_000, 256, 256, b)
-    assert lay.key_capacity == 100_000 and lay.total_bytes <= b
+    m0 = vis.make_opts(sort_mode=0)
+    b = vis.vis_workspace_size(10_000, 256, 256, 100_000, m0)
+    lay = vis.vis_workspace_layout(10_000, 256, 256, b, m0)
+    assert 100_000 <= lay.key_capacity < 100_100 and lay.total_bytes <= b
     assert lay.tiles_x == 16 and lay.sort_passes == 5 and lay.key_bytes == 8   # 32 depth + 8 tile bits
-    lay32 = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(tile=16))
+    lay32 = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(tile=16, sort_mode=0))
     assert lay32.sort_passes == 6                                # 8160 tiles -> 13 bits
     offs = [lay.off_ctrl, lay.off_rec, lay.off_depth, lay.off_rect, lay.off_touched, lay.off_keys[0],
             lay.off_keys[1], lay.off_vals[0], lay.off_vals[1], lay.off_ranges, lay.off_tfinal, lay.off_last,
@@ -52,6 +53,7 @@ def test_workspace_queries_and_validation(L):
     df = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=1))
     assert df.key_bytes == 4 and df.sort_mode == 1 and df.sort_passes == 2   # 13 tile bits
     assert vis.vis_workspace_size(10_000, 256, 256, 100_000, vis.make_opts(sort_mode=1)) < b
+    assert vis.make_opts().sort_mode == 1   # depth first is the default
     with pytest.raises(vis.VisError):
         vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=2))
     assert vis.vis_sort_workspace_size(0, 45) > 0
