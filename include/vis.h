@@ -81,6 +81,8 @@ typedef struct {
  *                  32-bit depth (as in the paper), their tile copies are emitted in that
  *                  order and stably sorted by tile id alone. Both give the same order
  *                  bit for bit; 1 moves about a quarter of the bytes.
+ *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
+ *              thread (default 1); the image does not depend on it.
  * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
 typedef struct {
     int tile;
@@ -90,6 +92,7 @@ typedef struct {
     float alpha_max;
     float t_stop;
     int sort_mode;
+    int pixels_per_thread;
 } vis_render_opts;
 
 VIS_API void vis_default_opts(vis_render_opts* opts);

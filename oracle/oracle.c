@@ -350,11 +350,12 @@ static int cmp_ord(const void* a, const void* b) {
 }
 
 /* Ambiguity margins: a decision taken within these of its threshold may go the
- * other way in float32 arithmetic. The float32 renderer evaluates q and alpha to
- * ~1e-6 relative (float-float pixel centres, whitened splat shape) and the
- * transmittance product to ~1e-5 relative after ~100 splats; each margin is a
- * safety factor of 8 above that. */
-#define AMB_Q_REL     (8.0 * 1e-6)
+ * other way in float32 arithmetic. The float32 renderer evaluates alpha to ~1e-6
+ * relative and the transmittance product to ~1e-5 relative after ~100 splats; q
+ * carries the rounding of the splat centre relative to the tile centre
+ * (|du| * 6e-8 px), which reaches ~2.5e-6 relative at q = 9 for a splat 100 px from
+ * the tile centre. Each margin is a safety factor of 8 above that. */
+#define AMB_Q_REL     (8.0 * 2.5e-6)
 #define AMB_ALPHA_REL (8.0 * 1e-6)
 #define AMB_T_REL     (8.0 * 1e-5)
 

@@ -39,7 +39,7 @@ class vis_camera(C.Structure):
 class vis_render_opts(C.Structure):
     _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
-                ("sort_mode", C.c_int)]
+                ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int)]
 
 
 class vis_ws_layout(C.Structure):

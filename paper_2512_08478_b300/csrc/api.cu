@@ -57,12 +57,15 @@ vis_render_opts resolve_opts(const vis_render_opts* o) {
     if (o) r = *o;
     if (r.tile == 0) r.tile = 16;
     if (r.digit_bits == 0) r.digit_bits = vis::kRadixBits;
+    if (r.pixels_per_thread == 0) r.pixels_per_thread = 1;
     return r;
 }
 
 vis_status check_opts(const vis_render_opts& o) {
     if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
     if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
+    if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
+        return fail(VIS_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2 (got %d)", o.pixels_per_thread);
     if (o.sort_mode != vis::kSortTileDepth && o.sort_mode != vis::kSortDepthFirst)
         return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0 or 1 (got %d)", o.sort_mode);
     if (!(o.dilation >= 0.f) || !std::isfinite(o.dilation)) return fail(VIS_ERR_INVALID_ARG, "dilation must be finite and >= 0");
@@ -107,6 +110,7 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     p.limy = (float)(1.3 * (H / (2.0 * c->fy)));
     p.W = W; p.H = H; p.tile = L.tile; p.tiles_x = L.tiles_x; p.tiles_y = L.tiles_y;
     p.dilation = o.dilation; p.alpha_min = o.alpha_min;
+    p.wscale = (float)std::sqrt(0.5 / std::log(2.0));
     vis::sh_constants(p.shc);
     return p;
 }
@@ -134,6 +138,11 @@ void prof_mark(int k, cudaStream_t stream) {
 namespace vis {
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+QScale q_scale() {
+    const double c = 0.5 / std::log(2.0);   // log2(e) / 2
+    return QScale{(float)(9.0 * c), (float)(1.0 / c)};
+}
 
 // K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!); the real SH polynomials in (x, y, z)
 // on the unit sphere (Condon-Shortley phase) are products of these with
@@ -232,6 +241,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->alpha_max = 0.99f;
     o->t_stop = 1e-4f;
     o->sort_mode = vis::kSortDepthFirst;
+    o->pixels_per_thread = 1;
 }
 
 const char* vis_last_error(void) { return g_err.c_str(); }
@@ -345,7 +355,8 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
         vis::launch_ranges(L, w, stream);
     }
     prof_mark(6, stream);
-    vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, out_rgb, out_alpha, stream);
+    vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread, out_rgb,
+                          out_alpha, stream);
     prof_mark(7, stream);
     if (g_prof.on && g_prof.count < kProfRing) { ++g_prof.count; g_prof.passes = L.passes; }
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;

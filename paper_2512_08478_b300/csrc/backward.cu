@@ -29,7 +29,7 @@ template <int TILE>
 __global__ void __launch_bounds__(TILE * TILE)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                           const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0,
-                          float bg1, float bg2, float alpha_min, float alpha_max,
+                          float bg1, float bg2, float alpha_min, float alpha_max, float qcut, float inv_scale,
                           const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
                           float* __restrict__ g2) {
@@ -43,7 +43,8 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
     const bool inside = px < W && py < H;
     const size_t pix = (size_t)py * W + px;
     const size_t HW = (size_t)H * W;
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
+    const float xc = (float)(tx * TILE) + 0.5f * TILE, yc = (float)(ty * TILE) + 0.5f * TILE;
+    const float lx = (float)px + 0.5f - xc, ly = (float)py + 0.5f - yc;
     const uint2 r = ranges[tile];
     const int lane = threadIdx.x & 31;
 
@@ -74,10 +75,11 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
         __syncthreads();
         if (threadIdx.x < cnt) {
             const uint32_t g = vals[lo + threadIdx.x];
+            const StagedSplat st = stage_splat(rec, g, xc, yc, qcut, alpha_min);
             s_g[threadIdx.x] = g;
-            s_a[threadIdx.x] = rec[3 * (size_t)g + 0];
-            s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
+            s_a[threadIdx.x] = st.a;
+            s_b[threadIdx.x] = st.b;
+            s_c[threadIdx.x] = st.c;
         }
         __syncthreads();
         for (int k = cnt - 1; k >= 0; --k) {
@@ -86,36 +88,35 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
             bool contrib = false;
             if (inside && pos < (int64_t)last) {
                 const float4 a = s_a[k], b = s_b[k];
-                const PairEval e = eval_pair(pcx, pcy, a, b);
-                if (e.q <= 9.f) {
+                const PairEval e = eval_pair(lx, ly, a, b);
+                if (e.q <= b.z) {   // the forward's decision: 3-sigma cut and alpha_min
+                    contrib = true;
                     const float4 c = s_c[k];
-                    const float G = gauss_of_q(e.q);
-                    const float raw = __fmul_rn(c.x, G);
+                    const float G = gauss_of_qs(e.q);
+                    const float raw = __fmul_rn(b.w, G);
                     const float alpha = fminf(alpha_max, raw);
-                    if (alpha >= alpha_min) {
-                        contrib = true;
-                        const float om = __fsub_rn(1.f, alpha);
-                        const float inv_om = 1.f / om;
-                        T = T * inv_om;                      // T before this splat
-                        const float w = alpha * T;
-                        g[6] = gC0 * w; g[7] = gC1 * w; g[8] = gC2 * w;
-                        float ga = T * ((c.y - S0) * gC0 + (c.z - S1) * gC1 + (c.w - S2) * gC2);
-                        ga += (gA - bgdot) * TN * inv_om;
-                        S0 = c.y * alpha + om * S0;
-                        S1 = c.z * alpha + om * S1;
-                        S2 = c.w * alpha + om * S2;
-                        if (raw <= alpha_max) {   // clamp inactive
-                            g[5] = ga * G;
-                            const float gq = -0.5f * ga * c.x * G;
-                            // dq/dd = 2 (f1 p1 + f2 p2); d = pixel - (u, v)
-                            const float qdx = b.x * e.p1 + b.z * e.p2;
-                            const float qdy = b.y * e.p1 + b.w * e.p2;
-                            g[0] = -2.f * gq * qdx;
-                            g[1] = -2.f * gq * qdy;
-                            g[2] = gq * e.dx * e.dx;
-                            g[3] = 2.f * gq * e.dx * e.dy;
-                            g[4] = gq * e.dy * e.dy;
-                        }
+                    const float om = __fsub_rn(1.f, alpha);
+                    const float inv_om = 1.f / om;
+                    T = T * inv_om;                      // T before this splat
+                    const float w = alpha * T;
+                    g[6] = gC0 * w; g[7] = gC1 * w; g[8] = gC2 * w;
+                    float ga = T * ((c.x - S0) * gC0 + (c.y - S1) * gC1 + (c.z - S2) * gC2);
+                    ga += (gA - bgdot) * TN * inv_om;
+                    S0 = c.x * alpha + om * S0;
+                    S1 = c.y * alpha + om * S1;
+                    S2 = c.z * alpha + om * S2;
+                    if (raw <= alpha_max) {   // clamp inactive
+                        g[5] = ga * G;
+                        // G = exp(-q/2) in the unscaled q = d^T S^-1 d
+                        const float gq = -0.5f * ga * b.w * G;
+                        // dq/dd = 2 S^-1 d = 2 (f1 p1 + f2 p2) / c for the scaled rows f, p
+                        const float qdx = (a.z * e.p1 + b.x * e.p2) * inv_scale;
+                        const float qdy = (a.w * e.p1 + b.y * e.p2) * inv_scale;
+                        g[0] = -2.f * gq * qdx;   // d = pixel - (u, v)
+                        g[1] = -2.f * gq * qdy;
+                        g[2] = gq * e.dx * e.dx;
+                        g[3] = 2.f * gq * e.dx * e.dy;
+                        g[4] = gq * e.dy * e.dy;
                     }
                 }
             }
@@ -329,11 +330,12 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
     const float* tfin = reinterpret_cast<const float*>(ws + L.off_tfinal);
     const int32_t* last = reinterpret_cast<const int32_t*>(ws + L.off_last);
     const int blocks = (int)L.ntiles;
+    const QScale qs = q_scale();
 #define VIS_LAUNCH_BWD(TS)                                                                                 \
     composite_backward_kernel<TS><<<blocks, TS * TS, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, \
                                                                   bg[0], bg[1], bg[2], alpha_min,         \
-                                                                  alpha_max, tfin, last, d_rgb, d_alpha,  \
-                                                                  g2)
+                                                                  alpha_max, qs.qcut, qs.inv_scale, tfin, \
+                                                                  last, d_rgb, d_alpha, g2)
     if (blocks > 0) {
         if (L.tile == 8) VIS_LAUNCH_BWD(8);
         else if (L.tile == 32) VIS_LAUNCH_BWD(32);

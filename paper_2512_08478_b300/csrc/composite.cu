@@ -1,86 +1,177 @@
 // K5 -- tile compositor (section 3.2 Eqs. 2-3, front to back).
 //
-// One CTA per TILE x TILE tile, one thread per pixel. The tile's range of the
-// sorted (tile, depth, index) list is walked in chunks of TILE^2 splats: each
-// thread gathers one splat record (3 x float4) into shared memory, then every
-// thread composites the whole chunk for its pixel from shared memory (broadcast
-// reads). A pixel is done when T (1 - alpha) would fall below t_stop (that splat
-// excluded); the CTA leaves as soon as all its pixels are done.
+// One CTA per TILE x TILE tile; each thread owns PPT vertically adjacent pixels and
+// each warp an 8 x (4 PPT) pixel block.
+// The tile's range of the sorted (tile, depth, index) list is walked in chunks of
+// CH splats: each thread stages splats (gather of the 48-byte record by index)
+// into shared memory -- centre relative to the tile centre, scaled whitening rows,
+// and one threshold for the 3-sigma cut and the alpha_min skip -- then every
+// warp builds (ballot compaction) the list of staged splats whose exact 3-sigma
+// bounding box meets its pixel block, and composites only those for its pixels,
+// from shared memory (broadcast reads).
+// A splat that misses costs two shared loads and ~10 FP32 operations; only hits
+// evaluate 2^-q'. A pixel is done when T (1 - alpha) would fall below t_stop
+// (that splat excluded); the CTA leaves as soon as all its pixels are done.
 // Outputs: planar rgb = C + T bg, alpha = 1 - T, and for the adjoint the final T
 // and 1 + the sorted position of the last composited splat.
 #include "splat_eval.cuh"
 
 namespace vis {
 
-template <int TILE>
-__global__ void __launch_bounds__(TILE * TILE)
+struct PixAcc {
+    float T, C0, C1, C2;
+    int32_t last;
+    bool done;
+};
+
+// Composite one staged splat into one pixel; returns false when the pixel stops.
+__device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& b, const float4& c, float alpha_max,
+                                              float t_stop, int32_t pos1) {
+    const float alpha = fminf(alpha_max, __fmul_rn(b.w, gauss_of_qs(q)));
+    const float Tn = __fmul_rn(P.T, __fsub_rn(1.f, alpha));
+    if (Tn < t_stop) { P.done = true; return; }
+    const float w = __fmul_rn(alpha, P.T);
+    P.C0 = __fmaf_rn(c.x, w, P.C0);
+    P.C1 = __fmaf_rn(c.y, w, P.C1);
+    P.C2 = __fmaf_rn(c.z, w, P.C2);
+    P.T = Tn;
+    P.last = pos1;
+}
+
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                  const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0, float bg1,
-                 float bg2, float alpha_min, float alpha_max, float t_stop, const Ctrl* __restrict__ ctrl,
-                 float* __restrict__ out_rgb, float* __restrict__ out_alpha, float* __restrict__ t_final,
-                 int32_t* __restrict__ last_out) {
-    constexpr int NT = TILE * TILE;
-    __shared__ float4 s_a[NT], s_b[NT], s_c[NT];
+                 float bg2, float alpha_min, float alpha_max, float t_stop, float qcut,
+                 const Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
+                 float* __restrict__ t_final, int32_t* __restrict__ last_out) {
+    constexpr int NT = TILE * TILE / PPT;   // threads
+    constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
+    constexpr int BX = TILE / 8;            // blocks per tile row
+    constexpr int BH = 4 * PPT;             // block height in pixels
+    constexpr int CH = NT < 256 ? NT : 256; // splats staged per chunk
+    static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
+    __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
+    __shared__ uint32_t s_mask[CH];
+    __shared__ uint16_t s_list[NW][CH];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
-    const bool inside = px < W && py < H;
-    const size_t pix = (size_t)py * W + px;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bx = warp % BX, by = warp / BX;
+    const int col = bx * 8 + (lane & 7), row0 = by * BH + (lane >> 3) * PPT;
+    const int px = tx * TILE + col;
+    const float half = 0.5f * TILE;
+    const float xc = (float)(tx * TILE) + half, yc = (float)(ty * TILE) + half;
+    const float lx = (float)px + 0.5f - xc;
     const size_t HW = (size_t)H * W;
     if (ctrl->error) {   // keys were not produced: make the failure visible
-        if (inside) {
-            const float nan = __int_as_float(0x7fc00000);
-            out_rgb[pix] = nan; out_rgb[HW + pix] = nan; out_rgb[2 * HW + pix] = nan;
-            out_alpha[pix] = nan; t_final[pix] = nan; last_out[pix] = 0;
+        const float nan = __int_as_float(0x7fc00000);
+        for (int r = 0; r < PPT; ++r) {
+            const int py = ty * TILE + row0 + r;
+            if (px < W && py < H) {
+                const size_t pix = (size_t)py * W + px;
+                out_rgb[pix] = nan; out_rgb[HW + pix] = nan; out_rgb[2 * HW + pix] = nan;
+                out_alpha[pix] = nan; t_final[pix] = nan; last_out[pix] = 0;
+            }
         }
         return;
     }
-    const float pcx = (float)px + 0.5f, pcy = (float)py + 0.5f;
-    const uint2 r = ranges[tile];
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int32_t last = 0;
-    bool done = !inside;
-    for (uint32_t base = r.x; base < r.y; base += NT) {
-        if (__syncthreads_count(done) == NT) break;
+    PixAcc P[PPT];
+    float ly[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int py = ty * TILE + row0 + r;
+        P[r].T = 1.f; P[r].C0 = P[r].C1 = P[r].C2 = 0.f; P[r].last = 0;
+        P[r].done = !(px < W && py < H);
+        ly[r] = (float)py + 0.5f - yc;
+    }
+    const uint2 rg = ranges[tile];
+    for (uint32_t base = rg.x; base < rg.y; base += CH) {
+        bool all_done = true;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) all_done = all_done && P[r].done;
+        if (__syncthreads_count(all_done) == NT) break;
         const uint32_t j = base + threadIdx.x;
-        if (j < r.y) {
-            const uint32_t g = vals[j];
-            s_a[threadIdx.x] = rec[3 * (size_t)g + 0];
-            s_b[threadIdx.x] = rec[3 * (size_t)g + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)g + 2];
+        if (threadIdx.x < CH && j < rg.y) {
+            const StagedSplat s = stage_splat(rec, vals[j], xc, yc, qcut, alpha_min);
+            s_a[threadIdx.x] = s.a;
+            s_b[threadIdx.x] = s.b;
+            s_c[threadIdx.x] = s.c;
+            // axis-aligned half extents of {d : q'(d) <= thr}: sqrt(thr (Q'^-1)_xx), ...
+            const float det = fabsf(__fmaf_rn(s.a.z, s.b.y, -__fmul_rn(s.a.w, s.b.x)));
+            const float ext = sqrtf(fmaxf(s.b.z, 0.f)) / det;
+            const float rx = ext * sqrtf(__fmaf_rn(s.a.w, s.a.w, __fmul_rn(s.b.y, s.b.y))) * 1.0001f + 1e-3f;
+            const float ry = ext * sqrtf(__fmaf_rn(s.a.z, s.a.z, __fmul_rn(s.b.x, s.b.x))) * 1.0001f + 1e-3f;
+            uint32_t m = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                // pixel centres of block w span [x0, x0 + 7] x [y0, y0 + BH - 1] (tile-centre relative)
+                const float mx = (float)((w % BX) * 8) + 4.f - half;
+                const float my = (float)((w / BX) * BH) + 0.5f * BH - half;
+                const float ox = fabsf(s.a.x - mx) - 3.5f, oy = fabsf(s.a.y - my) - (0.5f * BH - 0.5f);
+                if (ox <= rx && oy <= ry) m |= 1u << w;
+            }
+            s_mask[threadIdx.x] = m;
         }
         __syncthreads();
-        const int cnt = (int)umin((uint32_t)NT, r.y - base);
-        if (!done) {
-            for (int k = 0; k < cnt; ++k) {
-                const PairEval e = eval_pair(pcx, pcy, s_a[k], s_b[k]);
-                if (e.q > 9.f) continue;
-                const float4 c = s_c[k];
-                const float alpha = fminf(alpha_max, __fmul_rn(c.x, gauss_of_q(e.q)));
-                if (alpha < alpha_min) continue;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                if (Tn < t_stop) { done = true; break; }
-                const float w = __fmul_rn(alpha, T);
-                C0 = __fmaf_rn(c.y, w, C0);
-                C1 = __fmaf_rn(c.z, w, C1);
-                C2 = __fmaf_rn(c.w, w, C2);
-                T = Tn;
-                last = (int32_t)(base + k + 1);
+        const int cnt = (int)umin((uint32_t)CH, rg.y - base);
+        // this warp's list of splats whose 3-sigma box meets its pixel block, in depth order
+        int nlist = 0;
+        for (int g0 = 0; g0 < cnt; g0 += 32) {
+            const int k = g0 + lane;
+            const bool in = k < cnt && ((s_mask[k] >> warp) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, in);
+            if (in) s_list[warp][nlist + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)k;
+            nlist += __popc(bal);
+        }
+        __syncwarp();
+        if (!all_done) {
+            for (int i = 0; i < nlist; ++i) {
+                const int k = s_list[warp][i];
+                const float4 a = s_a[k], b = s_b[k];
+                const int32_t pos1 = (int32_t)(base + k + 1);
+                if (PPT == 1) {
+                    const PairEval e = eval_pair(lx, ly[0], a, b);
+                    if (e.q > b.z) continue;
+                    composite_hit(P[0], e.q, b, s_c[k], alpha_max, t_stop, pos1);
+                    if (P[0].done) break;
+                } else {
+                    // the same arithmetic as eval_pair for each row, sharing the dx products
+                    const float dx = __fsub_rn(lx, a.x);
+                    const float t1 = __fmul_rn(dx, a.z), t2 = __fmul_rn(dx, b.x);
+                    const float dy0 = __fsub_rn(ly[0], a.y), dy1 = __fsub_rn(ly[1], a.y);
+                    const float p10 = __fmaf_rn(dy0, a.w, t1), p20 = __fmaf_rn(dy0, b.y, t2);
+                    const float p11 = __fmaf_rn(dy1, a.w, t1), p21 = __fmaf_rn(dy1, b.y, t2);
+                    const float q0 = __fmaf_rn(p20, p20, __fmul_rn(p10, p10));
+                    const float q1 = __fmaf_rn(p21, p21, __fmul_rn(p11, p11));
+                    const bool h0 = !P[0].done && q0 <= b.z;
+                    const bool h1 = !P[1].done && q1 <= b.z;
+                    if (!(h0 || h1)) continue;
+                    const float4 c = s_c[k];
+                    if (h0) composite_hit(P[0], q0, b, c, alpha_max, t_stop, pos1);
+                    if (h1) composite_hit(P[1], q1, b, c, alpha_max, t_stop, pos1);
+                    if (P[0].done && P[1].done) break;
+                }
             }
         }
     }
-    if (inside) {
-        out_rgb[pix] = __fmaf_rn(T, bg0, C0);
-        out_rgb[HW + pix] = __fmaf_rn(T, bg1, C1);
-        out_rgb[2 * HW + pix] = __fmaf_rn(T, bg2, C2);
-        out_alpha[pix] = 1.f - T;
-        t_final[pix] = T;
-        last_out[pix] = last;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int py = ty * TILE + row0 + r;
+        if (px < W && py < H) {
+            const size_t pix = (size_t)py * W + px;
+            out_rgb[pix] = __fmaf_rn(P[r].T, bg0, P[r].C0);
+            out_rgb[HW + pix] = __fmaf_rn(P[r].T, bg1, P[r].C1);
+            out_rgb[2 * HW + pix] = __fmaf_rn(P[r].T, bg2, P[r].C2);
+            out_alpha[pix] = 1.f - P[r].T;
+            t_final[pix] = P[r].T;
+            last_out[pix] = P[r].last;
+        }
     }
 }
 
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
-                      float alpha_max, float t_stop, float* out_rgb, float* out_alpha,
+                      float alpha_max, float t_stop, int ppt, float* out_rgb, float* out_alpha,
                       cudaStream_t stream) {
     const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
     const uint32_t* vals = reinterpret_cast<const uint32_t*>(ws + L.off_vals[L.sorted_buffer]);
@@ -90,13 +181,16 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     int32_t* last = reinterpret_cast<int32_t*>(ws + L.off_last);
     const int blocks = (int)L.ntiles;
     if (blocks <= 0) return;
-#define VIS_LAUNCH_COMPOSITE(TS)                                                                      \
-    composite_kernel<TS><<<blocks, TS * TS, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, bg0, \
-                                                         bg1, bg2, alpha_min, alpha_max, t_stop,      \
-                                                         ctrl, out_rgb, out_alpha, tfin, last)
-    if (L.tile == 8) VIS_LAUNCH_COMPOSITE(8);
-    else if (L.tile == 32) VIS_LAUNCH_COMPOSITE(32);
-    else VIS_LAUNCH_COMPOSITE(16);
+    const float qcut = q_scale().qcut;
+#define VIS_LAUNCH_COMPOSITE(TS, PP)                                                                    \
+    composite_kernel<TS, PP><<<blocks, TS * TS / PP, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, \
+                                                                  bg0, bg1, bg2, alpha_min, alpha_max,   \
+                                                                  t_stop, qcut, ctrl, out_rgb, out_alpha, \
+                                                                  tfin, last)
+    const bool two = ppt == 2;
+    if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE(8, 2); else VIS_LAUNCH_COMPOSITE(8, 1); }
+    else if (L.tile == 32) { if (two) VIS_LAUNCH_COMPOSITE(32, 2); else VIS_LAUNCH_COMPOSITE(32, 1); }
+    else { if (two) VIS_LAUNCH_COMPOSITE(16, 2); else VIS_LAUNCH_COMPOSITE(16, 1); }
 #undef VIS_LAUNCH_COMPOSITE
 }
 

@@ -10,9 +10,10 @@
 // ~1e-7 px even 1000 px from the principal point. The 2D covariance is formed as
 // S = A A^T + dil I with A = J W R_q diag(s); its determinant as
 // |A_0 x A_1|^2 + dil tr(A A^T) + dil^2 (no cancellation), and the splat is stored
-// in whitened form: q = (d.f1)^2 + (d.f2)^2 with f_k = e_k / sqrt(lambda_k), the
-// eigenpairs of S. This equals d^T S^-1 d of Eq. 2 and stays well conditioned for
-// needle-shaped splats, where the conic form (a, b, c) loses digits.
+// in whitened form: q' = (d.f1)^2 + (d.f2)^2 with f_k = sqrt(c) e_k / sqrt(lambda_k),
+// (lambda_k, e_k) the eigenpairs of S and c = log2(e)/2. This is c d^T S^-1 d (Eq. 2's
+// exponent in base 2) and stays well conditioned for needle-shaped splats, where the
+// conic form (a, b, c) loses digits.
 #include "vis_internal.cuh"
 
 namespace vis {
@@ -114,7 +115,7 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 const float en2 = ex * ex + ey * ey;
                 if (en2 > 0.f) { const float inv = rsqrtf(en2); ex *= inv; ey *= inv; }
                 else { ex = 1.f; ey = 0.f; }
-                const float i1 = rsqrtf(lam1), i2 = rsqrtf(lam2);
+                const float i1 = rsqrtf(lam1) * p.wscale, i2 = rsqrtf(lam2) * p.wscale;
                 const float lam_ext = m + sqrtf(fmaxf(0.1f, disc));
                 const float radius = ceilf(3.f * sqrtf(lam_ext));
                 const float T = (float)p.tile;

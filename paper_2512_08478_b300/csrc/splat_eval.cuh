@@ -1,31 +1,61 @@
 // Per (pixel, splat) evaluation shared by the compositor and its adjoint, written
 // with explicit rounding intrinsics so both kernels take bit-identical decisions.
 //
-// Record layout (3 x float4 per Gaussian):
-//   a = (u_hi, v_hi, u_lo, v_lo)   pixel-space centre in float-float
-//   b = (f1x, f1y, f2x, f2y)       whitening rows: q = (d.f1)^2 + (d.f2)^2 = d^T S^-1 d
-//   c = (opacity, r, g, b)
-// d = pixel centre - (u, v). Eq. 2: w = opacity * exp(-q/2), cut at q > 9 (3 sigma).
+// Splat record in the workspace (3 x float4 per Gaussian, written by the preprocess):
+//   r0 = (u_hi, v_hi, u_lo, v_lo)   pixel-space centre in float-float
+//   r1 = (f1x, f1y, f2x, f2y)       scaled whitening rows: q' = (d.f1)^2 + (d.f2)^2
+//                                   = c d^T S^-1 d with c = log2(e)/2, so that the
+//                                   Gaussian factor of Eq. 2 is exp(-q/2) = 2^-q'
+//   r2 = (opacity, r, g, b)
+// For one tile the compositor stages each splat once (StagedSplat) with its centre
+// relative to the tile centre and one threshold that folds the 3-sigma cut (q <= 9)
+// and the alpha_min skip (opacity 2^-q' >= alpha_min) into q' <= thr.
 #pragma once
 #include "vis_internal.cuh"
 
 namespace vis {
 
+struct StagedSplat {
+    float4 a;   // (du, dv, f1x, f1y): centre relative to the tile centre
+    float4 b;   // (f2x, f2y, thr, opacity)
+    float4 c;   // (r, g, b, unused)
+};
+
+// qcut = 9 c (the 3-sigma cut in q' units), alpha_min as in the options.
+__device__ __forceinline__ StagedSplat stage_splat(const float4* __restrict__ rec, uint32_t g, float xc, float yc,
+                                                   float qcut, float alpha_min) {
+    const float4 r0 = rec[3 * (size_t)g + 0];
+    const float4 r1 = rec[3 * (size_t)g + 1];
+    const float4 r2 = rec[3 * (size_t)g + 2];
+    StagedSplat s;
+    s.a = make_float4(__fadd_rn(__fsub_rn(r0.x, xc), r0.z), __fadd_rn(__fsub_rn(r0.y, yc), r0.w), r1.x, r1.y);
+    const float thr = fminf(qcut, __log2f(__fdiv_rn(r2.x, alpha_min)));
+    s.b = make_float4(r1.z, r1.w, thr, r2.x);
+    s.c = make_float4(r2.y, r2.z, r2.w, 0.f);
+    return s;
+}
+
 struct PairEval {
     float dx, dy, p1, p2, q;
 };
 
-__device__ __forceinline__ PairEval eval_pair(float pcx, float pcy, float4 a, float4 b) {
+// (lx, ly): pixel centre relative to the tile centre; q is q' (scaled).
+__device__ __forceinline__ PairEval eval_pair(float lx, float ly, float4 a, float4 b) {
     PairEval e;
-    e.dx = __fsub_rn(__fsub_rn(pcx, a.x), a.z);
-    e.dy = __fsub_rn(__fsub_rn(pcy, a.y), a.w);
-    e.p1 = __fmaf_rn(e.dy, b.y, __fmul_rn(e.dx, b.x));
-    e.p2 = __fmaf_rn(e.dy, b.w, __fmul_rn(e.dx, b.z));
+    e.dx = __fsub_rn(lx, a.x);
+    e.dy = __fsub_rn(ly, a.y);
+    e.p1 = __fmaf_rn(e.dy, a.w, __fmul_rn(e.dx, a.z));
+    e.p2 = __fmaf_rn(e.dy, b.y, __fmul_rn(e.dx, b.x));
     e.q = __fmaf_rn(e.p2, e.p2, __fmul_rn(e.p1, e.p1));
     return e;
 }
 
-// Gaussian factor G = exp(-q/2)
-__device__ __forceinline__ float gauss_of_q(float q) { return __expf(__fmul_rn(-0.5f, q)); }
+// Gaussian factor of Eq. 2 from the scaled Mahalanobis distance: 2^-q' = exp(-q/2)
+// (one ex2 instruction; relative error ~2^-22 over the range used, q' <= 6.5)
+__device__ __forceinline__ float gauss_of_qs(float qs) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-qs));
+    return y;
+}
 
 }  // namespace vis

@@ -90,6 +90,7 @@ struct PrepParams {
     float limx, limy;
     int W, H, tile, tiles_x, tiles_y;
     float dilation, alpha_min;
+    float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
     float shc[12];           // SH polynomial constants, see sh_constants()
 };
 
@@ -153,8 +154,14 @@ void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uin
 // after its histogram). Ranges for its 32-bit tile keys:
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
 void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
+// q' = q * log2(e)/2 units: the 3-sigma cut is q' <= 9 log2(e)/2
+struct QScale {
+    float qcut;        // 9 log2(e) / 2
+    float inv_scale;   // 2 / log2(e) = 2 ln 2
+};
+QScale q_scale();
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
-                      float alpha_max, float t_stop, float* out_rgb, float* out_alpha,
+                      float alpha_max, float t_stop, int ppt, float* out_rgb, float* out_alpha,
                       cudaStream_t stream);
 void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3],
                      float alpha_min, float alpha_max, float t_stop, const float* d_rgb,

@@ -45,7 +45,8 @@ def gpu_stage_outputs(sc, ws):
     v = a[:, 1].astype(np.float64) + a[:, 3]
     f1 = b[:, 0:2].astype(np.float64)
     f2 = b[:, 2:4].astype(np.float64)
-    Q = f1[:, :, None] * f1[:, None, :] + f2[:, :, None] * f2[:, None, :]
+    qscale = 0.5 / np.log(2.0)   # the record's whitening rows are scaled by sqrt(log2(e)/2)
+    Q = (f1[:, :, None] * f1[:, None, :] + f2[:, :, None] * f2[:, None, :]) / qscale
     return dict(valid=(touched > 0).astype(np.int32), touched=touched, rect=rect.astype(np.int32),
                 zkey=depth, uv=np.stack([u, v], 1), conic=np.stack([Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]], 1),
                 opacity=c[:, 0].astype(np.float64), rgb=c[:, 1:4].astype(np.float64), keys=keys, vals=vals,
