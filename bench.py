@@ -182,9 +182,25 @@ def run_ours(args):
         d_rgb = torch.empty_like(rgb)
     cam_objs = [vis.make_camera(c) for c in cams]
     view0 = rank * args.steps
+    dynamic = args.workload == "6m"
+    if dynamic:
+        dyn = {k: torch.from_numpy(v).cuda() for k, v in extra.items()}
+        means0 = sc.tensors["means"].clone()
+        logits0 = sc.tensors["opacity_logits"].clone()
+        n_frames = desc["frames"]
+        upd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
 
-    def frame(i):
-        c = cam_objs[(view0 + i) % len(cam_objs)]
+    def frame(i, timed=False):
+        k = (view0 + i) % len(cam_objs)
+        c = cam_objs[k]
+        if dynamic:
+            if timed:
+                upd_ev[i][0].record(stream)
+            vis.vis_dynamic_update(means0, dyn["velocity"], logits0, dyn["amp"], dyn["freq"], dyn["phase"],
+                                   k / n_frames, sc.tensors["means"], sc.tensors["opacity_logits"])
+            if timed:
+                upd_ev[i][1].record(stream)
         vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         if fwdbwd:
             torch.sub(rgb, tgt_rgb, out=d_rgb)
@@ -210,7 +226,7 @@ def run_ours(args):
         vis.lib().vis_profile_begin()
         ev0.record(stream)
         for i in range(args.steps):
-            frame(i)
+            frame(i, timed=True)
         ev1.record(stream)
         torch.cuda.synchronize()
     import ctypes as C
@@ -226,6 +242,7 @@ def run_ours(args):
     frames_total = args.steps * world
     value = t_ms / frames_total
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
+    update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
     names = STAGES_DF if args.sort_mode == 1 else STAGES
     passes = npass.value
 
@@ -274,10 +291,11 @@ def run_ours(args):
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk.summary(), e2e=e2e,
                 gpu_launches=int(args.steps * ((6 + passes) if args.sort_mode == 0 else (11 + kDP + passes))
-                                 + (2 * args.steps if fwdbwd else 0)),
+                                 + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
                 roofline=roof,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
                 keys_per_frame=int(M), sort_passes=passes,
+                dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),
                 sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]) * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -83,6 +83,11 @@ typedef struct {
  *                  bit for bit; 1 moves about a quarter of the bytes.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
  *              thread (default 1); the image does not depend on it.
+ *  tile_extent which tiles a splat is listed in: 0 = every tile of the square of
+ *              radius ceil(3 sqrt(lambda_max(S))) + 1 px around its centre; 1 (default) =
+ *              every tile of the tight box around the region where a pixel can take the
+ *              splat (q <= min(9, 2 ln(opacity / alpha_min))). The image does not depend on
+ *              it; 1 lists ~40% fewer (tile, splat) pairs.
  * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
 typedef struct {
     int tile;
@@ -93,6 +98,7 @@ typedef struct {
     float t_stop;
     int sort_mode;
     int pixels_per_thread;
+    int tile_extent;
 } vis_render_opts;
 
 VIS_API void vis_default_opts(vis_render_opts* opts);
@@ -193,6 +199,18 @@ VIS_API vis_status vis_sort_workspace_size(int64_t m, int key_bits, size_t* byte
 VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                           uint32_t* vals_out, int64_t m, int key_bits, void* ws, size_t ws_bytes,
                           void* stream);
+
+/* Per-frame update of a dynamic scene (stands in for the per-frame Gaussian
+ * generator of section 3.3; the renderer re-sorts globally every frame, section 4):
+ *   means_out[i]  = means0[i] + t velocity[i]
+ *   logits_out[i] = logits0[i] + amp[i] sin(2 pi freq[i] t + phase[i])
+ *  means0, velocity      device float[n][3]
+ *  logits0, amp, freq, phase  device float[n]
+ *  means_out, logits_out device float[n][3], float[n] (may be the arrays a scene borrows)
+ * Outputs must not alias the inputs. */
+VIS_API vis_status vis_dynamic_update(const float* means0, const float* velocity, const float* logits0,
+                                      const float* amp, const float* freq, const float* phase, float t,
+                                      int64_t n, float* means_out, float* logits_out, void* stream);
 
 /* The same sort for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a library convenience). Some callers may not call cudaMalloc

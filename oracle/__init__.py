@@ -241,3 +241,13 @@ def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False):
     if return_g2:
         out["g2"] = g2
     return out
+
+
+def dynamic_update(means0, velocity, logits0, amp, freq, phase, t):
+    """FP64 frame-t update of the dynamic workload (stands in for the per-frame
+    generator of section 3.3): mu_t = mu_0 + t v, logit_t = logit_0 + A sin(2 pi f t + phi).
+    Computed from the float32 inputs and the float32 t."""
+    t = float(np.float32(t))
+    m = _f64(means0) + t * _f64(velocity)
+    lg = _f64(logits0) + _f64(amp) * np.sin(2.0 * np.pi * _f64(freq) * t + _f64(phase))
+    return m, lg

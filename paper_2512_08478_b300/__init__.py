@@ -39,7 +39,7 @@ class vis_camera(C.Structure):
 class vis_render_opts(C.Structure):
     _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
-                ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int)]
+                ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int), ("tile_extent", C.c_int)]
 
 
 class vis_ws_layout(C.Structure):
@@ -81,6 +81,7 @@ def lib():
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
             "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
             "vis_profile_begin": (C.c_int, []),
+            "vis_dynamic_update": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_float, C.c_int64, _P, _P, _P]),
             "vis_profile_end": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         }
@@ -207,6 +208,13 @@ def vis_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, key_bits, strea
     """Same sort with the library's static device scratch (no workspace; m <= 2^20)."""
     _ok(lib().vis_sort_pairs_noalloc(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
                                      int(keys_in.numel()), int(key_bits), _stream(stream)))
+
+
+def vis_dynamic_update(means0, velocity, logits0, amp, freq, phase, t, means_out, logits_out, stream=None):
+    """Frame-t update of a dynamic scene: means0 + t v, logits0 + A sin(2 pi f t + phi)."""
+    _ok(lib().vis_dynamic_update(_ptr(means0), _ptr(velocity), _ptr(logits0), _ptr(amp), _ptr(freq), _ptr(phase),
+                                 float(t), int(means0.shape[0]), _ptr(means_out), _ptr(logits_out),
+                                 _stream(stream)))
 
 
 def vis_last_error():

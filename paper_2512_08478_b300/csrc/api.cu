@@ -64,6 +64,8 @@ vis_render_opts resolve_opts(const vis_render_opts* o) {
 vis_status check_opts(const vis_render_opts& o) {
     if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
     if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
+    if (o.tile_extent != 0 && o.tile_extent != 1)
+        return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0 or 1 (got %d)", o.tile_extent);
     if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
         return fail(VIS_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2 (got %d)", o.pixels_per_thread);
     if (o.sort_mode != vis::kSortTileDepth && o.sort_mode != vis::kSortDepthFirst)
@@ -111,6 +113,7 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     p.W = W; p.H = H; p.tile = L.tile; p.tiles_x = L.tiles_x; p.tiles_y = L.tiles_y;
     p.dilation = o.dilation; p.alpha_min = o.alpha_min;
     p.wscale = (float)std::sqrt(0.5 / std::log(2.0));
+    p.tight_extent = o.tile_extent;
     vis::sh_constants(p.shc);
     return p;
 }
@@ -242,6 +245,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->t_stop = 1e-4f;
     o->sort_mode = vis::kSortDepthFirst;
     o->pixels_per_thread = 1;
+    o->tile_extent = 1;
 }
 
 const char* vis_last_error(void) { return g_err.c_str(); }
@@ -395,6 +399,24 @@ vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, 
     vis::launch_backward(p, L, static_cast<char*>(ws), bg, o.alpha_min, o.alpha_max, o.t_stop, d_rgb, d_alpha,
                          d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, stream);
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,
+                              const float* freq, const float* phase, float t, int64_t n, float* means_out,
+                              float* logits_out, void* stream_) {
+    if (n < 1 || n > 0x7fffffffLL) return fail(VIS_ERR_INVALID_ARG, "n must be in [1, 2^31-1]");
+    if (!std::isfinite(t)) return fail(VIS_ERR_INVALID_ARG, "t is not finite");
+    const void* ptrs[8] = {means0, velocity, logits0, amp, freq, phase, means_out, logits_out};
+    for (int k = 0; k < 8; ++k)
+        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "dynamic update buffer %d null or misaligned", k);
+    if ((const void*)means_out == (const void*)means0 || (const void*)logits_out == (const void*)logits0)
+        return fail(VIS_ERR_INVALID_ARG, "outputs must not alias the inputs");
+    vis::launch_dynamic_update(means0, velocity, logits0, amp, freq, phase, t, n, means_out, logits_out,
+                               reinterpret_cast<cudaStream_t>(stream_));
+    vis_status st = cuda_check(cudaGetLastError(), "launch");
+    if (st) return st;
     g_err.clear();
     return VIS_OK;
 }

@@ -116,15 +116,30 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 if (en2 > 0.f) { const float inv = rsqrtf(en2); ex *= inv; ey *= inv; }
                 else { ex = 1.f; ey = 0.f; }
                 const float i1 = rsqrtf(lam1) * p.wscale, i2 = rsqrtf(lam2) * p.wscale;
-                const float lam_ext = m + sqrtf(fmaxf(0.1f, disc));
-                const float radius = ceilf(3.f * sqrtf(lam_ext));
                 const float T = (float)p.tile;
                 const float ftx = (float)p.tiles_x, fty = (float)p.tiles_y;
+                float fx0, fx1, fy0, fy1;
+                if (p.tight_extent) {
+                    // tight box of the region a pixel can take the splat from: q <= min(9, 2 ln(o / alpha_min))
+                    // (the 3-sigma cut and the alpha_min skip), padded for float rounding
+                    const float qthr = fminf(9.f, 2.f * logf(opac / p.alpha_min)) * 1.0002f;
+                    const float rx = sqrtf(qthr * s00) * 1.0001f + 0.01f;
+                    const float ry = sqrtf(qthr * s11) * 1.0001f + 0.01f;
+                    // pixel px is reachable iff |px + 0.5 - u| <= rx
+                    fx0 = floorf((u.x - rx - 0.5f) / T); fx1 = floorf((u.x + rx - 0.5f) / T) + 1.f;
+                    fy0 = floorf((v.x - ry - 0.5f) / T); fy1 = floorf((v.x + ry - 0.5f) / T) + 1.f;
+                } else {
+                    // conservative square of radius ceil(3 sqrt(lambda_max)) plus one pixel
+                    const float lam_ext = m + sqrtf(fmaxf(0.1f, disc));
+                    const float radius = ceilf(3.f * sqrtf(lam_ext));
+                    fx0 = floorf((u.x - radius - 1.f) / T); fx1 = floorf((u.x + radius + 1.f) / T) + 1.f;
+                    fy0 = floorf((v.x - radius - 1.f) / T); fy1 = floorf((v.x + radius + 1.f) / T) + 1.f;
+                }
                 // clamp in float before converting (u may be far off screen)
-                const int ix0 = (int)fminf(ftx, fmaxf(0.f, floorf((u.x - radius - 1.f) / T)));
-                const int ix1 = (int)fminf(ftx, fmaxf(0.f, floorf((u.x + radius + 1.f) / T) + 1.f));
-                const int iy0 = (int)fminf(fty, fmaxf(0.f, floorf((v.x - radius - 1.f) / T)));
-                const int iy1 = (int)fminf(fty, fmaxf(0.f, floorf((v.x + radius + 1.f) / T) + 1.f));
+                const int ix0 = (int)fminf(ftx, fmaxf(0.f, fx0));
+                const int ix1 = (int)fminf(ftx, fmaxf(0.f, fx1));
+                const int iy0 = (int)fminf(fty, fmaxf(0.f, fy0));
+                const int iy1 = (int)fminf(fty, fmaxf(0.f, fy1));
                 touched = (ix1 > ix0 && iy1 > iy0) ? (uint32_t)((ix1 - ix0) * (iy1 - iy0)) : 0u;
                 if (touched > 0) {
                     x0 = ix0; x1 = ix1; y0 = iy0; y1 = iy1;

@@ -24,6 +24,7 @@ namespace vis {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr int kLookbackWindow = 16;   // predecessors read per look-back round
 
 template <typename K>
 __global__ void __launch_bounds__(256)
@@ -160,23 +161,34 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const uint32_t local_start = block_exclusive_scan_256(cnt, S.scan_tmp, nullptr);
     const uint32_t gstart = block_exclusive_scan_256(hist_pass[d], S.scan_tmp, nullptr);
 
-    // ---- decoupled look-back ----
+    // ---- decoupled look-back, a window of kLookbackWindow predecessors per round ----
+    // All loads of a window are issued together (one L2 round trip), then consumed
+    // in order until the first inclusive prefix; only a not-yet-published word is
+    // re-polled (bounded).
     uint32_t prefix = 0;
     if (part > 0) {
         int64_t q = (int64_t)part - 1;
-        bool timed_out = false;
-        while (true) {
-            uint32_t v = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
-            uint32_t spins = 0;
-            while ((v & ~kCountMask) == 0) {
-                if (++spins > kSpinLimit) { timed_out = true; break; }
-                if (spins > 8) __nanosleep(32);
-                v = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
+        bool timed_out = false, found = false;
+        while (!found && !timed_out && q >= 0) {
+            uint32_t v[kLookbackWindow];
+#pragma unroll
+            for (int i = 0; i < kLookbackWindow; ++i)
+                v[i] = (q - i >= 0) ? ld_relaxed(&lookback[(size_t)(q - i) * kRadix + d]) : kFlagInc;
+#pragma unroll
+            for (int i = 0; i < kLookbackWindow; ++i) {
+                if (found || timed_out || q - i < 0) break;
+                uint32_t w = v[i];
+                uint32_t spins = 0;
+                while ((w & ~kCountMask) == 0) {
+                    if (++spins > kSpinLimit) { timed_out = true; break; }
+                    if (spins > 8) __nanosleep(32);
+                    w = ld_relaxed(&lookback[(size_t)(q - i) * kRadix + d]);
+                }
+                if (timed_out) break;
+                prefix += w & kCountMask;
+                if ((w & ~kCountMask) == kFlagInc) found = true;
             }
-            if (timed_out) break;
-            prefix += v & kCountMask;
-            if ((v & ~kCountMask) == kFlagInc || q == 0) break;
-            --q;
+            q -= kLookbackWindow;
         }
         st_relaxed(&lb[d], kFlagInc | ((prefix + cnt) & kCountMask));
         if (timed_out) {

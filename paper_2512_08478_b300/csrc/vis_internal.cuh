@@ -91,6 +91,7 @@ struct PrepParams {
     int W, H, tile, tiles_x, tiles_y;
     float dilation, alpha_min;
     float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
+    int tight_extent;        // 1: tile rect from the tight opacity-aware 3-sigma box
     float shc[12];           // SH polynomial constants, see sh_constants()
 };
 
@@ -178,6 +179,10 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0);
+
+void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,
+                           const float* freq, const float* phase, float t, int64_t n, float* means_out,
+                           float* logits_out, cudaStream_t stream);
 
 // Sets the thread-local message returned by vis_last_error().
 void set_last_error(const char* msg);

@@ -28,6 +28,10 @@ def test_depth_first_equals_tile_depth_sort(tile):
     cam = synth.look_at((1.0, 2.0, 9.0), (0, 0, 0), 301, 187, 55.0)
     a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=0))
     b_rgb, b_alpha, sb, wb = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1))
+    c_rgb, c_alpha, sc_, wc = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1, tile_extent=0))
+    # the tile extent only changes which tiles list a splat, never a pixel
+    assert np.array_equal(c_rgb, b_rgb) and np.array_equal(c_alpha, b_alpha)
+    assert vis.vis_check(wb.buf) < vis.vis_check(wc.buf)
     va, ra, La = _sorted_vals_and_ranges(sa, wa)
     vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
     assert La.key_bytes == 8 and Lb.key_bytes == 4 and Lb.sort_mode == 1

@@ -44,7 +44,7 @@ def _stage_inputs():
 
 def test_preprocess_stage_matches_oracle():
     sc, cam = _stage_inputs()
-    _, _, s, ws = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=0))
+    _, _, s, ws = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=0, tile_extent=0))
     g = gpu_stage_outputs(s, ws)
     o = oracle.preprocess(sc, cam)
     both = (g["valid"] == 1) & (o["valid"] == 1)
@@ -67,7 +67,7 @@ def _expected_keys(o, tiles_x, keep):
 
 def test_keys_sort_and_ranges_bitexact():
     sc, cam = _stage_inputs()
-    _, _, s, ws = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=0))
+    _, _, s, ws = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=0, tile_extent=0))
     g = gpu_stage_outputs(s, ws)
     o = oracle.preprocess(sc, cam)
     # Gaussians whose float32 decisions differ from FP64 (rect edge, cull) are set aside

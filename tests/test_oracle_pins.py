@@ -373,3 +373,18 @@ def test_duplicate_and_ranges_match_naive_loops():
             assert (r[t, 0], r[t, 1]) == (idx[0], idx[-1] + 1)
         else:
             assert r[t, 0] == r[t, 1]
+
+
+def test_dynamic_update_reference_pins():
+    sc, ex, _ = synth.workload_dynamic(n=1000, frames=4)
+    m0, l0 = oracle.dynamic_update(sc["means"], ex["velocity"], sc["opacity_logits"], ex["amp"], ex["freq"],
+                                   ex["phase"], 0.0)
+    assert np.array_equal(m0, sc["means"].astype(np.float64))                 # t = 0: unchanged means
+    np.testing.assert_allclose(l0, sc["opacity_logits"] + ex["amp"] * np.sin(ex["phase"].astype(np.float64)),
+                               atol=1e-12)
+    ma, la = oracle.dynamic_update(sc["means"], ex["velocity"], sc["opacity_logits"], ex["amp"], ex["freq"],
+                                   ex["phase"], 0.25)
+    mb, lb = oracle.dynamic_update(sc["means"], ex["velocity"], sc["opacity_logits"], ex["amp"], ex["freq"],
+                                   ex["phase"], 1.25)
+    np.testing.assert_allclose(lb, la, atol=1e-9)                              # integer f: period 1 in t
+    np.testing.assert_allclose(mb - ma, ex["velocity"].astype(np.float64), atol=1e-9)   # linear in t
