@@ -306,6 +306,73 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """16 assets x 8 cameras = 128 images: one graph-captured vis_render_batch vs 128
+    sequential vis_render calls of the plain path (same options, images compared)."""
+    import ctypes as C
+    import torch
+    import paper_2512_08478_b300 as vis
+    from paper_2512_08478_b300 import synth, tuning
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    scenes_np, cams, cam_scene = synth.workload_batch()
+    scenes = [vis.Scene.from_numpy(s) for s in scenes_np]
+    if args.no_autotune:
+        opts_d, lanes, tuned_ms = dict(tile=16, pixels_per_thread=1, sort_mode=1), 8, None
+    else:
+        opts_d, lanes, tuned_ms = tuning.autotune(scenes, cams, cam_scene, cache=None,
+                                                  log=lambda m: print(m, file=sys.stderr))
+    opts = vis.make_opts(**opts_d)
+    b = vis.Batch(scenes, cams, cam_scene, lanes=lanes, opts=opts)
+    b.render()
+    stream = torch.cuda.current_stream()
+    # sequential plain path: one workspace for the largest image
+    nmax = max(s.n for s in scenes)
+    Wm = max(int(c.W) for c in cams)
+    Hm = max(int(c.H) for c in cams)
+    ws = vis.Workspace(nmax, Wm, Hm, key_capacity=16 * nmax + (1 << 20), opts=opts)
+    outs = [(torch.empty((3, c.H, c.W), device="cuda"), torch.empty((c.H, c.W), device="cuda")) for c in cams]
+    cam_objs = [vis.make_camera(c) for c in cams]
+
+    def sequential():
+        for i, c in enumerate(cam_objs):
+            vis.vis_render(scenes[cam_scene[i]].handle, c, cams[i].W, cams[i].H, (0.0, 0.0, 0.0), outs[i][0],
+                           outs[i][1], ws.buf, opts)
+
+    for _ in range(args.warmup):
+        b.launch()
+        sequential()
+    b.check()
+    vis.vis_check(ws.buf)
+    same = all(torch.equal(b.rgb[i], outs[i][0]) and torch.equal(b.alpha[i], outs[i][1]) for i in range(len(cams)))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e[0].record(stream)
+        for _ in range(args.steps):
+            b.launch()
+        e[1].record(stream)
+        for _ in range(args.steps):
+            sequential()
+        e[2].record(stream)
+        torch.cuda.synchronize()
+    b.check()
+    vis.vis_check(ws.buf)
+    t_batch = e[0].elapsed_time(e[1]) / args.steps
+    t_seq = e[1].elapsed_time(e[2]) / args.steps
+    n_g = sum(scenes[a].n for a in cam_scene)
+    line = dict(metric="ms per 128-image heterogeneous batch (16 assets x 8 cameras)", value=round(t_batch, 4),
+                unit="ms/batch", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=round(t_batch, 4),
+                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="16 assets (N log-uniform 2e4..2e6, SH 0..3) x 8 orbit cameras at "
+                                     "{512^2, 1280x720, 1920x1080}", images=len(cams),
+                            gaussians=[s.n for s in scenes], opts=opts_d, lanes=lanes),
+                sequential_ms=round(t_seq, 4), speedup_vs_sequential=round(t_seq / t_batch, 3),
+                images_identical_to_sequential=bool(same), autotune_best_ms=tuned_ms,
+                gaussian_views_per_s=round(n_g / t_batch * 1e3, 1), clocks=clk.summary())
+    print(json.dumps(line), flush=True)
+
+
 def _committed_traffic(kernel, M, n):
     """DRAM bytes per launch from a committed ncu capture (profiles/traffic.json), scaled
     to this launch by keys (sort, composite) or Gaussians (preprocess); None if absent."""
@@ -439,7 +506,8 @@ def main():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small"])
+    ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch"])
+    ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sort-mode", type=int, default=1, choices=[0, 1],
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth-first sort then tile sort")
@@ -449,6 +517,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

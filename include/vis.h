@@ -200,6 +200,35 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
                           uint32_t* vals_out, int64_t m, int key_bits, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* Batched render of many assets seen by many cameras (the paper renders several
+ * models per frame, Algorithm 1 "for all model M_k"; here every (asset, camera) pair
+ * is an independent image). A batch handle owns `lanes` streams. vis_render_batch
+ * assigns the images to lanes (longest first, to the least loaded lane); each lane
+ * renders its images one after another in its own slice of the workspace; the
+ * whole fork / render / join sequence is captured into a CUDA graph on the first
+ * call and replayed by later calls with identical arguments (same pointers, cameras,
+ * sizes, options), so the lanes run as concurrent graph branches.
+ *  scenes[n_scenes]        scene handles (host array)
+ *  cams[n_images]          host array of cameras; cam_scene[i] = asset of image i
+ *  W, H[n_images]          host arrays of image sizes
+ *  out_rgb, out_alpha      host arrays of n_images device pointers ([3][H][W], [H][W])
+ *  ws, ws_bytes            device workspace >= vis_batch_workspace_size(...)
+ * The first call synchronises nothing but must not itself be inside a stream capture.
+ * Device errors of any image are returned by vis_batch_check (which synchronises). */
+typedef struct vis_batch* vis_batch_t;
+VIS_API vis_status vis_batch_create(int lanes, vis_batch_t* out);
+VIS_API void vis_batch_destroy(vis_batch_t batch);
+VIS_API vis_status vis_batch_workspace_size(const vis_scene_t* scenes, int n_scenes, const int* cam_scene,
+                                            const int* W, const int* H, int n_images, int lanes,
+                                            int64_t key_capacity, const vis_render_opts* opts,
+                                            size_t* bytes);
+VIS_API vis_status vis_render_batch(vis_batch_t batch, const vis_scene_t* scenes, int n_scenes,
+                                    const vis_camera* cams, const int* cam_scene, const int* W,
+                                    const int* H, int n_images, const float bg[3],
+                                    float* const* out_rgb, float* const* out_alpha, void* ws,
+                                    size_t ws_bytes, const vis_render_opts* opts, void* stream);
+VIS_API vis_status vis_batch_check(const void* ws, int n_images, void* stream, int64_t* max_keys);
+
 /* Per-frame update of a dynamic scene (stands in for the per-frame Gaussian
  * generator of section 3.3; the renderer re-sorts globally every frame, section 4):
  *   means_out[i]  = means0[i] + t velocity[i]

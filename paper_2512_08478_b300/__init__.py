@@ -81,6 +81,13 @@ def lib():
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
             "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
             "vis_profile_begin": (C.c_int, []),
+            "vis_batch_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
+            "vis_batch_destroy": (None, [_P]),
+            "vis_batch_workspace_size": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, C.c_int, C.c_int64,
+                                                   C.POINTER(vis_render_opts), C.POINTER(C.c_size_t)]),
+            "vis_render_batch": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, _P, C.c_int, C.POINTER(C.c_float),
+                                           _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts), _P]),
+            "vis_batch_check": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int64)]),
             "vis_dynamic_update": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_float, C.c_int64, _P, _P, _P]),
             "vis_profile_end": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -351,3 +358,74 @@ def sort_pairs(keys, vals, key_bits=64):
     ws = torch.empty(max(16, vis_sort_workspace_size(m, key_bits)), dtype=torch.uint8, device=keys.device)
     vis_sort_pairs(keys, vals, ko, vo, key_bits, ws)
     return ko, vo
+
+
+class Batch:
+    """Many (asset, camera) images rendered by one vis_render_batch call (a CUDA graph).
+
+    scenes: list of Scene; cams: list of cameras; cam_scene: asset index per image.
+    Outputs are allocated here; the workspace has `lanes` slices of `key_capacity` keys.
+    """
+
+    def __init__(self, scenes, cams, cam_scene, lanes=8, key_capacity=None, opts=None):
+        torch = _torch()
+        self.scenes, self.cams, self.cam_scene = list(scenes), list(cams), list(cam_scene)
+        self.n = len(self.cams)
+        self.opts = opts
+        self.lanes = int(lanes)
+        h = _P()
+        _ok(lib().vis_batch_create(self.lanes, C.byref(h)))
+        self.handle = h
+        self._scene_arr = (_P * len(self.scenes))(*[s.handle.value for s in self.scenes])
+        self._cams = (vis_camera * self.n)(*[make_camera(c) for c in self.cams])
+        self._cs = (C.c_int * self.n)(*self.cam_scene)
+        self._W = (C.c_int * self.n)(*[int(c.W) for c in self.cams])
+        self._H = (C.c_int * self.n)(*[int(c.H) for c in self.cams])
+        self.rgb = [torch.empty((3, c.H, c.W), device="cuda") for c in self.cams]
+        self.alpha = [torch.empty((c.H, c.W), device="cuda") for c in self.cams]
+        self._rgb_p = (_P * self.n)(*[t.data_ptr() for t in self.rgb])
+        self._a_p = (_P * self.n)(*[t.data_ptr() for t in self.alpha])
+        if key_capacity is None:
+            key_capacity = max(1 << 16, 8 * max(s.n for s in self.scenes))
+        self._alloc(key_capacity)
+
+    def _alloc(self, key_capacity):
+        torch = _torch()
+        b = C.c_size_t()
+        _ok(lib().vis_batch_workspace_size(self._scene_arr, len(self.scenes), self._cs, self._W, self._H, self.n,
+                                           self.lanes, int(key_capacity), _opts_ref(self.opts), C.byref(b)))
+        self.ws = torch.empty((b.value + 15) // 16 * 16, dtype=torch.uint8, device="cuda")
+        self.key_capacity = key_capacity
+
+    def launch(self, bg=(0.0, 0.0, 0.0), stream=None):
+        _ok(lib().vis_render_batch(self.handle, self._scene_arr, len(self.scenes), self._cams, self._cs, self._W,
+                                   self._H, self.n, _bg(bg), self._rgb_p, self._a_p, _ptr(self.ws),
+                                   self.ws.numel(), _opts_ref(self.opts), _stream(stream)))
+
+    def check(self, stream=None):
+        m = C.c_int64()
+        st = lib().vis_batch_check(_ptr(self.ws), self.n, _stream(stream), C.byref(m))
+        if st != VIS_OK:
+            err = VisError(st, lib().vis_last_error().decode())
+            err.num_keys = m.value
+            raise err
+        return m.value
+
+    def render(self, bg=(0.0, 0.0, 0.0)):
+        """Launch, check, and grow the workspace once on a capacity error."""
+        for _ in range(2):
+            self.launch(bg)
+            try:
+                self.check()
+                return self.rgb, self.alpha
+            except VisError as e:
+                if e.status != VIS_ERR_CAPACITY:
+                    raise
+                self._alloc(int(e.num_keys * 1.25) + 1024)
+        raise VisError(VIS_ERR_CAPACITY, "batch workspace growth did not converge")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.vis_batch_destroy(h)
+            self.handle = None

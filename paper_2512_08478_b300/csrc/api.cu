@@ -133,6 +133,8 @@ Profiler g_prof;
 // Record event `k` (0 = start, k = end of stage k-1) of the current render.
 void prof_mark(int k, cudaStream_t stream) {
     if (!g_prof.on || g_prof.count >= kProfRing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     cudaEventRecord(g_prof.ev[g_prof.count][k], stream);
 }
 
@@ -141,6 +143,13 @@ void prof_mark(int k, cudaStream_t stream) {
 namespace vis {
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+int64_t scene_size(vis_scene_t s) { return s ? s->n : 0; }
+
+void append_scene_key(std::vector<unsigned char>& key, vis_scene_t s) {
+    const unsigned char* c = reinterpret_cast<const unsigned char*>(s);
+    key.insert(key.end(), c, c + sizeof(vis_scene));
+}
 
 QScale q_scale() {
     const double c = 0.5 / std::log(2.0);   // log2(e) / 2
@@ -362,7 +371,13 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread, out_rgb,
                           out_alpha, stream);
     prof_mark(7, stream);
-    if (g_prof.on && g_prof.count < kProfRing) { ++g_prof.count; g_prof.passes = L.passes; }
+    if (g_prof.on && g_prof.count < kProfRing) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            ++g_prof.count;
+            g_prof.passes = L.passes;
+        }
+    }
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;

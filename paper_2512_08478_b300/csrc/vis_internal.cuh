@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/vis.h"
 
 namespace vis {
@@ -183,6 +185,10 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
 void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,
                            const float* freq, const float* phase, float t, int64_t n, float* means_out,
                            float* logits_out, cudaStream_t stream);
+
+// Scene accessors for the batch planner (the scene struct is private to api.cu).
+int64_t scene_size(vis_scene_t s);
+void append_scene_key(std::vector<unsigned char>& key, vis_scene_t s);
 
 // Sets the thread-local message returned by vis_last_error().
 void set_last_error(const char* msg);
