@@ -44,6 +44,9 @@ STAGES = ["clear", "preprocess", "duplicate", "sort_histogram", "sort_passes", "
 # "sort_histogram"/"sort_passes" = the stable sort by tile id of 4-byte keys
 STAGES_DF = ["clear", "preprocess", "depth_sort_and_emit", "tile_sort_histogram", "tile_sort_passes", "ranges",
              "composite"]
+# sort_mode 2 (depth sort + counting binning): stage 3 = binning counts, scans and ranges,
+# stage 4 = binning emission (each Gaussian index written to its slot)
+STAGES_BIN = ["clear", "preprocess", "depth_sort", "bin_count_scan", "bin_emit", "ranges", "composite"]
 
 
 def _peaks():
@@ -167,6 +170,8 @@ def run_ours(args):
     sc = vis.Scene.from_numpy(sc_np)
     n = sc.n
     cap = 16 * n + (1 << 20)
+    if args.sort_mode is None:
+        args.sort_mode = vis.make_opts().sort_mode
     opts = vis.make_opts(sort_mode=args.sort_mode)
     ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
@@ -243,7 +248,7 @@ def run_ours(args):
     value = t_ms / frames_total
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
     update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
-    names = STAGES_DF if args.sort_mode == 1 else STAGES
+    names = {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode]
     passes = npass.value
 
     # keys per frame averaged over the views used
@@ -256,7 +261,8 @@ def run_ours(args):
 
     # ---- roofline of the dominant stage ----
     peaks = _peaks()
-    dom = max(("preprocess", "sort_passes", "composite"), key=lambda s: stage_ms[s])
+    cands = ("preprocess", "sort_passes", "composite") if args.sort_mode != 2 else ("preprocess", "composite")
+    dom = max(cands, key=lambda s: stage_ms[s])
     sh_k = (desc["sh_degree"] + 1) ** 2
     bytes_pre = n * (12 + 12 + 16 + 4 + 12 * sh_k) + n * (48 + 4 + 8 + 4)
     if dom == "sort_passes":
@@ -290,13 +296,14 @@ def run_ours(args):
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk.summary(), e2e=e2e,
-                gpu_launches=int(args.steps * ((6 + passes) if args.sort_mode == 0 else (11 + kDP + passes))
+                gpu_launches=int(args.steps * {0: 6 + passes, 1: 11 + kDP + passes, 2: 12 + kDP}[args.sort_mode]
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
                 roofline=roof,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
                 keys_per_frame=int(M), sort_passes=passes,
                 dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),
-                sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]) * 1e3, 1),
+                sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]
+                                           + (stage_ms["duplicate"] if args.sort_mode == 2 else 0.0)) * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
@@ -509,8 +516,9 @@ def main():
     ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch"])
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--sort-mode", type=int, default=1, choices=[0, 1],
-                    help="0: one sort of 64-bit (tile, depth) keys; 1: depth-first sort then tile sort")
+    ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1, 2],
+                    help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
+                         "2: depth sort then counting binning (default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -79,8 +79,11 @@ typedef struct {
  *              0 = one LSD sort of 64-bit (tile << 32 | depth) keys;
  *              1 = depth first (default): the surviving splats are sorted once by
  *                  32-bit depth (as in the paper), their tile copies are emitted in that
- *                  order and stably sorted by tile id alone. Both give the same order
- *                  bit for bit; 1 moves about a quarter of the bytes.
+ *                  order and stably sorted by tile id alone;
+ *              2 = depth first, then a stable counting binning into tiles (no tile keys;
+ *                  up to 29056 tiles, beyond that mode 1 is used).
+ *              All give the same order bit for bit; 1 moves about a quarter of the bytes
+ *              of 0.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
  *              thread (default 1); the image does not depend on it.
  *  tile_extent which tiles a splat is listed in: 0 = every tile of the square of

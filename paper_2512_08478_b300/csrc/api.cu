@@ -68,8 +68,8 @@ vis_status check_opts(const vis_render_opts& o) {
         return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0 or 1 (got %d)", o.tile_extent);
     if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
         return fail(VIS_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2 (got %d)", o.pixels_per_thread);
-    if (o.sort_mode != vis::kSortTileDepth && o.sort_mode != vis::kSortDepthFirst)
-        return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0 or 1 (got %d)", o.sort_mode);
+    if (o.sort_mode < vis::kSortTileDepth || o.sort_mode > vis::kSortDepthBin)
+        return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0, 1 or 2 (got %d)", o.sort_mode);
     if (!(o.dilation >= 0.f) || !std::isfinite(o.dilation)) return fail(VIS_ERR_INVALID_ARG, "dilation must be finite and >= 0");
     if (!(o.alpha_min > 0.f && o.alpha_min < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_min must be in (0, 1)");
     if (!(o.alpha_max > 0.f && o.alpha_max < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_max must be in (0, 1)");
@@ -183,20 +183,27 @@ void sh_constants(float out[12]) {
 
 Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     Layout L;
-    L.mode = mode;
     L.n = n; L.W = W; L.H = H; L.tile = tile;
     L.tiles_x = (W + tile - 1) / tile;
     L.tiles_y = (H + tile - 1) / tile;
     L.ntiles = (int64_t)L.tiles_x * L.tiles_y;
+    // the counting binning needs its per-tile counters in shared memory
+    if (mode == kSortDepthBin && L.ntiles > kBinMaxTiles4) mode = kSortDepthFirst;
+    L.mode = mode;
     L.tile_bits = ceil_log2(L.ntiles);
     L.cap = cap;
     L.prep_blocks = (n + kPrepThreads - 1) / kPrepThreads;
-    const bool df = mode == kSortDepthFirst;
+    const bool df = mode != kSortTileDepth;
+    const bool bin = mode == kSortDepthBin;
     L.key_bits = df ? L.tile_bits : 32 + L.tile_bits;
-    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
-    L.key_bytes = df ? 4 : 8;
-    L.sort_parts = df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap);
+    L.passes = bin ? 0 : (L.key_bits + kRadixBits - 1) / kRadixBits;
+    L.key_bytes = bin ? 0 : (df ? 4 : 8);
+    L.sort_parts = bin ? 0 : (df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap));
     L.sorted_buffer = L.passes & 1;
+    if (bin) {
+        L.bin_chunk = bin_chunk(n);
+        L.bin_chunks = (n + L.bin_chunk - 1) / L.bin_chunk;
+    }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     // cleared every frame: status block, histograms, look-back words, tile ranges
@@ -219,10 +226,20 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
         for (int b = 0; b < 2; ++b) L.off_dkeys[b] = take(sizeof(uint32_t) * (size_t)n);
         for (int b = 0; b < 2; ++b) L.off_dvals[b] = take(sizeof(uint32_t) * (size_t)n);
     }
-    L.off_keys[0] = take((size_t)L.key_bytes * (size_t)cap);
-    L.off_keys[1] = take((size_t)L.key_bytes * (size_t)cap);
-    L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
-    L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
+    if (bin) {
+        L.off_counts = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
+        L.off_chunk_base = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
+        L.off_totals = take(sizeof(uint32_t) * (size_t)L.ntiles);
+        L.off_tile_start = take(sizeof(uint32_t) * (size_t)L.ntiles);
+        L.off_keys[0] = L.off_keys[1] = 0;
+        L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
+        L.off_vals[1] = L.off_vals[0];
+    } else {
+        L.off_keys[0] = take((size_t)L.key_bytes * (size_t)cap);
+        L.off_keys[1] = take((size_t)L.key_bytes * (size_t)cap);
+        L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
+        L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
+    }
     L.off_tfinal = take(sizeof(float) * (size_t)W * H);
     L.off_last = take(sizeof(int32_t) * (size_t)W * H);
     L.off_g2 = take(sizeof(float) * 9 * (size_t)n);
@@ -356,7 +373,12 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     prof_mark(1, stream);
     vis::launch_preprocess(p, L, w, stream);
     prof_mark(2, stream);
-    if (L.mode == vis::kSortDepthFirst) {
+    if (L.mode == vis::kSortDepthBin) {
+        vis::launch_depth_sort(L, w, stream);
+        prof_mark(3, stream);
+        vis::launch_tile_bin(L, w, stream, g_prof.on ? &prof_mark : nullptr);
+        prof_mark(5, stream);
+    } else if (L.mode == vis::kSortDepthFirst) {
         vis::launch_depth_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
         prof_mark(5, stream);
         vis::launch_ranges32(L, w, stream);

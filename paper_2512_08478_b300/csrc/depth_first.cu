@@ -140,7 +140,7 @@ static int sms() {
     return s;
 }
 
-void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
+void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     const int blocks_n = (int)L.prep_blocks;
@@ -152,7 +152,6 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* dv1 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[1]);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
-
     // 1. compaction of the surviving splats, in index order
     visible_block_sums<<<blocks_n, kPrepThreads, 0, stream>>>(touched, L.n, bvis);
     launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0, stream);
@@ -161,6 +160,16 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // 2. sort by depth (4 passes; the result lands in buffer 0)
     launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
                                   ctrl->part_counter, &ctrl->error, stream);
+}
+
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
+    const int blocks_n = (int)L.prep_blocks;
+    uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[0]);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
+    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
+    launch_depth_sort(L, ws, stream);
     // 3. tile copies in depth order
     uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);

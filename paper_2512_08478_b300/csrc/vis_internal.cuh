@@ -38,6 +38,10 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // Sort modes (vis_render_opts.sort_mode)
 constexpr int kSortTileDepth = 0;   // one sort of 64-bit (tile << 32 | depth) keys
 constexpr int kSortDepthFirst = 1;  // depth sort of the surviving splats, then a tile sort
+constexpr int kSortDepthBin = 2;    // depth sort, then stable counting binning into tiles
+// tile counts that the binning's per-warp shared-memory counters hold (8 or 4 warps)
+constexpr int kBinMaxTiles8 = 14528;
+constexpr int kBinMaxTiles4 = 29056;
 
 struct Layout {
     int mode = kSortTileDepth;
@@ -58,6 +62,9 @@ struct Layout {
     size_t off_dkeys[2] = {0, 0}, off_dvals[2] = {0, 0}, off_bsum2 = 0, off_boff2 = 0;
     size_t lookback_words_depth = 0;
     int key_bytes = 8;
+    // depth-bin mode only
+    int64_t bin_chunk = 0, bin_chunks = 0;
+    size_t off_counts = 0, off_chunk_base = 0, off_totals = 0, off_tile_start = 0;
     size_t zero_begin = 0, zero_end = 0;   // region cleared before every render
     size_t total = 0;
     int sorted_buffer = 0;
@@ -156,6 +163,11 @@ void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uin
 // Depth-first mode: compaction, depth sort, emission (then mark(3)), tile sort (mark(4)
 // after its histogram). Ranges for its 32-bit tile keys:
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
+// Compaction of the surviving splats and their stable sort by depth (result in dvals[0]).
+void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream);
+// Depth-bin mode: counting binning of the depth-sorted splats (mark(4) after the scans).
+void launch_tile_bin(const Layout& L, char* ws, cudaStream_t stream, StageMark mark);
+int64_t bin_chunk(int64_t n);
 void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
 // q' = q * log2(e)/2 units: the 3-sigma cut is q' <= 9 log2(e)/2
 struct QScale {

@@ -53,9 +53,12 @@ def test_workspace_queries_and_validation(L):
     df = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=1))
     assert df.key_bytes == 4 and df.sort_mode == 1 and df.sort_passes == 2   # 13 tile bits
     assert vis.vis_workspace_size(10_000, 256, 256, 100_000, vis.make_opts(sort_mode=1)) < b
-    assert vis.make_opts().sort_mode == 1   # depth first is the default
+    bn = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=2))
+    assert bn.sort_mode == 2 and bn.key_bytes == 0
+    big = vis.vis_workspace_layout(10_000, 2048, 1024, 10 ** 9, vis.make_opts(sort_mode=2, tile=8))
+    assert big.sort_mode == 1     # 32768 tiles: too many for the binning's counters -> tile sort
     with pytest.raises(vis.VisError):
-        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=2))
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=3))
     assert vis.vis_sort_workspace_size(0, 45) > 0
     with pytest.raises(vis.VisError):
         vis.vis_sort_workspace_size(10, 65)

@@ -13,6 +13,13 @@ from gpu_helpers import image_parity, render_gpu, ws_view
 pytestmark = pytest.mark.gpu
 
 
+def _norm(ranges):
+    """Empty tiles may be [s, s) for any s: compare them as [0, 0)."""
+    r = ranges.copy()
+    r[r[:, 0] == r[:, 1]] = 0
+    return r
+
+
 def _sorted_vals_and_ranges(sc, ws):
     L = ws.layout()
     m = int(ws_view(ws, L.off_ctrl, 1, np.uint32)[0])
@@ -40,31 +47,34 @@ def test_depth_first_equals_tile_depth_sort(tile):
     assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
 
 
-def test_depth_first_small_workload_parity():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_depth_first_small_workload_parity(mode):
     sc, cams = synth.workload_small()
-    rgb, alpha, _, _ = render_gpu(sc, cams[0], opts=vis.make_opts(sort_mode=1))
+    rgb, alpha, _, _ = render_gpu(sc, cams[0], opts=vis.make_opts(sort_mode=mode))
     ref, _ = oracle.render(sc, cams[0])
     image_parity(rgb, alpha, ref)
 
 
-def test_depth_first_all_culled_and_single_tile():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_depth_first_all_culled_and_single_tile(mode):
     sc, cams = synth.workload_small()
     dead = dict(sc, opacity_logits=np.full_like(sc["opacity_logits"], -30.0))
-    rgb, alpha, _, ws = render_gpu(dead, cams[0], (0.5, 0.5, 0.5), vis.make_opts(sort_mode=1))
+    rgb, alpha, _, ws = render_gpu(dead, cams[0], (0.5, 0.5, 0.5), vis.make_opts(sort_mode=mode))
     assert np.all(alpha == 0.0) and vis.vis_check(ws.buf) == 0
     cam = synth.look_at((0, 0, 4), (0, 0, 0), 12, 10, 60.0)   # one tile
-    rgb, alpha, _, _ = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=1))
+    rgb, alpha, _, _ = render_gpu(sc, cam, opts=vis.make_opts(sort_mode=mode))
     ref, _ = oracle.render(sc, cam)
     image_parity(rgb, alpha, ref)
 
 
-def test_depth_first_gradients_match_oracle():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_depth_first_gradients_match_oracle(mode):
     import torch
     sc, cam = synth.fd_scene()
     rng = np.random.default_rng(8)
     gC = rng.standard_normal((3, cam.H, cam.W))
     gA = rng.standard_normal((cam.H, cam.W))
-    opts = vis.make_opts(sort_mode=1)
+    opts = vis.make_opts(sort_mode=mode)
     _, _, s, ws = render_gpu(sc, cam, (0, 0, 0), opts)
     grads = {k: torch.empty_like(s.tensors[k]) for k in vis.FIELDS}
     vis.vis_render_backward(s.handle, cam, cam.W, cam.H, (0, 0, 0),
@@ -77,13 +87,25 @@ def test_depth_first_gradients_match_oracle():
         assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), k
 
 
-def test_depth_first_capacity_error_then_retry():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_depth_first_capacity_error_then_retry(mode):
     sc_np, cams = synth.workload_small()
     cam = cams[0]
-    opts = vis.make_opts(sort_mode=1)
+    opts = vis.make_opts(sort_mode=mode)
     s = vis.Scene.from_numpy(sc_np)
     ws = vis.Workspace(s.n, cam.W, cam.H, key_capacity=100, opts=opts)
     rgb, alpha = vis._render_checked(s, cam, cam.W, cam.H, (0, 0, 0), ws, opts)
     assert ws.key_capacity > 100
     ref, _ = oracle.render(sc_np, cam)
     image_parity(rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), ref)
+
+
+@pytest.mark.slow
+def test_depth_bin_1m_sampled_equals_tile_depth_sort():
+    sc, cams = synth.workload_1m(views=32)
+    a_rgb, a_alpha, sa, wa = render_gpu(sc, cams[5], opts=vis.make_opts(sort_mode=0))
+    b_rgb, b_alpha, sb, wb = render_gpu(sc, cams[5], opts=vis.make_opts(sort_mode=2))
+    va, ra, _ = _sorted_vals_and_ranges(sa, wa)
+    vb, rb, _ = _sorted_vals_and_ranges(sb, wb)
+    assert np.array_equal(va, vb) and np.array_equal(_norm(ra), _norm(rb))
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
