@@ -1,9 +1,10 @@
 // K7 -- adjoint of the render (section 3.2: the splatting formulation is
 // differentiable in every Gaussian parameter).
 //
-// K7a composite_backward_kernel: one CTA per tile, one thread per pixel, walking
-// the tile's sorted range back to front in shared-memory chunks, starting from the
-// final transmittance and the last contributor the forward stored. Per-splat
+// K7a composite_backward_kernel: one CTA per tile, one thread per pixel, each warp an
+// 8 x 4 pixel block, walking the tile's sorted range back to front in shared-memory
+// chunks -- per warp only the splats whose 3-sigma box meets its block -- starting
+// from the final transmittance and the last contributor the forward stored. Per-splat
 // alphas are recomputed (with the forward's exact arithmetic, so every skip and cut
 // decision is the same) rather than stored; T before each splat is recovered as
 // T / (1 - alpha). With S the colour behind a splat, normalised by the
@@ -34,19 +35,25 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
                           float* __restrict__ g2) {
     constexpr int NT = TILE * TILE;
+    constexpr int NW = NT / 32;               // warps; each owns an 8 x 4 pixel block
+    constexpr int BX = TILE / 8, BH = 4;
     constexpr int CH = NT < 256 ? NT : 256;   // splats staged per chunk
+    static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
     __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
-    __shared__ uint32_t s_g[CH];
+    __shared__ uint32_t s_g[CH], s_mask[CH];
+    __shared__ uint16_t s_list[NW][CH];
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    const int px = tx * TILE + (threadIdx.x % TILE), py = ty * TILE + (threadIdx.x / TILE);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bx = warp % BX, by = warp / BX;
+    const int px = tx * TILE + bx * 8 + (lane & 7), py = ty * TILE + by * BH + (lane >> 3);
     const bool inside = px < W && py < H;
     const size_t pix = (size_t)py * W + px;
     const size_t HW = (size_t)H * W;
-    const float xc = (float)(tx * TILE) + 0.5f * TILE, yc = (float)(ty * TILE) + 0.5f * TILE;
+    const float half = 0.5f * TILE;
+    const float xc = (float)(tx * TILE) + half, yc = (float)(ty * TILE) + half;
     const float lx = (float)px + 0.5f - xc, ly = (float)py + 0.5f - yc;
     const uint2 r = ranges[tile];
-    const int lane = threadIdx.x & 31;
 
     float T = 1.f, TN = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gA = 0.f;
     int32_t last = 0;
@@ -80,9 +87,21 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
             s_c[threadIdx.x] = st.c;
+            s_mask[threadIdx.x] = warp_block_mask<NW, BX, BH>(st, half);
         }
         __syncthreads();
-        for (int k = cnt - 1; k >= 0; --k) {
+        // this warp's list of splats whose 3-sigma box meets its block, in depth order
+        int nlist = 0;
+        for (int g0 = 0; g0 < cnt; g0 += 32) {
+            const int k = g0 + lane;
+            const bool in = k < cnt && ((s_mask[k] >> warp) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, in);
+            if (in) s_list[warp][nlist + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)k;
+            nlist += __popc(bal);
+        }
+        __syncwarp();
+        for (int i = nlist - 1; i >= 0; --i) {     // back to front
+            const int k = s_list[warp][i];
             const int64_t pos = lo + k;   // sorted position of this splat
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;

@@ -97,20 +97,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             s_a[threadIdx.x] = s.a;
             s_b[threadIdx.x] = s.b;
             s_c[threadIdx.x] = s.c;
-            // axis-aligned half extents of {d : q'(d) <= thr}: sqrt(thr (Q'^-1)_xx), ...
-            const float det = fabsf(__fmaf_rn(s.a.z, s.b.y, -__fmul_rn(s.a.w, s.b.x)));
-            const float ext = sqrtf(fmaxf(s.b.z, 0.f)) / det;
-            const float rx = ext * sqrtf(__fmaf_rn(s.a.w, s.a.w, __fmul_rn(s.b.y, s.b.y))) * 1.0001f + 1e-3f;
-            const float ry = ext * sqrtf(__fmaf_rn(s.a.z, s.a.z, __fmul_rn(s.b.x, s.b.x))) * 1.0001f + 1e-3f;
-            uint32_t m = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                // pixel centres of block w span [x0, x0 + 7] x [y0, y0 + BH - 1] (tile-centre relative)
-                const float mx = (float)((w % BX) * 8) + 4.f - half;
-                const float my = (float)((w / BX) * BH) + 0.5f * BH - half;
-                const float ox = fabsf(s.a.x - mx) - 3.5f, oy = fabsf(s.a.y - my) - (0.5f * BH - 0.5f);
-                if (ox <= rx && oy <= ry) m |= 1u << w;
-            }
+            const uint32_t m = warp_block_mask<NW, BX, BH>(s, half);
             s_mask[threadIdx.x] = m;
         }
         __syncthreads();
