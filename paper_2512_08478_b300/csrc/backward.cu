@@ -26,6 +26,32 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sums eight per-lane values over the warp with 9 shuffles (recursive halving: each
+// exchange step hands half of the remaining values to the partner lane). On return,
+// lanes with (lane & 3) == 0 hold the total of value index
+// 4 bit4(lane) + 2 bit3(lane) + bit2(lane); the index is returned in *which.
+__device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane, int* which) {
+    const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4;
+    float w[4], x[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u4 ? v[i] : v[i + 4];
+        const float keep = u4 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u3 ? w[i] : w[i + 2];
+        const float keep = u3 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y = (u2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, u2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    *which = (u4 ? 4 : 0) + (u3 ? 2 : 0) + (u2 ? 1 : 0);
+    return y;
+}
+
 template <int TILE>
 __global__ void __launch_bounds__(TILE * TILE)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -140,26 +166,25 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int f = 0; f < 9; ++f) g[f] = warp_sum(g[f]);
-                if (lane == 0) {
-                    float* dst = g2 + 9 * (size_t)s_g[k];
-#pragma unroll
-                    for (int f = 0; f < 9; ++f)
-                        if (g[f] != 0.f) atomicAdd(dst + f, g[f]);
-                }
+                int which;
+                const float t8 = warp_sum8_transposed(g, lane, &which);
+                const float t9 = warp_sum(g[8]);
+                float* dst = g2 + 9 * (size_t)s_g[k];
+                if ((lane & 3) == 0 && t8 != 0.f) atomicAdd(dst + which, t8);
+                if (lane == 1 && t9 != 0.f) atomicAdd(dst + 8, t9);
             }
         }
     }
 }
 
+template <int DEG>
 __global__ void __launch_bounds__(kPrepThreads)
 preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uint32_t* __restrict__ touched,
                            float* __restrict__ d_means, float* __restrict__ d_log_scales,
                            float* __restrict__ d_quats, float* __restrict__ d_logits, float* __restrict__ d_sh) {
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
     if (i >= p.n) return;
-    const int K = (p.deg + 1) * (p.deg + 1);
+    constexpr int K = (DEG + 1) * (DEG + 1);
     float* dsh = d_sh + (size_t)i * K * 3;
     if (touched[i] == 0) {
         for (int k = 0; k < 3; ++k) { d_means[3 * i + k] = 0.f; d_log_scales[3 * i + k] = 0.f; }
@@ -182,19 +207,19 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
 #pragma unroll
     for (int k = 0; k < 16; ++k) { Y[k] = 0.f; Yx[k] = 0.f; Yy[k] = 0.f; Yz[k] = 0.f; }
     Y[0] = c[9];
-    if (p.deg >= 1) {
+    if (DEG >= 1) {
         Y[1] = -c[1] * y; Yy[1] = -c[1];
         Y[2] = c[0] * z;  Yz[2] = c[0];
         Y[3] = -c[1] * x; Yx[3] = -c[1];
     }
-    if (p.deg >= 2) {
+    if (DEG >= 2) {
         const float xx = x * x, yy = y * y, zz = z * z;
         Y[4] = 2.f * c[4] * x * y;       Yx[4] = 2.f * c[4] * y;  Yy[4] = 2.f * c[4] * x;
         Y[5] = -c[3] * y * z;            Yy[5] = -c[3] * z;       Yz[5] = -c[3] * y;
         Y[6] = c[2] * (3.f * zz - 1.f);  Yz[6] = 6.f * c[2] * z;
         Y[7] = -c[3] * x * z;            Yx[7] = -c[3] * z;       Yz[7] = -c[3] * x;
         Y[8] = c[4] * (xx - yy);         Yx[8] = 2.f * c[4] * x;  Yy[8] = -2.f * c[4] * y;
-        if (p.deg >= 3) {
+        if (DEG >= 3) {
             Y[9] = -c[8] * (3.f * xx * y - yy * y);
             Yx[9] = -6.f * c[8] * x * y;     Yy[9] = -c[8] * (3.f * xx - 3.f * yy);
             Y[10] = 2.f * c[7] * x * y * z;
@@ -212,16 +237,39 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
         }
     }
     const float* shi = p.sh + (size_t)i * K * 3;
+    float shv[3 * K];
+    if (K * 3 % 4 == 0) {   // 16-byte rows (degrees 1 and 3): vector loads
+#pragma unroll
+        for (int k = 0; k < 3 * K / 4; ++k) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(shi) + k);
+            shv[4 * k] = w4.x; shv[4 * k + 1] = w4.y; shv[4 * k + 2] = w4.z; shv[4 * k + 3] = w4.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) shv[k] = __ldg(shi + k);
+    }
     float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+    float dshv[3 * K];
+#pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
         float col = 0.5f;
-        for (int k = 0; k < K; ++k) col += shi[3 * k + ch] * Y[k];
+#pragma unroll
+        for (int k = 0; k < K; ++k) col += shv[3 * k + ch] * Y[k];
         const float gch = (col < 0.f) ? 0.f : gg[6 + ch];
+#pragma unroll
         for (int k = 0; k < K; ++k) {
-            dsh[3 * k + ch] = gch * Y[k];
-            const float s = shi[3 * k + ch] * gch;
-            gdx += s * Yx[k]; gdy += s * Yy[k]; gdz += s * Yz[k];
+            dshv[3 * k + ch] = gch * Y[k];
+            const float sv = shv[3 * k + ch] * gch;
+            gdx += sv * Yx[k]; gdy += sv * Yy[k]; gdz += sv * Yz[k];
         }
+    }
+    if (K * 3 % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < 3 * K / 4; ++k)
+            reinterpret_cast<float4*>(dsh)[k] = make_float4(dshv[4 * k], dshv[4 * k + 1], dshv[4 * k + 2], dshv[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) dsh[k] = dshv[k];
     }
     const float dd = gdx * x + gdy * y + gdz * z;
     float gmx = (gdx - x * dd) * vinv, gmy = (gdy - y * dd) * vinv, gmz = (gdz - z * dd) * vinv;
@@ -361,10 +409,18 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
         else VIS_LAUNCH_BWD(16);
     }
 #undef VIS_LAUNCH_BWD
-    if (p.n > 0)
-        preprocess_backward_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
-            p, g2, reinterpret_cast<const uint32_t*>(ws + L.off_touched), d_means, d_log_scales, d_quats,
-            d_logits, d_sh);
+    if (p.n > 0) {
+        const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
+        const int blocks = (int)L.prep_blocks;
+#define VIS_LAUNCH_PBWD(D)                                                                                \
+    preprocess_backward_kernel<D><<<blocks, kPrepThreads, 0, stream>>>(p, g2, touched, d_means, d_log_scales, \
+                                                                       d_quats, d_logits, d_sh)
+        if (p.deg == 0) VIS_LAUNCH_PBWD(0);
+        else if (p.deg == 1) VIS_LAUNCH_PBWD(1);
+        else if (p.deg == 2) VIS_LAUNCH_PBWD(2);
+        else VIS_LAUNCH_PBWD(3);
+#undef VIS_LAUNCH_PBWD
+    }
 }
 
 }  // namespace vis
