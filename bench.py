@@ -53,8 +53,8 @@ def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
         d = json.loads(p.read_text())
-        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
-    return dict(hbm_gbs=6400.0, source="fallback")
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=float(d.get("sm_max_mhz", 2032.0)))
+    return dict(hbm_gbs=6400.0, source="fallback", sm_max_mhz=2032.0)
 
 
 def _dist():
@@ -281,10 +281,43 @@ def run_ours(args):
         unit_note = "per key: value + gathered 48 B record; per pixel: rgb, alpha, T, last written"
     achieved = algo / (launch_ms * 1e-3) / 1e9
     traffic = _committed_traffic(dom, M, n)
-    roof = dict(kernel=names[STAGES.index(dom)], bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
-                frac=round(achieved / peaks["hbm_gbs"], 4), traffic=traffic,
+    roof = dict(kernel=names[STAGES.index(dom)], bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"],
+                unit="GB/s", frac=round(achieved / peaks["hbm_gbs"], 4), traffic=traffic,
                 peak_source=peaks["source"], algorithmic_bytes_per_launch=int(algo), launch_ms=round(launch_ms, 4),
                 bytes_model=unit_note)
+    clk_summary = clk.summary()
+    if dom == "composite":
+        # the compositor is bound by FP32 issue, not HBM: count its (pixel, splat) tests and hits
+        # on the first view (one extra render with statistics, outside the timed region)
+        st_opts = vis.make_opts(sort_mode=args.sort_mode, collect_stats=1)
+        vis.vis_render(sc.handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
+                       st_opts)
+        vis.vis_check(ws.buf)
+        ctrl = vis.read_ctrl(ws.buf)
+        flops = 11.0 * ctrl["pair_tests"] + 13.0 * ctrl["hits"]
+        mhz = clk_summary.get("sm_mhz") or _peaks().get("sm_max_mhz", 2032.0)
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_tf = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+        ach_tf = flops / (stage_ms["composite"] * 1e-3) / 1e12
+        roof = dict(kernel="composite", bound="alu", achieved=round(ach_tf, 2), peak=round(peak_tf, 1),
+                    unit="TFLOP/s", frac=round(ach_tf / peak_tf, 4), traffic=traffic,
+                    peak_source=f"FP32 FMA rate: {n_sm} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (sampled clock)",
+                    algorithmic_flops_per_launch=int(flops), pair_tests=ctrl["pair_tests"], hits=ctrl["hits"],
+                    launch_ms=round(stage_ms["composite"], 4),
+                    flop_model="11 flop per (pixel, splat) test (offset, two projections, squared norm), "
+                               "13 per composited pair (alpha, transmittance, 3 colour FMAs)",
+                    hbm_view=dict(achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                                  frac=round(achieved / peaks["hbm_gbs"], 4)))
+
+    # every HBM-bound stage against the copy peak (the spec bar is >= 60% for preprocess and sort)
+    hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
+                                     achieved_gbs=round(bytes_pre / (stage_ms["preprocess"] * 1e-3) / 1e9, 1))}
+    if args.sort_mode != 2 and passes > 0:
+        pk = 24.0 if args.sort_mode == 0 else 16.0
+        hbm_stages["sort_pass"] = dict(bytes=int(pk * M), ms=round(stage_ms["sort_passes"] / passes, 4),
+                                       achieved_gbs=round(pk * M / (stage_ms["sort_passes"] / passes * 1e-3) / 1e9, 1))
+    for v in hbm_stages.values():
+        v["frac"] = round(v["achieved_gbs"] / peaks["hbm_gbs"], 4)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts)
@@ -295,10 +328,10 @@ def run_ours(args):
                 config=dict(desc, sort_mode=args.sort_mode,
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-                clocks=clk.summary(), e2e=e2e,
+                clocks=clk_summary, e2e=e2e,
                 gpu_launches=int(args.steps * {0: 6 + passes, 1: 11 + kDP + passes, 2: 12 + kDP}[args.sort_mode]
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
-                roofline=roof,
+                roofline=roof, hbm_stages=hbm_stages,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
                 keys_per_frame=int(M), sort_passes=passes,
                 dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),

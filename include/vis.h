@@ -86,6 +86,8 @@ typedef struct {
  *              of 0.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
  *              thread (default 1); the image does not depend on it.
+ *  collect_stats  1: the compositor also counts the (pixel, splat) pairs it tests and
+ *              composites into vis_ctrl.pair_tests / hits (a few % slower); default 0.
  *  tile_extent which tiles a splat is listed in: 0 = every tile of the square of
  *              radius ceil(3 sqrt(lambda_max(S))) + 1 px around its centre; 1 (default) =
  *              every tile of the tight box around the region where a pixel can take the
@@ -102,6 +104,7 @@ typedef struct {
     int sort_mode;
     int pixels_per_thread;
     int tile_extent;
+    int collect_stats;
 } vis_render_opts;
 
 VIS_API void vis_default_opts(vis_render_opts* opts);
@@ -132,9 +135,14 @@ typedef struct {
 
 /* Device-written status block at workspace offset off_ctrl (= 0). */
 typedef struct {
-    uint32_t num_keys;       /* keys produced by the last render (may exceed capacity) */
+    uint32_t num_keys;       /* (tile, splat) pairs listed by the last render (may exceed capacity) */
     uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout */
-    uint32_t reserved[62];
+    uint32_t internal[16];   /* sort partition tickets */
+    uint32_t num_visible;    /* Gaussians that survived culling (sort_mode 1, 2) */
+    uint32_t pad0;
+    uint64_t pair_tests;     /* with collect_stats: (pixel, splat) pairs the compositor tested */
+    uint64_t hits;           /* with collect_stats: pairs it composited */
+    uint32_t reserved[40];
 } vis_ctrl;
 
 /* Borrow a scene (section 3.2: mean, scale, rotation quaternion, opacity, SH colour).

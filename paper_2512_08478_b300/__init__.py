@@ -39,7 +39,8 @@ class vis_camera(C.Structure):
 class vis_render_opts(C.Structure):
     _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
-                ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int), ("tile_extent", C.c_int)]
+                ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int), ("tile_extent", C.c_int),
+                ("collect_stats", C.c_int)]
 
 
 class vis_ws_layout(C.Structure):
@@ -190,6 +191,16 @@ def vis_check(ws, stream=None):
         err.num_keys = m.value
         raise err
     return m.value
+
+
+def read_ctrl(ws):
+    """The workspace's device-written status block as a dict (synchronises)."""
+    import numpy as np
+    raw = ws[:256].cpu().numpy()
+    u32 = raw.view(np.uint32)
+    u64 = raw[80:96].view(np.uint64)
+    return dict(num_keys=int(u32[0]), error=int(u32[1]), num_visible=int(u32[18]), pair_tests=int(u64[0]),
+                hits=int(u64[1]))
 
 
 def vis_render_backward(scene_handle, cam, W, H, bg, d_rgb, d_alpha, ws, grads, opts=None, stream=None):

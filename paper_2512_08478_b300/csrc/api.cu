@@ -272,6 +272,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->sort_mode = vis::kSortDepthFirst;
     o->pixels_per_thread = 1;
     o->tile_extent = 1;
+    o->collect_stats = 0;
 }
 
 const char* vis_last_error(void) { return g_err.c_str(); }
@@ -390,8 +391,8 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
         vis::launch_ranges(L, w, stream);
     }
     prof_mark(6, stream);
-    vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread, out_rgb,
-                          out_alpha, stream);
+    vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread,
+                          o.collect_stats != 0, out_rgb, out_alpha, stream);
     prof_mark(7, stream);
     if (g_prof.on && g_prof.count < kProfRing) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -38,12 +38,12 @@ __device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& 
     P.last = pos1;
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool STATS>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                  const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0, float bg1,
                  float bg2, float alpha_min, float alpha_max, float t_stop, float qcut,
-                 const Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
+                 Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
                  float* __restrict__ t_final, int32_t* __restrict__ last_out) {
     constexpr int NT = TILE * TILE / PPT;   // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
@@ -78,6 +78,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     }
     PixAcc P[PPT];
     float ly[PPT];
+    unsigned long long n_tests = 0, n_hits = 0;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         const int py = ty * TILE + row0 + r;
@@ -119,8 +120,10 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                 const int32_t pos1 = (int32_t)(base + k + 1);
                 if (PPT == 1) {
                     const PairEval e = eval_pair(lx, ly[0], a, b);
+                    if (STATS) ++n_tests;
                     if (e.q > b.z) continue;
                     composite_hit(P[0], e.q, b, s_c[k], alpha_max, t_stop, pos1);
+                    if (STATS && !P[0].done) ++n_hits;
                     if (P[0].done) break;
                 } else {
                     // the same arithmetic as eval_pair for each row, sharing the dx products
@@ -133,13 +136,26 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                     const float q1 = __fmaf_rn(p21, p21, __fmul_rn(p11, p11));
                     const bool h0 = !P[0].done && q0 <= b.z;
                     const bool h1 = !P[1].done && q1 <= b.z;
+                    if (STATS) n_tests += (P[0].done ? 0 : 1) + (P[1].done ? 0 : 1);
                     if (!(h0 || h1)) continue;
                     const float4 c = s_c[k];
                     if (h0) composite_hit(P[0], q0, b, c, alpha_max, t_stop, pos1);
                     if (h1) composite_hit(P[1], q1, b, c, alpha_max, t_stop, pos1);
+                    if (STATS) n_hits += (h0 && !P[0].done ? 1 : 0) + (h1 && !P[1].done ? 1 : 0);
                     if (P[0].done && P[1].done) break;
                 }
             }
+        }
+    }
+    if (STATS) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n_tests += __shfl_xor_sync(0xffffffffu, n_tests, o);
+            n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&ctrl->pair_tests, n_tests);
+            atomicAdd(&ctrl->hits, n_hits);
         }
     }
 #pragma unroll
@@ -158,27 +174,33 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
 }
 
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
-                      float alpha_max, float t_stop, int ppt, float* out_rgb, float* out_alpha,
+                      float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       cudaStream_t stream) {
     const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
     const uint32_t* vals = reinterpret_cast<const uint32_t*>(ws + L.off_vals[L.sorted_buffer]);
     const float4* rec = reinterpret_cast<const float4*>(ws + L.off_rec);
-    const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(ws + L.off_ctrl);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     float* tfin = reinterpret_cast<float*>(ws + L.off_tfinal);
     int32_t* last = reinterpret_cast<int32_t*>(ws + L.off_last);
     const int blocks = (int)L.ntiles;
     if (blocks <= 0) return;
     const float qcut = q_scale().qcut;
-#define VIS_LAUNCH_COMPOSITE(TS, PP)                                                                    \
-    composite_kernel<TS, PP><<<blocks, TS * TS / PP, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, \
-                                                                  bg0, bg1, bg2, alpha_min, alpha_max,   \
-                                                                  t_stop, qcut, ctrl, out_rgb, out_alpha, \
-                                                                  tfin, last)
+#define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST)                                                                    \
+    composite_kernel<TS, PP, ST><<<blocks, TS * TS / PP, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x,  \
+                                                                      bg0, bg1, bg2, alpha_min, alpha_max,    \
+                                                                      t_stop, qcut, ctrl, out_rgb, out_alpha, \
+                                                                      tfin, last)
+#define VIS_LAUNCH_COMPOSITE(TS, PP)                   \
+    do {                                               \
+        if (stats) VIS_LAUNCH_COMPOSITE_S(TS, PP, true);  \
+        else VIS_LAUNCH_COMPOSITE_S(TS, PP, false);       \
+    } while (0)
     const bool two = ppt == 2;
     if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE(8, 2); else VIS_LAUNCH_COMPOSITE(8, 1); }
     else if (L.tile == 32) { if (two) VIS_LAUNCH_COMPOSITE(32, 2); else VIS_LAUNCH_COMPOSITE(32, 1); }
     else { if (two) VIS_LAUNCH_COMPOSITE(16, 2); else VIS_LAUNCH_COMPOSITE(16, 1); }
 #undef VIS_LAUNCH_COMPOSITE
+#undef VIS_LAUNCH_COMPOSITE_S
 }
 
 }  // namespace vis

@@ -80,7 +80,10 @@ struct Ctrl {
     uint32_t error;
     uint32_t part_counter[2 * kMaxPasses];   // partition tickets of up to two sorts per render
     uint32_t num_visible;                    // Gaussians that survive culling (depth-first sort)
-    uint32_t reserved[45];
+    uint32_t pad0;
+    unsigned long long pair_tests;           // compositor statistics (collect_stats only)
+    unsigned long long hits;
+    uint32_t reserved[40];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
 
@@ -176,7 +179,7 @@ struct QScale {
 };
 QScale q_scale();
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
-                      float alpha_max, float t_stop, int ppt, float* out_rgb, float* out_alpha,
+                      float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       cudaStream_t stream);
 void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3],
                      float alpha_min, float alpha_max, float t_stop, const float* d_rgb,

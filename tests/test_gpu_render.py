@@ -202,3 +202,15 @@ def test_6m_dynamic_frame_sampled_tiles():
     means, logits = synth.dynamic_frame_inputs(sc, extras, k)
     frame = dict(sc, means=means, opacity_logits=logits)
     _sampled_tile_parity(frame, cams[k], n_tiles=32, seed=3)
+
+
+def test_compositor_statistics_do_not_change_the_image():
+    sc, cams = synth.workload_small()
+    a_rgb, a_alpha, _, _ = render_gpu(sc, cams[0])
+    b_rgb, b_alpha, _, ws = render_gpu(sc, cams[0], opts=vis.make_opts(collect_stats=1))
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
+    c = vis.read_ctrl(ws.buf)
+    ref, _ = oracle.render(sc, cams[0])
+    # every composited pair is one the oracle composites too (up to flagged pixels)
+    assert 0 < c["hits"] <= c["pair_tests"]
+    assert abs(c["hits"] - int(ref["n_contrib"].sum())) <= max(10, 1e-4 * c["hits"])
