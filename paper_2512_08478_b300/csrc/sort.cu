@@ -94,6 +94,14 @@ struct SortSmem {
 };
 
 // Three CTAs of 256 threads per SM: at most 85 registers per thread.
+//
+// Per partition: load (warp-striped), digit counts per warp with shared atomics
+// ("early counts"), publish the partition's counts and resolve its global digit
+// offsets by look-back *before* ranking, then rank stably (per warp, one
+// __match_any_sync per round; the group's leader takes the group's slots from the
+// warp's running digit counter with a shared atomic, which keeps rounds in program
+// order), reorder in shared memory and write digit runs. All indexing inside the
+// partition is 32-bit and relative to its base.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 3)
 sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
@@ -117,37 +125,28 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const uint32_t part = S.part;
     const int64_t base = (int64_t)part * PART;
     if (base >= m) return;
+    const int n_in = (m - base) < (int64_t)PART ? (int)(m - base) : PART;
+    const K* kin = keys_in + base;
+    const uint32_t* vin = vals_in + base;
 
-    // ---- load (warp-striped: warp w owns keys [w*512, (w+1)*512) of the partition) ----
+    // ---- load (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the partition) ----
+    const int wofs = warp * (32 * KPT) + lane;
     K key[KPT];
     uint32_t val[KPT];
-    const int64_t wbase = base + (int64_t)warp * (32 * KPT);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-        const int64_t idx = wbase + k * 32 + lane;
-        if (idx < m) { key[k] = keys_in[idx]; val[k] = vals_in[idx]; }
+        const int idx = wofs + k * 32;
+        if (idx < n_in) { key[k] = kin[idx]; val[k] = vin[idx]; }
         else { key[k] = 0; val[k] = 0; }
     }
-
-    // ---- stable per-warp ranking ----
-    uint32_t rank[KPT];
     uint32_t* wh = S.whist[warp];
-    const uint32_t lt = (1u << lane) - 1u;
+    // ---- early counts: per-warp digit histogram ----
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-        const bool valid = (wbase + k * 32 + lane) < m;
-        const uint32_t d = (uint32_t)(key[k] >> shift) & (kRadix - 1);
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : (kRadix + lane));
-        uint32_t before = 0;
-        if (valid) before = wh[d];
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wh[d] = before + __popc(peers);
-        __syncwarp();
-        rank[k] = before + __popc(peers & lt);
-    }
+    for (int k = 0; k < KPT; ++k)
+        if (wofs + k * 32 < n_in) atomicAdd(&wh[(uint32_t)(key[k] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
 
-    // ---- per-digit totals and warp offsets; publish the partition aggregate ----
+    // ---- per-digit totals, warp offsets; publish the aggregate; look-back ----
     const uint32_t d = tid;   // one digit per thread (256 threads, 256 digits)
     uint32_t cnt = 0;
 #pragma unroll
@@ -160,11 +159,9 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     st_relaxed(&lb[d], (part == 0 ? kFlagInc : kFlagAgg) | cnt);
     const uint32_t local_start = block_exclusive_scan_256(cnt, S.scan_tmp, nullptr);
     const uint32_t gstart = block_exclusive_scan_256(hist_pass[d], S.scan_tmp, nullptr);
-
-    // ---- decoupled look-back, a window of kLookbackWindow predecessors per round ----
-    // All loads of a window are issued together (one L2 round trip), then consumed
-    // in order until the first inclusive prefix; only a not-yet-published word is
-    // re-polled (bounded).
+    // decoupled look-back, a window of kLookbackWindow predecessors per round: all loads
+    // of a window are issued together, then consumed in order until the first
+    // inclusive prefix; only a not-yet-published word is re-polled (bounded)
     uint32_t prefix = 0;
     if (part > 0) {
         int64_t q = (int64_t)part - 1;
@@ -200,28 +197,40 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     S.digit_off[d] = gstart + prefix - local_start;
     __syncthreads();
 
-    // ---- reorder by digit in shared memory ----
+    // ---- stable ranking into partition-local positions, and reorder by digit ----
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t pos[KPT];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-        if ((wbase + k * 32 + lane) < m) {
-            const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
-            const uint32_t pos = S.local_start[dk] + wh[dk] + rank[k];
-            S.keys[pos] = key[k];
-            S.vals[pos] = val[k];
-        }
+        const bool valid = wofs + k * 32 < n_in;
+        const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dk : (kRadix + lane));
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) old = atomicAdd(&wh[dk], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        pos[k] = S.local_start[dk] + old + __popc(peers & lt);
     }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+        if (wofs + k * 32 < n_in) S.keys[pos[k]] = key[k];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+        if (wofs + k * 32 < n_in) S.vals[pos[k]] = val[k];
     __syncthreads();
     if (S.bad) return;
 
-    // ---- write out in digit runs ----
-    const int n_in = (int)((m - base) < PART ? (m - base) : PART);
-    for (int i = tid; i < n_in; i += kSortThreads) {
-        const K kk = S.keys[i];
-        const uint32_t dk = (uint32_t)(kk >> shift) & (kRadix - 1);
-        const uint32_t dest = S.digit_off[dk] + (uint32_t)i;   // modular: digit_off may wrap
-        if ((int64_t)dest < m) {
-            keys_out[dest] = kk;
-            vals_out[dest] = S.vals[i];
+    // ---- write out in digit runs (destinations are modular: digit_off may wrap) ----
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+        const int i = tid + k * kSortThreads;
+        if (i < n_in) {
+            const K kk = S.keys[i];
+            const uint32_t dest = S.digit_off[(uint32_t)(kk >> shift) & (kRadix - 1)] + (uint32_t)i;
+            if (dest < (uint32_t)m) {
+                keys_out[dest] = kk;
+                vals_out[dest] = S.vals[i];
+            }
         }
     }
 }
