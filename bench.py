@@ -252,19 +252,32 @@ def run_ours(args):
     passes = npass.value
 
     # keys per frame averaged over the views used
-    mlist = []
+    # and the preprocess traffic each view requires: every Gaussian is read for the depth and
+    # cull test, only those in front (z > near, opacity >= alpha_min) for the covariance, and
+    # only the survivors (tiles touched > 0) for their SH coefficients and splat record
+    mlist, nvis, nok = [], [], []
+    lay = ws.layout()
+    opac = torch.sigmoid(sc.tensors["opacity_logits"].reshape(-1))
+    a_min = float(np.float32(vis.make_opts().alpha_min))
     for i in range(min(args.steps, len(cam_objs))):
-        c = cam_objs[(view0 + i) % len(cam_objs)]
-        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
+        k = (view0 + i) % len(cam_objs)
+        vis.vis_render(sc.handle, cam_objs[k], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         mlist.append(vis.vis_check(ws.buf))
+        touched = ws.buf[lay.off_touched: lay.off_touched + 4 * n].view(torch.int32)
+        zview = ws.buf[lay.off_depth: lay.off_depth + 4 * n].view(torch.float32)
+        nvis.append(int((touched != 0).sum()))
+        nok.append(int(((zview > cams[k].near) & (opac >= a_min)).sum()))
     M = float(np.mean(mlist))
+    n_vis, n_ok = float(np.mean(nvis)), float(np.mean(nok))
 
     # ---- roofline of the dominant stage ----
     peaks = _peaks()
     cands = ("preprocess", "sort_passes", "composite") if args.sort_mode != 2 else ("preprocess", "composite")
     dom = max(cands, key=lambda s: stage_ms[s])
     sh_k = (desc["sh_degree"] + 1) ** 2
-    bytes_pre = n * (12 + 12 + 16 + 4 + 12 * sh_k) + n * (48 + 4 + 8 + 4)
+    # means + logit read, depth + rect + count written: 32 B each; quaternion + log-scales: 28 B
+    # for the Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
+    bytes_pre = n * 32 + n_ok * 28 + n_vis * (12 * sh_k + 48)
     if dom == "sort_passes":
         launch_ms = stage_ms["sort_passes"] / passes
         per_key = 24.0 if args.sort_mode == 0 else 16.0
@@ -274,7 +287,8 @@ def run_ours(args):
     elif dom == "preprocess":
         launch_ms = stage_ms["preprocess"]
         algo = float(bytes_pre)
-        unit_note = "attributes read + splat record, depth, rect, count written per Gaussian"
+        unit_note = ("32 B per Gaussian (means, logit, depth, rect, count) + 28 B per Gaussian in front "
+                     "(quaternion, log-scales) + SH and 48 B record per surviving splat")
     else:
         launch_ms = stage_ms[dom]
         algo = M * (4 + 48) + W * H * (16 + 8)
@@ -333,7 +347,7 @@ def run_ours(args):
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
                 roofline=roof, hbm_stages=hbm_stages,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
-                keys_per_frame=int(M), sort_passes=passes,
+                keys_per_frame=int(M), visible_per_frame=int(n_vis), sort_passes=passes,
                 dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),
                 sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]
                                            + (stage_ms["duplicate"] if args.sort_mode == 2 else 0.0)) * 1e3, 1),
