@@ -47,6 +47,11 @@ STAGES_DF = ["clear", "preprocess", "depth_sort_and_emit", "tile_sort_histogram"
 # sort_mode 2 (depth sort + counting binning): stage 3 = binning counts, scans and ranges,
 # stage 4 = binning emission (each Gaussian index written to its slot)
 STAGES_BIN = ["clear", "preprocess", "depth_sort", "bin_count_scan", "bin_emit", "ranges", "composite"]
+# sort_mode 1 with the counts-first tile sort (16-bit tile keys): stage 2 = compaction, depth sort
+# and emission in depth order; stage 3 = per-tile counts (histograms, ranges); stage 4 = the tile
+# passes; no ranges stage
+STAGES_FUSED = ["clear", "preprocess", "depth_sort_and_emit", "tile_counts", "tile_sort_passes", "ranges",
+                "composite"]
 
 
 def _peaks():
@@ -248,7 +253,8 @@ def run_ours(args):
     value = t_ms / frames_total
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
     update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
-    names = {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode]
+    fused = ws.layout().key_bytes == 2
+    names = STAGES_FUSED if fused else {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode]
     passes = npass.value
 
     # keys per frame averaged over the views used
@@ -278,7 +284,17 @@ def run_ours(args):
     # means + logit read, depth + rect + count written: 32 B each; quaternion + log-scales: 28 B
     # for the Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
     bytes_pre = n * 32 + n_ok * 28 + n_vis * (12 * sh_k + 48)
-    if dom == "sort_passes":
+    # bytes the tile sort must move: per digit pass key + value read and written; with the fused
+    # binning the first pass reads 16 B per surviving splat (first copy, index, rect) and writes a
+    # 2 B key + 4 B value per copy, the last reads those and writes the 4 B value
+    # 16-bit keys: every pass reads 2 + 4 B per copy and writes 2 + 4 B, the last only the 4 B value
+    tile_bytes = (M * (12 * passes - 2)) if fused else M * (24.0 if args.sort_mode == 0 else 16.0) * passes
+    if dom == "sort_passes" and fused:
+        launch_ms = stage_ms["sort_passes"] / passes
+        algo = tile_bytes / passes
+        unit_note = ("mean over the tile passes: 2 B key + 4 B value read and written per copy, "
+                     "the last pass writes the value only")
+    elif dom == "sort_passes":
         launch_ms = stage_ms["sort_passes"] / passes
         per_key = 24.0 if args.sort_mode == 0 else 16.0
         algo = per_key * M
@@ -327,9 +343,10 @@ def run_ours(args):
     hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
                                      achieved_gbs=round(bytes_pre / (stage_ms["preprocess"] * 1e-3) / 1e9, 1))}
     if args.sort_mode != 2 and passes > 0:
-        pk = 24.0 if args.sort_mode == 0 else 16.0
-        hbm_stages["sort_pass"] = dict(bytes=int(pk * M), ms=round(stage_ms["sort_passes"] / passes, 4),
-                                       achieved_gbs=round(pk * M / (stage_ms["sort_passes"] / passes * 1e-3) / 1e9, 1))
+        key = "tile_sort_pass"
+        b_st = tile_bytes / passes
+        ms_st = stage_ms["sort_passes"] / passes
+        hbm_stages[key] = dict(bytes=int(b_st), ms=round(ms_st, 4), achieved_gbs=round(b_st / (ms_st * 1e-3) / 1e9, 1))
     for v in hbm_stages.values():
         v["frac"] = round(v["achieved_gbs"] / peaks["hbm_gbs"], 4)
 

@@ -79,7 +79,10 @@ typedef struct {
  *              0 = one LSD sort of 64-bit (tile << 32 | depth) keys;
  *              1 = depth first (default): the surviving splats are sorted once by
  *                  32-bit depth (as in the paper), their tile copies are emitted in that
- *                  order and stably sorted by tile id alone;
+ *                  order and stably sorted by tile id alone. On grids of at most 51200
+ *                  tiles the per-tile counts (hence ranges and digit histograms) come
+ *                  first, the tile keys are 16-bit and the last pass writes only the
+ *                  Gaussian indices;
  *              2 = depth first, then a stable counting binning into tiles (no tile keys;
  *                  up to 29056 tiles, beyond that mode 1 is used).
  *              All give the same order bit for bit; 1 moves about a quarter of the bytes
@@ -123,13 +126,16 @@ typedef struct {
     size_t off_depth;        /* float[n] view depth (the sort key's low word) */
     size_t off_rect;         /* uint2[n] tile rect: x0 | x1<<16, y0 | y1<<16 (upper bounds exclusive) */
     size_t off_touched;      /* uint32[n] tiles touched (0 if culled) */
-    size_t off_keys[2];      /* key_bytes x cap: sort keys (see key_bytes) */
+    size_t off_keys[2];      /* key_bytes x cap: sort keys (see key_bytes); with key_bytes 2 the
+                                sorted keys are not stored (the tile of sorted position j is
+                                the tile whose range holds j) */
     size_t off_vals[2];      /* uint32[cap] Gaussian index */
     size_t off_ranges;       /* uint2[tiles] [start, end) into the sorted keys */
     size_t off_tfinal;       /* float[H*W] final transmittance */
     size_t off_last;         /* int32[H*W] 1 + position, in the sorted key list, of the last composited splat (0 if none) */
     size_t off_g2;           /* float[n][9] screen-space gradients (backward scratch) */
-    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1) */
+    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1
+                                beyond 51200 tiles); 2: 16-bit tile id (sort_mode 1); 0: none (2) */
     int sort_mode;
 } vis_ws_layout;
 

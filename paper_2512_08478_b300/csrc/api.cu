@@ -200,6 +200,15 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.key_bytes = bin ? 0 : (df ? 4 : 8);
     L.sort_parts = bin ? 0 : (df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap));
     L.sorted_buffer = L.passes & 1;
+    // depth-first mode: counts-first tile sort of 16-bit tile keys when the per-tile counters
+    // fit in shared memory; it runs at least one pass (the last writes values only)
+    L.tile_fused = mode == kSortDepthFirst && L.ntiles <= kTileFusedMaxTiles;
+    if (L.tile_fused) {
+        L.passes = L.tile_bits > kRadixBits ? 2 : 1;
+        L.key_bytes = 2;
+        L.sort_parts = sort_parts<uint16_t>(cap);
+        L.sorted_buffer = L.passes & 1;
+    }
     if (bin) {
         L.bin_chunk = bin_chunk(n);
         L.bin_chunks = (n + L.bin_chunk - 1) / L.bin_chunk;
@@ -213,6 +222,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.lookback_words_depth = df ? (size_t)kDepthPasses * sort_parts<uint32_t>(n) * kRadix : 0;
     L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * kRadix));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
+    if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
     L.zero_end = off;
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
     L.off_depth = take(sizeof(float) * (size_t)n);
@@ -226,6 +236,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
         for (int b = 0; b < 2; ++b) L.off_dkeys[b] = take(sizeof(uint32_t) * (size_t)n);
         for (int b = 0; b < 2; ++b) L.off_dvals[b] = take(sizeof(uint32_t) * (size_t)n);
     }
+
     if (bin) {
         L.off_counts = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
         L.off_chunk_base = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
@@ -382,7 +393,7 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     } else if (L.mode == vis::kSortDepthFirst) {
         vis::launch_depth_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
         prof_mark(5, stream);
-        vis::launch_ranges32(L, w, stream);
+        if (!L.tile_fused) vis::launch_ranges32(L, w, stream);   // the counts-first tile sort wrote them
     } else {
         vis::launch_scan_and_duplicate(L, w, scene->n, stream);
         prof_mark(3, stream);

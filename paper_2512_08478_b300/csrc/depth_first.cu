@@ -83,10 +83,12 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
     }
 }
 
+// KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles
+template <typename KT>
 __global__ void __launch_bounds__(kPrepThreads)
 emit_tiles(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
            const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
-           const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+           const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     if (ctrl->error & kErrCapacity) return;
     __shared__ uint32_t s_start[kPrepThreads];
     __shared__ uint32_t s_g[kPrepThreads];
@@ -117,7 +119,7 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touc
         const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu;
         const uint32_t w = x1 - x0;
         const uint32_t k = q - s_start[g0 + lo];
-        keys[warp_base + q] = (y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w);
+        keys[warp_base + q] = (KT)((y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w));
         vals[warp_base + q] = gi;
     }
 }
@@ -175,11 +177,24 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
     depth_touch_sums<<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, &ctrl->num_visible, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
+    if (L.tile_fused) {
+        // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
+        // the passes (tile_sort.cu)
+        emit_tiles<uint16_t><<<blocks_n, kPrepThreads, 0, stream>>>(
+            dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
+            reinterpret_cast<uint16_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
+        if (mark) mark(mark_index, stream);
+        launch_tile_counts(L, ws, stream);
+        if (mark) mark(mark_index + 1, stream);
+        launch_tile_passes(L, ws, stream);
+        (void)hist; (void)lb;
+        return;
+    }
     uint32_t* k0 = reinterpret_cast<uint32_t*>(ws + L.off_keys[0]);
     uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    emit_tiles<<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect),
+    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect),
                                                       &ctrl->num_visible, boff2, L.tiles_x, ctrl, k0, v0);
     if (mark) mark(mark_index, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer

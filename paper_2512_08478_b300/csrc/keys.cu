@@ -17,48 +17,41 @@
 namespace vis {
 
 // Exclusive scan of per-block sums; the total goes to *total, and if `error` is given
-// a total above `cap` sets kErrCapacity there.
+// a total above `cap` sets kErrCapacity there. One CTA of 1024 threads; thread t owns the
+// contiguous run [t*per, (t+1)*per) of the sums: it adds its run (loads unrolled so that
+// several are in flight), the 1024 run totals are scanned, then it writes its run's offsets.
 __global__ void __launch_bounds__(1024)
 scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
                 uint32_t* total_out, uint32_t* error, int64_t cap) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ unsigned long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
+    __shared__ unsigned long long warp_tot[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t base = 0; base < nblocks; base += 1024) {
-        const int64_t b = base + threadIdx.x;
-        uint32_t v = (b < nblocks) ? bsum[b] : 0u;
-        uint32_t incl = v;
+    const int64_t per = (nblocks + 1023) / 1024;
+    const int64_t b0 = (int64_t)threadIdx.x * per;
+    const int64_t b1 = min(nblocks, b0 + per);
+    unsigned long long run = 0;
+#pragma unroll 8
+    for (int64_t b = b0; b < b1; ++b) run += bsum[b];
+    unsigned long long incl = run;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t w = warp_tot[lane];
-            uint32_t wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += t;
-            }
-            warp_tot[lane] = wi - w;   // exclusive warp offsets
-        }
-        __syncthreads();
-        const unsigned long long c = carry;
-        const unsigned long long excl = c + warp_tot[warp] + (incl - v);
-        if (b < nblocks) boff[b] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned long long excl = incl - run, all = 0;
+    for (int w = 0; w < 32; ++w) {
+        const unsigned long long x = warp_tot[w];
+        if (w < warp) excl += x;
+        all += x;
+    }
+    for (int64_t b = b0; b < b1; ++b) {
+        boff[b] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
+        excl += bsum[b];
     }
     if (threadIdx.x == 0) {
-        const unsigned long long total = carry;
-        *total_out = (uint32_t)min(total, (unsigned long long)0xffffffffu);
-        if (error && total > (unsigned long long)cap) atomicOr(error, kErrCapacity);
+        *total_out = (uint32_t)min(all, (unsigned long long)0xffffffffu);
+        if (error && all > (unsigned long long)cap) atomicOr(error, kErrCapacity);
     }
 }
 

@@ -17,14 +17,9 @@
 //  - Spin waits on a predecessor are bounded (kSpinLimit polls); on expiry the
 //    CTA records kErrTimeout, publishes anyway so nobody waits on it, and writes
 //    nothing out of range (every destination is checked against the key count).
-#include "vis_internal.cuh"
+#include "onesweep.cuh"
 
 namespace vis {
-
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kLookbackWindow = 16;   // predecessors read per look-back round
 
 template <typename K>
 __global__ void __launch_bounds__(256)
@@ -46,40 +41,6 @@ sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// exclusive scan of one value per thread over a 256-thread block; returns total in *tot
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* s_warp, uint32_t* tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    uint32_t woff = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t x = s_warp[w];
-        if (w < warp) woff += x;
-        all += x;
-    }
-    __syncthreads();
-    if (tot) *tot = all;
-    return woff + incl - v;
-}
-
-static_assert(kSortThreads == kRadix, "one digit per thread");
-
 template <typename K>
 struct SortSmem {
     static constexpr int KPT = SortKPT<K>::value;
@@ -97,11 +58,9 @@ struct SortSmem {
 //
 // Per partition: load (warp-striped), digit counts per warp with shared atomics
 // ("early counts"), publish the partition's counts and resolve its global digit
-// offsets by look-back *before* ranking, then rank stably (per warp, one
-// __match_any_sync per round; the group's leader takes the group's slots from the
-// warp's running digit counter with a shared atomic, which keeps rounds in program
-// order), reorder in shared memory and write digit runs. All indexing inside the
-// partition is 32-bit and relative to its base.
+// offsets by look-back *before* ranking, then rank stably, reorder in shared memory
+// and write digit runs. All indexing inside the partition is 32-bit and relative to
+// its base. keys_out may be null (last pass of a sort whose keys are not needed).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 3)
 sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
@@ -148,69 +107,27 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 
     // ---- per-digit totals, warp offsets; publish the aggregate; look-back ----
     const uint32_t d = tid;   // one digit per thread (256 threads, 256 digits)
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-        const uint32_t c = S.whist[w][d];
-        S.whist[w][d] = cnt;
-        cnt += c;
-    }
-    uint32_t* lb = lookback + (size_t)part * kRadix;
-    st_relaxed(&lb[d], (part == 0 ? kFlagInc : kFlagAgg) | cnt);
+    const uint32_t cnt = warp_offsets_of_digit(S.whist, d);
+    publish_aggregate(lookback, part, d, cnt);
     const uint32_t local_start = block_exclusive_scan_256(cnt, S.scan_tmp, nullptr);
     const uint32_t gstart = block_exclusive_scan_256(hist_pass[d], S.scan_tmp, nullptr);
-    // decoupled look-back, a window of kLookbackWindow predecessors per round: all loads
-    // of a window are issued together, then consumed in order until the first
-    // inclusive prefix; only a not-yet-published word is re-polled (bounded)
-    uint32_t prefix = 0;
-    if (part > 0) {
-        int64_t q = (int64_t)part - 1;
-        bool timed_out = false, found = false;
-        while (!found && !timed_out && q >= 0) {
-            uint32_t v[kLookbackWindow];
-#pragma unroll
-            for (int i = 0; i < kLookbackWindow; ++i)
-                v[i] = (q - i >= 0) ? ld_relaxed(&lookback[(size_t)(q - i) * kRadix + d]) : kFlagInc;
-#pragma unroll
-            for (int i = 0; i < kLookbackWindow; ++i) {
-                if (found || timed_out || q - i < 0) break;
-                uint32_t w = v[i];
-                uint32_t spins = 0;
-                while ((w & ~kCountMask) == 0) {
-                    if (++spins > kSpinLimit) { timed_out = true; break; }
-                    if (spins > 8) __nanosleep(32);
-                    w = ld_relaxed(&lookback[(size_t)(q - i) * kRadix + d]);
-                }
-                if (timed_out) break;
-                prefix += w & kCountMask;
-                if ((w & ~kCountMask) == kFlagInc) found = true;
-            }
-            q -= kLookbackWindow;
-        }
-        st_relaxed(&lb[d], kFlagInc | ((prefix + cnt) & kCountMask));
-        if (timed_out) {
-            atomicOr(error, kErrTimeout);
-            S.bad = 1;
-        }
+    bool timed_out = false;
+    const uint32_t prefix = lookback_prefix(lookback, part, d, cnt, &timed_out);
+    if (timed_out) {
+        atomicOr(error, kErrTimeout);
+        S.bad = 1;
     }
     S.local_start[d] = local_start;
     S.digit_off[d] = gstart + prefix - local_start;
     __syncthreads();
 
     // ---- stable ranking into partition-local positions, and reorder by digit ----
-    const uint32_t lt = (1u << lane) - 1u;
     uint32_t pos[KPT];
+    uint32_t vmask = 0;
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-        const bool valid = wofs + k * 32 < n_in;
-        const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
-        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? dk : (kRadix + lane));
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (valid && lane == leader) old = atomicAdd(&wh[dk], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
-        pos[k] = S.local_start[dk] + old + __popc(peers & lt);
-    }
+    for (int k = 0; k < KPT; ++k)
+        if (wofs + k * 32 < n_in) vmask |= 1u << k;
+    rank_keys<KPT, K>(key, shift, vmask, wh, S.local_start, pos);
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
         if (wofs + k * 32 < n_in) S.keys[pos[k]] = key[k];
@@ -228,7 +145,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             const K kk = S.keys[i];
             const uint32_t dest = S.digit_off[(uint32_t)(kk >> shift) & (kRadix - 1)] + (uint32_t)i;
             if (dest < (uint32_t)m) {
-                keys_out[dest] = kk;
+                if (keys_out) keys_out[dest] = kk;
                 vals_out[dest] = S.vals[i];
             }
         }
@@ -278,6 +195,28 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
         src_v = dv;
     }
 }
+
+// One pass of sort_pass over m <= cap keys (read from *num_keys_dev) with digit
+// (key >> shift) & 255 and the digit histogram hist_pass; keys_out may be null.
+template <typename K>
+void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
+                      const uint32_t* num_keys_dev, int shift, const uint32_t* hist_pass, uint32_t* lookback,
+                      uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
+    if (cap <= 0) return;
+    static bool attr_done = false;
+    const size_t smem = sizeof(SortSmem<K>);
+    if (!attr_done) {
+        cudaFuncSetAttribute(sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done = true;
+    }
+    sort_pass<K><<<(int)sort_parts<K>(cap), kSortThreads, smem, stream>>>(keys_in, vals_in, keys_out, vals_out,
+                                                                           num_keys_dev, cap, shift, hist_pass,
+                                                                           lookback, part_counter, error);
+}
+
+template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint16_t*, uint32_t*, int64_t,
+                                         const uint32_t*, int, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                         cudaStream_t);
 
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,

@@ -1,0 +1,150 @@
+// Counts-first tile sort of the depth-sorted splats' copies (sort_mode 1 on tile grids of
+// at most kTileFusedMaxTiles tiles): the stable sort by tile id that turns the depth order
+// of Algorithm 1's radix sort (section 3.4) into every tile's front-to-back list.
+//
+//   tile_count_kernel  per-tile copy counts from the splats' tile rectangles: every
+//                      rectangle adds +1/-1/-1/+1 at its four corners of a 2D
+//                      difference array (shared memory per CTA, flushed with one
+//                      global atomic per non-zero entry);
+//   tile_scan_kernel   2D prefix sums -> counts; the digit histograms of both radix
+//                      passes and every tile's [start, end) range follow from the
+//                      counts alone (exclusive scan over the tiles in raster order),
+//                      so no pass over the keys builds histograms or finds ranges;
+//   passes             sort_pass<uint16_t> over the 16-bit tile ids emitted in depth
+//                      order (emit_tiles), low byte then high byte; the last pass
+//                      writes only the Gaussian indices.
+// The result is the (tile, depth, index) order of the 64-bit key sort, bit for bit.
+#include "onesweep.cuh"
+
+namespace vis {
+
+// ---- per-tile counts ----
+__global__ void __launch_bounds__(1024)
+tile_count_kernel(const uint2* __restrict__ rect, int64_t n, int tiles_x, int tiles_y, int* __restrict__ gdiff) {
+    extern __shared__ int diff[];
+    const int nt = tiles_x * tiles_y;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) diff[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint2 r = rect[i];
+        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
+        if (x1 <= x0 || y1 <= y0) continue;
+        // corners at x1 == tiles_x or y1 == tiles_y only affect tiles outside the grid
+        atomicAdd(&diff[y0 * tiles_x + x0], 1);
+        if (x1 < tiles_x) atomicAdd(&diff[y0 * tiles_x + x1], -1);
+        if (y1 < tiles_y) {
+            atomicAdd(&diff[y1 * tiles_x + x0], -1);
+            if (x1 < tiles_x) atomicAdd(&diff[y1 * tiles_x + x1], 1);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x)
+        if (diff[i]) atomicAdd(&gdiff[i], diff[i]);
+}
+
+// One CTA of 1024 threads. hist: [2][256] digit histograms (low byte, high byte of the
+// tile id); ranges: [start, end) per tile, (0, 0) for an empty tile.
+__global__ void __launch_bounds__(1024)
+tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32_t* __restrict__ hist,
+                 uint2* __restrict__ ranges) {
+    extern __shared__ int P[];
+    __shared__ uint32_t s_hist[2 * kRadix];
+    __shared__ uint32_t s_warp[32];
+    const int nt = tiles_x * tiles_y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < nt; i += 1024) P[i] = gdiff[i];
+    for (int i = tid; i < 2 * kRadix; i += 1024) s_hist[i] = 0;
+    __syncthreads();
+    for (int y = tid; y < tiles_y; y += 1024) {   // prefix along each row
+        int run = 0;
+        for (int x = 0; x < tiles_x; ++x) { run += P[y * tiles_x + x]; P[y * tiles_x + x] = run; }
+    }
+    __syncthreads();
+    for (int x = tid; x < tiles_x; x += 1024) {   // then along each column: counts
+        int run = 0;
+        for (int y = 0; y < tiles_y; ++y) { run += P[y * tiles_x + x]; P[y * tiles_x + x] = run; }
+    }
+    __syncthreads();
+    // exclusive scan of the counts in raster order: thread tid owns tiles [tid*per, (tid+1)*per)
+    const int per = (nt + 1023) / 1024;
+    const int t0 = tid * per, t1 = min(nt, t0 + per);
+    uint32_t local = 0;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = (uint32_t)P[t];
+        local += c;
+        if (c) {
+            atomicAdd(&s_hist[t & (kRadix - 1)], c);
+            atomicAdd(&s_hist[kRadix + ((t >> kRadixBits) & (kRadix - 1))], c);
+        }
+    }
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += s_warp[w];
+    uint32_t start = woff + incl - local;
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t c = (uint32_t)P[t];
+        ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
+        start += c;
+    }
+    for (int i = tid; i < 2 * kRadix; i += 1024) hist[i] = s_hist[i];
+}
+
+static int sm_count_ts() {
+    int dev = 0, s = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        s = 148;
+    return s;
+}
+
+void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        // the largest per-tile counter array of the fused path (tile_scan_kernel adds 2.2 KB of
+        // static shared memory, still within the 227 KB a CTA may use)
+        const int most = (int)(sizeof(int) * kTileFusedMaxTiles);
+        cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        attr_done = true;
+    }
+    const size_t smem = sizeof(int) * (size_t)L.ntiles;
+    int* gdiff = reinterpret_cast<int*>(ws + L.off_tdiff);
+    const int64_t want = (L.n + 16383) / 16384;
+    const int64_t lim = sm_count_ts();
+    const int grid = (int)(want < 1 ? 1 : (want < lim ? want : lim));
+    tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint2*>(ws + L.off_rect), L.n, L.tiles_x,
+                                                    L.tiles_y, gdiff);
+    tile_scan_kernel<<<1, 1024, smem, stream>>>(gdiff, L.tiles_x, L.tiles_y,
+                                                reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,
+                                                reinterpret_cast<uint2*>(ws + L.off_ranges));
+}
+
+void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix;
+    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback) + L.lookback_words_depth;
+    uint16_t* k0 = reinterpret_cast<uint16_t*>(ws + L.off_keys[0]);
+    uint16_t* k1 = reinterpret_cast<uint16_t*>(ws + L.off_keys[1]);
+    uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
+    uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
+    const size_t words = (size_t)L.sort_parts * kRadix;
+    // emitted copies in buffer 0; one pass -> values in 1, two passes -> keys + values in 1, then values in 0
+    if (L.passes == 1) {
+        launch_sort_pass<uint16_t>(k0, v0, nullptr, v1, L.cap, &ctrl->num_keys, 0, hist, lb,
+                                   &ctrl->part_counter[kMaxPasses], &ctrl->error, stream);
+        return;
+    }
+    launch_sort_pass<uint16_t>(k0, v0, k1, v1, L.cap, &ctrl->num_keys, 0, hist, lb, &ctrl->part_counter[kMaxPasses],
+                               &ctrl->error, stream);
+    launch_sort_pass<uint16_t>(k1, v1, nullptr, v0, L.cap, &ctrl->num_keys, kRadixBits, hist + kRadix, lb + words,
+                               &ctrl->part_counter[kMaxPasses + 1], &ctrl->error, stream);
+}
+
+}  // namespace vis

@@ -17,6 +17,10 @@ constexpr int kSortThreads = 256;        // threads per radix-sort CTA
 template <typename K> struct SortKPT;
 template <> struct SortKPT<uint64_t> { static constexpr int value = 8; };
 template <> struct SortKPT<uint32_t> { static constexpr int value = 16; };
+template <> struct SortKPT<uint16_t> { static constexpr int value = 16; };
+// counts-first tile sort of sort_mode 1 (tile_sort.cu): used when the tile grid has at most
+// kTileFusedMaxTiles tiles (its per-tile counters live in shared memory)
+constexpr int kTileFusedMaxTiles = 51200;
 template <typename K> constexpr int64_t sort_partition() { return (int64_t)kSortThreads * SortKPT<K>::value; }
 template <typename K> constexpr int64_t sort_parts(int64_t cap) {
     return (cap + sort_partition<K>() - 1) / sort_partition<K>();
@@ -62,6 +66,9 @@ struct Layout {
     size_t off_dkeys[2] = {0, 0}, off_dvals[2] = {0, 0}, off_bsum2 = 0, off_boff2 = 0;
     size_t lookback_words_depth = 0;
     int key_bytes = 8;
+    // depth-first mode with the counts-first tile sort of 16-bit keys (tile_sort.cu)
+    bool tile_fused = false;
+    size_t off_tdiff = 0;
     // depth-bin mode only
     int64_t bin_chunk = 0, bin_chunks = 0;
     size_t off_counts = 0, off_chunk_base = 0, off_totals = 0, off_tile_start = 0;
@@ -196,6 +203,18 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0);
+
+// One sort_pass over the keys (digit (key >> shift) & 255, histogram hist_pass); keys_out may
+// be null. `lookback` holds sort_parts<K>(cap) * kRadix zeroed words, *part_counter is zero.
+template <typename K>
+void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
+                      const uint32_t* num_keys_dev, int shift, const uint32_t* hist_pass, uint32_t* lookback,
+                      uint32_t* part_counter, uint32_t* error, cudaStream_t stream);
+
+// Counts-first tile sort of sort_mode 1 (tile_sort.cu): per-tile counts -> digit histograms
+// and ranges; then the passes over the 16-bit tile keys emitted in depth order.
+void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream);
+void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream);
 
 void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,
                            const float* freq, const float* phase, float t, int64_t n, float* means_out,

@@ -51,7 +51,12 @@ def test_workspace_queries_and_validation(L):
     with pytest.raises(vis.VisError):
         vis.vis_workspace_layout(10, 8, 8, 100)        # too small for even one key
     df = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=1))
-    assert df.key_bytes == 4 and df.sort_mode == 1 and df.sort_passes == 2   # 13 tile bits
+    assert df.key_bytes == 2 and df.sort_mode == 1 and df.sort_passes == 2   # 13 tile bits, 16-bit keys
+    assert df.sorted_buffer == 0 and df.off_keys[0] != df.off_keys[1]
+    one = vis.vis_workspace_layout(10_000, 100, 100, 10 ** 8, vis.make_opts(sort_mode=1))
+    assert one.sort_passes == 1 and one.key_bytes == 2                      # 49 tiles: one pass
+    wide = vis.vis_workspace_layout(10_000, 3840, 2160, 10 ** 9, vis.make_opts(sort_mode=1, tile=8))
+    assert wide.key_bytes == 4 and wide.sort_passes == 3   # 129600 tiles (17 bits): counters exceed shared memory
     assert vis.vis_workspace_size(10_000, 256, 256, 100_000, vis.make_opts(sort_mode=1)) < b
     bn = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=2))
     assert bn.sort_mode == 2 and bn.key_bytes == 0

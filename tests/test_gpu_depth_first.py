@@ -41,7 +41,45 @@ def test_depth_first_equals_tile_depth_sort(tile):
     assert vis.vis_check(wb.buf) < vis.vis_check(wc.buf)
     va, ra, La = _sorted_vals_and_ranges(sa, wa)
     vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
-    assert La.key_bytes == 8 and Lb.key_bytes == 4 and Lb.sort_mode == 1
+    assert La.key_bytes == 8 and Lb.key_bytes == 2 and Lb.sort_mode == 1
+    assert np.array_equal(va, vb)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
+
+
+def _huge_splat_scene(n, seed):
+    """A mixture scene whose first Gaussian covers the whole view (its copies span several
+    4096-copy partitions of the tile binning)."""
+    sc = synth.mixture_scene(n, seed, sh_degree=1, ball_radius=3.0, comp_std=0.5, log_scale_mean=-3.2)
+    sc = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    sc["means"][0] = 0.0
+    sc["log_scales"][0] = np.log(4.0)
+    sc["opacity_logits"][0] = -2.0
+    return sc
+
+
+@pytest.mark.parametrize("shape", [
+    ("one pass", 200, 150, 16, False),      # 130 tiles: the binning pass is the only pass
+    ("two passes", 301, 187, 8, False),     # 912 tiles
+    ("huge splat", 640, 480, 8, True),      # 4800 copies of one splat
+    ("big grid", 1920, 1080, 8, False),     # 32400 tiles: 130 KB of per-tile counters
+    ("unfused", 2048, 1632, 8, False),      # 52224 tiles: counters do not fit, 4-byte tile sort
+])
+def test_fused_binning_equals_tile_depth_sort(shape):
+    name, W, H, tile, huge = shape
+    sc = _huge_splat_scene(30000, 5) if huge else synth.mixture_scene(
+        30000, 17, sh_degree=1, ball_radius=3.0, comp_std=0.5, log_scale_mean=-3.2)
+    cam = synth.look_at((1.0, 2.0, 9.0), (0, 0, 0), W, H, 55.0)
+    a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=0))
+    b_rgb, b_alpha, sb, wb = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1))
+    va, ra, La = _sorted_vals_and_ranges(sa, wa)
+    vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
+    nt = Lb.tiles_x * Lb.tiles_y
+    assert Lb.key_bytes == (4 if nt > 51200 else 2), name
+    assert Lb.sort_passes == (1 if nt <= 256 else (2 if nt <= 65536 else 3))
+    if huge:
+        assert int(ws_view(wb, Lb.off_touched, 1, np.uint32)[0]) == nt   # splat 0 lists every tile
+    assert len(va) == len(vb) > 0
     assert np.array_equal(va, vb)
     assert np.array_equal(ra, rb)
     assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
