@@ -561,7 +561,8 @@ vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint
     vis::launch_sort_generic<uint64_t>(keys_in, vals_in, keys_out, vals_out, reinterpret_cast<uint64_t*>(w + off_k),
                                        reinterpret_cast<uint32_t*>(w + off_v), m, &ctrl->num_keys, passes,
                                        reinterpret_cast<uint32_t*>(w + off_hist), reinterpret_cast<uint32_t*>(w + off_lb),
-                                       ctrl->part_counter, &ctrl->error, stream);
+                                       ctrl->part_counter, &ctrl->error, stream, nullptr, 0,
+                                       key_bits - vis::kRadixBits * (passes - 1));
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;

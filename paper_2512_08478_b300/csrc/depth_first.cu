@@ -205,7 +205,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* vb = L.sorted_buffer ? v0 : v1;
     launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp, hist + kMaxPasses * kRadix,
                                   lb + L.lookback_words_depth, ctrl->part_counter + kMaxPasses, &ctrl->error, stream,
-                                  mark, mark_index + 1);
+                                  mark, mark_index + 1, L.tile_bits - kRadixBits * (tp - 1));
     (void)sms;
 }
 

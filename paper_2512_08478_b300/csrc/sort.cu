@@ -44,28 +44,34 @@ sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys
 template <typename K>
 struct SortSmem {
     static constexpr int KPT = SortKPT<K>::value;
-    K keys[kSortThreads * KPT];
-    uint32_t vals[kSortThreads * KPT];
+    K keys[kSortThreads * KPT];          // reordered by digit
+    uint32_t vals[kSortThreads * KPT];   // reordered by digit
+    uint32_t vin[kSortThreads * KPT];    // values in input order (asynchronous copies)
     uint32_t whist[kSortThreads / 32][kRadix];
     uint32_t digit_off[kRadix];
     uint32_t local_start[kRadix];
-    uint32_t scan_tmp[8];
+    uint32_t scan_a[8], scan_b[8];
     uint32_t part;
     uint32_t bad;
 };
 
 // Three CTAs of 256 threads per SM: at most 85 registers per thread.
 //
-// Per partition: load (warp-striped), digit counts per warp with shared atomics
-// ("early counts"), publish the partition's counts and resolve its global digit
-// offsets by look-back *before* ranking, then rank stably, reorder in shared memory
-// and write digit runs. All indexing inside the partition is 32-bit and relative to
-// its base. keys_out may be null (last pass of a sort whose keys are not needed).
+// Per partition (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT)):
+//   keys -> registers, values -> shared memory by asynchronous copies;
+//   per-warp digit counts (shared atomics) -> the partition's per-digit counts,
+//   published at once for the successors; exclusive scans of the counts and of the
+//   pass's global digit histogram; the look-back window is issued;
+//   stable ranking (rank_keys) and reorder by digit in shared memory;
+//   the look-back is resolved -> global digit offsets; digit runs are written out.
+// All indexing inside the partition is 32-bit and relative to its base. keys_out may be
+// null (last pass of a sort whose keys are not needed). nbits: significant bits of this
+// pass's digit (8, fewer for the top digit of a narrow key).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads, 3)
 sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-          const uint32_t* __restrict__ num_keys, int64_t cap, int shift,
+          const uint32_t* __restrict__ num_keys, int64_t cap, int shift, int nbits,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
     constexpr int KPT = SortKPT<K>::value;
@@ -88,52 +94,70 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const K* kin = keys_in + base;
     const uint32_t* vin = vals_in + base;
 
-    // ---- load (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the partition) ----
+    // ---- load: keys to registers, values to shared memory ----
     const int wofs = warp * (32 * KPT) + lane;
     K key[KPT];
-    uint32_t val[KPT];
+    uint32_t vmask = 0;
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
         const int idx = wofs + k * 32;
-        if (idx < n_in) { key[k] = kin[idx]; val[k] = vin[idx]; }
-        else { key[k] = 0; val[k] = 0; }
+        if (idx < n_in) {
+            key[k] = kin[idx];
+            vmask |= 1u << k;
+            cp_async4(&S.vin[idx], vin + idx);
+        } else {
+            key[k] = 0;
+        }
     }
+    cp_async_commit();
     uint32_t* wh = S.whist[warp];
     // ---- early counts: per-warp digit histogram ----
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
-        if (wofs + k * 32 < n_in) atomicAdd(&wh[(uint32_t)(key[k] >> shift) & (kRadix - 1)], 1u);
+        if ((vmask >> k) & 1u) atomicAdd(&wh[(uint32_t)(key[k] >> shift) & (kRadix - 1)], 1u);
     __syncthreads();
 
-    // ---- per-digit totals, warp offsets; publish the aggregate; look-back ----
+    // ---- per-digit counts and warp offsets; publish; scans; issue the look-back ----
     const uint32_t d = tid;   // one digit per thread (256 threads, 256 digits)
     const uint32_t cnt = warp_offsets_of_digit(S.whist, d);
     publish_aggregate(lookback, part, d, cnt);
-    const uint32_t local_start = block_exclusive_scan_256(cnt, S.scan_tmp, nullptr);
-    const uint32_t gstart = block_exclusive_scan_256(hist_pass[d], S.scan_tmp, nullptr);
-    bool timed_out = false;
-    const uint32_t prefix = lookback_prefix(lookback, part, d, cnt, &timed_out);
-    if (timed_out) {
-        atomicOr(error, kErrTimeout);
-        S.bad = 1;
+    const uint32_t h = hist_pass[d];
+    uint32_t ia = cnt, ib = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += ta; ib += tb; }
     }
+    if (lane == 31) { S.scan_a[warp] = ia; S.scan_b[warp] = ib; }
+    uint32_t lbw[kLookbackWindow];
+    lookback_issue<kLookbackWindow>(lookback, part, d, lbw);
+    __syncthreads();
+    uint32_t local_start = ia - cnt, gstart = ib - h;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w)
+        if (w < warp) { local_start += S.scan_a[w]; gstart += S.scan_b[w]; }
     S.local_start[d] = local_start;
-    S.digit_off[d] = gstart + prefix - local_start;
     __syncthreads();
 
     // ---- stable ranking into partition-local positions, and reorder by digit ----
     uint32_t pos[KPT];
-    uint32_t vmask = 0;
+    rank_keys<KPT, K>(key, shift, nbits, vmask, wh, S.local_start, pos);
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
-        if (wofs + k * 32 < n_in) vmask |= 1u << k;
-    rank_keys<KPT, K>(key, shift, vmask, wh, S.local_start, pos);
+        if ((vmask >> k) & 1u) S.keys[pos[k]] = key[k];
+    cp_async_wait_all();   // this thread's own values (same striped slots)
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
-        if (wofs + k * 32 < n_in) S.keys[pos[k]] = key[k];
-#pragma unroll
-    for (int k = 0; k < KPT; ++k)
-        if (wofs + k * 32 < n_in) S.vals[pos[k]] = val[k];
+        if ((vmask >> k) & 1u) S.vals[pos[k]] = S.vin[wofs + k * 32];
+
+    // ---- resolve the look-back: global digit offsets ----
+    bool timed_out = false;
+    const uint32_t prefix = lookback_resolve<kLookbackWindow>(lookback, part, d, cnt, lbw, &timed_out);
+    if (timed_out) {
+        atomicOr(error, kErrTimeout);
+        S.bad = 1;
+    }
+    S.digit_off[d] = gstart + prefix - local_start;
     __syncthreads();
     if (S.bad) return;
 
@@ -169,7 +193,7 @@ template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark, int mark_index) {
+                         StageMark mark, int mark_index, int last_bits) {
     if (cap <= 0 || passes <= 0) return;
     static bool attr_done = false;   // per process; the attribute is per function
     const size_t smem = sizeof(SortSmem<K>);
@@ -188,8 +212,9 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
         const bool to_a = ((passes - 1 - p) % 2) == 0;
         K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
+        const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < kRadixBits) ? last_bits : kRadixBits;
         sort_pass<K><<<(int)parts, kSortThreads, smem, stream>>>(
-            src_k, src_v, dk, dv, num_keys_dev, cap, kRadixBits * p, hist + p * kRadix,
+            src_k, src_v, dk, dv, num_keys_dev, cap, kRadixBits * p, nbits, hist + p * kRadix,
             lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
         src_k = dk;
         src_v = dv;
@@ -200,8 +225,8 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
 // (key >> shift) & 255 and the digit histogram hist_pass; keys_out may be null.
 template <typename K>
 void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
-                      const uint32_t* num_keys_dev, int shift, const uint32_t* hist_pass, uint32_t* lookback,
-                      uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
+                      const uint32_t* num_keys_dev, int shift, int nbits, const uint32_t* hist_pass,
+                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
     if (cap <= 0) return;
     static bool attr_done = false;
     const size_t smem = sizeof(SortSmem<K>);
@@ -210,20 +235,20 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
         attr_done = true;
     }
     sort_pass<K><<<(int)sort_parts<K>(cap), kSortThreads, smem, stream>>>(keys_in, vals_in, keys_out, vals_out,
-                                                                           num_keys_dev, cap, shift, hist_pass,
-                                                                           lookback, part_counter, error);
+                                                                           num_keys_dev, cap, shift, nbits,
+                                                                           hist_pass, lookback, part_counter, error);
 }
 
 template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint16_t*, uint32_t*, int64_t,
-                                         const uint32_t*, int, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
-                                         cudaStream_t);
+                                         const uint32_t*, int, int, const uint32_t*, uint32_t*, uint32_t*,
+                                         uint32_t*, cudaStream_t);
 
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int);
 template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);
@@ -239,7 +264,7 @@ void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark,
     launch_sort_generic<uint64_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, L.passes,
                                   reinterpret_cast<uint32_t*>(ws + L.off_hist),
                                   reinterpret_cast<uint32_t*>(ws + L.off_lookback), ctrl->part_counter,
-                                  &ctrl->error, stream, mark, mark_index);
+                                  &ctrl->error, stream, mark, mark_index, L.key_bits - kRadixBits * (L.passes - 1));
 }
 
 }  // namespace vis

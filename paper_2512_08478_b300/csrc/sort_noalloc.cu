@@ -101,7 +101,7 @@ extern "C" vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint
                                        reinterpret_cast<uint64_t*>(w + kOffKeys), reinterpret_cast<uint32_t*>(w + kOffVals),
                                        m, &ctrl->num_keys, passes, reinterpret_cast<uint32_t*>(w + kOffHist),
                                        reinterpret_cast<uint32_t*>(w + kOffLookback), ctrl->part_counter, &ctrl->error,
-                                       stream);
+                                       stream, nullptr, 0, key_bits - vis::kRadixBits * (passes - 1));
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
     vis::set_last_error("");

@@ -136,15 +136,16 @@ void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
     const size_t words = (size_t)L.sort_parts * kRadix;
     // emitted copies in buffer 0; one pass -> values in 1, two passes -> keys + values in 1, then values in 0
+    const int low_bits = L.tile_bits < kRadixBits ? L.tile_bits : kRadixBits;
     if (L.passes == 1) {
-        launch_sort_pass<uint16_t>(k0, v0, nullptr, v1, L.cap, &ctrl->num_keys, 0, hist, lb,
+        launch_sort_pass<uint16_t>(k0, v0, nullptr, v1, L.cap, &ctrl->num_keys, 0, low_bits, hist, lb,
                                    &ctrl->part_counter[kMaxPasses], &ctrl->error, stream);
         return;
     }
-    launch_sort_pass<uint16_t>(k0, v0, k1, v1, L.cap, &ctrl->num_keys, 0, hist, lb, &ctrl->part_counter[kMaxPasses],
-                               &ctrl->error, stream);
-    launch_sort_pass<uint16_t>(k1, v1, nullptr, v0, L.cap, &ctrl->num_keys, kRadixBits, hist + kRadix, lb + words,
-                               &ctrl->part_counter[kMaxPasses + 1], &ctrl->error, stream);
+    launch_sort_pass<uint16_t>(k0, v0, k1, v1, L.cap, &ctrl->num_keys, 0, low_bits, hist, lb,
+                               &ctrl->part_counter[kMaxPasses], &ctrl->error, stream);
+    launch_sort_pass<uint16_t>(k1, v1, nullptr, v0, L.cap, &ctrl->num_keys, kRadixBits, L.tile_bits - kRadixBits,
+                               hist + kRadix, lb + words, &ctrl->part_counter[kMaxPasses + 1], &ctrl->error, stream);
 }
 
 }  // namespace vis

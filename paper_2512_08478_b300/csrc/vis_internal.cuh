@@ -197,19 +197,21 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
 // Reads keys_in/vals_in, ping-pongs between the a and b buffers and leaves the result in a.
 // `lookback` must hold passes * sort_parts<K>(cap) * kRadix words, `hist` passes * kRadix
 // words and `part_counters` passes words, all zeroed; the key count is read from
-// num_keys_dev (<= cap). If `mark` is given it is called after the histogram.
+// num_keys_dev (<= cap). If `mark` is given it is called after the histogram. last_bits:
+// significant bits of the last pass's digit (key bits - 8 (passes - 1)).
 template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark = nullptr, int mark_index = 0);
+                         StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits);
 
-// One sort_pass over the keys (digit (key >> shift) & 255, histogram hist_pass); keys_out may
-// be null. `lookback` holds sort_parts<K>(cap) * kRadix zeroed words, *part_counter is zero.
+// One sort_pass over the keys (digit (key >> shift) & 255 with nbits significant bits,
+// histogram hist_pass); keys_out may be null. `lookback` holds sort_parts<K>(cap) * kRadix
+// zeroed words, *part_counter is zero.
 template <typename K>
 void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
-                      const uint32_t* num_keys_dev, int shift, const uint32_t* hist_pass, uint32_t* lookback,
-                      uint32_t* part_counter, uint32_t* error, cudaStream_t stream);
+                      const uint32_t* num_keys_dev, int shift, int nbits, const uint32_t* hist_pass,
+                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream);
 
 // Counts-first tile sort of sort_mode 1 (tile_sort.cu): per-tile counts -> digit histograms
 // and ranges; then the passes over the 16-bit tile keys emitted in depth order.
