@@ -86,21 +86,29 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
 // KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles
 template <typename KT>
 __global__ void __launch_bounds__(kPrepThreads)
-emit_tiles(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
+emit_tiles(const uint32_t* __restrict__ dvals, const uint2* __restrict__ rect,
            const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
            const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     if (ctrl->error & kErrCapacity) return;
     __shared__ uint32_t s_start[kPrepThreads];
     __shared__ uint32_t s_g[kPrepThreads];
+    __shared__ uint32_t s_rx[kPrepThreads], s_ry[kPrepThreads];
     __shared__ uint32_t warp_tot[kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nv = *num_visible;
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t g = 0, cnt = 0;
-    if (j < nv) { g = dvals[j]; cnt = touched[g]; }
+    uint2 r = make_uint2(0, 0);
+    if (j < nv) {   // the copy count is the rectangle's area: one gather per splat
+        g = dvals[j];
+        r = rect[g];
+        cnt = ((r.x >> 16) - (r.x & 0xffffu)) * ((r.y >> 16) - (r.y & 0xffffu));
+    }
     const uint32_t incl = warp_incl_scan(cnt, lane);
     s_start[threadIdx.x] = incl - cnt;
     s_g[threadIdx.x] = g;
+    s_rx[threadIdx.x] = r.x;
+    s_ry[threadIdx.x] = r.y;
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     uint32_t warp_base = boff[blockIdx.x];
@@ -115,8 +123,8 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touc
             if (s_start[g0 + mid] <= q) lo = mid; else hi = mid - 1;
         }
         const uint32_t gi = s_g[g0 + lo];
-        const uint2 r = rect[gi];
-        const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu;
+        const uint32_t rx = s_rx[g0 + lo], ry = s_ry[g0 + lo];
+        const uint32_t x0 = rx & 0xffffu, x1 = rx >> 16, y0 = ry & 0xffffu;
         const uint32_t w = x1 - x0;
         const uint32_t k = q - s_start[g0 + lo];
         keys[warp_base + q] = (KT)((y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w));
@@ -181,7 +189,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
         emit_tiles<uint16_t><<<blocks_n, kPrepThreads, 0, stream>>>(
-            dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
+            dv0, reinterpret_cast<const uint2*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
             reinterpret_cast<uint16_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
         if (mark) mark(mark_index, stream);
         launch_tile_counts(L, ws, stream);
@@ -194,7 +202,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, reinterpret_cast<const uint2*>(ws + L.off_rect),
+    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, reinterpret_cast<const uint2*>(ws + L.off_rect),
                                                       &ctrl->num_visible, boff2, L.tiles_x, ctrl, k0, v0);
     if (mark) mark(mark_index, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer

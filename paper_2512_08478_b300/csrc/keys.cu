@@ -17,41 +17,56 @@
 namespace vis {
 
 // Exclusive scan of per-block sums; the total goes to *total, and if `error` is given
-// a total above `cap` sets kErrCapacity there. One CTA of 1024 threads; thread t owns the
-// contiguous run [t*per, (t+1)*per) of the sums: it adds its run (loads unrolled so that
-// several are in flight), the 1024 run totals are scanned, then it writes its run's offsets.
+// a total above `cap` sets kErrCapacity there. One CTA of 1024 threads works through the
+// sums in chunks of kScanChunk: a coalesced load of the chunk into shared memory, a
+// sequential sum of each thread's contiguous run of it, a scan of the 1024 run totals,
+// the run's offsets written back in place, and a coalesced store; a carry links chunks.
+constexpr int kScanChunk = 8192;   // 32 KB of static shared memory
+
 __global__ void __launch_bounds__(1024)
 scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
                 uint32_t* total_out, uint32_t* error, int64_t cap) {
+    __shared__ uint32_t s[kScanChunk];
     __shared__ unsigned long long warp_tot[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (nblocks + 1023) / 1024;
-    const int64_t b0 = (int64_t)threadIdx.x * per;
-    const int64_t b1 = min(nblocks, b0 + per);
-    unsigned long long run = 0;
-#pragma unroll 8
-    for (int64_t b = b0; b < b1; ++b) run += bsum[b];
-    unsigned long long incl = run;
+    constexpr int per = kScanChunk / 1024;
+    unsigned long long carry = 0;
+    for (int64_t c0 = 0; c0 < nblocks; c0 += kScanChunk) {
+        const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
+        for (int i = threadIdx.x; i < kScanChunk; i += 1024) s[i] = i < n ? bsum[c0 + i] : 0u;
+        __syncthreads();
+        const int r0 = threadIdx.x * per;
+        unsigned long long run = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    unsigned long long excl = incl - run, all = 0;
-    for (int w = 0; w < 32; ++w) {
-        const unsigned long long x = warp_tot[w];
-        if (w < warp) excl += x;
-        all += x;
-    }
-    for (int64_t b = b0; b < b1; ++b) {
-        boff[b] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
-        excl += bsum[b];
+        for (int i = 0; i < per; ++i) run += s[r0 + i];
+        unsigned long long incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        unsigned long long excl = carry + incl - run, all = 0;
+        for (int w = 0; w < 32; ++w) {
+            const unsigned long long x = warp_tot[w];
+            if (w < warp) excl += x;
+            all += x;
+        }
+#pragma unroll
+        for (int i = 0; i < per; ++i) {
+            const uint32_t v = s[r0 + i];
+            s[r0 + i] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
+            excl += v;
+        }
+        carry += all;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += 1024) boff[c0 + i] = s[i];
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *total_out = (uint32_t)min(all, (unsigned long long)0xffffffffu);
-        if (error && all > (unsigned long long)cap) atomicOr(error, kErrCapacity);
+        *total_out = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
+        if (error && carry > (unsigned long long)cap) atomicOr(error, kErrCapacity);
     }
 }
 

@@ -1,9 +1,9 @@
 // Building blocks of one onesweep-style LSD radix pass (8-bit digit, 256 threads, one
 // digit per thread in the scan and look-back phases).
 //
-// Per partition: per-warp digit counts ("early counts"), publish the partition's
-// per-digit aggregate, issue the decoupled look-back over the preceding partitions,
-// rank every key stably inside its warp and reorder the partition by digit in shared
+// Per partition: rank every key stably inside its warp (which also yields the warp's
+// digit counts), publish the partition's per-digit aggregate, issue the decoupled
+// look-back over the preceding partitions, reorder the partition by digit in shared
 // memory while the look-back words are in flight, then resolve the global digit offsets
 // and write the digit runs.
 #pragma once
@@ -72,10 +72,10 @@ __device__ __forceinline__ void publish_aggregate(uint32_t* lookback, uint32_t p
 // bit k of valid_mask) inside the partition. Per round, the lanes holding the same digit
 // ("peers") are found with one ballot per digit bit (the digit's upper bits are zero when
 // nbits < 8); the group's leader (lowest lane) takes the group's slots from the warp's
-// private running counter wh[digit] (holding the warp's exclusive offset of the digit)
-// with a plain load and store -- groups of one round have distinct digits, and the rounds
-// are ordered by __syncwarp. Returns partition-local positions
-// local_start[digit] + (rank of the key among the partition's keys of its digit).
+// private running counter wh[digit] with a plain load and store -- groups of one round
+// have distinct digits, and the rounds are ordered by __syncwarp. Returns
+// local_start[digit] + wh[digit] on entry + (rank of the key among the warp's keys of its
+// digit); wh[digit] grows by the warp's count of the digit.
 template <int KPT, typename K>
 __device__ __forceinline__ void rank_keys(const K (&key)[KPT], int shift, int nbits, uint32_t valid_mask,
                                           uint32_t* wh, const uint32_t* local_start, uint32_t (&pos)[KPT]) {

@@ -50,6 +50,7 @@ struct SortSmem {
     uint32_t whist[kSortThreads / 32][kRadix];
     uint32_t digit_off[kRadix];
     uint32_t local_start[kRadix];
+    uint32_t zeros[kRadix];
     uint32_t scan_a[8], scan_b[8];
     uint32_t part;
     uint32_t bad;
@@ -59,10 +60,11 @@ struct SortSmem {
 //
 // Per partition (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT)):
 //   keys -> registers, values -> shared memory by asynchronous copies;
-//   per-warp digit counts (shared atomics) -> the partition's per-digit counts,
-//   published at once for the successors; exclusive scans of the counts and of the
-//   pass's global digit histogram; the look-back window is issued;
-//   stable ranking (rank_keys) and reorder by digit in shared memory;
+//   stable ranking inside each warp (rank_keys, warp counters from zero): the rank of
+//   every key among its warp's keys of the same digit, and the warp's digit counts;
+//   per-digit partition counts, published at once for the successors; exclusive scans
+//   of the counts and of the pass's global digit histogram; the look-back window is
+//   issued; the keys and values are reordered by digit in shared memory;
 //   the look-back is resolved -> global digit offsets; digit runs are written out.
 // All indexing inside the partition is 32-bit and relative to its base. keys_out may be
 // null (last pass of a sort whose keys are not needed). nbits: significant bits of this
@@ -86,6 +88,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         S.bad = 0;
     }
     for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+    S.zeros[tid] = 0;
     __syncthreads();
     const uint32_t part = S.part;
     const int64_t base = (int64_t)part * PART;
@@ -111,10 +114,9 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     }
     cp_async_commit();
     uint32_t* wh = S.whist[warp];
-    // ---- early counts: per-warp digit histogram ----
-#pragma unroll
-    for (int k = 0; k < KPT; ++k)
-        if ((vmask >> k) & 1u) atomicAdd(&wh[(uint32_t)(key[k] >> shift) & (kRadix - 1)], 1u);
+    // ---- stable ranking inside the warp; the warp counters end as the warp's digit counts ----
+    uint32_t pos[KPT];
+    rank_keys<KPT, K>(key, shift, nbits, vmask, wh, S.zeros, pos);
     __syncthreads();
 
     // ---- per-digit counts and warp offsets; publish; scans; issue the look-back ----
@@ -139,9 +141,12 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     S.local_start[d] = local_start;
     __syncthreads();
 
-    // ---- stable ranking into partition-local positions, and reorder by digit ----
-    uint32_t pos[KPT];
-    rank_keys<KPT, K>(key, shift, nbits, vmask, wh, S.local_start, pos);
+    // ---- reorder by digit: partition position = digit start + warp offset + rank ----
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+        const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
+        pos[k] += S.local_start[dk] + wh[dk];
+    }
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
         if ((vmask >> k) & 1u) S.keys[pos[k]] = key[k];
