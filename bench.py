@@ -360,7 +360,7 @@ def run_ours(args):
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk_summary, e2e=e2e,
-                gpu_launches=int(args.steps * {0: 6 + passes, 1: 11 + kDP + passes, 2: 12 + kDP}[args.sort_mode]
+                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes, 2: 11 + kDP}[args.sort_mode]
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
                 roofline=roof, hbm_stages=hbm_stages,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},

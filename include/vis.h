@@ -92,10 +92,12 @@ typedef struct {
  *  collect_stats  1: the compositor also counts the (pixel, splat) pairs it tests and
  *              composites into vis_ctrl.pair_tests / hits (a few % slower); default 0.
  *  tile_extent which tiles a splat is listed in: 0 = every tile of the square of
- *              radius ceil(3 sqrt(lambda_max(S))) + 1 px around its centre; 1 (default) =
- *              every tile of the tight box around the region where a pixel can take the
- *              splat (q <= min(9, 2 ln(opacity / alpha_min))). The image does not depend on
- *              it; 1 lists ~40% fewer (tile, splat) pairs.
+ *              radius ceil(3 sqrt(lambda_max(S))) + 1 px around its centre; 1 = every
+ *              tile of the tight box around the region where a pixel can take the splat
+ *              (q <= min(9, 2 ln(opacity / alpha_min))); 2 (default) = that box with its
+ *              top and bottom rows narrowed to the tiles whose band of pixel centres meets
+ *              that region. The image does not depend on it; 1 lists ~40% fewer (tile,
+ *              splat) pairs than 0, and 2 ~12% fewer than 1.
  * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
 typedef struct {
     int tile;
@@ -124,7 +126,10 @@ typedef struct {
     size_t off_ctrl;         /* vis_ctrl, device-written status */
     size_t off_rec;          /* float4[n][3] splat records: (u,v,u_lo,v_lo), (f1,f2), (opacity,rgb) */
     size_t off_depth;        /* float[n] view depth (the sort key's low word) */
-    size_t off_rect;         /* uint2[n] tile rect: x0 | x1<<16, y0 | y1<<16 (upper bounds exclusive) */
+    size_t off_rect;         /* uint4[n] tile footprint: x0 | x1<<16, y0 | y1<<16 (the tile box,
+                                upper bounds exclusive), row trims Lt | Rt<<8 | Lb<<16 | Rb<<24
+                                (tiles dropped at the left / right ends of the top and bottom
+                                rows, see tile_extent 2), 0 */
     size_t off_touched;      /* uint32[n] tiles touched (0 if culled) */
     size_t off_keys[2];      /* key_bytes x cap: sort keys (see key_bytes); with key_bytes 2 the
                                 sorted keys are not stored (the tile of sorted position j is

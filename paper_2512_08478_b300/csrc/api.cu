@@ -64,8 +64,8 @@ vis_render_opts resolve_opts(const vis_render_opts* o) {
 vis_status check_opts(const vis_render_opts& o) {
     if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
     if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
-    if (o.tile_extent != 0 && o.tile_extent != 1)
-        return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0 or 1 (got %d)", o.tile_extent);
+    if (o.tile_extent < 0 || o.tile_extent > 2)
+        return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0, 1 or 2 (got %d)", o.tile_extent);
     if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
         return fail(VIS_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2 (got %d)", o.pixels_per_thread);
     if (o.sort_mode < vis::kSortTileDepth || o.sort_mode > vis::kSortDepthBin)
@@ -114,6 +114,7 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     p.dilation = o.dilation; p.alpha_min = o.alpha_min;
     p.wscale = (float)std::sqrt(0.5 / std::log(2.0));
     p.tight_extent = o.tile_extent;
+    p.count_survivors = L.mode != vis::kSortTileDepth;
     vis::sh_constants(p.shc);
     return p;
 }
@@ -226,7 +227,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.zero_end = off;
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
     L.off_depth = take(sizeof(float) * (size_t)n);
-    L.off_rect = take(sizeof(uint2) * (size_t)n);
+    L.off_rect = take(sizeof(uint4) * (size_t)n);
     L.off_touched = take(sizeof(uint32_t) * (size_t)n);
     L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
@@ -282,7 +283,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->t_stop = 1e-4f;
     o->sort_mode = vis::kSortDepthFirst;
     o->pixels_per_thread = 1;
-    o->tile_extent = 1;
+    o->tile_extent = 2;
     o->collect_stats = 0;
 }
 

@@ -2,7 +2,8 @@
 // depths of the surviving splats, section 3.4), followed by a stable bucketing of
 // their tile copies by tile.
 //
-//   1. compact_visible: surviving Gaussians (tiles touched > 0), in index order, as
+//   1. compact_visible: surviving Gaussians (tiles touched > 0; the preprocess counts them
+//      per block), in index order, as
 //      (float bits of depth, index) pairs; the count goes to the status block.
 //   2. a stable radix sort of those pairs by the 32-bit depth key (4 passes of 8 bits;
 //      equal depths keep index order);
@@ -16,6 +17,7 @@
 // 64-bit (tile << 32 | depth) keys -- while the sort moves 4-byte keys, and only the
 // N surviving splats (not the M tile copies) take part in the four depth passes.
 #include "vis_internal.cuh"
+#include "footprint.cuh"
 
 namespace vis {
 
@@ -27,22 +29,6 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
         if (lane >= o) v += t;
     }
     return v;
-}
-
-// Block sums of `flag(i)` over blocks of kPrepThreads, for i < n.
-__global__ void __launch_bounds__(kPrepThreads)
-visible_block_sums(const uint32_t* __restrict__ touched, int64_t n, uint32_t* __restrict__ bsum) {
-    __shared__ uint32_t ws[kPrepThreads / 32];
-    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    const uint32_t f = (i < n && touched[i] > 0) ? 1u : 0u;
-    const uint32_t b = __popc(__ballot_sync(0xffffffffu, f));
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = b;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kPrepThreads / 32; ++w) t += ws[w];
-        bsum[blockIdx.x] = t;
-    }
 }
 
 __global__ void __launch_bounds__(kPrepThreads)
@@ -86,29 +72,28 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
 // KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles
 template <typename KT>
 __global__ void __launch_bounds__(kPrepThreads)
-emit_tiles(const uint32_t* __restrict__ dvals, const uint2* __restrict__ rect,
+emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
            const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
            const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     if (ctrl->error & kErrCapacity) return;
     __shared__ uint32_t s_start[kPrepThreads];
     __shared__ uint32_t s_g[kPrepThreads];
-    __shared__ uint32_t s_rx[kPrepThreads], s_ry[kPrepThreads];
+    __shared__ uint4 s_r[kPrepThreads];
     __shared__ uint32_t warp_tot[kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nv = *num_visible;
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t g = 0, cnt = 0;
-    uint2 r = make_uint2(0, 0);
-    if (j < nv) {   // the copy count is the rectangle's area: one gather per splat
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (j < nv) {   // the copy count follows from the footprint: one gather per splat
         g = dvals[j];
         r = rect[g];
-        cnt = ((r.x >> 16) - (r.x & 0xffffu)) * ((r.y >> 16) - (r.y & 0xffffu));
+        cnt = fp_count(fp_unpack(r));
     }
     const uint32_t incl = warp_incl_scan(cnt, lane);
     s_start[threadIdx.x] = incl - cnt;
     s_g[threadIdx.x] = g;
-    s_rx[threadIdx.x] = r.x;
-    s_ry[threadIdx.x] = r.y;
+    s_r[threadIdx.x] = r;
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     uint32_t warp_base = boff[blockIdx.x];
@@ -123,11 +108,8 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint2* __restrict__ rect,
             if (s_start[g0 + mid] <= q) lo = mid; else hi = mid - 1;
         }
         const uint32_t gi = s_g[g0 + lo];
-        const uint32_t rx = s_rx[g0 + lo], ry = s_ry[g0 + lo];
-        const uint32_t x0 = rx & 0xffffu, x1 = rx >> 16, y0 = ry & 0xffffu;
-        const uint32_t w = x1 - x0;
         const uint32_t k = q - s_start[g0 + lo];
-        keys[warp_base + q] = (KT)((y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w));
+        keys[warp_base + q] = (KT)fp_tile(fp_unpack(s_r[g0 + lo]), k, (uint32_t)tiles_x);
         vals[warp_base + q] = gi;
     }
 }
@@ -162,8 +144,8 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     uint32_t* dv1 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[1]);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
-    // 1. compaction of the surviving splats, in index order
-    visible_block_sums<<<blocks_n, kPrepThreads, 0, stream>>>(touched, L.n, bvis);
+    // 1. compaction of the surviving splats, in index order (the preprocess wrote the
+    //    per-block survivor counts)
     launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0, stream);
     compact_visible<<<blocks_n, kPrepThreads, 0, stream>>>(touched, reinterpret_cast<const float*>(ws + L.off_depth),
                                                            L.n, bvis_off, dk0, dv0);
@@ -189,7 +171,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
         emit_tiles<uint16_t><<<blocks_n, kPrepThreads, 0, stream>>>(
-            dv0, reinterpret_cast<const uint2*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
+            dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
             reinterpret_cast<uint16_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
         if (mark) mark(mark_index, stream);
         launch_tile_counts(L, ws, stream);
@@ -202,7 +184,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, reinterpret_cast<const uint2*>(ws + L.off_rect),
+    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, reinterpret_cast<const uint4*>(ws + L.off_rect),
                                                       &ctrl->num_visible, boff2, L.tiles_x, ctrl, k0, v0);
     if (mark) mark(mark_index, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer

@@ -10,9 +10,10 @@
 //      every warp emits its Gaussians' keys cooperatively, lane j writing key j of
 //      the warp's contiguous output run, so stores are coalesced whatever the
 //      per-Gaussian counts. key = (tile id << 32) | float bits of the view depth,
-//      val = Gaussian index; tiles in row-major order within each rectangle.
+//      val = Gaussian index; tiles in the footprint's row-major order (footprint.cuh).
 //   3. ranges_kernel: [start, end) of every tile in the sorted keys.
 #include "vis_internal.cuh"
+#include "footprint.cuh"
 
 namespace vis {
 
@@ -76,7 +77,7 @@ void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uin
 }
 
 __global__ void __launch_bounds__(kPrepThreads)
-duplicate_kernel(const uint32_t* __restrict__ touched, const uint2* __restrict__ rect,
+duplicate_kernel(const uint32_t* __restrict__ touched, const uint4* __restrict__ rect,
                  const float* __restrict__ depth, const uint32_t* __restrict__ boff, int64_t n,
                  int tiles_x, const Ctrl* __restrict__ ctrl, uint64_t* __restrict__ keys,
                  uint32_t* __restrict__ vals) {
@@ -108,12 +109,8 @@ duplicate_kernel(const uint32_t* __restrict__ touched, const uint2* __restrict__
             if (s_start[g0 + mid] <= j) lo = mid; else hi = mid - 1;
         }
         const int64_t gi = (int64_t)blockIdx.x * kPrepThreads + g0 + lo;
-        const uint2 r = rect[gi];
-        const uint32_t x0 = r.x & 0xffffu, x1 = r.x >> 16, y0 = r.y & 0xffffu;
-        const uint32_t w = x1 - x0;
         const uint32_t k = j - s_start[g0 + lo];
-        const uint32_t tx = x0 + k % w, ty = y0 + k / w;
-        const uint64_t tile = (uint64_t)ty * (uint64_t)tiles_x + tx;
+        const uint64_t tile = fp_tile(fp_unpack(rect[gi]), k, (uint32_t)tiles_x);
         const uint32_t zb = __float_as_uint(depth[gi]);
         keys[warp_base + j] = (tile << 32) | zb;
         vals[warp_base + j] = (uint32_t)gi;
@@ -127,7 +124,7 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
     launch_scan_sums(bsum, boff, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
     if (n <= 0) return;
     duplicate_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
-        reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint2*>(ws + L.off_rect),
+        reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint4*>(ws + L.off_rect),
         reinterpret_cast<const float*>(ws + L.off_depth), boff, n, L.tiles_x, ctrl,
         reinterpret_cast<uint64_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
 }

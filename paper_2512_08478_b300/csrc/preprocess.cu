@@ -1,9 +1,9 @@
 // K1 -- per-Gaussian preprocess (section 3.2 Eq. 1; Algorithm 1, Preprocess).
 //
 // One thread per Gaussian. Reads the caller's fp32 SoA attributes once and writes
-// a 48-byte splat record, the view depth, the tile rectangle and the number of
-// tiles touched; each block also writes the sum of its tiles-touched counts for
-// the key-offset scan.
+// a 48-byte splat record, the view depth, the tile footprint (footprint.cuh) and the
+// number of tiles touched; each block also writes the sum of its tiles-touched counts
+// (or of its survivors) for the offset scan.
 //
 // Numerics. The camera transform and the perspective division are carried in
 // float-float (error-free transforms) so that the pixel centre (u, v) is exact to
@@ -15,14 +15,16 @@
 // exponent in base 2) and stays well conditioned for needle-shaped splats, where the
 // conic form (a, b, c) loses digits.
 #include "vis_internal.cuh"
+#include "footprint.cuh"
 
 namespace vis {
 
-__global__ void __launch_bounds__(kPrepThreads)
+__global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
-                  uint2* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
+                  uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
                   uint32_t* __restrict__ block_sums) {
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    __shared__ float s_trim[7][kPrepThreads];
     uint32_t touched = 0;
     if (i < p.n) {
         // --- camera-space position in float-float: p = R mu + t ---
@@ -43,7 +45,7 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         const float opac = 1.f / (1.f + __expf(-logit));
         depth_out[i] = z;
         bool ok = (z > p.near_z) && (opac >= p.alpha_min);
-        uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, trims = 0;
         if (ok) {
             // --- pixel centre u = fx x/z + cx (float-float) ---
             const float2 rx = ff_div(pc[0], pc[2]);
@@ -141,6 +143,11 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 const int iy0 = (int)fminf(fty, fmaxf(0.f, fy0));
                 const int iy1 = (int)fminf(fty, fmaxf(0.f, fy1));
                 touched = (ix1 > ix0 && iy1 > iy0) ? (uint32_t)((ix1 - ix0) * (iy1 - iy0)) : 0u;
+                // the outer-row trims below need these after the colour; they wait in shared
+                // memory rather than in registers across the SH evaluation
+                s_trim[0][threadIdx.x] = s00; s_trim[1][threadIdx.x] = s11; s_trim[2][threadIdx.x] = s01;
+                s_trim[3][threadIdx.x] = det; s_trim[4][threadIdx.x] = opac;
+                s_trim[5][threadIdx.x] = u.x; s_trim[6][threadIdx.x] = v.x;
                 if (touched > 0) {
                     x0 = ix0; x1 = ix1; y0 = iy0; y1 = iy1;
                     // --- colour from SH at dir = normalize(mu - camera centre) ---
@@ -196,14 +203,57 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                     rec[3 * (size_t)i + 2] = make_float4(opac, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f),
                                                          fmaxf(col[2], 0.f));
                 }
+                if (touched > 0 && p.tight_extent == 2 && ix1 - ix0 > 1) {
+                    // exact outer rows: narrow the box's top and bottom rows to the tiles their
+                    // band of pixel centres of the ellipse d^T S^-1 d <= qthr reaches. For dy
+                    // fixed the ellipse spans dx = (s01/s11) dy +- sqrt((det/s11)(qthr - dy^2/s11));
+                    // over a band of dy its leftmost (rightmost) point is at dy = -+ s01 sqrt(qthr/s00)
+                    // clamped to the band. Padded like the box for float rounding.
+                    const float s00 = s_trim[0][threadIdx.x], s11 = s_trim[1][threadIdx.x];
+                    const float s01 = s_trim[2][threadIdx.x], det = s_trim[3][threadIdx.x];
+                    const float opac = s_trim[4][threadIdx.x], ux = s_trim[5][threadIdx.x];
+                    const float vx = s_trim[6][threadIdx.x];
+                    const float qthr = fminf(9.f, 2.f * logf(opac / p.alpha_min)) * 1.0002f;
+                    const float inv11 = 1.f / s11;
+                    const float kx = s01 * inv11, hwf = det * inv11;
+                    const float yext = sqrtf(qthr * s11) * 1.0001f + 0.01f;
+                    const float dyl = -s01 * sqrtf(qthr / s00);
+                    const float pad = 1e-4f * sqrtf(qthr * s00) + 0.02f;
+                    const float fW = (float)(ix1 - ix0);
+                    const int rows = iy1 - iy0;
+                    uint32_t lr[4] = {0u, 0u, 0u, 0u};
+#pragma unroll 1
+                    for (int e = 0; e < (rows > 1 ? 2 : 1); ++e) {
+                        const int ty = e == 0 ? iy0 : iy1 - 1;
+                        const float ya = (float)(ty * p.tile) + 0.5f - vx - 0.02f;
+                        const float yb = (float)(ty * p.tile + p.tile) - 0.5f - vx + 0.02f;
+                        float fl = fW, fr = 0.f;   // a row the ellipse misses keeps no tile
+                        if (ya <= yext && yb >= -yext) {
+                            const float lo = fmaxf(ya, -yext), hi = fminf(yb, yext);
+                            const float dL = fminf(fmaxf(dyl, lo), hi), dR = fminf(fmaxf(-dyl, lo), hi);
+                            const float xmin = kx * dL - sqrtf(fmaxf(0.f, hwf * (qthr - dL * dL * inv11))) - pad;
+                            const float xmax = kx * dR + sqrtf(fmaxf(0.f, hwf * (qthr - dR * dR * inv11))) + pad;
+                            const float ta = floorf((ux + xmin - 0.5f) / T), tb = floorf((ux + xmax - 0.5f) / T);
+                            fl = fminf(fmaxf(0.f, ta - (float)ix0), fW);
+                            fr = fminf(fmaxf(0.f, (float)(ix1 - 1) - tb), fW - fl);
+                        }
+                        lr[2 * e] = (uint32_t)fminf(fl, 255.f);
+                        lr[2 * e + 1] = (uint32_t)fminf(fr, 255.f);
+                    }
+                    trims = fp_pack_trims(lr[0], lr[1], lr[2], lr[3]);
+                    const Footprint f = {(uint32_t)ix0, (uint32_t)ix1, (uint32_t)iy0, (uint32_t)iy1, trims};
+                    touched = fp_count(f);   // the count every copy enumerator agrees with
+                }
             }
         }
-        rect_out[i] = make_uint2(x0 | (x1 << 16), y0 | (y1 << 16));
+        if (touched == 0) { x0 = x1 = y0 = y1 = 0; trims = 0; }
+        rect_out[i] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, 0u);
         touched_out[i] = touched;
     }
-    // block sum of tiles touched (for the offset scan)
+    // block sum of tiles touched (for the offset scan of the index-order duplication) or, for
+    // the depth-first sorts, of survivors (for their compaction)
     __shared__ uint32_t warp_sums[kPrepThreads / 32];
-    uint32_t s = touched;
+    uint32_t s = p.count_survivors ? (touched > 0 ? 1u : 0u) : touched;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
@@ -221,7 +271,7 @@ void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStrea
     const int blocks = (int)L.prep_blocks;
     preprocess_kernel<<<blocks, kPrepThreads, 0, stream>>>(
         p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
-        reinterpret_cast<uint2*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
+        reinterpret_cast<uint4*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
         reinterpret_cast<uint32_t*>(ws + L.off_bsum));
 }
 

@@ -21,11 +21,12 @@
 // stable depth sort): the same order as the 64-bit (tile, depth) key sort, with no
 // keys stored and the tile ranges produced by the scan.
 #include "vis_internal.cuh"
+#include "footprint.cuh"
 
 namespace vis {
 
 __global__ void __launch_bounds__(256)
-bin_count_kernel(const uint32_t* __restrict__ dvals, const uint2* __restrict__ rect,
+bin_count_kernel(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
                  const uint32_t* __restrict__ num_visible, int64_t C, int ntiles, int tiles_x,
                  uint32_t* __restrict__ counts) {
     extern __shared__ uint32_t cnt[];
@@ -36,10 +37,9 @@ bin_count_kernel(const uint32_t* __restrict__ dvals, const uint2* __restrict__ r
     for (int i = threadIdx.x; i < ntiles; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const uint2 r = rect[dvals[j]];
-        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) atomicAdd(&cnt[ty * tiles_x + tx], 1u);
+        const Footprint f = fp_unpack(rect[dvals[j]]);
+        const uint32_t n = fp_count(f);
+        for (uint32_t k = 0; k < n; ++k) atomicAdd(&cnt[fp_tile(f, k, (uint32_t)tiles_x)], 1u);
     }
     __syncthreads();
     uint32_t* row = counts + (size_t)blockIdx.x * ntiles;
@@ -89,7 +89,7 @@ __global__ void bin_ranges_kernel(const uint32_t* __restrict__ tile_start, const
 template <int NW>
 __global__ void __launch_bounds__(NW * 32)
 bin_emit_kernel(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched,
-                const uint2* __restrict__ rect, const uint32_t* __restrict__ num_visible, int64_t C, int ntiles,
+                const uint4* __restrict__ rect, const uint32_t* __restrict__ num_visible, int64_t C, int ntiles,
                 int tiles_x, const uint32_t* __restrict__ chunk_base, const uint32_t* __restrict__ tile_start,
                 const Ctrl* __restrict__ ctrl, int64_t cap, uint32_t* __restrict__ vals_out) {
     extern __shared__ uint32_t wc[];   // [NW][words]: two 16-bit counters per word
@@ -107,13 +107,12 @@ bin_emit_kernel(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__
     const int64_t s0 = j0 + warp * cw, s1 = min(j1, s0 + cw);
     uint32_t* mine = wc + (size_t)warp * words;
     for (int64_t j = s0 + lane; j < s1; j += 32) {
-        const uint2 r = rect[dvals[j]];
-        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) {
-                const int t = ty * tiles_x + tx;
-                atomicAdd(&mine[t >> 1], 1u << ((t & 1) * 16));
-            }
+        const Footprint f = fp_unpack(rect[dvals[j]]);
+        const uint32_t n = fp_count(f);
+        for (uint32_t k = 0; k < n; ++k) {
+            const uint32_t t = fp_tile(f, k, (uint32_t)tiles_x);
+            atomicAdd(&mine[t >> 1], 1u << ((t & 1) * 16));
+        }
     }
     __syncthreads();
     // exclusive prefix over the warps, per tile (both halves of a word at once)
@@ -132,7 +131,7 @@ bin_emit_kernel(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__
     for (int64_t gb = s0; gb < s1; gb += 32) {
         const int64_t j = gb + lane;
         uint32_t g = 0, cnt = 0;
-        uint2 r = make_uint2(0, 0);
+        uint4 r = make_uint4(0, 0, 0, 0);
         if (j < s1) { g = dvals[j]; cnt = touched[g]; r = rect[g]; }
         uint32_t incl = cnt;
 #pragma unroll
@@ -153,15 +152,14 @@ bin_emit_kernel(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__
                 if (st <= q) lo += step;
             }
             const uint32_t og = __shfl_sync(0xffffffffu, g, lo);
-            const uint32_t orx = __shfl_sync(0xffffffffu, r.x, lo);
-            const uint32_t ory = __shfl_sync(0xffffffffu, r.y, lo);
+            uint4 orr;
+            orr.x = __shfl_sync(0xffffffffu, r.x, lo);
+            orr.y = __shfl_sync(0xffffffffu, r.y, lo);
+            orr.z = __shfl_sync(0xffffffffu, r.z, lo);
+            orr.w = 0;
             const uint32_t ost = __shfl_sync(0xffffffffu, start, lo);
             uint32_t t = 0;
-            if (active) {
-                const uint32_t x0 = orx & 0xffffu, x1 = orx >> 16, y0 = ory & 0xffffu;
-                const uint32_t w = x1 - x0, k = q - ost;
-                t = (y0 + k / w) * (uint32_t)tiles_x + (x0 + k % w);
-            }
+            if (active) t = fp_tile(fp_unpack(orr), q - ost, (uint32_t)tiles_x);
             const uint32_t peers = __match_any_sync(0xffffffffu, active ? t : (0x80000000u | (uint32_t)lane));
             const int leader = __ffs(peers) - 1;
             uint32_t base = 0;
@@ -197,7 +195,7 @@ int64_t bin_chunk(int64_t n) {
 void launch_tile_bin(const Layout& L, char* ws, cudaStream_t stream, StageMark mark) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* dvals = reinterpret_cast<const uint32_t*>(ws + L.off_dvals[0]);
-    const uint2* rect = reinterpret_cast<const uint2*>(ws + L.off_rect);
+    const uint4* rect = reinterpret_cast<const uint4*>(ws + L.off_rect);
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.off_counts);
     uint32_t* chunk_base = reinterpret_cast<uint32_t*>(ws + L.off_chunk_base);

@@ -2,10 +2,11 @@
 // at most kTileFusedMaxTiles tiles): the stable sort by tile id that turns the depth order
 // of Algorithm 1's radix sort (section 3.4) into every tile's front-to-back list.
 //
-//   tile_count_kernel  per-tile copy counts from the splats' tile rectangles: every
-//                      rectangle adds +1/-1/-1/+1 at its four corners of a 2D
-//                      difference array (shared memory per CTA, flushed with one
-//                      global atomic per non-zero entry);
+//   tile_count_kernel  per-tile copy counts from the splats' footprints: every tile
+//                      box adds +1/-1/-1/+1 at its four corners of a 2D difference
+//                      array (shared memory per CTA, flushed with one global atomic per
+//                      non-zero entry), and the trimmed ends of its top and bottom rows
+//                      are taken out again the same way;
 //   tile_scan_kernel   2D prefix sums -> counts; the digit histograms of both radix
 //                      passes and every tile's [start, end) range follow from the
 //                      counts alone (exclusive scan over the tiles in raster order),
@@ -15,27 +16,44 @@
 //                      writes only the Gaussian indices.
 // The result is the (tile, depth, index) order of the 64-bit key sort, bit for bit.
 #include "onesweep.cuh"
+#include "footprint.cuh"
 
 namespace vis {
 
 // ---- per-tile counts ----
+// add v to the 2D difference array for the tile rectangle [x0, x1) x [y0, y1); corners at
+// x1 == tiles_x or y1 == tiles_y only affect tiles outside the grid
+__device__ __forceinline__ void diff_rect(int* diff, uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, int v,
+                                          uint32_t tiles_x, uint32_t tiles_y) {
+    atomicAdd(&diff[y0 * tiles_x + x0], v);
+    if (x1 < tiles_x) atomicAdd(&diff[y0 * tiles_x + x1], -v);
+    if (y1 < tiles_y) {
+        atomicAdd(&diff[y1 * tiles_x + x0], -v);
+        if (x1 < tiles_x) atomicAdd(&diff[y1 * tiles_x + x1], v);
+    }
+}
+
 __global__ void __launch_bounds__(1024)
-tile_count_kernel(const uint2* __restrict__ rect, int64_t n, int tiles_x, int tiles_y, int* __restrict__ gdiff) {
+tile_count_kernel(const uint4* __restrict__ rect, int64_t n, int tiles_x, int tiles_y, int* __restrict__ gdiff) {
     extern __shared__ int diff[];
     const int nt = tiles_x * tiles_y;
+    const uint32_t tx = (uint32_t)tiles_x, ty = (uint32_t)tiles_y;
     for (int i = threadIdx.x; i < nt; i += blockDim.x) diff[i] = 0;
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint2 r = rect[i];
-        const int x0 = r.x & 0xffff, x1 = r.x >> 16, y0 = r.y & 0xffff, y1 = r.y >> 16;
-        if (x1 <= x0 || y1 <= y0) continue;
-        // corners at x1 == tiles_x or y1 == tiles_y only affect tiles outside the grid
-        atomicAdd(&diff[y0 * tiles_x + x0], 1);
-        if (x1 < tiles_x) atomicAdd(&diff[y0 * tiles_x + x1], -1);
-        if (y1 < tiles_y) {
-            atomicAdd(&diff[y1 * tiles_x + x0], -1);
-            if (x1 < tiles_x) atomicAdd(&diff[y1 * tiles_x + x1], 1);
+        const Footprint f = fp_unpack(rect[i]);
+        if (f.x1 <= f.x0 || f.y1 <= f.y0) continue;
+        diff_rect(diff, f.x0, f.x1, f.y0, f.y1, 1, tx, ty);
+        if (f.trims) {   // take the trimmed ends of the top and bottom rows out again
+            const uint32_t lt = f.trims & 0xffu, rt = (f.trims >> 8) & 0xffu;
+            const uint32_t lb = (f.trims >> 16) & 0xffu, rb = f.trims >> 24;
+            if (lt) diff_rect(diff, f.x0, f.x0 + lt, f.y0, f.y0 + 1, -1, tx, ty);
+            if (rt) diff_rect(diff, f.x1 - rt, f.x1, f.y0, f.y0 + 1, -1, tx, ty);
+            if (f.y1 - f.y0 > 1) {
+                if (lb) diff_rect(diff, f.x0, f.x0 + lb, f.y1 - 1, f.y1, -1, tx, ty);
+                if (rb) diff_rect(diff, f.x1 - rb, f.x1, f.y1 - 1, f.y1, -1, tx, ty);
+            }
         }
     }
     __syncthreads();
@@ -119,7 +137,7 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     const int64_t want = (L.n + 16383) / 16384;
     const int64_t lim = sm_count_ts();
     const int grid = (int)(want < 1 ? 1 : (want < lim ? want : lim));
-    tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint2*>(ws + L.off_rect), L.n, L.tiles_x,
+    tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, L.tiles_x,
                                                     L.tiles_y, gdiff);
     tile_scan_kernel<<<1, 1024, smem, stream>>>(gdiff, L.tiles_x, L.tiles_y,
                                                 reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,

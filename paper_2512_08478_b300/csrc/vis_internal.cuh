@@ -111,6 +111,7 @@ struct PrepParams {
     float dilation, alpha_min;
     float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
     int tight_extent;        // 1: tile rect from the tight opacity-aware 3-sigma box
+    int count_survivors;     // block sums count survivors (depth-first sorts), else tiles touched
     float shc[12];           // SH polynomial constants, see sh_constants()
 };
 

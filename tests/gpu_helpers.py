@@ -31,7 +31,7 @@ def gpu_stage_outputs(sc, ws):
     n = sc.n
     rec = ws_view(ws, L.off_rec, 12 * n, np.float32).reshape(n, 3, 4)
     touched = ws_view(ws, L.off_touched, n, np.uint32)
-    rect_p = ws_view(ws, L.off_rect, 2 * n, np.uint32).reshape(n, 2)
+    rect_p = ws_view(ws, L.off_rect, 4 * n, np.uint32).reshape(n, 4)
     depth = ws_view(ws, L.off_depth, n, np.float32)
     ctrl = ws_view(ws, L.off_ctrl, 64, np.uint32)
     m = int(ctrl[0])
@@ -47,7 +47,7 @@ def gpu_stage_outputs(sc, ws):
     f2 = b[:, 2:4].astype(np.float64)
     qscale = 0.5 / np.log(2.0)   # the record's whitening rows are scaled by sqrt(log2(e)/2)
     Q = (f1[:, :, None] * f1[:, None, :] + f2[:, :, None] * f2[:, None, :]) / qscale
-    return dict(valid=(touched > 0).astype(np.int32), touched=touched, rect=rect.astype(np.int32),
+    return dict(valid=(touched > 0).astype(np.int32), touched=touched, rect=rect.astype(np.int32), trims=rect_p[:, 2],
                 zkey=depth, uv=np.stack([u, v], 1), conic=np.stack([Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]], 1),
                 opacity=c[:, 0].astype(np.float64), rgb=c[:, 1:4].astype(np.float64), keys=keys, vals=vals,
                 ranges=ranges, m=m, layout=L)
@@ -69,3 +69,21 @@ def image_parity(gpu_rgb, gpu_alpha, ref, max_abs=2e-4, mean_abs=1e-5, max_ambig
         assert d[ch].mean() <= mean_abs, f"channel {ch} mean-abs {d[ch].mean()}"
     assert da.mean() <= mean_abs, f"alpha mean-abs {da.mean()}"
     return dict(max_abs=float(worst), mean_abs=float(d.mean()), ambiguous=int(amb.sum()))
+
+
+def footprint_tiles(rect, trims, tiles_x):
+    """Tiles (row-major ids) of one footprint: the box [x0, x1) x [y0, y1) whose top and
+    bottom rows drop Lt, Rt and Lb, Rb tiles at their ends (trims = Lt | Rt << 8 | Lb << 16
+    | Rb << 24; a one-row box uses the top trims)."""
+    x0, y0, x1, y1 = (int(v) for v in rect)
+    t = int(trims)
+    lt, rt, lb, rb = t & 255, (t >> 8) & 255, (t >> 16) & 255, (t >> 24) & 255
+    out = []
+    for y in range(y0, y1):
+        a, b = x0, x1
+        if y == y0:
+            a, b = x0 + lt, x1 - rt
+        elif y == y1 - 1:
+            a, b = x0 + lb, x1 - rb
+        out += [y * tiles_x + x for x in range(a, b)]
+    return out

@@ -45,6 +45,9 @@ def test_workspace_queries_and_validation(L):
         assert e.value.status == vis.VIS_ERR_INVALID_ARG
     with pytest.raises(vis.VisError):
         vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(tile=12))
+    with pytest.raises(vis.VisError):
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(tile_extent=3))
+    assert vis.make_opts().tile_extent == 2
     with pytest.raises(vis.VisError) as e:
         vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(digit_bits=4))
     assert e.value.status == vis.VIS_ERR_UNSUPPORTED

@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2512_08478_b300 as vis
 from paper_2512_08478_b300 import synth
-from gpu_helpers import image_parity, render_gpu, ws_view
+from gpu_helpers import footprint_tiles, gpu_stage_outputs, image_parity, render_gpu, ws_view
 
 pytestmark = pytest.mark.gpu
 
@@ -36,9 +36,11 @@ def test_depth_first_equals_tile_depth_sort(tile):
     a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=0))
     b_rgb, b_alpha, sb, wb = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1))
     c_rgb, c_alpha, sc_, wc = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1, tile_extent=0))
+    d_rgb, d_alpha, sd, wd = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=1, tile_extent=1))
     # the tile extent only changes which tiles list a splat, never a pixel
     assert np.array_equal(c_rgb, b_rgb) and np.array_equal(c_alpha, b_alpha)
-    assert vis.vis_check(wb.buf) < vis.vis_check(wc.buf)
+    assert np.array_equal(d_rgb, b_rgb) and np.array_equal(d_alpha, b_alpha)
+    assert vis.vis_check(wb.buf) < vis.vis_check(wd.buf) < vis.vis_check(wc.buf)
     va, ra, La = _sorted_vals_and_ranges(sa, wa)
     vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
     assert La.key_bytes == 8 and Lb.key_bytes == 2 and Lb.sort_mode == 1
@@ -83,6 +85,42 @@ def test_fused_binning_equals_tile_depth_sort(shape):
     assert np.array_equal(va, vb)
     assert np.array_equal(ra, rb)
     assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_exact_row_footprint_covers_every_reachable_pixel(tile):
+    """tile_extent 2: every tile holding a pixel centre where the FP64 oracle's splat
+    passes q <= min(9, 2 ln(opacity / alpha_min)) is in the splat's footprint; the
+    footprint's copies are as many as tiles touched; the image equals tile_extent 0's."""
+    sc = synth.mixture_scene(4000, 23, sh_degree=0, ball_radius=2.0, comp_std=0.6, log_scale_mean=-2.6)
+    cam = synth.look_at((0.5, 1.5, 6.0), (0, 0, 0), 197, 131, 55.0)
+    a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, tile_extent=2))
+    b_rgb, b_alpha, _, _ = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, tile_extent=0))
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
+    g = gpu_stage_outputs(sa, wa)
+    o = oracle.preprocess(sc, cam)
+    L = g["layout"]
+    tx = L.tiles_x
+    px = np.arange(cam.W) + 0.5
+    py = np.arange(cam.H) + 0.5
+    trimmed = 0
+    for i in np.nonzero((g["valid"] == 1) & (o["valid"] == 1))[0]:
+        fp = footprint_tiles(g["rect"][i], g["trims"][i], tx)
+        assert len(fp) == int(g["touched"][i])
+        trimmed += g["trims"][i] != 0
+        x0, y0, x1, y1 = g["rect"][i]
+        u, v = o["uv"][i]
+        a, b, c = o["conic"][i]
+        thr = min(9.0, 2.0 * np.log(o["opacity"][i] * 255.0)) * (1.0 - 1e-5)
+        xs = px[max(0, int(x0 * tile) - tile): min(cam.W, int(x1 * tile) + tile)]
+        ys = py[max(0, int(y0 * tile) - tile): min(cam.H, int(y1 * tile) + tile)]
+        dx = xs[None, :] - u
+        dy = ys[:, None] - v
+        q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+        yy, xx = np.nonzero(q <= thr)
+        need = set(((ys[yy] // tile).astype(int) * tx + (xs[xx] // tile).astype(int)).tolist())
+        assert need <= set(fp), (i, sorted(need - set(fp)))
+    assert trimmed > 100
 
 
 @pytest.mark.parametrize("mode", [1, 2])
