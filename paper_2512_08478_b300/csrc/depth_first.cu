@@ -76,41 +76,66 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
            const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
            const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     if (ctrl->error & kErrCapacity) return;
+    // per splat slot: start of its copies in the warp's run, and its footprint unrolled into
+    // row segments: a = (index, first top-row tile, top width, end of the middle copies),
+    // b = (first middle tile, box width, first bottom-row tile, 0)
     __shared__ uint32_t s_start[kPrepThreads];
-    __shared__ uint32_t s_g[kPrepThreads];
-    __shared__ uint4 s_r[kPrepThreads];
+    __shared__ uint4 s_a[kPrepThreads], s_b[kPrepThreads];
     __shared__ uint32_t warp_tot[kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nv = *num_visible;
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    uint32_t g = 0, cnt = 0;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (j < nv) {   // the copy count follows from the footprint: one gather per splat
-        g = dvals[j];
-        r = rect[g];
-        cnt = fp_count(fp_unpack(r));
+    uint32_t cnt = 0;
+    uint4 sa = make_uint4(0, 0, 0, 0), sb = make_uint4(0, 1, 0, 0);
+    if (j < nv) {   // one gather per splat
+        const uint32_t g = dvals[j];
+        const Footprint f = fp_unpack(rect[g]);
+        cnt = fp_count(f);
+        if (cnt > 0) {
+            const uint32_t tx = (uint32_t)tiles_x, W = f.x1 - f.x0, rows = f.y1 - f.y0;
+            const uint32_t wt = fp_top_width(f);
+            const uint32_t mid = rows > 1 ? (rows - 2) * W : 0;
+            sa = make_uint4(g, f.y0 * tx + f.x0 + (f.trims & 0xffu), wt, wt + mid);
+            sb = make_uint4((f.y0 + 1) * tx + f.x0, W, (f.y1 - 1) * tx + f.x0 + ((f.trims >> 16) & 0xffu), 0u);
+        }
     }
     const uint32_t incl = warp_incl_scan(cnt, lane);
     s_start[threadIdx.x] = incl - cnt;
-    s_g[threadIdx.x] = g;
-    s_r[threadIdx.x] = r;
+    s_a[threadIdx.x] = sa;
+    s_b[threadIdx.x] = sb;
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     uint32_t warp_base = boff[blockIdx.x];
     for (int w = 0; w < warp; ++w) warp_base += warp_tot[w];
     const uint32_t run = warp_tot[warp];
     const int g0 = warp * 32;
+    const uint32_t tx = (uint32_t)tiles_x;
     for (uint32_t q = lane; q < run; q += 32) {
-        // owner: the last slot of the warp whose start is <= q (zero counts share starts)
-        int lo = 0, hi = 31;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_start[g0 + mid] <= q) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t gi = s_g[g0 + lo];
+        // owner: the last slot of the warp whose start is <= q (it has copies: zero counts
+        // share their start with the next slot)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+            if (s_start[g0 + lo + step] <= q) lo += step;
+        const uint4 a = s_a[g0 + lo];
         const uint32_t k = q - s_start[g0 + lo];
-        keys[warp_base + q] = (KT)fp_tile(fp_unpack(s_r[g0 + lo]), k, (uint32_t)tiles_x);
-        vals[warp_base + q] = gi;
+        uint32_t tile;
+        if (k < a.z) {
+            tile = a.y + k;                           // top row
+        } else {
+            const uint4 b = s_b[g0 + lo];
+            if (k < a.w) {                            // middle rows: row = kk / W
+                const uint32_t kk = k - a.z;
+                uint32_t r = (uint32_t)((float)kk * __frcp_rn((float)b.y));
+                if (r * b.y > kk) --r;
+                else if ((r + 1) * b.y <= kk) ++r;
+                tile = b.x + r * tx + (kk - r * b.y);
+            } else {
+                tile = b.z + (k - a.w);               // bottom row
+            }
+        }
+        keys[warp_base + q] = (KT)tile;
+        vals[warp_base + q] = a.x;
     }
 }
 

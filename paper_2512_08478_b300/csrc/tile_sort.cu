@@ -134,8 +134,8 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     }
     const size_t smem = sizeof(int) * (size_t)L.ntiles;
     int* gdiff = reinterpret_cast<int*>(ws + L.off_tdiff);
-    const int64_t want = (L.n + 16383) / 16384;
-    const int64_t lim = sm_count_ts();
+    const int64_t want = (L.n + 4095) / 4096;
+    const int64_t lim = 2 * (int64_t)sm_count_ts();
     const int grid = (int)(want < 1 ? 1 : (want < lim ? want : lim));
     tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, L.tiles_x,
                                                     L.tiles_y, gdiff);
