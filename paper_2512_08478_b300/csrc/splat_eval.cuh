@@ -35,23 +35,36 @@ __device__ __forceinline__ StagedSplat stage_splat(const float4* __restrict__ re
     return s;
 }
 
-// Bit w set iff the exact axis-aligned box of {d : q'(d) <= thr} meets the pixel
-// centres of warp block w. Blocks are 8 px wide and BH px tall, BX per tile row, NW
-// in all; coordinates are relative to the tile centre (half = TILE / 2).
+// Bit w set iff the pixel centres of warp block w may hold a pixel with q'(d) <= thr: the
+// block's rectangle of pixel centres meets both the exact axis-aligned box of the ellipse
+// {d : q'(d) <= thr} and its oriented box, the two slabs |d.f_k| <= sqrt(thr) along the
+// whitening rows (q' = (d.f1)^2 + (d.f2)^2, so every point of the ellipse lies in both).
+// Both tests are padded for float rounding, so no block with such a pixel is dropped.
+// Blocks are 8 px wide and BH px tall, BX per tile row, NW in all; coordinates are
+// relative to the tile centre (half = TILE / 2).
 template <int NW, int BX, int BH>
 __device__ __forceinline__ uint32_t warp_block_mask(const StagedSplat& s, float half) {
     // half extents sqrt(thr (Q'^-1)_xx), sqrt(thr (Q'^-1)_yy) with Q' = F^T F, F = [f1; f2]
     const float det = fabsf(__fmaf_rn(s.a.z, s.b.y, -__fmul_rn(s.a.w, s.b.x)));
-    const float ext = sqrtf(fmaxf(s.b.z, 0.f)) / det;
+    const float rt = sqrtf(fmaxf(s.b.z, 0.f));
+    const float ext = rt / det;
     const float rx = ext * sqrtf(__fmaf_rn(s.a.w, s.a.w, __fmul_rn(s.b.y, s.b.y))) * 1.0001f + 1e-3f;
     const float ry = ext * sqrtf(__fmaf_rn(s.a.z, s.a.z, __fmul_rn(s.b.x, s.b.x))) * 1.0001f + 1e-3f;
+    // slab half-widths of a block in the f1, f2 directions, and the padded slab bound
+    constexpr float hx = 3.5f, hy = 0.5f * BH - 0.5f;
+    const float e1 = fabsf(s.a.z) * hx + fabsf(s.a.w) * hy;
+    const float e2 = fabsf(s.b.x) * hx + fabsf(s.b.y) * hy;
+    const float bound = rt * 1.0001f + 1e-4f;
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float mx = (float)((w % BX) * 8) + 4.f - half;
         const float my = (float)((w / BX) * BH) + 0.5f * BH - half;
-        const float ox = fabsf(s.a.x - mx) - 3.5f, oy = fabsf(s.a.y - my) - (0.5f * BH - 0.5f);
-        if (ox <= rx && oy <= ry) m |= 1u << w;
+        const float dx = mx - s.a.x, dy = my - s.a.y;
+        const float ox = fabsf(dx) - 3.5f, oy = fabsf(dy) - (0.5f * BH - 0.5f);
+        const float p1 = fabsf(__fmaf_rn(dy, s.a.w, __fmul_rn(dx, s.a.z))) - e1;
+        const float p2 = fabsf(__fmaf_rn(dy, s.b.y, __fmul_rn(dx, s.b.x))) - e2;
+        if (ox <= rx && oy <= ry && p1 <= bound && p2 <= bound) m |= 1u << w;
     }
     return m;
 }
