@@ -52,6 +52,9 @@ STAGES_BIN = ["clear", "preprocess", "depth_sort", "bin_count_scan", "bin_emit",
 # passes; no ranges stage
 STAGES_FUSED = ["clear", "preprocess", "depth_sort_and_emit", "tile_counts", "tile_sort_passes", "ranges",
                 "composite"]
+# sort_mode 3 (tile first): stage 2 = per-CTA tile counts and the scan; stage 3 = emission into the
+# tiles; stage 4 = the per-tile sorts in shared memory (and merges of the largest tiles)
+STAGES_TF = ["clear", "preprocess", "tile_counts", "tile_emit", "tile_sorts", "ranges", "composite"]
 
 
 def _peaks():
@@ -254,7 +257,9 @@ def run_ours(args):
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
     update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
     fused = ws.layout().key_bytes == 2
-    names = STAGES_FUSED if fused else {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode]
+    tile_first = ws.layout().sort_mode == 3
+    names = (STAGES_TF if tile_first else STAGES_FUSED if fused
+             else {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode])
     passes = npass.value
 
     # keys per frame averaged over the views used
@@ -289,7 +294,13 @@ def run_ours(args):
     # 2 B key + 4 B value per copy, the last reads those and writes the 4 B value
     # 16-bit keys: every pass reads 2 + 4 B per copy and writes 2 + 4 B, the last only the 4 B value
     tile_bytes = (M * (12 * passes - 2)) if fused else M * (24.0 if args.sort_mode == 0 else 16.0) * passes
-    if dom == "sort_passes" and fused:
+    if tile_first:   # per-tile sorts: 8 B key read, 4 B index written per copy
+        tile_bytes = M * 12.0
+    if dom == "sort_passes" and tile_first:
+        launch_ms = stage_ms["sort_passes"]
+        algo = tile_bytes
+        unit_note = "per-tile sorts in shared memory: 8 B (depth, index) key read, 4 B index written per copy"
+    elif dom == "sort_passes" and fused:
         launch_ms = stage_ms["sort_passes"] / passes
         algo = tile_bytes / passes
         unit_note = ("mean over the tile passes: 2 B key + 4 B value read and written per copy, "
@@ -342,7 +353,10 @@ def run_ours(args):
     # every HBM-bound stage against the copy peak (the spec bar is >= 60% for preprocess and sort)
     hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
                                      achieved_gbs=round(bytes_pre / (stage_ms["preprocess"] * 1e-3) / 1e9, 1))}
-    if args.sort_mode != 2 and passes > 0:
+    if tile_first:
+        hbm_stages["tile_sorts"] = dict(bytes=int(tile_bytes), ms=round(stage_ms["sort_passes"], 4),
+                                        achieved_gbs=round(tile_bytes / (stage_ms["sort_passes"] * 1e-3) / 1e9, 1))
+    elif args.sort_mode != 2 and passes > 0:
         key = "tile_sort_pass"
         b_st = tile_bytes / passes
         ms_st = stage_ms["sort_passes"] / passes
@@ -360,7 +374,7 @@ def run_ours(args):
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk_summary, e2e=e2e,
-                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes, 2: 11 + kDP}[args.sort_mode]
+                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes, 2: 11 + kDP, 3: 16}[args.sort_mode]
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)),
                 roofline=roof, hbm_stages=hbm_stages,
                 stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
@@ -580,7 +594,7 @@ def main():
     ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch"])
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1, 2, 3],
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
                          "2: depth sort then counting binning (default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -84,7 +84,12 @@ typedef struct {
  *                  first, the tile keys are 16-bit and the last pass writes only the
  *                  Gaussian indices;
  *              2 = depth first, then a stable counting binning into tiles (no tile keys;
- *                  up to 29056 tiles, beyond that mode 1 is used).
+ *                  up to 29056 tiles, beyond that mode 1 is used);
+ *              3 = tile first: each copy is placed in its tile's range (per-tile counts
+ *                  first), then every tile's (depth bits << 32 | index) keys are sorted in
+ *                  shared memory (bitonic network; tiles above 16384 copies as runs that are
+ *                  then merged). No global sort. Up to 51200 tiles (beyond that mode 1 is
+ *                  used) and 16384 << 8 copies per tile (VIS_ERR_UNSUPPORTED beyond).
  *              All give the same order bit for bit; 1 moves about a quarter of the bytes
  *              of 0.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
@@ -139,8 +144,9 @@ typedef struct {
     size_t off_tfinal;       /* float[H*W] final transmittance */
     size_t off_last;         /* int32[H*W] 1 + position, in the sorted key list, of the last composited splat (0 if none) */
     size_t off_g2;           /* float[n][9] screen-space gradients (backward scratch) */
-    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1
-                                beyond 51200 tiles); 2: 16-bit tile id (sort_mode 1); 0: none (2) */
+    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0) or (depth bits << 32) |
+                                index (sort_mode 3); 4: tile id (sort_mode 1 beyond 51200 tiles);
+                                2: 16-bit tile id (sort_mode 1); 0: none (2) */
     int sort_mode;
 } vis_ws_layout;
 

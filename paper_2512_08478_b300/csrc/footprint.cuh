@@ -60,4 +60,36 @@ __host__ __device__ __forceinline__ uint32_t fp_tile(const Footprint& f, uint32_
     return (f.y1 - 1) * tiles_x + f.x0 + ((f.trims >> 16) & 0xffu) + k;
 }
 
+#ifdef __CUDACC__
+// add v to a 2D difference array over a tiles_x x tiles_y grid for the tile rectangle
+// [x0, x1) x [y0, y1); corners at x1 == tiles_x or y1 == tiles_y only affect tiles outside
+// the grid
+__device__ __forceinline__ void diff_rect(int* diff, uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, int v,
+                                          uint32_t tiles_x, uint32_t tiles_y) {
+    atomicAdd(&diff[y0 * tiles_x + x0], v);
+    if (x1 < tiles_x) atomicAdd(&diff[y0 * tiles_x + x1], -v);
+    if (y1 < tiles_y) {
+        atomicAdd(&diff[y1 * tiles_x + x0], -v);
+        if (x1 < tiles_x) atomicAdd(&diff[y1 * tiles_x + x1], v);
+    }
+}
+
+// add one footprint (its box, then its trimmed row ends taken out again) to a 2D difference
+// array, so that the array's 2D prefix sums count every copy once
+__device__ __forceinline__ void fp_add_to_diff(int* diff, const Footprint& f, uint32_t tiles_x, uint32_t tiles_y) {
+    if (f.x1 <= f.x0 || f.y1 <= f.y0) return;
+    diff_rect(diff, f.x0, f.x1, f.y0, f.y1, 1, tiles_x, tiles_y);
+    if (f.trims) {
+        const uint32_t lt = f.trims & 0xffu, rt = (f.trims >> 8) & 0xffu;
+        const uint32_t lb = (f.trims >> 16) & 0xffu, rb = f.trims >> 24;
+        if (lt) diff_rect(diff, f.x0, f.x0 + lt, f.y0, f.y0 + 1, -1, tiles_x, tiles_y);
+        if (rt) diff_rect(diff, f.x1 - rt, f.x1, f.y0, f.y0 + 1, -1, tiles_x, tiles_y);
+        if (f.y1 - f.y0 > 1) {
+            if (lb) diff_rect(diff, f.x0, f.x0 + lb, f.y1 - 1, f.y1, -1, tiles_x, tiles_y);
+            if (rb) diff_rect(diff, f.x1 - rb, f.x1, f.y1 - 1, f.y1, -1, tiles_x, tiles_y);
+        }
+    }
+}
+#endif
+
 }  // namespace vis

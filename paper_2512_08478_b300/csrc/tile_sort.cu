@@ -21,18 +21,6 @@
 namespace vis {
 
 // ---- per-tile counts ----
-// add v to the 2D difference array for the tile rectangle [x0, x1) x [y0, y1); corners at
-// x1 == tiles_x or y1 == tiles_y only affect tiles outside the grid
-__device__ __forceinline__ void diff_rect(int* diff, uint32_t x0, uint32_t x1, uint32_t y0, uint32_t y1, int v,
-                                          uint32_t tiles_x, uint32_t tiles_y) {
-    atomicAdd(&diff[y0 * tiles_x + x0], v);
-    if (x1 < tiles_x) atomicAdd(&diff[y0 * tiles_x + x1], -v);
-    if (y1 < tiles_y) {
-        atomicAdd(&diff[y1 * tiles_x + x0], -v);
-        if (x1 < tiles_x) atomicAdd(&diff[y1 * tiles_x + x1], v);
-    }
-}
-
 __global__ void __launch_bounds__(1024)
 tile_count_kernel(const uint4* __restrict__ rect, int64_t n, int tiles_x, int tiles_y, int* __restrict__ gdiff) {
     extern __shared__ int diff[];
@@ -42,19 +30,7 @@ tile_count_kernel(const uint4* __restrict__ rect, int64_t n, int tiles_x, int ti
     __syncthreads();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const Footprint f = fp_unpack(rect[i]);
-        if (f.x1 <= f.x0 || f.y1 <= f.y0) continue;
-        diff_rect(diff, f.x0, f.x1, f.y0, f.y1, 1, tx, ty);
-        if (f.trims) {   // take the trimmed ends of the top and bottom rows out again
-            const uint32_t lt = f.trims & 0xffu, rt = (f.trims >> 8) & 0xffu;
-            const uint32_t lb = (f.trims >> 16) & 0xffu, rb = f.trims >> 24;
-            if (lt) diff_rect(diff, f.x0, f.x0 + lt, f.y0, f.y0 + 1, -1, tx, ty);
-            if (rt) diff_rect(diff, f.x1 - rt, f.x1, f.y0, f.y0 + 1, -1, tx, ty);
-            if (f.y1 - f.y0 > 1) {
-                if (lb) diff_rect(diff, f.x0, f.x0 + lb, f.y1 - 1, f.y1, -1, tx, ty);
-                if (rb) diff_rect(diff, f.x1 - rb, f.x1, f.y1 - 1, f.y1, -1, tx, ty);
-            }
-        }
+        fp_add_to_diff(diff, fp_unpack(rect[i]), tx, ty);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nt; i += blockDim.x)

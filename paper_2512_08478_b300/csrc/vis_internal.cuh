@@ -34,6 +34,7 @@ constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit c
 // ctrl->error bits
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrTileOverflow = 4u;   // tile-first: a tile holds more copies than it can merge
 
 // Look-back spin limit, in polls (each poll ~ a few hundred ns with the backoff);
 // far beyond any legitimate wait, it only bounds a wait that can never end.
@@ -43,6 +44,8 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kSortTileDepth = 0;   // one sort of 64-bit (tile << 32 | depth) keys
 constexpr int kSortDepthFirst = 1;  // depth sort of the surviving splats, then a tile sort
 constexpr int kSortDepthBin = 2;    // depth sort, then stable counting binning into tiles
+constexpr int kSortTileFirst = 3;   // copies placed in their tiles, each tile sorted in shared memory
+constexpr int kTfMergeRounds = 8;   // tile-first: runs of 16384 copies merged; tiles up to 16384 << 8
 // tile counts that the binning's per-warp shared-memory counters hold (8 or 4 warps)
 constexpr int kBinMaxTiles8 = 14528;
 constexpr int kBinMaxTiles4 = 29056;
@@ -69,6 +72,9 @@ struct Layout {
     // depth-first mode with the counts-first tile sort of 16-bit keys (tile_sort.cu)
     bool tile_fused = false;
     size_t off_tdiff = 0;
+    // tile-first mode (tile_first.cu)
+    int64_t tf_grid = 0, tf_chunk = 0;
+    size_t off_tf_total = 0, off_tf_within = 0, off_tf_start = 0, off_tf_lists = 0;
     // depth-bin mode only
     int64_t bin_chunk = 0, bin_chunks = 0;
     size_t off_counts = 0, off_chunk_base = 0, off_totals = 0, off_tile_start = 0;
@@ -90,7 +96,8 @@ struct Ctrl {
     uint32_t pad0;
     unsigned long long pair_tests;           // compositor statistics (collect_stats only)
     unsigned long long hits;
-    uint32_t reserved[40];
+    uint32_t tf_count[4];                    // tile-first: sizes of the per-class tile work lists
+    uint32_t reserved[36];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
 
@@ -217,6 +224,10 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
 // Counts-first tile sort of sort_mode 1 (tile_sort.cu): per-tile counts -> digit histograms
 // and ranges; then the passes over the 16-bit tile keys emitted in depth order.
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream);
+// Tile-first ordering (sort_mode 3): counts, emission into the tiles, per-tile sorts; marks
+// mark_index after the counts and mark_index + 1 after the emission.
+void launch_tile_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
+int64_t tf_grid(int64_t n, int64_t ntiles);
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream);
 
 void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,

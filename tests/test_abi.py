@@ -66,7 +66,11 @@ def test_workspace_queries_and_validation(L):
     big = vis.vis_workspace_layout(10_000, 2048, 1024, 10 ** 9, vis.make_opts(sort_mode=2, tile=8))
     assert big.sort_mode == 1     # 32768 tiles: too many for the binning's counters -> tile sort
     with pytest.raises(vis.VisError):
-        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=3))
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=4))
+    tfl = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=3))
+    assert tfl.sort_mode == 3 and tfl.key_bytes == 8 and tfl.sort_passes == 0 and tfl.sorted_buffer == 0
+    tfw = vis.vis_workspace_layout(10_000, 3840, 2160, 10 ** 9, vis.make_opts(sort_mode=3, tile=8))
+    assert tfw.sort_mode == 1     # 129600 tiles: too many for the per-tile counters -> depth first
     assert vis.vis_sort_workspace_size(0, 45) > 0
     with pytest.raises(vis.VisError):
         vis.vis_sort_workspace_size(10, 65)
