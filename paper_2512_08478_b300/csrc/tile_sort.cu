@@ -37,41 +37,69 @@ tile_count_kernel(const uint4* __restrict__ rect, int64_t n, int tiles_x, int ti
         if (diff[i]) atomicAdd(&gdiff[i], diff[i]);
 }
 
+// inclusive warp scan of one value per lane
+__device__ __forceinline__ int warp_scan_incl(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
 // One CTA of 1024 threads. hist: [2][256] digit histograms (low byte, high byte of the
-// tile id); ranges: [start, end) per tile, (0, 0) for an empty tile.
+// tile id); ranges: [start, end) per tile, (0, 0) for an empty tile. The 2D prefix sums run
+// one warp per row, then one warp per column, 32 entries at a time with warp scans; the
+// histograms are plain sums (low byte: tiles d, d + 256, ...; high byte: a block of 256).
 __global__ void __launch_bounds__(1024)
 tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32_t* __restrict__ hist,
                  uint2* __restrict__ ranges) {
     extern __shared__ int P[];
-    __shared__ uint32_t s_hist[2 * kRadix];
     __shared__ uint32_t s_warp[32];
     const int nt = tiles_x * tiles_y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < nt; i += 1024) P[i] = gdiff[i];
-    for (int i = tid; i < 2 * kRadix; i += 1024) s_hist[i] = 0;
     __syncthreads();
-    for (int y = tid; y < tiles_y; y += 1024) {   // prefix along each row
-        int run = 0;
-        for (int x = 0; x < tiles_x; ++x) { run += P[y * tiles_x + x]; P[y * tiles_x + x] = run; }
+    for (int y = warp; y < tiles_y; y += 32) {   // prefix along each row
+        int carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            const int v = x < tiles_x ? P[y * tiles_x + x] : 0;
+            const int incl = warp_scan_incl(v, lane) + carry;
+            if (x < tiles_x) P[y * tiles_x + x] = incl;
+            carry = __shfl_sync(0xffffffffu, incl, 31);
+        }
     }
     __syncthreads();
-    for (int x = tid; x < tiles_x; x += 1024) {   // then along each column: counts
-        int run = 0;
-        for (int y = 0; y < tiles_y; ++y) { run += P[y * tiles_x + x]; P[y * tiles_x + x] = run; }
+    for (int x = warp; x < tiles_x; x += 32) {   // then along each column: counts
+        int carry = 0;
+        for (int y0 = 0; y0 < tiles_y; y0 += 32) {
+            const int y = y0 + lane;
+            const int v = y < tiles_y ? P[y * tiles_x + x] : 0;
+            const int incl = warp_scan_incl(v, lane) + carry;
+            if (y < tiles_y) P[y * tiles_x + x] = incl;
+            carry = __shfl_sync(0xffffffffu, incl, 31);
+        }
     }
     __syncthreads();
+    // digit histograms of the two passes
+    if (tid < kRadix) {
+        uint32_t h = 0;
+        for (int t = tid; t < nt; t += kRadix) h += (uint32_t)P[t];
+        hist[tid] = h;
+    }
+    for (int d = warp; d < kRadix; d += 32) {
+        uint32_t h = 0;
+        for (int t = d * kRadix + lane; t < min(nt, (d + 1) * kRadix); t += 32) h += (uint32_t)P[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+        if (lane == 0) hist[kRadix + d] = h;
+    }
     // exclusive scan of the counts in raster order: thread tid owns tiles [tid*per, (tid+1)*per)
     const int per = (nt + 1023) / 1024;
     const int t0 = tid * per, t1 = min(nt, t0 + per);
     uint32_t local = 0;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t c = (uint32_t)P[t];
-        local += c;
-        if (c) {
-            atomicAdd(&s_hist[t & (kRadix - 1)], c);
-            atomicAdd(&s_hist[kRadix + ((t >> kRadixBits) & (kRadix - 1))], c);
-        }
-    }
+    for (int t = t0; t < t1; ++t) local += (uint32_t)P[t];
     uint32_t incl = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -88,7 +116,6 @@ tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32
         ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
         start += c;
     }
-    for (int i = tid; i < 2 * kRadix; i += 1024) hist[i] = s_hist[i];
 }
 
 static int sm_count_ts() {
