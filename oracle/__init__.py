@@ -103,8 +103,19 @@ def preprocess(scene, cam, opts=None):
     return out
 
 
-def render_pixels(prep, px, py, bg=(0.0, 0.0, 0.0), opts=None):
+def _zlim(depth, count):
+    """float32 depth limits (or None): splats deeper than a pixel's limit are not composited."""
+    if depth is None:
+        return None, None
+    z = np.ascontiguousarray(np.asarray(depth, np.float32).reshape(-1))
+    if z.shape[0] != count:
+        raise ValueError("depth buffer has the wrong size")
+    return z, _p(z)
+
+
+def render_pixels(prep, px, py, bg=(0.0, 0.0, 0.0), opts=None, depth=None):
     """Brute-force definition at the given pixels: every valid splat is a candidate.
+    depth: optional float32 [P] depth limits (depth-buffer-aware compositing).
 
     Returns dict rgb [P,3], alpha [P], T [P], n_contrib [P], ambiguous [P].
     """
@@ -114,25 +125,28 @@ def render_pixels(prep, px, py, bg=(0.0, 0.0, 0.0), opts=None):
     P = px.shape[0]
     out = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), T=np.zeros(P),
                n_contrib=np.zeros(P, np.int32), ambiguous=np.zeros(P, np.int32))
+    zl, zl_p = _zlim(depth, P)
     _L().orc_render_pixels(C.c_int64(n), _p(prep["valid"]), _p(prep["uv"]), _p(prep["conic"]),
                            _p(prep["opacity"]), _p(prep["rgb"]), _p(prep["zkey"]), C.c_int64(P),
-                           _p(px), _p(py), _p(_f64(bg)), _p(opts_array(opts)),
+                           _p(px), _p(py), _p(_f64(bg)), _p(opts_array(opts)), zl_p,
                            _p(out["rgb"]), _p(out["alpha"]), _p(out["T"]), _p(out["n_contrib"]),
                            _p(out["ambiguous"]))
     return out
 
 
-def render_bruteforce(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None):
+def render_bruteforce(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, depth=None):
     """Whole image by the brute-force definition; rgb returned planar [3,H,W]."""
     ys, xs = np.mgrid[0:H, 0:W]
-    r = render_pixels(prep, xs.ravel(), ys.ravel(), bg, opts)
+    r = render_pixels(prep, xs.ravel(), ys.ravel(), bg, opts, depth)
     return dict(rgb=r["rgb"].T.reshape(3, H, W).copy(), alpha=r["alpha"].reshape(H, W),
                 T=r["T"].reshape(H, W), n_contrib=r["n_contrib"].reshape(H, W),
                 ambiguous=r["ambiguous"].reshape(H, W))
 
 
-def render_tiled(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
+def render_tiled(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None, depth=None):
     """Tile-binned render (same result as the brute force; faster on big scenes).
+    depth: optional float32 [H,W] depth buffer (view depth); a splat deeper than a
+    pixel's value is not composited there (tested, never written).
 
     tile_mask: optional uint8 [tiles_y * tiles_x]; only those tiles are computed
     (other pixels are NaN in rgb/alpha/T and -1 in n_contrib/ambiguous).
@@ -145,9 +159,10 @@ def render_tiled(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
     if tile_mask is not None:
         tile_mask = np.ascontiguousarray(tile_mask, np.uint8)
         mask_p = _p(tile_mask)
+    zl, zl_p = _zlim(depth, H * W)
     rc = _L().orc_render_tiled(C.c_int64(n), _p(prep["valid"]), _p(prep["uv"]), _p(prep["conic"]),
                                _p(prep["opacity"]), _p(prep["rgb"]), _p(prep["zkey"]), _p(prep["rect"]),
-                               C.c_int(W), C.c_int(H), _p(_f64(bg)), _p(opts_array(opts)), mask_p,
+                               C.c_int(W), C.c_int(H), _p(_f64(bg)), _p(opts_array(opts)), mask_p, zl_p,
                                _p(out["rgb"]), _p(out["alpha"]), _p(out["T"]), _p(out["n_contrib"]),
                                _p(out["ambiguous"]))
     if rc != 0:
@@ -155,10 +170,10 @@ def render_tiled(prep, W, H, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
     return out
 
 
-def render(scene, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None):
-    """Preprocess + tile-binned render of one view."""
+def render(scene, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None, depth=None):
+    """Preprocess + tile-binned render of one view (depth: optional [H,W] depth buffer)."""
     prep = preprocess(scene, cam, opts)
-    return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask), prep
+    return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask, depth), prep
 
 
 def duplicate(prep, tiles_x, cap=None):
@@ -219,11 +234,12 @@ def covariance(log_scales, quats):
     return out.reshape(n, 3, 3)
 
 
-def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False):
+def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False, depth=None):
     """FP64 gradient of L = sum(gC * rgb) + sum(gA * alpha) w.r.t. all Gaussian inputs.
 
-    gC: [3,H,W], gA: [H,W]. Returns dict means [N,3], log_scales [N,3], quats [N,4],
-    opacity_logits [N], sh [N,K,3] (and g2 [N,9] screen-space gradients if asked).
+    gC: [3,H,W], gA: [H,W]; depth: optional [H,W] depth buffer (as in render). Returns dict
+    means [N,3], log_scales [N,3], quats [N,4], opacity_logits [N], sh [N,K,3] (and g2
+    [N,9] screen-space gradients if asked).
     """
     n = scene["means"].shape[0]
     K = (scene["sh_degree"] + 1) ** 2
@@ -231,9 +247,10 @@ def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False):
                opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
     g2 = np.zeros((n, 9))
     arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    zl, zl_p = _zlim(depth, cam.W * cam.H)   # zl keeps the buffer alive through the call
     rc = _L().orc_adjoint(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]),
                           _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
-                          _p(_f64(bg)), _p(_f64(gC)), _p(_f64(gA)),
+                          _p(_f64(bg)), _p(_f64(gC)), _p(_f64(gA)), zl_p,
                           *[_p(out[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")],
                           _p(g2))
     if rc != 0:

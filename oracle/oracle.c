@@ -358,6 +358,8 @@ static int cmp_ord(const void* a, const void* b) {
 #define AMB_Q_REL     (8.0 * 2.5e-6)
 #define AMB_ALPHA_REL (8.0 * 1e-6)
 #define AMB_T_REL     (8.0 * 1e-5)
+/* the float32 renderer's view depth may differ from zkey (float32 of the FP64 depth) by an ulp */
+#define AMB_Z_REL     (8.0 * 1.2e-7)
 
 typedef struct {
     double rgb[3], alpha, T;
@@ -366,13 +368,21 @@ typedef struct {
     int ambiguous;
 } pix_out_t;
 
-/* Composite pixel centre (pcx, pcy) over `list` (already ordered). */
+/* Composite pixel centre (pcx, pcy) over `list` (already ordered). zlim: the pixel's depth
+ * limit (depth-buffer-aware compositing, a caller-supplied depth buffer tested without
+ * writing, section 3.4): a splat whose view depth zkey exceeds it is not composited there;
+ * +infinity when there is no depth buffer. */
 static void composite_pixel(const prep_t* pp, const ord_t* list, int64_t len, double pcx, double pcy,
-                            const double bg[3], const opts_t* op, pix_out_t* out) {
+                            double zlim, const double bg[3], const opts_t* op, pix_out_t* out) {
     double T = 1.0, C[3] = {0, 0, 0};
     int n_contrib = 0, last_pos = 0, amb = 0;
     for (int64_t j = 0; j < len; ++j) {
         int64_t i = list[j].idx;
+        if (isfinite(zlim)) {
+            const double z = (double)list[j].zkey;
+            if (fabs(z - zlim) <= AMB_Z_REL * fabs(zlim)) amb = 1;
+            if (z > zlim) continue;
+        }
         double dx = pcx - pp->uv[2 * i], dy = pcy - pp->uv[2 * i + 1];
         double a = pp->conic[3 * i], b = pp->conic[3 * i + 1], c = pp->conic[3 * i + 2];
         double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
@@ -418,6 +428,7 @@ static prep_t prep_view(const int* valid, const double* uv, const double* conic,
 int orc_render_pixels(int64_t n, const int* valid, const double* uv, const double* conic,
                       const double* opacity, const double* rgb, const float* zkey,
                       int64_t P, const int* px, const int* py, const double* bg, const double* opts6,
+                      const float* zlim /* [P] or NULL */,
                       double* out_rgb, double* out_alpha, double* out_T, int* out_ncontrib,
                       int* out_ambig) {
     opts_t op; load_opts(opts6, &op);
@@ -432,7 +443,7 @@ int orc_render_pixels(int64_t n, const int* valid, const double* uv, const doubl
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t p = 0; p < P; ++p) {
         pix_out_t o;
-        composite_pixel(&pp, all, nv, px[p] + 0.5, py[p] + 0.5, bg, &op, &o);
+        composite_pixel(&pp, all, nv, px[p] + 0.5, py[p] + 0.5, zlim ? (double)zlim[p] : INFINITY, bg, &op, &o);
         for (int ch = 0; ch < 3; ++ch) out_rgb[3 * p + ch] = o.rgb[ch];
         out_alpha[p] = o.alpha;
         out_T[p] = o.T;
@@ -502,6 +513,7 @@ static void free_bins(bins_t* b) { free(b->start); free(b->items); }
 int orc_render_tiled(int64_t n, const int* valid, const double* uv, const double* conic,
                      const double* opacity, const double* rgb, const float* zkey, const int* rect,
                      int W, int H, const double* bg, const double* opts6, const uint8_t* tile_mask,
+                     const float* zlim /* [H,W] or NULL */,
                      double* out_rgb, double* out_alpha, double* out_T, int* out_ncontrib,
                      int* out_ambig) {
     opts_t op; load_opts(opts6, &op);
@@ -518,9 +530,9 @@ int orc_render_tiled(int64_t n, const int* valid, const double* uv, const double
         for (int y = ty * op.tile; y < (ty + 1) * op.tile && y < H; ++y)
             for (int x = tx * op.tile; x < (tx + 1) * op.tile && x < W; ++x) {
                 pix_out_t o;
-                composite_pixel(&pp, b.items + b.start[t], b.start[t + 1] - b.start[t], x + 0.5, y + 0.5,
-                                bg, &op, &o);
                 int64_t pix = (int64_t)y * W + x;
+                composite_pixel(&pp, b.items + b.start[t], b.start[t + 1] - b.start[t], x + 0.5, y + 0.5,
+                                zlim ? (double)zlim[pix] : INFINITY, bg, &op, &o);
                 for (int ch = 0; ch < 3; ++ch) out_rgb[ch * HW + pix] = o.rgb[ch];
                 out_alpha[pix] = o.alpha;
                 out_T[pix] = o.T;
@@ -800,6 +812,7 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
 int orc_adjoint(int64_t n, const double* means, const double* log_scales, const double* quats,
                 const double* logits, const double* sh, int deg, const double* cam17, int W, int H,
                 const double* opts6, const double* bg, const double* gC, const double* gA,
+                const float* zlim /* [H,W] depth buffer or NULL */,
                 double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
                 double* d_sh, double* g2_out /* [n,9] or NULL */) {
     if (deg < 0 || deg > 3) return 1;
@@ -848,11 +861,13 @@ int orc_adjoint(int64_t n, const double* means, const double* log_scales, const 
             for (int yy = ty * op.tile; yy < (ty + 1) * op.tile && yy < H; ++yy)
                 for (int xx = tx * op.tile; xx < (tx + 1) * op.tile && xx < W; ++xx) {
                     double pcx = xx + 0.5, pcy = yy + 0.5;
-                    /* forward, recording contributors */
+                    const double zl = zlim ? (double)zlim[(int64_t)yy * W + xx] : INFINITY;
+                    /* forward, recording contributors (the same decisions as composite_pixel) */
                     double T = 1.0;
                     int64_t nc = 0;
                     for (int64_t j = 0; j < len; ++j) {
                         int64_t i = list[j].idx;
+                        if ((double)list[j].zkey > zl) continue;
                         double dx = pcx - pp.uv[2 * i], dy = pcy - pp.uv[2 * i + 1];
                         double a = pp.conic[3 * i], bb = pp.conic[3 * i + 1], c = pp.conic[3 * i + 2];
                         double q = a * dx * dx + 2.0 * bb * dx * dy + c * dy * dy;

@@ -16,17 +16,17 @@ from paper_2512_08478_b300 import synth
 FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
 
 
-def _loss(scene, cam, gC, gA, bg):
-    img, _ = oracle.render(scene, cam, bg)
+def _loss(scene, cam, gC, gA, bg, depth=None):
+    img, _ = oracle.render(scene, cam, bg, depth=depth)
     return float(np.sum(gC * img["rgb"]) + np.sum(gA * img["alpha"]))
 
 
-def _fd(scene, cam, gC, gA, bg, field, idx, h):
+def _fd(scene, cam, gC, gA, bg, field, idx, h, depth=None):
     vals = []
     for s in (+1, -1):
         sc = {k: (np.array(v, np.float64, copy=True) if k in FIELDS else v) for k, v in scene.items()}
         sc[field].reshape(-1)[idx] += s * h
-        vals.append(_loss(sc, cam, gC, gA, bg))
+        vals.append(_loss(sc, cam, gC, gA, bg, depth))
     return (vals[0] - vals[1]) / (2 * h)
 
 
@@ -53,4 +53,37 @@ def test_adjoint_matches_central_differences(bg):
             checked += 1
             assert abs(f1 - g[idx]) <= 1e-6 * abs(f1) + 1e-6 * scale, (field, idx, f1, g[idx])
     assert checked > 900
+    assert excluded < 0.05 * (checked + excluded), (checked, excluded)
+
+
+def test_adjoint_with_depth_buffer_matches_central_differences():
+    """The same check with a slanted depth buffer through the scene (depth-buffer-aware
+    compositing): splats behind a pixel's depth value take no part there, in the forward
+    and in the adjoint alike."""
+    scene, cam = synth.fd_scene()
+    scene = {k: (v.astype(np.float64) if k in FIELDS else v) for k, v in scene.items()}
+    rng = np.random.default_rng(23)
+    gC = rng.standard_normal((3, cam.H, cam.W))
+    gA = rng.standard_normal((cam.H, cam.W))
+    xs = np.arange(cam.W)[None, :].repeat(cam.H, 0)
+    depth = (3.75 + 0.5 * xs / cam.W).astype(np.float32)
+    bg = (0.2, 0.4, 0.6)
+    grads = oracle.adjoint(scene, cam, gC, gA, bg, depth=depth)
+    free = oracle.adjoint(scene, cam, gC, gA, bg)
+    assert not np.allclose(grads["means"], free["means"])   # the buffer does cut the scene
+    checked = excluded = 0
+    for field in FIELDS:
+        g = grads[field].reshape(-1)
+        n = g.shape[0]
+        idxs = rng.choice(n, min(n, 120), replace=False)
+        scale = np.max(np.abs(g)) + 1e-30
+        for idx in idxs:
+            f1 = _fd(scene, cam, gC, gA, bg, field, idx, 1e-6, depth)
+            f2 = _fd(scene, cam, gC, gA, bg, field, idx, 1e-5, depth)
+            if abs(f1 - f2) > 1e-4 * max(abs(f1), abs(f2)) + 1e-7 * scale:
+                excluded += 1
+                continue
+            checked += 1
+            assert abs(f1 - g[idx]) <= 1e-6 * abs(f1) + 1e-6 * scale, (field, idx, f1, g[idx])
+    assert checked > 300
     assert excluded < 0.05 * (checked + excluded), (checked, excluded)

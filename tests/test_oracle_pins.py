@@ -97,6 +97,43 @@ def test_two_coaxial_gaussians_closed_form_and_order():
         np.testing.assert_allclose(img["alpha"], 1 - (1 - a1) * (1 - a2), atol=1e-12)
 
 
+def test_depth_buffer_closed_forms():
+    """Depth-buffer-aware compositing (a splat deeper than the pixel's depth value is not
+    composited there): a plane between two coaxial Gaussians leaves the front one's closed
+    form over the background; +inf everywhere changes nothing; a plane in front of both
+    leaves the background; a plane that covers half the image splits it accordingly."""
+    W, H, d = 40, 40, 5.0
+    cam = synth.look_at((0, 0, d), (0, 0, 0), W, H, 60.0)
+    g_front = _one_gaussian_scene((0, 0, 1.0), 0.06, (1, 0, 0, 0), 0.5, (1.0, 0.0, 0.2))
+    g_back = _one_gaussian_scene((0, 0, -1.0), 0.12, (1, 0, 0, 0), 2.0, (0.1, 0.8, 0.3))
+    sc = _stack([g_back, g_front])
+    bg = np.array([0.3, 0.3, 0.6])
+    ys, xs = np.mgrid[0:H, 0:W]
+    rho2 = (xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2
+    s = float(np.exp(np.float64(g_front["log_scales"][0, 0])))
+    var = (cam.fx * s / (d - 1.0)) ** 2 + DIL
+    o = 1 / (1 + math.exp(-float(g_front["opacity_logits"][0])))
+    a1 = np.minimum(float(np.float32(0.99)), o * np.exp(-rho2 / (2 * var)))
+    a1 = np.where((rho2 / var <= 9) & (a1 >= np.float32(1 / 255)), a1, 0.0)
+    c1 = _dc_colour(g_front, 0)
+    front_only = c1[:, None, None] * a1 + bg[:, None, None] * (1 - a1)
+    plane = np.full((H, W), d, np.float32)                    # between the two (depths 4 and 6)
+    img, _ = oracle.render(sc, cam, bg, depth=plane)
+    np.testing.assert_allclose(img["rgb"], front_only, atol=1e-12)
+    np.testing.assert_allclose(img["alpha"], a1, atol=1e-12)
+    bf = oracle.render_bruteforce(oracle.preprocess(sc, cam), W, H, bg, depth=plane)
+    np.testing.assert_allclose(bf["rgb"], front_only, atol=1e-12)
+    free, _ = oracle.render(sc, cam, bg)
+    inf, _ = oracle.render(sc, cam, bg, depth=np.full((H, W), np.inf, np.float32))
+    assert np.array_equal(inf["rgb"], free["rgb"]) and np.array_equal(inf["alpha"], free["alpha"])
+    wall, _ = oracle.render(sc, cam, bg, depth=np.full((H, W), 1.0, np.float32))
+    assert np.all(wall["rgb"] == bg[:, None, None]) and np.all(wall["alpha"] == 0.0)
+    half = np.where(xs < W // 2, np.float32(1.0), np.float32(np.inf)).astype(np.float32)
+    split, _ = oracle.render(sc, cam, bg, depth=half)
+    assert np.all(split["rgb"][:, :, : W // 2] == bg[:, None, None])
+    assert np.array_equal(split["rgb"][:, :, W // 2:], free["rgb"][:, :, W // 2:])
+
+
 def test_early_stop_excludes_the_stopping_splat():
     # Three Gaussians stacked on the optical axis, seen at the pixel whose centre is
     # the principal point (G = 1 there): alpha = 0.99 (clamped), then 0.95, 0.95.
