@@ -216,6 +216,28 @@ VIS_API vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam,
                                float* d_means, float* d_log_scales, float* d_quats,
                                float* d_opacity_logits, float* d_sh, void* stream);
 
+/* Depth-buffer-aware compositing (section 3.4: the splats are drawn against the depth of
+ * opaque geometry with the depth test on and depth writes off). As vis_render, plus
+ *  depth   device float32 [H,W] (row-major, 16-byte aligned, not modified): per pixel,
+ *          a view depth (camera-space z, the units of the splat depths); a splat whose
+ *          view depth exceeds it is not composited at that pixel (a value of +inf tests
+ *          nothing, so an all-inf buffer gives vis_render's image bit for bit).
+ * The buffer is read by the compositor only; sorting and tile lists are unchanged.
+ * Errors: as vis_render, and VIS_ERR_INVALID_ARG for a null or misaligned depth. */
+VIS_API vis_status vis_render_depth(vis_scene_t scene, const vis_camera* cam, int W, int H,
+                                    const float bg[3], const float* depth, float* out_rgb,
+                                    float* out_alpha, void* ws, size_t ws_bytes,
+                                    const vis_render_opts* opts, void* stream);
+
+/* The adjoint of vis_render_depth (the same depth buffer, after vis_render_depth on the same
+ * workspace): as vis_render_backward, with the depth test among the held decisions. */
+VIS_API vis_status vis_render_backward_depth(vis_scene_t scene, const vis_camera* cam, int W, int H,
+                                             const float bg[3], const float* depth, const float* d_rgb,
+                                             const float* d_alpha, void* ws, size_t ws_bytes,
+                                             const vis_render_opts* opts, float* d_means,
+                                             float* d_log_scales, float* d_quats,
+                                             float* d_opacity_logits, float* d_sh, void* stream);
+
 /* Stable LSD radix sort of (key, value) pairs on the device: the sort stage of the
  * renderer (Algorithm 1, "Radix Sort"; section 3.4, GPU sorting) exposed on its own.
  *  keys_in, vals_in    device uint64[m], uint32[m] (not modified)

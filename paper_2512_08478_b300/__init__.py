@@ -74,10 +74,15 @@ def lib():
                                                C.POINTER(vis_render_opts), C.POINTER(vis_ws_layout)]),
             "vis_render": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int, C.POINTER(C.c_float),
                                      _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts), _P]),
+            "vis_render_depth": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int, C.POINTER(C.c_float),
+                                           _P, _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts), _P]),
             "vis_check": (C.c_int, [_P, _P, C.POINTER(C.c_int64)]),
             "vis_render_backward": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int,
                                               C.POINTER(C.c_float), _P, _P, _P, C.c_size_t,
                                               C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
+            "vis_render_backward_depth": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int,
+                                                    C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
+                                                    C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
             "vis_sort_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
             "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
@@ -176,10 +181,16 @@ def vis_workspace_layout(n, W, H, ws_bytes, opts=None) -> vis_ws_layout:
     return L
 
 
-def vis_render(scene_handle, cam, W, H, bg, out_rgb, out_alpha, ws, opts=None, stream=None):
+def vis_render(scene_handle, cam, W, H, bg, out_rgb, out_alpha, ws, opts=None, stream=None, depth=None):
+    """depth: optional float32 [H,W] CUDA tensor of per-pixel view depths (vis_render_depth)."""
     c = cam if isinstance(cam, vis_camera) else make_camera(cam)
-    _ok(lib().vis_render(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(out_rgb), _ptr(out_alpha),
-                         _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts), _stream(stream)))
+    if depth is None:
+        _ok(lib().vis_render(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(out_rgb), _ptr(out_alpha),
+                             _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts), _stream(stream)))
+    else:
+        _ok(lib().vis_render_depth(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(depth), _ptr(out_rgb),
+                                   _ptr(out_alpha), _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts),
+                                   _stream(stream)))
 
 
 def vis_check(ws, stream=None):
@@ -203,12 +214,18 @@ def read_ctrl(ws):
                 hits=int(u64[1]))
 
 
-def vis_render_backward(scene_handle, cam, W, H, bg, d_rgb, d_alpha, ws, grads, opts=None, stream=None):
+def vis_render_backward(scene_handle, cam, W, H, bg, d_rgb, d_alpha, ws, grads, opts=None, stream=None,
+                        depth=None):
     c = cam if isinstance(cam, vis_camera) else make_camera(cam)
-    _ok(lib().vis_render_backward(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(d_rgb), _ptr(d_alpha),
-                                  _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts),
-                                  *[_ptr(grads[k]) for k in ("means", "log_scales", "quats",
-                                                             "opacity_logits", "sh")], _stream(stream)))
+    g = [_ptr(grads[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+    if depth is None:
+        _ok(lib().vis_render_backward(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(d_rgb),
+                                      _ptr(d_alpha), _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts),
+                                      *g, _stream(stream)))
+    else:
+        _ok(lib().vis_render_backward_depth(scene_handle, C.byref(c), int(W), int(H), _bg(bg), _ptr(depth),
+                                            _ptr(d_rgb), _ptr(d_alpha), _ptr(ws), ws.numel() * ws.element_size(),
+                                            _opts_ref(opts), *g, _stream(stream)))
 
 
 def vis_sort_workspace_size(m, key_bits):
@@ -298,12 +315,12 @@ class Workspace:
         return vis_workspace_layout(self.n, self.W, self.H, self.buf.numel(), self.opts)
 
 
-def _render_checked(scene, cam, W, H, bg, ws, opts, stream=None):
+def _render_checked(scene, cam, W, H, bg, ws, opts, stream=None, depth=None):
     torch = _torch()
     out_rgb = torch.empty((3, H, W), dtype=torch.float32, device=ws.buf.device)
     out_alpha = torch.empty((H, W), dtype=torch.float32, device=ws.buf.device)
     for _ in range(2):
-        vis_render(scene.handle, cam, W, H, bg, out_rgb, out_alpha, ws.buf, opts, stream)
+        vis_render(scene.handle, cam, W, H, bg, out_rgb, out_alpha, ws.buf, opts, stream, depth)
         try:
             vis_check(ws.buf, stream)
             return out_rgb, out_alpha
@@ -319,9 +336,10 @@ def _make_autograd():
 
     class RenderFn(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, scene, cam, W, H, bg, ws, opts, means, log_scales, quats, opacity_logits, sh):
-            rgb, alpha = _render_checked(scene, cam, W, H, bg, ws, opts)
+        def forward(ctx, scene, cam, W, H, bg, ws, opts, depth, means, log_scales, quats, opacity_logits, sh):
+            rgb, alpha = _render_checked(scene, cam, W, H, bg, ws, opts, depth=depth)
             ctx.scene, ctx.cam, ctx.W, ctx.H, ctx.bg, ctx.ws, ctx.opts = scene, cam, W, H, bg, ws, opts
+            ctx.depth = depth
             return rgb, alpha
 
         @staticmethod
@@ -333,8 +351,8 @@ def _make_autograd():
             d_alpha = d_alpha.contiguous().float()
             grads = {k: torch.empty_like(sc.tensors[k]) for k in FIELDS}
             vis_render_backward(sc.handle, ctx.cam, ctx.W, ctx.H, ctx.bg, d_rgb, d_alpha, ctx.ws.buf, grads,
-                                ctx.opts)
-            return (None, None, None, None, None, None, None, grads["means"], grads["log_scales"],
+                                ctx.opts, depth=ctx.depth)
+            return (None, None, None, None, None, None, None, None, grads["means"], grads["log_scales"],
                     grads["quats"], grads["opacity_logits"], grads["sh"])
 
     return RenderFn
@@ -343,12 +361,13 @@ def _make_autograd():
 _RENDER_FN = None
 
 
-def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = None, opts=None):
+def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = None, opts=None, depth=None):
     """Render one view; differentiable w.r.t. the scene tensors (if they require grad).
 
-    Returns (rgb [3,H,W], alpha [H,W]). The workspace keeps the forward's
-    intermediates for the backward; do not reuse it for another render before
-    calling backward.
+    depth: optional float32 [H,W] CUDA tensor: depth-buffer-aware compositing (a splat
+    deeper than a pixel's value is not composited there). Returns (rgb [3,H,W],
+    alpha [H,W]). The workspace keeps the forward's intermediates for the backward; do
+    not reuse it for another render before calling backward.
     """
     global _RENDER_FN
     if _RENDER_FN is None:
@@ -356,7 +375,9 @@ def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = N
     if ws is None:
         ws = Workspace(scene.n, W, H, opts=opts)
     t = scene.tensors
-    return _RENDER_FN.apply(scene, cam, W, H, tuple(bg), ws, opts, t["means"], t["log_scales"], t["quats"],
+    if depth is not None:
+        depth = depth.contiguous().float()
+    return _RENDER_FN.apply(scene, cam, W, H, tuple(bg), ws, opts, depth, t["means"], t["log_scales"], t["quats"],
                             t["opacity_logits"], t["sh"])
 
 

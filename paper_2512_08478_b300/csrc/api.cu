@@ -388,8 +388,9 @@ static vis_status prepare(vis_scene_t scene, const vis_camera* cam, int W, int H
     return VIS_OK;
 }
 
-vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], float* out_rgb,
-                      float* out_alpha, void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
+static vis_status render_impl(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                              const float* zlim, float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
+                              const vis_render_opts* opts, void* stream_) {
     vis_render_opts o;
     vis::Layout L;
     vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
@@ -426,7 +427,7 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     }
     prof_mark(6, stream);
     vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread,
-                          o.collect_stats != 0, out_rgb, out_alpha, stream);
+                          o.collect_stats != 0, out_rgb, out_alpha, zlim, stream);
     prof_mark(7, stream);
     if (g_prof.on && g_prof.count < kProfRing) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -438,6 +439,18 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;
+}
+
+vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], float* out_rgb,
+                      float* out_alpha, void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
+    return render_impl(scene, cam, W, H, bg, nullptr, out_rgb, out_alpha, ws, ws_bytes, opts, stream_);
+}
+
+vis_status vis_render_depth(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                            const float* depth, float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
+                            const vis_render_opts* opts, void* stream_) {
+    if (!depth || !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer null or not 16-byte aligned");
+    return render_impl(scene, cam, W, H, bg, depth, out_rgb, out_alpha, ws, ws_bytes, opts, stream_);
 }
 
 vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
@@ -458,10 +471,10 @@ vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
     return VIS_OK;
 }
 
-vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
-                               const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
-                               const vis_render_opts* opts, float* d_means, float* d_log_scales, float* d_quats,
-                               float* d_opacity_logits, float* d_sh, void* stream_) {
+static vis_status backward_impl(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                                const float* zlim, const float* d_rgb, const float* d_alpha, void* ws,
+                                size_t ws_bytes, const vis_render_opts* opts, float* d_means, float* d_log_scales,
+                                float* d_quats, float* d_opacity_logits, float* d_sh, void* stream_) {
     vis_render_opts o;
     vis::Layout L;
     vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
@@ -472,10 +485,28 @@ vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, 
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     const vis::PrepParams p = make_params(scene, cam, W, H, L, o);
     vis::launch_backward(p, L, static_cast<char*>(ws), bg, o.alpha_min, o.alpha_max, o.t_stop, d_rgb, d_alpha,
-                         d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, stream);
+                         d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, zlim, stream);
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;
+}
+
+vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                               const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
+                               const vis_render_opts* opts, float* d_means, float* d_log_scales, float* d_quats,
+                               float* d_opacity_logits, float* d_sh, void* stream_) {
+    return backward_impl(scene, cam, W, H, bg, nullptr, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
+                         d_quats, d_opacity_logits, d_sh, stream_);
+}
+
+vis_status vis_render_backward_depth(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                                     const float* depth, const float* d_rgb, const float* d_alpha, void* ws,
+                                     size_t ws_bytes, const vis_render_opts* opts, float* d_means,
+                                     float* d_log_scales, float* d_quats, float* d_opacity_logits, float* d_sh,
+                                     void* stream_) {
+    if (!depth || !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer null or not 16-byte aligned");
+    return backward_impl(scene, cam, W, H, bg, depth, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
+                         d_quats, d_opacity_logits, d_sh, stream_);
 }
 
 vis_status vis_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,

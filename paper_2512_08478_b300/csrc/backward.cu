@@ -52,14 +52,15 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return y;
 }
 
-template <int TILE>
+template <int TILE, bool DEPTH>
 __global__ void __launch_bounds__(TILE * TILE)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                           const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0,
                           float bg1, float bg2, float alpha_min, float alpha_max, float qcut, float inv_scale,
                           const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
-                          float* __restrict__ g2) {
+                          float* __restrict__ g2, const float* __restrict__ depth,
+                          const float* __restrict__ zlim) {
     constexpr int NT = TILE * TILE;
     constexpr int NW = NT / 32;               // warps; each owns an 8 x 4 pixel block
     constexpr int BX = TILE / 8, BH = 4;
@@ -83,6 +84,7 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
 
     float T = 1.f, TN = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gA = 0.f;
     int32_t last = 0;
+    const float dl = (DEPTH && inside) ? zlim[pix] : __int_as_float(0x7f800000);   // depth limit
     if (inside) {
         TN = t_final[pix];
         T = TN;
@@ -108,7 +110,8 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
         __syncthreads();
         if (threadIdx.x < cnt) {
             const uint32_t g = vals[lo + threadIdx.x];
-            const StagedSplat st = stage_splat(rec, g, xc, yc, qcut, alpha_min);
+            StagedSplat st = stage_splat(rec, g, xc, yc, qcut, alpha_min);
+            if (DEPTH) st.c.w = depth[g];
             s_g[threadIdx.x] = g;
             s_a[threadIdx.x] = st.a;
             s_b[threadIdx.x] = st.b;
@@ -134,9 +137,10 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
             if (inside && pos < (int64_t)last) {
                 const float4 a = s_a[k], b = s_b[k];
                 const PairEval e = eval_pair(lx, ly, a, b);
-                if (e.q <= b.z) {   // the forward's decision: 3-sigma cut and alpha_min
+                const float4 c = s_c[k];
+                // the forward's decisions: 3-sigma cut and alpha_min (and the depth test)
+                if (e.q <= b.z && (!DEPTH || c.w <= dl)) {
                     contrib = true;
-                    const float4 c = s_c[k];
                     const float G = gauss_of_qs(e.q);
                     const float raw = __fmul_rn(b.w, G);
                     const float alpha = fminf(alpha_max, raw);
@@ -387,7 +391,8 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
 
 void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3], float alpha_min,
                      float alpha_max, float t_stop, const float* d_rgb, const float* d_alpha, float* d_means,
-                     float* d_log_scales, float* d_quats, float* d_logits, float* d_sh, cudaStream_t stream) {
+                     float* d_log_scales, float* d_quats, float* d_logits, float* d_sh, const float* zlim,
+                     cudaStream_t stream) {
     (void)t_stop;
     float* g2 = reinterpret_cast<float*>(ws + L.off_g2);
     cudaMemsetAsync(g2, 0, sizeof(float) * 9 * (size_t)L.n, stream);
@@ -398,16 +403,22 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
     const int32_t* last = reinterpret_cast<const int32_t*>(ws + L.off_last);
     const int blocks = (int)L.ntiles;
     const QScale qs = q_scale();
-#define VIS_LAUNCH_BWD(TS)                                                                                 \
-    composite_backward_kernel<TS><<<blocks, TS * TS, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, \
-                                                                  bg[0], bg[1], bg[2], alpha_min,         \
-                                                                  alpha_max, qs.qcut, qs.inv_scale, tfin, \
-                                                                  last, d_rgb, d_alpha, g2)
+    const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+#define VIS_LAUNCH_BWD_D(TS, DT)                                                                           \
+    composite_backward_kernel<TS, DT><<<blocks, TS * TS, 0, stream>>>(                                     \
+        ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut,        \
+        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim)
+#define VIS_LAUNCH_BWD(TS)                       \
+    do {                                         \
+        if (zlim) VIS_LAUNCH_BWD_D(TS, true);    \
+        else VIS_LAUNCH_BWD_D(TS, false);        \
+    } while (0)
     if (blocks > 0) {
         if (L.tile == 8) VIS_LAUNCH_BWD(8);
         else if (L.tile == 32) VIS_LAUNCH_BWD(32);
         else VIS_LAUNCH_BWD(16);
     }
+#undef VIS_LAUNCH_BWD_D
 #undef VIS_LAUNCH_BWD
     if (p.n > 0) {
         const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);

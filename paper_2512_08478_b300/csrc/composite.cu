@@ -14,6 +14,9 @@
 // (that splat excluded); the CTA leaves as soon as all its pixels are done.
 // Outputs: planar rgb = C + T bg, alpha = 1 - T, and for the adjoint the final T
 // and 1 + the sorted position of the last composited splat.
+// DEPTH: depth-buffer-aware compositing (section 3.4's depth test against a caller's
+// buffer, without writing it): a splat whose view depth exceeds the pixel's value in
+// zlim [H,W] is not composited at that pixel.
 #include "splat_eval.cuh"
 
 namespace vis {
@@ -38,13 +41,14 @@ __device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& 
     P.last = pos1;
 }
 
-template <int TILE, int PPT, bool STATS>
+template <int TILE, int PPT, bool STATS, bool DEPTH>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                  const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0, float bg1,
                  float bg2, float alpha_min, float alpha_max, float t_stop, float qcut,
                  Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
-                 float* __restrict__ t_final, int32_t* __restrict__ last_out) {
+                 float* __restrict__ t_final, int32_t* __restrict__ last_out,
+                 const float* __restrict__ depth, const float* __restrict__ zlim) {
     constexpr int NT = TILE * TILE / PPT;   // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
     constexpr int BX = TILE / 8;            // blocks per tile row
@@ -78,6 +82,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     }
     PixAcc P[PPT];
     float ly[PPT];
+    float dl[PPT];   // depth limits (DEPTH only)
     unsigned long long n_tests = 0, n_hits = 0;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
@@ -85,6 +90,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
         P[r].T = 1.f; P[r].C0 = P[r].C1 = P[r].C2 = 0.f; P[r].last = 0;
         P[r].done = !(px < W && py < H);
         ly[r] = (float)py + 0.5f - yc;
+        dl[r] = (DEPTH && !P[r].done) ? zlim[(size_t)py * W + px] : __int_as_float(0x7f800000);
     }
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += CH) {
@@ -94,7 +100,9 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
         if (__syncthreads_count(all_done) == NT) break;
         const uint32_t j = base + threadIdx.x;
         if (threadIdx.x < CH && j < rg.y) {
-            const StagedSplat s = stage_splat(rec, vals[j], xc, yc, qcut, alpha_min);
+            const uint32_t g = vals[j];
+            StagedSplat s = stage_splat(rec, g, xc, yc, qcut, alpha_min);
+            if (DEPTH) s.c.w = depth[g];
             s_a[threadIdx.x] = s.a;
             s_b[threadIdx.x] = s.b;
             s_c[threadIdx.x] = s.c;
@@ -122,7 +130,9 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                     const PairEval e = eval_pair(lx, ly[0], a, b);
                     if (STATS) ++n_tests;
                     if (e.q > b.z) continue;
-                    composite_hit(P[0], e.q, b, s_c[k], alpha_max, t_stop, pos1);
+                    const float4 c = s_c[k];
+                    if (DEPTH && c.w > dl[0]) continue;
+                    composite_hit(P[0], e.q, b, c, alpha_max, t_stop, pos1);
                     if (STATS && !P[0].done) ++n_hits;
                     if (P[0].done) break;
                 } else {
@@ -134,11 +144,16 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                     const float p11 = __fmaf_rn(dy1, a.w, t1), p21 = __fmaf_rn(dy1, b.y, t2);
                     const float q0 = __fmaf_rn(p20, p20, __fmul_rn(p10, p10));
                     const float q1 = __fmaf_rn(p21, p21, __fmul_rn(p11, p11));
-                    const bool h0 = !P[0].done && q0 <= b.z;
-                    const bool h1 = !P[1].done && q1 <= b.z;
+                    bool h0 = !P[0].done && q0 <= b.z;
+                    bool h1 = !P[1].done && q1 <= b.z;
                     if (STATS) n_tests += (P[0].done ? 0 : 1) + (P[1].done ? 0 : 1);
                     if (!(h0 || h1)) continue;
                     const float4 c = s_c[k];
+                    if (DEPTH) {
+                        h0 = h0 && c.w <= dl[0];
+                        h1 = h1 && c.w <= dl[1];
+                        if (!(h0 || h1)) continue;
+                    }
                     if (h0) composite_hit(P[0], q0, b, c, alpha_max, t_stop, pos1);
                     if (h1) composite_hit(P[1], q1, b, c, alpha_max, t_stop, pos1);
                     if (STATS) n_hits += (h0 && !P[0].done ? 1 : 0) + (h1 && !P[1].done ? 1 : 0);
@@ -175,7 +190,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
 
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
-                      cudaStream_t stream) {
+                      const float* zlim, cudaStream_t stream) {
     const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
     const uint32_t* vals = reinterpret_cast<const uint32_t*>(ws + L.off_vals[L.sorted_buffer]);
     const float4* rec = reinterpret_cast<const float4*>(ws + L.off_rec);
@@ -185,15 +200,16 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     const int blocks = (int)L.ntiles;
     if (blocks <= 0) return;
     const float qcut = q_scale().qcut;
-#define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST)                                                                    \
-    composite_kernel<TS, PP, ST><<<blocks, TS * TS / PP, 0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x,  \
-                                                                      bg0, bg1, bg2, alpha_min, alpha_max,    \
-                                                                      t_stop, qcut, ctrl, out_rgb, out_alpha, \
-                                                                      tfin, last)
-#define VIS_LAUNCH_COMPOSITE(TS, PP)                   \
-    do {                                               \
-        if (stats) VIS_LAUNCH_COMPOSITE_S(TS, PP, true);  \
-        else VIS_LAUNCH_COMPOSITE_S(TS, PP, false);       \
+    const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+#define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                \
+    composite_kernel<TS, PP, ST, DT><<<blocks, TS * TS / PP, 0, stream>>>(                                    \
+        ranges, vals, rec, L.W, L.H, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl,     \
+        out_rgb, out_alpha, tfin, last, depth, zlim)
+#define VIS_LAUNCH_COMPOSITE(TS, PP)                          \
+    do {                                                      \
+        if (zlim) VIS_LAUNCH_COMPOSITE_S(TS, PP, false, true);   \
+        else if (stats) VIS_LAUNCH_COMPOSITE_S(TS, PP, true, false); \
+        else VIS_LAUNCH_COMPOSITE_S(TS, PP, false, false);       \
     } while (0)
     const bool two = ppt == 2;
     if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE(8, 2); else VIS_LAUNCH_COMPOSITE(8, 1); }

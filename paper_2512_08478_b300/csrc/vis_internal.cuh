@@ -193,13 +193,14 @@ struct QScale {
     float inv_scale;   // 2 / log2(e) = 2 ln 2
 };
 QScale q_scale();
+// zlim: [H,W] depth buffer for the depth-tested compositing, or null
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
-                      cudaStream_t stream);
+                      const float* zlim, cudaStream_t stream);
 void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3],
                      float alpha_min, float alpha_max, float t_stop, const float* d_rgb,
                      const float* d_alpha, float* d_means, float* d_log_scales, float* d_quats,
-                     float* d_logits, float* d_sh, cudaStream_t stream);
+                     float* d_logits, float* d_sh, const float* zlim, cudaStream_t stream);
 
 // Stable LSD radix sort of (K key, uint32 value) pairs over `passes` 8-bit digits.
 // Reads keys_in/vals_in, ping-pongs between the a and b buffers and leaves the result in a.
