@@ -76,12 +76,28 @@ def cam_array(cam):
     return cam.as_array().astype(np.float64)
 
 
+def model_array(model):
+    """Per-model affine transform [A | b] (3x4, row-major) -> 12 float64 values made from its
+    float32 rounding (the values the CUDA library receives); None stays None (identity)."""
+    if model is None:
+        return None
+    m = np.asarray(model, np.float64).reshape(-1)
+    if m.shape[0] != 12:
+        raise ValueError("a model transform is 3x4 ([A | b])")
+    return m.astype(np.float32).astype(np.float64)
+
+
+def _mp(m):
+    return None if m is None else _p(m)
+
+
 def num_threads() -> int:
     return len(os.sched_getaffinity(0))
 
 
-def preprocess(scene, cam, opts=None):
+def preprocess(scene, cam, opts=None, model=None):
     """Per-Gaussian projection, conic, extent, tile rectangle and colour (Eq. 1).
+    model: optional 3x4 [A | b]; the scene is drawn transformed by it (Algorithm 1's M_k).
 
     Returns a dict of numpy arrays: valid [N] int32, uv [N,2], conic [N,3]
     (a, b, c with q = a dx^2 + 2 b dx dy + c dy^2), S [N,3] (s00, s01, s11),
@@ -94,7 +110,8 @@ def preprocess(scene, cam, opts=None):
                zkey=np.zeros(n, np.float32), radius=np.zeros(n, np.int32),
                rect=np.zeros((n, 4), np.int32))
     arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
-    rc = _L().orc_preprocess(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]),
+    m = model_array(model)
+    rc = _L().orc_preprocess(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]), _mp(m),
                              _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
                              *[_p(out[k]) for k in ("valid", "uv", "conic", "S", "opacity", "rgb",
                                                     "z", "zkey", "radius", "rect")])
@@ -176,6 +193,26 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None, depth=None
     return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask, depth), prep
 
 
+PREP_KEYS = ("valid", "uv", "conic", "S", "opacity", "rgb", "z", "zkey", "radius", "rect")
+
+
+def concat_preps(preps):
+    """One splat set from several models' preprocess outputs, in model order (the
+    global index of model k's Gaussian i is the sum of the earlier models' sizes + i)."""
+    return {k: np.ascontiguousarray(np.concatenate([p[k] for p in preps], axis=0)) for k in PREP_KEYS}
+
+
+def render_multi(scenes, models, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None, depth=None):
+    """Several models drawn into one image (Algorithm 1): each model is preprocessed
+    with its own transform M_k (None = identity), then all splats are sorted and
+    composited together in one global (tile, depth, index) order."""
+    models = [None] * len(scenes) if models is None else list(models)
+    if len(models) != len(scenes):
+        raise ValueError("one model transform per scene")
+    prep = concat_preps([preprocess(s, cam, opts, m) for s, m in zip(scenes, models)])
+    return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask, depth), prep
+
+
 def duplicate(prep, tiles_x, cap=None):
     """Keys (tile << 32 | float bits of zkey) and vals (Gaussian index), index-major."""
     n = prep["valid"].shape[0]
@@ -234,21 +271,28 @@ def covariance(log_scales, quats):
     return out.reshape(n, 3, 3)
 
 
-def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False, depth=None):
+def _grad_dict(n, K):
+    return dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+                opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
+
+
+def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False, depth=None, model=None):
     """FP64 gradient of L = sum(gC * rgb) + sum(gA * alpha) w.r.t. all Gaussian inputs.
 
-    gC: [3,H,W], gA: [H,W]; depth: optional [H,W] depth buffer (as in render). Returns dict
+    gC: [3,H,W], gA: [H,W]; depth: optional [H,W] depth buffer (as in render); model:
+    optional 3x4 transform (as in preprocess; gradients are w.r.t. the untransformed
+    parameters). Returns dict
     means [N,3], log_scales [N,3], quats [N,4], opacity_logits [N], sh [N,K,3] (and g2
     [N,9] screen-space gradients if asked).
     """
     n = scene["means"].shape[0]
     K = (scene["sh_degree"] + 1) ** 2
-    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-               opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
+    out = _grad_dict(n, K)
     g2 = np.zeros((n, 9))
     arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
     zl, zl_p = _zlim(depth, cam.W * cam.H)   # zl keeps the buffer alive through the call
-    rc = _L().orc_adjoint(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]),
+    m = model_array(model)
+    rc = _L().orc_adjoint(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]), _mp(m),
                           _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
                           _p(_f64(bg)), _p(_f64(gC)), _p(_f64(gA)), zl_p,
                           *[_p(out[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")],
@@ -258,6 +302,40 @@ def adjoint(scene, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, return_g2=False, 
     if return_g2:
         out["g2"] = g2
     return out
+
+
+def adjoint_multi(scenes, models, cam, gC, gA, bg=(0.0, 0.0, 0.0), opts=None, depth=None):
+    """FP64 gradients of a render_multi image's loss (as adjoint) w.r.t. every model's
+    own (untransformed) parameters: the compositing adjoint over the global order,
+    then each model's preprocess adjoint on its slice. Returns one dict per scene."""
+    models = [None] * len(scenes) if models is None else list(models)
+    _, prep = render_multi(scenes, models, cam, bg, opts, depth=depth)
+    n = prep["valid"].shape[0]
+    g2 = np.zeros((max(n, 1), 9))
+    zl, zl_p = _zlim(depth, cam.W * cam.H)
+    rc = _L().orc_composite_adjoint(C.c_int64(n), *[_p(prep[k]) for k in ("valid", "uv", "conic", "opacity",
+                                                                           "rgb", "zkey", "rect")],
+                                    C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)), _p(_f64(bg)),
+                                    _p(_f64(gC)), _p(_f64(gA)), zl_p, _p(g2))
+    if rc != 0:
+        raise ValueError("oracle compositing adjoint failed")
+    outs, off = [], 0
+    for sc, mdl in zip(scenes, models):
+        k = sc["means"].shape[0]
+        out = _grad_dict(k, (sc["sh_degree"] + 1) ** 2)
+        arrs = [_f64(sc[f]) for f in ("means", "log_scales", "quats", "opacity_logits", "sh")]
+        g2k = np.ascontiguousarray(g2[off:off + k])
+        m = model_array(mdl)
+        rc = _L().orc_preprocess_adjoint(C.c_int64(k), *[_p(a) for a in arrs], C.c_int(sc["sh_degree"]), _mp(m),
+                                         _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H),
+                                         _p(opts_array(opts)), _p(g2k),
+                                         *[_p(out[f]) for f in ("means", "log_scales", "quats",
+                                                                "opacity_logits", "sh")])
+        if rc != 0:
+            raise ValueError("oracle preprocess adjoint failed")
+        outs.append(out)
+        off += k
+    return outs
 
 
 def dynamic_update(means0, velocity, logits0, amp, freq, phase, t):

@@ -30,6 +30,12 @@
  *     by Gaussian index.
  *   - colour = max(0, sum_k sh_k Y_k(dir) + 0.5), dir = normalize(mu - camera
  *     centre), real SH with the Condon-Shortley phase, coefficient index l*l+l+m.
+ *   - per-model affine transform M_k = [A | b] (Algorithm 1, x_w = M_k [mu; 1];
+ *     section 3.4, the transform is applied to the whole model): the mean goes to
+ *     A mu + b and the covariance to A Sigma A^T; the SH colour keeps being evaluated
+ *     in the model's own frame, i.e. at the view ray mapped back by A^-1
+ *     (dir = normalize(A^-1 (x_w - camera centre))), so a rigidly moved asset carries
+ *     its view-dependent colour with it. A singular A is rejected.
  *
  * Everything is plain loops in double precision; OpenMP parallelises over
  * independent pixels, tiles or Gaussians only (no change of arithmetic order
@@ -202,7 +208,66 @@ typedef struct {
     const double *means, *log_scales, *quats, *logits, *sh;
     int deg;
     int64_t n;
+    /* per-model affine transform x_w = A mu + b (Algorithm 1, M_k); has_model 0 = identity */
+    int has_model;
+    double A[9], b[3], Ainv[9];
 } scene_t;
+
+/* model12 = [A | b] row-major 3x4, or NULL for the identity. Returns 1 if A is singular
+ * or not finite. */
+static int load_model(const double* model12, scene_t* sc) {
+    sc->has_model = 0;
+    if (!model12) return 0;
+    for (int k = 0; k < 12; ++k)
+        if (!isfinite(model12[k])) return 1;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) sc->A[r * 3 + c] = model12[r * 4 + c];
+        sc->b[r] = model12[r * 4 + 3];
+    }
+    const double* A = sc->A;
+    /* inverse by the adjugate: Ainv = adj(A) / det(A) */
+    double adj[9] = {
+        A[4] * A[8] - A[5] * A[7], A[2] * A[7] - A[1] * A[8], A[1] * A[5] - A[2] * A[4],
+        A[5] * A[6] - A[3] * A[8], A[0] * A[8] - A[2] * A[6], A[2] * A[3] - A[0] * A[5],
+        A[3] * A[7] - A[4] * A[6], A[1] * A[6] - A[0] * A[7], A[0] * A[4] - A[1] * A[3]};
+    double det = A[0] * adj[0] + A[1] * adj[3] + A[2] * adj[6];
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return 1;
+    for (int k = 0; k < 9; ++k) {
+        sc->Ainv[k] = adj[k] / det;
+        if (!isfinite(sc->Ainv[k])) return 1;
+    }
+    sc->has_model = 1;
+    return 0;
+}
+
+/* world-space mean x_w = A mu + b */
+static void world_mean(const scene_t* sc, const double* mu, double xw[3]) {
+    if (!sc->has_model) { xw[0] = mu[0]; xw[1] = mu[1]; xw[2] = mu[2]; return; }
+    for (int r = 0; r < 3; ++r)
+        xw[r] = sc->A[r * 3 + 0] * mu[0] + sc->A[r * 3 + 1] * mu[1] + sc->A[r * 3 + 2] * mu[2] + sc->b[r];
+}
+
+/* world-space covariance Sigma_w = A Sigma A^T (full 3x3 row-major) */
+static void world_cov(const scene_t* sc, const double Sig[9], double Sw[9]) {
+    if (!sc->has_model) { memcpy(Sw, Sig, sizeof(double) * 9); return; }
+    double AS[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            AS[r * 3 + c] = sc->A[r * 3 + 0] * Sig[0 * 3 + c] + sc->A[r * 3 + 1] * Sig[1 * 3 + c] +
+                            sc->A[r * 3 + 2] * Sig[2 * 3 + c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Sw[r * 3 + c] = AS[r * 3 + 0] * sc->A[c * 3 + 0] + AS[r * 3 + 1] * sc->A[c * 3 + 1] +
+                            AS[r * 3 + 2] * sc->A[c * 3 + 2];
+}
+
+/* the SH evaluation ray in the model's own frame (unnormalised): A^-1 (x_w - centre) */
+static void model_view_ray(const scene_t* sc, const double xw[3], const double centre[3], double d[3]) {
+    double w[3] = {xw[0] - centre[0], xw[1] - centre[1], xw[2] - centre[2]};
+    if (!sc->has_model) { d[0] = w[0]; d[1] = w[1]; d[2] = w[2]; return; }
+    for (int r = 0; r < 3; ++r)
+        d[r] = sc->Ainv[r * 3 + 0] * w[0] + sc->Ainv[r * 3 + 1] * w[1] + sc->Ainv[r * 3 + 2] * w[2];
+}
 
 /* Per-Gaussian outputs, all arrays of length n (x2, x3, x4 where noted). */
 typedef struct {
@@ -230,9 +295,10 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     out->radius[i] = 0;
     for (int k = 0; k < 4; ++k) out->rect[4 * i + k] = 0;
     const double* mu = sc->means + 3 * i;
-    double p[3];
+    double xw[3], p[3];
+    world_mean(sc, mu, xw);
     for (int r = 0; r < 3; ++r)
-        p[r] = cam->R[r * 3 + 0] * mu[0] + cam->R[r * 3 + 1] * mu[1] + cam->R[r * 3 + 2] * mu[2] + cam->t[r];
+        p[r] = cam->R[r * 3 + 0] * xw[0] + cam->R[r * 3 + 1] * xw[1] + cam->R[r * 3 + 2] * xw[2] + cam->t[r];
     double z = p[2];
     out->z[i] = z;
     out->zkey[i] = (float)z;
@@ -241,13 +307,16 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     if (!(z > cam->near_z)) return;
     if (o < op->alpha_min) return;
 
-    double Sig[9];
-    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig);
+    double Sig0[9], Sig[9];
+    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig0);
+    world_cov(sc, Sig0, Sig);
 
     double limx = 1.3 * (cam->W / (2.0 * cam->fx)), limy = 1.3 * (cam->H / (2.0 * cam->fy));
     double rx = p[0] / z, ry = p[1] / z;
-    if (rx > limx) rx = limx; if (rx < -limx) rx = -limx;
-    if (ry > limy) ry = limy; if (ry < -limy) ry = -limy;
+    if (rx > limx) rx = limx;
+    if (rx < -limx) rx = -limx;
+    if (ry > limy) ry = limy;
+    if (ry < -limy) ry = -limy;
     double J[6] = {cam->fx / z, 0.0, -cam->fx * rx / z,
                    0.0, cam->fy / z, -cam->fy * ry / z};
     /* T = J R  (2x3) */
@@ -298,9 +367,9 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     if (x1 <= x0 || y1 <= y0) return;
 
     /* colour */
-    double cc[3];
+    double cc[3], d[3];
     camera_centre(cam, cc);
-    double d[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+    model_view_ray(sc, xw, cc, d);
     double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     d[0] /= dn; d[1] /= dn; d[2] /= dn;
     int K = (sc->deg + 1) * (sc->deg + 1);
@@ -315,8 +384,9 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     out->valid[i] = 1;
 }
 
+/* model12: the model's [A | b] (row-major 3x4) or NULL for the identity */
 int orc_preprocess(int64_t n, const double* means, const double* log_scales, const double* quats,
-                   const double* logits, const double* sh, int deg,
+                   const double* logits, const double* sh, int deg, const double* model12,
                    const double* cam17, int W, int H, const double* opts6,
                    int* valid, double* uv, double* conic, double* S, double* opacity, double* rgb,
                    double* z, float* zkey, int* radius, int* rect) {
@@ -324,6 +394,7 @@ int orc_preprocess(int64_t n, const double* means, const double* log_scales, con
     cam_t cam; load_cam(cam17, W, H, &cam);
     opts_t op; load_opts(opts6, &op);
     scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    if (load_model(model12, &sc)) return 2;
     prep_t out = {valid, uv, conic, S, opacity, rgb, z, zkey, radius, rect};
     int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
     memset(conic, 0, sizeof(double) * 3 * n);
@@ -626,8 +697,9 @@ int orc_tile_ranges(int64_t m, const uint64_t* sorted_keys, int64_t ntiles, uint
  * then a = min(alpha_max, o G), G = exp(-q/2), q = d^T conic d, d = pixel - (u,v).
  * The per-Gaussian screen-space gradients g2 = (u, v, a, b, c, opacity, r, g, b)
  * are then chained through the preprocess: conic = S^-1, S = T Sigma T^T + dil I,
- * T = J R, J(p), p = R mu + t, Sigma = (Rq diag s)(Rq diag s)^T, s = exp(log_s),
- * Rq(q/|q|), opacity = sigmoid(logit), rgb = max(0, sum sh_k Y_k(dir) + 0.5).
+ * T = J R, J(p), p = R x_w + t, x_w = A mu + b, Sigma_w = A Sigma A^T,
+ * Sigma = (Rq diag s)(Rq diag s)^T, s = exp(log_s), Rq(q/|q|), opacity = sigmoid(logit),
+ * rgb = max(0, sum sh_k Y_k(dir) + 0.5), dir = normalize(A^-1 (x_w - centre)).
  */
 
 typedef struct { int64_t idx; double alpha, T, G, dx, dy; int clamped; } contrib_t;
@@ -658,12 +730,13 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
     const double* mu = sc->means + 3 * i;
     double gu = g2[0], gv = g2[1], ga = g2[2], gb = g2[3], gc = g2[4], go = g2[5];
     double grgb[3] = {g2[6], g2[7], g2[8]};
-    double gmu[3] = {0, 0, 0};
+    double xw[3], gxw[3] = {0, 0, 0};   /* world-space mean and dL/dx_w */
+    world_mean(sc, mu, xw);
 
     /* colour */
-    double cc[3];
+    double cc[3], dv[3];
     camera_centre(cam, cc);
-    double dv[3] = {mu[0] - cc[0], mu[1] - cc[1], mu[2] - cc[2]};
+    model_view_ray(sc, xw, cc, dv);
     double dn = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     double dir[3] = {dv[0] / dn, dv[1] / dn, dv[2] / dn};
     double Y[16], dY[48];
@@ -679,9 +752,13 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
             for (int a = 0; a < 3; ++a) gdir[a] += grgb[ch] * c * dY[k * 3 + a];
         }
     }
-    /* dir = v/|v|: d dir/d v = (I - dir dir^T)/|v| */
+    /* dir = v/|v|: d dir/d v = (I - dir dir^T)/|v|; v = A^-1 (x_w - centre) */
     double dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
-    for (int a = 0; a < 3; ++a) gmu[a] += (gdir[a] - dir[a] * dd) / dn;
+    double gv3[3];
+    for (int a = 0; a < 3; ++a) gv3[a] = (gdir[a] - dir[a] * dd) / dn;
+    for (int a = 0; a < 3; ++a)
+        gxw[a] += sc->has_model ? sc->Ainv[0 * 3 + a] * gv3[0] + sc->Ainv[1 * 3 + a] * gv3[1] + sc->Ainv[2 * 3 + a] * gv3[2]
+                                : gv3[a];
 
     /* opacity */
     double o = pp->opacity[i];
@@ -690,7 +767,7 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
     /* camera-space position */
     double p[3];
     for (int r = 0; r < 3; ++r)
-        p[r] = cam->R[r * 3 + 0] * mu[0] + cam->R[r * 3 + 1] * mu[1] + cam->R[r * 3 + 2] * mu[2] + cam->t[r];
+        p[r] = cam->R[r * 3 + 0] * xw[0] + cam->R[r * 3 + 1] * xw[1] + cam->R[r * 3 + 2] * xw[2] + cam->t[r];
     double x = p[0], y = p[1], z = p[2];
     double gp[3] = {0, 0, 0};
     /* u = fx x/z + cx, v = fy y/z + cy */
@@ -723,10 +800,11 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
             for (int k = 0; k < 3; ++k) acc += J[r * 3 + k] * cam->R[k * 3 + c];
             T[r * 3 + c] = acc;
         }
-    double Sig[9];
-    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig);
+    double Sig0[9], Sig[9];
+    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig0);
+    world_cov(sc, Sig0, Sig);
 
-    /* dL/dT = 2 MS T Sigma ; dL/dSigma = T^T MS T */
+    /* dL/dT = 2 MS T Sigma_w ; dL/dSigma_w = T^T MS T */
     double TS[6];
     for (int r = 0; r < 2; ++r)
         for (int c = 0; c < 3; ++c) {
@@ -737,14 +815,26 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
     double gT[6];
     for (int r = 0; r < 2; ++r)
         for (int c = 0; c < 3; ++c) gT[r * 3 + c] = 2.0 * (MS[r * 2 + 0] * TS[0 * 3 + c] + MS[r * 2 + 1] * TS[1 * 3 + c]);
-    double gSig[9];
+    double gSigw[9], gSig[9];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             double acc = 0;
             for (int r = 0; r < 2; ++r)
                 for (int c = 0; c < 2; ++c) acc += T[r * 3 + a] * MS[r * 2 + c] * T[c * 3 + b];
-            gSig[a * 3 + b] = acc;
+            gSigw[a * 3 + b] = acc;
         }
+    /* Sigma_w = A Sigma A^T: dL/dSigma = A^T (dL/dSigma_w) A */
+    if (sc->has_model) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) acc += sc->A[r * 3 + a] * gSigw[r * 3 + c] * sc->A[c * 3 + b];
+                gSig[a * 3 + b] = acc;
+            }
+    } else {
+        memcpy(gSig, gSigw, sizeof(gSig));
+    }
     /* T = J R: dL/dJ = dL/dT R^T */
     double gJ[6];
     for (int r = 0; r < 2; ++r)
@@ -764,10 +854,13 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
         gp[1] += gJ[5] * (-cam->fy / (z * z));
         gp[2] += gJ[5] * (cam->fy * y / (z * z * z));
     }
-    /* p = R mu + t */
+    /* p = R x_w + t, x_w = A mu + b */
     for (int a = 0; a < 3; ++a)
-        gmu[a] += cam->R[0 * 3 + a] * gp[0] + cam->R[1 * 3 + a] * gp[1] + cam->R[2 * 3 + a] * gp[2];
-    for (int a = 0; a < 3; ++a) d_means[3 * i + a] = gmu[a];
+        gxw[a] += cam->R[0 * 3 + a] * gp[0] + cam->R[1 * 3 + a] * gp[1] + cam->R[2 * 3 + a] * gp[2];
+    for (int a = 0; a < 3; ++a)
+        d_means[3 * i + a] = sc->has_model
+            ? sc->A[0 * 3 + a] * gxw[0] + sc->A[1 * 3 + a] * gxw[1] + sc->A[2 * 3 + a] * gxw[2]
+            : gxw[a];
 
     /* Sigma = M M^T, M = Rq diag(s): dL/dM = 2 gSig M */
     const double* qf = sc->quats + 4 * i;
@@ -809,33 +902,37 @@ static void preprocess_adjoint_one(const scene_t* sc, int64_t i, const cam_t* ca
     }
 }
 
-int orc_adjoint(int64_t n, const double* means, const double* log_scales, const double* quats,
-                const double* logits, const double* sh, int deg, const double* cam17, int W, int H,
-                const double* opts6, const double* bg, const double* gC, const double* gA,
-                const float* zlim /* [H,W] depth buffer or NULL */,
-                double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
-                double* d_sh, double* g2_out /* [n,9] or NULL */) {
-    if (deg < 0 || deg > 3) return 1;
-    cam_t cam; load_cam(cam17, W, H, &cam);
-    opts_t op; load_opts(opts6, &op);
-    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+/* prep arrays for n Gaussians (freed by free_prep) */
+static int alloc_prep(int64_t n, prep_t* pp) {
+    size_t m = (size_t)(n > 0 ? n : 1);
+    pp->valid = (int*)calloc(m, sizeof(int));
+    pp->uv = (double*)calloc(2 * m, sizeof(double));
+    pp->conic = (double*)calloc(3 * m, sizeof(double));
+    pp->S = (double*)calloc(3 * m, sizeof(double));
+    pp->opacity = (double*)calloc(m, sizeof(double));
+    pp->rgb = (double*)calloc(3 * m, sizeof(double));
+    pp->z = (double*)calloc(m, sizeof(double));
+    pp->zkey = (float*)calloc(m, sizeof(float));
+    pp->radius = (int*)calloc(m, sizeof(int));
+    pp->rect = (int*)calloc(4 * m, sizeof(int));
+    return !(pp->valid && pp->uv && pp->conic && pp->S && pp->opacity && pp->rgb && pp->z && pp->zkey &&
+             pp->radius && pp->rect);
+}
+
+static void free_prep(prep_t* pp) {
+    free(pp->valid); free(pp->uv); free(pp->conic); free(pp->S); free(pp->opacity); free(pp->rgb);
+    free(pp->z); free(pp->zkey); free(pp->radius); free(pp->rect);
+}
+
+/* Reverse mode of the compositing (Eqs. 2-3) over the splats of `pp` in the method's
+ * (tile, depth, index) order: accumulates the screen-space gradients g2 [n,9] =
+ * d/d(u, v, conic a, b, c, opacity, r, g, b). */
+static int composite_adjoint(int64_t n, const prep_t* pp_, int W, int H, const opts_t* op_, const double* bg,
+                             const double* gC, const double* gA, const float* zlim, double* g2) {
+    const prep_t pp = *pp_;
+    const opts_t op = *op_;
     int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
-
-    prep_t pp;
-    pp.valid = (int*)malloc(sizeof(int) * n);
-    pp.uv = (double*)calloc(2 * n, sizeof(double));
-    pp.conic = (double*)calloc(3 * n, sizeof(double));
-    pp.S = (double*)calloc(3 * n, sizeof(double));
-    pp.opacity = (double*)malloc(sizeof(double) * n);
-    pp.rgb = (double*)calloc(3 * n, sizeof(double));
-    pp.z = (double*)malloc(sizeof(double) * n);
-    pp.zkey = (float*)malloc(sizeof(float) * n);
-    pp.radius = (int*)malloc(sizeof(int) * n);
-    pp.rect = (int*)malloc(sizeof(int) * 4 * n);
-    double* g2 = (double*)calloc(9 * n, sizeof(double));
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) preprocess_one(&sc, i, &cam, &op, tiles_x, tiles_y, &pp);
-
+    memset(g2, 0, sizeof(double) * 9 * (size_t)n);
     bins_t b;
     if (build_bins(n, pp.valid, pp.rect, pp.zkey, tiles_x, tiles_y, NULL, &b)) return 1;
     int64_t ntiles = (int64_t)tiles_x * tiles_y;
@@ -932,11 +1029,78 @@ int orc_adjoint(int64_t n, const double* means, const double* log_scales, const 
         free(acc);
     }
     free_bins(&b);
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i)
-        preprocess_adjoint_one(&sc, i, &cam, &op, &pp, g2 + 9 * i, d_means, d_log_scales, d_quats, d_logits, d_sh);
-    if (g2_out) memcpy(g2_out, g2, sizeof(double) * 9 * n);
-    free(pp.valid); free(pp.uv); free(pp.conic); free(pp.S); free(pp.opacity); free(pp.rgb);
-    free(pp.z); free(pp.zkey); free(pp.radius); free(pp.rect); free(g2);
     return 0;
+}
+
+/* Reverse mode of the preprocess for one model: g2 [n,9] -> gradients of the model's own
+ * parameters (model12 as in orc_preprocess). */
+static int preprocess_adjoint(const scene_t* sc, const cam_t* cam, const opts_t* op, int W, int H,
+                              const prep_t* pp, const double* g2, double* d_means, double* d_log_scales,
+                              double* d_quats, double* d_logits, double* d_sh) {
+    (void)W; (void)H;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < sc->n; ++i)
+        preprocess_adjoint_one(sc, i, cam, op, pp, g2 + 9 * i, d_means, d_log_scales, d_quats, d_logits, d_sh);
+    return 0;
+}
+
+/* Exported halves of the adjoint, for a render of several models composited in one
+ * global order (Algorithm 1): the compositing adjoint over the concatenated splats ... */
+int orc_composite_adjoint(int64_t n, const int* valid, const double* uv, const double* conic,
+                          const double* opacity, const double* rgb, const float* zkey, const int* rect,
+                          int W, int H, const double* opts6, const double* bg, const double* gC,
+                          const double* gA, const float* zlim, double* g2_out) {
+    opts_t op; load_opts(opts6, &op);
+    prep_t pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.valid = (int*)valid; pp.uv = (double*)uv; pp.conic = (double*)conic; pp.opacity = (double*)opacity;
+    pp.rgb = (double*)rgb; pp.zkey = (float*)zkey; pp.rect = (int*)rect;
+    return composite_adjoint(n, &pp, W, H, &op, bg, gC, gA, zlim, g2_out);
+}
+
+/* ... and the preprocess adjoint of one model, given its slice of g2. */
+int orc_preprocess_adjoint(int64_t n, const double* means, const double* log_scales, const double* quats,
+                           const double* logits, const double* sh, int deg, const double* model12,
+                           const double* cam17, int W, int H, const double* opts6, const double* g2,
+                           double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
+                           double* d_sh) {
+    if (deg < 0 || deg > 3) return 1;
+    cam_t cam; load_cam(cam17, W, H, &cam);
+    opts_t op; load_opts(opts6, &op);
+    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    if (load_model(model12, &sc)) return 2;
+    int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
+    prep_t pp;
+    if (alloc_prep(n, &pp)) { free_prep(&pp); return 1; }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) preprocess_one(&sc, i, &cam, &op, tiles_x, tiles_y, &pp);
+    int rc = preprocess_adjoint(&sc, &cam, &op, W, H, &pp, g2, d_means, d_log_scales, d_quats, d_logits, d_sh);
+    free_prep(&pp);
+    return rc;
+}
+
+/* The whole adjoint of one model's render (model12 as in orc_preprocess). */
+int orc_adjoint(int64_t n, const double* means, const double* log_scales, const double* quats,
+                const double* logits, const double* sh, int deg, const double* model12, const double* cam17,
+                int W, int H, const double* opts6, const double* bg, const double* gC, const double* gA,
+                const float* zlim /* [H,W] depth buffer or NULL */,
+                double* d_means, double* d_log_scales, double* d_quats, double* d_logits,
+                double* d_sh, double* g2_out /* [n,9] or NULL */) {
+    if (deg < 0 || deg > 3) return 1;
+    cam_t cam; load_cam(cam17, W, H, &cam);
+    opts_t op; load_opts(opts6, &op);
+    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    if (load_model(model12, &sc)) return 2;
+    int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
+    prep_t pp;
+    double* g2 = (double*)calloc(9 * (size_t)(n > 0 ? n : 1), sizeof(double));
+    if (alloc_prep(n, &pp) || !g2) { free_prep(&pp); free(g2); return 1; }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) preprocess_one(&sc, i, &cam, &op, tiles_x, tiles_y, &pp);
+    int rc = composite_adjoint(n, &pp, W, H, &op, bg, gC, gA, zlim, g2);
+    if (!rc) rc = preprocess_adjoint(&sc, &cam, &op, W, H, &pp, g2, d_means, d_log_scales, d_quats, d_logits, d_sh);
+    if (!rc && g2_out) memcpy(g2_out, g2, sizeof(double) * 9 * (size_t)n);
+    free_prep(&pp);
+    free(g2);
+    return rc;
 }

@@ -251,6 +251,60 @@ def workload_batch(seed=4, assets=16, cams_per_asset=8, n_min=20_000, n_max=2_00
     return scenes, cams, cam_scene
 
 
+# --------------------------------------------------------------------------------------
+# Per-model affine transforms (Algorithm 1's M_k) and the multi-asset workload.
+# --------------------------------------------------------------------------------------
+
+def _axis_rotation(axis, angle_rad):
+    """Rotation matrix about a unit axis (Rodrigues)."""
+    a = np.asarray(axis, np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return np.eye(3) + math.sin(angle_rad) * K + (1.0 - math.cos(angle_rad)) * (K @ K)
+
+
+def rigid_model(angle_deg=0.0, axis=(0.0, 1.0, 0.0), translation=(0.0, 0.0, 0.0), scale=1.0):
+    """[A | b] (3x4 float32) with A = scale * rotation(axis, angle), b = translation."""
+    A = scale * _axis_rotation(axis, math.radians(angle_deg))
+    return np.ascontiguousarray(np.concatenate([A, np.asarray(translation, np.float64)[:, None]], 1), np.float32)
+
+
+def affine_model(rng, translation_std=0.3, log_scale_std=0.3, shear=0.3):
+    """A general affine [A | b] (3x4 float32): rotation * shear * anisotropic scale * rotation,
+    det(A) > 0."""
+    def rot():
+        return _axis_rotation(rng.standard_normal(3), rng.uniform(0.0, 2.0 * math.pi))
+    Sh = np.eye(3)
+    Sh[0, 1], Sh[0, 2], Sh[1, 2] = rng.uniform(-shear, shear, 3)
+    A = rot() @ Sh @ np.diag(np.exp(rng.normal(0.0, log_scale_std, 3))) @ rot()
+    b = rng.normal(0.0, translation_std, 3)
+    return np.ascontiguousarray(np.concatenate([A, b[:, None]], 1), np.float32)
+
+
+def workload_multi(seed=5, assets=4, n_min=100_000, n_max=1_000_000, W=1920, H=1080, scale=1.0):
+    """Multi-asset frame (section 3.4, several models in one image): `assets` mixture-scene
+    models (N log-uniform in [n_min, n_max], SH degree uniform in {0..3}, ball radius 2.5),
+    each placed by a rigid transform (rotation about y, uniform scale in [0.7, 1.4]) on a
+    ring of radius 2.5 around the origin, so that the models overlap on screen and
+    interleave in depth; one camera at (0, 3, 14) looking at the origin, 50 deg.
+    `scale` shrinks every Gaussian count (for small parity cases).
+    Returns (scenes, models [K,3,4] float32, camera)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.exp(rng.uniform(math.log(n_min), math.log(n_max), assets))
+    degs = rng.integers(0, 4, assets)
+    scenes, models = [], []
+    for a in range(assets):
+        n = max(1, int(round(ns[a] * scale)))
+        scenes.append(mixture_scene(n, seed * 1000 + a, sh_degree=int(degs[a]), ball_radius=2.5, comp_std=0.4,
+                                    log_scale_mean=-4.0))
+        ang = 2.0 * math.pi * a / assets + rng.uniform(-0.3, 0.3)
+        models.append(rigid_model(rng.uniform(0.0, 360.0), (0.0, 1.0, 0.0),
+                                  (2.5 * math.sin(ang), rng.uniform(-0.5, 0.5), 2.5 * math.cos(ang)),
+                                  rng.uniform(0.7, 1.4)))
+    cam = look_at((0.0, 3.0, 14.0), (0.0, 0.0, 0.0), W, H, 50.0)
+    return scenes, np.stack(models), cam
+
+
 def random_keys(m, seed, kind="random", tile_bits=13):
     """Synthetic (tile, depth) sort inputs for stage tests of the radix sort.
 
