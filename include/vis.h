@@ -238,6 +238,50 @@ VIS_API vis_status vis_render_backward_depth(vis_scene_t scene, const vis_camera
                                              float* d_log_scales, float* d_quats,
                                              float* d_opacity_logits, float* d_sh, void* stream);
 
+/* Several scenes ("models") composited into one image (Algorithm 1: every model is
+ * preprocessed under its own affine transform M_k, then ONE radix sort and one compositing
+ * pass run over the splats of all models, so that splats of different models interleave
+ * in depth -- the order a per-model sort cannot give; section 3.4).
+ *  scenes    host array of n_scenes scene handles (1..65536); the same handle may appear
+ *            more than once (instancing)
+ *  models    host float [n_scenes][12], or NULL for identity transforms: row-major 3x4
+ *            [A | b]; model k draws its Gaussians at A mu + b with covariance A Sigma A^T,
+ *            and evaluates their SH colour along the view ray mapped back into the
+ *            model's own frame (A^-1 (x - camera centre)), so that a rigidly moved model
+ *            keeps its view-dependent appearance. A must be invertible.
+ *  depth     device float32 [H,W] depth buffer as in vis_render_depth, or NULL
+ *  ws        a workspace sized for n = vis_multi_slots(scenes, n_scenes): scene k occupies
+ *            the slots [offset_k, offset_k + n_k), offset_k = sum over j < k of n_j rounded
+ *            up to 256 (the slot of model k's Gaussian i is offset_k + i; the padding
+ *            slots are never listed)
+ * Otherwise as vis_render / vis_render_depth. Errors: VIS_ERR_INVALID_ARG for a null
+ * scene, a non-finite or singular model, or more than 2^31-1 slots. */
+VIS_API vis_status vis_multi_slots(const vis_scene_t* scenes, int n_scenes, int64_t* slots);
+VIS_API vis_status vis_render_multi(const vis_scene_t* scenes, const float* models, int n_scenes,
+                                    const vis_camera* cam, int W, int H, const float bg[3],
+                                    const float* depth, float* out_rgb, float* out_alpha, void* ws,
+                                    size_t ws_bytes, const vis_render_opts* opts, void* stream);
+
+/* Gradient outputs of one scene (device, shaped like the scene's arrays, overwritten). */
+typedef struct {
+    float* d_means;
+    float* d_log_scales;
+    float* d_quats;
+    float* d_opacity_logits;
+    float* d_sh;
+} vis_scene_grads;
+
+/* The adjoint of vis_render_multi (same scenes, models, camera, depth, opts and workspace,
+ * after vis_render_multi): gradients with respect to each model's own, untransformed
+ * parameters. grads: host array of n_scenes gradient sets; a scene handle listed twice
+ * needs two distinct gradient sets (their sum is the handle's gradient). */
+VIS_API vis_status vis_render_backward_multi(const vis_scene_t* scenes, const float* models,
+                                             int n_scenes, const vis_camera* cam, int W, int H,
+                                             const float bg[3], const float* depth,
+                                             const float* d_rgb, const float* d_alpha, void* ws,
+                                             size_t ws_bytes, const vis_render_opts* opts,
+                                             const vis_scene_grads* grads, void* stream);
+
 /* Stable LSD radix sort of (key, value) pairs on the device: the sort stage of the
  * renderer (Algorithm 1, "Radix Sort"; section 3.4, GPU sorting) exposed on its own.
  *  keys_in, vals_in    device uint64[m], uint32[m] (not modified)

@@ -43,6 +43,11 @@ class vis_render_opts(C.Structure):
                 ("collect_stats", C.c_int)]
 
 
+class vis_scene_grads(C.Structure):
+    _fields_ = [("d_means", C.c_void_p), ("d_log_scales", C.c_void_p), ("d_quats", C.c_void_p),
+                ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
+
+
 class vis_ws_layout(C.Structure):
     _fields_ = [("total_bytes", C.c_size_t), ("key_capacity", C.c_int64), ("tiles_x", C.c_int),
                 ("tiles_y", C.c_int), ("sort_passes", C.c_int), ("sorted_buffer", C.c_int),
@@ -83,6 +88,13 @@ def lib():
             "vis_render_backward_depth": (C.c_int, [_P, C.POINTER(vis_camera), C.c_int, C.c_int,
                                                     C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
                                                     C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
+            "vis_multi_slots": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64)]),
+            "vis_render_multi": (C.c_int, [_P, _P, C.c_int, C.POINTER(vis_camera), C.c_int, C.c_int,
+                                           C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
+                                           C.POINTER(vis_render_opts), _P]),
+            "vis_render_backward_multi": (C.c_int, [_P, _P, C.c_int, C.POINTER(vis_camera), C.c_int, C.c_int,
+                                                    C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
+                                                    C.POINTER(vis_render_opts), _P, _P]),
             "vis_sort_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
             "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
@@ -257,6 +269,51 @@ def vis_last_error():
 
 
 # ----------------------------------------------------------------------------------
+def _handles(handles):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    return arr
+
+
+def _models(models, k):
+    """Host float32 [k][12] array (row-major [A | b] per scene) or None."""
+    if models is None:
+        return None, None
+    import numpy as np
+    m = np.ascontiguousarray(np.asarray(models, np.float32).reshape(k, 12))
+    return m, m.ctypes.data_as(_P)
+
+
+def vis_multi_slots(handles):
+    n = C.c_int64()
+    _ok(lib().vis_multi_slots(_handles(handles), len(handles), C.byref(n)))
+    return n.value
+
+
+def vis_render_multi(handles, models, cam, W, H, bg, out_rgb, out_alpha, ws, opts=None, stream=None, depth=None):
+    """handles: scene handles; models: [k,3,4] float array-like or None (identities)."""
+    c = cam if isinstance(cam, vis_camera) else make_camera(cam)
+    hs = _handles(handles)
+    m, mp = _models(models, len(handles))
+    _ok(lib().vis_render_multi(hs, mp, len(handles), C.byref(c), int(W), int(H), _bg(bg),
+                               None if depth is None else _ptr(depth), _ptr(out_rgb), _ptr(out_alpha), _ptr(ws),
+                               ws.numel() * ws.element_size(), _opts_ref(opts), _stream(stream)))
+
+
+def vis_render_backward_multi(handles, models, cam, W, H, bg, d_rgb, d_alpha, ws, grads, opts=None, stream=None,
+                              depth=None):
+    """grads: one dict of gradient tensors (FIELDS) per scene."""
+    c = cam if isinstance(cam, vis_camera) else make_camera(cam)
+    hs = _handles(handles)
+    m, mp = _models(models, len(handles))
+    gs = (vis_scene_grads * len(handles))(*[vis_scene_grads(*[g[k].data_ptr() for k in
+                                                               ("means", "log_scales", "quats", "opacity_logits",
+                                                                "sh")]) for g in grads])
+    _ok(lib().vis_render_backward_multi(hs, mp, len(handles), C.byref(c), int(W), int(H), _bg(bg),
+                                        None if depth is None else _ptr(depth), _ptr(d_rgb), _ptr(d_alpha),
+                                        _ptr(ws), ws.numel() * ws.element_size(), _opts_ref(opts), gs,
+                                        _stream(stream)))
+
+
 # Convenience layer
 # ----------------------------------------------------------------------------------
 
@@ -331,6 +388,23 @@ def _render_checked(scene, cam, W, H, bg, ws, opts, stream=None, depth=None):
     raise VisError(VIS_ERR_CAPACITY, "workspace growth did not converge")
 
 
+def _render_multi_checked(scenes, models, cam, W, H, bg, ws, opts, stream=None, depth=None):
+    torch = _torch()
+    out_rgb = torch.empty((3, H, W), dtype=torch.float32, device=ws.buf.device)
+    out_alpha = torch.empty((H, W), dtype=torch.float32, device=ws.buf.device)
+    handles = [s.handle for s in scenes]
+    for _ in range(2):
+        vis_render_multi(handles, models, cam, W, H, bg, out_rgb, out_alpha, ws.buf, opts, stream, depth)
+        try:
+            vis_check(ws.buf, stream)
+            return out_rgb, out_alpha
+        except VisError as e:
+            if e.status != VIS_ERR_CAPACITY:
+                raise
+            ws.grow(e.num_keys)
+    raise VisError(VIS_ERR_CAPACITY, "workspace growth did not converge")
+
+
 def _make_autograd():
     torch = _torch()
 
@@ -355,10 +429,30 @@ def _make_autograd():
             return (None, None, None, None, None, None, None, None, grads["means"], grads["log_scales"],
                     grads["quats"], grads["opacity_logits"], grads["sh"])
 
-    return RenderFn
+    class RenderMultiFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, scenes, models, cam, W, H, bg, ws, opts, depth, *tensors):
+            rgb, alpha = _render_multi_checked(scenes, models, cam, W, H, bg, ws, opts, depth=depth)
+            ctx.args = (scenes, models, cam, W, H, bg, ws, opts, depth)
+            return rgb, alpha
+
+        @staticmethod
+        def backward(ctx, d_rgb, d_alpha):
+            scenes, models, cam, W, H, bg, ws, opts, depth = ctx.args
+            dev = ws.buf.device
+            d_rgb = (d_rgb if d_rgb is not None else torch.zeros((3, H, W), device=dev)).contiguous().float()
+            d_alpha = (d_alpha if d_alpha is not None else torch.zeros((H, W), device=dev)).contiguous().float()
+            grads = [{k: torch.empty_like(s.tensors[k]) for k in FIELDS} for s in scenes]
+            vis_render_backward_multi([s.handle for s in scenes], models, cam, W, H, bg, d_rgb, d_alpha, ws.buf,
+                                      grads, opts, depth=depth)
+            flat = [g[k] for g in grads for k in FIELDS]
+            return (None,) * 9 + tuple(flat)
+
+    return RenderFn, RenderMultiFn
 
 
 _RENDER_FN = None
+_RENDER_MULTI_FN = None
 
 
 def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = None, opts=None, depth=None):
@@ -369,9 +463,9 @@ def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = N
     alpha [H,W]). The workspace keeps the forward's intermediates for the backward; do
     not reuse it for another render before calling backward.
     """
-    global _RENDER_FN
+    global _RENDER_FN, _RENDER_MULTI_FN
     if _RENDER_FN is None:
-        _RENDER_FN = _make_autograd()
+        _RENDER_FN, _RENDER_MULTI_FN = _make_autograd()
     if ws is None:
         ws = Workspace(scene.n, W, H, opts=opts)
     t = scene.tensors
@@ -379,6 +473,32 @@ def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = N
         depth = depth.contiguous().float()
     return _RENDER_FN.apply(scene, cam, W, H, tuple(bg), ws, opts, depth, t["means"], t["log_scales"], t["quats"],
                             t["opacity_logits"], t["sh"])
+
+
+def multi_workspace(scenes, W, H, key_capacity=None, opts=None):
+    """A Workspace sized for render_multi over `scenes` (vis_multi_slots slots)."""
+    return Workspace(vis_multi_slots([s.handle for s in scenes]), W, H, key_capacity, opts)
+
+
+def render_multi(scenes, models, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = None, opts=None,
+                 depth=None):
+    """Several scenes in one image, each under its own affine transform (models: [k,3,4]
+    float array-like, row-major [A | b], or None for identities), composited in one global
+    depth order (vis_render_multi). Differentiable w.r.t. every scene's tensors; the
+    gradients are w.r.t. the untransformed parameters. Returns (rgb [3,H,W], alpha [H,W])."""
+    global _RENDER_FN, _RENDER_MULTI_FN
+    if _RENDER_FN is None:
+        _RENDER_FN, _RENDER_MULTI_FN = _make_autograd()
+    scenes = list(scenes)
+    if ws is None:
+        ws = multi_workspace(scenes, W, H, opts=opts)
+    if models is not None:
+        import numpy as np
+        models = np.ascontiguousarray(np.asarray(models, np.float32).reshape(len(scenes), 12))
+    if depth is not None:
+        depth = depth.contiguous().float()
+    tensors = [s.tensors[k] for s in scenes for k in FIELDS]
+    return _RENDER_MULTI_FN.apply(scenes, models, cam, W, H, tuple(bg), ws, opts, depth, *tensors)
 
 
 def sort_pairs(keys, vals, key_bits=64):

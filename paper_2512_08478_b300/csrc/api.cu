@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "vis_internal.cuh"
 
@@ -99,7 +100,7 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     vis::PrepParams p;
     std::memset(&p, 0, sizeof(p));
     p.means = s->means; p.log_scales = s->log_scales; p.quats = s->quats; p.logits = s->logits; p.sh = s->sh;
-    p.deg = s->deg; p.n = (int)s->n;
+    p.deg = s->deg; p.n = (int)s->n; p.n_pad = (int)s->n; p.index_offset = 0;
     for (int k = 0; k < 9; ++k) p.R[k] = c->R[k];
     for (int k = 0; k < 3; ++k) p.t[k] = c->t[k];
     p.fx = c->fx; p.fy = c->fy; p.cx = c->cx; p.cy = c->cy; p.near_z = c->near_z;
@@ -117,6 +118,70 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     p.count_survivors = L.mode == vis::kSortDepthFirst || L.mode == vis::kSortDepthBin;
     vis::sh_constants(p.shc);
     return p;
+}
+
+constexpr int kMaxScenes = 1 << 16;   // scenes per multi-scene render
+
+// adjugate and determinant of a 3x3 row-major matrix
+double adjugate3(const double A[9], double adj[9]) {
+    adj[0] = A[4] * A[8] - A[5] * A[7]; adj[1] = A[2] * A[7] - A[1] * A[8]; adj[2] = A[1] * A[5] - A[2] * A[4];
+    adj[3] = A[5] * A[6] - A[3] * A[8]; adj[4] = A[0] * A[8] - A[2] * A[6]; adj[5] = A[2] * A[3] - A[0] * A[5];
+    adj[6] = A[3] * A[7] - A[4] * A[6]; adj[7] = A[1] * A[6] - A[0] * A[7]; adj[8] = A[0] * A[4] - A[1] * A[3];
+    return A[0] * adj[0] + A[1] * adj[3] + A[2] * adj[6];
+}
+
+// A model transform [A | b] (row-major 3x4) must be finite with A invertible.
+vis_status check_model(const float* m, int k) {
+    for (int j = 0; j < 12; ++j)
+        if (!std::isfinite(m[j])) return fail(VIS_ERR_INVALID_ARG, "model %d has a non-finite value", k);
+    double A[9], adj[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) A[3 * r + c] = m[4 * r + c];
+    const double det = adjugate3(A, adj);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return fail(VIS_ERR_INVALID_ARG, "model %d is singular", k);
+    for (int j = 0; j < 9; ++j)
+        if (!std::isfinite(adj[j] / det)) return fail(VIS_ERR_INVALID_ARG, "model %d is singular", k);
+    return VIS_OK;
+}
+
+// Fold a model transform M = [A | b] into the view (Algorithm 1: x_w = M [mu; 1], then the
+// camera): x_c = R (A mu + b) + t = (R A) mu + (R b + t). R A and R b + t are formed in double
+// and stored as float pairs (value + residue). The SH ray starts at the camera centre seen
+// from the model, A^-1 (c - b) with c = -R^T t, so colours are evaluated in the model's frame.
+void fold_model(vis::PrepParams& p, const vis_camera* c, const float* m) {
+    double A[9], b[3], R[9], t[3], adj[9];
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) { A[3 * r + k] = m[4 * r + k]; R[3 * r + k] = c->R[3 * r + k]; }
+        b[r] = m[4 * r + 3];
+        t[r] = c->t[r];
+    }
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) {
+            const double v = R[3 * r + 0] * A[k] + R[3 * r + 1] * A[3 + k] + R[3 * r + 2] * A[6 + k];
+            p.R[3 * r + k] = (float)v;
+            p.R_lo[3 * r + k] = (float)(v - (double)p.R[3 * r + k]);
+        }
+        const double v = R[3 * r + 0] * b[0] + R[3 * r + 1] * b[1] + R[3 * r + 2] * b[2] + t[r];
+        p.t[r] = (float)v;
+        p.t_lo[r] = (float)(v - (double)p.t[r]);
+    }
+    const double det = adjugate3(A, adj);
+    double w[3];
+    for (int j = 0; j < 3; ++j) w[j] = -(R[j] * t[0] + R[3 + j] * t[1] + R[6 + j] * t[2]) - b[j];
+    for (int r = 0; r < 3; ++r)
+        p.cam_pos[r] = (float)((adj[3 * r] * w[0] + adj[3 * r + 1] * w[1] + adj[3 * r + 2] * w[2]) / det);
+}
+
+// Workspace slots of a list of scenes: each scene starts at a multiple of kPrepThreads
+// (its Gaussians fill whole preprocess blocks) when `padded`, else the scene's own size.
+int64_t scene_slots(const vis_scene* const* scenes, int n_scenes, bool padded, int64_t* offsets) {
+    int64_t off = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        if (offsets) offsets[k] = off;
+        const int64_t n = scenes[k]->n;
+        off += padded ? (n + vis::kPrepThreads - 1) / vis::kPrepThreads * vis::kPrepThreads : n;
+    }
+    return off;
 }
 
 // ---- per-stage profiling (vis_profile_begin / vis_profile_end) ----
@@ -370,10 +435,25 @@ vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const 
     return VIS_OK;
 }
 
-static vis_status prepare(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], void* ws,
-                          size_t ws_bytes, const vis_render_opts* opts, vis_render_opts* o, vis::Layout* L) {
-    if (!scene) return fail(VIS_ERR_INVALID_ARG, "scene is null");
-    vis_status st = check_size(scene->n, W, H);
+// Validates a render's arguments for a list of scenes and lays out the workspace over their
+// slots (a single scene: its own n; several: each padded to whole preprocess blocks).
+static vis_status prepare(const vis_scene_t* scenes, int n_scenes, bool padded, const float* models,
+                          const vis_camera* cam, int W, int H, const float bg[3], void* ws, size_t ws_bytes,
+                          const vis_render_opts* opts, vis_render_opts* o, vis::Layout* L,
+                          std::vector<int64_t>* offsets) {
+    if (!scenes) return fail(VIS_ERR_INVALID_ARG, "scenes is null");
+    if (n_scenes < 1 || n_scenes > kMaxScenes)
+        return fail(VIS_ERR_INVALID_ARG, "n_scenes must be in [1, %d] (got %d)", kMaxScenes, n_scenes);
+    for (int k = 0; k < n_scenes; ++k) {
+        if (!scenes[k]) return fail(VIS_ERR_INVALID_ARG, "scene %d is null", k);
+        if (models) {
+            vis_status st = check_model(models + 12 * (size_t)k, k);
+            if (st) return st;
+        }
+    }
+    offsets->assign(n_scenes, 0);
+    const int64_t slots = scene_slots(scenes, n_scenes, padded, offsets->data());
+    vis_status st = check_size(slots, W, H);
     if (st) return st;
     if ((st = check_camera(cam))) return st;
     if (!bg) return fail(VIS_ERR_INVALID_ARG, "bg is null");
@@ -382,29 +462,45 @@ static vis_status prepare(vis_scene_t scene, const vis_camera* cam, int W, int H
     *o = resolve_opts(opts);
     if ((st = check_opts(*o))) return st;
     if (!ws || !aligned16(ws)) return fail(VIS_ERR_INVALID_ARG, "workspace is null or not 16-byte aligned");
-    const int64_t cap = vis::capacity_for(scene->n, W, H, o->tile, o->sort_mode, ws_bytes);
+    const int64_t cap = vis::capacity_for(slots, W, H, o->tile, o->sort_mode, ws_bytes);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
-    *L = vis::make_layout(scene->n, W, H, o->tile, cap, o->sort_mode);
+    *L = vis::make_layout(slots, W, H, o->tile, cap, o->sort_mode);
     return VIS_OK;
 }
 
-static vis_status render_impl(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+// Preprocess parameters of scene k of a (multi-)scene render.
+static vis::PrepParams scene_params(const vis_scene_t* scenes, const float* models, int k, bool padded,
+                                    const std::vector<int64_t>& offsets, const vis_camera* cam, int W, int H,
+                                    const vis::Layout& L, const vis_render_opts& o) {
+    vis::PrepParams p = make_params(scenes[k], cam, W, H, L, o);
+    p.index_offset = offsets[k];
+    if (padded) p.n_pad = (int)((scenes[k]->n + vis::kPrepThreads - 1) / vis::kPrepThreads * vis::kPrepThreads);
+    if (models) fold_model(p, cam, models + 12 * (size_t)k);
+    return p;
+}
+
+// One image of one or more scenes: every scene is preprocessed into its slots (with its
+// model transform folded into the view), then one global sort and one compositing pass run
+// over all slots (Algorithm 1).
+static vis_status render_impl(const vis_scene_t* scenes, const float* models, int n_scenes, bool padded,
+                              const vis_camera* cam, int W, int H, const float bg[3],
                               const float* zlim, float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
                               const vis_render_opts* opts, void* stream_) {
     vis_render_opts o;
     vis::Layout L;
-    vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
+    std::vector<int64_t> offsets;
+    vis_status st = prepare(scenes, n_scenes, padded, models, cam, W, H, bg, ws, ws_bytes, opts, &o, &L, &offsets);
     if (st) return st;
     if (!out_rgb || !out_alpha || !aligned16(out_rgb) || !aligned16(out_alpha))
         return fail(VIS_ERR_INVALID_ARG, "out_rgb / out_alpha null or not 16-byte aligned");
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     char* w = static_cast<char*>(ws);
-    const vis::PrepParams p = make_params(scene, cam, W, H, L, o);
     prof_mark(0, stream);
     if ((st = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, stream), "clear workspace")))
         return st;
     prof_mark(1, stream);
-    vis::launch_preprocess(p, L, w, stream);
+    for (int k = 0; k < n_scenes; ++k)
+        vis::launch_preprocess(scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o), L, w, stream);
     prof_mark(2, stream);
     if (L.mode == vis::kSortDepthBin) {
         vis::launch_depth_sort(L, w, stream);
@@ -419,7 +515,7 @@ static vis_status render_impl(vis_scene_t scene, const vis_camera* cam, int W, i
         prof_mark(5, stream);
         if (!L.tile_fused) vis::launch_ranges32(L, w, stream);   // the counts-first tile sort wrote them
     } else {
-        vis::launch_scan_and_duplicate(L, w, scene->n, stream);
+        vis::launch_scan_and_duplicate(L, w, L.n, stream);
         prof_mark(3, stream);
         vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark : nullptr, 4);
         prof_mark(5, stream);
@@ -443,14 +539,37 @@ static vis_status render_impl(vis_scene_t scene, const vis_camera* cam, int W, i
 
 vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3], float* out_rgb,
                       float* out_alpha, void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
-    return render_impl(scene, cam, W, H, bg, nullptr, out_rgb, out_alpha, ws, ws_bytes, opts, stream_);
+    return render_impl(&scene, nullptr, 1, false, cam, W, H, bg, nullptr, out_rgb, out_alpha, ws, ws_bytes, opts,
+                       stream_);
 }
 
 vis_status vis_render_depth(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
                             const float* depth, float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
                             const vis_render_opts* opts, void* stream_) {
     if (!depth || !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer null or not 16-byte aligned");
-    return render_impl(scene, cam, W, H, bg, depth, out_rgb, out_alpha, ws, ws_bytes, opts, stream_);
+    return render_impl(&scene, nullptr, 1, false, cam, W, H, bg, depth, out_rgb, out_alpha, ws, ws_bytes, opts,
+                       stream_);
+}
+
+vis_status vis_multi_slots(const vis_scene_t* scenes, int n_scenes, int64_t* slots) {
+    if (!slots) return fail(VIS_ERR_INVALID_ARG, "slots is null");
+    if (!scenes) return fail(VIS_ERR_INVALID_ARG, "scenes is null");
+    if (n_scenes < 1 || n_scenes > kMaxScenes)
+        return fail(VIS_ERR_INVALID_ARG, "n_scenes must be in [1, %d] (got %d)", kMaxScenes, n_scenes);
+    for (int k = 0; k < n_scenes; ++k)
+        if (!scenes[k]) return fail(VIS_ERR_INVALID_ARG, "scene %d is null", k);
+    *slots = scene_slots(scenes, n_scenes, true, nullptr);
+    if (*slots > 0x7fffffffLL) return fail(VIS_ERR_INVALID_ARG, "the scenes hold more than 2^31-1 slots");
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_render_multi(const vis_scene_t* scenes, const float* models, int n_scenes, const vis_camera* cam,
+                            int W, int H, const float bg[3], const float* depth, float* out_rgb, float* out_alpha,
+                            void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
+    if (depth && !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer not 16-byte aligned");
+    return render_impl(scenes, models, n_scenes, true, cam, W, H, bg, depth, out_rgb, out_alpha, ws, ws_bytes, opts,
+                       stream_);
 }
 
 vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
@@ -471,32 +590,55 @@ vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
     return VIS_OK;
 }
 
-static vis_status backward_impl(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
-                                const float* zlim, const float* d_rgb, const float* d_alpha, void* ws,
-                                size_t ws_bytes, const vis_render_opts* opts, float* d_means, float* d_log_scales,
-                                float* d_quats, float* d_opacity_logits, float* d_sh, void* stream_) {
+// Adjoint of render_impl: the compositing adjoint over all slots, then each scene's
+// preprocess adjoint into its own gradient buffers.
+static vis_status backward_impl(const vis_scene_t* scenes, const float* models, int n_scenes, bool padded,
+                                const vis_camera* cam, int W, int H, const float bg[3], const float* zlim,
+                                const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
+                                const vis_render_opts* opts, const vis_scene_grads* grads, void* stream_) {
     vis_render_opts o;
     vis::Layout L;
-    vis_status st = prepare(scene, cam, W, H, bg, ws, ws_bytes, opts, &o, &L);
+    std::vector<int64_t> offsets;
+    vis_status st = prepare(scenes, n_scenes, padded, models, cam, W, H, bg, ws, ws_bytes, opts, &o, &L, &offsets);
     if (st) return st;
-    const void* ptrs[7] = {d_rgb, d_alpha, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
-    for (int k = 0; k < 7; ++k)
-        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "gradient buffer %d null or misaligned", k);
+    if (!d_rgb || !d_alpha || !aligned16(d_rgb) || !aligned16(d_alpha))
+        return fail(VIS_ERR_INVALID_ARG, "d_rgb / d_alpha null or not 16-byte aligned");
+    if (!grads) return fail(VIS_ERR_INVALID_ARG, "grads is null");
+    for (int k = 0; k < n_scenes; ++k) {
+        const vis_scene_grads& g = grads[k];
+        const void* ptrs[5] = {g.d_means, g.d_log_scales, g.d_quats, g.d_opacity_logits, g.d_sh};
+        for (int j = 0; j < 5; ++j)
+            if (!ptrs[j] || !aligned16(ptrs[j]))
+                return fail(VIS_ERR_INVALID_ARG, "gradient buffer %d of scene %d null or misaligned", j, k);
+    }
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    const vis::PrepParams p = make_params(scene, cam, W, H, L, o);
-    vis::launch_backward(p, L, static_cast<char*>(ws), bg, o.alpha_min, o.alpha_max, o.t_stop, d_rgb, d_alpha,
-                         d_means, d_log_scales, d_quats, d_opacity_logits, d_sh, zlim, stream);
+    char* w = static_cast<char*>(ws);
+    vis::launch_composite_backward(L, w, bg, o.alpha_min, o.alpha_max, d_rgb, d_alpha, zlim, stream);
+    for (int k = 0; k < n_scenes; ++k) {
+        const vis_scene_grads& g = grads[k];
+        vis::launch_preprocess_backward(scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o), L, w,
+                                        g.d_means, g.d_log_scales, g.d_quats, g.d_opacity_logits, g.d_sh, stream);
+    }
     if ((st = cuda_check(cudaGetLastError(), "launch"))) return st;
     g_err.clear();
     return VIS_OK;
+}
+
+static vis_status backward_one(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
+                               const float* zlim, const float* d_rgb, const float* d_alpha, void* ws,
+                               size_t ws_bytes, const vis_render_opts* opts, float* d_means, float* d_log_scales,
+                               float* d_quats, float* d_opacity_logits, float* d_sh, void* stream_) {
+    const vis_scene_grads g = {d_means, d_log_scales, d_quats, d_opacity_logits, d_sh};
+    return backward_impl(&scene, nullptr, 1, false, cam, W, H, bg, zlim, d_rgb, d_alpha, ws, ws_bytes, opts, &g,
+                         stream_);
 }
 
 vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
                                const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
                                const vis_render_opts* opts, float* d_means, float* d_log_scales, float* d_quats,
                                float* d_opacity_logits, float* d_sh, void* stream_) {
-    return backward_impl(scene, cam, W, H, bg, nullptr, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
-                         d_quats, d_opacity_logits, d_sh, stream_);
+    return backward_one(scene, cam, W, H, bg, nullptr, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
+                        d_quats, d_opacity_logits, d_sh, stream_);
 }
 
 vis_status vis_render_backward_depth(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
@@ -505,8 +647,17 @@ vis_status vis_render_backward_depth(vis_scene_t scene, const vis_camera* cam, i
                                      float* d_log_scales, float* d_quats, float* d_opacity_logits, float* d_sh,
                                      void* stream_) {
     if (!depth || !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer null or not 16-byte aligned");
-    return backward_impl(scene, cam, W, H, bg, depth, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
-                         d_quats, d_opacity_logits, d_sh, stream_);
+    return backward_one(scene, cam, W, H, bg, depth, d_rgb, d_alpha, ws, ws_bytes, opts, d_means, d_log_scales,
+                        d_quats, d_opacity_logits, d_sh, stream_);
+}
+
+vis_status vis_render_backward_multi(const vis_scene_t* scenes, const float* models, int n_scenes,
+                                     const vis_camera* cam, int W, int H, const float bg[3], const float* depth,
+                                     const float* d_rgb, const float* d_alpha, void* ws, size_t ws_bytes,
+                                     const vis_render_opts* opts, const vis_scene_grads* grads, void* stream_) {
+    if (depth && !aligned16(depth)) return fail(VIS_ERR_INVALID_ARG, "depth buffer not 16-byte aligned");
+    return backward_impl(scenes, models, n_scenes, true, cam, W, H, bg, depth, d_rgb, d_alpha, ws, ws_bytes, opts,
+                         grads, stream_);
 }
 
 vis_status vis_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,

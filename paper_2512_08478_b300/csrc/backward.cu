@@ -186,11 +186,13 @@ __global__ void __launch_bounds__(kPrepThreads)
 preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uint32_t* __restrict__ touched,
                            float* __restrict__ d_means, float* __restrict__ d_log_scales,
                            float* __restrict__ d_quats, float* __restrict__ d_logits, float* __restrict__ d_sh) {
+    // i: the Gaussian in the scene's arrays; gi: its workspace slot (multi-scene renders)
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
     if (i >= p.n) return;
+    const int64_t gi = p.index_offset + i;
     constexpr int K = (DEG + 1) * (DEG + 1);
     float* dsh = d_sh + (size_t)i * K * 3;
-    if (touched[i] == 0) {
+    if (touched[gi] == 0) {
         for (int k = 0; k < 3; ++k) { d_means[3 * i + k] = 0.f; d_log_scales[3 * i + k] = 0.f; }
         for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = 0.f;
         d_logits[i] = 0.f;
@@ -199,7 +201,7 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
     }
     float gg[9];
 #pragma unroll
-    for (int f = 0; f < 9; ++f) gg[f] = g2[9 * (size_t)i + f];
+    for (int f = 0; f < 9; ++f) gg[f] = g2[9 * (size_t)gi + f];
     const float mx = p.means[3 * i], my = p.means[3 * i + 1], mz = p.means[3 * i + 2];
 
     // ---- colour: rgb_c = max(0, sum_k sh_kc Y_k(dir) + 0.5) ----
@@ -389,11 +391,8 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
     d_quats[4 * i + 3] = (gz - qz * dq) * qinv;
 }
 
-void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3], float alpha_min,
-                     float alpha_max, float t_stop, const float* d_rgb, const float* d_alpha, float* d_means,
-                     float* d_log_scales, float* d_quats, float* d_logits, float* d_sh, const float* zlim,
-                     cudaStream_t stream) {
-    (void)t_stop;
+void launch_composite_backward(const Layout& L, char* ws, const float bg[3], float alpha_min, float alpha_max,
+                               const float* d_rgb, const float* d_alpha, const float* zlim, cudaStream_t stream) {
     float* g2 = reinterpret_cast<float*>(ws + L.off_g2);
     cudaMemsetAsync(g2, 0, sizeof(float) * 9 * (size_t)L.n, stream);
     const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
@@ -420,9 +419,15 @@ void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float
     }
 #undef VIS_LAUNCH_BWD_D
 #undef VIS_LAUNCH_BWD
+}
+
+void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char* ws, float* d_means,
+                                float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
+                                cudaStream_t stream) {
+    const float* g2 = reinterpret_cast<const float*>(ws + L.off_g2);
     if (p.n > 0) {
         const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
-        const int blocks = (int)L.prep_blocks;
+        const int blocks = (p.n + kPrepThreads - 1) / kPrepThreads;
 #define VIS_LAUNCH_PBWD(D)                                                                                \
     preprocess_backward_kernel<D><<<blocks, kPrepThreads, 0, stream>>>(p, g2, touched, d_means, d_log_scales, \
                                                                        d_quats, d_logits, d_sh)

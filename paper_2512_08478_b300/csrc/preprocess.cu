@@ -23,7 +23,10 @@ __global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
                   uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
                   uint32_t* __restrict__ block_sums) {
+    // i: the Gaussian in the scene's arrays; gi: its slot in the workspace (a multi-scene
+    // render places scene k at index_offset = the sum of the earlier scenes' padded sizes)
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    const int64_t gi = p.index_offset + i;
     __shared__ float s_trim[7][kPrepThreads];
     uint32_t touched = 0;
     if (i < p.n) {
@@ -34,16 +37,19 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         float2 pc[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            float2 acc = make_float2(p.t[r], 0.f);
+            float2 acc = make_float2(p.t[r], p.t_lo[r]);
             acc = ff_add(acc, two_prod(p.R[3 * r + 0], mx));
             acc = ff_add(acc, two_prod(p.R[3 * r + 1], my));
             acc = ff_add(acc, two_prod(p.R[3 * r + 2], mz));
-            pc[r] = acc;
+            acc.y = __fmaf_rn(p.R_lo[3 * r + 0], mx, acc.y);   // residues of a folded model transform
+            acc.y = __fmaf_rn(p.R_lo[3 * r + 1], my, acc.y);
+            acc.y = __fmaf_rn(p.R_lo[3 * r + 2], mz, acc.y);
+            pc[r] = fast_two_sum(acc.x, acc.y);
         }
         const float z = pc[2].x;
         const float logit = __ldg(p.logits + i);
         const float opac = 1.f / (1.f + __expf(-logit));
-        depth_out[i] = z;
+        depth_out[gi] = z;
         bool ok = (z > p.near_z) && (opac >= p.alpha_min);
         uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, trims = 0;
         if (ok) {
@@ -198,9 +204,9 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                             col[2] += __ldg(shi + 3 * k + 2) * Y[k];
                         }
                     }
-                    rec[3 * (size_t)i + 0] = make_float4(u.x, v.x, u.y, v.y);
-                    rec[3 * (size_t)i + 1] = make_float4(ex * i1, ey * i1, -ey * i2, ex * i2);
-                    rec[3 * (size_t)i + 2] = make_float4(opac, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f),
+                    rec[3 * (size_t)gi + 0] = make_float4(u.x, v.x, u.y, v.y);
+                    rec[3 * (size_t)gi + 1] = make_float4(ex * i1, ey * i1, -ey * i2, ex * i2);
+                    rec[3 * (size_t)gi + 2] = make_float4(opac, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f),
                                                          fmaxf(col[2], 0.f));
                 }
                 if (touched > 0 && p.tight_extent == 2 && ix1 - ix0 > 1) {
@@ -247,8 +253,11 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             }
         }
         if (touched == 0) { x0 = x1 = y0 = y1 = 0; trims = 0; }
-        rect_out[i] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, 0u);
-        touched_out[i] = touched;
+        rect_out[gi] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, 0u);
+        touched_out[gi] = touched;
+    } else if (i < p.n_pad) {   // padding slots of a multi-scene render: no copies
+        rect_out[gi] = make_uint4(0u, 0u, 0u, 0u);
+        touched_out[gi] = 0u;
     }
     // block sum of tiles touched (for the offset scan of the index-order duplication) or, for
     // the depth-first sorts, of survivors (for their compaction)
@@ -262,13 +271,14 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         uint32_t tot = 0;
 #pragma unroll
         for (int w = 0; w < kPrepThreads / 32; ++w) tot += warp_sums[w];
-        block_sums[blockIdx.x] = tot;
+        block_sums[p.index_offset / kPrepThreads + blockIdx.x] = tot;
     }
 }
 
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream) {
-    if (p.n <= 0) return;
-    const int blocks = (int)L.prep_blocks;
+    if (p.n_pad <= 0) return;
+    const int blocks = (p.n_pad + kPrepThreads - 1) / kPrepThreads;
+    (void)L;
     preprocess_kernel<<<blocks, kPrepThreads, 0, stream>>>(
         p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
         reinterpret_cast<uint4*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),

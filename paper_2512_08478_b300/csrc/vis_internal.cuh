@@ -111,14 +111,20 @@ struct PrepParams {
     int deg;
     int n;
     float R[9], t[3];
+    // rounding residues of R and t (zero for a plain camera): a model transform M_k = [A | b]
+    // is folded into the camera as R A and R b + t, computed in double and carried as float
+    // pairs so that the camera-space position keeps float-float accuracy
+    float R_lo[9], t_lo[3];
     float fx, fy, cx, cy, near_z;
-    float cam_pos[3];
+    float cam_pos[3];        // camera centre in the scene's own frame (A^-1 (c - b) under a model)
     float limx, limy;
     int W, H, tile, tiles_x, tiles_y;
     float dilation, alpha_min;
     float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
     int tight_extent;        // 1: tile rect from the tight opacity-aware 3-sigma box
     int count_survivors;     // block sums count survivors (depth-first sorts), else tiles touched
+    int64_t index_offset;    // workspace slot of the scene's first Gaussian (a multiple of kPrepThreads)
+    int n_pad;               // n rounded up to kPrepThreads in a multi-scene render (else n)
     float shc[12];           // SH polynomial constants, see sh_constants()
 };
 
@@ -197,10 +203,15 @@ QScale q_scale();
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       const float* zlim, cudaStream_t stream);
-void launch_backward(const PrepParams& p, const Layout& L, char* ws, const float bg[3],
-                     float alpha_min, float alpha_max, float t_stop, const float* d_rgb,
-                     const float* d_alpha, float* d_means, float* d_log_scales, float* d_quats,
-                     float* d_logits, float* d_sh, const float* zlim, cudaStream_t stream);
+// Adjoint of the compositing: clears and accumulates the screen-space gradients g2 of
+// all L.n slots (zlim as in launch_composite).
+void launch_composite_backward(const Layout& L, char* ws, const float bg[3], float alpha_min, float alpha_max,
+                               const float* d_rgb, const float* d_alpha, const float* zlim, cudaStream_t stream);
+// Adjoint of the preprocess of one scene (slots p.index_offset ..): g2 -> the scene's
+// parameter gradients.
+void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char* ws, float* d_means,
+                                float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
+                                cudaStream_t stream);
 
 // Stable LSD radix sort of (K key, uint32 value) pairs over `passes` 8-bit digits.
 // Reads keys_in/vals_in, ping-pongs between the a and b buffers and leaves the result in a.

@@ -89,3 +89,41 @@ def test_scene_upload_rejects_null_and_bad_degree(L):
     st = L.vis_scene_upload(p, p, p, p, p, 3, 10, C.byref(h))
     assert st == vis.VIS_OK
     L.vis_scene_destroy(h)
+
+
+def test_multi_scene_slots_and_validation(L):
+    """vis_multi_slots pads every scene to whole 256-Gaussian blocks; vis_render_multi
+    rejects null scenes and non-finite or singular model transforms before any device work."""
+    import ctypes as C
+    import numpy as np
+    from paper_2512_08478_b300 import synth
+    p = C.c_void_p(1 << 20)   # never dereferenced
+    hs = []
+    for n in (300, 1000, 2049, 1):
+        h = C.c_void_p()
+        assert L.vis_scene_upload(p, p, p, p, p, 0, n, C.byref(h)) == vis.VIS_OK
+        hs.append(h)
+    assert vis.vis_multi_slots(hs) == 512 + 1024 + 2304 + 256
+    assert vis.vis_multi_slots(hs[:1]) == 512
+    cam = vis.make_camera(synth.look_at((0, 0, 4), (0, 0, 0), 64, 64, 50.0))
+    bg = (C.c_float * 3)(0, 0, 0)
+    arr = (C.c_void_p * 2)(hs[0].value, hs[1].value)
+
+    def call(models, k=2, scenes=arr):
+        mp = None if models is None else np.ascontiguousarray(models, np.float32).ctypes.data_as(C.c_void_p)
+        return L.vis_render_multi(scenes, mp, k, C.byref(cam), 64, 64, bg, None, p, p, p, 1 << 30, None, None)
+
+    good = np.tile(np.concatenate([np.eye(3), np.zeros((3, 1))], 1)[None], (2, 1, 1))
+    sing = good.copy()
+    sing[1, 2, :3] = 0.0
+    assert call(sing) == vis.VIS_ERR_INVALID_ARG and "model 1 is singular" in vis.vis_last_error()
+    nan = good.copy()
+    nan[0, 1, 3] = np.nan
+    assert call(nan) == vis.VIS_ERR_INVALID_ARG and "non-finite" in vis.vis_last_error()
+    assert call(good, k=0) == vis.VIS_ERR_INVALID_ARG and "n_scenes" in vis.vis_last_error()
+    holey = (C.c_void_p * 2)(hs[0].value, None)
+    assert call(good, scenes=holey) == vis.VIS_ERR_INVALID_ARG and "scene 1 is null" in vis.vis_last_error()
+    with pytest.raises(vis.VisError):
+        vis.vis_multi_slots([hs[0], C.c_void_p()])
+    for h in hs:
+        L.vis_scene_destroy(h)
