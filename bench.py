@@ -458,6 +458,107 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _merged_rigid(scenes_np, models):
+    """One plain scene of the models' Gaussians under rigid + uniform-scale transforms
+    (means A mu + b, log-scales + log s, rotations composed), SH zero-padded to the highest
+    degree: the same splats drawn through the single-scene path."""
+    from scipy.spatial.transform import Rotation
+    deg = max(s["sh_degree"] for s in scenes_np)
+    K = (deg + 1) ** 2
+    parts = {k: [] for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    for sc, M in zip(scenes_np, models):
+        A, b = M[:, :3].astype(np.float64), M[:, 3].astype(np.float64)
+        s = float(np.cbrt(np.linalg.det(A)))
+        q = sc["quats"].astype(np.float64)
+        rot = Rotation.from_matrix(A / s) * Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], 1))
+        xyzw = rot.as_quat()
+        parts["means"].append(sc["means"] @ A.T + b)
+        parts["log_scales"].append(sc["log_scales"] + math.log(s))
+        parts["quats"].append(np.stack([xyzw[:, 3], xyzw[:, 0], xyzw[:, 1], xyzw[:, 2]], 1))
+        parts["opacity_logits"].append(sc["opacity_logits"])
+        sh = np.zeros((sc["means"].shape[0], K, 3), np.float32)
+        sh[:, : sc["sh"].shape[1]] = sc["sh"]
+        parts["sh"].append(sh)
+    out = {k: np.ascontiguousarray(np.concatenate(v), np.float32) for k, v in parts.items()}
+    out["sh_degree"] = deg
+    return out
+
+
+def run_multi(args):
+    """Multi-asset frame: 4 models (1.8M Gaussians, SH 0..3) placed by rigid transforms,
+    drawn into one 1080p image by vis_render_multi (per-model preprocess, one global sort
+    and compositing); 8 views orbiting the group. Beside it: the same Gaussians merged into
+    one plain scene (SH zero-padded to degree 3) through vis_render."""
+    import ctypes as C
+    import torch
+    import paper_2512_08478_b300 as vis
+    from paper_2512_08478_b300 import synth
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    scenes_np, models, cam0 = synth.workload_multi()
+    W, H = cam0.W, cam0.H
+    cams = [synth.look_at((14.0 * math.sin(2 * math.pi * k / 8), 3.0, 14.0 * math.cos(2 * math.pi * k / 8)),
+                          (0, 0, 0), W, H, 50.0) for k in range(8)]
+    cam_objs = [vis.make_camera(c) for c in cams]
+    scenes = [vis.Scene.from_numpy(s) for s in scenes_np]
+    handles = [s.handle for s in scenes]
+    slots = vis.vis_multi_slots(handles)
+    n_total = sum(s.n for s in scenes)
+    opts = vis.make_opts()
+    ws = vis.Workspace(slots, W, H, key_capacity=16 * slots + (1 << 20), opts=opts)
+    merged = vis.Scene.from_numpy(_merged_rigid(scenes_np, models))
+    wsm = vis.Workspace(merged.n, W, H, key_capacity=16 * merged.n + (1 << 20), opts=opts)
+    rgb = torch.empty((3, H, W), device="cuda")
+    alpha = torch.empty((H, W), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def multi(i):
+        vis.vis_render_multi(handles, models, cam_objs[i % 8], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
+
+    def single(i):
+        vis.vis_render(merged.handle, cam_objs[i % 8], W, H, (0.0, 0.0, 0.0), rgb, alpha, wsm.buf, opts)
+
+    for i in range(args.warmup):
+        multi(i)
+        single(i)
+    keys = vis.vis_check(ws.buf)
+    vis.vis_check(wsm.buf)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        vis.lib().vis_profile_begin()
+        e[0].record(stream)
+        for i in range(args.steps):
+            multi(i)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        stage = (C.c_double * 7)()
+        ns, nr, npass = C.c_int(), C.c_int(), C.c_int()
+        vis._ok(vis.lib().vis_profile_end(stage, 7, C.byref(ns), C.byref(nr), C.byref(npass)))
+        for i in range(args.steps):
+            single(i)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+    vis.vis_check(ws.buf)
+    vis.vis_check(wsm.buf)
+    t_multi = e[0].elapsed_time(e[1]) / args.steps
+    t_single = e[1].elapsed_time(e[2]) / args.steps
+    stage_ms = {STAGES_FUSED[k]: round(stage[k] / max(nr.value, 1), 4) for k in range(7)}
+    line = dict(metric="1080p multi-asset frame ms (4 models, one global sort)", value=round(t_multi, 4),
+                unit="ms/frame", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=round(t_multi, 4),
+                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload="4 mixture models (N log-uniform 1e5..1e6, SH 0..3) placed by rigid "
+                                     "transforms on a ring, 8 orbit views r=14, 1920x1080, 50 deg vfov",
+                            gaussians=[s.n for s in scenes], slots=slots, sh_degrees=[s.sh_degree for s in scenes],
+                            l2="inputs larger than L2; no flush"),
+                merged_scene_ms=round(t_single, 4),
+                merged_note="the same Gaussians as one plain scene, SH zero-padded to degree 3",
+                stage_ms=stage_ms, keys_per_frame=int(keys), gaussians_per_s=round(n_total / t_multi * 1e3, 1),
+                gpu_launches=int(args.steps * (len(scenes) + 9 + kDP + npass.value)), clocks=clk.summary())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def _committed_traffic(kernel, M, n):
     """DRAM bytes per launch from a committed ncu capture (profiles/traffic.json), scaled
     to this launch by keys (sort, composite) or Gaussians (preprocess); None if absent."""
@@ -617,7 +718,7 @@ def main():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch"])
+    ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch", "multi"])
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1, 2, 3],
@@ -631,6 +732,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "multi":
+        run_multi(args)
     else:
         run_ours(args)
 
