@@ -19,6 +19,9 @@
 
 namespace vis {
 
+// FOLDED: the view carries a folded model transform, whose rounding residues R_lo, t_lo join
+// the float-float camera transform (a plain camera has none and skips them)
+template <bool FOLDED>
 __global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
                   uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
@@ -26,7 +29,7 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
     // i: the Gaussian in the scene's arrays; gi: its slot in the workspace (a multi-scene
     // render places scene k at index_offset = the sum of the earlier scenes' padded sizes)
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
-    const int64_t gi = p.index_offset + i;
+    const int gi = (int)p.index_offset + i;   // slots number at most 2^31 - 1
     __shared__ float s_trim[7][kPrepThreads];
     uint32_t touched = 0;
     if (i < p.n) {
@@ -37,14 +40,17 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         float2 pc[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            float2 acc = make_float2(p.t[r], p.t_lo[r]);
+            float2 acc = make_float2(p.t[r], FOLDED ? p.t_lo[r] : 0.f);
             acc = ff_add(acc, two_prod(p.R[3 * r + 0], mx));
             acc = ff_add(acc, two_prod(p.R[3 * r + 1], my));
             acc = ff_add(acc, two_prod(p.R[3 * r + 2], mz));
-            acc.y = __fmaf_rn(p.R_lo[3 * r + 0], mx, acc.y);   // residues of a folded model transform
-            acc.y = __fmaf_rn(p.R_lo[3 * r + 1], my, acc.y);
-            acc.y = __fmaf_rn(p.R_lo[3 * r + 2], mz, acc.y);
-            pc[r] = fast_two_sum(acc.x, acc.y);
+            if (FOLDED) {
+                acc.y = __fmaf_rn(p.R_lo[3 * r + 0], mx, acc.y);
+                acc.y = __fmaf_rn(p.R_lo[3 * r + 1], my, acc.y);
+                acc.y = __fmaf_rn(p.R_lo[3 * r + 2], mz, acc.y);
+                acc = fast_two_sum(acc.x, acc.y);
+            }
+            pc[r] = acc;
         }
         const float z = pc[2].x;
         const float logit = __ldg(p.logits + i);
@@ -278,8 +284,11 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream) {
     if (p.n_pad <= 0) return;
     const int blocks = (p.n_pad + kPrepThreads - 1) / kPrepThreads;
-    (void)L;
-    preprocess_kernel<<<blocks, kPrepThreads, 0, stream>>>(
+    bool folded = false;
+    for (int k = 0; k < 9; ++k) folded |= p.R_lo[k] != 0.f;
+    for (int k = 0; k < 3; ++k) folded |= p.t_lo[k] != 0.f;
+    auto kernel = folded ? preprocess_kernel<true> : preprocess_kernel<false>;
+    kernel<<<blocks, kPrepThreads, 0, stream>>>(
         p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
         reinterpret_cast<uint4*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
         reinterpret_cast<uint32_t*>(ws + L.off_bsum));
