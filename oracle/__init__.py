@@ -109,8 +109,17 @@ def preprocess(scene, cam, opts=None, model=None):
                S=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)), z=np.zeros(n),
                zkey=np.zeros(n, np.float32), radius=np.zeros(n, np.int32),
                rect=np.zeros((n, 4), np.int32))
-    arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
     m = model_array(model)
+    if "cov6" in scene:   # pre-packed form: mean, covariance upper triangle, opacity, SH
+        arrs = [_f64(scene[k]) for k in ("means", "cov6", "opacity", "sh")]
+        rc = _L().orc_preprocess_cov(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]), _mp(m),
+                                     _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
+                                     *[_p(out[k]) for k in ("valid", "uv", "conic", "S", "opacity", "rgb",
+                                                            "z", "zkey", "radius", "rect")])
+        if rc != 0:
+            raise ValueError("oracle preprocess rejected its arguments")
+        return out
+    arrs = [_f64(scene[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")]
     rc = _L().orc_preprocess(C.c_int64(n), *[_p(a) for a in arrs], C.c_int(scene["sh_degree"]), _mp(m),
                              _p(cam_array(cam)), C.c_int(cam.W), C.c_int(cam.H), _p(opts_array(opts)),
                              *[_p(out[k]) for k in ("valid", "uv", "conic", "S", "opacity", "rgb",
@@ -191,6 +200,50 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), opts=None, tile_mask=None, depth=None
     """Preprocess + tile-binned render of one view (depth: optional [H,W] depth buffer)."""
     prep = preprocess(scene, cam, opts)
     return render_tiled(prep, cam.W, cam.H, bg, opts, tile_mask, depth), prep
+
+
+def packed_words(sh_degree):
+    """uint32 words per Gaussian of the colour plane: 3 (deg+1)^2 halves, rounded up to an
+    even number of words (8-byte rows)."""
+    halves = 3 * (sh_degree + 1) ** 2
+    words = (halves + 1) // 2
+    return words + (words & 1)
+
+
+def prepack(scene):
+    """The pre-pack step of Algorithm 1 (section 3.4, FP16 layout), once per scene:
+    Sigma = CovFromScaleRot(s, r) in FP64, then mean, opacity alpha = sigmoid(logit),
+    the covariance's upper triangle (xx, xy, xz, yy, yz, zz) and the SH coefficients are
+    cast to fp16 (round to nearest even) and packed two halves per uint32, low half first:
+      pos  [n,2]  (mu_x, mu_y), (mu_z, alpha)
+      cov  [n,3]  (xx, xy), (xz, yy), (yz, zz)
+      col  [n,W]  the SH coefficients in their [K,3] order, zero-padded (W = packed_words)
+    Returns (planes, decoded): the uint32 planes and the scene they decode to (float64,
+    the pre-packed form the oracle's preprocess takes: means, cov6, opacity, sh)."""
+    n = scene["means"].shape[0]
+    deg = scene["sh_degree"]
+    K = (deg + 1) ** 2
+    sig = covariance(scene["log_scales"], scene["quats"])
+    cov6 = np.stack([sig[:, 0, 0], sig[:, 0, 1], sig[:, 0, 2], sig[:, 1, 1], sig[:, 1, 2], sig[:, 2, 2]], 1)
+    alpha = 1.0 / (1.0 + np.exp(-_f64(scene["opacity_logits"])))
+    mu_h = _f64(scene["means"]).astype(np.float16)
+    a_h = alpha.astype(np.float16)
+    cov_h = cov6.astype(np.float16)
+    sh_h = _f64(scene["sh"]).reshape(n, 3 * K).astype(np.float16)
+
+    def pack(halves):
+        h = np.ascontiguousarray(halves, np.float16)
+        if h.shape[1] % 2:
+            h = np.concatenate([h, np.zeros((n, 1), np.float16)], 1)
+        return np.ascontiguousarray(h).view(np.uint32)
+
+    words = packed_words(deg)
+    col_h = np.zeros((n, 2 * words), np.float16)
+    col_h[:, : 3 * K] = sh_h
+    planes = dict(pos=pack(np.concatenate([mu_h, a_h[:, None]], 1)), cov=pack(cov_h), col=pack(col_h))
+    decoded = dict(means=mu_h.astype(np.float64), cov6=cov_h.astype(np.float64), opacity=a_h.astype(np.float64),
+                   sh=sh_h.astype(np.float64).reshape(n, K, 3), sh_degree=deg)
+    return planes, decoded
 
 
 PREP_KEYS = ("valid", "uv", "conic", "S", "opacity", "rgb", "z", "zkey", "radius", "rect")

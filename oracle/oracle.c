@@ -36,6 +36,11 @@
  *     in the model's own frame, i.e. at the view ray mapped back by A^-1
  *     (dir = normalize(A^-1 (x_w - camera centre))), so a rigidly moved asset carries
  *     its view-dependent colour with it. A singular A is rejected.
+ *   - pre-packed attributes (Algorithm 1, "Pre-pack"; section 3.4, FP16 layout): a
+ *     Gaussian may be given by its mean, its covariance's upper triangle Sigma^(6)
+ *     = (xx, xy, xz, yy, yz, zz) and its opacity alpha directly (the values a packed
+ *     buffer decodes to) instead of log-scales, quaternion and logit; everything
+ *     downstream of Sigma and alpha is the same.
  *
  * Everything is plain loops in double precision; OpenMP parallelises over
  * independent pixels, tiles or Gaussians only (no change of arithmetic order
@@ -211,7 +216,28 @@ typedef struct {
     /* per-model affine transform x_w = A mu + b (Algorithm 1, M_k); has_model 0 = identity */
     int has_model;
     double A[9], b[3], Ainv[9];
+    /* pre-packed form: covariance upper triangle [n,6] and opacity [n] given directly
+     * (NULL: from log_scales, quats and logits) */
+    const double *cov6, *opacity;
 } scene_t;
+
+/* model-space covariance of Gaussian i: from Sigma^(6) when given, else CovFromScaleRot */
+static void model_cov(const scene_t* sc, int64_t i, double Sig[9]) {
+    if (sc->cov6) {
+        const double* c = sc->cov6 + 6 * i;
+        Sig[0] = c[0]; Sig[1] = c[1]; Sig[2] = c[2];
+        Sig[3] = c[1]; Sig[4] = c[3]; Sig[5] = c[4];
+        Sig[6] = c[2]; Sig[7] = c[4]; Sig[8] = c[5];
+        return;
+    }
+    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig);
+}
+
+/* opacity of Gaussian i: given, or sigmoid(logit) */
+static double model_opacity(const scene_t* sc, int64_t i) {
+    if (sc->opacity) return sc->opacity[i];
+    return 1.0 / (1.0 + exp(-(double)sc->logits[i]));
+}
 
 /* model12 = [A | b] row-major 3x4, or NULL for the identity. Returns 1 if A is singular
  * or not finite. */
@@ -302,13 +328,13 @@ static void preprocess_one(const scene_t* sc, int64_t i, const cam_t* cam, const
     double z = p[2];
     out->z[i] = z;
     out->zkey[i] = (float)z;
-    double o = 1.0 / (1.0 + exp(-(double)sc->logits[i]));
+    double o = model_opacity(sc, i);
     out->opacity[i] = o;
     if (!(z > cam->near_z)) return;
     if (o < op->alpha_min) return;
 
     double Sig0[9], Sig[9];
-    covariance3d(sc->log_scales + 3 * i, sc->quats + 4 * i, Sig0);
+    model_cov(sc, i, Sig0);
     world_cov(sc, Sig0, Sig);
 
     double limx = 1.3 * (cam->W / (2.0 * cam->fx)), limy = 1.3 * (cam->H / (2.0 * cam->fy));
@@ -393,9 +419,37 @@ int orc_preprocess(int64_t n, const double* means, const double* log_scales, con
     if (deg < 0 || deg > 3) return 1;
     cam_t cam; load_cam(cam17, W, H, &cam);
     opts_t op; load_opts(opts6, &op);
-    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    scene_t sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.means = means; sc.log_scales = log_scales; sc.quats = quats; sc.logits = logits; sc.sh = sh;
+    sc.deg = deg; sc.n = n;
     if (load_model(model12, &sc)) return 2;
     prep_t out = {valid, uv, conic, S, opacity, rgb, z, zkey, radius, rect};
+    int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
+    memset(conic, 0, sizeof(double) * 3 * n);
+    memset(S, 0, sizeof(double) * 3 * n);
+    memset(uv, 0, sizeof(double) * 2 * n);
+    memset(rgb, 0, sizeof(double) * 3 * n);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) preprocess_one(&sc, i, &cam, &op, tiles_x, tiles_y, &out);
+    return 0;
+}
+
+/* The same preprocess for Gaussians given in the pre-packed form: mean, covariance upper
+ * triangle cov6 [n,6] = (xx, xy, xz, yy, yz, zz), opacity [n] and SH coefficients. */
+int orc_preprocess_cov(int64_t n, const double* means, const double* cov6, const double* opacity,
+                       const double* sh, int deg, const double* model12,
+                       const double* cam17, int W, int H, const double* opts6,
+                       int* valid, double* uv, double* conic, double* S, double* opac_out, double* rgb,
+                       double* z, float* zkey, int* radius, int* rect) {
+    if (deg < 0 || deg > 3) return 1;
+    cam_t cam; load_cam(cam17, W, H, &cam);
+    opts_t op; load_opts(opts6, &op);
+    scene_t sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.means = means; sc.sh = sh; sc.deg = deg; sc.n = n; sc.cov6 = cov6; sc.opacity = opacity;
+    if (load_model(model12, &sc)) return 2;
+    prep_t out = {valid, uv, conic, S, opac_out, rgb, z, zkey, radius, rect};
     int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
     memset(conic, 0, sizeof(double) * 3 * n);
     memset(S, 0, sizeof(double) * 3 * n);
@@ -1067,7 +1121,10 @@ int orc_preprocess_adjoint(int64_t n, const double* means, const double* log_sca
     if (deg < 0 || deg > 3) return 1;
     cam_t cam; load_cam(cam17, W, H, &cam);
     opts_t op; load_opts(opts6, &op);
-    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    scene_t sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.means = means; sc.log_scales = log_scales; sc.quats = quats; sc.logits = logits; sc.sh = sh;
+    sc.deg = deg; sc.n = n;
     if (load_model(model12, &sc)) return 2;
     int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
     prep_t pp;
@@ -1089,7 +1146,10 @@ int orc_adjoint(int64_t n, const double* means, const double* log_scales, const 
     if (deg < 0 || deg > 3) return 1;
     cam_t cam; load_cam(cam17, W, H, &cam);
     opts_t op; load_opts(opts6, &op);
-    scene_t sc = {means, log_scales, quats, logits, sh, deg, n};
+    scene_t sc;
+    memset(&sc, 0, sizeof(sc));
+    sc.means = means; sc.log_scales = log_scales; sc.quats = quats; sc.logits = logits; sc.sh = sh;
+    sc.deg = deg; sc.n = n;
     if (load_model(model12, &sc)) return 2;
     int tiles_x = (W + op.tile - 1) / op.tile, tiles_y = (H + op.tile - 1) / op.tile;
     prep_t pp;
