@@ -195,7 +195,14 @@ def run_ours(args):
         d_rgb = torch.empty_like(rgb)
     cam_objs = [vis.make_camera(c) for c in cams]
     view0 = rank * args.steps
-    dynamic = args.workload == "6m"
+    # pre-packed fp16 scene (Algorithm 1's pre-pack, once, outside the timing); a packed frame
+    # is static (a dynamic scene would have to be re-packed every frame)
+    packed = bool(args.packed) and not fwdbwd
+    if packed:
+        psc = vis.PackedScene.pack(sc)
+        torch.cuda.synchronize()
+    handle = psc.handle if packed else sc.handle
+    dynamic = args.workload == "6m" and not packed
     if dynamic:
         dyn = {k: torch.from_numpy(v).cuda() for k, v in extra.items()}
         means0 = sc.tensors["means"].clone()
@@ -214,7 +221,7 @@ def run_ours(args):
                                    k / n_frames, sc.tensors["means"], sc.tensors["opacity_logits"])
             if timed:
                 upd_ev[i][1].record(stream)
-        vis.vis_render(sc.handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
+        vis.vis_render(handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         if fwdbwd:
             torch.sub(rgb, tgt_rgb, out=d_rgb)
             d_rgb.mul_(2.0 / rgb.numel())
@@ -272,7 +279,7 @@ def run_ours(args):
     a_min = float(np.float32(vis.make_opts().alpha_min))
     for i in range(min(args.steps, len(cam_objs))):
         k = (view0 + i) % len(cam_objs)
-        vis.vis_render(sc.handle, cam_objs[k], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
+        vis.vis_render(handle, cam_objs[k], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
         mlist.append(vis.vis_check(ws.buf))
         touched = ws.buf[lay.off_touched: lay.off_touched + 4 * n].view(torch.int32)
         zview = ws.buf[lay.off_depth: lay.off_depth + 4 * n].view(torch.float32)
@@ -288,7 +295,9 @@ def run_ours(args):
     sh_k = (desc["sh_degree"] + 1) ** 2
     # means + logit read, depth + rect + count written: 32 B each; quaternion + log-scales: 28 B
     # for the Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
-    bytes_pre = n * 32 + n_ok * 28 + n_vis * (12 * sh_k + 48)
+    bytes_pre = n * 40 + n_ok * 28 + n_vis * (12 * sh_k + 48)
+    if packed:   # fp16 planes: pos 8 B for all, cov 12 B in front, colour words per survivor
+        bytes_pre = n * 32 + n_ok * 12 + n_vis * (vis.vis_packed_size(1, desc["sh_degree"])[2] + 48)
     # bytes the tile sort must move: per digit pass key + value read and written; with the fused
     # binning the first pass reads 16 B per surviving splat (first copy, index, rect) and writes a
     # 2 B key + 4 B value per copy, the last reads those and writes the 4 B value
@@ -314,8 +323,11 @@ def run_ours(args):
     elif dom == "preprocess":
         launch_ms = stage_ms["preprocess"]
         algo = float(bytes_pre)
-        unit_note = ("32 B per Gaussian (means, logit, depth, rect, count) + 28 B per Gaussian in front "
+        unit_note = ("40 B per Gaussian (means, logit, depth, rect, count) + 28 B per Gaussian in front "
                      "(quaternion, log-scales) + SH and 48 B record per surviving splat")
+        if packed:
+            unit_note = ("32 B per Gaussian (fp16 mean + opacity, depth, rect, count) + 12 B fp16 covariance per "
+                         "Gaussian in front + fp16 SH words and 48 B record per surviving splat")
     else:
         launch_ms = stage_ms[dom]
         algo = M * (4 + 48) + W * H * (16 + 8)
@@ -331,7 +343,7 @@ def run_ours(args):
         # the compositor is bound by FP32 issue, not HBM: count its (pixel, splat) tests and hits
         # on the first view (one extra render with statistics, outside the timed region)
         st_opts = vis.make_opts(sort_mode=args.sort_mode, collect_stats=1)
-        vis.vis_render(sc.handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
+        vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
                        st_opts)
         vis.vis_check(ws.buf)
         ctrl = vis.read_ctrl(ws.buf)
@@ -365,12 +377,13 @@ def run_ours(args):
         v["frac"] = round(v["achieved_gbs"] / peaks["hbm_gbs"], 4)
 
     # ---- end to end through the C ABI with host buffers ----
-    e2e = run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts)
+    e2e = (run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts) if not packed
+           else dict(value=None, note="not measured for a pre-packed scene"))
 
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(desc, sort_mode=args.sort_mode,
+                config=dict(desc, sort_mode=args.sort_mode, packed=packed,
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk_summary, e2e=e2e,
@@ -383,7 +396,7 @@ def run_ours(args):
                 sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]
                                            + (stage_ms["duplicate"] if args.sort_mode == 2 else 0.0)) * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not packed:
         line["cpu_baseline"] = cpu_baseline(args.workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -725,6 +738,8 @@ def main():
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
                          "2: depth sort then counting binning (default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--packed", action="store_true",
+                    help="render a pre-packed fp16 copy of the scene (packed once, outside the timing)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

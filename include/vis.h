@@ -176,6 +176,30 @@ VIS_API vis_status vis_scene_upload(const float* means, const float* log_scales,
                             int64_t n, vis_scene_t* out);
 VIS_API void vis_scene_destroy(vis_scene_t scene);
 
+/* Pre-packed FP16 scenes (Algorithm 1, "Pre-pack (only once)"; section 3.4, "Pre-pack and
+ * FP16 layout": the covariance is formed once from scale and rotation, and mean, opacity,
+ * the covariance's upper triangle and the colour are cast to fp16 and packed two per
+ * 32-bit word to halve the per-frame attribute bytes). Three device planes per scene,
+ * every value an IEEE half, two per uint32 word, the first in the low 16 bits:
+ *  pos  uint32[n][2]  (mu_x, mu_y), (mu_z, alpha)      alpha = sigmoid(logit), the opacity
+ *  cov  uint32[n][3]  (xx, xy), (xz, yy), (yz, zz)     Sigma = R diag(s)^2 R^T, upper triangle
+ *  col  uint32[n][W]  the SH coefficients in the order of vis_scene_upload's sh array,
+ *                     zero-padded; W = 3 (sh_degree+1)^2 halves rounded up to an even
+ *                     number of words (W = 2, 6, 14, 24 for degrees 0..3)
+ * vis_packed_size gives each plane's bytes (any pointer may be NULL). vis_scene_pack fills
+ * the planes from an fp32 scene on `stream` (covariance and sigmoid in float, then rounding
+ * to nearest even). vis_scene_upload_packed borrows planes (16-byte aligned) as a scene that
+ * every render call accepts (vis_render, vis_render_depth, vis_render_multi, the batch);
+ * its preprocess reads about half the bytes. Values must lie in the fp16 range; a packed
+ * scene has no parameter gradients (the backward calls return VIS_ERR_UNSUPPORTED).
+ * Errors: VIS_ERR_INVALID_ARG for null/misaligned pointers, bad sizes, or packing a packed
+ * scene. */
+VIS_API vis_status vis_packed_size(int64_t n, int sh_degree, size_t* pos_bytes, size_t* cov_bytes,
+                                   size_t* col_bytes);
+VIS_API vis_status vis_scene_pack(vis_scene_t scene, void* pos, void* cov, void* col, void* stream);
+VIS_API vis_status vis_scene_upload_packed(const void* pos, const void* cov, const void* col,
+                                           int sh_degree, int64_t n, vis_scene_t* out);
+
 /* Bytes of workspace vis_render needs for n Gaussians at W x H holding up to
  * key_capacity (tile, Gaussian) keys (one per tile a splat's rectangle touches). */
 VIS_API vis_status vis_workspace_size(int64_t n, int W, int H, int64_t key_capacity,

@@ -89,6 +89,10 @@ def lib():
                                                     C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
                                                     C.POINTER(vis_render_opts), _P, _P, _P, _P, _P, _P]),
             "vis_multi_slots": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64)]),
+            "vis_packed_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                          C.POINTER(C.c_size_t)]),
+            "vis_scene_pack": (C.c_int, [_P, _P, _P, _P, _P]),
+            "vis_scene_upload_packed": (C.c_int, [_P, _P, _P, C.c_int, C.c_int64, C.POINTER(_P)]),
             "vis_render_multi": (C.c_int, [_P, _P, C.c_int, C.POINTER(vis_camera), C.c_int, C.c_int,
                                            C.POINTER(C.c_float), _P, _P, _P, _P, C.c_size_t,
                                            C.POINTER(vis_render_opts), _P]),
@@ -343,6 +347,57 @@ class Scene:
         torch = _torch()
         ts = {k: torch.from_numpy(scene[k]).to(device).contiguous() for k in FIELDS}
         return cls(**ts, sh_degree=scene["sh_degree"])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.vis_scene_destroy(h)
+            self.handle = None
+
+
+def vis_packed_size(n, sh_degree):
+    """Bytes of the (pos, cov, col) planes of a pre-packed scene."""
+    a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _ok(lib().vis_packed_size(int(n), int(sh_degree), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+class PackedScene:
+    """A pre-packed fp16 scene (vis_scene_upload_packed): device planes pos [n,2], cov [n,3],
+    col [n,W] of uint32 words (stored as int32 tensors), borrowed by the C handle."""
+
+    def __init__(self, pos, cov, col, sh_degree):
+        torch = _torch()
+        for name, t in (("pos", pos), ("cov", cov), ("col", col)):
+            if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
+        self.planes = dict(pos=pos, cov=cov, col=col)
+        self.sh_degree = int(sh_degree)
+        self.n = int(pos.shape[0])
+        h = _P()
+        _ok(lib().vis_scene_upload_packed(_ptr(pos), _ptr(cov), _ptr(col), self.sh_degree, self.n, C.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_planes(cls, planes, sh_degree, device="cuda"):
+        """From host uint32 planes (e.g. the oracle's prepack)."""
+        import numpy as np
+        torch = _torch()
+        ts = {k: torch.from_numpy(np.ascontiguousarray(planes[k], np.uint32).view(np.int32)).to(device)
+              for k in ("pos", "cov", "col")}
+        return cls(ts["pos"], ts["cov"], ts["col"], sh_degree)
+
+    @classmethod
+    def pack(cls, scene, stream=None):
+        """Pack an fp32 Scene on the device (vis_scene_pack)."""
+        torch = _torch()
+        a, b, c = vis_packed_size(scene.n, scene.sh_degree)
+        dev = scene.tensors["means"].device
+        pos = torch.empty(a // 4, dtype=torch.int32, device=dev).view(scene.n, 2)
+        cov = torch.empty(b // 4, dtype=torch.int32, device=dev).view(scene.n, 3)
+        col = torch.empty(c // 4, dtype=torch.int32, device=dev).view(scene.n, -1)
+        _ok(lib().vis_scene_pack(scene.handle, _ptr(pos), _ptr(cov), _ptr(col), _stream(stream)))
+        return cls(pos, cov, col, scene.sh_degree)
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -21,6 +21,10 @@ struct vis_scene {
     const float* sh;
     int deg;
     int64_t n;
+    // pre-packed fp16 planes (vis_scene_upload_packed); null for an fp32 scene
+    const uint32_t* pk_pos;
+    const uint32_t* pk_cov;
+    const uint32_t* pk_col;
 };
 
 namespace {
@@ -100,6 +104,8 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     vis::PrepParams p;
     std::memset(&p, 0, sizeof(p));
     p.means = s->means; p.log_scales = s->log_scales; p.quats = s->quats; p.logits = s->logits; p.sh = s->sh;
+    p.pk_pos = reinterpret_cast<const uint2*>(s->pk_pos); p.pk_cov = s->pk_cov; p.pk_col = s->pk_col;
+    p.col_words = vis::packed_col_words(s->deg);
     p.deg = s->deg; p.n = (int)s->n; p.n_pad = (int)s->n; p.index_offset = 0;
     for (int k = 0; k < 9; ++k) p.R[k] = c->R[k];
     for (int k = 0; k < 3; ++k) p.t[k] = c->t[k];
@@ -388,9 +394,59 @@ vis_status vis_scene_upload(const float* means, const float* log_scales, const f
     }
     vis_scene* s = new (std::nothrow) vis_scene;
     if (!s) return fail(VIS_ERR_INVALID_ARG, "out of host memory");
+    std::memset(s, 0, sizeof(*s));
     s->means = means; s->log_scales = log_scales; s->quats = quats; s->logits = opacity_logits; s->sh = sh;
     s->deg = sh_degree; s->n = n;
     *out = s;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_packed_size(int64_t n, int sh_degree, size_t* pos_bytes, size_t* cov_bytes, size_t* col_bytes) {
+    if (sh_degree < 0 || sh_degree > 3) return fail(VIS_ERR_INVALID_ARG, "sh_degree must be 0..3 (got %d)", sh_degree);
+    if (n < 1 || n > 0x7fffffffLL) return fail(VIS_ERR_INVALID_ARG, "n must be in [1, 2^31-1] (got %lld)", (long long)n);
+    if (pos_bytes) *pos_bytes = 8 * (size_t)n;
+    if (cov_bytes) *cov_bytes = 12 * (size_t)n;
+    if (col_bytes) *col_bytes = 4 * (size_t)vis::packed_col_words(sh_degree) * (size_t)n;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_scene_upload_packed(const void* pos, const void* cov, const void* col, int sh_degree, int64_t n,
+                                   vis_scene_t* out) {
+    if (!out) return fail(VIS_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    vis_status st = vis_packed_size(n, sh_degree, nullptr, nullptr, nullptr);
+    if (st) return st;
+    const void* ptrs[3] = {pos, cov, col};
+    const char* names[3] = {"pos", "cov", "col"};
+    for (int k = 0; k < 3; ++k) {
+        if (!ptrs[k]) return fail(VIS_ERR_INVALID_ARG, "%s is null", names[k]);
+        if (!aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "%s is not 16-byte aligned", names[k]);
+    }
+    vis_scene* s = new (std::nothrow) vis_scene;
+    if (!s) return fail(VIS_ERR_INVALID_ARG, "out of host memory");
+    std::memset(s, 0, sizeof(*s));
+    s->pk_pos = static_cast<const uint32_t*>(pos);
+    s->pk_cov = static_cast<const uint32_t*>(cov);
+    s->pk_col = static_cast<const uint32_t*>(col);
+    s->deg = sh_degree; s->n = n;
+    *out = s;
+    g_err.clear();
+    return VIS_OK;
+}
+
+vis_status vis_scene_pack(vis_scene_t scene, void* pos, void* cov, void* col, void* stream_) {
+    if (!scene) return fail(VIS_ERR_INVALID_ARG, "scene is null");
+    if (scene->pk_pos) return fail(VIS_ERR_INVALID_ARG, "scene is already packed");
+    const void* ptrs[3] = {pos, cov, col};
+    for (int k = 0; k < 3; ++k)
+        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "packed plane %d null or misaligned", k);
+    vis::launch_pack(scene->means, scene->log_scales, scene->quats, scene->logits, scene->sh, scene->deg, scene->n,
+                     static_cast<uint2*>(pos), static_cast<uint32_t*>(cov), static_cast<uint32_t*>(col),
+                     reinterpret_cast<cudaStream_t>(stream_));
+    vis_status st = cuda_check(cudaGetLastError(), "launch");
+    if (st) return st;
     g_err.clear();
     return VIS_OK;
 }
@@ -604,6 +660,9 @@ static vis_status backward_impl(const vis_scene_t* scenes, const float* models, 
     if (!d_rgb || !d_alpha || !aligned16(d_rgb) || !aligned16(d_alpha))
         return fail(VIS_ERR_INVALID_ARG, "d_rgb / d_alpha null or not 16-byte aligned");
     if (!grads) return fail(VIS_ERR_INVALID_ARG, "grads is null");
+    for (int k = 0; k < n_scenes; ++k)
+        if (scenes[k]->pk_pos)
+            return fail(VIS_ERR_UNSUPPORTED, "scene %d is pre-packed (fp16): it has no parameter gradients", k);
     for (int k = 0; k < n_scenes; ++k) {
         const vis_scene_grads& g = grads[k];
         const void* ptrs[5] = {g.d_means, g.d_log_scales, g.d_quats, g.d_opacity_logits, g.d_sh};

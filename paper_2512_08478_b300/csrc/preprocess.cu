@@ -14,14 +14,48 @@
 // (lambda_k, e_k) the eigenpairs of S and c = log2(e)/2. This is c d^T S^-1 d (Eq. 2's
 // exponent in base 2) and stays well conditioned for needle-shaped splats, where the
 // conic form (a, b, c) loses digits.
+//
+// Pre-packed scenes (PACKED: Algorithm 1's pre-pack, section 3.4's FP16 layout) give the
+// mean, the opacity, the covariance's upper triangle and the SH coefficients as fp16 pairs.
+// Their covariance arrives unfactored, so S = T Sigma T^T is formed in float-float: an
+// unstructured rounding of Sigma's entries in float would cost eps cond(S) of the small
+// eigenvalue, while the float-float products keep det(S) exact to float rounding.
+#include <cuda_fp16.h>
+
 #include "vis_internal.cuh"
 #include "footprint.cuh"
 
 namespace vis {
 
+__device__ __forceinline__ float half_lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+__device__ __forceinline__ float half_hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+
+// S = T Sigma T^T + dil I for T = [T0; T1] (2x3) and Sigma = (xx, xy, xz, yy, yz, zz), with
+// the products and sums in float-float; returns S's entries and det(S) rounded to float.
+__device__ __forceinline__ void screen_cov_ff(const float T0[3], const float T1[3], const float sg[6], float dil,
+                                              float& s00, float& s01, float& s11, float& det) {
+    const float Sg[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+    float2 e00 = make_float2(0.f, 0.f), e01 = e00, e11 = e00;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        // (T0 Sigma)_c and (T1 Sigma)_c
+        float2 b0 = ff_add(ff_add(two_prod(T0[0], Sg[c]), two_prod(T0[1], Sg[3 + c])), two_prod(T0[2], Sg[6 + c]));
+        float2 b1 = ff_add(ff_add(two_prod(T1[0], Sg[c]), two_prod(T1[1], Sg[3 + c])), two_prod(T1[2], Sg[6 + c]));
+        e00 = ff_add(e00, ff_mul_f(b0, T0[c]));
+        e01 = ff_add(e01, ff_mul_f(b0, T1[c]));
+        e11 = ff_add(e11, ff_mul_f(b1, T1[c]));
+    }
+    const float2 dd = make_float2(dil, 0.f);
+    const float2 a00 = ff_add(e00, dd), a11 = ff_add(e11, dd);
+    const float2 m01 = ff_mul(e01, e01);
+    const float2 dt = ff_add(ff_mul(a00, a11), make_float2(-m01.x, -m01.y));
+    s00 = a00.x; s11 = a11.x; s01 = e01.x;
+    det = dt.x;
+}
+
 // FOLDED: the view carries a folded model transform, whose rounding residues R_lo, t_lo join
 // the float-float camera transform (a plain camera has none and skips them)
-template <bool FOLDED>
+template <bool FOLDED, bool PACKED>
 __global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
                   uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
@@ -34,9 +68,16 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
     uint32_t touched = 0;
     if (i < p.n) {
         // --- camera-space position in float-float: p = R mu + t ---
-        const float mx = __ldg(p.means + 3 * i + 0);
-        const float my = __ldg(p.means + 3 * i + 1);
-        const float mz = __ldg(p.means + 3 * i + 2);
+        float mx, my, mz, opac;
+        if (PACKED) {
+            const uint2 w = __ldg(p.pk_pos + i);
+            mx = half_lo(w.x); my = half_hi(w.x); mz = half_lo(w.y); opac = half_hi(w.y);
+        } else {
+            mx = __ldg(p.means + 3 * i + 0);
+            my = __ldg(p.means + 3 * i + 1);
+            mz = __ldg(p.means + 3 * i + 2);
+            opac = 1.f / (1.f + __expf(-__ldg(p.logits + i)));
+        }
         float2 pc[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -53,8 +94,6 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             pc[r] = acc;
         }
         const float z = pc[2].x;
-        const float logit = __ldg(p.logits + i);
-        const float opac = 1.f / (1.f + __expf(-logit));
         depth_out[gi] = z;
         bool ok = (z > p.near_z) && (opac >= p.alpha_min);
         uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, trims = 0;
@@ -73,19 +112,6 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 float2 s2 = two_sum(b.x, p.cy);
                 v = fast_two_sum(s2.x, __fadd_rn(s2.y, b.y));
             }
-            // --- covariance factor M = R_q diag(s) ---
-            const float4 q4 = __ldg(reinterpret_cast<const float4*>(p.quats) + i);
-            float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
-            const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
-            if (qn2 < 1e-24f) { qw = 1.f; qx = qy = qz = 0.f; }
-            else { const float inv = rsqrtf(qn2); qw *= inv; qx *= inv; qy *= inv; qz *= inv; }
-            const float Rq[9] = {
-                1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
-                2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
-                2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-            const float s0 = __expf(__ldg(p.log_scales + 3 * i + 0));
-            const float s1 = __expf(__ldg(p.log_scales + 3 * i + 1));
-            const float s2 = __expf(__ldg(p.log_scales + 3 * i + 2));
             // --- EWA Jacobian at the camera-space mean, with the x/z, y/z guard ---
             const float zi = 1.f / z;
             const float tx = fminf(p.limx, fmaxf(-p.limx, rx.x));
@@ -99,24 +125,45 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 T0[c] = J00 * p.R[c] + J02 * p.R[6 + c];
                 T1[c] = J11 * p.R[3 + c] + J12 * p.R[6 + c];
             }
-            // A = T M: rows A0, A1 (3 each); M[:, k] = Rq[:, k] s_k
-            float A0[3], A1[3];
-            const float sk[3] = {s0, s1, s2};
+            float s00, s11, s01, det;
+            if (PACKED) {
+                const uint32_t w0 = __ldg(p.pk_cov + 3 * (size_t)i), w1 = __ldg(p.pk_cov + 3 * (size_t)i + 1);
+                const uint32_t w2 = __ldg(p.pk_cov + 3 * (size_t)i + 2);
+                const float sg[6] = {half_lo(w0), half_hi(w0), half_lo(w1), half_hi(w1), half_lo(w2), half_hi(w2)};
+                screen_cov_ff(T0, T1, sg, p.dilation, s00, s01, s11, det);
+            } else {
+                // --- covariance factor M = R_q diag(s) ---
+                const float4 q4 = __ldg(reinterpret_cast<const float4*>(p.quats) + i);
+                float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+                const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+                if (qn2 < 1e-24f) { qw = 1.f; qx = qy = qz = 0.f; }
+                else { const float inv = rsqrtf(qn2); qw *= inv; qx *= inv; qy *= inv; qz *= inv; }
+                const float Rq[9] = {
+                    1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                    2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                    2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+                const float s0 = __expf(__ldg(p.log_scales + 3 * i + 0));
+                const float s1 = __expf(__ldg(p.log_scales + 3 * i + 1));
+                const float s2 = __expf(__ldg(p.log_scales + 3 * i + 2));
+                // A = T M: rows A0, A1 (3 each); M[:, k] = Rq[:, k] s_k
+                float A0[3], A1[3];
+                const float sk[3] = {s0, s1, s2};
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float m0 = Rq[0 + k] * sk[k], m1 = Rq[3 + k] * sk[k], m2 = Rq[6 + k] * sk[k];
-                A0[k] = T0[0] * m0 + T0[1] * m1 + T0[2] * m2;
-                A1[k] = T1[0] * m0 + T1[1] * m1 + T1[2] * m2;
+                for (int k = 0; k < 3; ++k) {
+                    const float m0 = Rq[0 + k] * sk[k], m1 = Rq[3 + k] * sk[k], m2 = Rq[6 + k] * sk[k];
+                    A0[k] = T0[0] * m0 + T0[1] * m1 + T0[2] * m2;
+                    A1[k] = T1[0] * m0 + T1[1] * m1 + T1[2] * m2;
+                }
+                const float a00 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
+                const float a11 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+                const float a01 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
+                const float c0 = diff_of_products(A0[1], A1[2], A0[2], A1[1]);
+                const float c1 = diff_of_products(A0[2], A1[0], A0[0], A1[2]);
+                const float c2 = diff_of_products(A0[0], A1[1], A0[1], A1[0]);
+                const float dil = p.dilation;
+                s00 = a00 + dil; s11 = a11 + dil; s01 = a01;
+                det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (a00 + a11) + dil * dil;
             }
-            const float a00 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
-            const float a11 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
-            const float a01 = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-            const float c0 = diff_of_products(A0[1], A1[2], A0[2], A1[1]);
-            const float c1 = diff_of_products(A0[2], A1[0], A0[0], A1[2]);
-            const float c2 = diff_of_products(A0[0], A1[1], A0[1], A1[0]);
-            const float dil = p.dilation;
-            const float s00 = a00 + dil, s11 = a11 + dil, s01 = a01;
-            const float det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (a00 + a11) + dil * dil;
             if (det > 0.f) {
                 const float m = 0.5f * (s00 + s11);
                 const float h = 0.5f * (s00 - s11);
@@ -191,7 +238,35 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                     }
                     float col[3] = {0.5f, 0.5f, 0.5f};
                     const float* shi = p.sh + (size_t)i * K * 3;
-                    if (p.deg == 3) {
+                    if (PACKED) {
+                        const uint32_t* ci = p.pk_col + (size_t)i * p.col_words;
+                        if (p.deg == 3) {   // 24 words = six 16-byte loads
+                            const uint4* c4 = reinterpret_cast<const uint4*>(ci);
+                            float buf[48];
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) {
+                                const uint4 w = __ldg(c4 + k);
+                                buf[8 * k + 0] = half_lo(w.x); buf[8 * k + 1] = half_hi(w.x);
+                                buf[8 * k + 2] = half_lo(w.y); buf[8 * k + 3] = half_hi(w.y);
+                                buf[8 * k + 4] = half_lo(w.z); buf[8 * k + 5] = half_hi(w.z);
+                                buf[8 * k + 6] = half_lo(w.w); buf[8 * k + 7] = half_hi(w.w);
+                            }
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                col[0] += buf[3 * k] * Y[k]; col[1] += buf[3 * k + 1] * Y[k];
+                                col[2] += buf[3 * k + 2] * Y[k];
+                            }
+                        } else {
+                            for (int k = 0; k < K; ++k) {
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const int h = 3 * k + c;
+                                    const uint32_t w = __ldg(ci + (h >> 1));
+                                    col[c] += ((h & 1) ? half_hi(w) : half_lo(w)) * Y[k];
+                                }
+                            }
+                        }
+                    } else if (p.deg == 3) {
                         const float4* s4 = reinterpret_cast<const float4*>(shi);
                         float buf[48];
 #pragma unroll
@@ -287,11 +362,63 @@ void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStrea
     bool folded = false;
     for (int k = 0; k < 9; ++k) folded |= p.R_lo[k] != 0.f;
     for (int k = 0; k < 3; ++k) folded |= p.t_lo[k] != 0.f;
-    auto kernel = folded ? preprocess_kernel<true> : preprocess_kernel<false>;
+    const bool packed = p.pk_pos != nullptr;
+    auto kernel = packed ? (folded ? preprocess_kernel<true, true> : preprocess_kernel<false, true>)
+                         : (folded ? preprocess_kernel<true, false> : preprocess_kernel<false, false>);
     kernel<<<blocks, kPrepThreads, 0, stream>>>(
         p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
         reinterpret_cast<uint4*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
         reinterpret_cast<uint32_t*>(ws + L.off_bsum));
+}
+
+// Pre-pack (Algorithm 1, once per scene): Sigma = M M^T with M = R_q diag(exp(log_s)),
+// alpha = sigmoid(logit); mean, alpha, Sigma's upper triangle and the SH coefficients rounded
+// to fp16 (nearest even) and packed two per uint32, low half first.
+__global__ void __launch_bounds__(256)
+pack_kernel(const float* __restrict__ means, const float* __restrict__ log_scales, const float* __restrict__ quats,
+            const float* __restrict__ logits, const float* __restrict__ sh, int deg, int64_t n,
+            uint2* __restrict__ pos, uint32_t* __restrict__ cov, uint32_t* __restrict__ col) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    auto pk = [](float lo, float hi) {
+        return (uint32_t)__half_as_ushort(__float2half_rn(lo)) | ((uint32_t)__half_as_ushort(__float2half_rn(hi)) << 16);
+    };
+    const float alpha = 1.f / (1.f + expf(-logits[i]));
+    pos[i] = make_uint2(pk(means[3 * i], means[3 * i + 1]), pk(means[3 * i + 2], alpha));
+    float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    if (qn2 < 1e-24f) { qw = 1.f; qx = qy = qz = 0.f; }
+    else { const float inv = 1.f / sqrtf(qn2); qw *= inv; qx *= inv; qy *= inv; qz *= inv; }
+    const float Rq[9] = {
+        1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+        2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+        2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    float s2[3];
+    for (int k = 0; k < 3; ++k) { const float sk = expf(log_scales[3 * i + k]); s2[k] = sk * sk; }
+    float S[6];   // xx, xy, xz, yy, yz, zz
+    const int ra[6] = {0, 0, 0, 1, 1, 2}, rb[6] = {0, 1, 2, 1, 2, 2};
+    for (int e = 0; e < 6; ++e) {
+        float acc = 0.f;
+        for (int k = 0; k < 3; ++k) acc = __fmaf_rn(Rq[3 * ra[e] + k] * s2[k], Rq[3 * rb[e] + k], acc);
+        S[e] = acc;
+    }
+    cov[3 * i] = pk(S[0], S[1]);
+    cov[3 * i + 1] = pk(S[2], S[3]);
+    cov[3 * i + 2] = pk(S[4], S[5]);
+    const int K3 = 3 * (deg + 1) * (deg + 1), W = packed_col_words(deg);
+    const float* shi = sh + i * K3;
+    uint32_t* ci = col + i * W;
+    for (int w = 0; w < W; ++w) {
+        const int h = 2 * w;
+        ci[w] = pk(h < K3 ? shi[h] : 0.f, h + 1 < K3 ? shi[h + 1] : 0.f);
+    }
+}
+
+void launch_pack(const float* means, const float* log_scales, const float* quats, const float* logits,
+                 const float* sh, int deg, int64_t n, uint2* pos, uint32_t* cov, uint32_t* col, cudaStream_t stream) {
+    if (n <= 0) return;
+    pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(means, log_scales, quats, logits, sh, deg, n, pos,
+                                                                 cov, col);
 }
 
 }  // namespace vis

@@ -123,6 +123,13 @@ struct PrepParams {
     float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
     int tight_extent;        // 1: tile rect from the tight opacity-aware 3-sigma box
     int count_survivors;     // block sums count survivors (depth-first sorts), else tiles touched
+    // pre-packed scene (Algorithm 1 pre-pack, fp16 pairs in uint32 words; null for fp32 SoA):
+    // pos (mu_x, mu_y), (mu_z, alpha); cov (xx, xy), (xz, yy), (yz, zz); col: SH halves,
+    // col_words words per Gaussian
+    const uint2* pk_pos;
+    const uint32_t* pk_cov;
+    const uint32_t* pk_col;
+    int col_words;
     int64_t index_offset;    // workspace slot of the scene's first Gaussian (a multiple of kPrepThreads)
     int n_pad;               // n rounded up to kPrepThreads in a multi-scene render (else n)
     float shc[12];           // SH polynomial constants, see sh_constants()
@@ -156,6 +163,17 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
     return fast_two_sum(s.x, e);
 }
+// float-float times float, and float-float times float-float
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+    float2 p = two_prod(a.x, b);
+    p.y = __fmaf_rn(a.y, b, p.y);
+    return fast_two_sum(p.x, p.y);
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    float2 p = two_prod(a.x, b.x);
+    p.y = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, p.y));
+    return fast_two_sum(p.x, p.y);
+}
 // a.hi/a.lo divided by b.hi/b.lo
 __device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
     float q = __fdiv_rn(a.x, b.x);
@@ -173,8 +191,18 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
     return __fadd_rn(f, e);
 }
 
+// uint32 words per Gaussian of a packed colour plane: 3 (deg+1)^2 halves, rounded up to an
+// even number of words (8-byte rows)
+__host__ __device__ __forceinline__ int packed_col_words(int deg) {
+    const int words = (3 * (deg + 1) * (deg + 1) + 1) / 2;
+    return words + (words & 1);
+}
+
 // Launchers (host side, enqueue on `stream`).
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream);
+// Pre-pack (Algorithm 1, once per scene): fp32 SoA attributes -> fp16 planes pos, cov, col.
+void launch_pack(const float* means, const float* log_scales, const float* quats, const float* logits,
+                 const float* sh, int deg, int64_t n, uint2* pos, uint32_t* cov, uint32_t* col, cudaStream_t stream);
 void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_t stream);
 // Sorts keys[0] -> keys[L.sorted_buffer] over L.passes digit passes. If `mark` is
 // given it is called with (mark_index, stream) after the histogram, i.e. between

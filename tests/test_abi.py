@@ -127,3 +127,22 @@ def test_multi_scene_slots_and_validation(L):
         vis.vis_multi_slots([hs[0], C.c_void_p()])
     for h in hs:
         L.vis_scene_destroy(h)
+
+
+def test_packed_scene_sizes_and_validation(L):
+    import ctypes as C
+    for deg, words in ((0, 2), (1, 6), (2, 14), (3, 24)):
+        assert vis.vis_packed_size(1000, deg) == (8000, 12000, 4000 * words)
+    with pytest.raises(vis.VisError):
+        vis.vis_packed_size(0, 0)
+    with pytest.raises(vis.VisError):
+        vis.vis_packed_size(10, 4)
+    h = C.c_void_p()
+    p = C.c_void_p(1 << 20)
+    assert L.vis_scene_upload_packed(p, None, p, 0, 10, C.byref(h)) == vis.VIS_ERR_INVALID_ARG
+    assert "cov is null" in vis.vis_last_error()
+    assert L.vis_scene_upload_packed(p, p, C.c_void_p((1 << 20) + 8), 0, 10, C.byref(h)) == vis.VIS_ERR_INVALID_ARG
+    assert L.vis_scene_upload_packed(p, p, p, 2, 10, C.byref(h)) == vis.VIS_OK
+    assert L.vis_scene_pack(h, p, p, p, None) == vis.VIS_ERR_INVALID_ARG     # already packed
+    assert "already packed" in vis.vis_last_error()
+    L.vis_scene_destroy(h)
