@@ -69,7 +69,13 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
     if (i < p.n) {
         // --- camera-space position in float-float: p = R mu + t ---
         float mx, my, mz, opac;
+        uint32_t cw0 = 0, cw1 = 0, cw2 = 0;   // packed covariance words
         if (PACKED) {
+            // the covariance words go out with the position (one round trip fewer for the
+            // Gaussians in front; 12 B more for the culled ones)
+            cw0 = __ldg(p.pk_cov + 3 * (size_t)i);
+            cw1 = __ldg(p.pk_cov + 3 * (size_t)i + 1);
+            cw2 = __ldg(p.pk_cov + 3 * (size_t)i + 2);
             const uint2 w = __ldg(p.pk_pos + i);
             mx = half_lo(w.x); my = half_hi(w.x); mz = half_lo(w.y); opac = half_hi(w.y);
         } else {
@@ -77,6 +83,9 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             my = __ldg(p.means + 3 * i + 1);
             mz = __ldg(p.means + 3 * i + 2);
             opac = 1.f / (1.f + __expf(-__ldg(p.logits + i)));
+            // quaternion and log-scales are read after the cull test: start them towards L2
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.quats + 4 * (size_t)i));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p.log_scales + 3 * (size_t)i));
         }
         float2 pc[3];
 #pragma unroll
@@ -96,6 +105,13 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         const float z = pc[2].x;
         depth_out[gi] = z;
         bool ok = (z > p.near_z) && (opac >= p.alpha_min);
+        if (ok) {   // the colour row is read at the end: start it towards L2 now
+            const char* row = PACKED ? reinterpret_cast<const char*>(p.pk_col + (size_t)i * p.col_words)
+                                     : reinterpret_cast<const char*>(p.sh + (size_t)i * 3 * (p.deg + 1) * (p.deg + 1));
+            const int bytes = PACKED ? 4 * p.col_words : 12 * (p.deg + 1) * (p.deg + 1);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + bytes - 4));
+        }
         uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, trims = 0;
         if (ok) {
             // --- pixel centre u = fx x/z + cx (float-float) ---
@@ -127,9 +143,7 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             }
             float s00, s11, s01, det;
             if (PACKED) {
-                const uint32_t w0 = __ldg(p.pk_cov + 3 * (size_t)i), w1 = __ldg(p.pk_cov + 3 * (size_t)i + 1);
-                const uint32_t w2 = __ldg(p.pk_cov + 3 * (size_t)i + 2);
-                const float sg[6] = {half_lo(w0), half_hi(w0), half_lo(w1), half_hi(w1), half_lo(w2), half_hi(w2)};
+                const float sg[6] = {half_lo(cw0), half_hi(cw0), half_lo(cw1), half_hi(cw1), half_lo(cw2), half_hi(cw2)};
                 screen_cov_ff(T0, T1, sg, p.dilation, s00, s01, s11, det);
             } else {
                 // --- covariance factor M = R_q diag(s) ---
