@@ -17,9 +17,8 @@
 //
 // Pre-packed scenes (PACKED: Algorithm 1's pre-pack, section 3.4's FP16 layout) give the
 // mean, the opacity, the covariance's upper triangle and the SH coefficients as fp16 pairs.
-// Their covariance arrives unfactored, so S = T Sigma T^T is formed in float-float: an
-// unstructured rounding of Sigma's entries in float would cost eps cond(S) of the small
-// eigenvalue, while the float-float products keep det(S) exact to float rounding.
+// Their covariance arrives unfactored, so det S is formed from Sigma's cofactors
+// (screen_cov_packed) rather than from S's rounded entries, which would cost eps cond(S).
 #include <cuda_fp16.h>
 
 #include "vis_internal.cuh"
@@ -30,31 +29,35 @@ namespace vis {
 __device__ __forceinline__ float half_lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
 __device__ __forceinline__ float half_hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
 
-// S = T Sigma T^T + dil I for T = [T0; T1] (2x3) and Sigma = (xx, xy, xz, yy, yz, zz), with
-// the products and sums in float-float; returns S's entries and det(S) rounded to float.
-__device__ __forceinline__ void screen_cov_ff(const float T0[3], const float T1[3], const float sg[6], float dil,
-                                              float& s00, float& s01, float& s11, float& det) {
-    const float Sg[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
-    float2 e00 = make_float2(0.f, 0.f), e01 = e00, e11 = e00;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        // (T0 Sigma)_c and (T1 Sigma)_c
-        float2 b0 = ff_add(ff_add(two_prod(T0[0], Sg[c]), two_prod(T0[1], Sg[3 + c])), two_prod(T0[2], Sg[6 + c]));
-        float2 b1 = ff_add(ff_add(two_prod(T1[0], Sg[c]), two_prod(T1[1], Sg[3 + c])), two_prod(T1[2], Sg[6 + c]));
-        e00 = ff_add(e00, ff_mul_f(b0, T0[c]));
-        e01 = ff_add(e01, ff_mul_f(b0, T1[c]));
-        e11 = ff_add(e11, ff_mul_f(b1, T1[c]));
-    }
-    const float2 dd = make_float2(dil, 0.f);
-    const float2 a00 = ff_add(e00, dd), a11 = ff_add(e11, dd);
-    const float2 m01 = ff_mul(e01, e01);
-    const float2 dt = ff_add(ff_mul(a00, a11), make_float2(-m01.x, -m01.y));
-    s00 = a00.x; s11 = a11.x; s01 = e01.x;
-    det = dt.x;
+// S = T Sigma T^T + dil I for T = [T0; T1] (2x3) and Sigma = (xx, xy, xz, yy, yz, zz). The
+// entries are plain float sums; det(T Sigma T^T) is taken as (T0 x T1)^T adj(Sigma) (T0 x T1)
+// (the Cauchy-Binet form for a 2x3 T), with the cross product and Sigma's cofactors from
+// Kahan's accurate a b - c d, so Sigma's large entries never cancel against each other:
+// det S keeps ~1e-5 relative accuracy where s00 s11 - s01^2 in float loses eps cond(S).
+__device__ __forceinline__ void screen_cov_packed(const float T0[3], const float T1[3], const float sg[6], float dil,
+                                                  float& s00, float& s01, float& s11, float& det) {
+    const float xx = sg[0], xy = sg[1], xz = sg[2], yy = sg[3], yz = sg[4], zz = sg[5];
+    const float b00 = T0[0] * xx + T0[1] * xy + T0[2] * xz;   // (T0 Sigma)
+    const float b01 = T0[0] * xy + T0[1] * yy + T0[2] * yz;
+    const float b02 = T0[0] * xz + T0[1] * yz + T0[2] * zz;
+    const float b10 = T1[0] * xx + T1[1] * xy + T1[2] * xz;   // (T1 Sigma)
+    const float b11 = T1[0] * xy + T1[1] * yy + T1[2] * yz;
+    const float b12 = T1[0] * xz + T1[1] * yz + T1[2] * zz;
+    const float a00 = b00 * T0[0] + b01 * T0[1] + b02 * T0[2];
+    const float a01 = b00 * T1[0] + b01 * T1[1] + b02 * T1[2];
+    const float a11 = b10 * T1[0] + b11 * T1[1] + b12 * T1[2];
+    const float c0 = diff_of_products(T0[1], T1[2], T0[2], T1[1]);
+    const float c1 = diff_of_products(T0[2], T1[0], T0[0], T1[2]);
+    const float c2 = diff_of_products(T0[0], T1[1], T0[1], T1[0]);
+    const float A00 = diff_of_products(yy, zz, yz, yz), A11 = diff_of_products(xx, zz, xz, xz);
+    const float A22 = diff_of_products(xx, yy, xy, xy), A01 = diff_of_products(xz, yz, xy, zz);
+    const float A02 = diff_of_products(xy, yz, xz, yy), A12 = diff_of_products(xy, xz, xx, yz);
+    const float q = c0 * c0 * A00 + c1 * c1 * A11 + c2 * c2 * A22 +
+                    2.f * (c0 * c1 * A01 + c0 * c2 * A02 + c1 * c2 * A12);
+    s00 = a00 + dil; s11 = a11 + dil; s01 = a01;
+    det = q + dil * (a00 + a11) + dil * dil;
 }
 
-// FOLDED: the view carries a folded model transform, whose rounding residues R_lo, t_lo join
-// the float-float camera transform (a plain camera has none and skips them)
 template <bool FOLDED, bool PACKED>
 __global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
@@ -144,7 +147,7 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             float s00, s11, s01, det;
             if (PACKED) {
                 const float sg[6] = {half_lo(cw0), half_hi(cw0), half_lo(cw1), half_hi(cw1), half_lo(cw2), half_hi(cw2)};
-                screen_cov_ff(T0, T1, sg, p.dilation, s00, s01, s11, det);
+                screen_cov_packed(T0, T1, sg, p.dilation, s00, s01, s11, det);
             } else {
                 // --- covariance factor M = R_q diag(s) ---
                 const float4 q4 = __ldg(reinterpret_cast<const float4*>(p.quats) + i);

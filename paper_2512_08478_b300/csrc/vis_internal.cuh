@@ -163,17 +163,6 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
     return fast_two_sum(s.x, e);
 }
-// float-float times float, and float-float times float-float
-__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
-    float2 p = two_prod(a.x, b);
-    p.y = __fmaf_rn(a.y, b, p.y);
-    return fast_two_sum(p.x, p.y);
-}
-__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
-    float2 p = two_prod(a.x, b.x);
-    p.y = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, p.y));
-    return fast_two_sum(p.x, p.y);
-}
 // a.hi/a.lo divided by b.hi/b.lo
 __device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
     float q = __fdiv_rn(a.x, b.x);
