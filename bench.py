@@ -174,13 +174,14 @@ def run_ours(args):
         dist.init_process_group("nccl")
 
     sc_np, cams, desc, extra = load_workload(args.workload)
+    desc["tile"] = args.tile
     W, H = desc["width"], desc["height"]
     sc = vis.Scene.from_numpy(sc_np)
     n = sc.n
     cap = 16 * n + (1 << 20)
     if args.sort_mode is None:
         args.sort_mode = vis.make_opts().sort_mode
-    opts = vis.make_opts(sort_mode=args.sort_mode)
+    opts = vis.make_opts(sort_mode=args.sort_mode, tile=args.tile, pixels_per_thread=args.ppt)
     ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
@@ -342,7 +343,7 @@ def run_ours(args):
     if dom == "composite":
         # the compositor is bound by FP32 issue, not HBM: count its (pixel, splat) tests and hits
         # on the first view (one extra render with statistics, outside the timed region)
-        st_opts = vis.make_opts(sort_mode=args.sort_mode, collect_stats=1)
+        st_opts = vis.make_opts(sort_mode=args.sort_mode, tile=args.tile, pixels_per_thread=args.ppt, collect_stats=1)
         vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
                        st_opts)
         vis.vis_check(ws.buf)
@@ -383,7 +384,7 @@ def run_ours(args):
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(desc, sort_mode=args.sort_mode, packed=packed,
+                config=dict(desc, sort_mode=args.sort_mode, packed=packed, pixels_per_thread=args.ppt,
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk_summary, e2e=e2e,
@@ -738,6 +739,8 @@ def main():
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
                          "2: depth sort then counting binning (default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile size in pixels")
+    ap.add_argument("--ppt", type=int, default=1, choices=[1, 2], help="pixels per compositor thread")
     ap.add_argument("--packed", action="store_true",
                     help="render a pre-packed fp16 copy of the scene (packed once, outside the timing)")
     args = ap.parse_args()
