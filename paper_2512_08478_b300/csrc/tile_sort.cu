@@ -49,24 +49,33 @@ __device__ __forceinline__ int warp_scan_incl(int v, int lane) {
 
 // One CTA of 1024 threads. hist: [2][256] digit histograms (low byte, high byte of the
 // tile id); ranges: [start, end) per tile, (0, 0) for an empty tile. The 2D prefix sums run
-// one warp per row, then one warp per column, 32 entries at a time with warp scans; the
-// histograms are plain sums (low byte: tiles d, d + 256, ...; high byte: a block of 256).
+// one warp per row, then one warp per column, 32 entries at a time with warp scans, on rows
+// padded to tiles_x + 1 words (an odd stride: the column pass reads 32 rows without bank
+// conflicts). The histograms are plain sums (low byte: tiles d, d + 256, ...; high byte: a
+// block of 256); the ranges come from an exclusive scan in raster order taken 1024 tiles per
+// round (warp scans, then a scan of the 32 warp totals), written coalesced.
 __global__ void __launch_bounds__(1024)
 tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32_t* __restrict__ hist,
                  uint2* __restrict__ ranges) {
     extern __shared__ int P[];
     __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
     const int nt = tiles_x * tiles_y;
+    const int ld = tiles_x + 1;   // padded row stride
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nt; i += 1024) P[i] = gdiff[i];
+    for (int i = tid; i < nt; i += 1024) {
+        const int y = i / tiles_x;
+        P[y * ld + (i - y * tiles_x)] = gdiff[i];
+    }
+    if (tid == 0) s_carry = 0;
     __syncthreads();
     for (int y = warp; y < tiles_y; y += 32) {   // prefix along each row
         int carry = 0;
         for (int x0 = 0; x0 < tiles_x; x0 += 32) {
             const int x = x0 + lane;
-            const int v = x < tiles_x ? P[y * tiles_x + x] : 0;
+            const int v = x < tiles_x ? P[y * ld + x] : 0;
             const int incl = warp_scan_incl(v, lane) + carry;
-            if (x < tiles_x) P[y * tiles_x + x] = incl;
+            if (x < tiles_x) P[y * ld + x] = incl;
             carry = __shfl_sync(0xffffffffu, incl, 31);
         }
     }
@@ -75,46 +84,55 @@ tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32
         int carry = 0;
         for (int y0 = 0; y0 < tiles_y; y0 += 32) {
             const int y = y0 + lane;
-            const int v = y < tiles_y ? P[y * tiles_x + x] : 0;
+            const int v = y < tiles_y ? P[y * ld + x] : 0;
             const int incl = warp_scan_incl(v, lane) + carry;
-            if (y < tiles_y) P[y * tiles_x + x] = incl;
+            if (y < tiles_y) P[y * ld + x] = incl;
             carry = __shfl_sync(0xffffffffu, incl, 31);
         }
     }
     __syncthreads();
+    auto count = [&](int t) { const int y = t / tiles_x; return (uint32_t)P[y * ld + (t - y * tiles_x)]; };
     // digit histograms of the two passes
     if (tid < kRadix) {
         uint32_t h = 0;
-        for (int t = tid; t < nt; t += kRadix) h += (uint32_t)P[t];
+        for (int t = tid; t < nt; t += kRadix) h += count(t);
         hist[tid] = h;
     }
     for (int d = warp; d < kRadix; d += 32) {
         uint32_t h = 0;
-        for (int t = d * kRadix + lane; t < min(nt, (d + 1) * kRadix); t += 32) h += (uint32_t)P[t];
+        for (int t = d * kRadix + lane; t < min(nt, (d + 1) * kRadix); t += 32) h += count(t);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
         if (lane == 0) hist[kRadix + d] = h;
     }
-    // exclusive scan of the counts in raster order: thread tid owns tiles [tid*per, (tid+1)*per)
-    const int per = (nt + 1023) / 1024;
-    const int t0 = tid * per, t1 = min(nt, t0 + per);
-    uint32_t local = 0;
-    for (int t = t0; t < t1; ++t) local += (uint32_t)P[t];
-    uint32_t incl = local;
+    // exclusive scan of the counts in raster order, 1024 tiles per round
+    for (int t0 = 0; t0 < nt; t0 += 1024) {
+        const int t = t0 + tid;
+        const uint32_t c = t < nt ? count(t) : 0u;
+        uint32_t incl = c;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    uint32_t woff = 0;
-    for (int w = 0; w < warp; ++w) woff += s_warp[w];
-    uint32_t start = woff + incl - local;
-    for (int t = t0; t < t1; ++t) {
-        const uint32_t c = (uint32_t)P[t];
-        ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
-        start += c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = s_warp[lane];
+            uint32_t wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            s_warp[lane] = wi - w;   // exclusive warp offsets
+        }
+        __syncthreads();
+        const uint32_t start = s_carry + s_warp[warp] + incl - c;
+        if (t < nt) ranges[t] = c ? make_uint2(start, start + c) : make_uint2(0u, 0u);
+        __syncthreads();
+        if (tid == 1023) s_carry = start + c;
+        __syncthreads();
     }
 }
 
@@ -128,11 +146,13 @@ static int sm_count_ts() {
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     static bool attr_done = false;
     if (!attr_done) {
-        // the largest per-tile counter array of the fused path (tile_scan_kernel adds 2.2 KB of
-        // static shared memory, still within the 227 KB a CTA may use)
+        // the largest per-tile counter array of the fused path; the scan's rows are padded by one
+        // word (at most 1024 rows at 16-pixel tiles) and it adds ~0.2 KB of static shared
+        // memory, within the 227 KB a CTA may use
         const int most = (int)(sizeof(int) * kTileFusedMaxTiles);
         cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             most + (int)sizeof(int) * 2048);
         attr_done = true;
     }
     const size_t smem = sizeof(int) * (size_t)L.ntiles;
@@ -142,7 +162,8 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     const int grid = (int)(want < 1 ? 1 : (want < lim ? want : lim));
     tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, L.tiles_x,
                                                     L.tiles_y, gdiff);
-    tile_scan_kernel<<<1, 1024, smem, stream>>>(gdiff, L.tiles_x, L.tiles_y,
+    const size_t scan_smem = sizeof(int) * (size_t)(L.tiles_x + 1) * L.tiles_y;
+    tile_scan_kernel<<<1, 1024, scan_smem, stream>>>(gdiff, L.tiles_x, L.tiles_y,
                                                 reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,
                                                 reinterpret_cast<uint2*>(ws + L.off_ranges));
 }

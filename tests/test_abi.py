@@ -125,7 +125,16 @@ def test_multi_scene_slots_and_validation(L):
     assert call(good, scenes=holey) == vis.VIS_ERR_INVALID_ARG and "scene 1 is null" in vis.vis_last_error()
     with pytest.raises(vis.VisError):
         vis.vis_multi_slots([hs[0], C.c_void_p()])
-    for h in hs:
+    big = []
+    for _ in range(3):   # 3 x 2^30 slots exceed the 2^31 - 1 a workspace indexes
+        h = C.c_void_p()
+        assert L.vis_scene_upload(p, p, p, p, p, 0, 1 << 30, C.byref(h)) == vis.VIS_OK
+        big.append(h)
+    assert vis.vis_multi_slots(big[:1]) == 1 << 30
+    with pytest.raises(vis.VisError) as e:
+        vis.vis_multi_slots(big)
+    assert "2^31-1" in str(e.value)
+    for h in hs + big:
         L.vis_scene_destroy(h)
 
 
