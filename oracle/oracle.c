@@ -495,18 +495,19 @@ typedef struct {
 
 /* Composite pixel centre (pcx, pcy) over `list` (already ordered). zlim: the pixel's depth
  * limit (depth-buffer-aware compositing, a caller-supplied depth buffer tested without
- * writing, section 3.4): a splat whose view depth zkey exceeds it is not composited there;
- * +infinity when there is no depth buffer. */
+ * writing, section 3.4): a splat whose view depth zkey exceeds it is not composited there
+ * (read literally: -infinity rejects every splat, +infinity and NaN none); +infinity when
+ * there is no depth buffer. */
 static void composite_pixel(const prep_t* pp, const ord_t* list, int64_t len, double pcx, double pcy,
                             double zlim, const double bg[3], const opts_t* op, pix_out_t* out) {
     double T = 1.0, C[3] = {0, 0, 0};
     int n_contrib = 0, last_pos = 0, amb = 0;
     for (int64_t j = 0; j < len; ++j) {
         int64_t i = list[j].idx;
-        if (isfinite(zlim)) {
+        {
             const double z = (double)list[j].zkey;
-            if (fabs(z - zlim) <= AMB_Z_REL * fabs(zlim)) amb = 1;
-            if (z > zlim) continue;
+            if (isfinite(zlim) && fabs(z - zlim) <= AMB_Z_REL * fabs(zlim)) amb = 1;
+            if (z > zlim) continue;   /* a NaN limit compares false: it rejects nothing */
         }
         double dx = pcx - pp->uv[2 * i], dy = pcy - pp->uv[2 * i + 1];
         double a = pp->conic[3 * i], b = pp->conic[3 * i + 1], c = pp->conic[3 * i + 2];

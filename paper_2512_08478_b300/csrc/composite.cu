@@ -16,7 +16,10 @@
 // and 1 + the sorted position of the last composited splat.
 // DEPTH: depth-buffer-aware compositing (section 3.4's depth test against a caller's
 // buffer, without writing it): a splat whose view depth exceeds the pixel's value in
-// zlim [H,W] is not composited at that pixel.
+// zlim [H,W] is not composited at that pixel. A warp block's list leaves out the splats
+// deeper than all of its pixels' limits, and since a tile's list is in depth order the tile
+// stops at the first chunk that ends beyond every limit in the tile (behind a wall nothing
+// is walked).
 #include "splat_eval.cuh"
 
 namespace vis {
@@ -58,6 +61,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
     __shared__ uint32_t s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
+    __shared__ float s_wmax[NW];   // DEPTH: largest depth limit of each warp block's live pixels
     const int tile = blockIdx.x;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -92,6 +96,15 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
         ly[r] = (float)py + 0.5f - yc;
         dl[r] = (DEPTH && !P[r].done) ? zlim[(size_t)py * W + px] : __int_as_float(0x7f800000);
     }
+    if (DEPTH) {   // a NaN limit rejects nothing (no comparison holds): it counts as +inf here
+        float m = __int_as_float(0xff800000);
+#pragma unroll
+        for (int r = 0; r < PPT; ++r)
+            if (!P[r].done) m = fmaxf(m, isnan(dl[r]) ? __int_as_float(0x7f800000) : dl[r]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_wmax[warp] = m;
+    }
     const uint2 rg = ranges[tile];
     for (uint32_t base = rg.x; base < rg.y; base += CH) {
         bool all_done = true;
@@ -106,11 +119,23 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             s_a[threadIdx.x] = s.a;
             s_b[threadIdx.x] = s.b;
             s_c[threadIdx.x] = s.c;
-            const uint32_t m = warp_block_mask<NW, BX, BH>(s, half);
+            uint32_t m = warp_block_mask<NW, BX, BH>(s, half);
+            if (DEPTH) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w)
+                    if (!(s.c.w <= s_wmax[w])) m &= ~(1u << w);
+            }
             s_mask[threadIdx.x] = m;
         }
         __syncthreads();
         const int cnt = (int)umin((uint32_t)CH, rg.y - base);
+        bool beyond = false;   // DEPTH: this chunk ends deeper than every limit in the tile
+        if (DEPTH) {
+            float tmax = s_wmax[0];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) tmax = fmaxf(tmax, s_wmax[w]);
+            beyond = !(s_c[cnt - 1].w <= tmax);
+        }
         // this warp's list of splats whose 3-sigma box meets its pixel block, in depth order
         int nlist = 0;
         for (int g0 = 0; g0 < cnt; g0 += 32) {
@@ -161,6 +186,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                 }
             }
         }
+        if (DEPTH && beyond) break;   // every later splat of the tile is deeper still
     }
     if (STATS) {
 #pragma unroll

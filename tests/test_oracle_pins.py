@@ -132,6 +132,11 @@ def test_depth_buffer_closed_forms():
     split, _ = oracle.render(sc, cam, bg, depth=half)
     assert np.all(split["rgb"][:, :, : W // 2] == bg[:, None, None])
     assert np.array_equal(split["rgb"][:, :, W // 2:], free["rgb"][:, :, W // 2:])
+    # the test read literally (reject where z > limit): -inf rejects every splat, NaN none
+    ninf, _ = oracle.render(sc, cam, bg, depth=np.full((H, W), -np.inf, np.float32))
+    assert np.all(ninf["rgb"] == bg[:, None, None]) and np.all(ninf["alpha"] == 0.0)
+    nan, _ = oracle.render(sc, cam, bg, depth=np.full((H, W), np.nan, np.float32))
+    assert np.array_equal(nan["rgb"], free["rgb"]) and np.array_equal(nan["alpha"], free["alpha"])
 
 
 def test_early_stop_excludes_the_stopping_splat():
