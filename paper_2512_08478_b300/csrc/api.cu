@@ -343,6 +343,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
         L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
     }
     L.off_tfinal = take(sizeof(float) * (size_t)W * H);
+    L.off_zmax = take(sizeof(float) * (size_t)L.ntiles);
     L.off_last = take(sizeof(int32_t) * (size_t)W * H);
     L.off_g2 = take(sizeof(float) * 9 * (size_t)n);
     L.total = off;
@@ -555,8 +556,12 @@ static vis_status render_impl(const vis_scene_t* scenes, const float* models, in
     if ((st = cuda_check(cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, stream), "clear workspace")))
         return st;
     prof_mark(1, stream);
-    for (int k = 0; k < n_scenes; ++k)
-        vis::launch_preprocess(scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o), L, w, stream);
+    if (zlim) vis::launch_tile_zmax(L, w, zlim, stream);
+    for (int k = 0; k < n_scenes; ++k) {
+        vis::PrepParams p = scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o);
+        if (zlim) p.tile_zmax = reinterpret_cast<const float*>(w + L.off_zmax);
+        vis::launch_preprocess(p, L, w, stream);
+    }
     prof_mark(2, stream);
     if (L.mode == vis::kSortDepthBin) {
         vis::launch_depth_sort(L, w, stream);

@@ -58,7 +58,8 @@ __device__ __forceinline__ void screen_cov_packed(const float T0[3], const float
     det = q + dil * (a00 + a11) + dil * dil;
 }
 
-template <bool FOLDED, bool PACKED>
+// ZCULL: a depth-tested render's occlusion cull against p.tile_zmax.
+template <bool FOLDED, bool PACKED, bool ZCULL>
 __global__ void __launch_bounds__(kPrepThreads, 5)
 preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
                   uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
@@ -219,6 +220,13 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
                 const int iy0 = (int)fminf(fty, fmaxf(0.f, fy0));
                 const int iy1 = (int)fminf(fty, fmaxf(0.f, fy1));
                 touched = (ix1 > ix0 && iy1 > iy0) ? (uint32_t)((ix1 - ix0) * (iy1 - iy0)) : 0u;
+                if (ZCULL && touched > 0 && touched <= 64) {
+                    // behind the depth buffer in every tile it reaches: no pixel would take it
+                    float zm = __int_as_float(0xff800000);
+                    for (int ty = iy0; ty < iy1; ++ty)
+                        for (int tx = ix0; tx < ix1; ++tx) zm = fmaxf(zm, __ldg(p.tile_zmax + ty * p.tiles_x + tx));
+                    if (z > zm) touched = 0;
+                }
                 // the outer-row trims below need these after the colour; they wait in shared
                 // memory rather than in registers across the SH evaluation
                 s_trim[0][threadIdx.x] = s00; s_trim[1][threadIdx.x] = s11; s_trim[2][threadIdx.x] = s01;
@@ -380,12 +388,42 @@ void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStrea
     for (int k = 0; k < 9; ++k) folded |= p.R_lo[k] != 0.f;
     for (int k = 0; k < 3; ++k) folded |= p.t_lo[k] != 0.f;
     const bool packed = p.pk_pos != nullptr;
-    auto kernel = packed ? (folded ? preprocess_kernel<true, true> : preprocess_kernel<false, true>)
-                         : (folded ? preprocess_kernel<true, false> : preprocess_kernel<false, false>);
+    auto kernel = p.tile_zmax
+        ? (packed ? (folded ? preprocess_kernel<true, true, true> : preprocess_kernel<false, true, true>)
+                  : (folded ? preprocess_kernel<true, false, true> : preprocess_kernel<false, false, true>))
+        : (packed ? (folded ? preprocess_kernel<true, true, false> : preprocess_kernel<false, true, false>)
+                  : (folded ? preprocess_kernel<true, false, false> : preprocess_kernel<false, false, false>));
     kernel<<<blocks, kPrepThreads, 0, stream>>>(
         p, reinterpret_cast<float4*>(ws + L.off_rec), reinterpret_cast<float*>(ws + L.off_depth),
         reinterpret_cast<uint4*>(ws + L.off_rect), reinterpret_cast<uint32_t*>(ws + L.off_touched),
         reinterpret_cast<uint32_t*>(ws + L.off_bsum));
+}
+
+// Largest depth-buffer value of every tile (one warp per tile; NaN counts as +inf: it rejects
+// nothing), for the preprocess's occlusion cull.
+__global__ void __launch_bounds__(256)
+tile_zmax_kernel(const float* __restrict__ zlim, int W, int H, int tile, int tiles_x, int ntiles,
+                 float* __restrict__ zmax) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    float m = __int_as_float(0xff800000);
+    for (int k = lane; k < tile * tile; k += 32) {
+        const int x = tx * tile + k % tile, y = ty * tile + k / tile;
+        if (x < W && y < H) {
+            const float v = __ldg(zlim + (size_t)y * W + x);
+            m = fmaxf(m, isnan(v) ? __int_as_float(0x7f800000) : v);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) zmax[t] = m;
+}
+
+void launch_tile_zmax(const Layout& L, char* ws, const float* zlim, cudaStream_t stream) {
+    const int nt = (int)L.ntiles;
+    tile_zmax_kernel<<<(nt + 7) / 8, 256, 0, stream>>>(zlim, L.W, L.H, L.tile, L.tiles_x, nt,
+                                                       reinterpret_cast<float*>(ws + L.off_zmax));
 }
 
 // Pre-pack (Algorithm 1, once per scene): Sigma = M M^T with M = R_q diag(exp(log_s)),

@@ -65,6 +65,7 @@ struct Layout {
     size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
     size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
     size_t off_tfinal = 0, off_last = 0, off_g2 = 0;
+    size_t off_zmax = 0;     // float[tiles]: largest depth-buffer value per tile (depth-tested renders)
     // depth-first mode only
     size_t off_dkeys[2] = {0, 0}, off_dvals[2] = {0, 0}, off_bsum2 = 0, off_boff2 = 0;
     size_t lookback_words_depth = 0;
@@ -123,6 +124,9 @@ struct PrepParams {
     float wscale;            // sqrt(log2(e)/2): scales the whitening rows of the record
     int tight_extent;        // 1: tile rect from the tight opacity-aware 3-sigma box
     int count_survivors;     // block sums count survivors (depth-first sorts), else tiles touched
+    // depth-tested renders: largest depth limit per tile (NaN counted as +inf), or null; a
+    // splat deeper than the limit of every tile of its footprint is culled
+    const float* tile_zmax;
     // pre-packed scene (Algorithm 1 pre-pack, fp16 pairs in uint32 words; null for fp32 SoA):
     // pos (mu_x, mu_y), (mu_z, alpha); cov (xx, xy), (xz, yy), (yz, zz); col: SH halves,
     // col_words words per Gaussian
@@ -189,6 +193,8 @@ __host__ __device__ __forceinline__ int packed_col_words(int deg) {
 
 // Launchers (host side, enqueue on `stream`).
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream);
+// Per-tile maximum of a depth buffer zlim [H,W] into ws + L.off_zmax.
+void launch_tile_zmax(const Layout& L, char* ws, const float* zlim, cudaStream_t stream);
 // Pre-pack (Algorithm 1, once per scene): fp32 SoA attributes -> fp16 planes pos, cov, col.
 void launch_pack(const float* means, const float* log_scales, const float* quats, const float* logits,
                  const float* sh, int deg, int64_t n, uint2* pos, uint32_t* cov, uint32_t* col, cudaStream_t stream);
