@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -215,6 +216,14 @@ void prof_mark(int k, cudaStream_t stream) {
 namespace vis {
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("VIS_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 int64_t scene_size(vis_scene_t s) { return s ? s->n : 0; }
 

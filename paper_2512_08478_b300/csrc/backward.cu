@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kPrepThreads)
 preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uint32_t* __restrict__ touched,
                            float* __restrict__ d_means, float* __restrict__ d_log_scales,
                            float* __restrict__ d_quats, float* __restrict__ d_logits, float* __restrict__ d_sh) {
+    pdl_entry();
     // i: the Gaussian in the scene's arrays; gi: its workspace slot (multi-scene renders)
     const int i = blockIdx.x * kPrepThreads + threadIdx.x;
     if (i >= p.n) return;
@@ -429,8 +430,8 @@ void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char
         const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
         const int blocks = (p.n + kPrepThreads - 1) / kPrepThreads;
 #define VIS_LAUNCH_PBWD(D)                                                                                \
-    preprocess_backward_kernel<D><<<blocks, kPrepThreads, 0, stream>>>(p, g2, touched, d_means, d_log_scales, \
-                                                                       d_quats, d_logits, d_sh)
+    launch_k(true, preprocess_backward_kernel<D>, blocks, kPrepThreads, 0, stream, p, g2, touched, d_means,      \
+             d_log_scales, d_quats, d_logits, d_sh)
         if (p.deg == 0) VIS_LAUNCH_PBWD(0);
         else if (p.deg == 1) VIS_LAUNCH_PBWD(1);
         else if (p.deg == 2) VIS_LAUNCH_PBWD(2);

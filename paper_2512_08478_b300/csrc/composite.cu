@@ -52,6 +52,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                  Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
                  float* __restrict__ t_final, int32_t* __restrict__ last_out,
                  const float* __restrict__ depth, const float* __restrict__ zlim) {
+    pdl_entry();
     constexpr int NT = TILE * TILE / PPT;   // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
     constexpr int BX = TILE / 8;            // blocks per tile row
@@ -228,9 +229,9 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
 #define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                \
-    composite_kernel<TS, PP, ST, DT><<<blocks, TS * TS / PP, 0, stream>>>(                                    \
-        ranges, vals, rec, L.W, L.H, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl,     \
-        out_rgb, out_alpha, tfin, last, depth, zlim)
+    launch_k(true, composite_kernel<TS, PP, ST, DT>, blocks, TS * TS / PP, 0, stream, ranges, vals, rec, L.W, L.H, \
+             L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin, last,  \
+             depth, zlim)
 #define VIS_LAUNCH_COMPOSITE(TS, PP)                          \
     do {                                                      \
         if (zlim) VIS_LAUNCH_COMPOSITE_S(TS, PP, false, true);   \

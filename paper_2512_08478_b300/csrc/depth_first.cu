@@ -34,6 +34,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 __global__ void __launch_bounds__(kPrepThreads)
 compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ depth, int64_t n,
                 const uint32_t* __restrict__ boff, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals) {
+    pdl_entry();
     __shared__ uint32_t ws[kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
@@ -54,6 +55,7 @@ compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ 
 __global__ void __launch_bounds__(kPrepThreads)
 depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched,
                  const uint32_t* __restrict__ num_visible, uint32_t* __restrict__ bsum) {
+    pdl_entry();
     __shared__ uint32_t ws[kPrepThreads / 32];
     const int64_t nv = *num_visible;
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
@@ -75,6 +77,7 @@ __global__ void __launch_bounds__(kPrepThreads)
 emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
            const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
            const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
+    pdl_entry();
     if (ctrl->error & kErrCapacity) return;
     // per splat slot: start of its copies in the warp's run, and its footprint unrolled into
     // row segments: a = (index, first top-row tile, top width, end of the middle copies),
@@ -172,8 +175,8 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     // 1. compaction of the surviving splats, in index order (the preprocess wrote the
     //    per-block survivor counts)
     launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0, stream);
-    compact_visible<<<blocks_n, kPrepThreads, 0, stream>>>(touched, reinterpret_cast<const float*>(ws + L.off_depth),
-                                                           L.n, bvis_off, dk0, dv0);
+    launch_k(true, compact_visible, blocks_n, kPrepThreads, 0, stream, touched,
+             reinterpret_cast<const float*>(ws + L.off_depth), L.n, (const uint32_t*)bvis_off, dk0, dv0);
     // 2. sort by depth (4 passes; the result lands in buffer 0)
     launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
                                   ctrl->part_counter, &ctrl->error, stream);
@@ -190,14 +193,16 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // 3. tile copies in depth order
     uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
-    depth_touch_sums<<<blocks_n, kPrepThreads, 0, stream>>>(dv0, touched, &ctrl->num_visible, bsum2);
+    launch_k(true, depth_touch_sums, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0, touched,
+             (const uint32_t*)&ctrl->num_visible, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
     if (L.tile_fused) {
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
-        emit_tiles<uint16_t><<<blocks_n, kPrepThreads, 0, stream>>>(
-            dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), &ctrl->num_visible, boff2, L.tiles_x, ctrl,
-            reinterpret_cast<uint16_t*>(ws + L.off_keys[0]), reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
+        launch_k(true, emit_tiles<uint16_t>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
+                 reinterpret_cast<const uint4*>(ws + L.off_rect), (const uint32_t*)&ctrl->num_visible,
+                 (const uint32_t*)boff2, L.tiles_x, (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
+                 reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
         if (mark) mark(mark_index, stream);
         launch_tile_counts(L, ws, stream);
         if (mark) mark(mark_index + 1, stream);

@@ -27,6 +27,7 @@ constexpr int kScanChunk = 8192;   // 32 KB of static shared memory
 __global__ void __launch_bounds__(1024)
 scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
                 uint32_t* total_out, uint32_t* error, int64_t cap) {
+    pdl_entry();
     __shared__ uint32_t s[kScanChunk];
     __shared__ unsigned long long warp_tot[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,7 +74,7 @@ scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, 
 
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
                       int64_t cap, cudaStream_t stream) {
-    scan_block_sums<<<1, 1024, 0, stream>>>(bsum, boff, nblocks, total, error, cap);
+    launch_k(true, scan_block_sums, 1, 1024, 0, stream, bsum, boff, nblocks, total, error, cap);
 }
 
 __global__ void __launch_bounds__(kPrepThreads)

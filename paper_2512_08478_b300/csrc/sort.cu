@@ -25,6 +25,7 @@ template <typename K>
 __global__ void __launch_bounds__(256)
 sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap, int passes,
                uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
+    pdl_entry();
     __shared__ uint32_t sh[kMaxPasses * kRadix];
     for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -76,6 +77,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           const uint32_t* __restrict__ num_keys, int64_t cap, int shift, int nbits,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
+    pdl_entry();
     constexpr int KPT = SortKPT<K>::value;
     constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -209,7 +211,8 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
     const int64_t parts = sort_parts<K>(cap);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
-    sort_histogram<K><<<hist_blocks, 256, 0, stream>>>(keys_in, num_keys_dev, cap, passes, hist, error);
+    launch_k(true, sort_histogram<K>, hist_blocks, 256, 0, stream, keys_in, (const uint32_t*)num_keys_dev, cap,
+             passes, hist, (const uint32_t*)error);
     if (mark) mark(mark_index, stream);
     const K* src_k = keys_in;
     const uint32_t* src_v = vals_in;
@@ -218,9 +221,9 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
         K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < kRadixBits) ? last_bits : kRadixBits;
-        sort_pass<K><<<(int)parts, kSortThreads, smem, stream>>>(
-            src_k, src_v, dk, dv, num_keys_dev, cap, kRadixBits * p, nbits, hist + p * kRadix,
-            lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
+        launch_k(true, sort_pass<K>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
+                 (const uint32_t*)num_keys_dev, cap, kRadixBits * p, nbits, (const uint32_t*)(hist + p * kRadix),
+                 lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
         src_k = dk;
         src_v = dv;
     }
@@ -239,9 +242,9 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
         cudaFuncSetAttribute(sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    sort_pass<K><<<(int)sort_parts<K>(cap), kSortThreads, smem, stream>>>(keys_in, vals_in, keys_out, vals_out,
-                                                                           num_keys_dev, cap, shift, nbits,
-                                                                           hist_pass, lookback, part_counter, error);
+    launch_k(true, sort_pass<K>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
+             vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass, lookback,
+             part_counter, error);
 }
 
 template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint16_t*, uint32_t*, int64_t,

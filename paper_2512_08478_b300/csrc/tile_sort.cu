@@ -23,6 +23,7 @@ namespace vis {
 // ---- per-tile counts ----
 __global__ void __launch_bounds__(1024)
 tile_count_kernel(const uint4* __restrict__ rect, int64_t n, int tiles_x, int tiles_y, int* __restrict__ gdiff) {
+    pdl_entry();
     extern __shared__ int diff[];
     const int nt = tiles_x * tiles_y;
     const uint32_t tx = (uint32_t)tiles_x, ty = (uint32_t)tiles_y;
@@ -57,6 +58,7 @@ __device__ __forceinline__ int warp_scan_incl(int v, int lane) {
 __global__ void __launch_bounds__(1024)
 tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32_t* __restrict__ hist,
                  uint2* __restrict__ ranges) {
+    pdl_entry();
     extern __shared__ int P[];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
@@ -160,12 +162,12 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     const int64_t want = (L.n + 4095) / 4096;
     const int64_t lim = 2 * (int64_t)sm_count_ts();
     const int grid = (int)(want < 1 ? 1 : (want < lim ? want : lim));
-    tile_count_kernel<<<grid, 1024, smem, stream>>>(reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, L.tiles_x,
-                                                    L.tiles_y, gdiff);
+    launch_k(true, tile_count_kernel, grid, 1024, smem, stream, reinterpret_cast<const uint4*>(ws + L.off_rect), L.n,
+             L.tiles_x, L.tiles_y, gdiff);
     const size_t scan_smem = sizeof(int) * (size_t)(L.tiles_x + 1) * L.tiles_y;
-    tile_scan_kernel<<<1, 1024, scan_smem, stream>>>(gdiff, L.tiles_x, L.tiles_y,
-                                                reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,
-                                                reinterpret_cast<uint2*>(ws + L.off_ranges));
+    launch_k(true, tile_scan_kernel, 1, 1024, scan_smem, stream, (const int*)gdiff, L.tiles_x, L.tiles_y,
+             reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,
+             reinterpret_cast<uint2*>(ws + L.off_ranges));
 }
 
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {

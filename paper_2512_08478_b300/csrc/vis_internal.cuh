@@ -191,6 +191,37 @@ __host__ __device__ __forceinline__ int packed_col_words(int deg) {
     return words + (words & 1);
 }
 
+// Programmatic dependent launch (Hopper and later): a kernel of the render path may be launched
+// before its predecessor in the stream has finished. At entry it waits for the predecessor
+// grids to complete (their memory visible) and at once lets its own successor be launched, so
+// a kernel's launch and CTA start-up overlap the previous kernel's tail. Every kernel launched
+// with the attribute calls this before touching global memory.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// False when the environment sets VIS_PDL=0 (plain stream ordering for every launch).
+bool pdl_enabled();
+// Launch `kernel` on `stream`; with pdl (and pdl_enabled()) as a programmatic dependent of
+// the stream's previous kernel. The kernel must start with pdl_entry().
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    if (pdl && pdl_enabled()) {
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Launchers (host side, enqueue on `stream`).
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream);
 // Per-tile maximum of a depth buffer zlim [H,W] into ws + L.off_zmax.
