@@ -310,7 +310,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.zero_begin = off;
     L.off_ctrl = take(sizeof(Ctrl));
     L.off_hist = take(sizeof(uint32_t) * 2 * kMaxPasses * kRadix);
-    L.lookback_words_depth = df ? (size_t)kDepthPasses * sort_parts<uint32_t>(n) * kRadix : 0;
+    L.lookback_words_depth = df ? (size_t)kDepthPasses * depth_sort_parts(n) * kRadix : 0;
     L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * kRadix));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);

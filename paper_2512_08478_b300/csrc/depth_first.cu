@@ -179,7 +179,8 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
              reinterpret_cast<const float*>(ws + L.off_depth), L.n, (const uint32_t*)bvis_off, dk0, dv0);
     // 2. sort by depth (4 passes; the result lands in buffer 0)
     launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
-                                  ctrl->part_counter, &ctrl->error, stream);
+                                  ctrl->part_counter, &ctrl->error, stream, nullptr, 0, kRadixBits,
+                                  depth_sort_kpt(L.n));
 }
 
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {

@@ -17,6 +17,8 @@
 //  - Spin waits on a predecessor are bounded (kSpinLimit polls); on expiry the
 //    CTA records kErrTimeout, publishes anyway so nobody waits on it, and writes
 //    nothing out of range (every destination is checked against the key count).
+#include <type_traits>
+
 #include "onesweep.cuh"
 
 namespace vis {
@@ -42,9 +44,8 @@ sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-template <typename K>
+template <typename K, int KPT>
 struct SortSmem {
-    static constexpr int KPT = SortKPT<K>::value;
     K keys[kSortThreads * KPT];          // reordered by digit
     uint32_t vals[kSortThreads * KPT];   // reordered by digit
     uint32_t vin[kSortThreads * KPT];    // values in input order (asynchronous copies)
@@ -70,18 +71,17 @@ struct SortSmem {
 // All indexing inside the partition is 32-bit and relative to its base. keys_out may be
 // null (last pass of a sort whose keys are not needed). nbits: significant bits of this
 // pass's digit (8, fewer for the top digit of a narrow key).
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads, 3)
+template <typename K, int KPT>
+__global__ void __launch_bounds__(kSortThreads, (KPT <= 8 && sizeof(K) == 4) ? 4 : 3)
 sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
           const uint32_t* __restrict__ num_keys, int64_t cap, int shift, int nbits,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
     pdl_entry();
-    constexpr int KPT = SortKPT<K>::value;
     constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem<K>& S = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    SortSmem<K, KPT>& S = *reinterpret_cast<SortSmem<K, KPT>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_relaxed(error) & kErrCapacity) return;
     const int64_t m = min((int64_t)*num_keys, cap);
@@ -196,19 +196,18 @@ static int sm_count() {
     return sms;
 }
 
-template <typename K>
-void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
-                         uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
-                         uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark, int mark_index, int last_bits) {
-    if (cap <= 0 || passes <= 0) return;
+template <typename K, int KPT>
+static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
+                             uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                             uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
+                             StageMark mark, int mark_index, int last_bits) {
     static bool attr_done = false;   // per process; the attribute is per function
-    const size_t smem = sizeof(SortSmem<K>);
+    const size_t smem = sizeof(SortSmem<K, KPT>);
     if (!attr_done) {
-        cudaFuncSetAttribute(sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    const int64_t parts = sort_parts<K>(cap);
+    const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
     launch_k(true, sort_histogram<K>, hist_blocks, 256, 0, stream, keys_in, (const uint32_t*)num_keys_dev, cap,
@@ -221,12 +220,28 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
         K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < kRadixBits) ? last_bits : kRadixBits;
-        launch_k(true, sort_pass<K>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
+        launch_k(true, sort_pass<K, KPT>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
                  (const uint32_t*)num_keys_dev, cap, kRadixBits * p, nbits, (const uint32_t*)(hist + p * kRadix),
                  lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
         src_k = dk;
         src_v = dv;
     }
+}
+
+// kpt: keys per thread of the passes (0: SortKPT<K>; 8 is also built for 32-bit keys)
+template <typename K>
+void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
+                         uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                         uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
+                         StageMark mark, int mark_index, int last_bits, int kpt) {
+    if (cap <= 0 || passes <= 0) return;
+    if (std::is_same<K, uint32_t>::value && kpt == 8)
+        sort_generic_kpt<K, 8>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev, passes, hist,
+                               lookback, part_counters, error, stream, mark, mark_index, last_bits);
+    else
+        sort_generic_kpt<K, SortKPT<K>::value>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev,
+                                               passes, hist, lookback, part_counters, error, stream, mark,
+                                               mark_index, last_bits);
 }
 
 // One pass of sort_pass over m <= cap keys (read from *num_keys_dev) with digit
@@ -237,12 +252,13 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
                       uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
     if (cap <= 0) return;
     static bool attr_done = false;
-    const size_t smem = sizeof(SortSmem<K>);
+    constexpr int KPT = SortKPT<K>::value;
+    const size_t smem = sizeof(SortSmem<K, KPT>);
     if (!attr_done) {
-        cudaFuncSetAttribute(sort_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    launch_k(true, sort_pass<K>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
+    launch_k(true, sort_pass<K, KPT>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
              vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass, lookback,
              part_counter, error);
 }
@@ -253,10 +269,10 @@ template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint1
 
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int);
 template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);

@@ -25,6 +25,15 @@ template <typename K> constexpr int64_t sort_partition() { return (int64_t)kSort
 template <typename K> constexpr int64_t sort_parts(int64_t cap) {
     return (cap + sort_partition<K>() - 1) / sort_partition<K>();
 }
+// The depth sort of a scene of at most kSmallDepthSort Gaussians uses half-size partitions
+// (8 keys per thread): a pass over ~1M keys is a single wave of short-lived CTAs, twice as
+// many of them, instead of half a wave of long ones.
+constexpr int64_t kSmallDepthSort = (int64_t)2 << 20;
+inline int depth_sort_kpt(int64_t n) { return n <= kSmallDepthSort ? 8 : SortKPT<uint32_t>::value; }
+inline int64_t depth_sort_parts(int64_t n) {
+    const int64_t part = (int64_t)kSortThreads * depth_sort_kpt(n);
+    return (n + part - 1) / part;
+}
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;
@@ -277,7 +286,7 @@ template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits);
+                         StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits, int kpt = 0);
 
 // One sort_pass over the keys (digit (key >> shift) & 255 with nbits significant bits,
 // histogram hist_pass); keys_out may be null. `lookback` holds sort_parts<K>(cap) * kRadix
