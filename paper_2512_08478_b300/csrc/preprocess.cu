@@ -109,18 +109,21 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         const float z = pc[2].x;
         depth_out[gi] = z;
         bool ok = (z > p.near_z) && (opac >= p.alpha_min);
-        if (ok) {   // the colour row is read at the end: start it towards L2 now
-            const char* row = PACKED ? reinterpret_cast<const char*>(p.pk_col + (size_t)i * p.col_words)
-                                     : reinterpret_cast<const char*>(p.sh + (size_t)i * 3 * (p.deg + 1) * (p.deg + 1));
-            const int bytes = PACKED ? 4 * p.col_words : 12 * (p.deg + 1) * (p.deg + 1);
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + bytes - 4));
-        }
+
         uint32_t x0 = 0, x1 = 0, y0 = 0, y1 = 0, trims = 0;
         if (ok) {
             // --- pixel centre u = fx x/z + cx (float-float) ---
             const float2 rx = ff_div(pc[0], pc[2]);
             const float2 ry = ff_div(pc[1], pc[2]);
+            if (fabsf(rx.x) <= p.limx && fabsf(ry.x) <= p.limy) {
+                // centre inside the (guard-widened) frustum: the splat will very likely need its
+                // colour row at the end; start it towards L2 now
+                const char* row = PACKED ? reinterpret_cast<const char*>(p.pk_col + (size_t)i * p.col_words)
+                                         : reinterpret_cast<const char*>(p.sh + (size_t)i * 3 * (p.deg + 1) * (p.deg + 1));
+                const int bytes = PACKED ? 4 * p.col_words : 12 * (p.deg + 1) * (p.deg + 1);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + bytes - 4));
+            }
             float2 u, v;
             {
                 float2 a = two_prod(p.fx, rx.x);
