@@ -372,6 +372,18 @@ def run_ours(args):
                                "13 per composited pair (alpha, transmittance, 3 colour FMAs)",
                     hbm_view=dict(achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
                                   frac=round(achieved / peaks["hbm_gbs"], 4)))
+        # the compositor is issue-bound: its warp instructions (per test, from the committed ncu
+        # capture, times this launch's live test count) over the launch time, against one
+        # instruction per clock from each of the 4 schedulers of every SM
+        tj = ROOT / "profiles" / "traffic.json"
+        ipt = json.loads(tj.read_text()).get("composite", {}).get("warp_inst_per_test") if tj.exists() else None
+        if ipt:
+            inst = ipt * ctrl["pair_tests"]
+            ach_i = inst / (stage_ms["composite"] * 1e-3) / 1e9
+            peak_i = n_sm * 4 * mhz * 1e6 / 1e9
+            roof["issue_view"] = dict(achieved=round(ach_i, 1), peak=round(peak_i, 1), unit="G warp-inst/s",
+                                      frac=round(ach_i / peak_i, 4), warp_inst_per_launch=int(inst),
+                                      source="profiles/traffic.json warp_inst_per_test x live pair tests")
 
     # every HBM-bound stage against the copy peak (the spec bar is >= 60% for preprocess and sort)
     hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
