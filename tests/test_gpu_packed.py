@@ -45,7 +45,7 @@ def test_packed_mixture_parity(deg):
 
 def test_packed_needles_parity():
     """Strongly anisotropic Gaussians (scale ratios up to ~e^3): the unfactored fp16
-    covariance goes through the float-float projection."""
+    covariance goes through the cofactor form of the projected determinant."""
     sc = synth.mixture_scene(20_000, 95, sh_degree=1, components=16, ball_radius=2.0, log_scale_mean=-3.0,
                              log_scale_std=1.2)
     cam = synth.look_at((0.5, 0.5, 6.0), (0, 0, 0), 512, 384, 50.0)
