@@ -65,6 +65,22 @@ def _peaks():
     return dict(hbm_gbs=6400.0, source="fallback", sm_max_mhz=2032.0)
 
 
+def replica_first_view(rank, steps):
+    """Replicas shard by view: replica `rank` renders `steps` consecutive views starting at
+    rank * steps (modulo the orbit), so no two replicas render the same frames."""
+    return rank * steps
+
+
+def max_over_ranks(value, dist, device):
+    """The job's time: the slowest replica's (all_reduce MAX; the value itself on one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -195,7 +211,7 @@ def run_ours(args):
         d_alpha = torch.zeros_like(alpha)
         d_rgb = torch.empty_like(rgb)
     cam_objs = [vis.make_camera(c) for c in cams]
-    view0 = rank * args.steps
+    view0 = replica_first_view(rank, args.steps)
     # pre-packed fp16 scene (Algorithm 1's pre-pack, once, outside the timing); a packed frame
     # is static (a dynamic scene would have to be re-packed every frame)
     packed = bool(args.packed) and not fwdbwd
@@ -266,10 +282,7 @@ def run_ours(args):
     ns, nr, npass = C.c_int(), C.c_int(), C.c_int()
     vis._ok(vis.lib().vis_profile_end(stage, 7, C.byref(ns), C.byref(nr), C.byref(npass)))
     vis.vis_check(ws.buf)
-    if dist:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(t_ms, dist, "cuda")
     frames_total = args.steps * world
     value = t_ms / frames_total
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
@@ -679,9 +692,7 @@ def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts):
     t = e0.elapsed_time(e1)
     world = 1
     if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+        t = max_over_ranks(t, dist, "cuda")
         world = dist.get_world_size()
     return dict(value=round(t / (steps * world), 4), unit="ms/frame", h2d_bytes_per_step=int(h2d),
                 d2h_bytes_per_step=int(d2h), steps=steps,
