@@ -516,16 +516,19 @@ def render(scene: Scene, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | None = N
     depth: optional float32 [H,W] CUDA tensor: depth-buffer-aware compositing (a splat
     deeper than a pixel's value is not composited there). Returns (rgb [3,H,W],
     alpha [H,W]). The workspace keeps the forward's intermediates for the backward; do
-    not reuse it for another render before calling backward.
+    not reuse it for another render before calling backward. A PackedScene (fp16, for
+    viewing) renders without autograd.
     """
     global _RENDER_FN, _RENDER_MULTI_FN
     if _RENDER_FN is None:
         _RENDER_FN, _RENDER_MULTI_FN = _make_autograd()
     if ws is None:
         ws = Workspace(scene.n, W, H, opts=opts)
-    t = scene.tensors
     if depth is not None:
         depth = depth.contiguous().float()
+    if isinstance(scene, PackedScene):
+        return _render_checked(scene, cam, W, H, tuple(bg), ws, opts, depth=depth)
+    t = scene.tensors
     return _RENDER_FN.apply(scene, cam, W, H, tuple(bg), ws, opts, depth, t["means"], t["log_scales"], t["quats"],
                             t["opacity_logits"], t["sh"])
 
@@ -540,7 +543,8 @@ def render_multi(scenes, models, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | 
     """Several scenes in one image, each under its own affine transform (models: [k,3,4]
     float array-like, row-major [A | b], or None for identities), composited in one global
     depth order (vis_render_multi). Differentiable w.r.t. every scene's tensors; the
-    gradients are w.r.t. the untransformed parameters. Returns (rgb [3,H,W], alpha [H,W])."""
+    gradients are w.r.t. the untransformed parameters. If any scene is a PackedScene the
+    render runs without autograd. Returns (rgb [3,H,W], alpha [H,W])."""
     global _RENDER_FN, _RENDER_MULTI_FN
     if _RENDER_FN is None:
         _RENDER_FN, _RENDER_MULTI_FN = _make_autograd()
@@ -552,6 +556,8 @@ def render_multi(scenes, models, cam, W, H, bg=(0.0, 0.0, 0.0), ws: Workspace | 
         models = np.ascontiguousarray(np.asarray(models, np.float32).reshape(len(scenes), 12))
     if depth is not None:
         depth = depth.contiguous().float()
+    if any(isinstance(s, PackedScene) for s in scenes):
+        return _render_multi_checked(scenes, models, cam, W, H, tuple(bg), ws, opts, depth=depth)
     tensors = [s.tensors[k] for s in scenes for k in FIELDS]
     return _RENDER_MULTI_FN.apply(scenes, models, cam, W, H, tuple(bg), ws, opts, depth, *tensors)
 

@@ -114,3 +114,22 @@ def test_packed_scene_has_no_gradients():
         vis.vis_render_backward(ps.handle, cam, cam.W, cam.H, BG, torch.zeros((3, cam.H, cam.W), device="cuda"),
                                 torch.zeros((cam.H, cam.W), device="cuda"), ws.buf, g)
     assert e.value.status == vis.VIS_ERR_UNSUPPORTED
+
+
+def test_packed_scenes_through_the_python_renderers():
+    """vis.render and vis.render_multi take packed scenes (forward only) and give the images of
+    the plain calls."""
+    import torch
+    sc, cams = synth.workload_small()
+    cam = cams[0]
+    rgb, alpha, dec, ps, ws = _packed_render(sc, cam)
+    r2, a2 = vis.render(ps, cam, cam.W, cam.H, BG)
+    assert not r2.requires_grad
+    assert np.array_equal(r2.cpu().numpy().astype(np.float64), rgb)
+    assert np.array_equal(a2.cpu().numpy().astype(np.float64), alpha)
+    plain = vis.Scene.from_numpy(sc)
+    M = np.stack([synth.rigid_model(0.0, (0, 1, 0), (0.5, 0.0, 0.0)), synth.rigid_model(0.0, (0, 1, 0), (-0.5, 0.0, 0.0))])
+    r3, a3 = vis.render_multi([ps, plain], M, cam, cam.W, cam.H, BG)
+    ref, _ = oracle.render_multi([dec, sc], list(M), cam, BG)
+    image_parity(r3.cpu().numpy().astype(np.float64), a3.cpu().numpy().astype(np.float64), ref)
+    torch.cuda.synchronize()
