@@ -430,3 +430,52 @@ def test_dynamic_update_reference_pins():
                                    ex["phase"], 1.25)
     np.testing.assert_allclose(lb, la, atol=1e-9)                              # integer f: period 1 in t
     np.testing.assert_allclose(mb - ma, ex["velocity"].astype(np.float64), atol=1e-9)   # linear in t
+
+
+# ---------------------------------------------------------------------------------
+# Depth ties and the off-axis Jacobian guard (readings S9 and S5)
+# ---------------------------------------------------------------------------------
+
+def test_equal_depths_composite_in_index_order():
+    """Two Gaussians at the same point (same depth to the bit) with different colours and
+    opacities: the lower index is in front (ties go by index), so at the centre pixel
+    C = c0 a0 + c1 a1 (1 - a0) + bg (1 - a0)(1 - a1), and listing them the other way round
+    swaps the roles."""
+    W, H, d = 32, 32, 4.0
+    cam = synth.look_at((0, 0, d), (0, 0, 0), W, H, 60.0)
+    g0 = _one_gaussian_scene((0, 0, 0), 0.08, (1, 0, 0, 0), 0.8, (0.9, 0.1, 0.1))
+    g1 = _one_gaussian_scene((0, 0, 0), 0.08, (1, 0, 0, 0), -0.4, (0.1, 0.1, 0.9))
+    bg = np.array([0.0, 0.5, 0.0])
+    px, py = W // 2, H // 2                      # pixel centre 0.5 px off the splat centre
+    for order in ((g0, g1), (g1, g0)):
+        sc = _stack(list(order))
+        img, prep = oracle.render(sc, cam, bg)
+        assert prep["zkey"][0] == prep["zkey"][1]
+        s = math.exp(float(np.float32(math.log(0.08))))
+        var = (cam.fx * s / d) ** 2 + DIL
+        G = math.exp(-0.5 * (0.5 ** 2 + 0.5 ** 2) / var)
+        a = [1 / (1 + math.exp(-float(g["opacity_logits"][0]))) * G for g in order]
+        c = [_dc_colour(g, 0) for g in order]
+        want = c[0] * a[0] + c[1] * a[1] * (1 - a[0]) + bg * (1 - a[0]) * (1 - a[1])
+        np.testing.assert_allclose(img["rgb"][:, py, px], want, atol=1e-12)
+
+
+def test_jacobian_guard_freezes_the_footprint_beyond_it():
+    """J is taken at x/z clamped to 1.3 tan(half FOV): beyond the guard, moving a Gaussian
+    further sideways at the same depth leaves its projected covariance unchanged (only the
+    centre moves), while inside the guard the covariance does change."""
+    W, H, d = 64, 48, 5.0
+    cam = synth.look_at((0, 0, d), (0, 0, 0), W, H, 60.0)
+    limx = 1.3 * (W / (2.0 * cam.fx))
+    sig = 0.6                                     # large: reaches the image from outside it
+    outs = []
+    for k in (1.6, 2.4):                          # x/z beyond the guard, both sides
+        for sgn in (1.0, -1.0):
+            x = sgn * k * limx * d                # camera at z = d looking at the origin
+            sc = _one_gaussian_scene((x, 0.0, 0.0), sig, (1, 0, 0, 0), 2.0, (0.5, 0.5, 0.5))
+            outs.append(oracle.preprocess(sc, cam)["S"][0])
+    assert min(np.abs(o).max() for o in outs) > 0
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    inside = [oracle.preprocess(_one_gaussian_scene((f * limx * d, 0, 0), sig, (1, 0, 0, 0), 2.0,
+                                                     (0.5, 0.5, 0.5)), cam)["S"][0] for f in (0.2, 0.6)]
+    assert np.abs(inside[0] - inside[1]).max() > 1e-3 * np.abs(inside[0]).max()
