@@ -2,6 +2,8 @@
 reading fp16 planes against the FP64 oracle run on the values those planes decode to (the
 planes are built on the host by the oracle's prepack, so no oracle input comes from the
 GPU), and the GPU's own pack kernel against the host packing."""
+import math
+
 import numpy as np
 import pytest
 
@@ -133,3 +135,33 @@ def test_packed_scenes_through_the_python_renderers():
     ref, _ = oracle.render_multi([dec, sc], list(M), cam, BG)
     image_parity(r3.cpu().numpy().astype(np.float64), a3.cpu().numpy().astype(np.float64), ref)
     torch.cuda.synchronize()
+
+
+def test_thresholds_at_equality_on_the_gpu():
+    """The decisions at exact equality, as the oracle takes them: a splat whose alpha equals
+    alpha_min is composited (a pre-packed opacity equal to the alpha_min option, on a pixel
+    centre: q = 0), and a splat whose depth equals the depth-buffer value passes the test."""
+    import torch
+    W = H = 33
+    cam = synth.look_at((0, 0, 4.0), (0, 0, 0), W, H, 60.0)
+    amin = float(np.float16(1.0 / 255.0))
+    sc = synth.uniform_cube_scene(1, 0, sh_degree=0, extent=0.0, log_scale_mean=math.log(0.05), log_scale_std=0.0)
+    planes, dec = oracle.prepack(sc)
+    dec = dict(dec, opacity=np.array([amin]))
+    planes["pos"] = planes["pos"].copy()
+    planes["pos"][0, 1] = (planes["pos"][0, 1] & 0xFFFF) | (int(np.array([amin], np.float16).view(np.uint16)[0]) << 16)
+    ps = vis.PackedScene.from_planes(planes, 0)
+    opts = vis.make_opts(alpha_min=amin)
+    ws = vis.Workspace(1, W, H, opts=opts)
+    rgb, alpha = vis._render_checked(ps, cam, W, H, BG, ws, opts)
+    ref, prep = oracle.render(dec, cam, BG, opts=dict(alpha_min=amin))
+    assert prep["uv"][0, 0] == W / 2 and ref["n_contrib"][H // 2, W // 2] == 1
+    g = alpha.cpu().numpy().astype(np.float64)
+    assert abs(g[H // 2, W // 2] - amin) <= 1e-7 and abs(ref["alpha"][H // 2, W // 2] - amin) <= 1e-12
+    # depth equality: the buffer holds the splat's own float32 view depth
+    s = vis.Scene.from_numpy(sc)
+    free, fa = vis._render_checked(s, cam, W, H, BG, vis.Workspace(1, W, H), None)
+    z = float(oracle.preprocess(sc, cam)["zkey"][0])
+    d = torch.full((H, W), z, dtype=torch.float32, device="cuda")
+    eq, ea = vis._render_checked(s, cam, W, H, BG, vis.Workspace(1, W, H), None, depth=d)
+    assert torch.equal(eq, free) and torch.equal(ea, fa) and float(fa.max()) > 0.1

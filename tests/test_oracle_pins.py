@@ -479,3 +479,31 @@ def test_jacobian_guard_freezes_the_footprint_beyond_it():
     inside = [oracle.preprocess(_one_gaussian_scene((f * limx * d, 0, 0), sig, (1, 0, 0, 0), 2.0,
                                                      (0.5, 0.5, 0.5)), cam)["S"][0] for f in (0.2, 0.6)]
     assert np.abs(inside[0] - inside[1]).max() > 1e-3 * np.abs(inside[0]).max()
+
+
+def test_thresholds_at_equality():
+    """The readings at exact equality: a splat whose alpha equals alpha_min is composited (only
+    alpha < 1/255 is skipped), and a splat whose depth equals the depth-buffer value passes
+    the depth test (only deeper splats are rejected). Built exactly: the pre-packed form gives
+    the opacity directly (the float32 alpha_min itself), the splat sits on a pixel centre (odd
+    image size, q = 0, so alpha = opacity), and the buffer holds the splat's own float32 depth."""
+    W = H = 33
+    cam = synth.look_at((0, 0, 4.0), (0, 0, 0), W, H, 60.0)
+    amin = float(np.float32(1.0 / 255.0))
+    bg = np.array([0.2, 0.3, 0.4])
+    sc = dict(means=np.zeros((1, 3)), cov6=np.array([[0.01, 0, 0, 0.01, 0, 0.01]]), opacity=np.array([amin]),
+              sh=((np.array([[[0.9, 0.1, 0.5]]]) - 0.5) / Y00), sh_degree=0)
+    img, prep = oracle.render(sc, cam, bg)
+    assert prep["valid"][0] == 1 and prep["uv"][0, 0] == W / 2 and prep["uv"][0, 1] == H / 2
+    c = np.array([0.9, 0.1, 0.5])
+    np.testing.assert_allclose(img["rgb"][:, H // 2, W // 2], c * amin + bg * (1 - amin), atol=1e-15)
+    assert img["n_contrib"][H // 2, W // 2] == 1
+    # depth test at equality
+    sc2 = _one_gaussian_scene((0, 0, 0), 0.05, (1, 0, 0, 0), 2.0, (0.9, 0.1, 0.5))
+    free, p2 = oracle.render(sc2, cam, bg)
+    z = p2["zkey"][0]
+    eq, _ = oracle.render(sc2, cam, bg, depth=np.full((H, W), z, np.float32))
+    assert np.array_equal(eq["rgb"], free["rgb"]) and free["alpha"].max() > 0.5
+    below = np.nextafter(np.float32(z), np.float32(-np.inf))
+    wall, _ = oracle.render(sc2, cam, bg, depth=np.full((H, W), below, np.float32))
+    assert np.all(wall["alpha"] == 0.0)
