@@ -244,9 +244,13 @@ VIS_API vis_status vis_render_backward(vis_scene_t scene, const vis_camera* cam,
  * opaque geometry with the depth test on and depth writes off). As vis_render, plus
  *  depth   device float32 [H,W] (row-major, 16-byte aligned, not modified): per pixel,
  *          a view depth (camera-space z, the units of the splat depths); a splat whose
- *          view depth exceeds it is not composited at that pixel (a value of +inf tests
- *          nothing, so an all-inf buffer gives vis_render's image bit for bit).
- * The buffer is read by the compositor only; sorting and tile lists are unchanged.
+ *          view depth exceeds it is not composited at that pixel (+inf and NaN test
+ *          nothing, so an all-inf buffer gives vis_render's image bit for bit; -inf
+ *          rejects every splat).
+ * The buffer also culls work without changing any pixel: a small kernel takes each tile's
+ * largest value, the preprocess drops a splat deeper than that in every tile it reaches
+ * (so it is neither sorted nor listed), and the compositor skips splats deeper than all
+ * of a pixel block's values.
  * Errors: as vis_render, and VIS_ERR_INVALID_ARG for a null or misaligned depth. */
 VIS_API vis_status vis_render_depth(vis_scene_t scene, const vis_camera* cam, int W, int H,
                                     const float bg[3], const float* depth, float* out_rgb,
