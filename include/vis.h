@@ -20,7 +20,10 @@
  *    arrays (zero copy); they must outlive the handle and may be rewritten
  *    between frames.
  *  - Work is enqueued on the given stream and returns without synchronising,
- *    except vis_check(), which synchronises the stream.
+ *    except vis_check(), which synchronises the stream. The kernels of a render are
+ *    launched as programmatic dependents of their predecessor on the stream (each
+ *    waits for it at entry, so ordering is unchanged; launches overlap tails); set
+ *    the environment variable VIS_PDL=0 before the first call for plain launches.
  *  - Every call returns a vis_status; no exception or abort crosses the ABI.
  *    On failure, vis_last_error() returns a thread-local message.
  *  - Errors found on the device (key capacity exceeded, a bounded spin wait that
