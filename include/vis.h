@@ -156,7 +156,8 @@ typedef struct {
 /* Device-written status block at workspace offset off_ctrl (= 0). */
 typedef struct {
     uint32_t num_keys;       /* (tile, splat) pairs listed by the last render (may exceed capacity) */
-    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout */
+    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout, bit 2: a tile
+                                beyond sort_mode 3's merge limit */
     uint32_t internal[16];   /* sort partition tickets */
     uint32_t num_visible;    /* Gaussians that survived culling (sort_mode 1, 2) */
     uint32_t pad0;
@@ -226,7 +227,8 @@ VIS_API vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, i
                       const vis_render_opts* opts, void* stream);
 
 /* Synchronise `stream`, read the status block of `ws`, and return VIS_OK,
- * VIS_ERR_CAPACITY or VIS_ERR_TIMEOUT. num_keys (host, may be NULL) receives the
+ * VIS_ERR_CAPACITY, VIS_ERR_TIMEOUT or (sort_mode 3, a tile beyond its merge limit)
+ * VIS_ERR_UNSUPPORTED. num_keys (host, may be NULL) receives the
  * number of keys the last render produced (the capacity a retry needs). */
 VIS_API vis_status vis_check(const void* ws, void* stream, int64_t* num_keys);
 
