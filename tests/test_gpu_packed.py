@@ -165,3 +165,32 @@ def test_thresholds_at_equality_on_the_gpu():
     d = torch.full((H, W), z, dtype=torch.float32, device="cuda")
     eq, ea = vis._render_checked(s, cam, W, H, BG, vis.Workspace(1, W, H), None, depth=d)
     assert torch.equal(eq, free) and torch.equal(ea, fa) and float(fa.max()) > 0.1
+
+
+def test_packed_scenes_against_a_depth_buffer():
+    """Pre-packed scenes behind a slanted depth wall, alone and as transformed models of one
+    image (the packed, model-folded and occlusion-culled preprocess variants together)."""
+    import torch
+    sc = synth.mixture_scene(20_000, 97, sh_degree=2, components=16, ball_radius=1.5, comp_std=0.5,
+                             log_scale_mean=-3.5)
+    cam = synth.look_at((0.0, 0.0, 4.5), (0, 0, 0), 480, 270, 50.0)
+    xs = (np.arange(cam.W)[None, :] + 0.5) / cam.W - 0.5
+    depth = np.repeat(4.5 + 1.0 * xs, cam.H, axis=0).astype(np.float32)
+    d = torch.from_numpy(depth).cuda()
+    planes, dec = oracle.prepack(sc)
+    ps = vis.PackedScene.from_planes(planes, 2)
+    ws = vis.Workspace(ps.n, cam.W, cam.H)
+    rgb, alpha = vis._render_checked(ps, cam, cam.W, cam.H, BG, ws, None, depth=d)
+    ref, _ = oracle.render(dec, cam, BG, depth=depth)
+    free, _ = oracle.render(dec, cam, BG)
+    assert np.abs(ref["rgb"] - free["rgb"]).max() > 0.05
+    image_parity(rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), ref)
+    scs, models, mcam = synth.workload_multi(scale=0.01, W=480, H=270, seed=8)
+    packed = [oracle.prepack(s) for s in scs]
+    pss = [vis.PackedScene.from_planes(pl, s["sh_degree"]) for (pl, _), s in zip(packed, scs)]
+    mdepth = np.repeat(12.0 + 4.0 * (xs + 0.5), mcam.H, axis=0).astype(np.float32)
+    mws = vis.multi_workspace(pss, mcam.W, mcam.H)
+    r2, a2 = vis._render_multi_checked(pss, models, mcam, mcam.W, mcam.H, BG, mws, None,
+                                       depth=torch.from_numpy(mdepth).cuda())
+    ref2, _ = oracle.render_multi([dd for _, dd in packed], list(models), mcam, BG, depth=mdepth)
+    image_parity(r2.cpu().numpy().astype(np.float64), a2.cpu().numpy().astype(np.float64), ref2)
