@@ -201,11 +201,10 @@ static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_
                              uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                              uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                              StageMark mark, int mark_index, int last_bits) {
-    static bool attr_done = false;   // per process; the attribute is per function
+    static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     const size_t smem = sizeof(SortSmem<K, KPT>);
-    if (!attr_done) {
+    if (once_per_device(attr_dev)) {
         cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
     }
     const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
@@ -251,12 +250,11 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
                       const uint32_t* num_keys_dev, int shift, int nbits, const uint32_t* hist_pass,
                       uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
     if (cap <= 0) return;
-    static bool attr_done = false;
+    static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     constexpr int KPT = SortKPT<K>::value;
     const size_t smem = sizeof(SortSmem<K, KPT>);
-    if (!attr_done) {
+    if (once_per_device(attr_dev)) {
         cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
     }
     launch_k(true, sort_pass<K, KPT>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
              vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass, lookback,

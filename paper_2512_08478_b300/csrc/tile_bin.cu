@@ -203,15 +203,14 @@ void launch_tile_bin(const Layout& L, char* ws, cudaStream_t stream, StageMark m
     uint32_t* tile_start = reinterpret_cast<uint32_t*>(ws + L.off_tile_start);
     const int nt = (int)L.ntiles;
     const int grid = (int)L.bin_chunks;
-    static bool attr_done = false;
+    static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     const int emit_nw = (nt <= kBinMaxTiles8) ? 8 : 4;
     const size_t emit_smem = (size_t)emit_nw * ((nt + 1) / 2) * sizeof(uint32_t);
     const size_t count_smem = (size_t)nt * sizeof(uint32_t);
-    if (!attr_done) {
+    if (once_per_device(attr_dev)) {
         cudaFuncSetAttribute(bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         cudaFuncSetAttribute(bin_emit_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         cudaFuncSetAttribute(bin_emit_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_done = true;
     }
     bin_count_kernel<<<grid, 256, count_smem, stream>>>(dvals, rect, &ctrl->num_visible, L.bin_chunk, nt, L.tiles_x,
                                                         counts);

@@ -291,15 +291,14 @@ void launch_tile_first(const Layout& L, char* ws, cudaStream_t stream, StageMark
     uint32_t* vals = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     const int grid = (int)L.tf_grid;
     const size_t tsm = sizeof(uint32_t) * (size_t)nt;
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
+    if (once_per_device(attr_dev)) {
         const int most = (int)(sizeof(uint32_t) * kTileFusedMaxTiles);
         cudaFuncSetAttribute(tf_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(tf_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(tf_sort_kernel<1024, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 * 8);
         cudaFuncSetAttribute(tf_sort_kernel<4096, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 8);
         cudaFuncSetAttribute(tf_sort_kernel<16384, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8);
-        attr_done = true;
     }
     tf_count_kernel<<<grid, kTfThreads, tsm, stream>>>(rect, L.n, L.tf_chunk, L.tiles_x, L.tiles_y, total, within);
     tf_scan_kernel<<<1, 1024, 0, stream>>>(total, nt, L.cap, ranges, start, lists, ctrl);

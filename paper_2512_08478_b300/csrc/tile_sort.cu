@@ -146,8 +146,8 @@ static int sm_count_ts() {
 }
 
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
+    if (once_per_device(attr_dev)) {
         // the largest per-tile counter array of the fused path; the scan's rows are padded by one
         // word (at most 1024 rows at 16-pixel tiles) and it adds ~0.2 KB of static shared
         // memory, within the 227 KB a CTA may use
@@ -155,7 +155,6 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
         cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              most + (int)sizeof(int) * 2048);
-        attr_done = true;
     }
     const size_t smem = sizeof(int) * (size_t)L.ntiles;
     int* gdiff = reinterpret_cast<int*>(ws + L.off_tdiff);

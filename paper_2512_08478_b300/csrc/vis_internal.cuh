@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <stdint.h>
 
 #include <vector>
@@ -229,6 +230,16 @@ inline void launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, 
         cfg.numAttrs = 1;
     }
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// True the first time it is called for the current device with this flag word: function
+// attributes (cudaFuncSetAttribute) apply to the current device, so each device a process
+// renders on gets its own set-up. Thread safe.
+inline bool once_per_device(std::atomic<uint64_t>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    const uint64_t bit = 1ull << dev;
+    return !(done.fetch_or(bit) & bit);
 }
 
 // Launchers (host side, enqueue on `stream`).
