@@ -221,6 +221,36 @@ def fd_scene(seed=3, n=64, W=64, H=64):
     return scene, cam
 
 
+def fd_branch_scene(seed=3):
+    """The finite-difference scene plus three Gaussians that drive the definition's clamps:
+
+    index 64  "clamp": isotropic, logit 8 (opacity 0.99966), world (-0.632, -0.470, 0.9),
+              log-scale -1.785: about 3 px wide, centred 0.2 px right of and 0.1 px above
+              the centre of pixel (20, 40), so that pixel takes alpha = min(0.99, o G) at
+              the clamp while its neighbours stay near 0.95;
+    index 65  "guard": world (3.4, -0.1, 0), i.e. camera-space x/z = 0.85, beyond the
+              Jacobian guard 1.3 tan(30 deg) = 0.75 of the 60 deg view, with scales
+              (0.7, 0.5, 0.6) so that its footprint still reaches the right image border;
+    index 66  "black": SH3 with rendered DC colour (0.6, -0.4, 0.3), so that the green sum
+              stays below zero (the higher bands are N(0, 0.05)) and the channel renders
+              black under the colour clamp.
+    The 64x64 camera at (0, 0, 4) maps world (X, Y, Z) to camera (X, -Y, 4 - Z)."""
+    scene, cam = fd_scene(seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 2000))
+    means = np.array([[-0.632, -0.470, 0.9], [3.4, -0.1, 0.0], [0.1, 0.15, -0.3]])
+    log_scales = np.array([[-1.785] * 3, np.log([0.7, 0.5, 0.6]), [-1.9, -2.1, -2.0]])
+    quats = np.array([[1.0, 0.0, 0.0, 0.0], [0.9, 0.2, -0.3, 0.25], [0.6, -0.3, 0.5, 0.4]])
+    logits = np.array([8.0, 3.0, 1.5])
+    sh = np.zeros((3, 16, 3))
+    sh[:, 0, :] = (np.array([[0.8, 0.3, 0.6], [0.2, 0.7, 0.4], [0.6, -0.4, 0.3]]) - 0.5) / _Y00
+    sh[:, 1:, :] = rng.normal(0.0, 0.05, (3, 15, 3))
+    extra = _pack(means, log_scales, quats, logits, sh, 3)
+    out = {k: np.concatenate([scene[k], extra[k]]) for k in
+           ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    out["sh_degree"] = 3
+    return out, cam
+
+
 BATCH_RESOLUTIONS = ((512, 512), (1280, 720), (1920, 1080))
 
 

@@ -53,22 +53,29 @@ def gpu_stage_outputs(sc, ws):
                 ranges=ranges, m=m, layout=L)
 
 
-def image_parity(gpu_rgb, gpu_alpha, ref, max_abs=2e-4, mean_abs=1e-5, max_ambiguous_frac=5e-3):
-    """The parity bar: max-abs on unambiguous pixels, mean-abs on all, per channel."""
+def image_parity(gpu_rgb, gpu_alpha, ref, max_abs=2e-4, mean_abs=1e-5, max_exempt_frac=1e-4):
+    """The parity bar: max-abs on every pixel, mean-abs on all, per channel.
+
+    A pixel may exceed max-abs only if the oracle flags it as ambiguous (a decision within
+    FP32 rounding of its threshold, where both results are correct), and such exempt
+    pixels may make up at most 1e-4 of the image."""
     amb = ref["ambiguous"] != 0
-    ok = ~amb
-    frac = amb.mean()
     d = np.abs(gpu_rgb - ref["rgb"])
     da = np.abs(gpu_alpha - ref["alpha"])
-    worst = max(d[:, ok].max(initial=0.0), da[ok].max(initial=0.0))
-    print(f"parity: max-abs {worst:.3g} (unambiguous), mean-abs {d.mean():.3g}, ambiguous {amb.sum()} "
-          f"({frac:.2e}), max-abs incl. ambiguous {d.max(initial=0.0):.3g}")
-    assert frac <= max_ambiguous_frac, f"ambiguous fraction {frac}"
-    assert worst <= max_abs, f"max-abs {worst} on unambiguous pixels"
+    per_pix = np.maximum(d.max(axis=0), da)
+    over = per_pix > max_abs
+    exempt = over & amb
+    frac = exempt.mean()
+    worst = per_pix[~exempt].max(initial=0.0)
+    print(f"parity: max-abs {per_pix.max(initial=0.0):.3g} on all pixels, {worst:.3g} outside the exempt ones, "
+          f"mean-abs {d.mean():.3g}, flagged {int(amb.sum())} ({amb.mean():.2e}), exempt {int(exempt.sum())}")
+    assert frac <= max_exempt_frac, f"{int(exempt.sum())} flagged pixels beyond max-abs ({frac:.2e})"
+    assert worst <= max_abs, f"max-abs {worst} on a pixel the oracle does not flag"
     for ch in range(3):
         assert d[ch].mean() <= mean_abs, f"channel {ch} mean-abs {d[ch].mean()}"
     assert da.mean() <= mean_abs, f"alpha mean-abs {da.mean()}"
-    return dict(max_abs=float(worst), mean_abs=float(d.mean()), ambiguous=int(amb.sum()))
+    return dict(max_abs=float(per_pix.max(initial=0.0)), mean_abs=float(d.mean()), flagged=int(amb.sum()),
+                exempt=int(exempt.sum()))
 
 
 def footprint_tiles(rect, trims, tiles_x):

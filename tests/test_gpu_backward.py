@@ -49,6 +49,21 @@ def test_fd_scene_gradients_match_oracle(bg):
     _compare(_gpu_grads(sc, cam, gC, gA, bg), oracle.adjoint(sc, cam, gC, gA, bg))
 
 
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.25, 0.5, 0.75)])
+def test_clamp_branch_scene_gradients_match_oracle(bg):
+    """The finite-difference scene plus a Gaussian at the alpha clamp, one beyond the
+    Jacobian guard and one with a negative (clamped) colour sum: the three regimes where
+    the definition passes no gradient, each pinned in the oracle by central differences."""
+    sc, cam = synth.fd_branch_scene()
+    rng = np.random.default_rng(8)
+    gC = rng.standard_normal((3, cam.H, cam.W))
+    gA = rng.standard_normal((cam.H, cam.W))
+    g = _gpu_grads(sc, cam, gC, gA, bg)
+    ref = oracle.adjoint(sc, cam, gC, gA, bg)
+    _compare(g, ref)
+    assert np.all(g["sh"][66, :, 1] == 0.0)   # the clamped channel gets exactly nothing
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_mixture_scene_gradients_match_oracle(tile):
     sc = synth.mixture_scene(3000, 21, sh_degree=3, ball_radius=2.0, comp_std=0.4, log_scale_mean=-3.0)
@@ -76,8 +91,29 @@ def test_autograd_function_matches_c_abi():
     _compare({k: ts[k].grad.cpu().numpy().astype(np.float64) for k in vis.FIELDS}, ref)
 
 
+def _flagged_gaussians(prep, amb, tile=16, q_max=9.0):
+    """Gaussians that the oracle evaluates (q <= 9 in FP64) at a pixel it flags as ambiguous:
+    only their gradients may legitimately take a different decision in FP32."""
+    flagged = np.zeros(prep["valid"].shape[0], bool)
+    valid = prep["valid"] != 0
+    rect = prep["rect"]
+    by_tile = {}
+    for y, x in zip(*np.nonzero(amb)):
+        by_tile.setdefault((int(x) // tile, int(y) // tile), []).append((int(x), int(y)))
+    for (tx, ty), pix in by_tile.items():
+        cand = np.nonzero(valid & (rect[:, 0] <= tx) & (tx < rect[:, 2]) & (rect[:, 1] <= ty) & (ty < rect[:, 3]))[0]
+        uv, con = prep["uv"][cand], prep["conic"][cand]
+        for x, y in pix:
+            dx, dy = x + 0.5 - uv[:, 0], y + 0.5 - uv[:, 1]
+            q = con[:, 0] * dx * dx + 2.0 * con[:, 1] * dx * dy + con[:, 2] * dy * dy
+            flagged[cand[q <= q_max * (1.0 + 1e-6)]] = True
+    return flagged
+
+
 @pytest.mark.slow
 def test_500k_sh3_800px_l2_loss_gradients():
+    """The fwd+bwd workload at full size: group norms on every Gaussian, and the per-element
+    bar on every Gaussian that the oracle does not evaluate at an ambiguous pixel."""
     sc, target, cams = synth.workload_fwdbwd()
     cam = cams[0]
     tgt_rgb, _, _, _ = render_gpu(target, cam)
@@ -86,7 +122,16 @@ def test_500k_sh3_800px_l2_loss_gradients():
     gA = np.zeros((cam.H, cam.W))
     g = _gpu_grads(sc, cam, gC, gA)
     ref = oracle.adjoint(sc, cam, gC, gA)
-    # group norms at full size (per-element decisions at ambiguous pixels may differ)
+    img, prep = oracle.render(sc, cam)
+    flagged = _flagged_gaussians(prep, img["ambiguous"] != 0)
+    keep = ~flagged
+    print(f"flagged Gaussians: {int(flagged.sum())} of {flagged.size}")
+    assert flagged.mean() <= 0.2
+    n = flagged.size
     for k in vis.FIELDS:
-        a, b = g[k].reshape(-1), ref[k].reshape(-1)
+        a, b = g[k].reshape(n, -1), ref[k].reshape(n, -1)
         assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), (k, np.linalg.norm(a - b) / np.linalg.norm(b))
+        tol = 1e-3 * np.abs(b) + 1e-3 * np.abs(b).max()
+        bad = np.abs(a - b) > tol
+        print(f"{k}: per-element misses {int(bad[keep].sum())} kept, {int(bad[flagged].sum())} flagged")
+        assert bad[keep].sum() == 0, (k, int(bad[keep].sum()), float(np.abs(a - b)[bad & keep[:, None]].max()))

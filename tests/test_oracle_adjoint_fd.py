@@ -141,3 +141,55 @@ def test_multi_model_adjoint_matches_central_differences():
                 assert abs(f1 - g[idx]) <= 1e-6 * abs(f1) + 1e-6 * scale, (which, field, idx, f1, g[idx])
     assert checked > 350
     assert excluded < 0.05 * (checked + excluded), (checked, excluded)
+
+
+def test_adjoint_clamp_branches_match_central_differences():
+    """The three places where the definition passes no gradient, each pinned by central
+    differences of the forward on a Gaussian built to sit in it (synth.fd_branch_scene):
+
+    - alpha clamp (reading S11): Gaussian 64 reaches o G > 0.99 at one pixel, where
+      alpha = 0.99 whatever its parameters are, so that pixel adds nothing to any of its
+      derivatives;
+    - Jacobian guard (reading S5): Gaussian 65 sits at x/z = 0.85, beyond 1.3 tan(half
+      FOV), where J is taken at the clamped ratio and so does not move with x;
+    - colour clamp (reading S2): Gaussian 66's green sum is negative, rendered as 0, so
+      its green SH coefficients have zero derivative.
+    Every parameter of the three Gaussians is checked (59 each)."""
+    scene, cam = synth.fd_branch_scene()
+    scene = {k: (v.astype(np.float64) if k in FIELDS else v) for k, v in scene.items()}
+    prep = oracle.preprocess(scene, cam)
+    # the scene is what it claims to be
+    u, v = prep["uv"][64]
+    d = np.array([20.5 - u, 40.5 - v])
+    a, b, c = prep["conic"][64]
+    q = a * d[0] ** 2 + 2 * b * d[0] * d[1] + c * d[1] ** 2
+    assert prep["opacity"][64] * np.exp(-0.5 * q) > float(np.float32(0.99)) + 1e-3
+    p_cam = cam.R.astype(np.float64) @ scene["means"][65] + cam.t.astype(np.float64)
+    assert p_cam[0] / p_cam[2] > 1.3 * (cam.W / (2.0 * cam.fx)) + 0.05
+    assert prep["valid"][65] == 1 and prep["rect"][65][0] < cam.W // 16
+    assert prep["rgb"][66][1] == 0.0 and prep["valid"][66] == 1
+
+    rng = np.random.default_rng(41)
+    gC = rng.standard_normal((3, cam.H, cam.W))
+    gA = rng.standard_normal((cam.H, cam.W))
+    bg = (0.25, 0.5, 0.75)
+    grads = oracle.adjoint(scene, cam, gC, gA, bg)
+    K = 16
+    checked = excluded = 0
+    for field in FIELDS:
+        g = grads[field].reshape(-1)
+        per = g.shape[0] // scene["means"].shape[0]
+        scale = np.max(np.abs(g)) + 1e-30
+        for i in (64, 65, 66):
+            for idx in range(i * per, (i + 1) * per):
+                f1 = _fd(scene, cam, gC, gA, bg, field, idx, 1e-6)
+                f2 = _fd(scene, cam, gC, gA, bg, field, idx, 1e-5)
+                if abs(f1 - f2) > 1e-4 * max(abs(f1), abs(f2)) + 1e-7 * scale:
+                    excluded += 1
+                    continue
+                checked += 1
+                assert abs(f1 - g[idx]) <= 1e-6 * abs(f1) + 1e-6 * scale, (field, i, idx, f1, g[idx])
+    assert checked >= 170 and excluded <= 7, (checked, excluded)
+    # the clamped colour channel: exactly zero, from both sides
+    sh_g = grads["sh"].reshape(-1, K, 3)
+    assert np.all(sh_g[66, :, 1] == 0.0) and np.all(sh_g[66, :, 0] != 0.0)

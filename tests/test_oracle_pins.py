@@ -507,3 +507,38 @@ def test_thresholds_at_equality():
     below = np.nextafter(np.float32(z), np.float32(-np.inf))
     wall, _ = oracle.render(sc2, cam, bg, depth=np.full((H, W), below, np.float32))
     assert np.all(wall["alpha"] == 0.0)
+
+
+def test_negative_colour_sum_renders_black_closed_form():
+    """Reading S2's clamp rgb = max(0, sum + 0.5): an SH0 Gaussian whose stored DC gives a
+    negative sum in one channel draws that channel as a black splat, bg (1 - alpha), with the
+    other channels at their closed form; the adjoint passes no gradient to the clamped
+    channel's coefficient and the textbook c alpha to the others (dC/dc = alpha per pixel)."""
+    d, sig3, logit = 4.0, 0.05, 1.2
+    W, H = 48, 40
+    cam = synth.look_at((0, 0, d), (0, 0, 0), W, H, 60.0)
+    colour = (0.7, -0.35, 0.2)
+    sc = _one_gaussian_scene((0, 0, 0), sig3, (1, 0, 0, 0), logit, colour)
+    prep = oracle.preprocess(sc, cam)
+    s_true = math.exp(float(np.float32(math.log(sig3))))
+    var = (cam.fx * s_true / d) ** 2 + DIL
+    o = 1 / (1 + math.exp(-float(np.float32(logit))))
+    ys, xs = np.mgrid[0:H, 0:W]
+    rho2 = (xs + 0.5 - W / 2) ** 2 + (ys + 0.5 - H / 2) ** 2
+    a = np.minimum(float(np.float32(0.99)), o * np.exp(-rho2 / (2 * var)))
+    a = np.where((rho2 / var <= 9.0) & (a >= np.float32(1 / 255)), a, 0.0)
+    c = np.maximum(_dc_colour(sc, 0), 0.0)
+    assert c[1] == 0.0 and c[0] > 0 and c[2] > 0
+    bg = np.array([0.3, 0.6, 0.9])
+    expect = c[:, None, None] * a + bg[:, None, None] * (1 - a)
+    np.testing.assert_allclose(prep["rgb"][0], c, atol=1e-15)
+    for img in (oracle.render_bruteforce(prep, W, H, bg), oracle.render_tiled(prep, W, H, bg)):
+        np.testing.assert_allclose(img["rgb"], expect, atol=1e-12)
+        np.testing.assert_allclose(img["rgb"][1], bg[1] * (1 - a), atol=1e-12)
+    # L = sum over the image of channel ch: dL/dsh_ch = Y00 * sum alpha, or 0 where clamped
+    for ch in range(3):
+        gC = np.zeros((3, H, W))
+        gC[ch] = 1.0
+        g = oracle.adjoint(sc, cam, gC, np.zeros((H, W)), bg)
+        want = 0.0 if ch == 1 else Y00 * a.sum()
+        assert abs(g["sh"][0, 0, ch] - want) <= 1e-12 * max(1.0, abs(want)), (ch, g["sh"][0, 0, ch], want)
