@@ -44,17 +44,11 @@ STAGES = ["clear", "preprocess", "duplicate", "sort_histogram", "sort_passes", "
 # "sort_histogram"/"sort_passes" = the stable sort by tile id of 4-byte keys
 STAGES_DF = ["clear", "preprocess", "depth_sort_and_emit", "tile_sort_histogram", "tile_sort_passes", "ranges",
              "composite"]
-# sort_mode 2 (depth sort + counting binning): stage 3 = binning counts, scans and ranges,
-# stage 4 = binning emission (each Gaussian index written to its slot)
-STAGES_BIN = ["clear", "preprocess", "depth_sort", "bin_count_scan", "bin_emit", "ranges", "composite"]
 # sort_mode 1 with the counts-first tile sort (16-bit tile keys): stage 2 = compaction, depth sort
 # and emission in depth order; stage 3 = per-tile counts (histograms, ranges); stage 4 = the tile
 # passes; no ranges stage
 STAGES_FUSED = ["clear", "preprocess", "depth_sort_and_emit", "tile_counts", "tile_sort_passes", "ranges",
                 "composite"]
-# sort_mode 3 (tile first): stage 2 = per-CTA tile counts and the scan; stage 3 = emission into the
-# tiles; stage 4 = the per-tile sorts in shared memory (and merges of the largest tiles)
-STAGES_TF = ["clear", "preprocess", "tile_counts", "tile_emit", "tile_sorts", "ranges", "composite"]
 
 
 def _peaks():
@@ -288,9 +282,7 @@ def run_ours(args):
     stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
     update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
     fused = ws.layout().key_bytes == 2
-    tile_first = ws.layout().sort_mode == 3
-    names = (STAGES_TF if tile_first else STAGES_FUSED if fused
-             else {0: STAGES, 1: STAGES_DF, 2: STAGES_BIN}[args.sort_mode])
+    names = STAGES_FUSED if fused else {0: STAGES, 1: STAGES_DF}[args.sort_mode]
     passes = npass.value
 
     # keys per frame averaged over the views used
@@ -314,7 +306,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant stage ----
     peaks = _peaks()
-    cands = ("preprocess", "sort_passes", "composite") if args.sort_mode != 2 else ("preprocess", "composite")
+    cands = ("preprocess", "sort_passes", "composite")
     dom = max(cands, key=lambda s: stage_ms[s])
     sh_k = (desc["sh_degree"] + 1) ** 2
     # means + logit read, depth + rect + count written: 32 B each; quaternion + log-scales: 28 B
@@ -327,13 +319,7 @@ def run_ours(args):
     # 2 B key + 4 B value per copy, the last reads those and writes the 4 B value
     # 16-bit keys: every pass reads 2 + 4 B per copy and writes 2 + 4 B, the last only the 4 B value
     tile_bytes = (M * (12 * passes - 2)) if fused else M * (24.0 if args.sort_mode == 0 else 16.0) * passes
-    if tile_first:   # per-tile sorts: 8 B key read, 4 B index written per copy
-        tile_bytes = M * 12.0
-    if dom == "sort_passes" and tile_first:
-        launch_ms = stage_ms["sort_passes"]
-        algo = tile_bytes
-        unit_note = "per-tile sorts in shared memory: 8 B (depth, index) key read, 4 B index written per copy"
-    elif dom == "sort_passes" and fused:
+    if dom == "sort_passes" and fused:
         launch_ms = stage_ms["sort_passes"] / passes
         algo = tile_bytes / passes
         unit_note = ("mean over the tile passes: 2 B key + 4 B value read and written per copy, "
@@ -401,10 +387,7 @@ def run_ours(args):
     # every HBM-bound stage against the copy peak (the spec bar is >= 60% for preprocess and sort)
     hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
                                      achieved_gbs=round(bytes_pre / (stage_ms["preprocess"] * 1e-3) / 1e9, 1))}
-    if tile_first:
-        hbm_stages["tile_sorts"] = dict(bytes=int(tile_bytes), ms=round(stage_ms["sort_passes"], 4),
-                                        achieved_gbs=round(tile_bytes / (stage_ms["sort_passes"] * 1e-3) / 1e9, 1))
-    elif args.sort_mode != 2 and passes > 0:
+    if passes > 0:
         key = "tile_sort_pass"
         b_st = tile_bytes / passes
         ms_st = stage_ms["sort_passes"] / passes
@@ -424,7 +407,7 @@ def run_ours(args):
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
                 clocks=clk_summary, e2e=e2e,
-                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes, 2: 11 + kDP, 3: 16}[args.sort_mode]
+                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes}[args.sort_mode]
                                  + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)
                                  + (args.steps if dbuf is not None else 0)),
                 roofline=roof, hbm_stages=hbm_stages,
@@ -432,7 +415,7 @@ def run_ours(args):
                 keys_per_frame=int(M), visible_per_frame=int(n_vis), sort_passes=passes,
                 dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),
                 sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]
-                                           + (stage_ms["duplicate"] if args.sort_mode == 2 else 0.0)) * 1e3, 1),
+                                           ) * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
     if rank == 0 and world == 1 and not args.no_cpu and not packed:
         line["cpu_baseline"] = cpu_baseline(args.workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
@@ -772,7 +755,7 @@ def main():
     ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch", "multi"])
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1],
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
                          "2: depth sort then counting binning (default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

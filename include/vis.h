@@ -86,14 +86,7 @@ typedef struct {
  *                  tiles the per-tile counts (hence ranges and digit histograms) come
  *                  first, the tile keys are 16-bit and the last pass writes only the
  *                  Gaussian indices;
- *              2 = depth first, then a stable counting binning into tiles (no tile keys;
- *                  up to 29056 tiles, beyond that mode 1 is used);
- *              3 = tile first: each copy is placed in its tile's range (per-tile counts
- *                  first), then every tile's (depth bits << 32 | index) keys are sorted in
- *                  shared memory (bitonic network; tiles above 16384 copies as runs that are
- *                  then merged). No global sort. Up to 51200 tiles (beyond that mode 1 is
- *                  used) and 16384 << 8 copies per tile (VIS_ERR_UNSUPPORTED beyond).
- *              All give the same order bit for bit; 1 moves about a quarter of the bytes
+ *              Both give the same order bit for bit; 1 moves about a quarter of the bytes
  *              of 0.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
  *              thread (default 1); the image does not depend on it.
@@ -106,6 +99,14 @@ typedef struct {
  *              top and bottom rows narrowed to the tiles whose band of pixel centres meets
  *              that region. The image does not depend on it; 1 lists ~40% fewer (tile,
  *              splat) pairs than 0, and 2 ~12% fewer than 1.
+ *  spin_limit  how many times a sort partition may poll a predecessor's unpublished
+ *              look-back word before it gives up (0 = the default, 4194304; at most
+ *              2^30). A wait that runs out records VIS_ERR_TIMEOUT in the workspace
+ *              (returned by vis_check), publishes its own counts so that no other
+ *              partition waits on it, and the render's later kernels skip their work and
+ *              write NaN images; the workspace stays usable for the next render. The
+ *              default only bounds a wait that can never end; small values exist to
+ *              exercise that error path.
  * A splat reaches a pixel only inside its 3-sigma ellipse (Mahalanobis q <= 9). */
 typedef struct {
     int tile;
@@ -118,6 +119,7 @@ typedef struct {
     int pixels_per_thread;
     int tile_extent;
     int collect_stats;
+    int spin_limit;
 } vis_render_opts;
 
 VIS_API void vis_default_opts(vis_render_opts* opts);
@@ -147,19 +149,17 @@ typedef struct {
     size_t off_tfinal;       /* float[H*W] final transmittance */
     size_t off_last;         /* int32[H*W] 1 + position, in the sorted key list, of the last composited splat (0 if none) */
     size_t off_g2;           /* float[n][9] screen-space gradients (backward scratch) */
-    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0) or (depth bits << 32) |
-                                index (sort_mode 3); 4: tile id (sort_mode 1 beyond 51200 tiles);
-                                2: 16-bit tile id (sort_mode 1); 0: none (2) */
+    int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1
+                                beyond 51200 tiles); 2: 16-bit tile id (sort_mode 1) */
     int sort_mode;
 } vis_ws_layout;
 
 /* Device-written status block at workspace offset off_ctrl (= 0). */
 typedef struct {
     uint32_t num_keys;       /* (tile, splat) pairs listed by the last render (may exceed capacity) */
-    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout, bit 2: a tile
-                                beyond sort_mode 3's merge limit */
+    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout */
     uint32_t internal[16];   /* sort partition tickets */
-    uint32_t num_visible;    /* Gaussians that survived culling (sort_mode 1, 2) */
+    uint32_t num_visible;    /* Gaussians that survived culling (sort_mode 1) */
     uint32_t pad0;
     uint64_t pair_tests;     /* with collect_stats: (pixel, splat) pairs the compositor tested */
     uint64_t hits;           /* with collect_stats: pairs it composited */
@@ -227,8 +227,7 @@ VIS_API vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, i
                       const vis_render_opts* opts, void* stream);
 
 /* Synchronise `stream`, read the status block of `ws`, and return VIS_OK,
- * VIS_ERR_CAPACITY, VIS_ERR_TIMEOUT or (sort_mode 3, a tile beyond its merge limit)
- * VIS_ERR_UNSUPPORTED. num_keys (host, may be NULL) receives the
+ * VIS_ERR_CAPACITY or VIS_ERR_TIMEOUT. num_keys (host, may be NULL) receives the
  * number of keys the last render produced (the capacity a retry needs). */
 VIS_API vis_status vis_check(const void* ws, void* stream, int64_t* num_keys);
 
@@ -382,14 +381,22 @@ VIS_API vis_status vis_dynamic_update(const float* means0, const float* velocity
  *  key_bits   1..64
  * The first call on a device, with that device current, looks up the array's
  * device address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture. Every call shares the one array (it is cleared where needed
- * at the start of each call), so calls whose GPU work overlaps -- on different
- * streams, or from different threads -- race and must be serialised by the caller. */
+ * any stream capture; a device reset (cudaDeviceReset) after that first call is not
+ * supported, since the cached address may no longer be the array's. Every call shares
+ * the one array (it is cleared where needed at the start of each call), so calls whose
+ * GPU work overlaps -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.
+ * A device-side error of the sort (a look-back wait that ran out, VIS_ERR_TIMEOUT: the
+ * outputs are then invalid) is kept in the array's status word until the next call;
+ * vis_sort_noalloc_check(stream) synchronises `stream` and returns it (it allocates
+ * nothing either). The same error of vis_sort_pairs is read with vis_check(ws, ...),
+ * its workspace starting with the same status block. */
 #define VIS_SORT_NOALLOC_MAX_KEYS (1 << 20)
 #define VIS_SORT_NOALLOC_SCRATCH_BYTES 16785664
 VIS_API vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
                                           uint64_t* keys_out, uint32_t* vals_out, int64_t m,
                                           int key_bits, void* stream);
+VIS_API vis_status vis_sort_noalloc_check(void* stream);
 
 /* Per-stage timing of vis_render (tracing; the paper times its frame by stages,
  * Table 1 "Sort" vs "Prep.+Draw"). Between vis_profile_begin and vis_profile_end,

@@ -40,7 +40,7 @@ class vis_render_opts(C.Structure):
     _fields_ = [("tile", C.c_int), ("digit_bits", C.c_int), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_stop", C.c_float),
                 ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int), ("tile_extent", C.c_int),
-                ("collect_stats", C.c_int)]
+                ("collect_stats", C.c_int), ("spin_limit", C.c_int)]
 
 
 class vis_scene_grads(C.Structure):
@@ -102,6 +102,7 @@ def lib():
             "vis_sort_workspace_size": (C.c_int, [C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
             "vis_sort_pairs": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P, C.c_size_t, _P]),
             "vis_sort_pairs_noalloc": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int, _P]),
+            "vis_sort_noalloc_check": (C.c_int, [_P]),
             "vis_profile_begin": (C.c_int, []),
             "vis_batch_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
             "vis_batch_destroy": (None, [_P]),

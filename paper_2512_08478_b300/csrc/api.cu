@@ -74,12 +74,14 @@ vis_status check_opts(const vis_render_opts& o) {
         return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0, 1 or 2 (got %d)", o.tile_extent);
     if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
         return fail(VIS_ERR_INVALID_ARG, "pixels_per_thread must be 1 or 2 (got %d)", o.pixels_per_thread);
-    if (o.sort_mode < vis::kSortTileDepth || o.sort_mode > vis::kSortTileFirst)
-        return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0, 1, 2 or 3 (got %d)", o.sort_mode);
+    if (o.sort_mode != vis::kSortTileDepth && o.sort_mode != vis::kSortDepthFirst)
+        return fail(VIS_ERR_INVALID_ARG, "sort_mode must be 0 or 1 (got %d)", o.sort_mode);
     if (!(o.dilation >= 0.f) || !std::isfinite(o.dilation)) return fail(VIS_ERR_INVALID_ARG, "dilation must be finite and >= 0");
     if (!(o.alpha_min > 0.f && o.alpha_min < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_min must be in (0, 1)");
     if (!(o.alpha_max > 0.f && o.alpha_max < 1.f)) return fail(VIS_ERR_INVALID_ARG, "alpha_max must be in (0, 1)");
     if (!(o.t_stop >= 0.f && o.t_stop < 1.f)) return fail(VIS_ERR_INVALID_ARG, "t_stop must be in [0, 1)");
+    if (o.spin_limit < 0 || (uint32_t)o.spin_limit > vis::kMaxSpinLimit)
+        return fail(VIS_ERR_INVALID_ARG, "spin_limit must be in [0, 2^30] (got %d)", o.spin_limit);
     return VIS_OK;
 }
 
@@ -122,7 +124,7 @@ vis::PrepParams make_params(const vis_scene* s, const vis_camera* c, int W, int 
     p.dilation = o.dilation; p.alpha_min = o.alpha_min;
     p.wscale = (float)std::sqrt(0.5 / std::log(2.0));
     p.tight_extent = o.tile_extent;
-    p.count_survivors = L.mode == vis::kSortDepthFirst || L.mode == vis::kSortDepthBin;
+    p.count_survivors = L.mode == vis::kSortDepthFirst;
     vis::sh_constants(p.shc);
     return p;
 }
@@ -268,20 +270,15 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.tiles_x = (W + tile - 1) / tile;
     L.tiles_y = (H + tile - 1) / tile;
     L.ntiles = (int64_t)L.tiles_x * L.tiles_y;
-    // the counting binning and the tile-first ordering need per-tile counters in shared memory
-    if (mode == kSortDepthBin && L.ntiles > kBinMaxTiles4) mode = kSortDepthFirst;
-    if (mode == kSortTileFirst && L.ntiles > kTileFusedMaxTiles) mode = kSortDepthFirst;
-    const bool tf = mode == kSortTileFirst;
     L.mode = mode;
     L.tile_bits = ceil_log2(L.ntiles);
     L.cap = cap;
     L.prep_blocks = (n + kPrepThreads - 1) / kPrepThreads;
-    const bool df = mode == kSortDepthFirst || mode == kSortDepthBin;
-    const bool bin = mode == kSortDepthBin;
+    const bool df = mode == kSortDepthFirst;
     L.key_bits = df ? L.tile_bits : 32 + L.tile_bits;
-    L.passes = bin ? 0 : (L.key_bits + kRadixBits - 1) / kRadixBits;
-    L.key_bytes = bin ? 0 : (df ? 4 : 8);
-    L.sort_parts = bin ? 0 : (df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap));
+    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
+    L.key_bytes = df ? 4 : 8;
+    L.sort_parts = df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap);
     L.sorted_buffer = L.passes & 1;
     // depth-first mode: counts-first tile sort of 16-bit tile keys when the per-tile counters
     // fit in shared memory; it runs at least one pass (the last writes values only)
@@ -291,18 +288,6 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
         L.key_bytes = 2;
         L.sort_parts = sort_parts<uint16_t>(cap);
         L.sorted_buffer = L.passes & 1;
-    }
-    if (tf) {   // no radix passes; 64-bit (depth, index) keys sorted per tile, indices in buffer 0
-        L.passes = 0;
-        L.key_bytes = 8;
-        L.sort_parts = 0;
-        L.sorted_buffer = 0;
-        L.tf_grid = tf_grid(n, L.ntiles);
-        L.tf_chunk = (n + L.tf_grid - 1) / L.tf_grid;
-    }
-    if (bin) {
-        L.bin_chunk = bin_chunk(n);
-        L.bin_chunks = (n + L.bin_chunk - 1) / L.bin_chunk;
     }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -314,7 +299,6 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * kRadix));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
-    if (tf) L.off_tf_total = take(sizeof(uint32_t) * (size_t)L.ntiles);
     L.zero_end = off;
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
     L.off_depth = take(sizeof(float) * (size_t)n);
@@ -329,28 +313,10 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
         for (int b = 0; b < 2; ++b) L.off_dvals[b] = take(sizeof(uint32_t) * (size_t)n);
     }
 
-    if (tf) {
-        L.off_tf_within = take(sizeof(uint32_t) * (size_t)L.tf_grid * (size_t)L.ntiles);
-        L.off_tf_start = take(sizeof(uint32_t) * (size_t)L.ntiles);
-        L.off_tf_lists = take(sizeof(uint32_t) * (size_t)(5 * L.ntiles + cap / 16384 + 1));
-        L.off_keys[0] = take(sizeof(uint64_t) * (size_t)cap);   // (depth, index) keys
-        L.off_keys[1] = take(sizeof(uint64_t) * (size_t)cap);   // merge scratch of the largest tiles
-        L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
-        L.off_vals[1] = L.off_vals[0];
-    } else if (bin) {
-        L.off_counts = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
-        L.off_chunk_base = take(sizeof(uint32_t) * (size_t)L.bin_chunks * L.ntiles);
-        L.off_totals = take(sizeof(uint32_t) * (size_t)L.ntiles);
-        L.off_tile_start = take(sizeof(uint32_t) * (size_t)L.ntiles);
-        L.off_keys[0] = L.off_keys[1] = 0;
-        L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
-        L.off_vals[1] = L.off_vals[0];
-    } else {
-        L.off_keys[0] = take((size_t)L.key_bytes * (size_t)cap);
-        L.off_keys[1] = take((size_t)L.key_bytes * (size_t)cap);
-        L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
-        L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
-    }
+    L.off_keys[0] = take((size_t)L.key_bytes * (size_t)cap);
+    L.off_keys[1] = take((size_t)L.key_bytes * (size_t)cap);
+    L.off_vals[0] = take(sizeof(uint32_t) * (size_t)cap);
+    L.off_vals[1] = take(sizeof(uint32_t) * (size_t)cap);
     L.off_tfinal = take(sizeof(float) * (size_t)W * H);
     L.off_zmax = take(sizeof(float) * (size_t)L.ntiles);
     L.off_last = take(sizeof(int32_t) * (size_t)W * H);
@@ -385,6 +351,7 @@ void vis_default_opts(vis_render_opts* o) {
     o->pixels_per_thread = 1;
     o->tile_extent = 2;
     o->collect_stats = 0;
+    o->spin_limit = 0;
 }
 
 const char* vis_last_error(void) { return g_err.c_str(); }
@@ -531,6 +498,7 @@ static vis_status prepare(const vis_scene_t* scenes, int n_scenes, bool padded, 
     const int64_t cap = vis::capacity_for(slots, W, H, o->tile, o->sort_mode, ws_bytes);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
     *L = vis::make_layout(slots, W, H, o->tile, cap, o->sort_mode);
+    L->spin_limit = o->spin_limit > 0 ? (uint32_t)o->spin_limit : vis::kSpinLimit;
     return VIS_OK;
 }
 
@@ -572,15 +540,7 @@ static vis_status render_impl(const vis_scene_t* scenes, const float* models, in
         vis::launch_preprocess(p, L, w, stream);
     }
     prof_mark(2, stream);
-    if (L.mode == vis::kSortDepthBin) {
-        vis::launch_depth_sort(L, w, stream);
-        prof_mark(3, stream);
-        vis::launch_tile_bin(L, w, stream, g_prof.on ? &prof_mark : nullptr);
-        prof_mark(5, stream);
-    } else if (L.mode == vis::kSortTileFirst) {
-        vis::launch_tile_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
-        prof_mark(5, stream);
-    } else if (L.mode == vis::kSortDepthFirst) {
+    if (L.mode == vis::kSortDepthFirst) {
         vis::launch_depth_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
         prof_mark(5, stream);
         if (!L.tile_fused) vis::launch_ranges32(L, w, stream);   // the counts-first tile sort wrote them
@@ -653,9 +613,6 @@ vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
     if (c.error & vis::kErrCapacity)
         return fail(VIS_ERR_CAPACITY, "%u keys exceed the workspace capacity", c.num_keys);
     if (c.error & vis::kErrTimeout) return fail(VIS_ERR_TIMEOUT, "a device spin wait timed out");
-    if (c.error & vis::kErrTileOverflow)
-        return fail(VIS_ERR_UNSUPPORTED, "a tile holds more copies than sort_mode 3 merges (16384 << %d)",
-                    vis::kTfMergeRounds);
     g_err.clear();
     return VIS_OK;
 }

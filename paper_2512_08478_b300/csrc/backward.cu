@@ -60,7 +60,8 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                           const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
                           float* __restrict__ g2, const float* __restrict__ depth,
-                          const float* __restrict__ zlim) {
+                          const float* __restrict__ zlim, const Ctrl* __restrict__ ctrl) {
+    if (ctrl->error) return;   // the forward produced no valid lists: leave the gradients at zero
     constexpr int NT = TILE * TILE;
     constexpr int NW = NT / 32;               // warps; each owns an 8 x 4 pixel block
     constexpr int BX = TILE / 8, BH = 4;
@@ -404,10 +405,11 @@ void launch_composite_backward(const Layout& L, char* ws, const float bg[3], flo
     const int blocks = (int)L.ntiles;
     const QScale qs = q_scale();
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+    const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(ws + L.off_ctrl);
 #define VIS_LAUNCH_BWD_D(TS, DT)                                                                           \
     composite_backward_kernel<TS, DT><<<blocks, TS * TS, 0, stream>>>(                                     \
         ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut,        \
-        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim)
+        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl)
 #define VIS_LAUNCH_BWD(TS)                       \
     do {                                         \
         if (zlim) VIS_LAUNCH_BWD_D(TS, true);    \

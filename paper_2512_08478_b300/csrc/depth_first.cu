@@ -51,15 +51,18 @@ compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ 
     }
 }
 
-// Block sums of tiles touched, in depth order.
+// Block sums of tiles touched, in depth order. After a failed depth sort (a look-back
+// that timed out) the sorted indices are not trustworthy: every block sum is then zero and
+// nothing is read through them.
 __global__ void __launch_bounds__(kPrepThreads)
-depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched,
-                 const uint32_t* __restrict__ num_visible, uint32_t* __restrict__ bsum) {
+depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched, int64_t n,
+                 const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ bsum) {
     pdl_entry();
     __shared__ uint32_t ws[kPrepThreads / 32];
-    const int64_t nv = *num_visible;
+    const int64_t nv = ctrl->error ? 0 : min((int64_t)ctrl->num_visible, n);
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    uint32_t c = (j < nv) ? touched[dvals[j]] : 0u;
+    const uint32_t g = (j < nv) ? dvals[j] : 0xffffffffu;
+    uint32_t c = (g < (uint64_t)n) ? touched[g] : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
@@ -74,11 +77,11 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
 // KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles
 template <typename KT>
 __global__ void __launch_bounds__(kPrepThreads)
-emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
-           const uint32_t* __restrict__ num_visible, const uint32_t* __restrict__ boff, int tiles_x,
+emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, int64_t n,
+           const uint32_t* __restrict__ boff, int tiles_x,
            const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     pdl_entry();
-    if (ctrl->error & kErrCapacity) return;
+    if (ctrl->error) return;   // capacity exceeded, or a sort that timed out
     // per splat slot: start of its copies in the warp's run, and its footprint unrolled into
     // row segments: a = (index, first top-row tile, top width, end of the middle copies),
     // b = (first middle tile, box width, first bottom-row tile, 0)
@@ -86,12 +89,12 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect,
     __shared__ uint4 s_a[kPrepThreads], s_b[kPrepThreads];
     __shared__ uint32_t warp_tot[kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nv = *num_visible;
+    const int64_t nv = min((int64_t)ctrl->num_visible, n);
     const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
     uint32_t cnt = 0;
     uint4 sa = make_uint4(0, 0, 0, 0), sb = make_uint4(0, 1, 0, 0);
-    if (j < nv) {   // one gather per splat
-        const uint32_t g = dvals[j];
+    const uint32_t g = j < nv ? dvals[j] : 0xffffffffu;
+    if (g < (uint64_t)n) {   // one gather per splat
         const Footprint f = fp_unpack(rect[g]);
         cnt = fp_count(f);
         if (cnt > 0) {
@@ -180,7 +183,7 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     // 2. sort by depth (4 passes; the result lands in buffer 0)
     launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
                                   ctrl->part_counter, &ctrl->error, stream, nullptr, 0, kRadixBits,
-                                  depth_sort_kpt(L.n));
+                                  depth_sort_kpt(L.n), L.spin_limit);
 }
 
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
@@ -194,15 +197,15 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // 3. tile copies in depth order
     uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
-    launch_k(true, depth_touch_sums, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0, touched,
-             (const uint32_t*)&ctrl->num_visible, bsum2);
+    launch_k(true, depth_touch_sums, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0, touched, L.n,
+             (const Ctrl*)ctrl, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
     if (L.tile_fused) {
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
         launch_k(true, emit_tiles<uint16_t>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
-                 reinterpret_cast<const uint4*>(ws + L.off_rect), (const uint32_t*)&ctrl->num_visible,
-                 (const uint32_t*)boff2, L.tiles_x, (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
+                 reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
+                 (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
                  reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
         if (mark) mark(mark_index, stream);
         launch_tile_counts(L, ws, stream);
@@ -216,7 +219,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
     emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, reinterpret_cast<const uint4*>(ws + L.off_rect),
-                                                      &ctrl->num_visible, boff2, L.tiles_x, ctrl, k0, v0);
+                                                                L.n, boff2, L.tiles_x, ctrl, k0, v0);
     if (mark) mark(mark_index, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer
     const int tp = L.passes;
@@ -226,7 +229,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* vb = L.sorted_buffer ? v0 : v1;
     launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp, hist + kMaxPasses * kRadix,
                                   lb + L.lookback_words_depth, ctrl->part_counter + kMaxPasses, &ctrl->error, stream,
-                                  mark, mark_index + 1, L.tile_bits - kRadixBits * (tp - 1));
+                                  mark, mark_index + 1, L.tile_bits - kRadixBits * (tp - 1), 0, L.spin_limit);
     (void)sms;
 }
 

@@ -115,7 +115,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Decoupled look-back, split in two so that its loads overlap the ranking:
 // lookback_issue reads the window of WIN predecessors of partition `part` for digit d;
 // lookback_resolve consumes it in order up to the first inclusive prefix, polling a word
-// not yet published at most kSpinLimit times, continues one predecessor at a time past
+// not yet published at most `limit` times, continues one predecessor at a time past
 // the window if needed, publishes this partition's inclusive prefix and returns the
 // count of d over all preceding partitions (*timed_out set if a poll gave up).
 template <int WIN>
@@ -127,10 +127,11 @@ __device__ __forceinline__ void lookback_issue(const uint32_t* lookback, uint32_
         v[i] = (q0 - i >= 0) ? ld_relaxed(&lookback[(size_t)(q0 - i) * kRadix + d]) : kFlagInc;
 }
 
-__device__ __forceinline__ bool lookback_wait(const uint32_t* lookback, int64_t q, uint32_t d, uint32_t* w) {
+__device__ __forceinline__ bool lookback_wait(const uint32_t* lookback, int64_t q, uint32_t d, uint32_t* w,
+                                              uint32_t limit) {
     uint32_t spins = 0;
     while ((*w & ~kCountMask) == 0) {
-        if (++spins > kSpinLimit) return false;
+        if (++spins > limit) return false;
         if (spins > 8) __nanosleep(32);
         *w = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
     }
@@ -139,7 +140,8 @@ __device__ __forceinline__ bool lookback_wait(const uint32_t* lookback, int64_t 
 
 template <int WIN>
 __device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_t part, uint32_t d, uint32_t cnt,
-                                                     const uint32_t (&v)[WIN], bool* timed_out) {
+                                                     const uint32_t (&v)[WIN], uint32_t limit,
+                                                     bool* timed_out) {
     *timed_out = false;
     if (part == 0) return 0;
     uint32_t prefix = 0;
@@ -149,13 +151,13 @@ __device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_
     for (int i = 0; i < WIN; ++i) {
         if (found || to || q0 - i < 0) break;
         uint32_t w = v[i];
-        if (!lookback_wait(lookback, q0 - i, d, &w)) { to = true; break; }
+        if (!lookback_wait(lookback, q0 - i, d, &w, limit)) { to = true; break; }
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }
     for (int64_t q = q0 - WIN; !found && !to && q >= 0; --q) {
         uint32_t w = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
-        if (!lookback_wait(lookback, q, d, &w)) { to = true; break; }
+        if (!lookback_wait(lookback, q, d, &w, limit)) { to = true; break; }
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }

@@ -14,9 +14,10 @@
 //    offsets by decoupled look-back over the preceding partitions' published
 //    counts. The keys are then reordered by digit in shared memory and written out
 //    in runs, so global stores are coalesced within each digit run.
-//  - Spin waits on a predecessor are bounded (kSpinLimit polls); on expiry the
+//  - Spin waits on a predecessor are bounded (spin_limit polls); on expiry the
 //    CTA records kErrTimeout, publishes anyway so nobody waits on it, and writes
 //    nothing out of range (every destination is checked against the key count).
+#include <mutex>
 #include <type_traits>
 
 #include "onesweep.cuh"
@@ -77,7 +78,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
           const uint32_t* __restrict__ num_keys, int64_t cap, int shift, int nbits,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
-          uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error) {
+          uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error, uint32_t spin_limit) {
     pdl_entry();
     constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -159,7 +160,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 
     // ---- resolve the look-back: global digit offsets ----
     bool timed_out = false;
-    const uint32_t prefix = lookback_resolve<kLookbackWindow>(lookback, part, d, cnt, lbw, &timed_out);
+    const uint32_t prefix = lookback_resolve<kLookbackWindow>(lookback, part, d, cnt, lbw, spin_limit, &timed_out);
     if (timed_out) {
         atomicOr(error, kErrTimeout);
         S.bad = 1;
@@ -200,12 +201,14 @@ template <typename K, int KPT>
 static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                              uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                              uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                             StageMark mark, int mark_index, int last_bits) {
+                             StageMark mark, int mark_index, int last_bits, uint32_t spin_limit) {
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
+    static std::mutex attr_mu;
     const size_t smem = sizeof(SortSmem<K, KPT>);
-    if (once_per_device(attr_dev)) {
-        cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+    set_up_per_device(attr_dev, attr_mu, [&] {
+        return cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+               cudaSuccess;
+    });
     const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
@@ -221,7 +224,7 @@ static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < kRadixBits) ? last_bits : kRadixBits;
         launch_k(true, sort_pass<K, KPT>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
                  (const uint32_t*)num_keys_dev, cap, kRadixBits * p, nbits, (const uint32_t*)(hist + p * kRadix),
-                 lookback + (size_t)p * parts * kRadix, &part_counters[p], error);
+                 lookback + (size_t)p * parts * kRadix, &part_counters[p], error, spin_limit);
         src_k = dk;
         src_v = dv;
     }
@@ -232,15 +235,15 @@ template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark, int mark_index, int last_bits, int kpt) {
+                         StageMark mark, int mark_index, int last_bits, int kpt, uint32_t spin_limit) {
     if (cap <= 0 || passes <= 0) return;
     if (std::is_same<K, uint32_t>::value && kpt == 8)
         sort_generic_kpt<K, 8>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev, passes, hist,
-                               lookback, part_counters, error, stream, mark, mark_index, last_bits);
+                               lookback, part_counters, error, stream, mark, mark_index, last_bits, spin_limit);
     else
         sort_generic_kpt<K, SortKPT<K>::value>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev,
                                                passes, hist, lookback, part_counters, error, stream, mark,
-                                               mark_index, last_bits);
+                                               mark_index, last_bits, spin_limit);
 }
 
 // One pass of sort_pass over m <= cap keys (read from *num_keys_dev) with digit
@@ -248,29 +251,32 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
 template <typename K>
 void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
                       const uint32_t* num_keys_dev, int shift, int nbits, const uint32_t* hist_pass,
-                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream) {
+                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream,
+                      uint32_t spin_limit) {
     if (cap <= 0) return;
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
+    static std::mutex attr_mu;
     constexpr int KPT = SortKPT<K>::value;
     const size_t smem = sizeof(SortSmem<K, KPT>);
-    if (once_per_device(attr_dev)) {
-        cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+    set_up_per_device(attr_dev, attr_mu, [&] {
+        return cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+               cudaSuccess;
+    });
     launch_k(true, sort_pass<K, KPT>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
              vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass, lookback,
-             part_counter, error);
+             part_counter, error, spin_limit);
 }
 
 template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint16_t*, uint32_t*, int64_t,
                                          const uint32_t*, int, int, const uint32_t*, uint32_t*, uint32_t*,
-                                         uint32_t*, cudaStream_t);
+                                         uint32_t*, cudaStream_t, uint32_t);
 
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t);
 template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);
@@ -286,7 +292,8 @@ void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark,
     launch_sort_generic<uint64_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, L.passes,
                                   reinterpret_cast<uint32_t*>(ws + L.off_hist),
                                   reinterpret_cast<uint32_t*>(ws + L.off_lookback), ctrl->part_counter,
-                                  &ctrl->error, stream, mark, mark_index, L.key_bits - kRadixBits * (L.passes - 1));
+                                  &ctrl->error, stream, mark, mark_index, L.key_bits - kRadixBits * (L.passes - 1), 0,
+                                  L.spin_limit);
 }
 
 }  // namespace vis

@@ -14,7 +14,10 @@
 // VIS_SORT_NOALLOC_SCRATCH_BYTES of it until the process exits, and every call
 // shares it. In host code the array's name is only a host-side stand-in, never a
 // device address: the first call on each device (with that device current) looks
-// the real address up with cudaGetSymbolAddress and caches it per device.
+// the real address up with cudaGetSymbolAddress and caches it per device (so a device
+// reset after that first call is not supported: the module may be reloaded elsewhere).
+// A device-side error of the sort (a look-back wait that ran out) lands in the status
+// word at the start of the array; vis_sort_noalloc_check() reads it.
 #include <cstdio>
 #include <mutex>
 
@@ -91,12 +94,15 @@ extern "C" vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint
     if (st) return st;
     char* w = static_cast<char*>(base);
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-    // the array keeps the previous call's contents: clear status, histograms and look-back words
-    cudaError_t e = cudaMemsetAsync(w, 0, kOffKeys, stream);
+    // the array keeps the previous call's contents: clear the status block, the histograms and
+    // the look-back words that this sort's passes read (passes x partitions x digits)
+    const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
+    const size_t used = kOffLookback + sizeof(uint32_t) * (size_t)passes * (size_t)vis::sort_parts<uint64_t>(m) *
+                                           vis::kRadix;
+    cudaError_t e = cudaMemsetAsync(w, 0, used, stream);
     if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
     vis::Ctrl* ctrl = reinterpret_cast<vis::Ctrl*>(w + kOffCtrl);
     vis::launch_set_u32(&ctrl->num_keys, (uint32_t)m, stream);
-    const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
     vis::launch_sort_generic<uint64_t>(keys_in, vals_in, keys_out, vals_out,
                                        reinterpret_cast<uint64_t*>(w + kOffKeys), reinterpret_cast<uint32_t*>(w + kOffVals),
                                        m, &ctrl->num_keys, passes, reinterpret_cast<uint32_t*>(w + kOffHist),
@@ -104,6 +110,20 @@ extern "C" vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint
                                        stream, nullptr, 0, key_bits - vis::kRadixBits * (passes - 1));
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
+    vis::set_last_error("");
+    return VIS_OK;
+}
+
+extern "C" vis_status vis_sort_noalloc_check(void* stream_) {
+    void* base = nullptr;
+    vis_status st = scratch_address(&base);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_));
+    if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
+    uint32_t word[2] = {0, 0};   // num_keys, error (the head of the status block)
+    e = cudaMemcpy(word, base, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));
+    if (word[1] & vis::kErrTimeout) return fail_na(VIS_ERR_TIMEOUT, "a look-back wait of the sort timed out");
     vis::set_last_error("");
     return VIS_OK;
 }

@@ -147,15 +147,17 @@ static int sm_count_ts() {
 
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
-    if (once_per_device(attr_dev)) {
+    static std::mutex attr_mu;
+    set_up_per_device(attr_dev, attr_mu, [] {
         // the largest per-tile counter array of the fused path; the scan's rows are padded by one
         // word (at most 1024 rows at 16-pixel tiles) and it adds ~0.2 KB of static shared
         // memory, within the 227 KB a CTA may use
         const int most = (int)(sizeof(int) * kTileFusedMaxTiles);
-        cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             most + (int)sizeof(int) * 2048);
-    }
+        return cudaFuncSetAttribute(tile_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(tile_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    most + (int)sizeof(int) * 2048) == cudaSuccess;
+    });
     const size_t smem = sizeof(int) * (size_t)L.ntiles;
     int* gdiff = reinterpret_cast<int*>(ws + L.off_tdiff);
     const int64_t want = (L.n + 4095) / 4096;
@@ -182,13 +184,14 @@ void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
     const int low_bits = L.tile_bits < kRadixBits ? L.tile_bits : kRadixBits;
     if (L.passes == 1) {
         launch_sort_pass<uint16_t>(k0, v0, nullptr, v1, L.cap, &ctrl->num_keys, 0, low_bits, hist, lb,
-                                   &ctrl->part_counter[kMaxPasses], &ctrl->error, stream);
+                                   &ctrl->part_counter[kMaxPasses], &ctrl->error, stream, L.spin_limit);
         return;
     }
     launch_sort_pass<uint16_t>(k0, v0, k1, v1, L.cap, &ctrl->num_keys, 0, low_bits, hist, lb,
-                               &ctrl->part_counter[kMaxPasses], &ctrl->error, stream);
+                               &ctrl->part_counter[kMaxPasses], &ctrl->error, stream, L.spin_limit);
     launch_sort_pass<uint16_t>(k1, v1, nullptr, v0, L.cap, &ctrl->num_keys, kRadixBits, L.tile_bits - kRadixBits,
-                               hist + kRadix, lb + words, &ctrl->part_counter[kMaxPasses + 1], &ctrl->error, stream);
+                               hist + kRadix, lb + words, &ctrl->part_counter[kMaxPasses + 1], &ctrl->error, stream,
+                               L.spin_limit);
 }
 
 }  // namespace vis

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <atomic>
+#include <mutex>
 #include <stdint.h>
 
 #include <vector>
@@ -44,21 +45,16 @@ constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit c
 // ctrl->error bits
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
-constexpr uint32_t kErrTileOverflow = 4u;   // tile-first: a tile holds more copies than it can merge
 
-// Look-back spin limit, in polls (each poll ~ a few hundred ns with the backoff);
-// far beyond any legitimate wait, it only bounds a wait that can never end.
+// Default look-back spin limit, in polls (each poll ~ a few hundred ns with the backoff);
+// far beyond any legitimate wait, it only bounds a wait that can never end. A render's
+// vis_render_opts.spin_limit overrides it.
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kMaxSpinLimit = 1u << 30;
 
 // Sort modes (vis_render_opts.sort_mode)
 constexpr int kSortTileDepth = 0;   // one sort of 64-bit (tile << 32 | depth) keys
 constexpr int kSortDepthFirst = 1;  // depth sort of the surviving splats, then a tile sort
-constexpr int kSortDepthBin = 2;    // depth sort, then stable counting binning into tiles
-constexpr int kSortTileFirst = 3;   // copies placed in their tiles, each tile sorted in shared memory
-constexpr int kTfMergeRounds = 8;   // tile-first: runs of 16384 copies merged; tiles up to 16384 << 8
-// tile counts that the binning's per-warp shared-memory counters hold (8 or 4 warps)
-constexpr int kBinMaxTiles8 = 14528;
-constexpr int kBinMaxTiles4 = 29056;
 
 struct Layout {
     int mode = kSortTileDepth;
@@ -83,15 +79,10 @@ struct Layout {
     // depth-first mode with the counts-first tile sort of 16-bit keys (tile_sort.cu)
     bool tile_fused = false;
     size_t off_tdiff = 0;
-    // tile-first mode (tile_first.cu)
-    int64_t tf_grid = 0, tf_chunk = 0;
-    size_t off_tf_total = 0, off_tf_within = 0, off_tf_start = 0, off_tf_lists = 0;
-    // depth-bin mode only
-    int64_t bin_chunk = 0, bin_chunks = 0;
-    size_t off_counts = 0, off_chunk_base = 0, off_totals = 0, off_tile_start = 0;
     size_t zero_begin = 0, zero_end = 0;   // region cleared before every render
     size_t total = 0;
     int sorted_buffer = 0;
+    uint32_t spin_limit = kSpinLimit;      // polls a look-back wait may make (from the render options)
 };
 
 // Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`, sort mode.
@@ -107,8 +98,7 @@ struct Ctrl {
     uint32_t pad0;
     unsigned long long pair_tests;           // compositor statistics (collect_stats only)
     unsigned long long hits;
-    uint32_t tf_count[4];                    // tile-first: sizes of the per-class tile work lists
-    uint32_t reserved[36];
+    uint32_t reserved[40];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
 
@@ -232,14 +222,23 @@ inline void launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, 
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-// True the first time it is called for the current device with this flag word: function
-// attributes (cudaFuncSetAttribute) apply to the current device, so each device a process
-// renders on gets its own set-up. Thread safe.
-inline bool once_per_device(std::atomic<uint64_t>& done) {
+// Runs setup() for the current device unless it has already succeeded there (function
+// attributes such as cudaFuncSetAttribute apply to the current device only). The device's
+// bit in `done` is published only after setup() has returned true, and concurrent callers
+// wait on `mu`, so every launch that follows a return of this function on that device sees
+// the attributes set; a failed set-up is retried by the next call. Returns false if setup()
+// failed.
+template <typename F>
+inline bool set_up_per_device(std::atomic<uint64_t>& done, std::mutex& mu, F setup) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return setup();
     const uint64_t bit = 1ull << dev;
-    return !(done.fetch_or(bit) & bit);
+    if (done.load(std::memory_order_acquire) & bit) return true;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.load(std::memory_order_relaxed) & bit) return true;
+    if (!setup()) return false;
+    done.fetch_or(bit, std::memory_order_release);
+    return true;
 }
 
 // Launchers (host side, enqueue on `stream`).
@@ -263,9 +262,6 @@ void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uin
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
 // Compaction of the surviving splats and their stable sort by depth (result in dvals[0]).
 void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream);
-// Depth-bin mode: counting binning of the depth-sorted splats (mark(4) after the scans).
-void launch_tile_bin(const Layout& L, char* ws, cudaStream_t stream, StageMark mark);
-int64_t bin_chunk(int64_t n);
 void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
 // q' = q * log2(e)/2 units: the 3-sigma cut is q' <= 9 log2(e)/2
 struct QScale {
@@ -297,7 +293,8 @@ template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits, int kpt = 0);
+                         StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits, int kpt = 0,
+                         uint32_t spin_limit = kSpinLimit);
 
 // One sort_pass over the keys (digit (key >> shift) & 255 with nbits significant bits,
 // histogram hist_pass); keys_out may be null. `lookback` holds sort_parts<K>(cap) * kRadix
@@ -305,15 +302,12 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
 template <typename K>
 void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, uint32_t* vals_out, int64_t cap,
                       const uint32_t* num_keys_dev, int shift, int nbits, const uint32_t* hist_pass,
-                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream);
+                      uint32_t* lookback, uint32_t* part_counter, uint32_t* error, cudaStream_t stream,
+                      uint32_t spin_limit = kSpinLimit);
 
 // Counts-first tile sort of sort_mode 1 (tile_sort.cu): per-tile counts -> digit histograms
 // and ranges; then the passes over the 16-bit tile keys emitted in depth order.
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream);
-// Tile-first ordering (sort_mode 3): counts, emission into the tiles, per-tile sorts; marks
-// mark_index after the counts and mark_index + 1 after the emission.
-void launch_tile_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
-int64_t tf_grid(int64_t n, int64_t ntiles);
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream);
 
 void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,

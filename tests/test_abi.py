@@ -61,16 +61,8 @@ def test_workspace_queries_and_validation(L):
     wide = vis.vis_workspace_layout(10_000, 3840, 2160, 10 ** 9, vis.make_opts(sort_mode=1, tile=8))
     assert wide.key_bytes == 4 and wide.sort_passes == 3   # 129600 tiles (17 bits): counters exceed shared memory
     assert vis.vis_workspace_size(10_000, 256, 256, 100_000, vis.make_opts(sort_mode=1)) < b
-    bn = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=2))
-    assert bn.sort_mode == 2 and bn.key_bytes == 0
-    big = vis.vis_workspace_layout(10_000, 2048, 1024, 10 ** 9, vis.make_opts(sort_mode=2, tile=8))
-    assert big.sort_mode == 1     # 32768 tiles: too many for the binning's counters -> tile sort
     with pytest.raises(vis.VisError):
-        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=4))
-    tfl = vis.vis_workspace_layout(10_000, 1920, 1080, 10 ** 9, vis.make_opts(sort_mode=3))
-    assert tfl.sort_mode == 3 and tfl.key_bytes == 8 and tfl.sort_passes == 0 and tfl.sorted_buffer == 0
-    tfw = vis.vis_workspace_layout(10_000, 3840, 2160, 10 ** 9, vis.make_opts(sort_mode=3, tile=8))
-    assert tfw.sort_mode == 1     # 129600 tiles: too many for the per-tile counters -> depth first
+        vis.vis_workspace_size(10, 8, 8, 10, vis.make_opts(sort_mode=2))
     assert vis.vis_sort_workspace_size(0, 45) > 0
     with pytest.raises(vis.VisError):
         vis.vis_sort_workspace_size(10, 65)

@@ -35,7 +35,7 @@ def _concat(scenes):
                 sh_degree=scenes[0]["sh_degree"])
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(sort_mode=3), dict(tile=8),
+@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(tile=8),
                                   dict(pixels_per_thread=2)])
 def test_identity_models_equal_the_concatenated_scene(opts):
     """Ragged scene sizes (padding slots between the scenes): the image is the single
@@ -53,7 +53,7 @@ def test_identity_models_equal_the_concatenated_scene(opts):
     assert np.array_equal(a_rgb, e_rgb) and np.array_equal(a_alpha, e_alpha)
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(sort_mode=3), dict(tile=8)])
+@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(tile=8)])
 def test_multi_asset_workload_parity(opts):
     """The multi-asset workload (rigidly placed models, SH degrees 0..3) at 1/50 of its size."""
     scs, models, cam = synth.workload_multi(scale=0.02, W=480, H=270)

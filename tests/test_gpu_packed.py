@@ -25,7 +25,7 @@ def _packed_render(sc_np, cam, opts=None, bg=BG):
     return rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), dec, ps, ws
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(sort_mode=3), dict(tile=8),
+@pytest.mark.parametrize("opts", [dict(), dict(sort_mode=0), dict(tile=8),
                                   dict(pixels_per_thread=2)])
 def test_packed_small_workload_parity(opts):
     sc, cams = synth.workload_small()
