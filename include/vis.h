@@ -71,7 +71,12 @@ typedef struct {
 
 /* Render options. Pass NULL for the defaults, or fill with vis_default_opts().
  *  tile        tile edge in pixels: 8, 16 or 32 (default 16)
- *  digit_bits  radix digit width of the sort: 8 (default 8)
+ *  digit_bits  radix digit width of the depth-first order's 32-bit sorts (the depth sort
+ *              of the surviving splats, and the tile sort of grids beyond the 16-bit path or
+ *              of a batch): 8 (default), 10 or 11 bits per pass, i.e. 4, 4 or 3 passes over
+ *              a depth. Wider digits mean fewer passes, each publishing 2^digit_bits
+ *              look-back words per partition. sort_mode 0 and the 16-bit tile sort always
+ *              use 8-bit digits. The order, hence the image, does not depend on it.
  *  dilation    low-pass term added to the diagonal of S (px^2, default 0.3)
  *  alpha_min   splats with alpha < alpha_min are skipped; Gaussians whose opacity
  *              is below it are culled (default 1/255)

@@ -69,7 +69,8 @@ vis_render_opts resolve_opts(const vis_render_opts* o) {
 
 vis_status check_opts(const vis_render_opts& o) {
     if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(VIS_ERR_INVALID_ARG, "tile must be 8, 16 or 32 (got %d)", o.tile);
-    if (o.digit_bits != vis::kRadixBits) return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be %d (got %d)", vis::kRadixBits, o.digit_bits);
+    if (o.digit_bits != 8 && o.digit_bits != 10 && o.digit_bits != 11)
+        return fail(VIS_ERR_UNSUPPORTED, "digit_bits must be 8, 10 or 11 (got %d)", o.digit_bits);
     if (o.tile_extent < 0 || o.tile_extent > 2)
         return fail(VIS_ERR_INVALID_ARG, "tile_extent must be 0, 1 or 2 (got %d)", o.tile_extent);
     if (o.pixels_per_thread != 1 && o.pixels_per_thread != 2)
@@ -264,7 +265,7 @@ void sh_constants(float out[12]) {
     out[10] = out[11] = 0.f;
 }
 
-Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int digit_bits) {
     Layout L;
     L.n = n; L.W = W; L.H = H; L.tile = tile;
     L.tiles_x = (W + tile - 1) / tile;
@@ -275,28 +276,39 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     L.cap = cap;
     L.prep_blocks = (n + kPrepThreads - 1) / kPrepThreads;
     const bool df = mode == kSortDepthFirst;
+    // the digit width applies to the 32-bit sorts of the depth-first order (the depth sort
+    // and a tile sort of 32-bit ids); the 64-bit keys of sort_mode 0 and the 16-bit tile ids
+    // always take 8-bit digits
+    L.digit_bits = df ? digit_bits : kRadixBits;
+    L.depth_passes = df ? passes_for(32, L.digit_bits) : 0;
     L.key_bits = df ? L.tile_bits : 32 + L.tile_bits;
-    L.passes = (L.key_bits + kRadixBits - 1) / kRadixBits;
+    L.passes = passes_for(L.key_bits, L.digit_bits);
     L.key_bytes = df ? 4 : 8;
-    L.sort_parts = df ? sort_parts<uint32_t>(cap) : sort_parts<uint64_t>(cap);
+    L.sort_parts = df ? (cap + (int64_t)kSortThreads * 16 - 1) / ((int64_t)kSortThreads * 16)
+                      : sort_parts<uint64_t>(cap);
     L.sorted_buffer = L.passes & 1;
     // depth-first mode: counts-first tile sort of 16-bit tile keys when the per-tile counters
     // fit in shared memory; it runs at least one pass (the last writes values only)
     L.tile_fused = mode == kSortDepthFirst && L.ntiles <= kTileFusedMaxTiles;
+    int tile_digit = L.digit_bits;
     if (L.tile_fused) {
         L.passes = L.tile_bits > kRadixBits ? 2 : 1;
         L.key_bytes = 2;
         L.sort_parts = sort_parts<uint16_t>(cap);
         L.sorted_buffer = L.passes & 1;
+        tile_digit = kRadixBits;
     }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
     // cleared every frame: status block, histograms, look-back words, tile ranges
     L.zero_begin = off;
     L.off_ctrl = take(sizeof(Ctrl));
-    L.off_hist = take(sizeof(uint32_t) * 2 * kMaxPasses * kRadix);
-    L.lookback_words_depth = df ? (size_t)kDepthPasses * depth_sort_parts(n) * kRadix : 0;
-    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * kRadix));
+    L.off_hist = take(sizeof(uint32_t) * kMaxPasses * ((size_t)1 << L.digit_bits));
+    L.off_hist_tile = take(sizeof(uint32_t) * kMaxPasses * ((size_t)1 << tile_digit));
+    L.lookback_words_depth =
+        df ? (size_t)L.depth_passes * depth_sort_parts(n, L.digit_bits) * ((size_t)1 << L.digit_bits) : 0;
+    L.off_lookback = take(sizeof(uint32_t) *
+                          (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * ((size_t)1 << tile_digit)));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
     L.zero_end = off;
@@ -325,12 +337,12 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode) {
     return L;
 }
 
-int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes) {
-    if (make_layout(n, W, H, tile, 1, mode).total > ws_bytes) return 0;
+int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes, int digit_bits) {
+    if (make_layout(n, W, H, tile, 1, mode, digit_bits).total > ws_bytes) return 0;
     int64_t lo = 1, hi = kMaxKeys;
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
-        if (make_layout(n, W, H, tile, mid, mode).total <= ws_bytes) lo = mid; else hi = mid - 1;
+        if (make_layout(n, W, H, tile, mid, mode, digit_bits).total <= ws_bytes) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -439,7 +451,7 @@ vis_status vis_workspace_size(int64_t n, int W, int H, int64_t key_capacity, con
     if ((st = check_opts(o))) return st;
     if (key_capacity < 1 || key_capacity > (int64_t)vis::kMaxKeys)
         return fail(VIS_ERR_INVALID_ARG, "key_capacity must be in [1, 2^30-1]");
-    *bytes = vis::make_layout(n, W, H, o.tile, key_capacity, o.sort_mode).total;
+    *bytes = vis::make_layout(n, W, H, o.tile, key_capacity, o.sort_mode, o.digit_bits).total;
     return VIS_OK;
 }
 
@@ -450,9 +462,9 @@ vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const 
     if (st) return st;
     const vis_render_opts o = resolve_opts(opts);
     if ((st = check_opts(o))) return st;
-    const int64_t cap = vis::capacity_for(n, W, H, o.tile, o.sort_mode, ws_bytes);
+    const int64_t cap = vis::capacity_for(n, W, H, o.tile, o.sort_mode, ws_bytes, o.digit_bits);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
-    const vis::Layout L = vis::make_layout(n, W, H, o.tile, cap, o.sort_mode);
+    const vis::Layout L = vis::make_layout(n, W, H, o.tile, cap, o.sort_mode, o.digit_bits);
     out->total_bytes = L.total;
     out->key_capacity = L.cap;
     out->tiles_x = L.tiles_x; out->tiles_y = L.tiles_y;
@@ -495,9 +507,9 @@ static vis_status prepare(const vis_scene_t* scenes, int n_scenes, bool padded, 
     *o = resolve_opts(opts);
     if ((st = check_opts(*o))) return st;
     if (!ws || !aligned16(ws)) return fail(VIS_ERR_INVALID_ARG, "workspace is null or not 16-byte aligned");
-    const int64_t cap = vis::capacity_for(slots, W, H, o->tile, o->sort_mode, ws_bytes);
+    const int64_t cap = vis::capacity_for(slots, W, H, o->tile, o->sort_mode, ws_bytes, o->digit_bits);
     if (cap < 1) return fail(VIS_ERR_INVALID_ARG, "workspace of %zu bytes holds no keys", ws_bytes);
-    *L = vis::make_layout(slots, W, H, o->tile, cap, o->sort_mode);
+    *L = vis::make_layout(slots, W, H, o->tile, cap, o->sort_mode, o->digit_bits);
     L->spin_limit = o->spin_limit > 0 ? (uint32_t)o->spin_limit : vis::kSpinLimit;
     return VIS_OK;
 }

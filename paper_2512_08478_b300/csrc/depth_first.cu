@@ -178,12 +178,18 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     // 1. compaction of the surviving splats, in index order (the preprocess wrote the
     //    per-block survivor counts)
     launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0, stream);
+    // the compaction writes buffer 1 when the depth sort has an odd number of passes, so
+    // that the passes ping-pong (a pass never writes its own input) and end in buffer 0
+    const bool odd = (L.depth_passes & 1) != 0;
+    uint32_t* ck = odd ? dk1 : dk0;
+    uint32_t* cv = odd ? dv1 : dv0;
     launch_k(true, compact_visible, blocks_n, kPrepThreads, 0, stream, touched,
-             reinterpret_cast<const float*>(ws + L.off_depth), L.n, (const uint32_t*)bvis_off, dk0, dv0);
-    // 2. sort by depth (4 passes; the result lands in buffer 0)
-    launch_sort_generic<uint32_t>(dk0, dv0, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, kDepthPasses, hist, lb,
-                                  ctrl->part_counter, &ctrl->error, stream, nullptr, 0, kRadixBits,
-                                  depth_sort_kpt(L.n), L.spin_limit);
+             reinterpret_cast<const float*>(ws + L.off_depth), L.n, (const uint32_t*)bvis_off, ck, cv);
+    // 2. sort by depth; the result lands in buffer 0
+    launch_sort_generic<uint32_t>(ck, cv, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, L.depth_passes, hist, lb,
+                                  ctrl->part_counter, &ctrl->error, stream, nullptr, 0,
+                                  32 - L.digit_bits * (L.depth_passes - 1), depth_sort_kpt(L.n, L.digit_bits),
+                                  L.spin_limit, L.digit_bits);
 }
 
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
@@ -227,9 +233,10 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* va = L.sorted_buffer ? v1 : v0;
     uint32_t* kb = L.sorted_buffer ? k0 : k1;
     uint32_t* vb = L.sorted_buffer ? v0 : v1;
-    launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp, hist + kMaxPasses * kRadix,
-                                  lb + L.lookback_words_depth, ctrl->part_counter + kMaxPasses, &ctrl->error, stream,
-                                  mark, mark_index + 1, L.tile_bits - kRadixBits * (tp - 1), 0, L.spin_limit);
+    launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp,
+                                  reinterpret_cast<uint32_t*>(ws + L.off_hist_tile), lb + L.lookback_words_depth,
+                                  ctrl->part_counter + kMaxPasses, &ctrl->error, stream, mark, mark_index + 1,
+                                  L.tile_bits - L.digit_bits * (tp - 1), 16, L.spin_limit, L.digit_bits);
     (void)sms;
 }
 

@@ -1,5 +1,6 @@
-// Building blocks of one onesweep-style LSD radix pass (8-bit digit, 256 threads, one
-// digit per thread in the scan and look-back phases).
+// Building blocks of one onesweep-style LSD radix pass: 256 threads, a digit of DBITS = 8,
+// 10 or 11 bits, so that in the scan and look-back phases each thread owns 1, 4 or 8
+// consecutive digits.
 //
 // Per partition: rank every key stably inside its warp (which also yields the warp's
 // digit counts), publish the partition's per-digit aggregate, issue the decoupled
@@ -7,6 +8,8 @@
 // memory while the look-back words are in flight, then resolve the global digit offsets
 // and write the digit runs.
 #pragma once
+#include <type_traits>
+
 #include "vis_internal.cuh"
 
 namespace vis {
@@ -14,9 +17,21 @@ namespace vis {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr int kLookbackWindow = 16;   // predecessors read per look-back round
 
-static_assert(kSortThreads == kRadix, "one digit per thread");
+static_assert(kSortThreads == 256, "the scan phase assumes 8 warps");
+
+// Per digit width: D digits, DPT of them per thread, the look-back window (predecessors
+// read per round; narrower for wide digits, whose DPT windows share the registers), and
+// the type of the per-warp digit counters (a warp counts at most 32 x 16 = 512 keys of one
+// digit, so 16 bits suffice and halve the shared memory of the wide digits).
+template <int DBITS>
+struct RadixCfg {
+    static constexpr int D = 1 << DBITS;
+    static constexpr int DPT = D > kSortThreads ? D / kSortThreads : 1;
+    static constexpr int WIN = D > kSortThreads ? 4 : 16;
+    using Counter = typename std::conditional<(D > kSortThreads), uint16_t, uint32_t>::type;
+    static_assert(D >= kSortThreads, "at least one digit per thread");
+};
 
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -27,64 +42,24 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     return v;
 }
 
-// exclusive scan of one value per thread over a 256-thread block; returns total in *tot
-__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* s_warp, uint32_t* tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    uint32_t woff = 0, all = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t x = s_warp[w];
-        if (w < warp) woff += x;
-        all += x;
-    }
-    __syncthreads();
-    if (tot) *tot = all;
-    return woff + incl - v;
-}
-
-// Turn the per-warp counts of digit d (whist[w][d]) into exclusive per-warp offsets and
-// return the partition's count of d.
-__device__ __forceinline__ uint32_t warp_offsets_of_digit(uint32_t (*whist)[kRadix], uint32_t d) {
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-        const uint32_t c = whist[w][d];
-        whist[w][d] = cnt;
-        cnt += c;
-    }
-    return cnt;
-}
-
-// Publish this partition's count of digit d (partition 0 publishes it as inclusive).
-__device__ __forceinline__ void publish_aggregate(uint32_t* lookback, uint32_t part, uint32_t d, uint32_t cnt) {
-    st_relaxed(&lookback[(size_t)part * kRadix + d], (part == 0 ? kFlagInc : kFlagAgg) | cnt);
-}
-
-// Stable rank of KPT warp-striped keys (digit (key[k] >> shift) & 255, key k valid iff
-// bit k of valid_mask) inside the partition. Per round, the lanes holding the same digit
-// ("peers") are found with one ballot per digit bit (the digit's upper bits are zero when
-// nbits < 8); the group's leader (lowest lane) takes the group's slots from the warp's
+// Stable rank of KPT warp-striped keys (digit (key[k] >> shift) & (D - 1), with nbits
+// significant bits; key k valid iff bit k of valid_mask) among the warp's keys of the same
+// digit. Per round, the lanes holding the same digit ("peers") are found with one ballot per
+// digit bit; the group's leader (lowest lane) takes the group's slots from the warp's
 // private running counter wh[digit] with a plain load and store -- groups of one round
-// have distinct digits, and the rounds are ordered by __syncwarp. Returns
-// local_start[digit] + wh[digit] on entry + (rank of the key among the warp's keys of its
-// digit); wh[digit] grows by the warp's count of the digit.
-template <int KPT, typename K>
+// have distinct digits, and the rounds are ordered by __syncwarp. Returns wh[digit] on
+// entry + (rank of the key among the warp's keys of its digit in this round); wh[digit]
+// grows by the warp's count of the digit.
+template <int KPT, int DBITS, typename K, typename Counter>
 __device__ __forceinline__ void rank_keys(const K (&key)[KPT], int shift, int nbits, uint32_t valid_mask,
-                                          uint32_t* wh, const uint32_t* local_start, uint32_t (&pos)[KPT]) {
+                                          Counter* wh, uint32_t (&pos)[KPT]) {
+    constexpr uint32_t kMask = (1u << DBITS) - 1;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
         const bool valid = (valid_mask >> k) & 1u;
-        const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
+        const uint32_t dk = (uint32_t)(key[k] >> shift) & kMask;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
         for (int b = 0; b < nbits; ++b) {
             const uint32_t bit = (dk >> b) & 1u;
@@ -96,11 +71,11 @@ __device__ __forceinline__ void rank_keys(const K (&key)[KPT], int shift, int nb
         uint32_t old = 0;
         if (valid && lane == leader) {
             old = wh[dk];
-            wh[dk] = old + (uint32_t)__popc(peers);
+            wh[dk] = (Counter)(old + (uint32_t)__popc(peers));
         }
         __syncwarp();
         old = __shfl_sync(0xffffffffu, old, leader);
-        pos[k] = local_start[dk] + old + __popc(peers & lt);
+        pos[k] = old + __popc(peers & lt);
     }
 }
 
@@ -112,36 +87,36 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Decoupled look-back, split in two so that its loads overlap the ranking:
-// lookback_issue reads the window of WIN predecessors of partition `part` for digit d;
-// lookback_resolve consumes it in order up to the first inclusive prefix, polling a word
-// not yet published at most `limit` times, continues one predecessor at a time past
-// the window if needed, publishes this partition's inclusive prefix and returns the
-// count of d over all preceding partitions (*timed_out set if a poll gave up).
-template <int WIN>
+// Decoupled look-back over the words lookback[q * D + d] of the partitions q preceding
+// `part`, split in two so that its loads overlap the reordering: lookback_issue reads the
+// window of WIN predecessors for digit d; lookback_resolve consumes it in order up to the
+// first inclusive prefix, polling a word not yet published at most `limit` times,
+// continues one predecessor at a time past the window if needed, publishes this
+// partition's inclusive prefix and returns the count of d over all preceding partitions
+// (*timed_out set if a poll gave up; the prefix is then wrong, but still published, so
+// that no successor waits on this partition).
+template <int WIN, int D>
 __device__ __forceinline__ void lookback_issue(const uint32_t* lookback, uint32_t part, uint32_t d,
                                                uint32_t (&v)[WIN]) {
     const int64_t q0 = (int64_t)part - 1;
 #pragma unroll
     for (int i = 0; i < WIN; ++i)
-        v[i] = (q0 - i >= 0) ? ld_relaxed(&lookback[(size_t)(q0 - i) * kRadix + d]) : kFlagInc;
+        v[i] = (q0 - i >= 0) ? ld_relaxed(&lookback[(size_t)(q0 - i) * D + d]) : kFlagInc;
 }
 
-__device__ __forceinline__ bool lookback_wait(const uint32_t* lookback, int64_t q, uint32_t d, uint32_t* w,
-                                              uint32_t limit) {
+__device__ __forceinline__ bool lookback_wait(const uint32_t* word, uint32_t* w, uint32_t limit) {
     uint32_t spins = 0;
     while ((*w & ~kCountMask) == 0) {
         if (++spins > limit) return false;
         if (spins > 8) __nanosleep(32);
-        *w = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
+        *w = ld_relaxed(word);
     }
     return true;
 }
 
-template <int WIN>
+template <int WIN, int D>
 __device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_t part, uint32_t d, uint32_t cnt,
-                                                     const uint32_t (&v)[WIN], uint32_t limit,
-                                                     bool* timed_out) {
+                                                     const uint32_t (&v)[WIN], uint32_t limit, bool* timed_out) {
     *timed_out = false;
     if (part == 0) return 0;
     uint32_t prefix = 0;
@@ -151,17 +126,18 @@ __device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_
     for (int i = 0; i < WIN; ++i) {
         if (found || to || q0 - i < 0) break;
         uint32_t w = v[i];
-        if (!lookback_wait(lookback, q0 - i, d, &w, limit)) { to = true; break; }
+        if (!lookback_wait(&lookback[(size_t)(q0 - i) * D + d], &w, limit)) { to = true; break; }
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }
     for (int64_t q = q0 - WIN; !found && !to && q >= 0; --q) {
-        uint32_t w = ld_relaxed(&lookback[(size_t)q * kRadix + d]);
-        if (!lookback_wait(lookback, q, d, &w, limit)) { to = true; break; }
+        const uint32_t* word = &lookback[(size_t)q * D + d];
+        uint32_t w = ld_relaxed(word);
+        if (!lookback_wait(word, &w, limit)) { to = true; break; }
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }
-    st_relaxed(&lookback[(size_t)part * kRadix + d], kFlagInc | ((prefix + cnt) & kCountMask));
+    st_relaxed(&lookback[(size_t)part * D + d], kFlagInc | ((prefix + cnt) & kCountMask));
     *timed_out = to;
     return prefix;
 }

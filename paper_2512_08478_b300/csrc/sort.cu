@@ -3,17 +3,19 @@
 // Algorithm 1 sorts the splats on the GPU with a radix sort (section 3.4, "GPU
 // sorting and rasterization"); here the keys are 64-bit (tile id << 32 | float bits
 // of the view depth) with the Gaussian index as payload, so one stable sort yields
-// the (tile, depth, index) order the compositor walks.
+// the (tile, depth, index) order the compositor walks; the depth-first order sorts
+// 32-bit depth keys, then 16- or 32-bit tile ids.
 //
 //  - sort_histogram: one read of all keys builds the digit histograms of every
 //    pass at once (shared-memory counters, one global atomic per bin per CTA).
-//  - sort_pass (one launch per 8-bit digit): a CTA takes the next partition of
-//    2048 64-bit or 4096 32-bit keys from an atomic ticket (so partitions start in order and the
-//    look-back below always makes progress), ranks its keys stably per warp with
-//    __match_any_sync, publishes its per-digit counts, and resolves its global
-//    offsets by decoupled look-back over the preceding partitions' published
-//    counts. The keys are then reordered by digit in shared memory and written out
-//    in runs, so global stores are coalesced within each digit run.
+//  - sort_pass (one launch per digit of DBITS = 8, 10 or 11 bits): a CTA takes the next
+//    partition of 256 x KPT keys from an atomic ticket (so partitions start in order and
+//    the look-back below always makes progress), ranks its keys stably per warp with
+//    ballots, publishes its per-digit counts, and resolves its global offsets by
+//    decoupled look-back over the preceding partitions' published counts. The keys are
+//    then reordered by digit in shared memory and written out in runs, so global stores
+//    are coalesced within each digit run. Wider digits need fewer passes but publish and
+//    read D = 2^DBITS look-back words per partition (4 D bytes against 4096 keys).
 //  - Spin waits on a predecessor are bounded (spin_limit polls); on expiry the
 //    CTA records kErrTimeout, publishes anyway so nobody waits on it, and writes
 //    nothing out of range (every destination is checked against the key count).
@@ -24,13 +26,16 @@
 
 namespace vis {
 
-template <typename K>
+// Digit histograms of `passes` digits of DBITS bits (pass p: digit (key >> DBITS p)),
+// hist[p * D + digit]; dynamic shared memory of passes * D words.
+template <typename K, int DBITS>
 __global__ void __launch_bounds__(256)
 sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap, int passes,
                uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
+    constexpr int D = 1 << DBITS;
     pdl_entry();
-    __shared__ uint32_t sh[kMaxPasses * kRadix];
-    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
+    extern __shared__ uint32_t sh[];
+    for (int i = threadIdx.x; i < passes * D; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     if (*error) return;
     const int64_t m = min((int64_t)*num_keys, cap);
@@ -38,51 +43,61 @@ sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
         const K k = keys[j];
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&sh[p * kRadix + (uint32_t)((k >> (kRadixBits * p)) & (kRadix - 1))], 1u);
+            atomicAdd(&sh[p * D + (uint32_t)((k >> (DBITS * p)) & (D - 1))], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+    for (int i = threadIdx.x; i < passes * D; i += blockDim.x)
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-template <typename K, int KPT>
+template <typename K, int KPT, int DBITS>
 struct SortSmem {
+    using Cfg = RadixCfg<DBITS>;
     K keys[kSortThreads * KPT];          // reordered by digit
     uint32_t vals[kSortThreads * KPT];   // reordered by digit
     uint32_t vin[kSortThreads * KPT];    // values in input order (asynchronous copies)
-    uint32_t whist[kSortThreads / 32][kRadix];
-    uint32_t digit_off[kRadix];
-    uint32_t local_start[kRadix];
-    uint32_t zeros[kRadix];
+    typename Cfg::Counter whist[kSortThreads / 32][Cfg::D];
+    uint32_t digit_off[Cfg::D];
+    uint32_t local_start[Cfg::D];
     uint32_t scan_a[8], scan_b[8];
     uint32_t part;
     uint32_t bad;
 };
 
-// Three CTAs of 256 threads per SM: at most 85 registers per thread.
-//
+// CTAs per SM the register budget is set for: three (85 registers) for 8- and 10-bit
+// digits, four for the short 32-bit partitions, two for the 11-bit digits, whose shared
+// memory (~96 KB) admits no more.
+template <typename K, int KPT, int DBITS>
+struct SortOcc {
+    static constexpr int value = DBITS == 11 ? 2 : (KPT <= 8 && sizeof(K) == 4) ? 4 : 3;
+};
+
 // Per partition (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT)):
 //   keys -> registers, values -> shared memory by asynchronous copies;
 //   stable ranking inside each warp (rank_keys, warp counters from zero): the rank of
 //   every key among its warp's keys of the same digit, and the warp's digit counts;
-//   per-digit partition counts, published at once for the successors; exclusive scans
-//   of the counts and of the pass's global digit histogram; the look-back window is
-//   issued; the keys and values are reordered by digit in shared memory;
-//   the look-back is resolved -> global digit offsets; digit runs are written out.
+//   per-digit partition counts (each thread its DPT consecutive digits), published at
+//   once for the successors; exclusive scans of the counts and of the pass's global digit
+//   histogram; the look-back windows are issued; the keys and values are reordered by
+//   digit in shared memory; the look-back is resolved -> global digit offsets; digit runs
+//   are written out.
 // All indexing inside the partition is 32-bit and relative to its base. keys_out may be
 // null (last pass of a sort whose keys are not needed). nbits: significant bits of this
-// pass's digit (8, fewer for the top digit of a narrow key).
-template <typename K, int KPT>
-__global__ void __launch_bounds__(kSortThreads, (KPT <= 8 && sizeof(K) == 4) ? 4 : 3)
+// pass's digit (DBITS, fewer for the top digit of a narrow key).
+template <typename K, int KPT, int DBITS>
+__global__ void __launch_bounds__(kSortThreads, SortOcc<K, KPT, DBITS>::value)
 sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
           const uint32_t* __restrict__ num_keys, int64_t cap, int shift, int nbits,
           const uint32_t* __restrict__ hist_pass, uint32_t* __restrict__ lookback,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error, uint32_t spin_limit) {
+    using Cfg = RadixCfg<DBITS>;
+    using Counter = typename Cfg::Counter;
+    constexpr int D = Cfg::D, DPT = Cfg::DPT, WIN = Cfg::WIN;
     pdl_entry();
     constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem<K, KPT>& S = *reinterpret_cast<SortSmem<K, KPT>*>(smem_raw);
+    SortSmem<K, KPT, DBITS>& S = *reinterpret_cast<SortSmem<K, KPT, DBITS>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_relaxed(error) & kErrCapacity) return;
     const int64_t m = min((int64_t)*num_keys, cap);
@@ -90,8 +105,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         S.part = atomicAdd(part_counter, 1u);
         S.bad = 0;
     }
-    for (int i = tid; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&S.whist[0][0])[i] = 0;
-    S.zeros[tid] = 0;
+    for (int i = tid; i < (kSortThreads / 32) * D; i += kSortThreads) (&S.whist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t part = S.part;
     const int64_t base = (int64_t)part * PART;
@@ -116,39 +130,63 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         }
     }
     cp_async_commit();
-    uint32_t* wh = S.whist[warp];
+    Counter* wh = S.whist[warp];
     // ---- stable ranking inside the warp; the warp counters end as the warp's digit counts ----
     uint32_t pos[KPT];
-    rank_keys<KPT, K>(key, shift, nbits, vmask, wh, S.zeros, pos);
+    rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
     __syncthreads();
 
     // ---- per-digit counts and warp offsets; publish; scans; issue the look-back ----
-    const uint32_t d = tid;   // one digit per thread (256 threads, 256 digits)
-    const uint32_t cnt = warp_offsets_of_digit(S.whist, d);
-    publish_aggregate(lookback, part, d, cnt);
-    const uint32_t h = hist_pass[d];
-    uint32_t ia = cnt, ib = h;
+    const uint32_t d0 = (uint32_t)tid * DPT;   // this thread's digits d0 .. d0 + DPT - 1
+    uint32_t cnt[DPT], h[DPT];
+    uint32_t ta = 0, tb = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        const uint32_t d = d0 + j;
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t x = S.whist[w][d];
+            S.whist[w][d] = (Counter)c;   // exclusive offset of warp w within digit d
+            c += x;
+        }
+        cnt[j] = c;
+        st_relaxed(&lookback[(size_t)part * D + d], (part == 0 ? kFlagInc : kFlagAgg) | c);
+        h[j] = hist_pass[d];
+        ta += c;
+        tb += h[j];
+    }
+    uint32_t ia = ta, ib = tb;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) { ia += ta; ib += tb; }
+        const uint32_t xa = __shfl_up_sync(0xffffffffu, ia, o), xb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += xa; ib += xb; }
     }
     if (lane == 31) { S.scan_a[warp] = ia; S.scan_b[warp] = ib; }
-    uint32_t lbw[kLookbackWindow];
-    lookback_issue<kLookbackWindow>(lookback, part, d, lbw);
+    uint32_t lbw[DPT][WIN];
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) lookback_issue<WIN, D>(lookback, part, d0 + j, lbw[j]);
     __syncthreads();
-    uint32_t local_start = ia - cnt, gstart = ib - h;
+    uint32_t ls = ia - ta, gs = ib - tb;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w)
-        if (w < warp) { local_start += S.scan_a[w]; gstart += S.scan_b[w]; }
-    S.local_start[d] = local_start;
+        if (w < warp) { ls += S.scan_a[w]; gs += S.scan_b[w]; }
+    uint32_t lsd[DPT], gsd[DPT];
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        lsd[j] = ls;
+        gsd[j] = gs;
+        S.local_start[d0 + j] = ls;
+        ls += cnt[j];
+        gs += h[j];
+    }
     __syncthreads();
 
     // ---- reorder by digit: partition position = digit start + warp offset + rank ----
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-        const uint32_t dk = (uint32_t)(key[k] >> shift) & (kRadix - 1);
-        pos[k] += S.local_start[dk] + wh[dk];
+        const uint32_t dk = (uint32_t)(key[k] >> shift) & (D - 1);
+        pos[k] += S.local_start[dk] + (uint32_t)wh[dk];
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
@@ -160,12 +198,17 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 
     // ---- resolve the look-back: global digit offsets ----
     bool timed_out = false;
-    const uint32_t prefix = lookback_resolve<kLookbackWindow>(lookback, part, d, cnt, lbw, spin_limit, &timed_out);
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        bool to = false;
+        const uint32_t prefix = lookback_resolve<WIN, D>(lookback, part, d0 + j, cnt[j], lbw[j], spin_limit, &to);
+        timed_out = timed_out || to;
+        S.digit_off[d0 + j] = gsd[j] + prefix - lsd[j];
+    }
     if (timed_out) {
         atomicOr(error, kErrTimeout);
         S.bad = 1;
     }
-    S.digit_off[d] = gstart + prefix - local_start;
     __syncthreads();
     if (S.bad) return;
 
@@ -175,7 +218,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         const int i = tid + k * kSortThreads;
         if (i < n_in) {
             const K kk = S.keys[i];
-            const uint32_t dest = S.digit_off[(uint32_t)(kk >> shift) & (kRadix - 1)] + (uint32_t)i;
+            const uint32_t dest = S.digit_off[(uint32_t)(kk >> shift) & (D - 1)] + (uint32_t)i;
             if (dest < (uint32_t)m) {
                 if (keys_out) keys_out[dest] = kk;
                 vals_out[dest] = S.vals[i];
@@ -197,23 +240,27 @@ static int sm_count() {
     return sms;
 }
 
-template <typename K, int KPT>
-static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
-                             uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
-                             uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                             StageMark mark, int mark_index, int last_bits, uint32_t spin_limit) {
+template <typename K, int KPT, int DBITS>
+static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
+                              uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
+                              uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
+                              StageMark mark, int mark_index, int last_bits, uint32_t spin_limit) {
+    constexpr int D = 1 << DBITS;
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     static std::mutex attr_mu;
-    const size_t smem = sizeof(SortSmem<K, KPT>);
+    const size_t smem = sizeof(SortSmem<K, KPT, DBITS>);
+    const size_t hsmem = sizeof(uint32_t) * kMaxPasses * D;
     set_up_per_device(attr_dev, attr_mu, [&] {
-        return cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-               cudaSuccess;
+        return cudaFuncSetAttribute(sort_pass<K, KPT, DBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem) == cudaSuccess &&
+               cudaFuncSetAttribute(sort_histogram<K, DBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)hsmem) == cudaSuccess;
     });
     const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
-    launch_k(true, sort_histogram<K>, hist_blocks, 256, 0, stream, keys_in, (const uint32_t*)num_keys_dev, cap,
-             passes, hist, (const uint32_t*)error);
+    launch_k(true, sort_histogram<K, DBITS>, hist_blocks, 256, sizeof(uint32_t) * passes * D, stream, keys_in,
+             (const uint32_t*)num_keys_dev, cap, passes, hist, (const uint32_t*)error);
     if (mark) mark(mark_index, stream);
     const K* src_k = keys_in;
     const uint32_t* src_v = vals_in;
@@ -221,29 +268,38 @@ static void sort_generic_kpt(const K* keys_in, const uint32_t* vals_in, K* keys_
         const bool to_a = ((passes - 1 - p) % 2) == 0;
         K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
-        const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < kRadixBits) ? last_bits : kRadixBits;
-        launch_k(true, sort_pass<K, KPT>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
-                 (const uint32_t*)num_keys_dev, cap, kRadixBits * p, nbits, (const uint32_t*)(hist + p * kRadix),
-                 lookback + (size_t)p * parts * kRadix, &part_counters[p], error, spin_limit);
+        const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < DBITS) ? last_bits : DBITS;
+        launch_k(true, sort_pass<K, KPT, DBITS>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
+                 (const uint32_t*)num_keys_dev, cap, DBITS * p, nbits, (const uint32_t*)(hist + (size_t)p * D),
+                 lookback + (size_t)p * parts * D, &part_counters[p], error, spin_limit);
         src_k = dk;
         src_v = dv;
     }
 }
 
-// kpt: keys per thread of the passes (0: SortKPT<K>; 8 is also built for 32-bit keys)
+// kpt: keys per thread of the passes (0: SortKPT<K>; 8 is also built for 32-bit keys of
+// 8-bit digits); digit_bits 8, or 10 / 11 for 32-bit keys
 template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                         StageMark mark, int mark_index, int last_bits, int kpt, uint32_t spin_limit) {
+                         StageMark mark, int mark_index, int last_bits, int kpt, uint32_t spin_limit,
+                         int digit_bits) {
     if (cap <= 0 || passes <= 0) return;
-    if (std::is_same<K, uint32_t>::value && kpt == 8)
-        sort_generic_kpt<K, 8>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev, passes, hist,
-                               lookback, part_counters, error, stream, mark, mark_index, last_bits, spin_limit);
-    else
-        sort_generic_kpt<K, SortKPT<K>::value>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev,
-                                               passes, hist, lookback, part_counters, error, stream, mark,
-                                               mark_index, last_bits, spin_limit);
+    constexpr bool k32 = std::is_same<K, uint32_t>::value;
+#define VIS_SORT_IMPL(KPT_, DB_)                                                                                   \
+    sort_generic_impl<K, KPT_, DB_>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev, passes, \
+                                    hist, lookback, part_counters, error, stream, mark, mark_index, last_bits,     \
+                                    spin_limit)
+    if constexpr (k32) {
+        if (digit_bits == 11) VIS_SORT_IMPL(16, 11);
+        else if (digit_bits == 10) VIS_SORT_IMPL(16, 10);
+        else if (kpt == 8) VIS_SORT_IMPL(8, 8);
+        else VIS_SORT_IMPL(16, 8);
+    } else {
+        VIS_SORT_IMPL(SortKPT<K>::value, 8);
+    }
+#undef VIS_SORT_IMPL
 }
 
 // One pass of sort_pass over m <= cap keys (read from *num_keys_dev) with digit
@@ -257,14 +313,14 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     static std::mutex attr_mu;
     constexpr int KPT = SortKPT<K>::value;
-    const size_t smem = sizeof(SortSmem<K, KPT>);
+    const size_t smem = sizeof(SortSmem<K, KPT, 8>);
     set_up_per_device(attr_dev, attr_mu, [&] {
-        return cudaFuncSetAttribute(sort_pass<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        return cudaFuncSetAttribute(sort_pass<K, KPT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                cudaSuccess;
     });
-    launch_k(true, sort_pass<K, KPT>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in, keys_out,
-             vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass, lookback,
-             part_counter, error, spin_limit);
+    launch_k(true, sort_pass<K, KPT, 8>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in,
+             keys_out, vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass,
+             lookback, part_counter, error, spin_limit);
 }
 
 template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint16_t*, uint32_t*, int64_t,
@@ -273,10 +329,12 @@ template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint1
 
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t,
+                                            int);
 template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
-                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t);
+                                            uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t,
+                                            int);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);
@@ -293,7 +351,7 @@ void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark,
                                   reinterpret_cast<uint32_t*>(ws + L.off_hist),
                                   reinterpret_cast<uint32_t*>(ws + L.off_lookback), ctrl->part_counter,
                                   &ctrl->error, stream, mark, mark_index, L.key_bits - kRadixBits * (L.passes - 1), 0,
-                                  L.spin_limit);
+                                  L.spin_limit, kRadixBits);
 }
 
 }  // namespace vis

@@ -167,13 +167,13 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
              L.tiles_x, L.tiles_y, gdiff);
     const size_t scan_smem = sizeof(int) * (size_t)(L.tiles_x + 1) * L.tiles_y;
     launch_k(true, tile_scan_kernel, 1, 1024, scan_smem, stream, (const int*)gdiff, L.tiles_x, L.tiles_y,
-             reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix,
+             reinterpret_cast<uint32_t*>(ws + L.off_hist_tile),
              reinterpret_cast<uint2*>(ws + L.off_ranges));
 }
 
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist) + kMaxPasses * kRadix;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist_tile);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback) + L.lookback_words_depth;
     uint16_t* k0 = reinterpret_cast<uint16_t*>(ws + L.off_keys[0]);
     uint16_t* k1 = reinterpret_cast<uint16_t*>(ws + L.off_keys[1]);

@@ -31,15 +31,19 @@ template <typename K> constexpr int64_t sort_parts(int64_t cap) {
 // (8 keys per thread): a pass over ~1M keys is a single wave of short-lived CTAs, twice as
 // many of them, instead of half a wave of long ones.
 constexpr int64_t kSmallDepthSort = (int64_t)2 << 20;
-inline int depth_sort_kpt(int64_t n) { return n <= kSmallDepthSort ? 8 : SortKPT<uint32_t>::value; }
-inline int64_t depth_sort_parts(int64_t n) {
-    const int64_t part = (int64_t)kSortThreads * depth_sort_kpt(n);
+inline int depth_sort_kpt(int64_t n, int digit_bits = 8) {
+    return (n <= kSmallDepthSort && digit_bits == 8) ? 8 : SortKPT<uint32_t>::value;
+}
+inline int64_t depth_sort_parts(int64_t n, int digit_bits = 8) {
+    const int64_t part = (int64_t)kSortThreads * depth_sort_kpt(n, digit_bits);
     return (n + part - 1) / part;
 }
+// passes of a key of `bits` significant bits at digit_bits per pass
+inline int passes_for(int bits, int digit_bits) { return bits <= 0 ? 0 : (bits + digit_bits - 1) / digit_bits; }
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxDigitBits = 11;        // widest radix digit (vis_render_opts.digit_bits)
 constexpr int kMaxPasses = 8;
-constexpr int kDepthPasses = 4;          // 8-bit passes over the float bits of a positive depth
 constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit counts
 
 // ctrl->error bits
@@ -63,6 +67,9 @@ struct Layout {
     int tiles_x = 0, tiles_y = 0;
     int64_t ntiles = 0;
     int tile_bits = 0, key_bits = 0, passes = 0;
+    int digit_bits = kRadixBits;           // digit of the depth sort and of a 32-bit tile sort
+    int depth_passes = 4;                  // passes of the depth sort (32-bit keys)
+    size_t off_hist_tile = 0;              // histograms of the tile sort (after the depth sort's)
     int64_t cap = 0;
     int64_t prep_blocks = 0;
     int64_t sort_parts = 0;
@@ -85,10 +92,11 @@ struct Layout {
     uint32_t spin_limit = kSpinLimit;      // polls a look-back wait may make (from the render options)
 };
 
-// Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`, sort mode.
-Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode);
+// Workspace layout for n Gaussians, W x H, tile size, key capacity `cap`, sort mode, radix
+// digit width.
+Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int digit_bits = kRadixBits);
 // Largest capacity whose layout fits ws_bytes (0 if none).
-int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes);
+int64_t capacity_for(int64_t n, int W, int H, int tile, int mode, size_t ws_bytes, int digit_bits = kRadixBits);
 
 struct Ctrl {
     uint32_t num_keys;
@@ -283,18 +291,19 @@ void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char
                                 float* d_log_scales, float* d_quats, float* d_logits, float* d_sh,
                                 cudaStream_t stream);
 
-// Stable LSD radix sort of (K key, uint32 value) pairs over `passes` 8-bit digits.
-// Reads keys_in/vals_in, ping-pongs between the a and b buffers and leaves the result in a.
-// `lookback` must hold passes * sort_parts<K>(cap) * kRadix words, `hist` passes * kRadix
-// words and `part_counters` passes words, all zeroed; the key count is read from
-// num_keys_dev (<= cap). If `mark` is given it is called after the histogram. last_bits:
-// significant bits of the last pass's digit (key bits - 8 (passes - 1)).
+// Stable LSD radix sort of (K key, uint32 value) pairs over `passes` digits of digit_bits
+// bits (8; 10 or 11 for 32-bit keys). Reads keys_in/vals_in, ping-pongs between the a and b
+// buffers and leaves the result in a. `lookback` must hold passes * parts * 2^digit_bits
+// words (parts = sort_parts_for(cap, kpt, digit_bits)), `hist` passes * 2^digit_bits words
+// and `part_counters` passes words, all zeroed; the key count is read from num_keys_dev
+// (<= cap). If `mark` is given it is called after the histogram. last_bits: significant
+// bits of the last pass's digit (key bits - digit_bits (passes - 1)).
 template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits, int kpt = 0,
-                         uint32_t spin_limit = kSpinLimit);
+                         uint32_t spin_limit = kSpinLimit, int digit_bits = kRadixBits);
 
 // One sort_pass over the keys (digit (key >> shift) & 255 with nbits significant bits,
 // histogram hist_pass); keys_out may be null. `lookback` holds sort_parts<K>(cap) * kRadix

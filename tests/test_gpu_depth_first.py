@@ -174,3 +174,24 @@ def test_depth_first_capacity_error_then_retry(mode):
     assert ws.key_capacity > 100
     ref, _ = oracle.render(sc_np, cam)
     image_parity(rgb.cpu().numpy().astype(np.float64), alpha.cpu().numpy().astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("digit_bits", [10, 11])
+@pytest.mark.parametrize("grid", [(1280, 720, 16), (2048, 1632, 8)])
+def test_wide_radix_digits_equal_tile_depth_sort(digit_bits, grid):
+    """The depth sort with 10- or 11-bit digits (32-bit keys in 4 or 3 passes, an odd count
+    at 11 bits) and, on a grid beyond the 16-bit tile path, the 4-byte tile sort too: the
+    same (tile, depth, index) order as the 64-bit key sort, bit for bit, over enough
+    survivors to span hundreds of partitions."""
+    W, H, tile = grid
+    sc = synth.mixture_scene(300_000, 23, sh_degree=1, ball_radius=4.0, comp_std=0.6, log_scale_mean=-3.4)
+    cam = synth.look_at((1.0, 2.0, 11.0), (0, 0, 0), W, H, 55.0)
+    a_rgb, a_alpha, sa, wa = render_gpu(sc, cam, (0.1, 0.2, 0.3), vis.make_opts(tile=tile, sort_mode=0))
+    b_rgb, b_alpha, sb, wb = render_gpu(sc, cam, (0.1, 0.2, 0.3),
+                                        vis.make_opts(tile=tile, sort_mode=1, digit_bits=digit_bits))
+    assert int(vis.read_ctrl(wb.buf)["num_visible"]) > 100_000
+    va, ra, _ = _sorted_vals_and_ranges(sa, wa)
+    vb, rb, Lb = _sorted_vals_and_ranges(sb, wb)
+    assert np.array_equal(va, vb)
+    assert np.array_equal(_norm(ra), _norm(rb))
+    assert np.array_equal(a_rgb, b_rgb) and np.array_equal(a_alpha, b_alpha)
