@@ -144,7 +144,7 @@ typedef struct {
     size_t off_rect;         /* uint4[n] tile footprint: x0 | x1<<16, y0 | y1<<16 (the tile box,
                                 upper bounds exclusive), row trims Lt | Rt<<8 | Lb<<16 | Rb<<24
                                 (tiles dropped at the left / right ends of the top and bottom
-                                rows, see tile_extent 2), 0 */
+                                rows, see tile_extent 2), 0 (a fused batch: the image) */
     size_t off_touched;      /* uint32[n] tiles touched (0 if culled) */
     size_t off_keys[2];      /* key_bytes x cap: sort keys (see key_bytes); with key_bytes 2 the
                                 sorted keys are not stored (the tile of sorted position j is
@@ -331,21 +331,39 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
                           uint32_t* vals_out, int64_t m, int key_bits, void* ws, size_t ws_bytes,
                           void* stream);
 
-/* Batched render of many assets seen by many cameras (the paper renders several
- * models per frame, Algorithm 1 "for all model M_k"; here every (asset, camera) pair
- * is an independent image). A batch handle owns `lanes` streams. vis_render_batch
- * assigns the images to lanes (longest first, to the least loaded lane); each lane
- * renders its images one after another in its own slice of the workspace; the
- * whole fork / render / join sequence is captured into a CUDA graph on the first
- * call and replayed by later calls with identical arguments (same pointers, cameras,
- * sizes, options), so the lanes run as concurrent graph branches.
- *  scenes[n_scenes]        scene handles (host array)
+/* Batched render of many assets seen by many cameras (the paper renders several models
+ * per frame with one global radix sort, Algorithm 1 "for all model M_k", section 3.4);
+ * every (asset, camera) pair is an independent image. A batch handle is created with
+ * `lanes`:
+ *  lanes = 0   one fused pipeline over all images: one preprocess launch over the work
+ *              list of items (each image's Gaussians in their own run of workspace slots),
+ *              one depth sort of the survivors of every image, the tile copies emitted in
+ *              that order with global tile ids (each image's tiles numbered after the
+ *              previous image's), one stable sort by that id -- i.e. by (image, tile), keeping
+ *              depth order inside each tile --, the tile ranges, and one compositor launch
+ *              over all tiles of all images. It always uses the depth-first order
+ *              (opts->sort_mode is ignored); opts->tile, digit_bits and pixels_per_thread
+ *              apply to every image. key_capacity counts the tile copies of all images
+ *              together. Each image is bit-identical to vis_render of the same (asset,
+ *              camera, options).
+ *  lanes >= 1  per-image vis_render calls on that many streams forked from the batch's
+ *              origin stream (longest-processing-time assignment of images to lanes), each
+ *              lane in its own workspace slice of key_capacity keys.
+ * In both forms the whole launch sequence is captured into a CUDA graph on the first call
+ * and replayed by later calls with identical arguments (same pointers, cameras, sizes,
+ * options); the fused form also copies its item tables (a few hundred bytes per image)
+ * from host memory into the workspace before every launch.
+ *  scenes[n_scenes]        scene handles (host array; plain or pre-packed)
  *  cams[n_images]          host array of cameras; cam_scene[i] = asset of image i
  *  W, H[n_images]          host arrays of image sizes
  *  out_rgb, out_alpha      host arrays of n_images device pointers ([3][H][W], [H][W])
- *  ws, ws_bytes            device workspace >= vis_batch_workspace_size(...)
+ *  ws, ws_bytes            device workspace >= vis_batch_workspace_size(...) (256-byte
+ *                          aligned for lanes = 0); at most 65536 images and 2^31-1
+ *                          Gaussian slots in a fused batch
  * The first call synchronises nothing but must not itself be inside a stream capture.
- * Device errors of any image are returned by vis_batch_check (which synchronises). */
+ * Device errors of any image are returned by vis_batch_check (which synchronises); its
+ * max_keys is the largest image's key count (lanes >= 1) or the batch's total (lanes = 0),
+ * the capacity a retry needs. */
 typedef struct vis_batch* vis_batch_t;
 VIS_API vis_status vis_batch_create(int lanes, vis_batch_t* out);
 VIS_API void vis_batch_destroy(vis_batch_t batch);

@@ -578,10 +578,14 @@ class Batch:
     """Many (asset, camera) images rendered by one vis_render_batch call (a CUDA graph).
 
     scenes: list of Scene; cams: list of cameras; cam_scene: asset index per image.
-    Outputs are allocated here; the workspace has `lanes` slices of `key_capacity` keys.
+    lanes = 0 (default): one fused pipeline over all images (one preprocess over the work
+    list, one depth sort, one sort by (image, tile), one compositor over all tiles); the
+    workspace holds `key_capacity` tile copies of all images together. lanes >= 1: per-image
+    renders on that many concurrent lanes, each a workspace slice of `key_capacity` keys.
+    Outputs are allocated here.
     """
 
-    def __init__(self, scenes, cams, cam_scene, lanes=8, key_capacity=None, opts=None):
+    def __init__(self, scenes, cams, cam_scene, lanes=0, key_capacity=None, opts=None):
         torch = _torch()
         self.scenes, self.cams, self.cam_scene = list(scenes), list(cams), list(cam_scene)
         self.n = len(self.cams)
@@ -600,7 +604,11 @@ class Batch:
         self._rgb_p = (_P * self.n)(*[t.data_ptr() for t in self.rgb])
         self._a_p = (_P * self.n)(*[t.data_ptr() for t in self.alpha])
         if key_capacity is None:
-            key_capacity = max(1 << 16, 8 * max(s.n for s in self.scenes))
+            if self.lanes == 0:   # all images' copies: about 5 per Gaussian seen, grown on demand
+                slots = sum((self.scenes[a].n + 255) // 256 * 256 for a in self.cam_scene)
+                key_capacity = min((1 << 30) - 1, 5 * slots + (1 << 20))
+            else:
+                key_capacity = max(1 << 16, 8 * max(s.n for s in self.scenes))
         self._alloc(key_capacity)
 
     def _alloc(self, key_capacity):
@@ -635,7 +643,7 @@ class Batch:
             except VisError as e:
                 if e.status != VIS_ERR_CAPACITY:
                     raise
-                self._alloc(int(e.num_keys * 1.25) + 1024)
+                self._alloc(min((1 << 30) - 1, int(e.num_keys * 1.25) + 1024))
         raise VisError(VIS_ERR_CAPACITY, "batch workspace growth did not converge")
 
     def __del__(self):

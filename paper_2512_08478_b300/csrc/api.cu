@@ -235,6 +235,27 @@ void append_scene_key(std::vector<unsigned char>& key, vis_scene_t s) {
     key.insert(key.end(), c, c + sizeof(vis_scene));
 }
 
+vis_status batch_opts(const vis_render_opts* in, vis_render_opts* out) {
+    *out = resolve_opts(in);
+    return check_opts(*out);
+}
+
+vis_status batch_item(vis_scene_t s, const vis_camera* cam, int W, int H, const vis_render_opts& o, int64_t slot0,
+                      uint32_t image, PrepParams* out) {
+    if (!s) return fail(VIS_ERR_INVALID_ARG, "scene of image %u is null", image);
+    vis_status st = check_size(s->n, W, H);
+    if (st) return st;
+    if ((st = check_camera(cam))) return st;
+    const Layout L = make_layout(1, W, H, o.tile, 1, kSortDepthFirst, o.digit_bits);
+    *out = make_params(s, cam, W, H, L, o);
+    out->index_offset = slot0;
+    out->n_pad = (int)((s->n + kPrepThreads - 1) / kPrepThreads * kPrepThreads);
+    out->batch_image = image;
+    return VIS_OK;
+}
+
+bool scene_packed(vis_scene_t s) { return s && s->pk_pos != nullptr; }
+
 QScale q_scale() {
     const double c = 0.5 / std::log(2.0);   // log2(e) / 2
     return QScale{(float)(9.0 * c), (float)(1.0 / c)};

@@ -1,16 +1,28 @@
 // vis_render_batch -- many assets seen by many cameras in one call (the paper renders
-// several models per frame with one global sort, Algorithm 1; here each image is an
-// independent render, and the batch is one CUDA graph).
+// several models per frame with one global sort, Algorithm 1).
 //
-// Plan: images are assigned to `lanes` (streams forked from the batch's origin stream)
-// by longest-processing-time scheduling on the estimated cost (Gaussians + pixels);
-// each lane renders its images one after another in its own workspace slice, and
-// after every image a one-thread kernel copies the slice's status (key count, error
-// bits) into the image's status word, so no image's error is lost. The whole fork /
-// render / join sequence is captured once into a CUDA graph and replayed by later
-// calls with the same arguments: lanes become concurrent graph branches, so small
-// images of small assets overlap instead of leaving the GPU idle between launches.
+// Fused (a batch created with lanes = 0, the default of the Python binding): every
+// (asset, camera) image is one item of ONE pipeline over all of them --
+//   one preprocess launch over the work list of items (each item's Gaussians fill their
+//   own run of workspace slots, padded to whole blocks; the footprints record the image);
+//   one compaction of the survivors of every image and one depth sort of all of them;
+//   the tile copies emitted in that order with global tile ids (each image's tiles are
+//   numbered after the previous image's), and one stable sort by tile id, which yields
+//   (image, tile, depth, index) -- every image's own front-to-back order;
+//   the tile ranges, and one compositor launch over all tiles of all images, each CTA
+//   finding its image in the image table.
+// The whole sequence is captured once into a CUDA graph and replayed by later calls with
+// the same arguments; the item tables are uploaded before every launch. Each image is
+// bit-identical to vis_render of the same (asset, camera, options).
+//
+// Lanes (lanes >= 1, kept as a baseline): images are assigned to `lanes` streams forked
+// from the batch's origin stream by longest-processing-time scheduling on the estimated
+// cost (Gaussians + pixels); each lane renders its images one after another with
+// vis_render in its own workspace slice, and after every image a one-thread kernel
+// copies the slice's status into the image's status word. The fork / render / join
+// sequence is captured into a CUDA graph, so the lanes run as concurrent branches.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -19,7 +31,7 @@
 #include "vis_internal.cuh"
 
 struct vis_batch {
-    int lanes = 0;
+    int lanes = 0;                   // 0: the fused pipeline
     cudaStream_t origin = nullptr;   // the graph is captured on and launched from this stream
     cudaEvent_t in_ev = nullptr, out_ev = nullptr;
     std::vector<cudaStream_t> streams;
@@ -28,6 +40,8 @@ struct vis_batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<unsigned char> key;   // serialised arguments of the captured graph
     int device = -1;
+    std::vector<unsigned char> tables;   // fused: item and image tables, uploaded before each launch
+    size_t tables_off = 0;               // their offset in the workspace
 };
 
 namespace vis {
@@ -35,6 +49,16 @@ namespace vis {
 __global__ void copy_status_kernel(const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ status) {
     status[0] = ctrl->num_keys;
     status[1] = ctrl->error;
+}
+
+// fused batch: the one status block's key count (all images) and error bits into every
+// image's status word
+__global__ void copy_status_all_kernel(const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ status, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        status[2 * i] = ctrl->num_keys;
+        status[2 * i + 1] = ctrl->error;
+    }
 }
 
 }  // namespace vis
@@ -81,6 +105,117 @@ Plan make_plan(const vis_scene_t* scenes, const int* cam_scene, const int* W, co
     return p;
 }
 
+int ceil_log2_b(int64_t v) {
+    int b = 0;
+    while (((int64_t)1 << b) < v) ++b;
+    return b;
+}
+
+int64_t pad_blocks(int64_t n) { return (n + vis::kPrepThreads - 1) / vis::kPrepThreads * vis::kPrepThreads; }
+
+// Workspace of a fused batch: the status words (2 per image), the region cleared before
+// every launch (status block, digit histograms, look-back words, ranges of every tile of
+// every image), the tables (the items' preprocess parameters in list order -- plain scenes,
+// then pre-packed ones --, each list's first blocks, the image table), then the per-slot and
+// per-copy buffers of the depth-first order over all slots.
+struct Fused {
+    vis::Layout L;
+    int64_t slots = 0, total_tiles = 0;
+    int n_list[2] = {0, 0};           // images of the plain and of the pre-packed list
+    int64_t blocks[2] = {0, 0};       // preprocess blocks of each list
+    size_t off_items = 0, off_blk0 = 0, off_images = 0, tables_end = 0;
+};
+
+Fused fused_layout(const std::vector<int64_t>& n_img, const std::vector<char>& packed, const int* W, const int* H,
+                   int n_images, int tile, int64_t cap, int digit_bits) {
+    Fused F;
+    for (int i = 0; i < n_images; ++i) {
+        F.slots += pad_blocks(n_img[i]);
+        F.total_tiles += (int64_t)((W[i] + tile - 1) / tile) * ((H[i] + tile - 1) / tile);
+        F.n_list[packed[i] ? 1 : 0] += 1;
+        F.blocks[packed[i] ? 1 : 0] += pad_blocks(n_img[i]) / vis::kPrepThreads;
+    }
+    vis::Layout& L = F.L;
+    L.mode = vis::kSortDepthFirst;
+    L.n = F.slots;
+    L.tile = tile;
+    L.ntiles = F.total_tiles;
+    L.tile_bits = ceil_log2_b(F.total_tiles > 1 ? F.total_tiles : 2);
+    L.key_bits = L.tile_bits;
+    L.digit_bits = digit_bits;
+    L.depth_passes = vis::passes_for(32, digit_bits);
+    L.passes = vis::passes_for(L.tile_bits, digit_bits);
+    L.key_bytes = 4;
+    L.cap = cap;
+    L.prep_blocks = F.slots / vis::kPrepThreads;
+    L.sort_parts = (cap + (int64_t)vis::kSortThreads * 16 - 1) / ((int64_t)vis::kSortThreads * 16);
+    L.sorted_buffer = L.passes & 1;
+    L.tile_fused = false;
+    const size_t D = (size_t)1 << digit_bits;
+    size_t off = status_bytes(n_images);
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.zero_begin = off;
+    L.off_ctrl = take(sizeof(vis::Ctrl));
+    L.off_hist = take(sizeof(uint32_t) * vis::kMaxPasses * D);
+    L.off_hist_tile = take(sizeof(uint32_t) * vis::kMaxPasses * D);
+    L.lookback_words_depth = (size_t)L.depth_passes * vis::depth_sort_parts(F.slots, digit_bits) * D;
+    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * D));
+    L.off_ranges = take(sizeof(uint2) * (size_t)F.total_tiles);
+    L.zero_end = off;
+    F.off_items = take(sizeof(vis::PrepParams) * (size_t)n_images);
+    F.off_blk0 = take(sizeof(uint32_t) * (size_t)n_images);
+    F.off_images = take(sizeof(vis::BatchImage) * (size_t)n_images);
+    F.tables_end = off;
+    L.off_rec = take(sizeof(float4) * 3 * (size_t)F.slots);
+    L.off_depth = take(sizeof(float) * (size_t)F.slots);
+    L.off_rect = take(sizeof(uint4) * (size_t)F.slots);
+    L.off_touched = take(sizeof(uint32_t) * (size_t)F.slots);
+    L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    for (int k = 0; k < 2; ++k) L.off_dkeys[k] = take(sizeof(uint32_t) * (size_t)F.slots);
+    for (int k = 0; k < 2; ++k) L.off_dvals[k] = take(sizeof(uint32_t) * (size_t)F.slots);
+    for (int k = 0; k < 2; ++k) L.off_keys[k] = take(sizeof(uint32_t) * (size_t)cap);
+    for (int k = 0; k < 2; ++k) L.off_vals[k] = take(sizeof(uint32_t) * (size_t)cap);
+    L.total = off;
+    return F;
+}
+
+// Per-image sizes and kinds of a batch; VIS_ERR_INVALID_ARG on a bad image.
+vis_status fused_inputs(const vis_scene_t* scenes, int n_scenes, const int* cam_scene, const int* W, const int* H,
+                        int n_images, std::vector<int64_t>* n_img, std::vector<char>* packed) {
+    if (n_images > (1 << 16)) return fail_b(VIS_ERR_INVALID_ARG, "a fused batch holds at most 65536 images");
+    n_img->assign(n_images, 0);
+    packed->assign(n_images, 0);
+    int64_t slots = 0, tiles = 0;
+    for (int i = 0; i < n_images; ++i) {
+        if (cam_scene[i] < 0 || cam_scene[i] >= n_scenes || !scenes[cam_scene[i]])
+            return fail_b(VIS_ERR_INVALID_ARG, "cam_scene out of range");
+        if (W[i] < 1 || H[i] < 1 || W[i] > 16384 || H[i] > 16384)
+            return fail_b(VIS_ERR_INVALID_ARG, "image size out of [1, 16384]");
+        (*n_img)[i] = vis::scene_size(scenes[cam_scene[i]]);
+        (*packed)[i] = vis::scene_packed(scenes[cam_scene[i]]) ? 1 : 0;
+        slots += pad_blocks((*n_img)[i]);
+        tiles += (int64_t)((W[i] + 7) / 8) * ((H[i] + 7) / 8);
+    }
+    if (slots > 0x7fffffffLL) return fail_b(VIS_ERR_INVALID_ARG, "the batch's images hold more than 2^31-1 Gaussians");
+    if (tiles > 0x7fffffffLL) return fail_b(VIS_ERR_INVALID_ARG, "the batch's images hold more than 2^31-1 tiles");
+    return VIS_OK;
+}
+
+int64_t fused_capacity(const std::vector<int64_t>& n_img, const std::vector<char>& packed, const int* W, const int* H,
+                       int n_images, int tile, int digit_bits, size_t ws_bytes) {
+    if (fused_layout(n_img, packed, W, H, n_images, tile, 1, digit_bits).L.total > ws_bytes) return 0;
+    int64_t lo = 1, hi = vis::kMaxKeys;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (fused_layout(n_img, packed, W, H, n_images, tile, mid, digit_bits).L.total <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 void append(std::vector<unsigned char>& k, const void* p, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(p);
     k.insert(k.end(), c, c + n);
@@ -93,7 +228,7 @@ extern "C" {
 vis_status vis_batch_create(int lanes, vis_batch_t* out) {
     if (!out) return fail_b(VIS_ERR_INVALID_ARG, "out is null");
     *out = nullptr;
-    if (lanes < 1 || lanes > 64) return fail_b(VIS_ERR_INVALID_ARG, "lanes must be in [1, 64]");
+    if (lanes < 0 || lanes > 64) return fail_b(VIS_ERR_INVALID_ARG, "lanes must be in [0, 64]");
     vis_batch* b = new (std::nothrow) vis_batch;
     if (!b) return fail_b(VIS_ERR_INVALID_ARG, "out of host memory");
     b->lanes = lanes;
@@ -133,7 +268,20 @@ vis_status vis_batch_workspace_size(const vis_scene_t* scenes, int n_scenes, con
                                     const int* H, int n_images, int lanes, int64_t key_capacity,
                                     const vis_render_opts* opts, size_t* bytes) {
     if (!scenes || !cam_scene || !W || !H || !bytes) return fail_b(VIS_ERR_INVALID_ARG, "null argument");
-    if (n_images < 1 || n_scenes < 1 || lanes < 1) return fail_b(VIS_ERR_INVALID_ARG, "empty batch");
+    if (n_images < 1 || n_scenes < 1 || lanes < 0) return fail_b(VIS_ERR_INVALID_ARG, "empty batch");
+    if (lanes == 0) {   // fused: key_capacity counts the copies of all images together
+        vis_render_opts o;
+        vis_status st = vis::batch_opts(opts, &o);
+        if (st) return st;
+        if (key_capacity < 1 || key_capacity > (int64_t)vis::kMaxKeys)
+            return fail_b(VIS_ERR_INVALID_ARG, "key_capacity must be in [1, 2^30-1]");
+        std::vector<int64_t> n_img;
+        std::vector<char> packed;
+        if ((st = fused_inputs(scenes, n_scenes, cam_scene, W, H, n_images, &n_img, &packed))) return st;
+        *bytes = fused_layout(n_img, packed, W, H, n_images, o.tile, key_capacity, o.digit_bits).L.total;
+        vis::set_last_error("");
+        return VIS_OK;
+    }
     size_t slice = 0;
     for (int i = 0; i < n_images; ++i) {
         if (cam_scene[i] < 0 || cam_scene[i] >= n_scenes || !scenes[cam_scene[i]])
@@ -148,6 +296,114 @@ vis_status vis_batch_workspace_size(const vis_scene_t* scenes, int n_scenes, con
     return VIS_OK;
 }
 
+static vis_status render_fused(vis_batch_t b, const vis_scene_t* scenes, int n_scenes, const vis_camera* cams,
+                               const int* cam_scene, const int* W, const int* H, int n_images, const float bg[3],
+                               float* const* out_rgb, float* const* out_alpha, void* ws, size_t ws_bytes,
+                               const vis_render_opts* opts, cudaStream_t stream) {
+    vis_render_opts o;
+    vis_status st = vis::batch_opts(opts, &o);
+    if (st) return st;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(bg[k])) return fail_b(VIS_ERR_INVALID_ARG, "bg is not finite");
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return fail_b(VIS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    std::vector<int64_t> n_img;
+    std::vector<char> packed;
+    if ((st = fused_inputs(scenes, n_scenes, cam_scene, W, H, n_images, &n_img, &packed))) return st;
+    for (int i = 0; i < n_images; ++i)
+        if (!out_rgb[i] || !out_alpha[i] || (reinterpret_cast<uintptr_t>(out_rgb[i]) & 15u) ||
+            (reinterpret_cast<uintptr_t>(out_alpha[i]) & 15u))
+            return fail_b(VIS_ERR_INVALID_ARG, "image outputs null or not 16-byte aligned");
+    const int64_t cap = fused_capacity(n_img, packed, W, H, n_images, o.tile, o.digit_bits, ws_bytes);
+    if (cap < 1) return fail_b(VIS_ERR_INVALID_ARG, "batch workspace too small");
+    const Fused F = fused_layout(n_img, packed, W, H, n_images, o.tile, cap, o.digit_bits);
+    vis::Layout L = F.L;
+    L.spin_limit = o.spin_limit > 0 ? (uint32_t)o.spin_limit : vis::kSpinLimit;
+    char* w = static_cast<char*>(ws);
+
+    std::vector<unsigned char> key;
+    append(key, &o, sizeof(o));
+    append(key, &ws, sizeof(ws));
+    append(key, &ws_bytes, sizeof(ws_bytes));
+    append(key, bg, 3 * sizeof(float));
+    append(key, &n_images, sizeof(n_images));
+    for (int i = 0; i < n_images; ++i) {
+        append(key, &cams[i], sizeof(vis_camera));
+        append(key, &W[i], sizeof(int));
+        append(key, &H[i], sizeof(int));
+        append(key, &out_rgb[i], sizeof(float*));
+        append(key, &out_alpha[i], sizeof(float*));
+        vis::append_scene_key(key, scenes[cam_scene[i]]);
+    }
+    if (!b->exec || key != b->key) {
+        // the item tables: preprocess parameters in list order (plain scenes, then pre-packed
+        // ones), each list's first blocks, and the image table in image order
+        std::vector<vis::PrepParams> items(n_images);
+        std::vector<uint32_t> blk0(n_images);
+        std::vector<vis::BatchImage> images(n_images);
+        int pos[2] = {0, F.n_list[0]};
+        int64_t nb[2] = {0, 0}, slot0 = 0, tile0 = 0;
+        for (int i = 0; i < n_images; ++i) {
+            const int lst = packed[i] ? 1 : 0;
+            vis::PrepParams p;
+            if ((st = vis::batch_item(scenes[cam_scene[i]], &cams[i], W[i], H[i], o, slot0, (uint32_t)i, &p))) return st;
+            items[pos[lst]] = p;
+            blk0[pos[lst]] = (uint32_t)nb[lst];
+            ++pos[lst];
+            nb[lst] += pad_blocks(n_img[i]) / vis::kPrepThreads;
+            const int tx = (W[i] + o.tile - 1) / o.tile, ty = (H[i] + o.tile - 1) / o.tile;
+            vis::BatchImage im;
+            std::memset(&im, 0, sizeof(im));
+            im.slot0 = slot0; im.tile0 = (uint32_t)tile0; im.W = W[i]; im.H = H[i]; im.tiles_x = tx; im.tiles_y = ty;
+            im.out_rgb = out_rgb[i]; im.out_alpha = out_alpha[i];
+            images[i] = im;
+            slot0 += pad_blocks(n_img[i]);
+            tile0 += (int64_t)tx * ty;
+        }
+        b->tables.assign(F.tables_end - F.off_items, 0);
+        std::memcpy(b->tables.data(), items.data(), sizeof(vis::PrepParams) * n_images);
+        std::memcpy(b->tables.data() + (F.off_blk0 - F.off_items), blk0.data(), sizeof(uint32_t) * n_images);
+        std::memcpy(b->tables.data() + (F.off_images - F.off_items), images.data(), sizeof(vis::BatchImage) * n_images);
+        b->tables_off = F.off_items;
+        const vis::PrepParams* d_items = reinterpret_cast<const vis::PrepParams*>(w + F.off_items);
+        const uint32_t* d_blk0 = reinterpret_cast<const uint32_t*>(w + F.off_blk0);
+        const vis::BatchImage* d_images = reinterpret_cast<const vis::BatchImage*>(w + F.off_images);
+
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        cudaStream_t s = b->origin;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return fail_b(VIS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, s);
+        vis::launch_preprocess_batch(d_items, d_blk0, F.n_list[0], F.blocks[0], false, L, w, s);
+        vis::launch_preprocess_batch(d_items + F.n_list[0], d_blk0 + F.n_list[0], F.n_list[1], F.blocks[1], true, L,
+                                     w, s);
+        vis::launch_depth_first(L, w, s, nullptr, 0, d_images);
+        vis::launch_ranges32(L, w, s);
+        vis::launch_composite_batch(L, w, d_images, n_images, F.total_tiles, bg[0], bg[1], bg[2], o.alpha_min,
+                                    o.alpha_max, o.t_stop, o.pixels_per_thread, s);
+        vis::copy_status_all_kernel<<<(n_images + 255) / 256, 256, 0, s>>>(
+            reinterpret_cast<const vis::Ctrl*>(w + L.off_ctrl), reinterpret_cast<uint32_t*>(w), n_images);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) return fail_b(VIS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { b->exec = nullptr; return fail_b(VIS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+        b->key = key;
+    }
+    // order the tables and the graph after the caller's prior work, and the caller's later
+    // work after them
+    cudaError_t e = cudaEventRecord(b->in_ev, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->in_ev, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w + b->tables_off, b->tables.data(), b->tables.size(), cudaMemcpyHostToDevice, b->origin);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->origin);
+    if (e == cudaSuccess) e = cudaEventRecord(b->out_ev, b->origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->out_ev, 0);
+    if (e != cudaSuccess) return fail_b(VIS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    vis::set_last_error("");
+    return VIS_OK;
+}
+
 vis_status vis_render_batch(vis_batch_t b, const vis_scene_t* scenes, int n_scenes, const vis_camera* cams,
                             const int* cam_scene, const int* W, const int* H, int n_images, const float bg[3],
                             float* const* out_rgb, float* const* out_alpha, void* ws, size_t ws_bytes,
@@ -156,6 +412,9 @@ vis_status vis_render_batch(vis_batch_t b, const vis_scene_t* scenes, int n_scen
     if (!scenes || !cams || !cam_scene || !W || !H || !bg || !out_rgb || !out_alpha || !ws)
         return fail_b(VIS_ERR_INVALID_ARG, "null argument");
     if (n_images < 1 || n_scenes < 1) return fail_b(VIS_ERR_INVALID_ARG, "empty batch");
+    if (b->lanes == 0)
+        return render_fused(b, scenes, n_scenes, cams, cam_scene, W, H, n_images, bg, out_rgb, out_alpha, ws, ws_bytes,
+                            opts, reinterpret_cast<cudaStream_t>(stream_));
     const size_t sb = status_bytes(n_images);
     if (ws_bytes <= sb) return fail_b(VIS_ERR_INVALID_ARG, "batch workspace too small");
     const size_t slice = ((ws_bytes - sb) / b->lanes) / 256 * 256;

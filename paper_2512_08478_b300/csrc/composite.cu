@@ -44,14 +44,15 @@ __device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& 
     P.last = pos1;
 }
 
-template <int TILE, int PPT, bool STATS, bool DEPTH>
+template <int TILE, int PPT, bool STATS, bool DEPTH, bool BATCH>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                  const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0, float bg1,
                  float bg2, float alpha_min, float alpha_max, float t_stop, float qcut,
                  Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
                  float* __restrict__ t_final, int32_t* __restrict__ last_out,
-                 const float* __restrict__ depth, const float* __restrict__ zlim) {
+                 const float* __restrict__ depth, const float* __restrict__ zlim,
+                 const BatchImage* __restrict__ images, int n_images) {
     pdl_entry();
     constexpr int NT = TILE * TILE / PPT;   // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
@@ -63,7 +64,21 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     __shared__ uint32_t s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
     __shared__ float s_wmax[NW];   // DEPTH: largest depth limit of each warp block's live pixels
-    const int tile = blockIdx.x;
+    const uint32_t gtile = blockIdx.x;   // the tile's index in `ranges`
+    int tile = (int)gtile;
+    if (BATCH) {
+        // a batch's tiles are numbered image after image: find this tile's image (the last
+        // whose first tile is <= gtile) and take its size and outputs
+        int lo = 0, hi = n_images - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (images[mid].tile0 <= gtile) lo = mid; else hi = mid - 1;
+        }
+        const BatchImage im = images[lo];
+        tile = (int)(gtile - im.tile0);
+        W = im.W; H = im.H; tiles_x = im.tiles_x;
+        out_rgb = im.out_rgb; out_alpha = im.out_alpha;
+    }
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bx = warp % BX, by = warp / BX;
@@ -80,7 +95,8 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             if (px < W && py < H) {
                 const size_t pix = (size_t)py * W + px;
                 out_rgb[pix] = nan; out_rgb[HW + pix] = nan; out_rgb[2 * HW + pix] = nan;
-                out_alpha[pix] = nan; t_final[pix] = nan; last_out[pix] = 0;
+                out_alpha[pix] = nan;
+                if (!BATCH) { t_final[pix] = nan; last_out[pix] = 0; }
             }
         }
         return;
@@ -106,7 +122,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) s_wmax[warp] = m;
     }
-    const uint2 rg = ranges[tile];
+    const uint2 rg = ranges[gtile];
     for (uint32_t base = rg.x; base < rg.y; base += CH) {
         bool all_done = true;
 #pragma unroll
@@ -209,8 +225,10 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             out_rgb[HW + pix] = __fmaf_rn(P[r].T, bg1, P[r].C1);
             out_rgb[2 * HW + pix] = __fmaf_rn(P[r].T, bg2, P[r].C2);
             out_alpha[pix] = 1.f - P[r].T;
-            t_final[pix] = P[r].T;
-            last_out[pix] = P[r].last;
+            if (!BATCH) {   // the adjoint's inputs (a batch is forward only)
+                t_final[pix] = P[r].T;
+                last_out[pix] = P[r].last;
+            }
         }
     }
 }
@@ -229,9 +247,9 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
 #define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                \
-    launch_k(true, composite_kernel<TS, PP, ST, DT>, blocks, TS * TS / PP, 0, stream, ranges, vals, rec, L.W, L.H, \
-             L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin, last,  \
-             depth, zlim)
+    launch_k(true, composite_kernel<TS, PP, ST, DT, false>, blocks, TS * TS / PP, 0, stream, ranges, vals, rec, L.W, \
+             L.H, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin,    \
+             last, depth, zlim, (const BatchImage*)nullptr, 0)
 #define VIS_LAUNCH_COMPOSITE(TS, PP)                          \
     do {                                                      \
         if (zlim) VIS_LAUNCH_COMPOSITE_S(TS, PP, false, true);   \
@@ -244,6 +262,28 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     else { if (two) VIS_LAUNCH_COMPOSITE(16, 2); else VIS_LAUNCH_COMPOSITE(16, 1); }
 #undef VIS_LAUNCH_COMPOSITE
 #undef VIS_LAUNCH_COMPOSITE_S
+}
+
+void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images, int n_images, int64_t total_tiles,
+                            float bg0, float bg1, float bg2, float alpha_min, float alpha_max, float t_stop, int ppt,
+                            cudaStream_t stream) {
+    const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
+    const uint32_t* vals = reinterpret_cast<const uint32_t*>(ws + L.off_vals[L.sorted_buffer]);
+    const float4* rec = reinterpret_cast<const float4*>(ws + L.off_rec);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
+    if (total_tiles <= 0) return;
+    const int blocks = (int)total_tiles;
+    const float qcut = q_scale().qcut;
+    const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+#define VIS_LAUNCH_COMPOSITE_B(TS, PP)                                                                         \
+    launch_k(true, composite_kernel<TS, PP, false, false, true>, blocks, TS * TS / PP, 0, stream, ranges, vals, \
+             rec, 0, 0, 1, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,             \
+             (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images)
+    const bool two = ppt == 2;
+    if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE_B(8, 2); else VIS_LAUNCH_COMPOSITE_B(8, 1); }
+    else if (L.tile == 32) { if (two) VIS_LAUNCH_COMPOSITE_B(32, 2); else VIS_LAUNCH_COMPOSITE_B(32, 1); }
+    else { if (two) VIS_LAUNCH_COMPOSITE_B(16, 2); else VIS_LAUNCH_COMPOSITE_B(16, 1); }
+#undef VIS_LAUNCH_COMPOSITE_B
 }
 
 }  // namespace vis

@@ -74,17 +74,21 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
     }
 }
 
-// KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles
-template <typename KT>
+// KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles. BATCH (a fused batch):
+// the footprint's last word is the slot's image, whose tiles are numbered from
+// images[item].tile0 on a grid of images[item].tiles_x columns; otherwise tile ids are
+// y * tiles_x + x.
+template <typename KT, bool BATCH>
 __global__ void __launch_bounds__(kPrepThreads)
 emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, int64_t n,
            const uint32_t* __restrict__ boff, int tiles_x,
-           const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
+           const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals,
+           const BatchImage* __restrict__ images) {
     pdl_entry();
     if (ctrl->error) return;   // capacity exceeded, or a sort that timed out
     // per splat slot: start of its copies in the warp's run, and its footprint unrolled into
     // row segments: a = (index, first top-row tile, top width, end of the middle copies),
-    // b = (first middle tile, box width, first bottom-row tile, 0)
+    // b = (first middle tile, box width, first bottom-row tile, row stride)
     __shared__ uint32_t s_start[kPrepThreads];
     __shared__ uint4 s_a[kPrepThreads], s_b[kPrepThreads];
     __shared__ uint32_t warp_tot[kPrepThreads / 32];
@@ -95,14 +99,22 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, i
     uint4 sa = make_uint4(0, 0, 0, 0), sb = make_uint4(0, 1, 0, 0);
     const uint32_t g = j < nv ? dvals[j] : 0xffffffffu;
     if (g < (uint64_t)n) {   // one gather per splat
-        const Footprint f = fp_unpack(rect[g]);
+        const uint4 r = rect[g];
+        const Footprint f = fp_unpack(r);
         cnt = fp_count(f);
         if (cnt > 0) {
-            const uint32_t tx = (uint32_t)tiles_x, W = f.x1 - f.x0, rows = f.y1 - f.y0;
+            uint32_t tx = (uint32_t)tiles_x, t0 = 0;
+            if (BATCH) {
+                const BatchImage& im = images[r.w];
+                tx = (uint32_t)im.tiles_x;
+                t0 = im.tile0;
+            }
+            const uint32_t W = f.x1 - f.x0, rows = f.y1 - f.y0;
             const uint32_t wt = fp_top_width(f);
             const uint32_t mid = rows > 1 ? (rows - 2) * W : 0;
-            sa = make_uint4(g, f.y0 * tx + f.x0 + (f.trims & 0xffu), wt, wt + mid);
-            sb = make_uint4((f.y0 + 1) * tx + f.x0, W, (f.y1 - 1) * tx + f.x0 + ((f.trims >> 16) & 0xffu), 0u);
+            sa = make_uint4(g, t0 + f.y0 * tx + f.x0 + (f.trims & 0xffu), wt, wt + mid);
+            sb = make_uint4(t0 + (f.y0 + 1) * tx + f.x0, W, t0 + (f.y1 - 1) * tx + f.x0 + ((f.trims >> 16) & 0xffu),
+                            tx);
         }
     }
     const uint32_t incl = warp_incl_scan(cnt, lane);
@@ -115,7 +127,6 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, i
     for (int w = 0; w < warp; ++w) warp_base += warp_tot[w];
     const uint32_t run = warp_tot[warp];
     const int g0 = warp * 32;
-    const uint32_t tx = (uint32_t)tiles_x;
     for (uint32_t q = lane; q < run; q += 32) {
         // owner: the last slot of the warp whose start is <= q (it has copies: zero counts
         // share their start with the next slot)
@@ -135,7 +146,7 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, i
                 uint32_t r = (uint32_t)((float)kk * __frcp_rn((float)b.y));
                 if (r * b.y > kk) --r;
                 else if ((r + 1) * b.y <= kk) ++r;
-                tile = b.x + r * tx + (kk - r * b.y);
+                tile = b.x + r * b.w + (kk - r * b.y);
             } else {
                 tile = b.z + (k - a.w);               // bottom row
             }
@@ -192,7 +203,8 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
                                   L.spin_limit, L.digit_bits);
 }
 
-void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
+                        const BatchImage* images) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     const int blocks_n = (int)L.prep_blocks;
@@ -206,13 +218,13 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     launch_k(true, depth_touch_sums, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0, touched, L.n,
              (const Ctrl*)ctrl, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
-    if (L.tile_fused) {
+    if (L.tile_fused && !images) {
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
-        launch_k(true, emit_tiles<uint16_t>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
+        launch_k(true, emit_tiles<uint16_t, false>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
                  reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
                  (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
-                 reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
+                 reinterpret_cast<uint32_t*>(ws + L.off_vals[0]), (const BatchImage*)nullptr);
         if (mark) mark(mark_index, stream);
         launch_tile_counts(L, ws, stream);
         if (mark) mark(mark_index + 1, stream);
@@ -224,8 +236,14 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(dv0, reinterpret_cast<const uint4*>(ws + L.off_rect),
-                                                                L.n, boff2, L.tiles_x, ctrl, k0, v0);
+    if (images)   // a fused batch: global tile ids, image after image
+        launch_k(true, emit_tiles<uint32_t, true>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
+                 reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
+                 (const Ctrl*)ctrl, k0, v0, images);
+    else
+        emit_tiles<uint32_t, false><<<blocks_n, kPrepThreads, 0, stream>>>(
+            dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, boff2, L.tiles_x, ctrl, k0, v0,
+            (const BatchImage*)nullptr);
     if (mark) mark(mark_index, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer
     const int tp = L.passes;

@@ -58,15 +58,17 @@ __device__ __forceinline__ void screen_cov_packed(const float T0[3], const float
     det = q + dil * (a00 + a11) + dil * dil;
 }
 
-// ZCULL: a depth-tested render's occlusion cull against p.tile_zmax.
+// One block of the preprocess: Gaussians local_block * 256 + threadIdx.x of the scene of p.
+// ZCULL: a depth-tested render's occlusion cull against p.tile_zmax. `item` goes into the
+// footprint's last word (the image of a fused batch; 0 otherwise).
 template <bool FOLDED, bool PACKED, bool ZCULL>
-__global__ void __launch_bounds__(kPrepThreads, 5)
-preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
-                  uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
-                  uint32_t* __restrict__ block_sums) {
+__device__ __forceinline__ void preprocess_block(const PrepParams& p, int local_block, uint32_t item,
+                                                 float4* __restrict__ rec, float* __restrict__ depth_out,
+                                                 uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
+                                                 uint32_t* __restrict__ block_sums) {
     // i: the Gaussian in the scene's arrays; gi: its slot in the workspace (a multi-scene
     // render places scene k at index_offset = the sum of the earlier scenes' padded sizes)
-    const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+    const int i = local_block * kPrepThreads + threadIdx.x;
     const int gi = (int)p.index_offset + i;   // slots number at most 2^31 - 1
     __shared__ float s_trim[7][kPrepThreads];
     uint32_t touched = 0;
@@ -362,10 +364,10 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
             }
         }
         if (touched == 0) { x0 = x1 = y0 = y1 = 0; trims = 0; }
-        rect_out[gi] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, 0u);
+        rect_out[gi] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, item);
         touched_out[gi] = touched;
-    } else if (i < p.n_pad) {   // padding slots of a multi-scene render: no copies
-        rect_out[gi] = make_uint4(0u, 0u, 0u, 0u);
+    } else if (i < p.n_pad) {   // padding slots of a multi-scene render or a batch: no copies
+        rect_out[gi] = make_uint4(0u, 0u, 0u, item);
         touched_out[gi] = 0u;
     }
     // block sum of tiles touched (for the offset scan of the index-order duplication) or, for
@@ -380,8 +382,61 @@ preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ de
         uint32_t tot = 0;
 #pragma unroll
         for (int w = 0; w < kPrepThreads / 32; ++w) tot += warp_sums[w];
-        block_sums[p.index_offset / kPrepThreads + blockIdx.x] = tot;
+        block_sums[p.index_offset / kPrepThreads + local_block] = tot;
     }
+}
+
+template <bool FOLDED, bool PACKED, bool ZCULL>
+__global__ void __launch_bounds__(kPrepThreads, 5)
+preprocess_kernel(PrepParams p, float4* __restrict__ rec, float* __restrict__ depth_out,
+                  uint4* __restrict__ rect_out, uint32_t* __restrict__ touched_out,
+                  uint32_t* __restrict__ block_sums) {
+    preprocess_block<FOLDED, PACKED, ZCULL>(p, (int)blockIdx.x, 0u, rec, depth_out, rect_out, touched_out,
+                                            block_sums);
+}
+
+// The preprocess of a fused batch: one launch over the work list of every (asset, camera)
+// item. Block b belongs to the item whose first block blk0[item] is the last <= b; the
+// item's parameters (scene arrays, camera, image size, workspace slots) are read into
+// shared memory and the block runs as block b - blk0[item] of that item's preprocess. This
+// file is compiled without floating-point contraction (every a * b + c not written as an
+// fma is a rounded product and a rounded sum), so that the arithmetic cannot depend on
+// where the parameters live: a batch's images are bit for bit those of plain renders.
+static_assert(sizeof(PrepParams) % 4 == 0, "parameters copied as words");
+template <bool PACKED>
+__global__ void __launch_bounds__(kPrepThreads, 5)
+preprocess_batch_kernel(const PrepParams* __restrict__ items, const uint32_t* __restrict__ blk0, int n_items,
+                        float4* __restrict__ rec, float* __restrict__ depth_out, uint4* __restrict__ rect_out,
+                        uint32_t* __restrict__ touched_out, uint32_t* __restrict__ block_sums) {
+    pdl_entry();
+    __shared__ PrepParams sp;
+    __shared__ int s_item;
+    const uint32_t b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_items - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (blk0[mid] <= b) lo = mid; else hi = mid - 1;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const int item = s_item;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(items + item);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
+    for (int k = threadIdx.x; k < (int)(sizeof(PrepParams) / 4); k += kPrepThreads) dst[k] = src[k];
+    __syncthreads();
+    preprocess_block<false, PACKED, false>(sp, (int)(b - blk0[item]), sp.batch_image, rec, depth_out, rect_out,
+                                           touched_out, block_sums);
+}
+
+void launch_preprocess_batch(const PrepParams* items, const uint32_t* blk0, int n_items, int64_t blocks,
+                             bool packed, const Layout& L, char* ws, cudaStream_t stream) {
+    if (n_items <= 0 || blocks <= 0) return;
+    launch_k(false, packed ? preprocess_batch_kernel<true> : preprocess_batch_kernel<false>, (unsigned)blocks,
+             kPrepThreads, 0, stream, items, blk0, n_items, reinterpret_cast<float4*>(ws + L.off_rec),
+             reinterpret_cast<float*>(ws + L.off_depth), reinterpret_cast<uint4*>(ws + L.off_rect),
+             reinterpret_cast<uint32_t*>(ws + L.off_touched), reinterpret_cast<uint32_t*>(ws + L.off_bsum));
 }
 
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream) {

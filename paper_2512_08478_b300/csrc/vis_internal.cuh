@@ -145,6 +145,20 @@ struct PrepParams {
     int64_t index_offset;    // workspace slot of the scene's first Gaussian (a multiple of kPrepThreads)
     int n_pad;               // n rounded up to kPrepThreads in a multi-scene render (else n)
     float shc[12];           // SH polynomial constants, see sh_constants()
+    uint32_t batch_image;    // a fused batch: the item's image index (kept in the footprints)
+    uint32_t pad1;
+};
+
+// One image of a fused batch (vis_render_batch with lanes = 0): its (asset, camera) item's
+// Gaussians occupy the workspace slots [slot0, slot0 + n) and its tiles the global tile
+// ids [tile0, tile0 + tiles_x * tiles_y); images are listed in increasing tile0.
+struct BatchImage {
+    int64_t slot0;
+    uint32_t tile0;
+    int W, H, tiles_x, tiles_y;
+    int pad0;
+    float* out_rgb;     // [3][H][W]
+    float* out_alpha;   // [H][W]
 };
 
 // SH polynomial constants from the normalisation K_l^m (computed in double).
@@ -251,6 +265,11 @@ inline bool set_up_per_device(std::atomic<uint64_t>& done, std::mutex& mu, F set
 
 // Launchers (host side, enqueue on `stream`).
 void launch_preprocess(const PrepParams& p, const Layout& L, char* ws, cudaStream_t stream);
+// The preprocess of a fused batch over its work list: items[k] (device) are the items'
+// parameters, blk0[k] (device, n_items entries) their first blocks, `blocks` the total;
+// only plain (packed = false) or only pre-packed scenes per launch.
+void launch_preprocess_batch(const PrepParams* items, const uint32_t* blk0, int n_items, int64_t blocks,
+                             bool packed, const Layout& L, char* ws, cudaStream_t stream);
 // Per-tile maximum of a depth buffer zlim [H,W] into ws + L.off_zmax.
 void launch_tile_zmax(const Layout& L, char* ws, const float* zlim, cudaStream_t stream);
 // Pre-pack (Algorithm 1, once per scene): fp32 SoA attributes -> fp16 planes pos, cov, col.
@@ -266,8 +285,10 @@ void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
                       int64_t cap, cudaStream_t stream);
 // Depth-first mode: compaction, depth sort, emission (then mark(3)), tile sort (mark(4)
-// after its histogram). Ranges for its 32-bit tile keys:
-void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
+// after its histogram). With `images` (a fused batch; the footprints carry their image) the
+// copies take global tile ids and the 32-bit tile sort runs. Ranges for its 32-bit tile keys:
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
+                        const BatchImage* images = nullptr);
 // Compaction of the surviving splats and their stable sort by depth (result in dvals[0]).
 void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream);
 void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
@@ -281,6 +302,11 @@ QScale q_scale();
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       const float* zlim, cudaStream_t stream);
+// Compositor over every tile of a fused batch (global tile ids, image table `images` in
+// device memory), forward only.
+void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images, int n_images, int64_t total_tiles,
+                            float bg0, float bg1, float bg2, float alpha_min, float alpha_max, float t_stop, int ppt,
+                            cudaStream_t stream);
 // Adjoint of the compositing: clears and accumulates the screen-space gradients g2 of
 // all L.n slots (zlim as in launch_composite).
 void launch_composite_backward(const Layout& L, char* ws, const float bg[3], float alpha_min, float alpha_max,
@@ -326,6 +352,13 @@ void launch_dynamic_update(const float* means0, const float* velocity, const flo
 // Scene accessors for the batch planner (the scene struct is private to api.cu).
 int64_t scene_size(vis_scene_t s);
 void append_scene_key(std::vector<unsigned char>& key, vis_scene_t s);
+bool scene_packed(vis_scene_t s);
+// Render options with the defaults filled in, validated (sets the error message).
+vis_status batch_opts(const vis_render_opts* in, vis_render_opts* out);
+// Validated preprocess parameters of image `image` of a fused batch: scene s seen by cam at
+// W x H, its Gaussians at workspace slots slot0 .. (a multiple of kPrepThreads).
+vis_status batch_item(vis_scene_t s, const vis_camera* cam, int W, int H, const vis_render_opts& o, int64_t slot0,
+                      uint32_t image, PrepParams* out);
 
 // Sets the thread-local message returned by vis_last_error().
 void set_last_error(const char* msg);

@@ -1,10 +1,10 @@
-"""Autotuner for batched renders: picks tile size, compositor block shape, sort mode
-and lane count for a batch signature by timing the candidates on the device.
+"""Autotuner for batched renders: picks the tile size, the radix digit width and the
+compositor block shape of a fused batch (one pipeline over all images) for a batch
+signature by timing every candidate on the device.
 
-Only configuration is searched here; every candidate runs the library's kernels. The
-radix digit width is fixed at 8 bits (the only width the library implements), so it
-is reported but not searched. Results are cached in a JSON file keyed by GPU name and
-batch signature (asset sizes and SH degrees, image sizes).
+Only configuration is searched here; every candidate runs the library's kernels. Results
+are cached in a JSON file keyed by GPU name and batch signature (asset sizes and SH
+degrees, image sizes).
 """
 from __future__ import annotations
 
@@ -15,7 +15,9 @@ from pathlib import Path
 
 DEFAULT_CACHE = Path(os.environ.get("XDG_CACHE_HOME", str(Path.home() / ".cache"))) / "vis_autotune.json"
 
-CANDIDATES = dict(tile=(8, 16, 32), pixels_per_thread=(1, 2), sort_mode=(0, 1), lanes=(4, 8, 16))
+# tile edge (px), radix digit width of the depth sort and the (image, tile) sort, and pixels
+# per compositor thread (block shape)
+CANDIDATES = dict(tile=(8, 16, 32), digit_bits=(8, 10, 11), pixels_per_thread=(1, 2))
 
 
 def signature(scenes, cams, cam_scene) -> str:
@@ -40,7 +42,8 @@ def _time_batch(b, reps):
 
 
 def autotune(scenes, cams, cam_scene, candidates=None, reps=3, cache: Path | None = DEFAULT_CACHE, log=None):
-    """Return (opts dict, lanes, ms) of the fastest candidate; cached per GPU and signature."""
+    """Return (opts dict, ms) of the fastest candidate of a fused batch; cached per GPU and
+    batch signature."""
     import torch
     import paper_2512_08478_b300 as vis
     cand = dict(CANDIDATES)
@@ -53,22 +56,21 @@ def autotune(scenes, cams, cam_scene, candidates=None, reps=3, cache: Path | Non
             table = json.loads(Path(cache).read_text())
         except ValueError:
             table = {}
-    if key in table:
+    if key in table and "digit_bits" in table[key].get("opts", {}):
         r = table[key]
-        return r["opts"], r["lanes"], r["ms"]
+        return r["opts"], r["ms"]
     best = None
-    for tile, ppt, mode, lanes in itertools.product(cand["tile"], cand["pixels_per_thread"], cand["sort_mode"],
-                                                    cand["lanes"]):
-        opts = dict(tile=tile, pixels_per_thread=ppt, sort_mode=mode)
-        b = vis.Batch(scenes, cams, cam_scene, lanes=lanes, opts=vis.make_opts(**opts))
+    for tile, digit_bits, ppt in itertools.product(cand["tile"], cand["digit_bits"], cand["pixels_per_thread"]):
+        opts = dict(tile=tile, digit_bits=digit_bits, pixels_per_thread=ppt)
+        b = vis.Batch(scenes, cams, cam_scene, lanes=0, opts=vis.make_opts(**opts))
         ms = _time_batch(b, reps)
         del b
         if log:
-            log(f"autotune tile={tile} ppt={ppt} sort_mode={mode} lanes={lanes}: {ms:.3f} ms")
-        if best is None or ms < best[2]:
-            best = (opts, lanes, ms)
+            log(f"autotune tile={tile} digit_bits={digit_bits} ppt={ppt}: {ms:.3f} ms")
+        if best is None or ms < best[1]:
+            best = (opts, ms)
     if cache is not None:
-        table[key] = dict(opts=best[0], lanes=best[1], ms=best[2], digit_bits=8)
+        table[key] = dict(opts=best[0], ms=best[1])
         Path(cache).parent.mkdir(parents=True, exist_ok=True)
         Path(cache).write_text(json.dumps(table, indent=1))
     return best

@@ -14,12 +14,13 @@ def test_autotune_picks_the_fastest_and_caches(tmp_path, monkeypatch):
 
     class FakeBatch:
         def __init__(self, scenes, cams, cam_scene, lanes, opts):
-            self.key = (opts.tile, opts.pixels_per_thread, opts.sort_mode, lanes)
+            assert lanes == 0   # the tuner times the fused pipeline
+            self.key = (opts.tile, opts.digit_bits, opts.pixels_per_thread)
             made.append(self.key)
 
     def fake_time(b, reps):
-        t, ppt, mode, lanes = b.key
-        return 1.0 + 0.1 * abs(t - 16) + 0.05 * ppt + 0.2 * mode + 0.01 * abs(lanes - 8)
+        t, digit_bits, ppt = b.key
+        return 1.0 + 0.1 * abs(t - 16) + 0.01 * abs(digit_bits - 10) + 0.05 * ppt
 
     monkeypatch.setattr(vis, "Batch", FakeBatch)
     monkeypatch.setattr(tuning, "_time_batch", fake_time)
@@ -27,21 +28,21 @@ def test_autotune_picks_the_fastest_and_caches(tmp_path, monkeypatch):
     scenes = [SimpleNamespace(n=1000, sh_degree=3), SimpleNamespace(n=50, sh_degree=0)]
     cams = [SimpleNamespace(W=64, H=48), SimpleNamespace(W=32, H=32)]
     cache = tmp_path / "tune.json"
-    opts, lanes, ms = tuning.autotune(scenes, cams, [0, 1], cache=cache)
+    opts, ms = tuning.autotune(scenes, cams, [0, 1], cache=cache)
     n_cand = 1
     for v in tuning.CANDIDATES.values():
         n_cand *= len(v)
     assert len(made) == n_cand
-    assert opts == dict(tile=16, pixels_per_thread=1, sort_mode=0) and lanes == 8
+    assert opts == dict(tile=16, digit_bits=10, pixels_per_thread=1)
     assert abs(ms - 1.05) < 1e-12
     table = json.loads(cache.read_text())
     assert len(table) == 1 and next(iter(table)).startswith("FakeGPU|")
     made.clear()
     again = tuning.autotune(scenes, cams, [0, 1], cache=cache)
-    assert made == [] and again == (opts, lanes, ms)
+    assert made == [] and again == (opts, ms)
     # another batch signature is tuned afresh
-    tuning.autotune(scenes[:1], cams[:1], [0], cache=cache, candidates=dict(tile=(16,), lanes=(8,)))
-    assert len(made) == 4 and len(json.loads(cache.read_text())) == 2
+    tuning.autotune(scenes[:1], cams[:1], [0], cache=cache, candidates=dict(tile=(16,), pixels_per_thread=(1,)))
+    assert len(made) == 3 and len(json.loads(cache.read_text())) == 2
 
 
 def test_signature_depends_on_sizes_degrees_and_images():
