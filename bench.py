@@ -1,21 +1,29 @@
 """Benchmark of the B300 3DGS rasterizer; prints ONE JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload 1m|6m|fwdbwd|small]
+                    [--workload 1m|6m|fwdbwd|small|batch|multi] [--no-legs]
 
-A step is one pass of the whole hot path over one frame: preprocess, key
-duplication, radix sort, tile ranges and compositing of one view (fwdbwd: plus
-the adjoint). The default workload is 1M Gaussians with SH degree 3 seen from a
-32-camera orbit at 1920x1080 (steps cycle through the views); the attribute
-arrays (236 MB) exceed the 126 MB L2, so no flush is needed between steps.
+A step is one pass of the whole hot path over one frame: preprocess, depth sort of
+the surviving splats, emission of their tile copies, tile sort, and compositing of
+one view (fwdbwd: plus the adjoint). The default workload is 1M Gaussians with SH
+degree 3 seen from a 32-camera orbit at 1920x1080 (steps cycle through the views);
+the attribute arrays (236 MB) exceed the 126 MB L2, so no flush is needed between
+steps.
 
 value      frame time in ms (whole job: max-over-ranks time / frames of all ranks),
            inputs resident in HBM, CUDA events on the launching stream.
 e2e        the same through the C ABI with host buffers: every step copies the
            scene from pinned host memory, renders, and reads the image back.
-roofline   the stage that dominates the frame, against the measured HBM copy
-           bandwidth (MEASURED_PEAKS.json), algorithmic bytes per launch over the
-           CUDA-event launch time.
+roofline   the stage that dominates the frame: against the measured HBM copy
+           bandwidth (MEASURED_PEAKS.json) for the HBM-bound stages, algorithmic
+           bytes per launch over the CUDA-event launch time; against the FP32 issue
+           rate for the compositor (15 instructions per (pixel, splat) test).
+hbm_stages every HBM-bound stage (preprocess, depth sort, emission, tile sort)
+           against the copy peak.
+legs       (default run) the metric's other legs, each with its own clocks: the 6M
+           dynamic frame, the 500k forward + backward step, and the 128-image batch
+           (fused pipeline, autotuned) against the 8-lane graph and 128 sequential
+           renders.
 cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same
            frame (a stride of its tiles), scaled to a frame.
 --impl reference   times that oracle alone as the reference arm.
@@ -37,18 +45,11 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-kDP = 4   # depth passes of sort_mode 1
-METRIC = "1080p frame ms at 1M/6M Gaussians SH3; fwd+bwd ms; sort keys/s vs HBM peak"
-STAGES = ["clear", "preprocess", "duplicate", "sort_histogram", "sort_passes", "ranges", "composite"]
-# sort_mode 1 (depth first): "duplicate" = compaction + depth sort + emission in depth order,
-# "sort_histogram"/"sort_passes" = the stable sort by tile id of 4-byte keys
-STAGES_DF = ["clear", "preprocess", "depth_sort_and_emit", "tile_sort_histogram", "tile_sort_passes", "ranges",
+# per-stage times of vis_profile_end (8 stages), by sort mode
+STAGES_DF = ["clear", "preprocess", "depth_sort", "emission", "tile_counts", "tile_sort_passes", "ranges",
              "composite"]
-# sort_mode 1 with the counts-first tile sort (16-bit tile keys): stage 2 = compaction, depth sort
-# and emission in depth order; stage 3 = per-tile counts (histograms, ranges); stage 4 = the tile
-# passes; no ranges stage
-STAGES_FUSED = ["clear", "preprocess", "depth_sort_and_emit", "tile_counts", "tile_sort_passes", "ranges",
-                "composite"]
+STAGES_TD = ["clear", "preprocess", "duplicate", "sort_histogram", "none", "sort_passes", "ranges", "composite"]
+METRIC = "1080p frame ms at 1M/6M Gaussians SH3; fwd+bwd ms; sort keys/s vs HBM peak"
 
 
 def _peaks():
@@ -172,31 +173,53 @@ class ClockSampler:
 # our arm
 # ------------------------------------------------------------------------------------------
 
-def run_ours(args):
+def _kernel_sha(files):
+    """Hash of the kernel sources a committed ncu capture was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update((ROOT / "paper_2512_08478_b300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def _committed_traffic(stage, M, n):
+    """DRAM bytes (read + write) per launch of the stage's kernel from a committed ncu capture
+    (profiles/traffic.json), scaled to this launch by keys or Gaussians; None if absent or if
+    the kernel's source changed since the capture (the entry records the sources' hash)."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text()).get(stage)
+    if not d or "sources" not in d or d.get("source_sha") != _kernel_sha(d["sources"]):
+        return None
+    if "bytes_per_key" in d:
+        return int(d["bytes_per_key"] * M)
+    if "bytes_per_gaussian" in d:
+        return int(d["bytes_per_gaussian"] * n)
+    return None
+
+
+def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
+    """Times `args.steps` frames of `workload` (after `args.warmup`), with per-stage times from
+    a second pass, the dominant stage's roofline and the HBM-bound stages against the copy
+    peak; returns the result line (dict)."""
     import torch
     import paper_2512_08478_b300 as vis
 
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    sc_np, cams, desc, extra = load_workload(args.workload)
+    sc_np, cams, desc, extra = load_workload(workload)
     desc["tile"] = args.tile
     W, H = desc["width"], desc["height"]
     sc = vis.Scene.from_numpy(sc_np)
     n = sc.n
     cap = 16 * n + (1 << 20)
-    if args.sort_mode is None:
-        args.sort_mode = vis.make_opts().sort_mode
-    opts = vis.make_opts(sort_mode=args.sort_mode, tile=args.tile, pixels_per_thread=args.ppt)
+    sort_mode = args.sort_mode if args.sort_mode is not None else vis.make_opts().sort_mode
+    opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt)
     ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
     stream = torch.cuda.current_stream()
-    fwdbwd = args.workload == "fwdbwd"
+    fwdbwd = workload == "fwdbwd"
     if fwdbwd:
         tgt = vis.Scene.from_numpy(extra)
         tgt_rgb = torch.empty_like(rgb)
@@ -217,7 +240,7 @@ def run_ours(args):
     # test without writes; the buffer stands in for an opaque mesh's depth prepass)
     dbuf = (torch.full((H, W), float(args.depth_plane), dtype=torch.float32, device="cuda")
             if args.depth_plane is not None else None)
-    dynamic = args.workload == "6m" and not packed
+    dynamic = workload == "6m" and not packed
     if dynamic:
         dyn = {k: torch.from_numpy(v).cuda() for k, v in extra.items()}
         means0 = sc.tensors["means"].clone()
@@ -248,7 +271,7 @@ def run_ours(args):
 
     for i in range(args.warmup):
         frame(i)
-    num_keys = vis.vis_check(ws.buf)
+    vis.vis_check(ws.buf)
 
     # ---- device-timed region ----
     if dist:
@@ -256,7 +279,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    keys_seen = []
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for i in range(args.steps):
@@ -265,6 +287,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     vis.vis_check(ws.buf)
     t_ms = ev0.elapsed_time(ev1)
+    clk_summary = clk.summary()
     # per-stage times: the same frames once more with events between the stages, outside the
     # timed region (an event between two kernels stops the second one's early launch)
     import ctypes as C
@@ -272,25 +295,25 @@ def run_ours(args):
     for i in range(args.steps):
         frame(i, timed=True)
     torch.cuda.synchronize()
-    stage = (C.c_double * 7)()
+    stage = (C.c_double * 8)()
     ns, nr, npass = C.c_int(), C.c_int(), C.c_int()
-    vis._ok(vis.lib().vis_profile_end(stage, 7, C.byref(ns), C.byref(nr), C.byref(npass)))
+    vis._ok(vis.lib().vis_profile_end(stage, 8, C.byref(ns), C.byref(nr), C.byref(npass)))
     vis.vis_check(ws.buf)
     t_ms = max_over_ranks(t_ms, dist, "cuda")
     frames_total = args.steps * world
     value = t_ms / frames_total
-    stage_ms = {STAGES[k]: stage[k] / max(nr.value, 1) for k in range(7)}
+    names = STAGES_DF if sort_mode == 1 else STAGES_TD
+    stage_ms = {names[k]: stage[k] / max(nr.value, 1) for k in range(8)}
     update_ms = (sum(a.elapsed_time(b) for a, b in upd_ev) / args.steps) if dynamic else None
-    fused = ws.layout().key_bytes == 2
-    names = STAGES_FUSED if fused else {0: STAGES, 1: STAGES_DF}[args.sort_mode]
+    lay = ws.layout()
+    fused = lay.key_bytes == 2
     passes = npass.value
 
-    # keys per frame averaged over the views used
-    # and the preprocess traffic each view requires: every Gaussian is read for the depth and
-    # cull test, only those in front (z > near, opacity >= alpha_min) for the covariance, and
-    # only the survivors (tiles touched > 0) for their SH coefficients and splat record
+    # keys per frame averaged over the views used, and the preprocess traffic each view needs:
+    # every Gaussian is read for the depth and cull test, only those in front (z > near,
+    # opacity >= alpha_min) for the covariance, and only the survivors (tiles touched > 0) for
+    # their SH coefficients and splat record
     mlist, nvis, nok = [], [], []
-    lay = ws.layout()
     opac = torch.sigmoid(sc.tensors["opacity_logits"].reshape(-1))
     a_min = float(np.float32(vis.make_opts().alpha_min))
     for i in range(min(args.steps, len(cam_objs))):
@@ -304,152 +327,198 @@ def run_ours(args):
     M = float(np.mean(mlist))
     n_vis, n_ok = float(np.mean(nvis)), float(np.mean(nok))
 
-    # ---- roofline of the dominant stage ----
+    # ---- algorithmic bytes of the HBM-bound stages ----
     peaks = _peaks()
-    cands = ("preprocess", "sort_passes", "composite")
-    dom = max(cands, key=lambda s: stage_ms[s])
     sh_k = (desc["sh_degree"] + 1) ** 2
-    # means + logit read, depth + rect + count written: 32 B each; quaternion + log-scales: 28 B
-    # for the Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
+    # means + logit read, depth + rect + count written: 40 B; quaternion + log-scales: 28 B for the
+    # Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
     bytes_pre = n * 40 + n_ok * 28 + n_vis * (12 * sh_k + 48)
     if packed:   # fp16 planes: pos 8 B for all, cov 12 B in front, colour words per survivor
         bytes_pre = n * 32 + n_ok * 12 + n_vis * (vis.vis_packed_size(1, desc["sh_degree"])[2] + 48)
-    # bytes the tile sort must move: per digit pass key + value read and written; with the fused
-    # binning the first pass reads 16 B per surviving splat (first copy, index, rect) and writes a
-    # 2 B key + 4 B value per copy, the last reads those and writes the 4 B value
-    # 16-bit keys: every pass reads 2 + 4 B per copy and writes 2 + 4 B, the last only the 4 B value
-    tile_bytes = (M * (12 * passes - 2)) if fused else M * (24.0 if args.sort_mode == 0 else 16.0) * passes
-    if dom == "sort_passes" and fused:
-        launch_ms = stage_ms["sort_passes"] / passes
-        algo = tile_bytes / passes
-        unit_note = ("mean over the tile passes: 2 B key + 4 B value read and written per copy, "
-                     "the last pass writes the value only")
-    elif dom == "sort_passes":
-        launch_ms = stage_ms["sort_passes"] / passes
-        per_key = 24.0 if args.sort_mode == 0 else 16.0
-        algo = per_key * M
-        unit_note = (f"{int(per_key)} B per key per digit pass ({'8' if args.sort_mode == 0 else '4'} B key + "
-                     f"4 B value, read and written)")
-    elif dom == "preprocess":
-        launch_ms = stage_ms["preprocess"]
-        algo = float(bytes_pre)
-        unit_note = ("40 B per Gaussian (means, logit, depth, rect, count) + 28 B per Gaussian in front "
-                     "(quaternion, log-scales) + SH and 48 B record per surviving splat")
-        if packed:
-            unit_note = ("32 B per Gaussian (fp16 mean + opacity, depth, rect, count) + 12 B fp16 covariance per "
-                         "Gaussian in front + fp16 SH words and 48 B record per surviving splat")
+    hbm = {"preprocess": (bytes_pre, stage_ms["preprocess"],
+                          "40 B per Gaussian + 28 B per Gaussian in front + SH and 48 B record per survivor")}
+    if sort_mode == 1:
+        dp = 4   # 8-bit digit passes of the depth sort
+        # compaction: count + depth read per Gaussian, (depth, index) written per survivor; the
+        # depth histogram reads 4 B per survivor; each pass reads and writes 8 B per survivor
+        hbm["depth_sort"] = (8 * n + 8 * n_vis + 4 * n_vis + 16 * dp * n_vis, stage_ms["depth_sort"],
+                             "compaction 8 B per Gaussian + 8 B per survivor, histogram 4 B and 4 passes of "
+                             "16 B per survivor")
+        # touch sums and emission: index + count, then index + footprint per survivor; 2 B tile id
+        # + 4 B index written per copy
+        hbm["emission"] = (28 * n_vis + 6 * M, stage_ms["emission"],
+                           "28 B per survivor (indices, counts, footprints) + 6 B per copy written")
+        # per-tile counts: footprint read per Gaussian; passes: 2 + 4 B read and written per copy,
+        # the last writes the 4 B value only
+        tile_b = 16 * n + M * (12 * passes - 2) if fused else 16 * n + M * 16 * passes
+        hbm["tile_sort"] = (tile_b, stage_ms["tile_counts"] + stage_ms["tile_sort_passes"],
+                            "16 B footprint per Gaussian + 12 B per copy per pass (the last pass 10 B)")
+        sort_ms = stage_ms["depth_sort"] + stage_ms["emission"] + stage_ms["tile_counts"] + \
+            stage_ms["tile_sort_passes"] + stage_ms["ranges"]
     else:
-        launch_ms = stage_ms[dom]
-        algo = M * (4 + 48) + W * H * (16 + 8)
-        unit_note = "per key: value + gathered 48 B record; per pixel: rgb, alpha, T, last written"
-    achieved = algo / (launch_ms * 1e-3) / 1e9
-    traffic = _committed_traffic(dom, M, n)
-    roof = dict(kernel=names[STAGES.index(dom)], bound="hbm", achieved=round(achieved, 1), peak=peaks["hbm_gbs"],
-                unit="GB/s", frac=round(achieved / peaks["hbm_gbs"], 4), traffic=traffic,
-                peak_source=peaks["source"], algorithmic_bytes_per_launch=int(algo), launch_ms=round(launch_ms, 4),
-                bytes_model=unit_note)
-    clk_summary = clk.summary()
+        hbm["sort"] = (M * (8 + 24 * passes), stage_ms["sort_histogram"] + stage_ms["sort_passes"],
+                       "8 B key read by the histogram + 24 B per key per pass")
+        sort_ms = stage_ms["duplicate"] + stage_ms["sort_histogram"] + stage_ms["sort_passes"] + stage_ms["ranges"]
+    hbm_stages = {}
+    for k, (b, ms, note) in hbm.items():
+        a = b / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        hbm_stages[k] = dict(bytes=int(b), ms=round(ms, 4), achieved_gbs=round(a, 1),
+                             frac=round(a / peaks["hbm_gbs"], 4), bytes_model=note)
+
+    # ---- roofline of the dominant stage ----
+    cands = ["preprocess", "composite"] + (["tile_sort", "depth_sort"] if sort_mode == 1 else ["sort"])
+    dom_ms = {c: (hbm_stages[c]["ms"] if c in hbm_stages else stage_ms[c]) for c in cands}
+    dom = max(cands, key=lambda c: dom_ms[c])
     if dom == "composite":
-        # the compositor is bound by FP32 issue, not HBM: count its (pixel, splat) tests and hits
-        # on the first view (one extra render with statistics, outside the timed region)
-        st_opts = vis.make_opts(sort_mode=args.sort_mode, tile=args.tile, pixels_per_thread=args.ppt, collect_stats=1)
+        # the compositor is bound by FP32 issue (SURVEY: ~15 FP32 instructions per (pixel,
+        # splat) test, one ex2 per composited pair): count its tests on the first view (one
+        # extra render with statistics, outside the timed region)
+        st_opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt, collect_stats=1)
         vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
-                       st_opts)
+                       st_opts, depth=dbuf)
         vis.vis_check(ws.buf)
         ctrl = vis.read_ctrl(ws.buf)
-        flops = 11.0 * ctrl["pair_tests"] + 13.0 * ctrl["hits"]
-        mhz = clk_summary.get("sm_mhz") or _peaks().get("sm_max_mhz", 2032.0)
-        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        peak_tf = n_sm * 128 * 2 * mhz * 1e6 / 1e12
-        ach_tf = flops / (stage_ms["composite"] * 1e-3) / 1e12
-        roof = dict(kernel="composite", bound="alu", achieved=round(ach_tf, 2), peak=round(peak_tf, 1),
-                    unit="TFLOP/s", frac=round(ach_tf / peak_tf, 4), traffic=traffic,
-                    peak_source=f"FP32 FMA rate: {n_sm} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz (sampled clock)",
-                    algorithmic_flops_per_launch=int(flops), pair_tests=ctrl["pair_tests"], hits=ctrl["hits"],
-                    launch_ms=round(stage_ms["composite"], 4),
-                    flop_model="11 flop per (pixel, splat) test (offset, two projections, squared norm), "
-                               "13 per composited pair (alpha, transmittance, 3 colour FMAs)",
-                    hbm_view=dict(achieved=round(achieved, 1), peak=peaks["hbm_gbs"], unit="GB/s",
-                                  frac=round(achieved / peaks["hbm_gbs"], 4)))
-        # the compositor is issue-bound: its warp instructions (per test, from the committed ncu
-        # capture, times this launch's live test count) over the launch time, against one
-        # instruction per clock from each of the 4 schedulers of every SM
-        tj = ROOT / "profiles" / "traffic.json"
-        ipt = json.loads(tj.read_text()).get("composite", {}).get("warp_inst_per_test") if tj.exists() else None
-        if ipt:
-            inst = ipt * ctrl["pair_tests"]
-            ach_i = inst / (stage_ms["composite"] * 1e-3) / 1e9
-            peak_i = n_sm * 4 * mhz * 1e6 / 1e9
-            roof["issue_view"] = dict(achieved=round(ach_i, 1), peak=round(peak_i, 1), unit="G warp-inst/s",
-                                      frac=round(ach_i / peak_i, 4), warp_inst_per_launch=int(inst),
-                                      source="profiles/traffic.json warp_inst_per_test x live pair tests")
-
-    # every HBM-bound stage against the copy peak (the spec bar is >= 60% for preprocess and sort)
-    hbm_stages = {"preprocess": dict(bytes=int(bytes_pre), ms=round(stage_ms["preprocess"], 4),
-                                     achieved_gbs=round(bytes_pre / (stage_ms["preprocess"] * 1e-3) / 1e9, 1))}
-    if passes > 0:
-        key = "tile_sort_pass"
-        b_st = tile_bytes / passes
-        ms_st = stage_ms["sort_passes"] / passes
-        hbm_stages[key] = dict(bytes=int(b_st), ms=round(ms_st, 4), achieved_gbs=round(b_st / (ms_st * 1e-3) / 1e9, 1))
-    for v in hbm_stages.values():
-        v["frac"] = round(v["achieved_gbs"] / peaks["hbm_gbs"], 4)
+        inst = 15.0 * ctrl["pair_tests"]
+        mhz = clk_summary.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_t = n_sm * 128 * mhz * 1e6 / 1e12
+        ach_t = inst / (stage_ms["composite"] * 1e-3) / 1e12
+        hb = M * (4 + 48) + W * H * (16 + 8)
+        roof = dict(kernel="composite", bound="alu", achieved=round(ach_t, 3), peak=round(peak_t, 2),
+                    unit="T FP32 lane-instructions/s", frac=round(ach_t / peak_t, 4),
+                    traffic=_committed_traffic("composite", M, n),
+                    peak_source=f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled clock)",
+                    algorithmic_instructions_per_launch=int(inst), pair_tests=ctrl["pair_tests"],
+                    hits=ctrl["hits"], launch_ms=round(stage_ms["composite"], 4),
+                    instruction_model="15 FP32 instructions per (pixel, splat) test (offset, two whitened "
+                                      "projections, squared norm, threshold, and the composited pair's share)",
+                    hbm_view=dict(achieved=round(hb / (stage_ms["composite"] * 1e-3) / 1e9, 1),
+                                  peak=peaks["hbm_gbs"], unit="GB/s",
+                                  frac=round(hb / (stage_ms["composite"] * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)))
+    else:
+        h = hbm_stages[dom]
+        roof = dict(kernel=dom, bound="hbm", achieved=h["achieved_gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=h["frac"], traffic=_committed_traffic(dom, M, n), peak_source=peaks["source"],
+                    algorithmic_bytes_per_launch=h["bytes"], launch_ms=h["ms"], bytes_model=h["bytes_model"])
 
     # ---- end to end through the C ABI with host buffers ----
-    e2e = (run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts) if not (packed or dbuf is not None)
-           else dict(value=None, note="not measured for a pre-packed scene or a depth buffer"))
+    e2e = None
+    if with_e2e:
+        e2e = (run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts) if not (packed or dbuf is not None)
+               else dict(value=None, note="not measured for a pre-packed scene or a depth buffer"))
 
+    launches = {0: 7 + passes, 1: 10 + 4 + passes}[sort_mode] + (2 if fwdbwd else 0) + (1 if dynamic else 0) + \
+        (1 if dbuf is not None else 0)
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(desc, sort_mode=args.sort_mode, packed=packed, pixels_per_thread=args.ppt,
+                config=dict(desc, sort_mode=sort_mode, packed=packed, pixels_per_thread=args.ppt,
                             depth_buffer=(f"wall at view depth {args.depth_plane}" if dbuf is not None else None),
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-                clocks=clk_summary, e2e=e2e,
-                gpu_launches=int(args.steps * {0: 6 + passes, 1: 10 + kDP + passes}[args.sort_mode]
-                                 + (2 * args.steps if fwdbwd else 0) + (args.steps if dynamic else 0)
-                                 + (args.steps if dbuf is not None else 0)),
+                clocks=clk_summary, e2e=e2e, gpu_launches=int(args.steps * launches),
                 roofline=roof, hbm_stages=hbm_stages,
-                stage_ms={names[STAGES.index(k)]: round(v, 4) for k, v in stage_ms.items()},
+                stage_ms={k: round(v, 4) for k, v in stage_ms.items() if k != "none"},
                 keys_per_frame=int(M), visible_per_frame=int(n_vis), sort_passes=passes,
                 dynamic_update_ms=(round(update_ms, 4) if update_ms is not None else None),
-                sort_keys_per_s=round(M / (stage_ms["sort_passes"] + stage_ms["sort_histogram"]
-                                           ) * 1e3, 1),
+                sort_ms=round(sort_ms, 4), sort_keys_per_s=round(M / sort_ms * 1e3, 1),
                 gaussians_per_s=round(n / value * 1e3, 1))
-    if rank == 0 and world == 1 and not args.no_cpu and not packed:
-        line["cpu_baseline"] = cpu_baseline(args.workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
+    if fwdbwd:
+        fwd = sum(stage_ms.values())
+        line["forward_ms"] = round(fwd, 4)
+        line["backward_ms"] = round(value - fwd, 4)
+    if rank == 0 and world == 1 and with_cpu and not packed:
+        line["cpu_baseline"] = cpu_baseline(workload, sc_np, cams, desc, budget_s=args.cpu_seconds)
+    return line
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = measure(args, args.workload, with_e2e=True, with_cpu=not args.no_cpu, dist=dist)
+    if args.workload == "1m" and world == 1 and not args.no_legs and not args.packed and args.depth_plane is None:
+        # the metric's other legs, each timed on its own: the 6M dynamic frame, the 500k
+        # fwd+bwd step and the 128-image batch
+        line["legs"] = legs(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batch(args):
-    """16 assets x 8 cameras = 128 images: one graph-captured vis_render_batch vs 128
-    sequential vis_render calls of the plain path (same options, images compared)."""
-    import ctypes as C
+def legs(args):
+    import copy
+    import torch
+    out = {}
+    keep = ("value", "unit", "steps", "warmup", "clocks", "config", "stage_ms", "hbm_stages", "roofline",
+            "keys_per_frame", "visible_per_frame", "sort_ms", "sort_keys_per_s", "gaussians_per_s",
+            "dynamic_update_ms", "forward_ms", "backward_ms", "gpu_launches")
+    for name, wl in (("dynamic_6m", "6m"), ("fwdbwd_500k", "fwdbwd")):
+        a = copy.copy(args)
+        a.steps = min(args.steps, 20)
+        r = measure(a, wl, with_e2e=False, with_cpu=False)
+        out[name] = {k: r[k] for k in keep if k in r and r[k] is not None}
+        torch.cuda.empty_cache()
+    out["batch_128"] = batch_leg(args)
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_leg(args):
+    """16 assets x 8 cameras = 128 images, the autotuned fused pipeline (one graph-captured
+    vis_render_batch) against the 8-lane graph and against 128 sequential vis_render calls of
+    the plain path, all with the tuned options (images compared bit for bit)."""
     import torch
     import paper_2512_08478_b300 as vis
     from paper_2512_08478_b300 import synth, tuning
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
     scenes_np, cams, cam_scene = synth.workload_batch()
     scenes = [vis.Scene.from_numpy(s) for s in scenes_np]
+    tried = []
     if args.no_autotune:
-        opts_d, lanes, tuned_ms = dict(tile=16, pixels_per_thread=1, sort_mode=1), 8, None
+        opts_d, tuned_ms = dict(tile=16, digit_bits=8, pixels_per_thread=1), None
     else:
-        opts_d, lanes, tuned_ms = tuning.autotune(scenes, cams, cam_scene, cache=None,
-                                                  log=lambda m: print(m, file=sys.stderr))
+        opts_d, tuned_ms = tuning.autotune(scenes, cams, cam_scene, cache=None, log=tried.append)
     opts = vis.make_opts(**opts_d)
-    b = vis.Batch(scenes, cams, cam_scene, lanes=lanes, opts=opts)
-    b.render()
     stream = torch.cuda.current_stream()
-    # sequential plain path: one workspace for the largest image
+    steps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup // 2)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, clk.summary()
+
+    fused = vis.Batch(scenes, cams, cam_scene, lanes=0, opts=opts)
+    fused.render()
+    t_fused, clk_fused = timed(fused.launch)
+    keys = fused.check()
+    ref = [(r.clone(), a.clone()) for r, a in zip(fused.rgb, fused.alpha)]
+    del fused
+    torch.cuda.empty_cache()
+    lanes = vis.Batch(scenes, cams, cam_scene, lanes=8, opts=opts)
+    lanes.render()
+    t_lanes, clk_lanes = timed(lanes.launch)
+    lanes.check()
+    same_lanes = all(torch.equal(lanes.rgb[i], ref[i][0]) and torch.equal(lanes.alpha[i], ref[i][1])
+                     for i in range(len(cams)))
+    del lanes
+    torch.cuda.empty_cache()
     nmax = max(s.n for s in scenes)
-    Wm = max(int(c.W) for c in cams)
-    Hm = max(int(c.H) for c in cams)
-    ws = vis.Workspace(nmax, Wm, Hm, key_capacity=16 * nmax + (1 << 20), opts=opts)
+    ws = vis.Workspace(nmax, max(int(c.W) for c in cams), max(int(c.H) for c in cams),
+                       key_capacity=16 * nmax + (1 << 20), opts=opts)
     outs = [(torch.empty((3, c.H, c.W), device="cuda"), torch.empty((c.H, c.W), device="cuda")) for c in cams]
     cam_objs = [vis.make_camera(c) for c in cams]
 
@@ -458,37 +527,30 @@ def run_batch(args):
             vis.vis_render(scenes[cam_scene[i]].handle, c, cams[i].W, cams[i].H, (0.0, 0.0, 0.0), outs[i][0],
                            outs[i][1], ws.buf, opts)
 
-    for _ in range(args.warmup):
-        b.launch()
-        sequential()
-    b.check()
+    t_seq, clk_seq = timed(sequential)
     vis.vis_check(ws.buf)
-    same = all(torch.equal(b.rgb[i], outs[i][0]) and torch.equal(b.alpha[i], outs[i][1]) for i in range(len(cams)))
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        e[0].record(stream)
-        for _ in range(args.steps):
-            b.launch()
-        e[1].record(stream)
-        for _ in range(args.steps):
-            sequential()
-        e[2].record(stream)
-        torch.cuda.synchronize()
-    b.check()
-    vis.vis_check(ws.buf)
-    t_batch = e[0].elapsed_time(e[1]) / args.steps
-    t_seq = e[1].elapsed_time(e[2]) / args.steps
+    same_seq = all(torch.equal(outs[i][0], ref[i][0]) and torch.equal(outs[i][1], ref[i][1]) for i in range(len(cams)))
     n_g = sum(scenes[a].n for a in cam_scene)
-    line = dict(metric="ms per 128-image heterogeneous batch (16 assets x 8 cameras)", value=round(t_batch, 4),
-                unit="ms/batch", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=round(t_batch, 4),
-                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+    return dict(value=round(t_fused, 4), unit="ms/batch", steps=steps,
                 config=dict(workload="16 assets (N log-uniform 2e4..2e6, SH 0..3) x 8 orbit cameras at "
                                      "{512^2, 1280x720, 1920x1080}", images=len(cams),
-                            gaussians=[s.n for s in scenes], opts=opts_d, lanes=lanes),
-                sequential_ms=round(t_seq, 4), speedup_vs_sequential=round(t_seq / t_batch, 3),
-                images_identical_to_sequential=bool(same), autotune_best_ms=tuned_ms,
-                gaussian_views_per_s=round(n_g / t_batch * 1e3, 1), clocks=clk.summary())
+                            gaussians=[s.n for s in scenes], opts=opts_d, pipeline="fused (lanes = 0)"),
+                lanes8_ms=round(t_lanes, 4), sequential_ms=round(t_seq, 4),
+                speedup_vs_sequential=round(t_seq / t_fused, 3), speedup_vs_lanes=round(t_lanes / t_fused, 3),
+                images_identical_to_sequential=bool(same_seq), images_identical_to_lanes=bool(same_lanes),
+                keys_per_batch=int(keys), gaussian_views_per_s=round(n_g / t_fused * 1e3, 1),
+                autotune=dict(best_ms=tuned_ms, tried=tried), clocks=clk_fused,
+                clocks_lanes=clk_lanes, clocks_sequential=clk_seq)
+
+
+def run_batch(args):
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    leg = batch_leg(args)
+    line = dict(metric="ms per 128-image heterogeneous batch (16 assets x 8 cameras)", n_gpus=1, warmup=args.warmup,
+                ms_per_step=leg["value"], higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32",
+                data="synthetic", **leg)
     print(json.dumps(line), flush=True)
 
 
@@ -572,14 +634,14 @@ def run_multi(args):
     for i in range(args.steps):
         multi(i)
     torch.cuda.synchronize()
-    stage = (C.c_double * 7)()
+    stage = (C.c_double * 8)()
     ns, nr, npass = C.c_int(), C.c_int(), C.c_int()
-    vis._ok(vis.lib().vis_profile_end(stage, 7, C.byref(ns), C.byref(nr), C.byref(npass)))
+    vis._ok(vis.lib().vis_profile_end(stage, 8, C.byref(ns), C.byref(nr), C.byref(npass)))
     vis.vis_check(ws.buf)
     vis.vis_check(wsm.buf)
     t_multi = e[0].elapsed_time(e[1]) / args.steps
     t_single = e[1].elapsed_time(e[2]) / args.steps
-    stage_ms = {STAGES_FUSED[k]: round(stage[k] / max(nr.value, 1), 4) for k in range(7)}
+    stage_ms = {STAGES_DF[k]: round(stage[k] / max(nr.value, 1), 4) for k in range(8)}
     line = dict(metric="1080p multi-asset frame ms (4 models, one global sort)", value=round(t_multi, 4),
                 unit="ms/frame", n_gpus=1, steps=args.steps, warmup=args.warmup, ms_per_step=round(t_multi, 4),
                 higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
@@ -590,25 +652,9 @@ def run_multi(args):
                 merged_scene_ms=round(t_single, 4),
                 merged_note="the same Gaussians as one plain scene, SH zero-padded to degree 3",
                 stage_ms=stage_ms, keys_per_frame=int(keys), gaussians_per_s=round(n_total / t_multi * 1e3, 1),
-                gpu_launches=int(args.steps * (len(scenes) + 9 + kDP + npass.value)), clocks=clk.summary())
+                gpu_launches=int(args.steps * (len(scenes) + 9 + 4 + npass.value)), clocks=clk.summary())
     if rank == 0:
         print(json.dumps(line), flush=True)
-
-
-def _committed_traffic(kernel, M, n):
-    """DRAM bytes per launch from a committed ncu capture (profiles/traffic.json), scaled
-    to this launch by keys (sort, composite) or Gaussians (preprocess); None if absent."""
-    p = ROOT / "profiles" / "traffic.json"
-    if not p.exists():
-        return None
-    d = json.loads(p.read_text()).get(kernel)
-    if not d:
-        return None
-    if "bytes_per_key" in d:
-        return int(d["bytes_per_key"] * M)
-    if "bytes_per_gaussian" in d:
-        return int(d["bytes_per_gaussian"] * n)
-    return None
 
 
 def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts):
@@ -755,9 +801,11 @@ def main():
     ap.add_argument("--workload", default="1m", choices=["1m", "6m", "fwdbwd", "small", "batch", "multi"])
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: skip the autotuner")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="1m workload: skip the 6M, fwd+bwd and batch legs of the line")
     ap.add_argument("--sort-mode", type=int, default=None, choices=[0, 1],
-                    help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort; "
-                         "2: depth sort then counting binning (default: the library default)")
+                    help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort "
+                         "(default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile size in pixels")
     ap.add_argument("--ppt", type=int, default=1, choices=[1, 2], help="pixels per compositor thread")

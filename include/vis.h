@@ -426,10 +426,13 @@ VIS_API vis_status vis_sort_noalloc_check(void* stream);
  * every vis_render records CUDA events on its stream between its stages, for up
  * to 1024 renders. vis_profile_end synchronises those events and returns, per
  * stage, the summed milliseconds over the recorded renders, in this order:
- *   0 clear, 1 preprocess, 2 scan + key duplication, 3 sort histogram,
- *   4 sort digit passes (all of them), 5 tile ranges, 6 composite.
+ *   0 clear, 1 preprocess,
+ *   sort_mode 1: 2 compaction + depth sort, 3 emission of the tile copies in depth order,
+ *                4 per-tile counts (or the tile histogram), 5 tile digit passes;
+ *   sort_mode 0: 2 scan + key duplication, 3 sort histogram, 4 (empty), 5 digit passes;
+ *   6 tile ranges (empty when the counts produced them), 7 composite.
  *  stage_ms   host double[max_stages]
- *  n_stages   host out: number of stages written (7)
+ *  n_stages   host out: number of stages written (8)
  *  n_renders  host out: renders summed
  *  n_passes   host out: radix passes per render (of the last render)
  * Profiling is per process and not thread safe. */

@@ -195,7 +195,7 @@ int64_t scene_slots(const vis_scene* const* scenes, int n_scenes, bool padded, i
 }
 
 // ---- per-stage profiling (vis_profile_begin / vis_profile_end) ----
-constexpr int kProfStages = 7;
+constexpr int kProfStages = 8;
 constexpr int kProfRing = 1024;
 struct Profiler {
     bool on = false;
@@ -212,6 +212,12 @@ void prof_mark(int k, cudaStream_t stream) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     cudaEventRecord(g_prof.ev[g_prof.count][k], stream);
+}
+
+// Marks k and k + 1 (an empty stage k): the 64-bit key sort has no tile-count stage.
+void prof_mark_twice(int k, cudaStream_t stream) {
+    prof_mark(k, stream);
+    prof_mark(k + 1, stream);
 }
 
 }  // namespace
@@ -574,20 +580,22 @@ static vis_status render_impl(const vis_scene_t* scenes, const float* models, in
     }
     prof_mark(2, stream);
     if (L.mode == vis::kSortDepthFirst) {
+        // marks 3 (after the depth sort), 4 (after the emission), 5 (after the tile counts or
+        // the tile histogram)
         vis::launch_depth_first(L, w, stream, g_prof.on ? &prof_mark : nullptr, 3);
-        prof_mark(5, stream);
+        prof_mark(6, stream);
         if (!L.tile_fused) vis::launch_ranges32(L, w, stream);   // the counts-first tile sort wrote them
     } else {
         vis::launch_scan_and_duplicate(L, w, L.n, stream);
         prof_mark(3, stream);
-        vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark : nullptr, 4);
-        prof_mark(5, stream);
+        vis::launch_sort(L, w, stream, g_prof.on ? &prof_mark_twice : nullptr, 4);
+        prof_mark(6, stream);
         vis::launch_ranges(L, w, stream);
     }
-    prof_mark(6, stream);
+    prof_mark(7, stream);
     vis::launch_composite(L, w, bg[0], bg[1], bg[2], o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread,
                           o.collect_stats != 0, out_rgb, out_alpha, zlim, stream);
-    prof_mark(7, stream);
+    prof_mark(8, stream);
     if (g_prof.on && g_prof.count < kProfRing) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {

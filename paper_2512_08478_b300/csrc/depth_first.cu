@@ -212,6 +212,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
     launch_depth_sort(L, ws, stream);
+    if (mark) mark(mark_index, stream);
     // 3. tile copies in depth order
     uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
@@ -225,9 +226,9 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
                  reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
                  (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
                  reinterpret_cast<uint32_t*>(ws + L.off_vals[0]), (const BatchImage*)nullptr);
-        if (mark) mark(mark_index, stream);
-        launch_tile_counts(L, ws, stream);
         if (mark) mark(mark_index + 1, stream);
+        launch_tile_counts(L, ws, stream);
+        if (mark) mark(mark_index + 2, stream);
         launch_tile_passes(L, ws, stream);
         (void)hist; (void)lb;
         return;
@@ -244,7 +245,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
         emit_tiles<uint32_t, false><<<blocks_n, kPrepThreads, 0, stream>>>(
             dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, boff2, L.tiles_x, ctrl, k0, v0,
             (const BatchImage*)nullptr);
-    if (mark) mark(mark_index, stream);
+    if (mark) mark(mark_index + 1, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer
     const int tp = L.passes;
     uint32_t* ka = L.sorted_buffer ? k1 : k0;
@@ -253,7 +254,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* vb = L.sorted_buffer ? v0 : v1;
     launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp,
                                   reinterpret_cast<uint32_t*>(ws + L.off_hist_tile), lb + L.lookback_words_depth,
-                                  ctrl->part_counter + kMaxPasses, &ctrl->error, stream, mark, mark_index + 1,
+                                  ctrl->part_counter + kMaxPasses, &ctrl->error, stream, mark, mark_index + 2,
                                   L.tile_bits - L.digit_bits * (tp - 1), 16, L.spin_limit, L.digit_bits);
     (void)sms;
 }

@@ -284,8 +284,9 @@ void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark 
 void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
                       int64_t cap, cudaStream_t stream);
-// Depth-first mode: compaction, depth sort, emission (then mark(3)), tile sort (mark(4)
-// after its histogram). With `images` (a fused batch; the footprints carry their image) the
+// Depth-first mode: compaction and depth sort (then mark(mark_index)), emission (then
+// mark(mark_index + 1)), tile counts or the tile histogram (then mark(mark_index + 2)), tile
+// passes. With `images` (a fused batch; the footprints carry their image) the
 // copies take global tile ids and the 32-bit tile sort runs. Ranges for its 32-bit tile keys:
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
                         const BatchImage* images = nullptr);
