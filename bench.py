@@ -214,7 +214,7 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     n = sc.n
     cap = 16 * n + (1 << 20)
     sort_mode = args.sort_mode if args.sort_mode is not None else vis.make_opts().sort_mode
-    opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt)
+    opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt, digit_bits=args.digit_bits)
     ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
@@ -338,11 +338,11 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     hbm = {"preprocess": (bytes_pre, stage_ms["preprocess"],
                           "40 B per Gaussian + 28 B per Gaussian in front + SH and 48 B record per survivor")}
     if sort_mode == 1:
-        dp = 4   # 8-bit digit passes of the depth sort
+        dp = {8: 4, 10: 4, 11: 3}[args.digit_bits]   # digit passes of the depth sort
         # compaction: count + depth read per Gaussian, (depth, index) written per survivor; the
         # depth histogram reads 4 B per survivor; each pass reads and writes 8 B per survivor
         hbm["depth_sort"] = (8 * n + 8 * n_vis + 4 * n_vis + 16 * dp * n_vis, stage_ms["depth_sort"],
-                             "compaction 8 B per Gaussian + 8 B per survivor, histogram 4 B and 4 passes of "
+                             f"compaction 8 B per Gaussian + 8 B per survivor, histogram 4 B and {dp} passes of "
                              "16 B per survivor")
         # touch sums and emission: index + count, then index + footprint per survivor; 2 B tile id
         # + 4 B index written per copy
@@ -373,7 +373,8 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         # the compositor is bound by FP32 issue (SURVEY: ~15 FP32 instructions per (pixel,
         # splat) test, one ex2 per composited pair): count its tests on the first view (one
         # extra render with statistics, outside the timed region)
-        st_opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt, collect_stats=1)
+        st_opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=args.ppt,
+                                digit_bits=args.digit_bits, collect_stats=1)
         vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
                        st_opts, depth=dbuf)
         vis.vis_check(ws.buf)
@@ -407,12 +408,17 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         e2e = (run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts) if not (packed or dbuf is not None)
                else dict(value=None, note="not measured for a pre-packed scene or a depth buffer"))
 
-    launches = {0: 7 + passes, 1: 10 + 4 + passes}[sort_mode] + (2 if fwdbwd else 0) + (1 if dynamic else 0) + \
-        (1 if dbuf is not None else 0)
+    # kernels per frame: preprocess, (mode 1) block-sum scan, compaction, depth histogram,
+    # depth passes, touch sums, scan, emission, tile counts, tile scan, tile passes / (mode 0)
+    # scan, duplication, histogram, passes, ranges; the compositor
+    depth_passes = {8: 4, 10: 4, 11: 3}[args.digit_bits]
+    launches = {0: 6 + passes, 1: 10 + depth_passes + passes}[sort_mode] + (2 if fwdbwd else 0) + \
+        (1 if dynamic else 0) + (1 if dbuf is not None else 0)
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(desc, sort_mode=sort_mode, packed=packed, pixels_per_thread=args.ppt,
+                            digit_bits=args.digit_bits,
                             depth_buffer=(f"wall at view depth {args.depth_plane}" if dbuf is not None else None),
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
                             parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
@@ -808,6 +814,8 @@ def main():
                          "(default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile size in pixels")
+    ap.add_argument("--digit-bits", type=int, default=8, choices=[8, 10, 11],
+                    help="radix digit width of the depth sort (and of 32-bit tile sorts)")
     ap.add_argument("--ppt", type=int, default=1, choices=[1, 2], help="pixels per compositor thread")
     ap.add_argument("--depth-plane", type=float, default=None,
                     help="composite against a depth buffer holding this view depth everywhere")

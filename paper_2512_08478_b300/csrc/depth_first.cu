@@ -209,7 +209,6 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     const int blocks_n = (int)L.prep_blocks;
     uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[0]);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
     launch_depth_sort(L, ws, stream);
     if (mark) mark(mark_index, stream);
@@ -230,7 +229,6 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
         launch_tile_counts(L, ws, stream);
         if (mark) mark(mark_index + 2, stream);
         launch_tile_passes(L, ws, stream);
-        (void)hist; (void)lb;
         return;
     }
     uint32_t* k0 = reinterpret_cast<uint32_t*>(ws + L.off_keys[0]);

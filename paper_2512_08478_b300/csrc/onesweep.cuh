@@ -20,15 +20,13 @@ constexpr uint32_t kCountMask = (1u << 30) - 1;
 
 static_assert(kSortThreads == 256, "the scan phase assumes 8 warps");
 
-// Per digit width: D digits, DPT of them per thread, the look-back window (predecessors
-// read per round; narrower for wide digits, whose DPT windows share the registers), and
-// the type of the per-warp digit counters (a warp counts at most 32 x 16 = 512 keys of one
-// digit, so 16 bits suffice and halve the shared memory of the wide digits).
+// Per digit width: D digits, DPT of them per thread, and the type of the per-warp digit
+// counters (a warp counts at most 32 x 16 = 512 keys of one digit, so 16 bits suffice and
+// halve the shared memory of the wide digits).
 template <int DBITS>
 struct RadixCfg {
     static constexpr int D = 1 << DBITS;
     static constexpr int DPT = D > kSortThreads ? D / kSortThreads : 1;
-    static constexpr int WIN = D > kSortThreads ? 4 : 16;
     using Counter = typename std::conditional<(D > kSortThreads), uint16_t, uint32_t>::type;
     static_assert(D >= kSortThreads, "at least one digit per thread");
 };

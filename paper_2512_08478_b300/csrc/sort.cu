@@ -65,11 +65,17 @@ struct SortSmem {
 };
 
 // CTAs per SM the register budget is set for: three (85 registers) for 8- and 10-bit
-// digits, four for the short 32-bit partitions, two for the 11-bit digits, whose shared
-// memory (~96 KB) admits no more.
+// digits, four for the short 32-bit partitions and for the 16-bit tile keys (64 registers,
+// with a look-back window of 8: measured 4-5% faster per tile pass than three CTAs with a
+// window of 16), two for the 11-bit digits, whose shared memory (~96 KB) admits no more.
 template <typename K, int KPT, int DBITS>
 struct SortOcc {
-    static constexpr int value = DBITS == 11 ? 2 : (KPT <= 8 && sizeof(K) == 4) ? 4 : 3;
+    static constexpr int value = DBITS == 11 ? 2 : ((KPT <= 8 && sizeof(K) == 4) || sizeof(K) == 2) ? 4 : 3;
+};
+// Look-back window (predecessors read per round) by key type and digit width.
+template <typename K, int DBITS>
+struct SortWin {
+    static constexpr int value = DBITS > 8 ? 4 : (sizeof(K) == 2 ? 8 : 16);
 };
 
 // Per partition (warp-striped: warp w owns keys [w*32*KPT, (w+1)*32*KPT)):
@@ -93,7 +99,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
           uint32_t* __restrict__ part_counter, uint32_t* __restrict__ error, uint32_t spin_limit) {
     using Cfg = RadixCfg<DBITS>;
     using Counter = typename Cfg::Counter;
-    constexpr int D = Cfg::D, DPT = Cfg::DPT, WIN = Cfg::WIN;
+    constexpr int D = Cfg::D, DPT = Cfg::DPT, WIN = SortWin<K, DBITS>::value;
     pdl_entry();
     constexpr int PART = kSortThreads * KPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
