@@ -345,6 +345,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
     L.off_touched = take(sizeof(uint32_t) * (size_t)n);
     L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_scan_tot = take(sizeof(unsigned long long) * (size_t)kMaxScanChunks);
     if (df) {
         L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
         L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);

@@ -172,6 +172,7 @@ Fused fused_layout(const std::vector<int64_t>& n_img, const std::vector<char>& p
     L.off_touched = take(sizeof(uint32_t) * (size_t)F.slots);
     L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
+    L.off_scan_tot = take(sizeof(unsigned long long) * (size_t)vis::kMaxScanChunks);
     L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     for (int k = 0; k < 2; ++k) L.off_dkeys[k] = take(sizeof(uint32_t) * (size_t)F.slots);

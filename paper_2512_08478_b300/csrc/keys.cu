@@ -22,7 +22,7 @@ namespace vis {
 // sums in chunks of kScanChunk: a coalesced load of the chunk into shared memory, a
 // sequential sum of each thread's contiguous run of it, a scan of the 1024 run totals,
 // the run's offsets written back in place, and a coalesced store; a carry links chunks.
-constexpr int kScanChunk = 8192;   // 32 KB of static shared memory
+// kScanChunk (8192 sums, 32 KB of static shared memory) is declared in vis_internal.cuh.
 
 __global__ void __launch_bounds__(1024)
 scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
@@ -72,9 +72,99 @@ scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, 
     }
 }
 
+// Beyond one chunk the scan runs on one CTA per chunk: scan_chunk_totals sums each chunk
+// into chunk_tot[c]; scan_chunks adds, per CTA, the totals of the chunks before its own to
+// the same in-chunk scan as scan_block_sums, and the last chunk's CTA writes the total.
+__global__ void __launch_bounds__(1024)
+scan_chunk_totals(const uint32_t* __restrict__ bsum, int64_t nblocks, unsigned long long* __restrict__ chunk_tot) {
+    pdl_entry();
+    __shared__ unsigned long long warp_tot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
+    const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
+    unsigned long long v = 0;
+    for (int i = threadIdx.x; i < n; i += 1024) v += bsum[c0 + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) warp_tot[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 32; ++w) t += warp_tot[w];
+        chunk_tot[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+scan_chunks(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
+            const unsigned long long* __restrict__ chunk_tot, uint32_t* total_out, uint32_t* error, int64_t cap) {
+    pdl_entry();
+    __shared__ uint32_t s[kScanChunk];
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int per = kScanChunk / 1024;
+    const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
+    const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
+    // the totals of the chunks before this one
+    unsigned long long pre = 0;
+    for (int c = threadIdx.x; c < (int)blockIdx.x; c += 1024) pre += chunk_tot[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    if (lane == 0) warp_tot[warp] = pre;
+    for (int i = threadIdx.x; i < kScanChunk; i += 1024) s[i] = i < n ? bsum[c0 + i] : 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 32; ++w) t += warp_tot[w];
+        s_carry = t;
+    }
+    __syncthreads();
+    const unsigned long long carry = s_carry;
+    const int r0 = threadIdx.x * per;
+    unsigned long long run = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) run += s[r0 + i];
+    unsigned long long incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned long long excl = carry + incl - run, all = 0;
+    for (int w = 0; w < 32; ++w) {
+        const unsigned long long x = warp_tot[w];
+        if (w < warp) excl += x;
+        all += x;
+    }
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        const uint32_t v = s[r0 + i];
+        s[r0 + i] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
+        excl += v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += 1024) boff[c0 + i] = s[i];
+    if (threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) {
+        const unsigned long long tot = carry + all;
+        *total_out = (uint32_t)min(tot, (unsigned long long)0xffffffffu);
+        if (error && tot > (unsigned long long)cap) atomicOr(error, kErrCapacity);
+    }
+}
+
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
-                      int64_t cap, cudaStream_t stream) {
-    launch_k(true, scan_block_sums, 1, 1024, 0, stream, bsum, boff, nblocks, total, error, cap);
+                      int64_t cap, unsigned long long* chunk_tot, cudaStream_t stream) {
+    const int64_t chunks = (nblocks + kScanChunk - 1) / kScanChunk;
+    if (chunks <= 1 || !chunk_tot) {
+        launch_k(true, scan_block_sums, 1, 1024, 0, stream, bsum, boff, nblocks, total, error, cap);
+        return;
+    }
+    launch_k(true, scan_chunk_totals, (int)chunks, 1024, 0, stream, bsum, nblocks, chunk_tot);
+    launch_k(true, scan_chunks, (int)chunks, 1024, 0, stream, bsum, boff, nblocks,
+             (const unsigned long long*)chunk_tot, total, error, cap);
 }
 
 __global__ void __launch_bounds__(kPrepThreads)
@@ -122,7 +212,8 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* bsum = reinterpret_cast<const uint32_t*>(ws + L.off_bsum);
     uint32_t* boff = reinterpret_cast<uint32_t*>(ws + L.off_boff);
-    launch_scan_sums(bsum, boff, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap, stream);
+    launch_scan_sums(bsum, boff, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap,
+                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
     if (n <= 0) return;
     duplicate_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
         reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint4*>(ws + L.off_rect),

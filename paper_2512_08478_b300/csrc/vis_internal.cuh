@@ -75,6 +75,7 @@ struct Layout {
     int64_t sort_parts = 0;
     size_t off_ctrl = 0, off_rec = 0, off_depth = 0, off_rect = 0, off_touched = 0;
     size_t off_bsum = 0, off_boff = 0;
+    size_t off_scan_tot = 0;   // kMaxScanChunks 64-bit chunk totals of the block-sum scans
     size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
     size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
     size_t off_tfinal = 0, off_last = 0, off_g2 = 0;
@@ -282,8 +283,13 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
 typedef void (*StageMark)(int, cudaStream_t);
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark = nullptr, int mark_index = 0);
 void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
+// Exclusive scan of nblocks per-block sums into boff, the total into *total (a total above
+// cap sets kErrCapacity in *error if given). Beyond kScanChunk sums it takes one CTA per chunk
+// and needs chunk_tot (ceil(nblocks / kScanChunk) 64-bit words of scratch).
+constexpr int kScanChunk = 8192;
+constexpr int64_t kMaxScanChunks = 1024;   // 8.4 M blocks of 256: every slot count up to 2^31
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
-                      int64_t cap, cudaStream_t stream);
+                      int64_t cap, unsigned long long* chunk_tot, cudaStream_t stream);
 // Depth-first mode: compaction and depth sort (then mark(mark_index)), emission (then
 // mark(mark_index + 1)), tile counts or the tile histogram (then mark(mark_index + 2)), tile
 // passes. With `images` (a fused batch; the footprints carry their image) the
