@@ -147,3 +147,43 @@ def test_packed_scene_sizes_and_validation(L):
     assert L.vis_scene_pack(h, p, p, p, None) == vis.VIS_ERR_INVALID_ARG     # already packed
     assert "already packed" in vis.vis_last_error()
     L.vis_scene_destroy(h)
+
+
+def test_fused_batch_workspace_and_validation(L):
+    """The fused batch (lanes = 0) lays out one workspace for all its images: it grows with
+    the key capacity (two 32-bit key and two value buffers: 16 B per copy) and with every
+    image's slots and tiles, any digit width is accepted, and bad images are rejected on the
+    host before any device work."""
+    import ctypes as C
+    p = C.c_void_p(1 << 20)   # never dereferenced
+    hs = []
+    for n in (1000, 70_000):
+        h = C.c_void_p()
+        assert L.vis_scene_upload(p, p, p, p, p, 1, n, C.byref(h)) == vis.VIS_OK
+        hs.append(h)
+    scenes = (C.c_void_p * 2)(hs[0].value, hs[1].value)
+
+    def size(cam_scene, W, H, cap, lanes=0, opts=None):
+        n = len(cam_scene)
+        b = C.c_size_t()
+        st = L.vis_batch_workspace_size(scenes, 2, (C.c_int * n)(*cam_scene), (C.c_int * n)(*W), (C.c_int * n)(*H),
+                                        n, lanes, cap, vis._opts_ref(opts), C.byref(b))
+        return st, b.value
+
+    st, a = size([0, 1], [640, 320], [480, 240], 1 << 20)
+    assert st == vis.VIS_OK
+    st, b = size([0, 1], [640, 320], [480, 240], 2 << 20)
+    assert st == vis.VIS_OK and b - a >= 16 * (1 << 20)
+    st, c = size([0, 1, 1], [640, 320, 1920], [480, 240, 1080], 1 << 20)
+    assert st == vis.VIS_OK and c > a + 70_000 * 80   # a third image: its slots and tiles
+    for d in (8, 10, 11):
+        assert size([0, 1], [640, 320], [480, 240], 1 << 20, opts=vis.make_opts(digit_bits=d))[0] == vis.VIS_OK
+    st, lane_b = size([0, 1], [640, 320], [480, 240], 1 << 20, lanes=4)
+    assert st == vis.VIS_OK and lane_b != a   # the lane baseline's slices
+    assert size([0, 2], [640, 320], [480, 240], 1 << 20)[0] == vis.VIS_ERR_INVALID_ARG   # no scene 2
+    assert size([0, 1], [640, 0], [480, 240], 1 << 20)[0] == vis.VIS_ERR_INVALID_ARG     # empty image
+    assert size([0, 1], [640, 320], [480, 240], 0)[0] == vis.VIS_ERR_INVALID_ARG         # no capacity
+    assert size([0, 1], [640, 320], [480, 240], 1 << 20, opts=vis.make_opts(digit_bits=9))[0] \
+        == vis.VIS_ERR_UNSUPPORTED
+    for h in hs:
+        L.vis_scene_destroy(h)
