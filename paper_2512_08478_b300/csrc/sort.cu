@@ -157,8 +157,10 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             c += x;
         }
         cnt[j] = c;
-        st_relaxed(&lookback[(size_t)part * D + d], (part == 0 ? kFlagInc : kFlagAgg) | c);
         h[j] = hist_pass[d];
+        // a digit that no key of the pass has (zero in the global histogram, which every
+        // partition reads) has no look-back chain: nobody publishes or reads its words
+        if (h[j] != 0) st_relaxed(&lookback[(size_t)part * D + d], (part == 0 ? kFlagInc : kFlagAgg) | c);
         ta += c;
         tb += h[j];
     }
@@ -171,7 +173,8 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     if (lane == 31) { S.scan_a[warp] = ia; S.scan_b[warp] = ib; }
     uint32_t lbw[DPT][WIN];
 #pragma unroll
-    for (int j = 0; j < DPT; ++j) lookback_issue<WIN, D>(lookback, part, d0 + j, lbw[j]);
+    for (int j = 0; j < DPT; ++j)
+        if (h[j] != 0) lookback_issue<WIN, D>(lookback, part, d0 + j, lbw[j]);
     __syncthreads();
     uint32_t ls = ia - ta, gs = ib - tb;
 #pragma unroll
@@ -207,7 +210,8 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
         bool to = false;
-        const uint32_t prefix = lookback_resolve<WIN, D>(lookback, part, d0 + j, cnt[j], lbw[j], spin_limit, &to);
+        const uint32_t prefix =
+            h[j] != 0 ? lookback_resolve<WIN, D>(lookback, part, d0 + j, cnt[j], lbw[j], spin_limit, &to) : 0u;
         timed_out = timed_out || to;
         S.digit_off[d0 + j] = gsd[j] + prefix - lsd[j];
     }
