@@ -685,7 +685,8 @@ static vis_status backward_impl(const vis_scene_t* scenes, const float* models, 
     }
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     char* w = static_cast<char*>(ws);
-    vis::launch_composite_backward(L, w, bg, o.alpha_min, o.alpha_max, d_rgb, d_alpha, zlim, stream);
+    vis::launch_composite_backward(L, w, bg, o.alpha_min, o.alpha_max, o.pixels_per_thread, d_rgb, d_alpha, zlim,
+                                   stream);
     for (int k = 0; k < n_scenes; ++k) {
         const vis_scene_grads& g = grads[k];
         vis::launch_preprocess_backward(scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o), L, w,

@@ -52,8 +52,8 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return y;
 }
 
-template <int TILE, bool DEPTH>
-__global__ void __launch_bounds__(TILE * TILE)
+template <int TILE, int PPT, bool DEPTH>
+__global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                           const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0,
                           float bg1, float bg2, float alpha_min, float alpha_max, float qcut, float inv_scale,
@@ -62,9 +62,9 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                           float* __restrict__ g2, const float* __restrict__ depth,
                           const float* __restrict__ zlim, const Ctrl* __restrict__ ctrl) {
     if (ctrl->error) return;   // the forward produced no valid lists: leave the gradients at zero
-    constexpr int NT = TILE * TILE;
-    constexpr int NW = NT / 32;               // warps; each owns an 8 x 4 pixel block
-    constexpr int BX = TILE / 8, BH = 4;
+    constexpr int NT = TILE * TILE / PPT;     // threads; each owns PPT vertically adjacent pixels
+    constexpr int NW = NT / 32;               // warps; each owns an 8 x (4 PPT) pixel block
+    constexpr int BX = TILE / 8, BH = 4 * PPT;
     constexpr int CH = NT < 256 ? NT : 256;   // splats staged per chunk
     static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
     __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
@@ -74,34 +74,45 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bx = warp % BX, by = warp / BX;
-    const int px = tx * TILE + bx * 8 + (lane & 7), py = ty * TILE + by * BH + (lane >> 3);
-    const bool inside = px < W && py < H;
-    const size_t pix = (size_t)py * W + px;
+    const int px = tx * TILE + bx * 8 + (lane & 7);
     const size_t HW = (size_t)H * W;
     const float half = 0.5f * TILE;
     const float xc = (float)(tx * TILE) + half, yc = (float)(ty * TILE) + half;
-    const float lx = (float)px + 0.5f - xc, ly = (float)py + 0.5f - yc;
+    const float lx = (float)px + 0.5f - xc;
     const uint2 r = ranges[tile];
 
-    float T = 1.f, TN = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gA = 0.f;
-    int32_t last = 0;
-    const float dl = (DEPTH && inside) ? zlim[pix] : __int_as_float(0x7f800000);   // depth limit
-    if (inside) {
-        TN = t_final[pix];
-        T = TN;
-        last = last_in[pix];
-        gC0 = d_rgb[pix]; gC1 = d_rgb[HW + pix]; gC2 = d_rgb[2 * HW + pix];
-        gA = d_alpha[pix];
+    // per pixel: the walk state (T, S), the incoming gradients and the terms constant
+    // along the walk
+    bool inside[PPT];
+    float ly[PPT], T[PPT], TN[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gA[PPT], dl[PPT];
+    float bgdot[PPT], S0[PPT], S1[PPT], S2[PPT];
+    int32_t last[PPT];
+    int32_t my_last = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+        const int py = ty * TILE + by * BH + (lane >> 3) * PPT + q;
+        inside[q] = px < W && py < H;
+        const size_t pix = (size_t)py * W + px;
+        ly[q] = (float)py + 0.5f - yc;
+        T[q] = TN[q] = 1.f; gC0[q] = gC1[q] = gC2[q] = gA[q] = 0.f; last[q] = 0;
+        dl[q] = (DEPTH && inside[q]) ? zlim[pix] : __int_as_float(0x7f800000);   // depth limit
+        if (inside[q]) {
+            TN[q] = t_final[pix];
+            T[q] = TN[q];
+            last[q] = last_in[pix];
+            gC0[q] = d_rgb[pix]; gC1[q] = d_rgb[HW + pix]; gC2[q] = d_rgb[2 * HW + pix];
+            gA[q] = d_alpha[pix];
+        }
+        bgdot[q] = bg0 * gC0[q] + bg1 * gC1[q] + bg2 * gC2[q];
+        S0[q] = S1[q] = S2[q] = 0.f;
+        my_last = max(my_last, last[q]);
     }
-    // terms constant along the walk
-    const float bgdot = bg0 * gC0 + bg1 * gC1 + bg2 * gC2;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 
     // block-wide maximum of `last` bounds the walk
     __shared__ int32_t s_max_last;
     if (threadIdx.x == 0) s_max_last = 0;
     __syncthreads();
-    atomicMax(&s_max_last, last);
+    atomicMax(&s_max_last, my_last);
     __syncthreads();
     const uint32_t end = (uint32_t)max((int32_t)r.x, s_max_last);
 
@@ -133,41 +144,42 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
         for (int i = nlist - 1; i >= 0; --i) {     // back to front
             const int k = s_list[warp][i];
             const int64_t pos = lo + k;   // sorted position of this splat
+            const float4 a = s_a[k], b = s_b[k], c = s_c[k];
+            // this thread's gradient terms, summed over its pixels
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-            if (inside && pos < (int64_t)last) {
-                const float4 a = s_a[k], b = s_b[k];
-                const PairEval e = eval_pair(lx, ly, a, b);
-                const float4 c = s_c[k];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                if (!(inside[q] && pos < (int64_t)last[q])) continue;
+                const PairEval e = eval_pair(lx, ly[q], a, b);
                 // the forward's decisions: 3-sigma cut and alpha_min (and the depth test)
-                if (e.q <= b.z && (!DEPTH || c.w <= dl)) {
-                    contrib = true;
-                    const float G = gauss_of_qs(e.q);
-                    const float raw = __fmul_rn(b.w, G);
-                    const float alpha = fminf(alpha_max, raw);
-                    const float om = __fsub_rn(1.f, alpha);
-                    const float inv_om = 1.f / om;
-                    T = T * inv_om;                      // T before this splat
-                    const float w = alpha * T;
-                    g[6] = gC0 * w; g[7] = gC1 * w; g[8] = gC2 * w;
-                    float ga = T * ((c.x - S0) * gC0 + (c.y - S1) * gC1 + (c.z - S2) * gC2);
-                    ga += (gA - bgdot) * TN * inv_om;
-                    S0 = c.x * alpha + om * S0;
-                    S1 = c.y * alpha + om * S1;
-                    S2 = c.z * alpha + om * S2;
-                    if (raw <= alpha_max) {   // clamp inactive
-                        g[5] = ga * G;
-                        // G = exp(-q/2) in the unscaled q = d^T S^-1 d
-                        const float gq = -0.5f * ga * b.w * G;
-                        // dq/dd = 2 S^-1 d = 2 (f1 p1 + f2 p2) / c for the scaled rows f, p
-                        const float qdx = (a.z * e.p1 + b.x * e.p2) * inv_scale;
-                        const float qdy = (a.w * e.p1 + b.y * e.p2) * inv_scale;
-                        g[0] = -2.f * gq * qdx;   // d = pixel - (u, v)
-                        g[1] = -2.f * gq * qdy;
-                        g[2] = gq * e.dx * e.dx;
-                        g[3] = 2.f * gq * e.dx * e.dy;
-                        g[4] = gq * e.dy * e.dy;
-                    }
+                if (!(e.q <= b.z && (!DEPTH || c.w <= dl[q]))) continue;
+                contrib = true;
+                const float G = gauss_of_qs(e.q);
+                const float raw = __fmul_rn(b.w, G);
+                const float alpha = fminf(alpha_max, raw);
+                const float om = __fsub_rn(1.f, alpha);
+                const float inv_om = 1.f / om;
+                T[q] = T[q] * inv_om;                      // T before this splat
+                const float w = alpha * T[q];
+                g[6] += gC0[q] * w; g[7] += gC1[q] * w; g[8] += gC2[q] * w;
+                float ga = T[q] * ((c.x - S0[q]) * gC0[q] + (c.y - S1[q]) * gC1[q] + (c.z - S2[q]) * gC2[q]);
+                ga += (gA[q] - bgdot[q]) * TN[q] * inv_om;
+                S0[q] = c.x * alpha + om * S0[q];
+                S1[q] = c.y * alpha + om * S1[q];
+                S2[q] = c.z * alpha + om * S2[q];
+                if (raw <= alpha_max) {   // clamp inactive
+                    g[5] += ga * G;
+                    // G = exp(-q/2) in the unscaled q = d^T S^-1 d
+                    const float gq = -0.5f * ga * b.w * G;
+                    // dq/dd = 2 S^-1 d = 2 (f1 p1 + f2 p2) / c for the scaled rows f, p
+                    const float qdx = (a.z * e.p1 + b.x * e.p2) * inv_scale;
+                    const float qdy = (a.w * e.p1 + b.y * e.p2) * inv_scale;
+                    g[0] += -2.f * gq * qdx;   // d = pixel - (u, v)
+                    g[1] += -2.f * gq * qdy;
+                    g[2] += gq * e.dx * e.dx;
+                    g[3] += 2.f * gq * e.dx * e.dy;
+                    g[4] += gq * e.dy * e.dy;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -394,7 +406,8 @@ preprocess_backward_kernel(PrepParams p, const float* __restrict__ g2, const uin
 }
 
 void launch_composite_backward(const Layout& L, char* ws, const float bg[3], float alpha_min, float alpha_max,
-                               const float* d_rgb, const float* d_alpha, const float* zlim, cudaStream_t stream) {
+                               int ppt, const float* d_rgb, const float* d_alpha, const float* zlim,
+                               cudaStream_t stream) {
     float* g2 = reinterpret_cast<float*>(ws + L.off_g2);
     cudaMemsetAsync(g2, 0, sizeof(float) * 9 * (size_t)L.n, stream);
     const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.off_ranges);
@@ -406,19 +419,20 @@ void launch_composite_backward(const Layout& L, char* ws, const float bg[3], flo
     const QScale qs = q_scale();
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
     const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(ws + L.off_ctrl);
-#define VIS_LAUNCH_BWD_D(TS, DT)                                                                           \
-    composite_backward_kernel<TS, DT><<<blocks, TS * TS, 0, stream>>>(                                     \
+#define VIS_LAUNCH_BWD_D(TS, PP, DT)                                                                       \
+    composite_backward_kernel<TS, PP, DT><<<blocks, TS * TS / PP, 0, stream>>>(                            \
         ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut,        \
         qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl)
-#define VIS_LAUNCH_BWD(TS)                       \
-    do {                                         \
-        if (zlim) VIS_LAUNCH_BWD_D(TS, true);    \
-        else VIS_LAUNCH_BWD_D(TS, false);        \
+#define VIS_LAUNCH_BWD(TS, PP)                       \
+    do {                                             \
+        if (zlim) VIS_LAUNCH_BWD_D(TS, PP, true);    \
+        else VIS_LAUNCH_BWD_D(TS, PP, false);        \
     } while (0)
     if (blocks > 0) {
-        if (L.tile == 8) VIS_LAUNCH_BWD(8);
-        else if (L.tile == 32) VIS_LAUNCH_BWD(32);
-        else VIS_LAUNCH_BWD(16);
+        const bool two = ppt == 2;
+        if (L.tile == 8) { if (two) VIS_LAUNCH_BWD(8, 2); else VIS_LAUNCH_BWD(8, 1); }
+        else if (L.tile == 32) { if (two) VIS_LAUNCH_BWD(32, 2); else VIS_LAUNCH_BWD(32, 1); }
+        else { if (two) VIS_LAUNCH_BWD(16, 2); else VIS_LAUNCH_BWD(16, 1); }
     }
 #undef VIS_LAUNCH_BWD_D
 #undef VIS_LAUNCH_BWD

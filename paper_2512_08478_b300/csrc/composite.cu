@@ -1,7 +1,9 @@
 // K5 -- tile compositor (section 3.2 Eqs. 2-3, front to back).
 //
 // One CTA per TILE x TILE tile; each thread owns PPT vertically adjacent pixels and
-// each warp an 8 x (4 PPT) pixel block.
+// each warp an 8 x (4 PPT) pixel block. With PPT = 2 the two pixels are evaluated and
+// composited together with packed f32x2 arithmetic (one instruction for both pixels' add,
+// multiply or FMA), rounded exactly as the one-pixel code, so the image does not depend on PPT.
 // The tile's range of the sorted (tile, depth, index) list is walked in chunks of
 // CH splats: each thread stages splats (gather of the 48-byte record by index)
 // into shared memory -- centre relative to the tile centre, scaled whitening rows,
@@ -60,7 +62,11 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     constexpr int BH = 4 * PPT;             // block height in pixels
     constexpr int CH = NT < 256 ? NT : 256; // splats staged per chunk
     static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
-    __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
+    // staged splats, NS float4 slots each: PPT 1 -> (du, dv, f1x, f1y), (f2x, f2y, thr, opacity),
+    // (r, g, b, depth); PPT 2 -> the same values laid out as packed pairs for the f32x2
+    // instructions (see the pair walk below)
+    constexpr int NS = PPT == 1 ? 3 : 6;
+    __shared__ float4 s_st[NS][CH];
     __shared__ uint32_t s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
     __shared__ float s_wmax[NW];   // DEPTH: largest depth limit of each warp block's live pixels
@@ -113,6 +119,9 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
         ly[r] = (float)py + 0.5f - yc;
         dl[r] = (DEPTH && !P[r].done) ? zlim[(size_t)py * W + px] : __int_as_float(0x7f800000);
     }
+    // PPT 2: the two pixels' state as packed pairs (x: row0, y: row0 + 1)
+    float2 T2 = make_float2(1.f, 1.f), Cr = make_float2(0.f, 0.f), Cg = Cr, Cb = Cr;
+    const float2 lx2 = make_float2(lx, lx), ly2 = make_float2(ly[0], ly[PPT - 1]), one2 = T2;
     if (DEPTH) {   // a NaN limit rejects nothing (no comparison holds): it counts as +inf here
         float m = __int_as_float(0xff800000);
 #pragma unroll
@@ -128,21 +137,31 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
 #pragma unroll
         for (int r = 0; r < PPT; ++r) all_done = all_done && P[r].done;
         if (__syncthreads_count(all_done) == NT) break;
-        const uint32_t j = base + threadIdx.x;
-        if (threadIdx.x < CH && j < rg.y) {
-            const uint32_t g = vals[j];
-            StagedSplat s = stage_splat(rec, g, xc, yc, qcut, alpha_min);
-            if (DEPTH) s.c.w = depth[g];
-            s_a[threadIdx.x] = s.a;
-            s_b[threadIdx.x] = s.b;
-            s_c[threadIdx.x] = s.c;
+        for (int t = threadIdx.x; t < CH && base + t < rg.y; t += NT) {
+            const uint32_t g = vals[base + t];
+            const StagedSplat s = stage_splat(rec, g, xc, yc, qcut, alpha_min);
+            const float z = DEPTH ? depth[g] : 0.f;
+            if constexpr (PPT == 1) {
+                s_st[0][t] = s.a;
+                s_st[1][t] = s.b;
+                s_st[2][t] = make_float4(s.c.x, s.c.y, s.c.z, z);
+            } else {
+                // negated centre and colour, so that a pair add and a pair FMA give dx, dy and
+                // C + c w exactly as the single-pixel arithmetic does
+                s_st[0][t] = make_float4(-s.a.x, -s.a.x, -s.a.y, -s.a.y);
+                s_st[1][t] = make_float4(s.a.z, s.a.z, s.b.x, s.b.x);
+                s_st[2][t] = make_float4(s.a.w, s.a.w, s.b.y, s.b.y);
+                s_st[3][t] = make_float4(s.b.z, z, s.b.w, s.b.w);
+                s_st[4][t] = make_float4(-s.c.x, -s.c.x, -s.c.y, -s.c.y);
+                s_st[5][t] = make_float4(-s.c.z, -s.c.z, 0.f, 0.f);
+            }
             uint32_t m = warp_block_mask<NW, BX, BH>(s, half);
             if (DEPTH) {
 #pragma unroll
                 for (int w = 0; w < NW; ++w)
-                    if (!(s.c.w <= s_wmax[w])) m &= ~(1u << w);
+                    if (!(z <= s_wmax[w])) m &= ~(1u << w);
             }
-            s_mask[threadIdx.x] = m;
+            s_mask[t] = m;
         }
         __syncthreads();
         const int cnt = (int)umin((uint32_t)CH, rg.y - base);
@@ -151,7 +170,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             float tmax = s_wmax[0];
 #pragma unroll
             for (int w = 1; w < NW; ++w) tmax = fmaxf(tmax, s_wmax[w]);
-            beyond = !(s_c[cnt - 1].w <= tmax);
+            beyond = !((PPT == 1 ? s_st[2][cnt - 1].w : s_st[3][cnt - 1].y) <= tmax);
         }
         // this warp's list of splats whose 3-sigma box meets its pixel block, in depth order
         int nlist = 0;
@@ -163,45 +182,65 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             nlist += __popc(bal);
         }
         __syncwarp();
-        if (!all_done) {
-            for (int i = 0; i < nlist; ++i) {
-                const int k = s_list[warp][i];
-                const float4 a = s_a[k], b = s_b[k];
-                const int32_t pos1 = (int32_t)(base + k + 1);
-                if (PPT == 1) {
+        if constexpr (PPT == 1) {
+            if (!all_done) {
+                for (int i = 0; i < nlist; ++i) {
+                    const int k = s_list[warp][i];
+                    const float4 a = s_st[0][k], b = s_st[1][k];
+                    const int32_t pos1 = (int32_t)(base + k + 1);
                     const PairEval e = eval_pair(lx, ly[0], a, b);
                     if (STATS) ++n_tests;
                     if (e.q > b.z) continue;
-                    const float4 c = s_c[k];
+                    const float4 c = s_st[2][k];
                     if (DEPTH && c.w > dl[0]) continue;
                     composite_hit(P[0], e.q, b, c, alpha_max, t_stop, pos1);
                     if (STATS && !P[0].done) ++n_hits;
                     if (P[0].done) break;
-                } else {
-                    // the same arithmetic as eval_pair for each row, sharing the dx products
-                    const float dx = __fsub_rn(lx, a.x);
-                    const float t1 = __fmul_rn(dx, a.z), t2 = __fmul_rn(dx, b.x);
-                    const float dy0 = __fsub_rn(ly[0], a.y), dy1 = __fsub_rn(ly[1], a.y);
-                    const float p10 = __fmaf_rn(dy0, a.w, t1), p20 = __fmaf_rn(dy0, b.y, t2);
-                    const float p11 = __fmaf_rn(dy1, a.w, t1), p21 = __fmaf_rn(dy1, b.y, t2);
-                    const float q0 = __fmaf_rn(p20, p20, __fmul_rn(p10, p10));
-                    const float q1 = __fmaf_rn(p21, p21, __fmul_rn(p11, p11));
-                    bool h0 = !P[0].done && q0 <= b.z;
-                    bool h1 = !P[1].done && q1 <= b.z;
-                    if (STATS) n_tests += (P[0].done ? 0 : 1) + (P[1].done ? 0 : 1);
-                    if (!(h0 || h1)) continue;
-                    const float4 c = s_c[k];
-                    if (DEPTH) {
-                        h0 = h0 && c.w <= dl[0];
-                        h1 = h1 && c.w <= dl[1];
-                        if (!(h0 || h1)) continue;
-                    }
-                    if (h0) composite_hit(P[0], q0, b, c, alpha_max, t_stop, pos1);
-                    if (h1) composite_hit(P[1], q1, b, c, alpha_max, t_stop, pos1);
-                    if (STATS) n_hits += (h0 && !P[0].done ? 1 : 0) + (h1 && !P[1].done ? 1 : 0);
-                    if (P[0].done && P[1].done) break;
                 }
             }
+        } else if (__any_sync(0xffffffffu, !all_done)) {
+            // Two vertically adjacent pixels per thread, evaluated together with the packed
+            // f32x2 instructions: per staged splat the eval_pair arithmetic (dx, dy, the two
+            // whitened projections, q') and the composite_hit update (alpha, T, C) for both
+            // pixels, each lane of a pair rounded exactly as the single-pixel code rounds it.
+            // The update is branch-free: a pixel that does not take the splat gets w = 0 and
+            // keeps T. The warp walks its list together and leaves once none of its pixels is live.
+            bool live0 = !P[0].done, live1 = !P[PPT - 1].done;
+            for (int i = 0; i < nlist; ++i) {
+                const int k = s_list[warp][i];
+                const float4 q0 = s_st[0][k], q1 = s_st[1][k], q2 = s_st[2][k], q3 = s_st[3][k];
+                const float2 dx = __fadd2_rn(lx2, make_float2(q0.x, q0.y));
+                const float2 dy = __fadd2_rn(ly2, make_float2(q0.z, q0.w));
+                const float2 t1 = __fmul2_rn(dx, make_float2(q1.x, q1.y));
+                const float2 t2 = __fmul2_rn(dx, make_float2(q1.z, q1.w));
+                const float2 p1 = __ffma2_rn(dy, make_float2(q2.x, q2.y), t1);
+                const float2 p2 = __ffma2_rn(dy, make_float2(q2.z, q2.w), t2);
+                const float2 q = __ffma2_rn(p2, p2, __fmul2_rn(p1, p1));
+                bool h0 = live0 && q.x <= q3.x, h1 = live1 && q.y <= q3.x;
+                if (DEPTH) { h0 = h0 && q3.y <= dl[0]; h1 = h1 && q3.y <= dl[1]; }
+                if (STATS) n_tests += (live0 ? 1 : 0) + (live1 ? 1 : 0);
+                // -alpha = max(-alpha_max, -(opacity 2^-q'))
+                const float2 a = __fmul2_rn(make_float2(q3.z, q3.w), make_float2(gauss_of_qs(q.x), gauss_of_qs(q.y)));
+                const float2 na = make_float2(fmaxf(-alpha_max, -a.x), fmaxf(-alpha_max, -a.y));
+                const float2 Tn = __fmul2_rn(T2, __fadd2_rn(one2, na));
+                const bool s0 = h0 && Tn.x < t_stop, s1 = h1 && Tn.y < t_stop;   // stops, splat excluded
+                const bool c0 = h0 && !s0, c1 = h1 && !s1;                       // composited
+                const float2 nw = __fmul2_rn(make_float2(c0 ? na.x : 0.f, c1 ? na.y : 0.f), T2);   // -alpha T
+                const float4 k0 = s_st[4][k], k1 = s_st[5][k];
+                Cr = __ffma2_rn(make_float2(k0.x, k0.y), nw, Cr);
+                Cg = __ffma2_rn(make_float2(k0.z, k0.w), nw, Cg);
+                Cb = __ffma2_rn(make_float2(k1.x, k1.y), nw, Cb);
+                T2 = make_float2(c0 ? Tn.x : T2.x, c1 ? Tn.y : T2.y);
+                const int32_t pos1 = (int32_t)(base + k + 1);
+                if (c0) P[0].last = pos1;
+                if (c1) P[PPT - 1].last = pos1;
+                if (STATS) n_hits += (c0 ? 1 : 0) + (c1 ? 1 : 0);
+                live0 = live0 && !s0;
+                live1 = live1 && !s1;
+                if (!__any_sync(0xffffffffu, live0 || live1)) break;
+            }
+            P[0].done = !live0;
+            P[PPT - 1].done = !live1;
         }
         if (DEPTH && beyond) break;   // every later splat of the tile is deeper still
     }
@@ -215,6 +254,10 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             atomicAdd(&ctrl->pair_tests, n_tests);
             atomicAdd(&ctrl->hits, n_hits);
         }
+    }
+    if constexpr (PPT == 2) {
+        P[0].T = T2.x; P[0].C0 = Cr.x; P[0].C1 = Cg.x; P[0].C2 = Cb.x;
+        P[PPT - 1].T = T2.y; P[PPT - 1].C0 = Cr.y; P[PPT - 1].C1 = Cg.y; P[PPT - 1].C2 = Cb.y;
     }
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {

@@ -204,6 +204,38 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
                                   L.spin_limit, L.digit_bits);
 }
 
+SideStream* side_stream() {
+    constexpr int kMaxDevices = 64;
+    thread_local SideStream side[kMaxDevices];
+    thread_local bool tried[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    SideStream& sd = side[dev];
+    if (!tried[dev]) {
+        tried[dev] = true;
+        if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess)
+            sd.s = nullptr;
+    }
+    return sd.s ? &sd : nullptr;
+}
+
+bool side_fork(SideStream* side, cudaStream_t stream) {
+    return cudaEventRecord(side->fork, stream) == cudaSuccess &&
+           cudaStreamWaitEvent(side->s, side->fork, 0) == cudaSuccess;
+}
+
+bool side_join_point(SideStream* side, cudaStream_t stream) {
+    if (cudaEventRecord(side->join, side->s) == cudaSuccess) return true;
+    // cannot join: let the host wait for the side stream instead (a capture in progress is
+    // invalid after the failed call and ends with an error)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+        cudaStreamSynchronize(side->s);
+    return false;
+}
+
 void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
                         const BatchImage* images) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
@@ -211,6 +243,17 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     const int blocks_n = (int)L.prep_blocks;
     uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[0]);
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
+    // The per-tile counts of the counts-first tile sort need only the footprints: outside a
+    // profiled render they run on a side stream, beside the depth sort and the emission
+    // (which leave most SMs idle at a million splats), and join before the tile passes.
+    SideStream* side = (L.tile_fused && !images && !mark) ? side_stream() : nullptr;
+    if (side && !side_fork(side, stream)) side = nullptr;
+    bool counted = false;   // the counts were queued on the side stream
+    if (side) {
+        launch_tile_counts(L, ws, side->s);
+        counted = true;
+        if (!side_join_point(side, stream)) side = nullptr;
+    }
     launch_depth_sort(L, ws, stream);
     if (mark) mark(mark_index, stream);
     // 3. tile copies in depth order
@@ -228,7 +271,8 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
                  (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
                  reinterpret_cast<uint32_t*>(ws + L.off_vals[0]), (const BatchImage*)nullptr);
         if (mark) mark(mark_index + 1, stream);
-        launch_tile_counts(L, ws, stream);
+        if (side) cudaStreamWaitEvent(stream, side->join, 0);
+        else if (!counted) launch_tile_counts(L, ws, stream);
         if (mark) mark(mark_index + 2, stream);
         launch_tile_passes(L, ws, stream);
         return;

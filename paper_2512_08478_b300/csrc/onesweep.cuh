@@ -89,7 +89,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // `part`, split in two so that its loads overlap the reordering: lookback_issue reads the
 // window of WIN predecessors for digit d; lookback_resolve consumes it in order up to the
 // first inclusive prefix, polling a word not yet published at most `limit` times,
-// continues one predecessor at a time past the window if needed, publishes this
+// continues past the window a window at a time if needed, publishes this
 // partition's inclusive prefix and returns the count of d over all preceding partitions
 // (*timed_out set if a poll gave up; the prefix is then wrong, but still published, so
 // that no successor waits on this partition).
@@ -128,12 +128,19 @@ __device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }
-    for (int64_t q = q0 - WIN; !found && !to && q >= 0; --q) {
-        const uint32_t* word = &lookback[(size_t)q * D + d];
-        uint32_t w = ld_relaxed(word);
-        if (!lookback_wait(word, &w, limit)) { to = true; break; }
-        prefix += w & kCountMask;
-        if ((w & ~kCountMask) == kFlagInc) found = true;
+    // beyond the first window: the next WIN predecessors at a time, their loads in flight together
+    for (int64_t qb = q0 - WIN; !found && !to && qb >= 0; qb -= WIN) {
+        uint32_t u[WIN];
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) u[i] = (qb - i >= 0) ? ld_relaxed(&lookback[(size_t)(qb - i) * D + d]) : 0u;
+#pragma unroll
+        for (int i = 0; i < WIN; ++i) {
+            if (found || to || qb - i < 0) break;
+            uint32_t w = u[i];
+            if (!lookback_wait(&lookback[(size_t)(qb - i) * D + d], &w, limit)) { to = true; break; }
+            prefix += w & kCountMask;
+            if ((w & ~kCountMask) == kFlagInc) found = true;
+        }
     }
     st_relaxed(&lookback[(size_t)part * D + d], kFlagInc | ((prefix + cnt) & kCountMask));
     *timed_out = to;

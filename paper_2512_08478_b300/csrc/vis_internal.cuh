@@ -315,9 +315,10 @@ void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images,
                             float bg0, float bg1, float bg2, float alpha_min, float alpha_max, float t_stop, int ppt,
                             cudaStream_t stream);
 // Adjoint of the compositing: clears and accumulates the screen-space gradients g2 of
-// all L.n slots (zlim as in launch_composite).
+// all L.n slots (ppt pixels per thread, 1 or 2; zlim as in launch_composite).
 void launch_composite_backward(const Layout& L, char* ws, const float bg[3], float alpha_min, float alpha_max,
-                               const float* d_rgb, const float* d_alpha, const float* zlim, cudaStream_t stream);
+                               int ppt, const float* d_rgb, const float* d_alpha, const float* zlim,
+                               cudaStream_t stream);
 // Adjoint of the preprocess of one scene (slots p.index_offset ..): g2 -> the scene's
 // parameter gradients.
 void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char* ws, float* d_means,
@@ -350,6 +351,20 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
 // Counts-first tile sort of sort_mode 1 (tile_sort.cu): per-tile counts -> digit histograms
 // and ranges; then the passes over the 16-bit tile keys emitted in depth order.
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream);
+
+// A second stream of the calling host thread on the current device, with a fork and a join
+// event, for work that can run beside the main stream's: side_stream() creates it on first
+// use and keeps it for the thread's lifetime (nullptr if creation failed -- the caller then
+// runs the work in order). side_fork makes the side stream wait for the main stream's work
+// so far; side_join_point records the join event after the side stream's work (false if that
+// failed, after the host waited for the side stream); the main stream then waits on `join`.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream* side_stream();
+bool side_fork(SideStream* side, cudaStream_t stream);
+bool side_join_point(SideStream* side, cudaStream_t stream);
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream);
 
 void launch_dynamic_update(const float* means0, const float* velocity, const float* logits0, const float* amp,

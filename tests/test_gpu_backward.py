@@ -64,14 +64,15 @@ def test_clamp_branch_scene_gradients_match_oracle(bg):
     assert np.all(g["sh"][66, :, 1] == 0.0)   # the clamped channel gets exactly nothing
 
 
+@pytest.mark.parametrize("ppt", [1, 2])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-def test_mixture_scene_gradients_match_oracle(tile):
+def test_mixture_scene_gradients_match_oracle(tile, ppt):
     sc = synth.mixture_scene(3000, 21, sh_degree=3, ball_radius=2.0, comp_std=0.4, log_scale_mean=-3.0)
     cam = synth.look_at((1.0, 2.0, 7.0), (0, 0, 0), 133, 97, 55.0)
     rng = np.random.default_rng(6)
     gC = rng.standard_normal((3, cam.H, cam.W))
     gA = rng.standard_normal((cam.H, cam.W))
-    g = _gpu_grads(sc, cam, gC, gA, (0.1, 0.1, 0.1), vis.make_opts(tile=tile))
+    g = _gpu_grads(sc, cam, gC, gA, (0.1, 0.1, 0.1), vis.make_opts(tile=tile, pixels_per_thread=ppt))
     ref = oracle.adjoint(sc, cam, gC, gA, (0.1, 0.1, 0.1), dict(tile=tile))
     _compare(g, ref)
 

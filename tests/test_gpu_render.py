@@ -11,7 +11,7 @@ import pytest
 import oracle
 import paper_2512_08478_b300 as vis
 from paper_2512_08478_b300 import synth
-from gpu_helpers import gpu_stage_outputs, image_parity, render_gpu
+from gpu_helpers import gpu_stage_outputs, image_parity, render_gpu, ws_view
 
 pytestmark = pytest.mark.gpu
 
@@ -24,17 +24,35 @@ def test_small_workload_image_parity():
     image_parity(rgb, alpha, ref)
 
 
+@pytest.mark.parametrize("ppt", [1, 2])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("deg", [0, 1, 2, 3])
-def test_ragged_image_all_tiles_and_degrees(tile, deg):
+def test_ragged_image_all_tiles_and_degrees(tile, deg, ppt):
     sc = synth.mixture_scene(4000, 100 + deg, sh_degree=deg, ball_radius=2.0, comp_std=0.4,
                              log_scale_mean=-3.0)
     cam = synth.look_at((2.0, 1.0, 7.0), (0, 0, 0), 203, 117, 55.0)
     bg = (0.2, 0.45, 0.7)
     opts = dict(tile=tile)
-    rgb, alpha, _, _ = render_gpu(sc, cam, bg, vis.make_opts(tile=tile))
+    rgb, alpha, _, _ = render_gpu(sc, cam, bg, vis.make_opts(tile=tile, pixels_per_thread=ppt))
     ref, _ = oracle.render(sc, cam, bg, opts)
     image_parity(rgb, alpha, ref)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_two_pixels_per_thread_bit_identical(tile):
+    """The packed two-pixel compositor rounds each pixel as the one-pixel compositor does:
+    images, final transmittance and last composited positions are identical bit for bit."""
+    sc = synth.mixture_scene(200_000, 17, sh_degree=3)
+    cam = synth.look_at((0.0, 2.0, 14.0), (0, 0, 0), 1001, 603, 50.0)
+    out = []
+    for ppt in (1, 2):
+        rgb, alpha, s, ws = render_gpu(sc, cam, (0.3, 0.2, 0.1), vis.make_opts(tile=tile, pixels_per_thread=ppt))
+        L = ws.layout()
+        npx = cam.W * cam.H
+        out.append((rgb, alpha, ws_view(ws, L.off_tfinal, npx, np.float32), ws_view(ws, L.off_last, npx, np.int32)))
+    assert (out[0][2] < 1.0).mean() > 0.3   # the view covers a good part of the image
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
 
 
 def _stage_inputs():
