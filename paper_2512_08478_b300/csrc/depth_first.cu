@@ -16,6 +16,9 @@
 // Stability makes the final order (tile, depth, index) -- identical to sorting the
 // 64-bit (tile << 32 | depth) keys -- while the sort moves 4-byte keys, and only the
 // N surviving splats (not the M tile copies) take part in the four depth passes.
+#include <map>
+#include <utility>
+
 #include "vis_internal.cuh"
 #include "footprint.cuh"
 
@@ -204,21 +207,25 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
                                   L.spin_limit, L.digit_bits);
 }
 
-SideStream* side_stream() {
-    constexpr int kMaxDevices = 64;
-    thread_local SideStream side[kMaxDevices];
-    thread_local bool tried[kMaxDevices] = {};
+SideStream* side_stream(cudaStream_t stream) {
+    // one side stream per (device, main stream) of this host thread, so that renders issued
+    // on different streams (as the lanes of a batch) keep their independence
+    constexpr size_t kMaxSides = 64;
+    thread_local std::map<std::pair<int, cudaStream_t>, SideStream> sides;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    SideStream& sd = side[dev];
-    if (!tried[dev]) {
-        tried[dev] = true;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    const auto key = std::make_pair(dev, stream);
+    auto it = sides.find(key);
+    if (it == sides.end()) {
+        if (sides.size() >= kMaxSides) return nullptr;
+        SideStream sd;
         if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess)
             sd.s = nullptr;
+        it = sides.emplace(key, sd).first;
     }
-    return sd.s ? &sd : nullptr;
+    return it->second.s ? &it->second : nullptr;
 }
 
 bool side_fork(SideStream* side, cudaStream_t stream) {
@@ -246,7 +253,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // The per-tile counts of the counts-first tile sort need only the footprints: outside a
     // profiled render they run on a side stream, beside the depth sort and the emission
     // (which leave most SMs idle at a million splats), and join before the tile passes.
-    SideStream* side = (L.tile_fused && !images && !mark) ? side_stream() : nullptr;
+    SideStream* side = (L.tile_fused && !images && !mark) ? side_stream(stream) : nullptr;
     if (side && !side_fork(side, stream)) side = nullptr;
     bool counted = false;   // the counts were queued on the side stream
     if (side) {

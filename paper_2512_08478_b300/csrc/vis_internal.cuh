@@ -352,17 +352,17 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
 // and ranges; then the passes over the 16-bit tile keys emitted in depth order.
 void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream);
 
-// A second stream of the calling host thread on the current device, with a fork and a join
-// event, for work that can run beside the main stream's: side_stream() creates it on first
-// use and keeps it for the thread's lifetime (nullptr if creation failed -- the caller then
-// runs the work in order). side_fork makes the side stream wait for the main stream's work
+// A second stream of the calling host thread for a main stream on the current device, with a
+// fork and a join event, for work that can run beside the main stream's: side_stream(stream)
+// creates it on first use and keeps it for the thread's lifetime (nullptr if creation failed
+// or 64 are in use -- the caller then runs the work in order). side_fork makes the side stream wait for the main stream's work
 // so far; side_join_point records the join event after the side stream's work (false if that
 // failed, after the host waited for the side stream); the main stream then waits on `join`.
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
 };
-SideStream* side_stream();
+SideStream* side_stream(cudaStream_t stream);
 bool side_fork(SideStream* side, cudaStream_t stream);
 bool side_join_point(SideStream* side, cudaStream_t stream);
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream);

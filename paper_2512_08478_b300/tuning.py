@@ -1,6 +1,7 @@
-"""Autotuner for batched renders: picks the tile size, the radix digit width and the
-compositor block shape of a fused batch (one pipeline over all images) for a batch
-signature by timing every candidate on the device.
+"""Autotuners: for batched renders, the tile size, the radix digit width and the compositor
+block shape of a fused batch (one pipeline over all images) for a batch signature; for a
+single-image workload, the compositor block shape (pick_fastest over any step callable).
+Both time every candidate on the device.
 
 Only configuration is searched here; every candidate runs the library's kernels. Results
 are cached in a JSON file keyed by GPU name and batch signature (asset sizes and SH
@@ -74,3 +75,25 @@ def autotune(scenes, cams, cam_scene, candidates=None, reps=3, cache: Path | Non
         Path(cache).parent.mkdir(parents=True, exist_ok=True)
         Path(cache).write_text(json.dumps(table, indent=1))
     return best
+
+
+def pick_fastest(candidates, run, reps=4, warmup=2, log=None):
+    """Time `run(c)` (one step of device work on the current stream) for every candidate c and
+    return (fastest candidate, {candidate: ms per step})."""
+    import torch
+    s = torch.cuda.current_stream()
+    times = {}
+    for c in candidates:
+        for _ in range(warmup):
+            run(c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            run(c)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times[c] = e0.elapsed_time(e1) / reps
+        if log:
+            log(f"pick_fastest {c}: {times[c]:.4f} ms")
+    return min(times, key=times.get), times
