@@ -107,6 +107,9 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_relaxed(error) & kErrCapacity) return;
     const int64_t m = min((int64_t)*num_keys, cap);
+    // persistent: the grid holds about one wave of CTAs, each takes partitions (tickets in
+    // order) until none is left; a CTA waits only on lower tickets, all taken by running CTAs
+    for (;;) {
     if (tid == 0) {
         S.part = atomicAdd(part_counter, 1u);
         S.bad = 0;
@@ -235,6 +238,8 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             }
         }
     }
+    __syncthreads();   // the next partition reuses the shared memory
+    }
 }
 
 __global__ void set_u32_kernel(uint32_t* ptr, uint32_t value) { *ptr = value; }
@@ -248,6 +253,12 @@ static int sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms;
+}
+
+// CTAs of a persistent pass: one wave at `occ` CTAs per SM, at most one per partition.
+static int pass_grid(int64_t parts, int occ) {
+    const int64_t wave = (int64_t)sm_count() * occ;
+    return (int)(parts < wave ? parts : wave);
 }
 
 template <typename K, int KPT, int DBITS>
@@ -267,6 +278,7 @@ static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys
                                     (int)hsmem) == cudaSuccess;
     });
     const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
+    const int grid = pass_grid(parts, SortOcc<K, KPT, DBITS>::value);
     const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
     launch_k(true, sort_histogram<K, DBITS>, hist_blocks, 256, sizeof(uint32_t) * passes * D, stream, keys_in,
@@ -279,7 +291,7 @@ static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys
         K* dk = to_a ? keys_a : keys_b;
         uint32_t* dv = to_a ? vals_a : vals_b;
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < DBITS) ? last_bits : DBITS;
-        launch_k(true, sort_pass<K, KPT, DBITS>, (int)parts, kSortThreads, smem, stream, src_k, src_v, dk, dv,
+        launch_k(true, sort_pass<K, KPT, DBITS>, grid, kSortThreads, smem, stream, src_k, src_v, dk, dv,
                  (const uint32_t*)num_keys_dev, cap, DBITS * p, nbits, (const uint32_t*)(hist + (size_t)p * D),
                  lookback + (size_t)p * parts * D, &part_counters[p], error, spin_limit);
         src_k = dk;
@@ -328,7 +340,8 @@ void launch_sort_pass(const K* keys_in, const uint32_t* vals_in, K* keys_out, ui
         return cudaFuncSetAttribute(sort_pass<K, KPT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
                cudaSuccess;
     });
-    launch_k(true, sort_pass<K, KPT, 8>, (int)sort_parts<K>(cap), kSortThreads, smem, stream, keys_in, vals_in,
+    launch_k(true, sort_pass<K, KPT, 8>, pass_grid(sort_parts<K>(cap), SortOcc<K, KPT, 8>::value), kSortThreads,
+             smem, stream, keys_in, vals_in,
              keys_out, vals_out, (const uint32_t*)num_keys_dev, cap, shift, nbits, (const uint32_t*)hist_pass,
              lookback, part_counter, error, spin_limit);
 }
