@@ -64,13 +64,13 @@ struct SortSmem {
     uint32_t bad;
 };
 
-// CTAs per SM the register budget is set for: three (85 registers) for 8- and 10-bit
-// digits, four for the short 32-bit partitions and for the 16-bit tile keys (64 registers,
-// with a look-back window of 8: measured 4-5% faster per tile pass than three CTAs with a
-// window of 16), two for the 11-bit digits, whose shared memory (~96 KB) admits no more.
+// CTAs per SM the register budget is set for: three (80-85 registers, no spills) for 8- and
+// 10-bit digits and for the 16-bit tile keys (with the persistent passes measured 1-3% faster
+// on the tile keys than four CTAs at 64 registers, which spill), four for the short 32-bit
+// partitions, two for the 11-bit digits, whose shared memory (~96 KB) admits no more.
 template <typename K, int KPT, int DBITS>
 struct SortOcc {
-    static constexpr int value = DBITS == 11 ? 2 : ((KPT <= 8 && sizeof(K) == 4) || sizeof(K) == 2) ? 4 : 3;
+    static constexpr int value = DBITS == 11 ? 2 : (KPT <= 8 && sizeof(K) == 4) ? 4 : 3;
 };
 // Look-back window (predecessors read per round) by key type and digit width.
 template <typename K, int DBITS>
