@@ -107,39 +107,49 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ld_relaxed(error) & kErrCapacity) return;
     const int64_t m = min((int64_t)*num_keys, cap);
-    // persistent: the grid holds about one wave of CTAs, each takes partitions (tickets in
-    // order) until none is left; a CTA waits only on lower tickets, all taken by running CTAs
-    for (;;) {
-    if (tid == 0) {
-        S.part = atomicAdd(part_counter, 1u);
-        S.bad = 0;
-    }
-    for (int i = tid; i < (kSortThreads / 32) * D; i += kSortThreads) (&S.whist[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t part = S.part;
-    const int64_t base = (int64_t)part * PART;
-    if (base >= m) return;
-    const int n_in = (m - base) < (int64_t)PART ? (int)(m - base) : PART;
-    const K* kin = keys_in + base;
-    const uint32_t* vin = vals_in + base;
-
-    // ---- load: keys to registers, values to shared memory ----
     const int wofs = warp * (32 * KPT) + lane;
     K key[KPT];
     uint32_t vmask = 0;
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-        const int idx = wofs + k * 32;
-        if (idx < n_in) {
-            key[k] = kin[idx];
-            vmask |= 1u << k;
-            cp_async4(&S.vin[idx], vin + idx);
-        } else {
-            key[k] = 0;
+    // Take the next partition (ticket) and start loading it: keys to registers, values to
+    // shared memory by asynchronous copies; false if no partition is left. Requires whist and
+    // vin free (a barrier since their last use).
+    auto take_and_load = [&](uint32_t& part, int& n_in) -> bool {
+        if (tid == 0) {
+            S.part = atomicAdd(part_counter, 1u);
+            S.bad = 0;
         }
-    }
-    cp_async_commit();
+        for (int i = tid; i < (kSortThreads / 32) * D; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+        __syncthreads();
+        part = S.part;
+        const int64_t base = (int64_t)part * PART;
+        if (base >= m) return false;
+        n_in = (m - base) < (int64_t)PART ? (int)(m - base) : PART;
+        const K* kin = keys_in + base;
+        const uint32_t* vin = vals_in + base;
+        vmask = 0;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k) {
+            const int idx = wofs + k * 32;
+            if (idx < n_in) {
+                key[k] = kin[idx];
+                vmask |= 1u << k;
+                cp_async4(&S.vin[idx], vin + idx);
+            } else {
+                key[k] = 0;
+            }
+        }
+        cp_async_commit();
+        return true;
+    };
+    // persistent: the grid holds about one wave of CTAs, each takes partitions (tickets in
+    // order) until none is left; a CTA waits only on lower tickets, all taken by running CTAs.
+    // The next partition's loads are issued before this one's look-back is resolved, so that
+    // they are in flight during the wait and the write-out.
     Counter* wh = S.whist[warp];
+    uint32_t part;
+    int n_in;
+    if (!take_and_load(part, n_in)) return;
+    for (;;) {
     // ---- stable ranking inside the warp; the warp counters end as the warp's digit counts ----
     uint32_t pos[KPT];
     rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
@@ -207,6 +217,10 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 #pragma unroll
     for (int k = 0; k < KPT; ++k)
         if ((vmask >> k) & 1u) S.vals[pos[k]] = S.vin[wofs + k * 32];
+    __syncthreads();   // whist and vin are free: start the next partition's loads
+    uint32_t next_part;
+    int next_n;
+    const bool more = take_and_load(next_part, next_n);
 
     // ---- resolve the look-back: global digit offsets ----
     bool timed_out = false;
@@ -223,7 +237,10 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         S.bad = 1;
     }
     __syncthreads();
-    if (S.bad) return;
+    if (S.bad) {   // give up: wait for the next partition's copies to this CTA's shared memory
+        cp_async_wait_all();
+        return;
+    }
 
     // ---- write out in digit runs (destinations are modular: digit_off may wrap) ----
 #pragma unroll
@@ -238,7 +255,10 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
             }
         }
     }
-    __syncthreads();   // the next partition reuses the shared memory
+    if (!more) return;
+    __syncthreads();   // the next partition reuses keys, vals and digit_off
+    part = next_part;
+    n_in = next_n;
     }
 }
 
