@@ -149,11 +149,11 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t part;
     int n_in;
     if (!take_and_load(part, n_in)) return;
-    for (;;) {
     // ---- stable ranking inside the warp; the warp counters end as the warp's digit counts ----
     uint32_t pos[KPT];
     rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
     __syncthreads();
+    for (;;) {
 
     // ---- per-digit counts and warp offsets; publish; scans; issue the look-back ----
     const uint32_t d0 = (uint32_t)tid * DPT;   // this thread's digits d0 .. d0 + DPT - 1
@@ -221,6 +221,8 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t next_part;
     int next_n;
     const bool more = take_and_load(next_part, next_n);
+    // rank the next partition now, while this one's look-back words arrive
+    if (more) rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
 
     // ---- resolve the look-back: global digit offsets ----
     bool timed_out = false;
@@ -256,7 +258,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         }
     }
     if (!more) return;
-    __syncthreads();   // the next partition reuses keys, vals and digit_off
+    __syncthreads();   // the next partition reuses keys, vals and digit_off; its warp counts are in
     part = next_part;
     n_in = next_n;
     }
