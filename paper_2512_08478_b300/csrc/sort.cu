@@ -145,6 +145,21 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     // order) until none is left; a CTA waits only on lower tickets, all taken by running CTAs.
     // The next partition's loads are issued before this one's look-back is resolved, so that
     // they are in flight during the wait and the write-out.
+    // Publish a ranked partition's per-digit aggregate (the warp counts summed; the warp
+    // counters hold the counts until the next barrier-separated step turns them into offsets).
+    // A digit that no key of the pass has (zero in the global histogram, which every partition
+    // reads) has no look-back chain: nobody publishes or reads its words.
+    auto publish = [&](uint32_t p) {
+#pragma unroll
+        for (int j = 0; j < DPT; ++j) {
+            const uint32_t d = (uint32_t)tid * DPT + j;
+            if (hist_pass[d] == 0) continue;
+            uint32_t c = 0;
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) c += S.whist[w][d];
+            st_relaxed(&lookback[(size_t)p * D + d], (p == 0 ? kFlagInc : kFlagAgg) | c);
+        }
+    };
     Counter* wh = S.whist[warp];
     uint32_t part;
     int n_in;
@@ -153,9 +168,10 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t pos[KPT];
     rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
     __syncthreads();
+    publish(part);
     for (;;) {
 
-    // ---- per-digit counts and warp offsets; publish; scans; issue the look-back ----
+    // ---- per-digit counts and warp offsets (the aggregate is published); scans; issue the look-back ----
     const uint32_t d0 = (uint32_t)tid * DPT;   // this thread's digits d0 .. d0 + DPT - 1
     uint32_t cnt[DPT], h[DPT];
     uint32_t ta = 0, tb = 0;
@@ -171,9 +187,6 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
         }
         cnt[j] = c;
         h[j] = hist_pass[d];
-        // a digit that no key of the pass has (zero in the global histogram, which every
-        // partition reads) has no look-back chain: nobody publishes or reads its words
-        if (h[j] != 0) st_relaxed(&lookback[(size_t)part * D + d], (part == 0 ? kFlagInc : kFlagAgg) | c);
         ta += c;
         tb += h[j];
     }
@@ -221,8 +234,13 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t next_part;
     int next_n;
     const bool more = take_and_load(next_part, next_n);
-    // rank the next partition now, while this one's look-back words arrive
-    if (more) rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
+    // rank the next partition now, while this one's look-back words arrive, and publish its
+    // aggregate at once for the partitions behind it
+    if (more) {
+        rank_keys<KPT, DBITS, K, Counter>(key, shift, nbits, vmask, wh, pos);
+        __syncthreads();
+        publish(next_part);
+    }
 
     // ---- resolve the look-back: global digit offsets ----
     bool timed_out = false;
