@@ -339,6 +339,7 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
     L.zero_end = off;
+    if (L.tile_fused) L.off_order = take(sizeof(uint32_t) * (size_t)L.ntiles);
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
     L.off_depth = take(sizeof(float) * (size_t)n);
     L.off_rect = take(sizeof(uint4) * (size_t)n);

@@ -60,7 +60,8 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                           const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
                           float* __restrict__ g2, const float* __restrict__ depth,
-                          const float* __restrict__ zlim, const Ctrl* __restrict__ ctrl) {
+                          const float* __restrict__ zlim, const Ctrl* __restrict__ ctrl,
+                          const uint32_t* __restrict__ order) {
     if (ctrl->error) return;   // the forward produced no valid lists: leave the gradients at zero
     constexpr int NT = TILE * TILE / PPT;     // threads; each owns PPT vertically adjacent pixels
     constexpr int NW = NT / 32;               // warps; each owns an 8 x (4 PPT) pixel block
@@ -70,7 +71,7 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
     __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
     __shared__ uint32_t s_g[CH], s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
-    const int tile = blockIdx.x;
+    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;   // longest tiles first if ordered
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bx = warp % BX, by = warp / BX;
@@ -423,10 +424,11 @@ void launch_composite_backward(const Layout& L, char* ws, const float bg[3], flo
     const QScale qs = q_scale();
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
     const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(ws + L.off_ctrl);
+    const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
 #define VIS_LAUNCH_BWD_D(TS, PP, DT)                                                                       \
     composite_backward_kernel<TS, PP, DT><<<blocks, TS * TS / PP, 0, stream>>>(                            \
         ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut,        \
-        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl)
+        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl, order)
 #define VIS_LAUNCH_BWD(TS, PP)                       \
     do {                                             \
         if (zlim) VIS_LAUNCH_BWD_D(TS, PP, true);    \

@@ -54,7 +54,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                  Ctrl* __restrict__ ctrl, float* __restrict__ out_rgb, float* __restrict__ out_alpha,
                  float* __restrict__ t_final, int32_t* __restrict__ last_out,
                  const float* __restrict__ depth, const float* __restrict__ zlim,
-                 const BatchImage* __restrict__ images, int n_images) {
+                 const BatchImage* __restrict__ images, int n_images, const uint32_t* __restrict__ order) {
     pdl_entry();
     constexpr int NT = TILE * TILE / PPT;   // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
@@ -70,7 +70,8 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     __shared__ uint32_t s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
     __shared__ float s_wmax[NW];   // DEPTH: largest depth limit of each warp block's live pixels
-    const uint32_t gtile = blockIdx.x;   // the tile's index in `ranges`
+    // the tile's index in `ranges`: CTAs take the tiles longest first when an order is given
+    const uint32_t gtile = order ? order[blockIdx.x] : blockIdx.x;
     int tile = (int)gtile;
     if (BATCH) {
         // a batch's tiles are numbered image after image: find this tile's image (the last
@@ -289,10 +290,11 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     if (blocks <= 0) return;
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+    const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
 #define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                \
     launch_k(true, composite_kernel<TS, PP, ST, DT, false>, blocks, TS * TS / PP, 0, stream, ranges, vals, rec, L.W, \
              L.H, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin,    \
-             last, depth, zlim, (const BatchImage*)nullptr, 0)
+             last, depth, zlim, (const BatchImage*)nullptr, 0, order)
 #define VIS_LAUNCH_COMPOSITE(TS, PP)                          \
     do {                                                      \
         if (zlim) VIS_LAUNCH_COMPOSITE_S(TS, PP, false, true);   \
@@ -321,7 +323,8 @@ void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images,
 #define VIS_LAUNCH_COMPOSITE_B(TS, PP)                                                                         \
     launch_k(true, composite_kernel<TS, PP, false, false, true>, blocks, TS * TS / PP, 0, stream, ranges, vals, \
              rec, 0, 0, 1, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,             \
-             (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images)
+             (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images, \
+             (const uint32_t*)nullptr)
     const bool two = ppt == 2;
     if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE_B(8, 2); else VIS_LAUNCH_COMPOSITE_B(8, 1); }
     else if (L.tile == 32) { if (two) VIS_LAUNCH_COMPOSITE_B(32, 2); else VIS_LAUNCH_COMPOSITE_B(32, 1); }

@@ -57,11 +57,12 @@ __device__ __forceinline__ int warp_scan_incl(int v, int lane) {
 // round (warp scans, then a scan of the 32 warp totals), written coalesced.
 __global__ void __launch_bounds__(1024)
 tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32_t* __restrict__ hist,
-                 uint2* __restrict__ ranges) {
+                 uint2* __restrict__ ranges, uint32_t* __restrict__ order) {
     pdl_entry();
     extern __shared__ int P[];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_bucket[kOrderBuckets];
     const int nt = tiles_x * tiles_y;
     const int ld = tiles_x + 1;   // padded row stride
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -70,6 +71,7 @@ tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32
         P[y * ld + (i - y * tiles_x)] = gdiff[i];
     }
     if (tid == 0) s_carry = 0;
+    for (int i = tid; i < kOrderBuckets; i += 1024) s_bucket[i] = 0;
     __syncthreads();
     for (int y = warp; y < tiles_y; y += 32) {   // prefix along each row
         int carry = 0;
@@ -136,6 +138,48 @@ tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32
         if (tid == 1023) s_carry = start + c;
         __syncthreads();
     }
+    // compositing order: tiles by decreasing count (log-spaced buckets, two per octave), so
+    // that the longest tiles start first and the launch ends on short ones. The lanes of a
+    // warp with the same bucket (found with one ballot per bucket bit) add to it once.
+    const int nt32 = (nt + 31) & ~31;
+    auto peers_of = [&](int b) {
+        uint32_t pm = __ballot_sync(0xffffffffu, b >= 0);
+#pragma unroll
+        for (int k = 0; k < kOrderBits; ++k) {
+            const uint32_t bit = (uint32_t)(b >> k) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            pm &= bit ? bal : ~bal;
+        }
+        return pm;
+    };
+    for (int t = tid; t < nt32; t += 1024) {   // a warp's 32 tiles are all in or all out of the loop
+        const int b = t < nt ? order_bucket(count(t)) : -1;
+        const uint32_t peers = peers_of(b);
+        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    static_assert(kOrderBuckets == 64, "the bucket scan below takes two buckets per lane");
+    if (warp == 0) {   // exclusive scan of the bucket sizes, kOrderBuckets = 2 x 32
+        const uint32_t v0 = s_bucket[2 * lane], v1 = s_bucket[2 * lane + 1], tot = v0 + v1;
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        s_bucket[2 * lane] = incl - tot;
+        s_bucket[2 * lane + 1] = incl - tot + v0;
+    }
+    __syncthreads();
+    for (int t = tid; t < nt32; t += 1024) {
+        const int b = t < nt ? order_bucket(count(t)) : -1;
+        const uint32_t peers = peers_of(b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (b >= 0 && lane == leader) base = atomicAdd(&s_bucket[b], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b >= 0) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+    }
 }
 
 static int sm_count_ts() {
@@ -168,7 +212,7 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     const size_t scan_smem = sizeof(int) * (size_t)(L.tiles_x + 1) * L.tiles_y;
     launch_k(true, tile_scan_kernel, 1, 1024, scan_smem, stream, (const int*)gdiff, L.tiles_x, L.tiles_y,
              reinterpret_cast<uint32_t*>(ws + L.off_hist_tile),
-             reinterpret_cast<uint2*>(ws + L.off_ranges));
+             reinterpret_cast<uint2*>(ws + L.off_ranges), reinterpret_cast<uint32_t*>(ws + L.off_order));
 }
 
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {

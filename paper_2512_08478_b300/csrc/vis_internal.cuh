@@ -23,6 +23,16 @@ template <> struct SortKPT<uint16_t> { static constexpr int value = 16; };
 // counts-first tile sort of sort_mode 1 (tile_sort.cu): used when the tile grid has at most
 // kTileFusedMaxTiles tiles (its per-tile counters live in shared memory)
 constexpr int kTileFusedMaxTiles = 51200;
+// Compositing order: bucket of a tile's key count c, 0 for the largest counts: two
+// log-spaced buckets per octave (the bit after the leading one), the empty tiles last.
+constexpr int kOrderBits = 6;
+constexpr int kOrderBuckets = 1 << kOrderBits;
+__device__ __forceinline__ int order_bucket(uint32_t c) {
+    if (c == 0) return kOrderBuckets - 1;
+    const int lg = 31 - __clz(c);
+    const int k = lg * 2 + (lg >= 1 ? (int)((c >> (lg - 1)) & 1u) : 0);
+    return kOrderBuckets - 2 - (k < kOrderBuckets - 2 ? k : kOrderBuckets - 2);
+}
 template <typename K> constexpr int64_t sort_partition() { return (int64_t)kSortThreads * SortKPT<K>::value; }
 template <typename K> constexpr int64_t sort_parts(int64_t cap) {
     return (cap + sort_partition<K>() - 1) / sort_partition<K>();
@@ -87,6 +97,7 @@ struct Layout {
     // depth-first mode with the counts-first tile sort of 16-bit keys (tile_sort.cu)
     bool tile_fused = false;
     size_t off_tdiff = 0;
+    size_t off_order = 0;    // compositing order of the tiles (counts-first tile sort only)
     size_t zero_begin = 0, zero_end = 0;   // region cleared before every render
     size_t total = 0;
     int sorted_buffer = 0;
