@@ -94,7 +94,9 @@ typedef struct {
  *              Both give the same order bit for bit; 1 moves about a quarter of the bytes
  *              of 0.
  *  pixels_per_thread  compositor block shape: 1 or 2 vertically adjacent pixels per
- *              thread (default 1); the image does not depend on it.
+ *              thread (default 1); 2 evaluates both pixels with packed two-float
+ *              arithmetic, rounded as the one-pixel code is: the image (and the adjoint's
+ *              inputs) do not depend on it.
  *  collect_stats  1: the compositor also counts the (pixel, splat) pairs it tests and
  *              composites into vis_ctrl.pair_tests / hits (a few % slower); default 0.
  *  tile_extent which tiles a splat is listed in: 0 = every tile of the square of
@@ -157,6 +159,10 @@ typedef struct {
     int key_bytes;           /* 8: (tile << 32) | depth bits (sort_mode 0); 4: tile id (sort_mode 1
                                 beyond 51200 tiles); 2: 16-bit tile id (sort_mode 1) */
     int sort_mode;
+    size_t off_order;        /* key_bytes 2 only (else 0): uint32[tiles], the order in which the
+                                compositor and its adjoint take the tiles -- a permutation of the
+                                tiles by non-increasing key count, in log-spaced buckets of two
+                                per octave (ties in any order); the image does not depend on it */
 } vis_ws_layout;
 
 /* Device-written status block at workspace offset off_ctrl (= 0). */

@@ -55,7 +55,7 @@ class vis_ws_layout(C.Structure):
                 ("off_rect", C.c_size_t), ("off_touched", C.c_size_t), ("off_keys", C.c_size_t * 2),
                 ("off_vals", C.c_size_t * 2), ("off_ranges", C.c_size_t), ("off_tfinal", C.c_size_t),
                 ("off_last", C.c_size_t), ("off_g2", C.c_size_t), ("key_bytes", C.c_int),
-                ("sort_mode", C.c_int)]
+                ("sort_mode", C.c_int), ("off_order", C.c_size_t)]
 
 
 _P = C.c_void_p

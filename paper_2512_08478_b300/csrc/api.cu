@@ -503,6 +503,7 @@ vis_status vis_workspace_layout(int64_t n, int W, int H, size_t ws_bytes, const 
     out->off_keys[0] = L.off_keys[0]; out->off_keys[1] = L.off_keys[1];
     out->off_vals[0] = L.off_vals[0]; out->off_vals[1] = L.off_vals[1];
     out->off_ranges = L.off_ranges; out->off_tfinal = L.off_tfinal; out->off_last = L.off_last;
+    out->off_order = L.tile_fused ? L.off_order : 0;
     out->off_g2 = L.off_g2;
     out->key_bytes = L.key_bytes;
     out->sort_mode = L.mode;

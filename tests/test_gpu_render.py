@@ -232,3 +232,27 @@ def test_compositor_statistics_do_not_change_the_image():
     # every composited pair is one the oracle composites too (up to flagged pixels)
     assert 0 < c["hits"] <= c["pair_tests"]
     assert abs(c["hits"] - int(ref["n_contrib"].sum())) <= max(10, 1e-4 * c["hits"])
+
+
+def test_tile_order_is_a_longest_first_permutation():
+    """The compositor's tile order: every tile once, by non-increasing key count up to the
+    width of a bucket (two per octave)."""
+    sc = synth.mixture_scene(300_000, 23, sh_degree=1)
+    cam = synth.look_at((0.0, 3.0, 15.0), (0, 0, 0), 1280, 720, 50.0)
+    _, _, s, ws = render_gpu(sc, cam)
+    L = ws.layout()
+    nt = L.tiles_x * L.tiles_y
+    assert L.key_bytes == 2 and L.off_order > 0
+    order = ws_view(ws, L.off_order, nt, np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(nt, dtype=np.uint32))
+    ranges = ws_view(ws, L.off_ranges, 2 * nt, np.uint32).reshape(nt, 2).astype(np.int64)
+    c = (ranges[:, 1] - ranges[:, 0])[order]
+    assert c.max() > 100 and (c == 0).any()
+
+    def bucket(x):   # 2 log2(x) rounded down to half octaves; empty tiles last
+        lg = np.floor(np.log2(np.maximum(x, 1))).astype(np.int64)
+        half = np.where(lg >= 1, (x >> np.maximum(lg - 1, 0)) & 1, 0)
+        return np.where(x == 0, -1, 2 * lg + half)
+    b = bucket(c)
+    assert np.all(np.diff(b) <= 0)
+
