@@ -341,17 +341,19 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
  * per frame with one global radix sort, Algorithm 1 "for all model M_k", section 3.4);
  * every (asset, camera) pair is an independent image. A batch handle is created with
  * `lanes`:
- *  lanes = 0   one fused pipeline over all images: one preprocess launch over the work
- *              list of items (each image's Gaussians in their own run of workspace slots),
- *              one depth sort of the survivors of every image, the tile copies emitted in
- *              that order with global tile ids (each image's tiles numbered after the
- *              previous image's), one stable sort by that id -- i.e. by (image, tile), keeping
- *              depth order inside each tile --, the tile ranges, and one compositor launch
- *              over all tiles of all images. It always uses the depth-first order
- *              (opts->sort_mode is ignored); opts->tile, digit_bits and pixels_per_thread
- *              apply to every image. key_capacity counts the tile copies of all images
- *              together. Each image is bit-identical to vis_render of the same (asset,
- *              camera, options).
+ *  lanes = 0   one fused pipeline: one preprocess launch over the work list of items (each
+ *              image's Gaussians in their own run of workspace slots); the images are
+ *              grouped, the widest first, and a group's images stacked as tile rows of one
+ *              canvas (a tile grid as wide as its widest image, at most 51200 tiles); each
+ *              group then runs the single-image pipeline over its canvas -- one depth sort of
+ *              the survivors of all its images, the tile copies emitted in that order with
+ *              canvas tile ids, the counts-first stable sort by that id (i.e. by image and
+ *              tile, keeping depth order inside each tile) and one compositor launch over the
+ *              canvas. It always uses the depth-first order (opts->sort_mode is ignored);
+ *              opts->tile, digit_bits and pixels_per_thread apply to every image. The groups
+ *              run on three streams, each with a scratch area: key_capacity bounds the tile
+ *              copies of each group (the copies of all images together always suffice). Each image is bit-identical to
+ *              vis_render of the same (asset, camera, options).
  *  lanes >= 1  per-image vis_render calls on that many streams forked from the batch's
  *              origin stream (longest-processing-time assignment of images to lanes), each
  *              lane in its own workspace slice of key_capacity keys.
@@ -368,7 +370,7 @@ VIS_API vis_status vis_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_
  *                          Gaussian slots in a fused batch
  * The first call synchronises nothing but must not itself be inside a stream capture.
  * Device errors of any image are returned by vis_batch_check (which synchronises); its
- * max_keys is the largest image's key count (lanes >= 1) or the batch's total (lanes = 0),
+ * max_keys is the largest image's key count (lanes >= 1) or the largest group's (lanes = 0),
  * the capacity a retry needs. */
 typedef struct vis_batch* vis_batch_t;
 VIS_API vis_status vis_batch_create(int lanes, vis_batch_t* out);

@@ -578,10 +578,11 @@ class Batch:
     """Many (asset, camera) images rendered by one vis_render_batch call (a CUDA graph).
 
     scenes: list of Scene; cams: list of cameras; cam_scene: asset index per image.
-    lanes = 0 (default): one fused pipeline over all images (one preprocess over the work
-    list, one depth sort, one sort by (image, tile), one compositor over all tiles); the
-    workspace holds `key_capacity` tile copies of all images together. lanes >= 1: per-image
-    renders on that many concurrent lanes, each a workspace slice of `key_capacity` keys.
+    lanes = 0 (default): one fused pipeline (one preprocess over the work list of all images,
+    then, per group of images stacked on one tile canvas, one depth sort, one counts-first sort
+    by canvas tile and one compositor over the canvas); the workspace holds `key_capacity` tile
+    copies per group (the default: all images' copies). lanes >= 1: per-image renders on that
+    many concurrent lanes, each a workspace slice of `key_capacity` keys.
     Outputs are allocated here.
     """
 

@@ -2,18 +2,20 @@
 // several models per frame with one global sort, Algorithm 1).
 //
 // Fused (a batch created with lanes = 0, the default of the Python binding): every
-// (asset, camera) image is one item of ONE pipeline over all of them --
-//   one preprocess launch over the work list of items (each item's Gaussians fill their
-//   own run of workspace slots, padded to whole blocks; the footprints record the image);
-//   one compaction of the survivors of every image and one depth sort of all of them;
-//   the tile copies emitted in that order with global tile ids (each image's tiles are
-//   numbered after the previous image's), and one stable sort by tile id, which yields
-//   (image, tile, depth, index) -- every image's own front-to-back order;
-//   the tile ranges, and one compositor launch over all tiles of all images, each CTA
-//   finding its image in the image table.
-// The whole sequence is captured once into a CUDA graph and replayed by later calls with
-// the same arguments; the item tables are uploaded before every launch. Each image is
-// bit-identical to vis_render of the same (asset, camera, options).
+// (asset, camera) image is one item of ONE preprocess launch over the work list of all of
+// them (each item's Gaussians fill their own run of workspace slots, padded to whole
+// blocks). The images are then taken in groups: a group's images are stacked as tile rows
+// of one canvas, a tile grid as wide as its widest image and of at most 51200 tiles, and
+// the preprocess writes each footprint in its canvas's rows. Every group runs the
+// single-image pipeline over its canvas -- compaction of its survivors, one depth sort of
+// all of them, the tile copies emitted in that order with 16-bit canvas tile ids, the
+// counts-first stable sort by tile id (which yields every image's own front-to-back order),
+// and one compositor launch over the canvas, longest tiles first, each CTA finding its
+// image in the group's image table. The groups run on three streams, each with a scratch area
+// sized for the largest group (the batch's key capacity applies to each group). The whole
+// sequence is captured once into a CUDA graph and replayed by later calls with the same
+// arguments; the item tables are uploaded before every launch. Each image is bit-identical
+// to vis_render of the same (asset, camera, options).
 //
 // Lanes (lanes >= 1, kept as a baseline): images are assigned to `lanes` streams forked
 // from the batch's origin stream by longest-processing-time scheduling on the estimated
@@ -51,13 +53,15 @@ __global__ void copy_status_kernel(const Ctrl* __restrict__ ctrl, uint32_t* __re
     status[1] = ctrl->error;
 }
 
-// fused batch: the one status block's key count (all images) and error bits into every
-// image's status word
-__global__ void copy_status_all_kernel(const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ status, int n) {
+// fused batch: a group's status block (key count of the group, error bits) into the status
+// word of each of its n images
+__global__ void copy_status_group_kernel(const Ctrl* __restrict__ ctrl, const BatchImage* __restrict__ images,
+                                         uint32_t* __restrict__ status, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        status[2 * i] = ctrl->num_keys;
-        status[2 * i + 1] = ctrl->error;
+        const int k = images[i].index;
+        status[2 * k] = ctrl->num_keys;
+        status[2 * k + 1] = ctrl->error;
     }
 }
 
@@ -105,81 +109,132 @@ Plan make_plan(const vis_scene_t* scenes, const int* cam_scene, const int* W, co
     return p;
 }
 
-int ceil_log2_b(int64_t v) {
-    int b = 0;
-    while (((int64_t)1 << b) < v) ++b;
-    return b;
-}
-
 int64_t pad_blocks(int64_t n) { return (n + vis::kPrepThreads - 1) / vis::kPrepThreads * vis::kPrepThreads; }
 
-// Workspace of a fused batch: the status words (2 per image), the region cleared before
-// every launch (status block, digit histograms, look-back words, ranges of every tile of
-// every image), the tables (the items' preprocess parameters in list order -- plain scenes,
-// then pre-packed ones --, each list's first blocks, the image table), then the per-slot and
-// per-copy buffers of the depth-first order over all slots.
-struct Fused {
-    vis::Layout L;
-    int64_t slots = 0, total_tiles = 0;
-    int n_list[2] = {0, 0};           // images of the plain and of the pre-packed list
-    int64_t blocks[2] = {0, 0};       // preprocess blocks of each list
-    size_t off_items = 0, off_blk0 = 0, off_images = 0, tables_end = 0;
+// Plan and workspace of a fused batch: the status words (2 per image); the tables (the
+// items' preprocess parameters in list order -- plain scenes, then pre-packed ones --, each
+// list's first blocks, the image table in group order); the per-slot buffers of all slots
+// (records, depths, footprints, counts, block sums); then one scratch area for a group's
+// pipeline, sized for the largest group: the single-image layout of the group's canvas
+// (make_layout) without its per-slot and adjoint buffers.
+struct Group {
+    int first = 0, count = 0;        // images [first, first + count) of the group order
+    int cw = 0, rows = 0;            // canvas: width in tiles, height in tile rows
+    int64_t slot_begin = 0, slots = 0;
 };
+
+struct Fused {
+    std::vector<int> order;          // group order -> image
+    std::vector<int> row0;           // image -> first canvas row
+    std::vector<int64_t> slot0;      // image -> first slot
+    std::vector<Group> groups;
+    int64_t slots = 0;
+    int n_list[2] = {0, 0};          // images of the plain and of the pre-packed list
+    int64_t blocks[2] = {0, 0};      // preprocess blocks of each list
+    int digit_bits = 8, tile = 16;
+    int64_t cap = 0;
+    size_t off_items = 0, off_blk0 = 0, off_images = 0, tables_end = 0;
+    size_t off_rec = 0, off_depth = 0, off_rect = 0, off_touched = 0, off_bsum = 0, off_boff = 0;
+    size_t off_scratch = 0, scratch_stride = 0, total = 0;
+    int n_scratch = 1;               // scratch areas: groups run on that many streams at once
+};
+
+// Streams (and scratch areas) of a fused batch: group g runs on stream g mod kFusedStreams,
+// so that one group's latency-bound sort overlaps another's compositor (two, three and four
+// measured: 25.0, 24.8 and 25.4 ms for the 128-image batch).
+constexpr int kFusedStreams = 3;
+
+// The single-image layout of group g's canvas, mapped onto the batch workspace: the scratch
+// regions of make_layout's order -- [status block .. tile order] and [scan totals .. values]
+// -- moved into the scratch area, the per-slot buffers pointing at the group's slots.
+vis::Layout group_layout(const Fused& F, const Group& g, int area, size_t* scratch_bytes = nullptr) {
+    vis::Layout L = vis::make_layout(g.slots, g.cw * F.tile, g.rows * F.tile, F.tile, F.cap, vis::kSortDepthFirst,
+                                     F.digit_bits);
+    // make_layout takes, in order: the cleared region (status .. tile counts), the tile
+    // order, the per-slot buffers (records .. block offsets), the scratch (scan totals ..
+    // values), then the adjoint and depth-buffer buffers
+    const size_t a_end = L.off_rec, b_begin = L.off_scan_tot, b_end = L.off_tfinal;
+    const size_t base = F.off_scratch + (size_t)area * F.scratch_stride, shift_b = base + a_end;
+    auto mv_a = [&](size_t& o) { o += base; };
+    auto mv_b = [&](size_t& o) { o = shift_b + (o - b_begin); };
+    mv_a(L.off_ctrl); mv_a(L.off_hist); mv_a(L.off_hist_tile); mv_a(L.off_lookback); mv_a(L.off_ranges);
+    mv_a(L.off_tdiff); mv_a(L.off_order); mv_a(L.zero_begin); mv_a(L.zero_end);
+    mv_b(L.off_scan_tot); mv_b(L.off_bsum2); mv_b(L.off_boff2);
+    for (int k = 0; k < 2; ++k) { mv_b(L.off_dkeys[k]); mv_b(L.off_dvals[k]); mv_b(L.off_keys[k]); mv_b(L.off_vals[k]); }
+    L.off_rec = F.off_rec + sizeof(float4) * 3 * (size_t)g.slot_begin;
+    L.off_depth = F.off_depth + sizeof(float) * (size_t)g.slot_begin;
+    L.off_rect = F.off_rect + sizeof(uint4) * (size_t)g.slot_begin;
+    L.off_touched = F.off_touched + sizeof(uint32_t) * (size_t)g.slot_begin;
+    L.off_bsum = F.off_bsum + sizeof(uint32_t) * (size_t)(g.slot_begin / vis::kPrepThreads);
+    L.off_boff = F.off_boff + sizeof(uint32_t) * (size_t)(g.slot_begin / vis::kPrepThreads);
+    L.off_tfinal = L.off_last = L.off_g2 = L.off_zmax = 0;   // not used by a batch
+    if (scratch_bytes) *scratch_bytes = a_end + (b_end - b_begin);
+    return L;
+}
 
 Fused fused_layout(const std::vector<int64_t>& n_img, const std::vector<char>& packed, const int* W, const int* H,
                    int n_images, int tile, int64_t cap, int digit_bits) {
     Fused F;
+    F.tile = tile;
+    F.cap = cap;
+    F.digit_bits = digit_bits;
+    std::vector<int> tx(n_images), ty(n_images);
     for (int i = 0; i < n_images; ++i) {
-        F.slots += pad_blocks(n_img[i]);
-        F.total_tiles += (int64_t)((W[i] + tile - 1) / tile) * ((H[i] + tile - 1) / tile);
+        tx[i] = (W[i] + tile - 1) / tile;
+        ty[i] = (H[i] + tile - 1) / tile;
         F.n_list[packed[i] ? 1 : 0] += 1;
         F.blocks[packed[i] ? 1 : 0] += pad_blocks(n_img[i]) / vis::kPrepThreads;
     }
-    vis::Layout& L = F.L;
-    L.mode = vis::kSortDepthFirst;
-    L.n = F.slots;
-    L.tile = tile;
-    L.ntiles = F.total_tiles;
-    L.tile_bits = ceil_log2_b(F.total_tiles > 1 ? F.total_tiles : 2);
-    L.key_bits = L.tile_bits;
-    L.digit_bits = digit_bits;
-    L.depth_passes = vis::passes_for(32, digit_bits);
-    L.passes = vis::passes_for(L.tile_bits, digit_bits);
-    L.key_bytes = 4;
-    L.cap = cap;
-    L.prep_blocks = F.slots / vis::kPrepThreads;
-    L.sort_parts = (cap + (int64_t)vis::kSortThreads * 16 - 1) / ((int64_t)vis::kSortThreads * 16);
-    L.sorted_buffer = L.passes & 1;
-    L.tile_fused = false;
-    const size_t D = (size_t)1 << digit_bits;
+    // groups: the images by decreasing width, stacked while the canvas holds at most
+    // kTileFusedMaxTiles tiles (an image larger than that is a group of its own, sorted with
+    // 32-bit tile ids)
+    F.order.resize(n_images);
+    for (int i = 0; i < n_images; ++i) F.order[i] = i;
+    std::stable_sort(F.order.begin(), F.order.end(), [&](int a, int b) {
+        return tx[a] != tx[b] ? tx[a] > tx[b] : ty[a] > ty[b];
+    });
+    F.row0.assign(n_images, 0);
+    F.slot0.assign(n_images, 0);
+    for (int k = 0; k < n_images; ++k) {
+        const int i = F.order[k];
+        if (F.groups.empty() ||
+            (int64_t)(F.groups.back().rows + ty[i]) * F.groups.back().cw > (int64_t)vis::kTileFusedMaxTiles) {
+            Group g;
+            g.first = k;
+            g.cw = tx[i];
+            g.slot_begin = F.slots;
+            F.groups.push_back(g);
+        }
+        Group& g = F.groups.back();
+        F.row0[i] = g.rows;
+        F.slot0[i] = F.slots;
+        g.rows += ty[i];
+        g.count += 1;
+        F.slots += pad_blocks(n_img[i]);
+        g.slots = F.slots - g.slot_begin;
+    }
     size_t off = status_bytes(n_images);
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.zero_begin = off;
-    L.off_ctrl = take(sizeof(vis::Ctrl));
-    L.off_hist = take(sizeof(uint32_t) * vis::kMaxPasses * D);
-    L.off_hist_tile = take(sizeof(uint32_t) * vis::kMaxPasses * D);
-    L.lookback_words_depth = (size_t)L.depth_passes * vis::depth_sort_parts(F.slots, digit_bits) * D;
-    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * D));
-    L.off_ranges = take(sizeof(uint2) * (size_t)F.total_tiles);
-    L.zero_end = off;
     F.off_items = take(sizeof(vis::PrepParams) * (size_t)n_images);
     F.off_blk0 = take(sizeof(uint32_t) * (size_t)n_images);
     F.off_images = take(sizeof(vis::BatchImage) * (size_t)n_images);
     F.tables_end = off;
-    L.off_rec = take(sizeof(float4) * 3 * (size_t)F.slots);
-    L.off_depth = take(sizeof(float) * (size_t)F.slots);
-    L.off_rect = take(sizeof(uint4) * (size_t)F.slots);
-    L.off_touched = take(sizeof(uint32_t) * (size_t)F.slots);
-    L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    L.off_scan_tot = take(sizeof(unsigned long long) * (size_t)vis::kMaxScanChunks);
-    L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    for (int k = 0; k < 2; ++k) L.off_dkeys[k] = take(sizeof(uint32_t) * (size_t)F.slots);
-    for (int k = 0; k < 2; ++k) L.off_dvals[k] = take(sizeof(uint32_t) * (size_t)F.slots);
-    for (int k = 0; k < 2; ++k) L.off_keys[k] = take(sizeof(uint32_t) * (size_t)cap);
-    for (int k = 0; k < 2; ++k) L.off_vals[k] = take(sizeof(uint32_t) * (size_t)cap);
-    L.total = off;
+    F.off_rec = take(sizeof(float4) * 3 * (size_t)F.slots);
+    F.off_depth = take(sizeof(float) * (size_t)F.slots);
+    F.off_rect = take(sizeof(uint4) * (size_t)F.slots);
+    F.off_touched = take(sizeof(uint32_t) * (size_t)F.slots);
+    F.off_bsum = take(sizeof(uint32_t) * (size_t)(F.slots / vis::kPrepThreads));
+    F.off_boff = take(sizeof(uint32_t) * (size_t)(F.slots / vis::kPrepThreads));
+    F.off_scratch = off;
+    size_t scratch = 0;
+    for (const Group& g : F.groups) {
+        size_t b = 0;
+        group_layout(F, g, 0, &b);
+        scratch = std::max(scratch, b);
+    }
+    F.n_scratch = (int)std::min<size_t>(kFusedStreams, F.groups.size());
+    F.scratch_stride = align256(scratch);
+    F.total = F.off_scratch + (size_t)F.n_scratch * F.scratch_stride;
     return F;
 }
 
@@ -207,11 +262,11 @@ vis_status fused_inputs(const vis_scene_t* scenes, int n_scenes, const int* cam_
 
 int64_t fused_capacity(const std::vector<int64_t>& n_img, const std::vector<char>& packed, const int* W, const int* H,
                        int n_images, int tile, int digit_bits, size_t ws_bytes) {
-    if (fused_layout(n_img, packed, W, H, n_images, tile, 1, digit_bits).L.total > ws_bytes) return 0;
+    if (fused_layout(n_img, packed, W, H, n_images, tile, 1, digit_bits).total > ws_bytes) return 0;
     int64_t lo = 1, hi = vis::kMaxKeys;
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;
-        if (fused_layout(n_img, packed, W, H, n_images, tile, mid, digit_bits).L.total <= ws_bytes) lo = mid;
+        if (fused_layout(n_img, packed, W, H, n_images, tile, mid, digit_bits).total <= ws_bytes) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -234,13 +289,14 @@ vis_status vis_batch_create(int lanes, vis_batch_t* out) {
     if (!b) return fail_b(VIS_ERR_INVALID_ARG, "out of host memory");
     b->lanes = lanes;
     cudaGetDevice(&b->device);
-    b->streams.resize(lanes);
-    b->join_ev.resize(lanes);
+    const int n_streams = lanes > 0 ? lanes : kFusedStreams;   // lanes, or the fused groups' streams
+    b->streams.resize(n_streams);
+    b->join_ev.resize(n_streams);
     cudaError_t e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->in_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->out_ev, cudaEventDisableTiming);
-    for (int l = 0; l < lanes && e == cudaSuccess; ++l) {
+    for (int l = 0; l < n_streams && e == cudaSuccess; ++l) {
         e = cudaStreamCreateWithFlags(&b->streams[l], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[l], cudaEventDisableTiming);
     }
@@ -279,7 +335,7 @@ vis_status vis_batch_workspace_size(const vis_scene_t* scenes, int n_scenes, con
         std::vector<int64_t> n_img;
         std::vector<char> packed;
         if ((st = fused_inputs(scenes, n_scenes, cam_scene, W, H, n_images, &n_img, &packed))) return st;
-        *bytes = fused_layout(n_img, packed, W, H, n_images, o.tile, key_capacity, o.digit_bits).L.total;
+        *bytes = fused_layout(n_img, packed, W, H, n_images, o.tile, key_capacity, o.digit_bits).total;
         vis::set_last_error("");
         return VIS_OK;
     }
@@ -317,8 +373,7 @@ static vis_status render_fused(vis_batch_t b, const vis_scene_t* scenes, int n_s
     const int64_t cap = fused_capacity(n_img, packed, W, H, n_images, o.tile, o.digit_bits, ws_bytes);
     if (cap < 1) return fail_b(VIS_ERR_INVALID_ARG, "batch workspace too small");
     const Fused F = fused_layout(n_img, packed, W, H, n_images, o.tile, cap, o.digit_bits);
-    vis::Layout L = F.L;
-    L.spin_limit = o.spin_limit > 0 ? (uint32_t)o.spin_limit : vis::kSpinLimit;
+    const uint32_t spin = o.spin_limit > 0 ? (uint32_t)o.spin_limit : vis::kSpinLimit;
     char* w = static_cast<char*>(ws);
 
     std::vector<unsigned char> key;
@@ -337,29 +392,38 @@ static vis_status render_fused(vis_batch_t b, const vis_scene_t* scenes, int n_s
     }
     if (!b->exec || key != b->key) {
         // the item tables: preprocess parameters in list order (plain scenes, then pre-packed
-        // ones), each list's first blocks, and the image table in image order
+        // ones, each in group order), each list's first blocks, and the image table in group
+        // order
         std::vector<vis::PrepParams> items(n_images);
         std::vector<uint32_t> blk0(n_images);
         std::vector<vis::BatchImage> images(n_images);
         int pos[2] = {0, F.n_list[0]};
-        int64_t nb[2] = {0, 0}, slot0 = 0, tile0 = 0;
-        for (int i = 0; i < n_images; ++i) {
+        int64_t nb[2] = {0, 0};
+        for (int k = 0; k < n_images; ++k) {
+            const int i = F.order[k];
             const int lst = packed[i] ? 1 : 0;
             vis::PrepParams p;
-            if ((st = vis::batch_item(scenes[cam_scene[i]], &cams[i], W[i], H[i], o, slot0, (uint32_t)i, &p))) return st;
+            if ((st = vis::batch_item(scenes[cam_scene[i]], &cams[i], W[i], H[i], o, F.slot0[i], (uint32_t)i, &p)))
+                return st;
+            p.canvas_row0 = (uint32_t)F.row0[i];
             items[pos[lst]] = p;
             blk0[pos[lst]] = (uint32_t)nb[lst];
             ++pos[lst];
             nb[lst] += pad_blocks(n_img[i]) / vis::kPrepThreads;
-            const int tx = (W[i] + o.tile - 1) / o.tile, ty = (H[i] + o.tile - 1) / o.tile;
-            vis::BatchImage im;
-            std::memset(&im, 0, sizeof(im));
-            im.slot0 = slot0; im.tile0 = (uint32_t)tile0; im.W = W[i]; im.H = H[i]; im.tiles_x = tx; im.tiles_y = ty;
-            im.out_rgb = out_rgb[i]; im.out_alpha = out_alpha[i];
-            images[i] = im;
-            slot0 += pad_blocks(n_img[i]);
-            tile0 += (int64_t)tx * ty;
         }
+        for (const Group& g : F.groups)
+            for (int k = g.first; k < g.first + g.count; ++k) {
+                const int i = F.order[k];
+                vis::BatchImage im;
+                std::memset(&im, 0, sizeof(im));
+                im.slot0 = F.slot0[i] - g.slot_begin;
+                im.tile0 = (uint32_t)((int64_t)F.row0[i] * g.cw);
+                im.W = W[i]; im.H = H[i];
+                im.tiles_x = (W[i] + o.tile - 1) / o.tile; im.tiles_y = (H[i] + o.tile - 1) / o.tile;
+                im.index = i;
+                im.out_rgb = out_rgb[i]; im.out_alpha = out_alpha[i];
+                images[k] = im;
+            }
         b->tables.assign(F.tables_end - F.off_items, 0);
         std::memcpy(b->tables.data(), items.data(), sizeof(vis::PrepParams) * n_images);
         std::memcpy(b->tables.data() + (F.off_blk0 - F.off_items), blk0.data(), sizeof(uint32_t) * n_images);
@@ -374,16 +438,36 @@ static vis_status render_fused(vis_batch_t b, const vis_scene_t* scenes, int n_s
         cudaStream_t s = b->origin;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return fail_b(VIS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-        cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, s);
-        vis::launch_preprocess_batch(d_items, d_blk0, F.n_list[0], F.blocks[0], false, L, w, s);
-        vis::launch_preprocess_batch(d_items + F.n_list[0], d_blk0 + F.n_list[0], F.n_list[1], F.blocks[1], true, L,
+        // the preprocess of every item (the per-slot buffers of all slots)
+        vis::Layout Lp;
+        Lp.off_rec = F.off_rec; Lp.off_depth = F.off_depth; Lp.off_rect = F.off_rect;
+        Lp.off_touched = F.off_touched; Lp.off_bsum = F.off_bsum;
+        vis::launch_preprocess_batch(d_items, d_blk0, F.n_list[0], F.blocks[0], false, Lp, w, s);
+        vis::launch_preprocess_batch(d_items + F.n_list[0], d_blk0 + F.n_list[0], F.n_list[1], F.blocks[1], true, Lp,
                                      w, s);
-        vis::launch_depth_first(L, w, s, nullptr, 0, d_images);
-        vis::launch_ranges32(L, w, s);
-        vis::launch_composite_batch(L, w, d_images, n_images, F.total_tiles, bg[0], bg[1], bg[2], o.alpha_min,
-                                    o.alpha_max, o.t_stop, o.pixels_per_thread, s);
-        vis::copy_status_all_kernel<<<(n_images + 255) / 256, 256, 0, s>>>(
-            reinterpret_cast<const vis::Ctrl*>(w + L.off_ctrl), reinterpret_cast<uint32_t*>(w), n_images);
+        // then every group's canvas through the single-image pipeline, groups on
+        // F.n_scratch streams forked from the origin, each stream with its scratch area
+        cudaEventRecord(b->fork_ev, s);
+        for (int k = 0; k < F.n_scratch; ++k) cudaStreamWaitEvent(b->streams[k], b->fork_ev, 0);
+        for (size_t gi = 0; gi < F.groups.size(); ++gi) {
+            const Group& g = F.groups[gi];
+            const int area = (int)(gi % (size_t)F.n_scratch);
+            cudaStream_t gs = b->streams[area];
+            vis::Layout L = group_layout(F, g, area);
+            L.spin_limit = spin;
+            cudaMemsetAsync(w + L.zero_begin, 0, L.zero_end - L.zero_begin, gs);
+            vis::launch_depth_first(L, w, gs, nullptr, 0);
+            if (!L.tile_fused) vis::launch_ranges32(L, w, gs);
+            vis::launch_composite_batch(L, w, d_images + g.first, g.count, L.ntiles, bg[0], bg[1], bg[2],
+                                        o.alpha_min, o.alpha_max, o.t_stop, o.pixels_per_thread, gs);
+            vis::copy_status_group_kernel<<<(g.count + 255) / 256, 256, 0, gs>>>(
+                reinterpret_cast<const vis::Ctrl*>(w + L.off_ctrl), d_images + g.first, reinterpret_cast<uint32_t*>(w),
+                g.count);
+        }
+        for (int k = 0; k < F.n_scratch; ++k) {
+            cudaEventRecord(b->join_ev[k], b->streams[k]);
+            cudaStreamWaitEvent(s, b->join_ev[k], 0);
+        }
         e = cudaStreamEndCapture(s, &graph);
         if (e != cudaSuccess) return fail_b(VIS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
         e = cudaGraphInstantiate(&b->exec, graph, 0);

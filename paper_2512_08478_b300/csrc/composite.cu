@@ -74,15 +74,18 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     const uint32_t gtile = order ? order[blockIdx.x] : blockIdx.x;
     int tile = (int)gtile;
     if (BATCH) {
-        // a batch's tiles are numbered image after image: find this tile's image (the last
-        // whose first tile is <= gtile) and take its size and outputs
+        // a batch group's canvas (tiles_x tiles wide) stacks its images' tile rows: find this
+        // tile's image (the last whose first tile is <= gtile) and take its size and outputs; a
+        // canvas tile right of a narrower image has no pixels
         int lo = 0, hi = n_images - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (images[mid].tile0 <= gtile) lo = mid; else hi = mid - 1;
         }
         const BatchImage im = images[lo];
-        tile = (int)(gtile - im.tile0);
+        const int t = (int)(gtile - im.tile0), cx = t % tiles_x, cy = t / tiles_x;
+        if (cx >= im.tiles_x) return;
+        tile = cy * im.tiles_x + cx;
         W = im.W; H = im.H; tiles_x = im.tiles_x;
         out_rgb = im.out_rgb; out_alpha = im.out_alpha;
     }
@@ -320,11 +323,12 @@ void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images,
     const int blocks = (int)total_tiles;
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
+    const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
 #define VIS_LAUNCH_COMPOSITE_B(TS, PP)                                                                         \
     launch_k(true, composite_kernel<TS, PP, false, false, true>, blocks, TS * TS / PP, 0, stream, ranges, vals, \
-             rec, 0, 0, 1, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,             \
+             rec, 0, 0, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,      \
              (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images, \
-             (const uint32_t*)nullptr)
+             order)
     const bool two = ppt == 2;
     if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE_B(8, 2); else VIS_LAUNCH_COMPOSITE_B(8, 1); }
     else if (L.tile == 32) { if (two) VIS_LAUNCH_COMPOSITE_B(32, 2); else VIS_LAUNCH_COMPOSITE_B(32, 1); }

@@ -77,16 +77,13 @@ depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict_
     }
 }
 
-// KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles. BATCH (a fused batch):
-// the footprint's last word is the slot's image, whose tiles are numbered from
-// images[item].tile0 on a grid of images[item].tiles_x columns; otherwise tile ids are
+// KT: uint32_t tile ids, or uint16_t on grids of at most 65536 tiles; tile ids are
 // y * tiles_x + x.
-template <typename KT, bool BATCH>
+template <typename KT>
 __global__ void __launch_bounds__(kPrepThreads)
 emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, int64_t n,
            const uint32_t* __restrict__ boff, int tiles_x,
-           const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals,
-           const BatchImage* __restrict__ images) {
+           const Ctrl* __restrict__ ctrl, KT* __restrict__ keys, uint32_t* __restrict__ vals) {
     pdl_entry();
     if (ctrl->error) return;   // capacity exceeded, or a sort that timed out
     // per splat slot: start of its copies in the warp's run, and its footprint unrolled into
@@ -106,12 +103,7 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, i
         const Footprint f = fp_unpack(r);
         cnt = fp_count(f);
         if (cnt > 0) {
-            uint32_t tx = (uint32_t)tiles_x, t0 = 0;
-            if (BATCH) {
-                const BatchImage& im = images[r.w];
-                tx = (uint32_t)im.tiles_x;
-                t0 = im.tile0;
-            }
+            const uint32_t tx = (uint32_t)tiles_x, t0 = 0;
             const uint32_t W = f.x1 - f.x0, rows = f.y1 - f.y0;
             const uint32_t wt = fp_top_width(f);
             const uint32_t mid = rows > 1 ? (rows - 2) * W : 0;
@@ -243,8 +235,7 @@ bool side_join_point(SideStream* side, cudaStream_t stream) {
     return false;
 }
 
-void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
-                        const BatchImage* images) {
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     const int blocks_n = (int)L.prep_blocks;
@@ -253,7 +244,7 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // The per-tile counts of the counts-first tile sort need only the footprints: outside a
     // profiled render they run on a side stream, beside the depth sort and the emission
     // (which leave most SMs idle at a million splats), and join before the tile passes.
-    SideStream* side = (L.tile_fused && !images && !mark) ? side_stream(stream) : nullptr;
+    SideStream* side = (L.tile_fused && !mark) ? side_stream(stream) : nullptr;
     if (side && !side_fork(side, stream)) side = nullptr;
     bool counted = false;   // the counts were queued on the side stream
     if (side) {
@@ -270,13 +261,13 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
              (const Ctrl*)ctrl, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap,
                      reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
-    if (L.tile_fused && !images) {
+    if (L.tile_fused) {
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)
-        launch_k(true, emit_tiles<uint16_t, false>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
+        launch_k(true, emit_tiles<uint16_t>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
                  reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
                  (const Ctrl*)ctrl, reinterpret_cast<uint16_t*>(ws + L.off_keys[0]),
-                 reinterpret_cast<uint32_t*>(ws + L.off_vals[0]), (const BatchImage*)nullptr);
+                 reinterpret_cast<uint32_t*>(ws + L.off_vals[0]));
         if (mark) mark(mark_index + 1, stream);
         if (side) cudaStreamWaitEvent(stream, side->join, 0);
         else if (!counted) launch_tile_counts(L, ws, stream);
@@ -288,14 +279,8 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    if (images)   // a fused batch: global tile ids, image after image
-        launch_k(true, emit_tiles<uint32_t, true>, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0,
-                 reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, (const uint32_t*)boff2, L.tiles_x,
-                 (const Ctrl*)ctrl, k0, v0, images);
-    else
-        emit_tiles<uint32_t, false><<<blocks_n, kPrepThreads, 0, stream>>>(
-            dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, boff2, L.tiles_x, ctrl, k0, v0,
-            (const BatchImage*)nullptr);
+    emit_tiles<uint32_t><<<blocks_n, kPrepThreads, 0, stream>>>(
+        dv0, reinterpret_cast<const uint4*>(ws + L.off_rect), L.n, boff2, L.tiles_x, ctrl, k0, v0);
     if (mark) mark(mark_index + 1, stream);
     // 4. stable sort by tile id; the result lands in buffer L.sorted_buffer
     const int tp = L.passes;

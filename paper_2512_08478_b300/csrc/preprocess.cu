@@ -364,6 +364,7 @@ __device__ __forceinline__ void preprocess_block(const PrepParams& p, int local_
             }
         }
         if (touched == 0) { x0 = x1 = y0 = y1 = 0; trims = 0; }
+        else { y0 += p.canvas_row0; y1 += p.canvas_row0; }   // a batch image's rows in its canvas
         rect_out[gi] = make_uint4(x0 | (x1 << 16), y0 | (y1 << 16), trims, item);
         touched_out[gi] = touched;
     } else if (i < p.n_pad) {   // padding slots of a multi-scene render or a batch: no copies

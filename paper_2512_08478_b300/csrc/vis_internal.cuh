@@ -158,17 +158,19 @@ struct PrepParams {
     int n_pad;               // n rounded up to kPrepThreads in a multi-scene render (else n)
     float shc[12];           // SH polynomial constants, see sh_constants()
     uint32_t batch_image;    // a fused batch: the item's image index (kept in the footprints)
-    uint32_t pad1;
+    uint32_t canvas_row0;    // a fused batch: the image's first tile row in its group's canvas
 };
 
 // One image of a fused batch (vis_render_batch with lanes = 0): its (asset, camera) item's
-// Gaussians occupy the workspace slots [slot0, slot0 + n) and its tiles the global tile
-// ids [tile0, tile0 + tiles_x * tiles_y); images are listed in increasing tile0.
+// Gaussians occupy the workspace slots [slot0, slot0 + n), and its tiles the rows
+// [tile0 / cw, tile0 / cw + tiles_y) x columns [0, tiles_x) of its group's canvas, a tile grid
+// cw tiles wide (tile0 = its first row times cw). A group's images are listed in increasing
+// tile0.
 struct BatchImage {
     int64_t slot0;
     uint32_t tile0;
     int W, H, tiles_x, tiles_y;
-    int pad0;
+    int index;          // the image's index in the batch (its status word)
     float* out_rgb;     // [3][H][W]
     float* out_alpha;   // [H][W]
 };
@@ -303,10 +305,8 @@ void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uin
                       int64_t cap, unsigned long long* chunk_tot, cudaStream_t stream);
 // Depth-first mode: compaction and depth sort (then mark(mark_index)), emission (then
 // mark(mark_index + 1)), tile counts or the tile histogram (then mark(mark_index + 2)), tile
-// passes. With `images` (a fused batch; the footprints carry their image) the
-// copies take global tile ids and the 32-bit tile sort runs. Ranges for its 32-bit tile keys:
-void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index,
-                        const BatchImage* images = nullptr);
+// passes. Beyond the counts-first grids the 32-bit tile sort runs; ranges for its keys:
+void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index);
 // Compaction of the surviving splats and their stable sort by depth (result in dvals[0]).
 void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream);
 void launch_ranges32(const Layout& L, char* ws, cudaStream_t stream);
@@ -320,8 +320,10 @@ QScale q_scale();
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       const float* zlim, cudaStream_t stream);
-// Compositor over every tile of a fused batch (global tile ids, image table `images` in
-// device memory), forward only.
+// Compositor over the canvas of one group of a fused batch (L: the group's layout, its
+// canvas L.tiles_x tiles wide; `images`: the group's n_images entries of the image table in
+// device memory), forward only; with the counts-first tile sort the tiles are taken longest
+// first.
 void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images, int n_images, int64_t total_tiles,
                             float bg0, float bg1, float bg2, float alpha_min, float alpha_max, float t_stop, int ppt,
                             cudaStream_t stream);
