@@ -563,7 +563,7 @@ def batch_leg(args):
                 lanes8_ms=round(t_lanes, 4), sequential_ms=round(t_seq, 4),
                 speedup_vs_sequential=round(t_seq / t_fused, 3), speedup_vs_lanes=round(t_lanes / t_fused, 3),
                 images_identical_to_sequential=bool(same_seq), images_identical_to_lanes=bool(same_lanes),
-                keys_per_batch=int(keys), gaussian_views_per_s=round(n_g / t_fused * 1e3, 1),
+                keys_largest_group=int(keys), gaussian_views_per_s=round(n_g / t_fused * 1e3, 1),
                 autotune=dict(best_ms=tuned_ms, tried=tried), clocks=clk_fused,
                 clocks_lanes=clk_lanes, clocks_sequential=clk_seq)
 
