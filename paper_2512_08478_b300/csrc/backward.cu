@@ -52,6 +52,16 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return y;
 }
 
+// The warp's nine gradient terms of one splat summed over the warp and added to dst[0..8]
+// (one lane per value; zero sums are skipped).
+__device__ __forceinline__ void warp_add_gradients(const float g[9], int lane, float* dst) {
+    int which;
+    const float t8 = warp_sum8_transposed(g, lane, &which);
+    const float t9 = warp_sum(g[8]);
+    if ((lane & 3) == 0 && t8 != 0.f) atomicAdd(dst + which, t8);
+    if (lane == 1 && t9 != 0.f) atomicAdd(dst + 8, t9);
+}
+
 template <int TILE, int PPT, bool DEPTH>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
@@ -68,7 +78,10 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
     constexpr int BX = TILE / 8, BH = 4 * PPT;
     constexpr int CH = NT < 256 ? NT : 256;   // splats staged per chunk
     static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
-    __shared__ float4 s_a[CH], s_b[CH], s_c[CH];
+    // staged splats, NS float4 slots each: PPT 1 -> (du, dv, f1x, f1y), (f2x, f2y, thr, opacity),
+    // (r, g, b, depth); PPT 2 -> packed pairs for the f32x2 instructions (see the pair walk)
+    constexpr int NS = PPT == 1 ? 3 : 6;
+    __shared__ float4 s_st[NS][CH];
     __shared__ uint32_t s_g[CH], s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
     const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;   // longest tiles first if ordered
@@ -122,14 +135,24 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
         const int cnt = (int)(top - lo);
         __syncthreads();
         if (threadIdx.x < cnt) {
-            const uint32_t g = vals[lo + threadIdx.x];
-            StagedSplat st = stage_splat(rec, g, xc, yc, qcut, alpha_min);
-            if (DEPTH) st.c.w = depth[g];
-            s_g[threadIdx.x] = g;
-            s_a[threadIdx.x] = st.a;
-            s_b[threadIdx.x] = st.b;
-            s_c[threadIdx.x] = st.c;
-            s_mask[threadIdx.x] = warp_block_mask<NW, BX, BH>(st, half);
+            const int t = threadIdx.x;
+            const uint32_t g = vals[lo + t];
+            const StagedSplat st = stage_splat(rec, g, xc, yc, qcut, alpha_min);
+            const float z = DEPTH ? depth[g] : 0.f;
+            s_g[t] = g;
+            if constexpr (PPT == 1) {
+                s_st[0][t] = st.a;
+                s_st[1][t] = st.b;
+                s_st[2][t] = make_float4(st.c.x, st.c.y, st.c.z, z);
+            } else {
+                s_st[0][t] = make_float4(-st.a.x, -st.a.x, -st.a.y, -st.a.y);
+                s_st[1][t] = make_float4(st.a.z, st.a.z, st.b.x, st.b.x);
+                s_st[2][t] = make_float4(st.a.w, st.a.w, st.b.y, st.b.y);
+                s_st[3][t] = make_float4(st.b.z, z, st.b.w, st.b.w);
+                s_st[4][t] = make_float4(st.c.x, st.c.x, st.c.y, st.c.y);
+                s_st[5][t] = make_float4(st.c.z, st.c.z, 0.f, 0.f);
+            }
+            s_mask[t] = warp_block_mask<NW, BX, BH>(st, half);
         }
         __syncthreads();
         // this warp's list of splats whose 3-sigma box meets its block, in depth order
@@ -142,59 +165,131 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
             nlist += __popc(bal);
         }
         __syncwarp();
+        if constexpr (PPT == 1) {
         for (int i = nlist - 1; i >= 0; --i) {     // back to front
             const int k = s_list[warp][i];
             const int64_t pos = lo + k;   // sorted position of this splat
-            const float4 a = s_a[k], b = s_b[k], c = s_c[k];
-            // this thread's gradient terms, summed over its pixels
+            const float4 a = s_st[0][k], b = s_st[1][k], c = s_st[2][k];
+            // this thread's gradient terms
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool contrib = false;
-#pragma unroll
-            for (int q = 0; q < PPT; ++q) {
-                if (!(inside[q] && pos < (int64_t)last[q])) continue;
+            const int q = 0;
+            if (inside[q] && pos < (int64_t)last[q]) {
                 const PairEval e = eval_pair(lx, ly[q], a, b);
                 // the forward's decisions: 3-sigma cut and alpha_min (and the depth test)
-                if (!(e.q <= b.z && (!DEPTH || c.w <= dl[q]))) continue;
-                contrib = true;
-                const float G = gauss_of_qs(e.q);
-                const float raw = __fmul_rn(b.w, G);
-                const float alpha = fminf(alpha_max, raw);
-                const float om = __fsub_rn(1.f, alpha);
-                // 1 / (1 - alpha) with alpha <= alpha_max < 1: one approximate reciprocal
-                // (relative error ~1e-7 per splat, far inside the gradients' tolerance)
-                float inv_om;
-                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv_om) : "f"(om));
-                T[q] = T[q] * inv_om;                      // T before this splat
-                const float w = alpha * T[q];
-                g[6] += gC0[q] * w; g[7] += gC1[q] * w; g[8] += gC2[q] * w;
-                float ga = T[q] * ((c.x - S0[q]) * gC0[q] + (c.y - S1[q]) * gC1[q] + (c.z - S2[q]) * gC2[q]);
-                ga += aterm[q] * inv_om;
-                S0[q] = c.x * alpha + om * S0[q];
-                S1[q] = c.y * alpha + om * S1[q];
-                S2[q] = c.z * alpha + om * S2[q];
-                if (raw <= alpha_max) {   // clamp inactive
-                    g[5] += ga * G;
-                    // G = exp(-q/2) in the unscaled q = d^T S^-1 d: dL/dq = -ga opacity G / 2
-                    const float gq = -0.5f * ga * raw;
-                    // dq/dd = 2 S^-1 d = 2 (f1 p1 + f2 p2) / c for the scaled rows f, p, and
-                    // d = pixel - (u, v): dL/du = -2 gq (f1 p1 + f2 p2)_x / c
-                    const float gu = -2.f * inv_scale * gq;
-                    g[0] += gu * (a.z * e.p1 + b.x * e.p2);
-                    g[1] += gu * (a.w * e.p1 + b.y * e.p2);
-                    const float gdx = gq * e.dx;
-                    g[2] += gdx * e.dx;
-                    g[3] += 2.f * gdx * e.dy;
-                    g[4] += gq * e.dy * e.dy;
+                if (e.q <= b.z && (!DEPTH || c.w <= dl[q])) {
+                    contrib = true;
+                    const float G = gauss_of_qs(e.q);
+                    const float raw = __fmul_rn(b.w, G);
+                    const float alpha = fminf(alpha_max, raw);
+                    const float om = __fsub_rn(1.f, alpha);
+                    // 1 / (1 - alpha) with alpha <= alpha_max < 1: one approximate reciprocal
+                    // (relative error ~1e-7 per splat, far inside the gradients' tolerance)
+                    float inv_om;
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv_om) : "f"(om));
+                    T[q] = T[q] * inv_om;                      // T before this splat
+                    const float w = alpha * T[q];
+                    g[6] = gC0[q] * w; g[7] = gC1[q] * w; g[8] = gC2[q] * w;
+                    float ga = T[q] * ((c.x - S0[q]) * gC0[q] + (c.y - S1[q]) * gC1[q] + (c.z - S2[q]) * gC2[q]);
+                    ga += aterm[q] * inv_om;
+                    S0[q] = c.x * alpha + om * S0[q];
+                    S1[q] = c.y * alpha + om * S1[q];
+                    S2[q] = c.z * alpha + om * S2[q];
+                    if (raw <= alpha_max) {   // clamp inactive
+                        g[5] = ga * G;
+                        // G = exp(-q/2) in the unscaled q = d^T S^-1 d: dL/dq = -ga opacity G / 2
+                        const float gq = -0.5f * ga * raw;
+                        // dq/dd = 2 S^-1 d = 2 (f1 p1 + f2 p2) / c for the scaled rows f, p, and
+                        // d = pixel - (u, v): dL/du = -2 gq (f1 p1 + f2 p2)_x / c
+                        const float gu = -2.f * inv_scale * gq;
+                        g[0] = gu * (a.z * e.p1 + b.x * e.p2);
+                        g[1] = gu * (a.w * e.p1 + b.y * e.p2);
+                        const float gdx = gq * e.dx;
+                        g[2] = gdx * e.dx;
+                        g[3] = 2.f * gdx * e.dy;
+                        g[4] = gq * e.dy * e.dy;
+                    }
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                int which;
-                const float t8 = warp_sum8_transposed(g, lane, &which);
-                const float t9 = warp_sum(g[8]);
-                float* dst = g2 + 9 * (size_t)s_g[k];
-                if ((lane & 3) == 0 && t8 != 0.f) atomicAdd(dst + which, t8);
-                if (lane == 1 && t9 != 0.f) atomicAdd(dst + 8, t9);
-            }
+            if (__any_sync(0xffffffffu, contrib)) warp_add_gradients(g, lane, g2 + 9 * (size_t)s_g[k]);
+        }
+        } else {
+        // Two vertically adjacent pixels per thread: the same arithmetic for both with packed
+        // f32x2 instructions (the forward's decisions exactly as the forward takes them: q' is
+        // the one-pixel rounding), branch-free over the pair -- a pixel that does not take the
+        // splat gets alpha = 0 (T, S unchanged: 1 - 0 = 1 and reciprocal 1) and a zero term.
+        // S is carried negated (nS = -S) so that c - S and the S update are pair adds and FMAs.
+        const float2 lx2 = make_float2(lx, lx), ly2 = make_float2(ly[0], ly[PPT - 1]);
+        const float2 one2 = make_float2(1.f, 1.f);
+        float2 T2 = make_float2(T[0], T[PPT - 1]);
+        float2 nR = make_float2(-S0[0], -S0[PPT - 1]), nG = make_float2(-S1[0], -S1[PPT - 1]),
+               nB = make_float2(-S2[0], -S2[PPT - 1]);
+        const float2 gR = make_float2(gC0[0], gC0[PPT - 1]), gG = make_float2(gC1[0], gC1[PPT - 1]),
+                     gB = make_float2(gC2[0], gC2[PPT - 1]), at2 = make_float2(aterm[0], aterm[PPT - 1]);
+        const float2 is2 = make_float2(inv_scale, inv_scale);
+        for (int i = nlist - 1; i >= 0; --i) {     // back to front
+            const int k = s_list[warp][i];
+            const int64_t pos = lo + k;   // sorted position of this splat
+            const float4 q0 = s_st[0][k], q1 = s_st[1][k], q2 = s_st[2][k], q3 = s_st[3][k];
+            const float2 dx = __fadd2_rn(lx2, make_float2(q0.x, q0.y));
+            const float2 dy = __fadd2_rn(ly2, make_float2(q0.z, q0.w));
+            const float2 f1x = make_float2(q1.x, q1.y), f2x = make_float2(q1.z, q1.w);
+            const float2 f1y = make_float2(q2.x, q2.y), f2y = make_float2(q2.z, q2.w);
+            const float2 p1 = __ffma2_rn(dy, f1y, __fmul2_rn(dx, f1x));
+            const float2 p2 = __ffma2_rn(dy, f2y, __fmul2_rn(dx, f2x));
+            const float2 qq = __ffma2_rn(p2, p2, __fmul2_rn(p1, p1));
+            const bool h0 = inside[0] && pos < (int64_t)last[0] && qq.x <= q3.x && (!DEPTH || q3.y <= dl[0]);
+            const bool h1 = inside[PPT - 1] && pos < (int64_t)last[PPT - 1] && qq.y <= q3.x &&
+                            (!DEPTH || q3.y <= dl[PPT - 1]);
+            if (!__any_sync(0xffffffffu, h0 || h1)) continue;
+            const float2 G = make_float2(gauss_of_qs(qq.x), gauss_of_qs(qq.y));
+            const float2 raw = __fmul2_rn(make_float2(q3.z, q3.w), G);
+            // -alpha (0 for a pixel that does not take the splat)
+            const float2 na = make_float2(h0 ? fmaxf(-alpha_max, -raw.x) : 0.f, h1 ? fmaxf(-alpha_max, -raw.y) : 0.f);
+            const float2 om = __fadd2_rn(one2, na);
+            float r0, r1;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(om.x));
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(om.y));
+            const float2 inv_om = make_float2(h0 ? r0 : 1.f, h1 ? r1 : 1.f);
+            T2 = __fmul2_rn(T2, inv_om);                  // T before this splat
+            const float2 nw = __fmul2_rn(na, T2);         // -alpha T
+            const float4 k0 = s_st[4][k], k1 = s_st[5][k];
+            const float2 cR = make_float2(k0.x, k0.y), cG = make_float2(k0.z, k0.w), cB = make_float2(k1.x, k1.y);
+            // sum over the colours of (c - S) dL/dC, then the pixel's dL/dalpha
+            const float2 e = __ffma2_rn(__fadd2_rn(cB, nB), gB,
+                                        __ffma2_rn(__fadd2_rn(cG, nG), gG, __fmul2_rn(__fadd2_rn(cR, nR), gR)));
+            const float2 ga = __ffma2_rn(at2, inv_om, __fmul2_rn(T2, e));
+            nR = __ffma2_rn(cR, na, __fmul2_rn(om, nR));   // -S <- om (-S) - c alpha
+            nG = __ffma2_rn(cG, na, __fmul2_rn(om, nG));
+            nB = __ffma2_rn(cB, na, __fmul2_rn(om, nB));
+            // clamp inactive and taking the splat: the conic, centre and opacity terms
+            const float2 gam = make_float2(h0 && raw.x <= alpha_max ? ga.x : 0.f,
+                                           h1 && raw.y <= alpha_max ? ga.y : 0.f);
+            const float2 gr = __fmul2_rn(gam, raw);      // -2 dL/dq
+            const float2 gu = __fmul2_rn(gr, is2);       // -2 inv_scale dL/dq
+            const float2 qx = __ffma2_rn(f1x, p1, __fmul2_rn(f2x, p2));
+            const float2 qy = __ffma2_rn(f1y, p1, __fmul2_rn(f2y, p2));
+            const float2 t0 = __fmul2_rn(gu, qx), t1 = __fmul2_rn(gu, qy);
+            const float2 gdx = __fmul2_rn(gr, dx), gdy = __fmul2_rn(gr, dy);
+            const float2 t2 = __fmul2_rn(gdx, dx), t3 = __fmul2_rn(gdx, dy), t4 = __fmul2_rn(gdy, dy);
+            const float2 t5 = __fmul2_rn(gam, G);
+            const float2 t6 = __fmul2_rn(gR, nw), t7 = __fmul2_rn(gG, nw), t8 = __fmul2_rn(gB, nw);
+            float g[9];
+            g[0] = t0.x + t0.y;
+            g[1] = t1.x + t1.y;
+            g[2] = -0.5f * (t2.x + t2.y);
+            g[3] = -(t3.x + t3.y);
+            g[4] = -0.5f * (t4.x + t4.y);
+            g[5] = t5.x + t5.y;
+            g[6] = -(t6.x + t6.y);
+            g[7] = -(t7.x + t7.y);
+            g[8] = -(t8.x + t8.y);
+            warp_add_gradients(g, lane, g2 + 9 * (size_t)s_g[k]);
+        }
+        T[0] = T2.x; T[PPT - 1] = T2.y;
+        S0[0] = -nR.x; S0[PPT - 1] = -nR.y;
+        S1[0] = -nG.x; S1[PPT - 1] = -nG.y;
+        S2[0] = -nB.x; S2[PPT - 1] = -nB.y;
         }
     }
 }
