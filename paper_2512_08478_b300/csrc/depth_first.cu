@@ -34,23 +34,44 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
     return v;
 }
 
+// Both kernels below take kBlocksPerCta blocks of kPrepThreads slots per CTA, each thread one
+// slot of every block, so that a thread has that many independent loads in flight (one per
+// block) instead of one; the per-block results are those of one CTA per block.
+constexpr int kBlocksPerCta = 4;
+
 __global__ void __launch_bounds__(kPrepThreads)
 compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ depth, int64_t n,
-                const uint32_t* __restrict__ boff, uint32_t* __restrict__ dkeys, uint32_t* __restrict__ dvals) {
+                int64_t nblocks, const uint32_t* __restrict__ boff, uint32_t* __restrict__ dkeys,
+                uint32_t* __restrict__ dvals) {
     pdl_entry();
-    __shared__ uint32_t ws[kPrepThreads / 32];
+    __shared__ uint32_t ws[kBlocksPerCta][kPrepThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    const bool f = i < n && touched[i] > 0;
-    const uint32_t bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) ws[warp] = __popc(bal);
+    const int64_t b0 = (int64_t)blockIdx.x * kBlocksPerCta;
+    bool f[kBlocksPerCta];
+    float z[kBlocksPerCta];
+#pragma unroll
+    for (int k = 0; k < kBlocksPerCta; ++k) {
+        const int64_t i = (b0 + k) * kPrepThreads + threadIdx.x;
+        f[k] = i < n && touched[i] > 0;
+        z[k] = i < n ? depth[i] : 0.f;
+    }
+    uint32_t bal[kBlocksPerCta];
+#pragma unroll
+    for (int k = 0; k < kBlocksPerCta; ++k) {
+        bal[k] = __ballot_sync(0xffffffffu, f[k]);
+        if (lane == 0) ws[k][warp] = __popc(bal[k]);
+    }
     __syncthreads();
-    uint32_t off = boff[blockIdx.x];
-    for (int w = 0; w < warp; ++w) off += ws[w];
-    if (f) {
-        const uint32_t o = off + __popc(bal & ((1u << lane) - 1u));
-        dkeys[o] = __float_as_uint(depth[i]);   // z > near > 0: bit order = numeric order
-        dvals[o] = (uint32_t)i;
+#pragma unroll
+    for (int k = 0; k < kBlocksPerCta; ++k) {
+        if (b0 + k >= nblocks) break;
+        uint32_t off = boff[b0 + k];
+        for (int w = 0; w < warp; ++w) off += ws[k][w];
+        if (f[k]) {
+            const uint32_t o = off + __popc(bal[k] & ((1u << lane) - 1u));
+            dkeys[o] = __float_as_uint(z[k]);   // z > near > 0: bit order = numeric order
+            dvals[o] = (uint32_t)((b0 + k) * kPrepThreads + threadIdx.x);
+        }
     }
 }
 
@@ -59,21 +80,31 @@ compact_visible(const uint32_t* __restrict__ touched, const float* __restrict__ 
 // nothing is read through them.
 __global__ void __launch_bounds__(kPrepThreads)
 depth_touch_sums(const uint32_t* __restrict__ dvals, const uint32_t* __restrict__ touched, int64_t n,
-                 const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ bsum) {
+                 int64_t nblocks, const Ctrl* __restrict__ ctrl, uint32_t* __restrict__ bsum) {
     pdl_entry();
-    __shared__ uint32_t ws[kPrepThreads / 32];
+    __shared__ uint32_t ws[kBlocksPerCta][kPrepThreads / 32];
     const int64_t nv = ctrl->error ? 0 : min((int64_t)ctrl->num_visible, n);
-    const int64_t j = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x;
-    const uint32_t g = (j < nv) ? dvals[j] : 0xffffffffu;
-    uint32_t c = (g < (uint64_t)n) ? touched[g] : 0u;
+    const int64_t b0 = (int64_t)blockIdx.x * kBlocksPerCta;
+    uint32_t g[kBlocksPerCta], c[kBlocksPerCta];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    for (int k = 0; k < kBlocksPerCta; ++k) {
+        const int64_t j = (b0 + k) * kPrepThreads + threadIdx.x;
+        g[k] = (j < nv) ? dvals[j] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int k = 0; k < kBlocksPerCta; ++k) c[k] = (g[k] < (uint64_t)n) ? touched[g[k]] : 0u;
+#pragma unroll
+    for (int k = 0; k < kBlocksPerCta; ++k) {
+        uint32_t v = c[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) ws[k][threadIdx.x >> 5] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < kBlocksPerCta && b0 + threadIdx.x < nblocks) {
         uint32_t t = 0;
-        for (int w = 0; w < kPrepThreads / 32; ++w) t += ws[w];
-        bsum[blockIdx.x] = t;
+        for (int w = 0; w < kPrepThreads / 32; ++w) t += ws[threadIdx.x][w];
+        bsum[b0 + threadIdx.x] = t;
     }
 }
 
@@ -190,8 +221,9 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     const bool odd = (L.depth_passes & 1) != 0;
     uint32_t* ck = odd ? dk1 : dk0;
     uint32_t* cv = odd ? dv1 : dv0;
-    launch_k(true, compact_visible, blocks_n, kPrepThreads, 0, stream, touched,
-             reinterpret_cast<const float*>(ws + L.off_depth), L.n, (const uint32_t*)bvis_off, ck, cv);
+    launch_k(true, compact_visible, (blocks_n + kBlocksPerCta - 1) / kBlocksPerCta, kPrepThreads, 0, stream,
+             touched, reinterpret_cast<const float*>(ws + L.off_depth), L.n, (int64_t)blocks_n,
+             (const uint32_t*)bvis_off, ck, cv);
     // 2. sort by depth; the result lands in buffer 0
     launch_sort_generic<uint32_t>(ck, cv, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, L.depth_passes, hist, lb,
                                   ctrl->part_counter, &ctrl->error, stream, nullptr, 0,
@@ -257,8 +289,8 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     // 3. tile copies in depth order
     uint32_t* bsum2 = reinterpret_cast<uint32_t*>(ws + L.off_bsum2);
     uint32_t* boff2 = reinterpret_cast<uint32_t*>(ws + L.off_boff2);
-    launch_k(true, depth_touch_sums, blocks_n, kPrepThreads, 0, stream, (const uint32_t*)dv0, touched, L.n,
-             (const Ctrl*)ctrl, bsum2);
+    launch_k(true, depth_touch_sums, (blocks_n + kBlocksPerCta - 1) / kBlocksPerCta, kPrepThreads, 0, stream,
+             (const uint32_t*)dv0, touched, L.n, (int64_t)blocks_n, (const Ctrl*)ctrl, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap,
                      reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
     if (L.tile_fused) {

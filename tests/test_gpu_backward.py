@@ -111,19 +111,27 @@ def _flagged_gaussians(prep, amb, tile=16, q_max=9.0):
     return flagged
 
 
-@pytest.mark.slow
-def test_500k_sh3_800px_l2_loss_gradients():
-    """The fwd+bwd workload at full size: group norms on every Gaussian, and the per-element
-    bar on every Gaussian that the oracle does not evaluate at an ambiguous pixel."""
+@pytest.fixture(scope="module")
+def fwdbwd_reference():
     sc, target, cams = synth.workload_fwdbwd()
     cam = cams[0]
     tgt_rgb, _, _, _ = render_gpu(target, cam)
     rgb, _, _, _ = render_gpu(sc, cam)
     gC = 2.0 * (rgb - tgt_rgb) / rgb.size
     gA = np.zeros((cam.H, cam.W))
-    g = _gpu_grads(sc, cam, gC, gA)
     ref = oracle.adjoint(sc, cam, gC, gA)
     img, prep = oracle.render(sc, cam)
+    return sc, cam, gC, gA, ref, img, prep
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ppt", [1, 2])
+def test_500k_sh3_800px_l2_loss_gradients(fwdbwd_reference, ppt):
+    """The fwd+bwd workload at full size, with one and two pixels per compositor thread: group
+    norms on every Gaussian, and the per-element bar on every Gaussian that the oracle does not
+    evaluate at an ambiguous pixel."""
+    sc, cam, gC, gA, ref, img, prep = fwdbwd_reference
+    g = _gpu_grads(sc, cam, gC, gA, (0.0, 0.0, 0.0), vis.make_opts(pixels_per_thread=ppt))
     flagged = _flagged_gaussians(prep, img["ambiguous"] != 0)
     keep = ~flagged
     print(f"flagged Gaussians: {int(flagged.sum())} of {flagged.size}")
