@@ -813,7 +813,9 @@ def run_reference(args):
                 higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(desc), cpu_baseline=dict(value=round(value, 1), unit="ms/frame", cores=cores,
                                                      kind="oracle", sample=sample),
-                e2e=dict(value=round(value, 1), unit="ms/frame", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+                e2e=dict(value=round(value, 1), unit="ms/frame", h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                ms_per_step_note="wall time of a sampled step; value scales the sampled tiles' time to the whole "
+                                 "frame")
     print(json.dumps(line), flush=True)
 
 
