@@ -1,9 +1,10 @@
 """Batched render (vis_render_batch). The fused pipeline (lanes = 0: one preprocess over
-the work list of (asset, camera) items, one depth sort of every image's survivors, one
-stable sort by (image, tile), one compositor over all tiles of all images) and the lane
-baseline (lanes >= 1: per-image renders on concurrent streams) must both give every image
-bit-identical to vis_render of the same (asset, camera, options), and so inherit its
-oracle parity; the fused images are also checked against the oracle directly."""
+the work list of (asset, camera) items; per group of images stacked on one tile canvas, one
+depth sort of the group's survivors, one stable sort by canvas tile -- i.e. by (image, tile)
+--, one compositor over the canvas) and the lane baseline (lanes >= 1: per-image renders on
+concurrent streams) must both give every image bit-identical to vis_render of the same
+(asset, camera, options), and so inherit its oracle parity; the fused images are also
+checked against the oracle directly."""
 import numpy as np
 import pytest
 
@@ -94,3 +95,19 @@ def test_batch_capacity_error_is_reported_then_grown(lanes):
     assert b.key_capacity > 32
     b.check()
     _equal_plain(b, scenes_np, cams, cam_scene, bg=(0.0, 0.0, 0.0))
+
+
+def test_fused_batch_groups_and_oversized_image():
+    """Many images fill several canvases (groups, on several streams), and an image of more
+    tiles than a canvas holds (2048 x 1632 at 8-pixel tiles: 52224 tiles) is a group of its own
+    with 32-bit tile ids: every image equals its plain render."""
+    scenes_np, cams, cam_scene = _small_batch(assets=3, cams_per_asset=8, scale=0.01, seed=11)
+    big = synth.look_at((0.0, 1.0, 6.0), (0, 0, 0), 2048, 1632, 55.0)
+    cams = list(cams) + [big]
+    cam_scene = list(cam_scene) + [1]
+    scenes = [vis.Scene.from_numpy(s) for s in scenes_np]
+    o = vis.make_opts(tile=8)
+    b = vis.Batch(scenes, cams, cam_scene, lanes=0, opts=o)
+    b.render(bg=(0.1, 0.2, 0.3))
+    _equal_plain(b, scenes_np, cams, cam_scene, opts=o)
+
