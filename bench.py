@@ -384,11 +384,11 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     dom_ms = {c: (hbm_stages[c]["ms"] if c in hbm_stages else stage_ms[c]) for c in cands}
     dom = max(cands, key=lambda c: dom_ms[c])
     if dom == "composite":
-        # the compositor is bound by FP32 issue (SURVEY: ~15 FP32 instructions per (pixel,
-        # splat) test, one ex2 per composited pair): count its tests on the first view (one
-        # extra render with statistics, outside the timed region)
-        # tests counted by the one-pixel compositor (8 x 4 warp blocks) whichever block shape is
-        # timed, so that the algorithmic count does not depend on the implementation's choice
+        # the compositor is bound by FP32 issue (~15 FP32 instructions per (pixel, splat) test,
+        # one ex2 per composited pair): count its tests on the first view (one extra render with
+        # statistics, outside the timed region), as the one-pixel compositor (8 x 4 warp blocks)
+        # counts them whichever block shape is timed, so that the algorithmic count does not
+        # depend on the implementation's choice
         st_opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=1,
                                 digit_bits=args.digit_bits, collect_stats=1)
         vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
