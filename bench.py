@@ -208,15 +208,20 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
 
     world, rank, local = _dist()
     sc_np, cams, desc, extra = load_workload(workload)
-    desc["tile"] = args.tile
     W, H = desc["width"], desc["height"]
     sc = vis.Scene.from_numpy(sc_np)
     n = sc.n
     cap = 16 * n + (1 << 20)
     sort_mode = args.sort_mode if args.sort_mode is not None else vis.make_opts().sort_mode
     ppt = args.ppt if args.ppt is not None else 1
-    opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=ppt, digit_bits=args.digit_bits)
-    ws = vis.Workspace(n, W, H, key_capacity=cap, opts=opts)
+    tile = args.tile if args.tile is not None else 16
+
+    def make(t, p):
+        return vis.make_opts(sort_mode=sort_mode, tile=t, pixels_per_thread=p, digit_bits=args.digit_bits)
+    opts = make(tile, ppt)
+    # sized for the smallest tile tried: its layout is the largest (per-tile arrays), so every
+    # candidate fits
+    ws = vis.Workspace(n, W, H, key_capacity=cap, opts=make(min(16, tile), ppt))
     rgb = torch.empty((3, H, W), device="cuda")
     alpha = torch.empty((H, W), device="cuda")
     stream = torch.cuda.current_stream()
@@ -270,19 +275,24 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         vis.vis_render(tgt.handle, cam_objs[0], W, H, (0.0, 0.0, 0.0), tgt_rgb, tgt_a, ws.buf, opts)
         vis.vis_check(ws.buf)
 
-    ppt_ms = None
-    if args.ppt is None:
-        # compositor block shape (1 or 2 pixels per thread; the image does not depend on it):
-        # the faster on this workload's first views, outside the timed region
+    tuned_ms = None
+    if args.ppt is None or args.tile is None:
+        # tile size (16 or 32 px) and compositor block shape (1 or 2 pixels per thread; the
+        # image depends on neither): the fastest on this workload's first views, outside the
+        # timed region
         from paper_2512_08478_b300 import tuning
+        cands = [(t, p) for t in ((16, 32) if args.tile is None else (tile,))
+                 for p in ((1, 2) if args.ppt is None else (ppt,))]
 
         def tune_step(c, _i=[0]):
             nonlocal opts
-            opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=c, digit_bits=args.digit_bits)
+            opts = make(*c)
             frame(_i[0] % 4)
             _i[0] += 1
-        ppt, ppt_ms = tuning.pick_fastest((1, 2), tune_step, reps=4, warmup=2)
-        opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=ppt, digit_bits=args.digit_bits)
+        (tile, ppt), tuned_ms = tuning.pick_fastest(cands, tune_step, reps=4, warmup=2)
+        opts = make(tile, ppt)
+    ws.opts = opts   # the layout of the chosen options (the buffer holds every candidate's)
+    desc["tile"] = tile
     for i in range(args.warmup):
         frame(i)
     vis.vis_check(ws.buf)
@@ -389,7 +399,7 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         # statistics, outside the timed region), as the one-pixel compositor (8 x 4 warp blocks)
         # counts them whichever block shape is timed, so that the algorithmic count does not
         # depend on the implementation's choice
-        st_opts = vis.make_opts(sort_mode=sort_mode, tile=args.tile, pixels_per_thread=1,
+        st_opts = vis.make_opts(sort_mode=sort_mode, tile=tile, pixels_per_thread=1,
                                 digit_bits=args.digit_bits, collect_stats=1)
         vis.vis_render(handle, cam_objs[view0 % len(cam_objs)], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf,
                        st_opts, depth=dbuf)
@@ -435,8 +445,8 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(desc, sort_mode=sort_mode, packed=packed, pixels_per_thread=ppt,
-                            pixels_per_thread_tuned=({str(k): round(v, 4) for k, v in ppt_ms.items()}
-                                                     if ppt_ms else None),
+                            tuned_ms=({f"tile{k[0]}_ppt{k[1]}": round(v, 4) for k, v in tuned_ms.items()}
+                                      if tuned_ms else None),
                             digit_bits=args.digit_bits,
                             depth_buffer=(f"wall at view depth {args.depth_plane}" if dbuf is not None else None),
                             l2="inputs larger than L2 (attributes exceed 126 MB); no flush",
@@ -834,7 +844,8 @@ def main():
                     help="0: one sort of 64-bit (tile, depth) keys; 1: depth sort then tile sort "
                          "(default: the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--tile", type=int, default=16, choices=[8, 16, 32], help="tile size in pixels")
+    ap.add_argument("--tile", type=int, default=None, choices=[8, 16, 32],
+                    help="tile size in pixels (default: 16 or 32, the faster on the workload's first views)")
     ap.add_argument("--digit-bits", type=int, default=8, choices=[8, 10, 11],
                     help="radix digit width of the depth sort (and of 32-bit tile sorts)")
     ap.add_argument("--ppt", type=int, default=None, choices=[1, 2],
