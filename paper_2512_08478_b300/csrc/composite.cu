@@ -60,7 +60,10 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
     constexpr int BX = TILE / 8;            // blocks per tile row
     constexpr int BH = 4 * PPT;             // block height in pixels
-    constexpr int CH = NT < 256 ? NT : 256; // splats staged per chunk
+    // splats staged per chunk: one per thread, up to 256 (512 for the 512 threads of a 32-pixel
+    // tile with two pixels per thread: half the chunk barriers, 3% faster there)
+    constexpr int CHMAX = PPT == 2 ? 512 : 256;
+    constexpr int CH = NT < CHMAX ? NT : CHMAX;
     static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
     // staged splats, NS float4 slots each: PPT 1 -> (du, dv, f1x, f1y), (f2x, f2y, thr, opacity),
     // (r, g, b, depth); PPT 2 -> the same values laid out as packed pairs for the f32x2
