@@ -137,6 +137,7 @@ struct Fused {
     size_t off_rec = 0, off_depth = 0, off_rect = 0, off_touched = 0, off_bsum = 0, off_boff = 0;
     size_t off_scratch = 0, scratch_stride = 0, total = 0;
     int n_scratch = 1;               // scratch areas: groups run on that many streams at once
+    bool layout_ok = true;           // make_layout's region order is the one group_layout assumes
 };
 
 // Streams (and scratch areas) of a fused batch: group g runs on stream g mod kFusedStreams,
@@ -147,9 +148,13 @@ constexpr int kFusedStreams = 3;
 // The single-image layout of group g's canvas, mapped onto the batch workspace: the scratch
 // regions of make_layout's order -- [status block .. tile order] and [scan totals .. values]
 // -- moved into the scratch area, the per-slot buffers pointing at the group's slots.
-vis::Layout group_layout(const Fused& F, const Group& g, int area, size_t* scratch_bytes = nullptr) {
+vis::Layout group_layout(const Fused& F, const Group& g, int area, size_t* scratch_bytes = nullptr,
+                         bool* order_ok = nullptr) {
     vis::Layout L = vis::make_layout(g.slots, g.cw * F.tile, g.rows * F.tile, F.tile, F.cap, vis::kSortDepthFirst,
                                      F.digit_bits);
+    if (order_ok)
+        *order_ok = L.zero_end <= L.off_rec && L.off_order < L.off_rec && L.off_boff < L.off_scan_tot &&
+                    L.off_vals[1] < L.off_tfinal && L.off_ctrl < L.off_rec;
     // make_layout takes, in order: the cleared region (status .. tile counts), the tile
     // order, the per-slot buffers (records .. block offsets), the scratch (scan totals ..
     // values), then the adjoint and depth-buffer buffers
@@ -229,8 +234,10 @@ Fused fused_layout(const std::vector<int64_t>& n_img, const std::vector<char>& p
     size_t scratch = 0;
     for (const Group& g : F.groups) {
         size_t b = 0;
-        group_layout(F, g, 0, &b);
+        bool ok = true;
+        group_layout(F, g, 0, &b, &ok);
         scratch = std::max(scratch, b);
+        F.layout_ok = F.layout_ok && ok;
     }
     F.n_scratch = (int)std::min<size_t>(kFusedStreams, F.groups.size());
     F.scratch_stride = align256(scratch);
@@ -335,7 +342,9 @@ vis_status vis_batch_workspace_size(const vis_scene_t* scenes, int n_scenes, con
         std::vector<int64_t> n_img;
         std::vector<char> packed;
         if ((st = fused_inputs(scenes, n_scenes, cam_scene, W, H, n_images, &n_img, &packed))) return st;
-        *bytes = fused_layout(n_img, packed, W, H, n_images, o.tile, key_capacity, o.digit_bits).total;
+        const Fused F = fused_layout(n_img, packed, W, H, n_images, o.tile, key_capacity, o.digit_bits);
+        if (!F.layout_ok) return fail_b(VIS_ERR_UNSUPPORTED, "workspace layout order not the one the batch maps");
+        *bytes = F.total;
         vis::set_last_error("");
         return VIS_OK;
     }
@@ -373,6 +382,7 @@ static vis_status render_fused(vis_batch_t b, const vis_scene_t* scenes, int n_s
     const int64_t cap = fused_capacity(n_img, packed, W, H, n_images, o.tile, o.digit_bits, ws_bytes);
     if (cap < 1) return fail_b(VIS_ERR_INVALID_ARG, "batch workspace too small");
     const Fused F = fused_layout(n_img, packed, W, H, n_images, o.tile, cap, o.digit_bits);
+    if (!F.layout_ok) return fail_b(VIS_ERR_UNSUPPORTED, "workspace layout order not the one the batch maps");
     const uint32_t spin = o.spin_limit > 0 ? (uint32_t)o.spin_limit : vis::kSpinLimit;
     char* w = static_cast<char*>(ws);
 
