@@ -224,11 +224,12 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     launch_k(true, compact_visible, (blocks_n + kBlocksPerCta - 1) / kBlocksPerCta, kPrepThreads, 0, stream,
              touched, reinterpret_cast<const float*>(ws + L.off_depth), L.n, (int64_t)blocks_n,
              (const uint32_t*)bvis_off, ck, cv);
-    // 2. sort by depth; the result lands in buffer 0
+    // 2. sort by depth; the sorted indices land in buffer 0 (the sorted depths are not needed:
+    //    the last pass writes only the indices)
     launch_sort_generic<uint32_t>(ck, cv, dk0, dv0, dk1, dv1, L.n, &ctrl->num_visible, L.depth_passes, hist, lb,
                                   ctrl->part_counter, &ctrl->error, stream, nullptr, 0,
                                   32 - L.digit_bits * (L.depth_passes - 1), depth_sort_kpt(L.n, L.digit_bits),
-                                  L.spin_limit, L.digit_bits);
+                                  L.spin_limit, L.digit_bits, false);
 }
 
 SideStream* side_stream(cudaStream_t stream) {

@@ -305,7 +305,8 @@ template <typename K, int KPT, int DBITS>
 static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                               uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                               uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
-                              StageMark mark, int mark_index, int last_bits, uint32_t spin_limit) {
+                              StageMark mark, int mark_index, int last_bits, uint32_t spin_limit,
+                              bool last_keys) {
     constexpr int D = 1 << DBITS;
     static std::atomic<uint64_t> attr_dev{0};   // devices whose attributes are set
     static std::mutex attr_mu;
@@ -328,7 +329,7 @@ static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys
     const uint32_t* src_v = vals_in;
     for (int p = 0; p < passes; ++p) {
         const bool to_a = ((passes - 1 - p) % 2) == 0;
-        K* dk = to_a ? keys_a : keys_b;
+        K* dk = (p == passes - 1 && !last_keys) ? nullptr : (to_a ? keys_a : keys_b);
         uint32_t* dv = to_a ? vals_a : vals_b;
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < DBITS) ? last_bits : DBITS;
         launch_k(true, sort_pass<K, KPT, DBITS>, grid, kSortThreads, smem, stream, src_k, src_v, dk, dv,
@@ -346,13 +347,13 @@ void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, u
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark, int mark_index, int last_bits, int kpt, uint32_t spin_limit,
-                         int digit_bits) {
+                         int digit_bits, bool last_keys) {
     if (cap <= 0 || passes <= 0) return;
     constexpr bool k32 = std::is_same<K, uint32_t>::value;
 #define VIS_SORT_IMPL(KPT_, DB_)                                                                                   \
     sort_generic_impl<K, KPT_, DB_>(keys_in, vals_in, keys_a, vals_a, keys_b, vals_b, cap, num_keys_dev, passes, \
                                     hist, lookback, part_counters, error, stream, mark, mark_index, last_bits,     \
-                                    spin_limit)
+                                    spin_limit, last_keys)
     if constexpr (k32) {
         if (digit_bits == 11) VIS_SORT_IMPL(16, 11);
         else if (digit_bits == 10) VIS_SORT_IMPL(16, 10);
@@ -393,11 +394,11 @@ template void launch_sort_pass<uint16_t>(const uint16_t*, const uint32_t*, uint1
 template void launch_sort_generic<uint64_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*, uint64_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
                                             uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t,
-                                            int);
+                                            int, bool);
 template void launch_sort_generic<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                             uint32_t*, int64_t, const uint32_t*, int, uint32_t*, uint32_t*,
                                             uint32_t*, uint32_t*, cudaStream_t, StageMark, int, int, int, uint32_t,
-                                            int);
+                                            int, bool);
 
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark, int mark_index) {
     uint64_t* k0 = reinterpret_cast<uint64_t*>(ws + L.off_keys[0]);

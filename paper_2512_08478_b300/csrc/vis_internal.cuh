@@ -344,13 +344,14 @@ void launch_preprocess_backward(const PrepParams& p, const Layout& L, const char
 // words (parts = sort_parts_for(cap, kpt, digit_bits)), `hist` passes * 2^digit_bits words
 // and `part_counters` passes words, all zeroed; the key count is read from num_keys_dev
 // (<= cap). If `mark` is given it is called after the histogram. last_bits: significant
-// bits of the last pass's digit (key bits - digit_bits (passes - 1)).
+// bits of the last pass's digit (key bits - digit_bits (passes - 1)). With last_keys false the
+// last pass writes only the values (keys_a then holds the previous pass's keys).
 template <typename K>
 void launch_sort_generic(const K* keys_in, const uint32_t* vals_in, K* keys_a, uint32_t* vals_a, K* keys_b,
                          uint32_t* vals_b, int64_t cap, const uint32_t* num_keys_dev, int passes, uint32_t* hist,
                          uint32_t* lookback, uint32_t* part_counters, uint32_t* error, cudaStream_t stream,
                          StageMark mark = nullptr, int mark_index = 0, int last_bits = kRadixBits, int kpt = 0,
-                         uint32_t spin_limit = kSpinLimit, int digit_bits = kRadixBits);
+                         uint32_t spin_limit = kSpinLimit, int digit_bits = kRadixBits, bool last_keys = true);
 
 // One sort_pass over the keys (digit (key >> shift) & 255 with nbits significant bits,
 // histogram hist_pass); keys_out may be null. `lookback` holds sort_parts<K>(cap) * kRadix
