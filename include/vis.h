@@ -423,7 +423,7 @@ VIS_API vis_status vis_dynamic_update(const float* means0, const float* velocity
  * nothing either). The same error of vis_sort_pairs is read with vis_check(ws, ...),
  * its workspace starting with the same status block. */
 #define VIS_SORT_NOALLOC_MAX_KEYS (1 << 20)
-#define VIS_SORT_NOALLOC_SCRATCH_BYTES 16785664
+#define VIS_SORT_NOALLOC_SCRATCH_BYTES 17047808
 VIS_API vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
                                           uint64_t* keys_out, uint32_t* vals_out, int64_t m,
                                           int key_bits, void* stream);

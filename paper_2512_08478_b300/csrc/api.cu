@@ -333,9 +333,13 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
     L.off_hist = take(sizeof(uint32_t) * kMaxPasses * ((size_t)1 << L.digit_bits));
     L.off_hist_tile = take(sizeof(uint32_t) * kMaxPasses * ((size_t)1 << tile_digit));
     L.lookback_words_depth =
-        df ? (size_t)L.depth_passes * depth_sort_parts(n, L.digit_bits) * ((size_t)1 << L.digit_bits) : 0;
-    L.off_lookback = take(sizeof(uint32_t) *
-                          (L.lookback_words_depth + (size_t)L.passes * L.sort_parts * ((size_t)1 << tile_digit)));
+        df ? (size_t)L.depth_passes * lookback_rows(depth_sort_parts(n, L.digit_bits), lookback_group(4, L.digit_bits)) *
+                 ((size_t)1 << L.digit_bits)
+           : 0;
+    const int tile_group = lookback_group(L.tile_fused ? 2 : L.key_bytes, tile_digit);
+    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes *
+                                                                           lookback_rows(L.sort_parts, tile_group) *
+                                                                           ((size_t)1 << tile_digit)));
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
     L.zero_end = off;
@@ -800,7 +804,10 @@ static size_t sort_ws_layout(int64_t m, int passes, size_t* off_hist, size_t* of
     *parts = vis::sort_parts<uint64_t>(m);
     size_t off = align_up(sizeof(vis::Ctrl), 256);
     *off_hist = off; off = align_up(off + sizeof(uint32_t) * vis::kMaxPasses * vis::kRadix, 256);
-    *off_lb = off; off = align_up(off + sizeof(uint32_t) * (size_t)passes * (*parts) * vis::kRadix, 256);
+    *off_lb = off;
+    off = align_up(off + sizeof(uint32_t) * (size_t)passes * vis::lookback_rows(*parts, vis::lookback_group(8, 8)) *
+                             vis::kRadix,
+                   256);
     const size_t zero_end = off;
     *off_k = off; off = align_up(off + sizeof(uint64_t) * (size_t)m, 256);
     *off_v = off; off = align_up(off + sizeof(uint32_t) * (size_t)m, 256);

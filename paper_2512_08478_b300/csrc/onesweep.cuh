@@ -17,6 +17,13 @@ namespace vis {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
+// Group words (one row of D per group of WIN consecutive partitions, after the partitions'
+// rows): every partition of the group adds its digit count plus one arrival, in one atomic,
+// so a word whose arrivals reach WIN holds the group's complete count (at most WIN x 4096).
+constexpr int kGroupArriveShift = 26;
+constexpr uint32_t kGroupArrive = 1u << kGroupArriveShift;
+constexpr uint32_t kGroupCountMask = kGroupArrive - 1;
+constexpr int kGroupRound = 4;   // group words read per round of the look-back's group walk
 
 static_assert(kSortThreads == 256, "the scan phase assumes 8 warps");
 
@@ -86,20 +93,31 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Decoupled look-back over the words lookback[q * D + d] of the partitions q preceding
-// `part`, split in two so that its loads overlap the reordering: lookback_issue reads the
-// window of WIN predecessors for digit d; lookback_resolve consumes it in order up to the
-// first inclusive prefix, polling a word not yet published at most `limit` times,
-// continues past the window a window at a time if needed, publishes this
-// partition's inclusive prefix and returns the count of d over all preceding partitions
-// (*timed_out set if a poll gave up; the prefix is then wrong, but still published, so
-// that no successor waits on this partition).
+// `part`, in two levels. The partitions form groups of WIN (group g: partitions g WIN ..
+// g WIN + WIN - 1); besides its own word every partition adds its count to its group's word
+// groups[g * D + d] (group_add). lookback_issue reads this partition's predecessors within
+// its own group (at most WIN - 1) while the reordering runs; lookback_resolve consumes them in
+// order up to the first inclusive prefix, then walks whole groups back, kGroupRound groups per
+// round with their loads in flight together: a group counts by its last partition's inclusive
+// prefix if published (and the walk stops there), else by its complete group count. A word
+// not yet published is polled at most `limit` times. The walk covers WIN partitions per
+// group word, so a partition far from the last published inclusive prefix (all partitions
+// of a single wave start together) waits a few rounds, not one per WIN partitions. It then
+// publishes this partition's inclusive prefix and returns the count of d over all preceding
+// partitions (*timed_out set if a poll gave up; the prefix is then wrong, but still
+// published, so that no successor waits on this partition).
 template <int WIN, int D>
 __device__ __forceinline__ void lookback_issue(const uint32_t* lookback, uint32_t part, uint32_t d,
                                                uint32_t (&v)[WIN]) {
-    const int64_t q0 = (int64_t)part - 1;
+    const int64_t q0 = (int64_t)part - 1, gstart = (int64_t)(part / WIN) * WIN;
 #pragma unroll
     for (int i = 0; i < WIN; ++i)
-        v[i] = (q0 - i >= 0) ? ld_relaxed(&lookback[(size_t)(q0 - i) * D + d]) : kFlagInc;
+        v[i] = (q0 - i >= gstart) ? ld_relaxed(&lookback[(size_t)(q0 - i) * D + d]) : kFlagInc;
+}
+
+template <int WIN, int D>
+__device__ __forceinline__ void group_add(uint32_t* groups, uint32_t part, uint32_t d, uint32_t cnt) {
+    atomicAdd(&groups[(size_t)(part / WIN) * D + d], cnt + kGroupArrive);
 }
 
 __device__ __forceinline__ bool lookback_wait(const uint32_t* word, uint32_t* w, uint32_t limit) {
@@ -112,34 +130,63 @@ __device__ __forceinline__ bool lookback_wait(const uint32_t* word, uint32_t* w,
     return true;
 }
 
+// Wait until group g's last partition has published its inclusive prefix (*lw) or all WIN
+// partitions of the group have added their counts (*gw); false if `limit` polls pass.
+template <int WIN>
+__device__ __forceinline__ bool group_wait(const uint32_t* last_word, const uint32_t* group_word, uint32_t* lw,
+                                           uint32_t* gw, uint32_t limit) {
+    uint32_t spins = 0;
+    while ((*lw & ~kCountMask) != kFlagInc && (*gw >> kGroupArriveShift) != (uint32_t)WIN) {
+        if (++spins > limit) return false;
+        if (spins > 8) __nanosleep(32);
+        *lw = ld_relaxed(last_word);
+        *gw = ld_relaxed(group_word);
+    }
+    return true;
+}
+
 template <int WIN, int D>
-__device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, uint32_t part, uint32_t d, uint32_t cnt,
-                                                     const uint32_t (&v)[WIN], uint32_t limit, bool* timed_out) {
+__device__ __forceinline__ uint32_t lookback_resolve(uint32_t* lookback, const uint32_t* groups, uint32_t part,
+                                                     uint32_t d, uint32_t cnt, const uint32_t (&v)[WIN],
+                                                     uint32_t limit, bool* timed_out) {
     *timed_out = false;
     if (part == 0) return 0;
     uint32_t prefix = 0;
     bool found = false, to = false;
-    const int64_t q0 = (int64_t)part - 1;
+    const int64_t q0 = (int64_t)part - 1, gstart = (int64_t)(part / WIN) * WIN;
+    // this partition's predecessors in its own group
 #pragma unroll
     for (int i = 0; i < WIN; ++i) {
-        if (found || to || q0 - i < 0) break;
+        if (found || to || q0 - i < gstart) break;
         uint32_t w = v[i];
         if (!lookback_wait(&lookback[(size_t)(q0 - i) * D + d], &w, limit)) { to = true; break; }
         prefix += w & kCountMask;
         if ((w & ~kCountMask) == kFlagInc) found = true;
     }
-    // beyond the first window: the next WIN predecessors at a time, their loads in flight together
-    for (int64_t qb = q0 - WIN; !found && !to && qb >= 0; qb -= WIN) {
-        uint32_t u[WIN];
+    // the whole groups before it, kGroupRound groups per round
+    for (int64_t gb = (int64_t)(part / WIN) - 1; !found && !to && gb >= 0; gb -= kGroupRound) {
+        uint32_t lw[kGroupRound], gw[kGroupRound];
 #pragma unroll
-        for (int i = 0; i < WIN; ++i) u[i] = (qb - i >= 0) ? ld_relaxed(&lookback[(size_t)(qb - i) * D + d]) : 0u;
+        for (int i = 0; i < kGroupRound; ++i) {
+            const bool ok = gb - i >= 0;
+            lw[i] = ok ? ld_relaxed(&lookback[(size_t)((gb - i) * WIN + WIN - 1) * D + d]) : 0u;
+            gw[i] = ok ? ld_relaxed(&groups[(size_t)(gb - i) * D + d]) : 0u;
+        }
 #pragma unroll
-        for (int i = 0; i < WIN; ++i) {
-            if (found || to || qb - i < 0) break;
-            uint32_t w = u[i];
-            if (!lookback_wait(&lookback[(size_t)(qb - i) * D + d], &w, limit)) { to = true; break; }
-            prefix += w & kCountMask;
-            if ((w & ~kCountMask) == kFlagInc) found = true;
+        for (int i = 0; i < kGroupRound; ++i) {
+            if (found || to || gb - i < 0) break;
+            const int64_t g = gb - i;
+            if (!group_wait<WIN>(&lookback[(size_t)(g * WIN + WIN - 1) * D + d], &groups[(size_t)g * D + d], &lw[i],
+                                 &gw[i], limit)) {
+                to = true;
+                break;
+            }
+            if ((lw[i] & ~kCountMask) == kFlagInc) {
+                prefix += lw[i] & kCountMask;
+                found = true;
+            } else {
+                prefix += gw[i] & kGroupCountMask;
+            }
         }
     }
     st_relaxed(&lookback[(size_t)part * D + d], kFlagInc | ((prefix + cnt) & kCountMask));

@@ -100,8 +100,12 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     using Cfg = RadixCfg<DBITS>;
     using Counter = typename Cfg::Counter;
     constexpr int D = Cfg::D, DPT = Cfg::DPT, WIN = SortWin<K, DBITS>::value;
+    static_assert(WIN == lookback_group((int)sizeof(K), DBITS), "look-back groups are one window wide");
     pdl_entry();
     constexpr int PART = kSortThreads * KPT;
+    // the pass's look-back region: a row of D words per partition of the capacity, then a row
+    // per group of WIN partitions
+    uint32_t* groups = lookback + (size_t)((cap + PART - 1) / PART) * D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem<K, KPT, DBITS>& S = *reinterpret_cast<SortSmem<K, KPT, DBITS>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -158,6 +162,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
 #pragma unroll
             for (int w = 0; w < kSortThreads / 32; ++w) c += S.whist[w][d];
             st_relaxed(&lookback[(size_t)p * D + d], (p == 0 ? kFlagInc : kFlagAgg) | c);
+            group_add<WIN, D>(groups, p, d, c);
         }
     };
     Counter* wh = S.whist[warp];
@@ -248,7 +253,7 @@ sort_pass(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     for (int j = 0; j < DPT; ++j) {
         bool to = false;
         const uint32_t prefix =
-            h[j] != 0 ? lookback_resolve<WIN, D>(lookback, part, d0 + j, cnt[j], lbw[j], spin_limit, &to) : 0u;
+            h[j] != 0 ? lookback_resolve<WIN, D>(lookback, groups, part, d0 + j, cnt[j], lbw[j], spin_limit, &to) : 0u;
         timed_out = timed_out || to;
         S.digit_off[d0 + j] = gsd[j] + prefix - lsd[j];
     }
@@ -334,7 +339,8 @@ static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys
         const int nbits = (p == passes - 1 && last_bits > 0 && last_bits < DBITS) ? last_bits : DBITS;
         launch_k(true, sort_pass<K, KPT, DBITS>, grid, kSortThreads, smem, stream, src_k, src_v, dk, dv,
                  (const uint32_t*)num_keys_dev, cap, DBITS * p, nbits, (const uint32_t*)(hist + (size_t)p * D),
-                 lookback + (size_t)p * parts * D, &part_counters[p], error, spin_limit);
+                 lookback + (size_t)p * lookback_rows(parts, SortWin<K, DBITS>::value) * D, &part_counters[p], error,
+                 spin_limit);
         src_k = dk;
         src_v = dv;
     }

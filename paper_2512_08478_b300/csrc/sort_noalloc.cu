@@ -30,7 +30,8 @@ constexpr int64_t kMaxParts = vis::sort_parts<uint64_t>(kMaxKeys);
 constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffHist = 256;
 constexpr size_t kOffLookback = kOffHist + sizeof(uint32_t) * vis::kMaxPasses * vis::kRadix;
-constexpr size_t kLookbackBytes = sizeof(uint32_t) * vis::kMaxPasses * kMaxParts * vis::kRadix;
+constexpr int64_t kMaxRows = kMaxParts + (kMaxParts + vis::lookback_group(8, 8) - 1) / vis::lookback_group(8, 8);
+constexpr size_t kLookbackBytes = sizeof(uint32_t) * vis::kMaxPasses * kMaxRows * vis::kRadix;
 constexpr size_t kOffKeys = (kOffLookback + kLookbackBytes + 255) / 256 * 256;   // cleared below this
 constexpr size_t kOffVals = kOffKeys + sizeof(uint64_t) * kMaxKeys;
 constexpr size_t kScratchBytes = kOffVals + sizeof(uint32_t) * kMaxKeys;
@@ -97,7 +98,9 @@ extern "C" vis_status vis_sort_pairs_noalloc(const uint64_t* keys_in, const uint
     // the array keeps the previous call's contents: clear the status block, the histograms and
     // the look-back words that this sort's passes read (passes x partitions x digits)
     const int passes = (key_bits + vis::kRadixBits - 1) / vis::kRadixBits;
-    const size_t used = kOffLookback + sizeof(uint32_t) * (size_t)passes * (size_t)vis::sort_parts<uint64_t>(m) *
+    const size_t used = kOffLookback + sizeof(uint32_t) * (size_t)passes *
+                                           (size_t)vis::lookback_rows(vis::sort_parts<uint64_t>(m),
+                                                                      vis::lookback_group(8, 8)) *
                                            vis::kRadix;
     cudaError_t e = cudaMemsetAsync(w, 0, used, stream);
     if (e != cudaSuccess) return fail_na(VIS_ERR_CUDA, cudaGetErrorString(e));

@@ -223,7 +223,7 @@ void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
     uint16_t* k1 = reinterpret_cast<uint16_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);
     uint32_t* v1 = reinterpret_cast<uint32_t*>(ws + L.off_vals[1]);
-    const size_t words = (size_t)L.sort_parts * kRadix;
+    const size_t words = (size_t)lookback_rows(L.sort_parts, lookback_group(2, kRadixBits)) * kRadix;
     // emitted copies in buffer 0; one pass -> values in 1, two passes -> keys + values in 1, then values in 0
     const int low_bits = L.tile_bits < kRadixBits ? L.tile_bits : kRadixBits;
     if (L.passes == 1) {

@@ -48,6 +48,13 @@ inline int64_t depth_sort_parts(int64_t n, int digit_bits = 8) {
     const int64_t part = (int64_t)kSortThreads * depth_sort_kpt(n, digit_bits);
     return (n + part - 1) / part;
 }
+// Look-back region of one radix pass over `parts` partitions (onesweep.cuh): a row of
+// 2^digit_bits words per partition, then a row per group of lookback_group consecutive
+// partitions (the group's counts and arrivals). The group is one look-back window wide.
+constexpr int lookback_group(int key_bytes, int digit_bits) {
+    return digit_bits > 8 ? 4 : (key_bytes == 2 ? 8 : 16);
+}
+inline int64_t lookback_rows(int64_t parts, int group) { return parts + (parts + group - 1) / group; }
 // passes of a key of `bits` significant bits at digit_bits per pass
 inline int passes_for(int bits, int digit_bits) { return bits <= 0 ? 0 : (bits + digit_bits - 1) / digit_bits; }
 constexpr int kRadixBits = 8;
