@@ -337,13 +337,16 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
                  ((size_t)1 << L.digit_bits)
            : 0;
     const int tile_group = lookback_group(L.tile_fused ? 2 : L.key_bytes, tile_digit);
-    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (size_t)L.passes *
-                                                                           lookback_rows(L.sort_parts, tile_group) *
-                                                                           ((size_t)1 << tile_digit)));
+    const size_t tile_lb_words = (size_t)L.passes * lookback_rows(L.sort_parts, tile_group) * ((size_t)1 << tile_digit);
+    L.off_lookback = take(sizeof(uint32_t) * (L.lookback_words_depth + (L.tile_fused ? 0 : tile_lb_words)));
+    if (!L.tile_fused) L.off_lookback_tile = L.off_lookback + sizeof(uint32_t) * L.lookback_words_depth;
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
     L.zero_end = off;
-    if (L.tile_fused) L.off_order = take(sizeof(uint32_t) * (size_t)L.ntiles);
+    if (L.tile_fused) {
+        L.off_order = take(sizeof(uint32_t) * (size_t)L.ntiles);
+        L.off_lookback_tile = take(sizeof(uint32_t) * tile_lb_words);
+    }
     L.off_rec = take(sizeof(float4) * 3 * (size_t)n);
     L.off_depth = take(sizeof(float) * (size_t)n);
     L.off_rect = take(sizeof(uint4) * (size_t)n);

@@ -273,7 +273,6 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     const uint32_t* touched = reinterpret_cast<const uint32_t*>(ws + L.off_touched);
     const int blocks_n = (int)L.prep_blocks;
     uint32_t* dv0 = reinterpret_cast<uint32_t*>(ws + L.off_dvals[0]);
-    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
     // The per-tile counts of the counts-first tile sort need only the footprints: outside a
     // profiled render they run on a side stream, beside the depth sort and the emission
     // (which leave most SMs idle at a million splats), and join before the tile passes.
@@ -322,7 +321,8 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     uint32_t* kb = L.sorted_buffer ? k0 : k1;
     uint32_t* vb = L.sorted_buffer ? v0 : v1;
     launch_sort_generic<uint32_t>(k0, v0, ka, va, kb, vb, L.cap, &ctrl->num_keys, tp,
-                                  reinterpret_cast<uint32_t*>(ws + L.off_hist_tile), lb + L.lookback_words_depth,
+                                  reinterpret_cast<uint32_t*>(ws + L.off_hist_tile),
+                                  reinterpret_cast<uint32_t*>(ws + L.off_lookback_tile),
                                   ctrl->part_counter + kMaxPasses, &ctrl->error, stream, mark, mark_index + 2,
                                   L.tile_bits - L.digit_bits * (tp - 1), 16, L.spin_limit, L.digit_bits);
     (void)sms;

@@ -182,6 +182,39 @@ tile_scan_kernel(const int* __restrict__ gdiff, int tiles_x, int tiles_y, uint32
     }
 }
 
+// Clears the look-back rows the tile passes of this render read, in their own region (not in
+// the cleared workspace region): per pass, the rows of the partitions of min(copies, cap) keys
+// and those of their groups. The copies are the sum of the first pass's digit histogram, which
+// the tile scan has just written.
+__global__ void __launch_bounds__(256)
+clear_tile_lookback(const uint32_t* __restrict__ hist, int64_t cap, int64_t parts_cap, int passes,
+                    uint32_t* __restrict__ lb) {
+    pdl_entry();
+    constexpr int64_t kPart = sort_partition<uint16_t>();
+    constexpr int kGroup = lookback_group(2, kRadixBits);
+    __shared__ uint32_t s_m;
+    if (threadIdx.x < 32) {
+        uint32_t v = 0;
+        for (int i = threadIdx.x; i < kRadix; i += 32) v += hist[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) s_m = v;
+    }
+    __syncthreads();
+    const int64_t m = min((int64_t)s_m, cap);
+    const int64_t parts = min((m + kPart - 1) / kPart, parts_cap), groups = (parts + kGroup - 1) / kGroup;
+    const int64_t row4 = kRadix / 4;   // 16-byte words per row
+    const int64_t pass4 = lookback_rows(parts_cap, kGroup) * row4;
+    const int64_t n1 = parts * row4, n2 = groups * row4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int p = 0; p < passes; ++p) {
+        uint4* base = reinterpret_cast<uint4*>(lb) + p * pass4;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1 + n2; i += stride)
+            base[i < n1 ? i : parts_cap * row4 + (i - n1)] = z;
+    }
+}
+
 static int sm_count_ts() {
     int dev = 0, s = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -213,12 +246,15 @@ void launch_tile_counts(const Layout& L, char* ws, cudaStream_t stream) {
     launch_k(true, tile_scan_kernel, 1, 1024, scan_smem, stream, (const int*)gdiff, L.tiles_x, L.tiles_y,
              reinterpret_cast<uint32_t*>(ws + L.off_hist_tile),
              reinterpret_cast<uint2*>(ws + L.off_ranges), reinterpret_cast<uint32_t*>(ws + L.off_order));
+    launch_k(true, clear_tile_lookback, sm_count_ts() / 2, 256, 0, stream,
+             (const uint32_t*)(ws + L.off_hist_tile), L.cap, L.sort_parts, L.passes,
+             reinterpret_cast<uint32_t*>(ws + L.off_lookback_tile));
 }
 
 void launch_tile_passes(const Layout& L, char* ws, cudaStream_t stream) {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ws + L.off_hist_tile);
-    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback) + L.lookback_words_depth;
+    uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback_tile);
     uint16_t* k0 = reinterpret_cast<uint16_t*>(ws + L.off_keys[0]);
     uint16_t* k1 = reinterpret_cast<uint16_t*>(ws + L.off_keys[1]);
     uint32_t* v0 = reinterpret_cast<uint32_t*>(ws + L.off_vals[0]);

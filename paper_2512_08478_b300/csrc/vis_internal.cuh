@@ -54,7 +54,7 @@ inline int64_t depth_sort_parts(int64_t n, int digit_bits = 8) {
 constexpr int lookback_group(int key_bytes, int digit_bits) {
     return digit_bits > 8 ? 4 : (key_bytes == 2 ? 8 : 16);
 }
-inline int64_t lookback_rows(int64_t parts, int group) { return parts + (parts + group - 1) / group; }
+__host__ __device__ inline int64_t lookback_rows(int64_t parts, int group) { return parts + (parts + group - 1) / group; }
 // passes of a key of `bits` significant bits at digit_bits per pass
 inline int passes_for(int bits, int digit_bits) { return bits <= 0 ? 0 : (bits + digit_bits - 1) / digit_bits; }
 constexpr int kRadixBits = 8;
@@ -95,6 +95,10 @@ struct Layout {
     size_t off_scan_tot = 0;   // kMaxScanChunks 64-bit chunk totals of the block-sum scans
     size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
     size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
+    // look-back words of the tile sort's passes: after the depth sort's, inside the cleared
+    // region; with the counts-first tile sort a region of their own, of which each render clears
+    // only the rows its passes read (clear_tile_lookback, beside the depth sort)
+    size_t off_lookback_tile = 0;
     size_t off_tfinal = 0, off_last = 0, off_g2 = 0;
     size_t off_zmax = 0;     // float[tiles]: largest depth-buffer value per tile (depth-tested renders)
     // depth-first mode only
