@@ -153,13 +153,21 @@ emit_tiles(const uint32_t* __restrict__ dvals, const uint4* __restrict__ rect, i
     for (int w = 0; w < warp; ++w) warp_base += warp_tot[w];
     const uint32_t run = warp_tot[warp];
     const int g0 = warp * 32;
-    for (uint32_t q = lane; q < run; q += 32) {
-        // owner: the last slot of the warp whose start is <= q (it has copies: zero counts
-        // share their start with the next slot)
-        int lo = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-            if (s_start[g0 + lo + step] <= q) lo += step;
+    const uint32_t start = incl - cnt;
+    const bool has = cnt > 0;
+    for (uint32_t q0 = 0; q0 < run; q0 += 32) {
+        // owner of copy q0 + lane: the slots with copies are a prefix of the warp (every
+        // survivor has one, the slots past the last survivor none), their runs in slot order,
+        // so the owner is the number of runs that start at or before the copy, minus one: the
+        // runs starting before q0 (a ballot) plus those starting in q0 .. q0 + lane (an OR of
+        // their start bits)
+        const uint32_t nb = __popc(__ballot_sync(0xffffffffu, has && start < q0));
+        const uint32_t in = __reduce_or_sync(0xffffffffu, (has && start >= q0 && start - q0 < 32u) ? 1u << (start - q0)
+                                                                                                 : 0u);
+        const uint32_t q = q0 + lane;
+        if (q >= run) continue;   // the last round; no collective follows in it
+        const int owner = (int)(nb + __popc(in & (0xffffffffu >> (31 - lane)))) - 1;
+        const int lo = owner < 0 ? 0 : owner;
         const uint4 a = s_a[g0 + lo];
         const uint32_t k = q - s_start[g0 + lo];
         uint32_t tile;
