@@ -293,17 +293,18 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         opts = make(tile, ppt)
     ws.opts = opts   # the layout of the chosen options (the buffer holds every candidate's)
     desc["tile"] = tile
-    for i in range(args.warmup):
-        frame(i)
-    vis.vis_check(ws.buf)
-
-    # ---- device-timed region ----
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        # the warm-up runs after the sampler's start-up pause, right before the timed frames,
+        # so that the GPU is not left idle just before the first of them
+        for i in range(args.warmup):
+            frame(i)
+        vis.vis_check(ws.buf)
+        # ---- device-timed region ----
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         ev0.record(stream)
         for i in range(args.steps):
             frame(i)
@@ -524,11 +525,11 @@ def batch_leg(args):
     steps = max(3, min(args.steps, 10))
 
     def timed(fn):
-        for _ in range(max(3, args.warmup // 2)):
-            fn()
-        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
+            for _ in range(max(3, args.warmup // 2)):   # warm-up right before the timed steps
+                fn()
+            torch.cuda.synchronize()
             e0.record(stream)
             for _ in range(steps):
                 fn()
@@ -649,14 +650,14 @@ def run_multi(args):
     def single(i):
         vis.vis_render(merged.handle, cam_objs[i % 8], W, H, (0.0, 0.0, 0.0), rgb, alpha, wsm.buf, opts)
 
-    for i in range(args.warmup):
-        multi(i)
-        single(i)
-    keys = vis.vis_check(ws.buf)
-    vis.vis_check(wsm.buf)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        for i in range(args.warmup):   # warm-up right before the timed frames
+            multi(i)
+            single(i)
+        keys = vis.vis_check(ws.buf)
+        vis.vis_check(wsm.buf)
+        torch.cuda.synchronize()
         e[0].record(stream)
         for i in range(args.steps):
             multi(i)
