@@ -248,9 +248,13 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
             if args.depth_plane is not None else None)
     dynamic = workload == "6m" and not packed
     if dynamic:
+        # the scene keeps frame 0; a frame renders with the update applied inside the
+        # preprocess (vis_render_dynamic); the update kernel on its own is timed in the stage
+        # pass, into scratch arrays
         dyn = {k: torch.from_numpy(v).cuda() for k, v in extra.items()}
-        means0 = sc.tensors["means"].clone()
-        logits0 = sc.tensors["opacity_logits"].clone()
+        means0 = sc.tensors["means"]
+        logits0 = sc.tensors["opacity_logits"]
+        upd_means, upd_logits = torch.empty_like(means0), torch.empty_like(logits0)
         n_frames = desc["frames"]
         upd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
@@ -261,11 +265,13 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         if dynamic:
             if timed:
                 upd_ev[i][0].record(stream)
-            vis.vis_dynamic_update(means0, dyn["velocity"], logits0, dyn["amp"], dyn["freq"], dyn["phase"],
-                                   k / n_frames, sc.tensors["means"], sc.tensors["opacity_logits"])
-            if timed:
+                vis.vis_dynamic_update(means0, dyn["velocity"], logits0, dyn["amp"], dyn["freq"], dyn["phase"],
+                                       k / n_frames, upd_means, upd_logits)
                 upd_ev[i][1].record(stream)
-        vis.vis_render(handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts, depth=dbuf)
+            vis.vis_render_dynamic(handle, dyn["velocity"], dyn["amp"], dyn["freq"], dyn["phase"], k / n_frames, c,
+                                   W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts)
+        else:
+            vis.vis_render(handle, c, W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts, depth=dbuf)
         if fwdbwd:
             torch.sub(rgb, tgt_rgb, out=d_rgb)
             d_rgb.mul_(2.0 / rgb.numel())
@@ -343,7 +349,11 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     a_min = float(np.float32(vis.make_opts().alpha_min))
     for i in range(min(args.steps, len(cam_objs))):
         k = (view0 + i) % len(cam_objs)
-        vis.vis_render(handle, cam_objs[k], W, H, (0.0, 0.0, 0.0), rgb, alpha, ws.buf, opts, depth=dbuf)
+        if dynamic:   # the frame's own attributes
+            vis.vis_dynamic_update(means0, dyn["velocity"], logits0, dyn["amp"], dyn["freq"], dyn["phase"],
+                                   k / n_frames, upd_means, upd_logits)
+            opac = torch.sigmoid(upd_logits.reshape(-1))
+        frame(i)
         mlist.append(vis.vis_check(ws.buf))
         touched = ws.buf[lay.off_touched: lay.off_touched + 4 * n].view(torch.int32)
         zview = ws.buf[lay.off_depth: lay.off_depth + 4 * n].view(torch.float32)
@@ -437,11 +447,16 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
                else dict(value=None, note="not measured for a pre-packed scene or a depth buffer"))
 
     # kernels per frame: preprocess, (mode 1) block-sum scan, compaction, depth histogram,
-    # depth passes, touch sums, scan, emission, tile counts, tile scan, tile passes / (mode 0)
-    # scan, duplication, histogram, passes, ranges; the compositor
+    # depth passes, touch sums, scan, emission, tile counts, tile scan, tile look-back clear,
+    # tile passes / (mode 0) scan, duplication, histogram, passes, ranges; the compositor; a
+    # block-sum scan over more than 8192 blocks takes two kernels; the backward adds the
+    # compositor's adjoint and the preprocess adjoint; a depth buffer its per-tile maximum
     depth_passes = {8: 4, 10: 4, 11: 3}[args.digit_bits]
-    launches = {0: 6 + passes, 1: 10 + depth_passes + passes}[sort_mode] + (2 if fwdbwd else 0) + \
-        (1 if dynamic else 0) + (1 if dbuf is not None else 0)
+    scan_k = 2 if (n + 255) // 256 > 8192 else 1
+    fused_tiles = lay.key_bytes == 2
+    launches = {0: 5 + scan_k + passes,
+                1: 6 + 2 * scan_k + depth_passes + passes + (3 if fused_tiles else 2)}[sort_mode] + \
+        (2 if fwdbwd else 0) + (1 if dbuf is not None else 0)
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",

@@ -168,10 +168,11 @@ typedef struct {
 /* Device-written status block at workspace offset off_ctrl (= 0). */
 typedef struct {
     uint32_t num_keys;       /* (tile, splat) pairs listed by the last render (may exceed capacity) */
-    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout */
+    uint32_t error;          /* bit 0: capacity exceeded, bit 1: spin timeout, bit 2: an adjoint asked
+                                of a dynamic frame (vis_render_dynamic) */
     uint32_t internal[16];   /* sort partition tickets */
     uint32_t num_visible;    /* Gaussians that survived culling (sort_mode 1) */
-    uint32_t pad0;
+    uint32_t flags;          /* bit 0: the last render was a dynamic frame (it has no adjoint) */
     uint64_t pair_tests;     /* with collect_stats: (pixel, splat) pairs the compositor tested */
     uint64_t hits;           /* with collect_stats: pairs it composited */
     uint32_t reserved[40];
@@ -397,6 +398,22 @@ VIS_API vis_status vis_batch_check(const void* ws, int n_images, void* stream, i
 VIS_API vis_status vis_dynamic_update(const float* means0, const float* velocity, const float* logits0,
                                       const float* amp, const float* freq, const float* phase, float t,
                                       int64_t n, float* means_out, float* logits_out, void* stream);
+
+/* Frame t of a dynamic scene without storing it: `scene` borrows the frame-0 attributes
+ * (its means and opacity_logits are means0 and logits0 above), and the preprocess applies
+ * vis_dynamic_update's formulas to them as it reads them, rounding exactly as that kernel
+ * does; the image is the one vis_dynamic_update into a scene followed by vis_render of it
+ * gives, bit for bit, without the update's 16 B per Gaussian written and read back.
+ *  velocity            device float[n][3]   (n = the scene's size)
+ *  amp, freq, phase    device float[n]
+ * Plain fp32 scenes only (VIS_ERR_UNSUPPORTED for a pre-packed scene). The frame has no
+ * adjoint: a vis_render_backward on its workspace computes nothing, and vis_check then
+ * returns VIS_ERR_UNSUPPORTED (status bit 2) until the next render. Other arguments and
+ * errors as vis_render. */
+VIS_API vis_status vis_render_dynamic(vis_scene_t scene, const float* velocity, const float* amp,
+                                      const float* freq, const float* phase, float t, const vis_camera* cam,
+                                      int W, int H, const float bg[3], float* out_rgb, float* out_alpha,
+                                      void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream);
 
 /* The same sort for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a library convenience). Some callers may not call cudaMalloc

@@ -112,6 +112,9 @@ def lib():
                                            _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts), _P]),
             "vis_batch_check": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int64)]),
             "vis_dynamic_update": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_float, C.c_int64, _P, _P, _P]),
+            "vis_render_dynamic": (C.c_int, [_P, _P, _P, _P, _P, C.c_float, C.POINTER(vis_camera), C.c_int, C.c_int,
+                                             C.POINTER(C.c_float), _P, _P, _P, C.c_size_t, C.POINTER(vis_render_opts),
+                                             _P]),
             "vis_profile_end": (C.c_int, [C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         }
@@ -134,7 +137,7 @@ def _torch():
 
 
 def _ptr(t):
-    return _P(t.data_ptr())
+    return _P(t.data_ptr() if t is not None else None)
 
 
 def _stream(stream=None):
@@ -267,6 +270,16 @@ def vis_dynamic_update(means0, velocity, logits0, amp, freq, phase, t, means_out
     _ok(lib().vis_dynamic_update(_ptr(means0), _ptr(velocity), _ptr(logits0), _ptr(amp), _ptr(freq), _ptr(phase),
                                  float(t), int(means0.shape[0]), _ptr(means_out), _ptr(logits_out),
                                  _stream(stream)))
+
+
+def vis_render_dynamic(scene_handle, velocity, amp, freq, phase, t, cam, W, H, bg, out_rgb, out_alpha, ws, opts=None,
+                       stream=None):
+    """Frame t of a dynamic scene whose handle borrows the frame-0 means and logits: the
+    update of vis_dynamic_update applied inside the preprocess (the same image, bit for bit)."""
+    c = cam if isinstance(cam, vis_camera) else make_camera(cam)
+    _ok(lib().vis_render_dynamic(scene_handle, _ptr(velocity), _ptr(amp), _ptr(freq), _ptr(phase), float(t),
+                                 C.byref(c), int(W), int(H), _bg(bg), _ptr(out_rgb), _ptr(out_alpha), _ptr(ws),
+                                 ws.numel() * ws.element_size(), _opts_ref(opts), _stream(stream)))
 
 
 def vis_last_error():

@@ -23,8 +23,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", str(ROOT / "include")]
 # preprocess.cu: no floating-point contraction, so that the plain kernel (parameters by value)
-# and the fused batch's kernel (parameters in shared memory) round identically
-PER_FILE = {"preprocess.cu": ["--fmad=false"]}
+# and the fused batch's kernel (parameters in shared memory) round identically; dynamic.cu
+# likewise, so that the update kernel and the preprocess that applies the same update on the
+# fly (dynamic.cuh) round identically
+PER_FILE = {"preprocess.cu": ["--fmad=false"], "dynamic.cu": ["--fmad=false"]}
 
 
 def _headers():

@@ -562,13 +562,22 @@ static vis::PrepParams scene_params(const vis_scene_t* scenes, const float* mode
     return p;
 }
 
+// The per-frame update arrays of a dynamic frame (vis_render_dynamic).
+struct DynFrame {
+    const float* velocity;
+    const float* amp;
+    const float* freq;
+    const float* phase;
+    float t;
+};
+
 // One image of one or more scenes: every scene is preprocessed into its slots (with its
 // model transform folded into the view), then one global sort and one compositing pass run
-// over all slots (Algorithm 1).
+// over all slots (Algorithm 1). dyn: a dynamic frame of the one scene (else null).
 static vis_status render_impl(const vis_scene_t* scenes, const float* models, int n_scenes, bool padded,
                               const vis_camera* cam, int W, int H, const float bg[3],
                               const float* zlim, float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
-                              const vis_render_opts* opts, void* stream_) {
+                              const vis_render_opts* opts, void* stream_, const DynFrame* dyn = nullptr) {
     vis_render_opts o;
     vis::Layout L;
     std::vector<int64_t> offsets;
@@ -586,6 +595,11 @@ static vis_status render_impl(const vis_scene_t* scenes, const float* models, in
     for (int k = 0; k < n_scenes; ++k) {
         vis::PrepParams p = scene_params(scenes, models, k, padded, offsets, cam, W, H, L, o);
         if (zlim) p.tile_zmax = reinterpret_cast<const float*>(w + L.off_zmax);
+        if (dyn) {
+            p.dyn_velocity = dyn->velocity; p.dyn_amp = dyn->amp; p.dyn_freq = dyn->freq; p.dyn_phase = dyn->phase;
+            p.dyn_t = dyn->t;
+            p.dyn_flags = &reinterpret_cast<vis::Ctrl*>(w + L.off_ctrl)->flags;
+        }
         vis::launch_preprocess(p, L, w, stream);
     }
     prof_mark(2, stream);
@@ -622,6 +636,21 @@ vis_status vis_render(vis_scene_t scene, const vis_camera* cam, int W, int H, co
                       float* out_alpha, void* ws, size_t ws_bytes, const vis_render_opts* opts, void* stream_) {
     return render_impl(&scene, nullptr, 1, false, cam, W, H, bg, nullptr, out_rgb, out_alpha, ws, ws_bytes, opts,
                        stream_);
+}
+
+vis_status vis_render_dynamic(vis_scene_t scene, const float* velocity, const float* amp, const float* freq,
+                              const float* phase, float t, const vis_camera* cam, int W, int H, const float bg[3],
+                              float* out_rgb, float* out_alpha, void* ws, size_t ws_bytes,
+                              const vis_render_opts* opts, void* stream_) {
+    if (!scene) return fail(VIS_ERR_INVALID_ARG, "scene is null");
+    if (scene->pk_pos) return fail(VIS_ERR_UNSUPPORTED, "a pre-packed scene has no fp32 frame-0 attributes to update");
+    if (!std::isfinite(t)) return fail(VIS_ERR_INVALID_ARG, "t is not finite");
+    const void* ptrs[4] = {velocity, amp, freq, phase};
+    for (int k = 0; k < 4; ++k)
+        if (!ptrs[k] || !aligned16(ptrs[k])) return fail(VIS_ERR_INVALID_ARG, "dynamic array %d null or misaligned", k);
+    const DynFrame dyn = {velocity, amp, freq, phase, t};
+    return render_impl(&scene, nullptr, 1, false, cam, W, H, bg, nullptr, out_rgb, out_alpha, ws, ws_bytes, opts,
+                       stream_, &dyn);
 }
 
 vis_status vis_render_depth(vis_scene_t scene, const vis_camera* cam, int W, int H, const float bg[3],
@@ -664,6 +693,9 @@ vis_status vis_check(const void* ws, void* stream_, int64_t* num_keys) {
     if (c.error & vis::kErrCapacity)
         return fail(VIS_ERR_CAPACITY, "%u keys exceed the workspace capacity", c.num_keys);
     if (c.error & vis::kErrTimeout) return fail(VIS_ERR_TIMEOUT, "a device spin wait timed out");
+    if (c.error & vis::kErrNoAdjoint)
+        return fail(VIS_ERR_UNSUPPORTED, "no adjoint of a dynamic frame: its updated attributes were never stored "
+                                         "(update the scene with vis_dynamic_update and render it with vis_render)");
     g_err.clear();
     return VIS_OK;
 }

@@ -70,8 +70,12 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                           const float* __restrict__ t_final, const int32_t* __restrict__ last_in,
                           const float* __restrict__ d_rgb, const float* __restrict__ d_alpha,
                           float* __restrict__ g2, const float* __restrict__ depth,
-                          const float* __restrict__ zlim, const Ctrl* __restrict__ ctrl,
+                          const float* __restrict__ zlim, Ctrl* __restrict__ ctrl,
                           const uint32_t* __restrict__ order) {
+    if (ctrl->flags & kFlagNoAdjoint) {   // a dynamic frame: its attributes were never stored
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctrl->error, kErrNoAdjoint);
+        return;
+    }
     if (ctrl->error) return;   // the forward produced no valid lists: leave the gradients at zero
     constexpr int NT = TILE * TILE / PPT;     // threads; each owns PPT vertically adjacent pixels
     constexpr int NW = NT / 32;               // warps; each owns an 8 x (4 PPT) pixel block
@@ -518,7 +522,7 @@ void launch_composite_backward(const Layout& L, char* ws, const float bg[3], flo
     const int blocks = (int)L.ntiles;
     const QScale qs = q_scale();
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
-    const Ctrl* ctrl = reinterpret_cast<const Ctrl*>(ws + L.off_ctrl);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
 #define VIS_LAUNCH_BWD_D(TS, PP, DT)                                                                       \
     composite_backward_kernel<TS, PP, DT><<<blocks, TS * TS / PP, 0, stream>>>(                            \

@@ -1,25 +1,19 @@
-// Per-frame update of a dynamic scene, standing in for the paper's per-frame
-// Gaussian generator (section 3.3: a model produces the Gaussians of each frame,
-// which the renderer then preprocesses and re-sorts globally; section 4 shows that
-// re-sorting every frame is what avoids lazy-sort artifacts):
-//   mu_t    = mu_0 + t v
-//   logit_t = logit_0 + A sin(2 pi f t + phi)
-// Elementwise and bandwidth-bound: 40 B read and 16 B written per Gaussian.
-#include "vis_internal.cuh"
+// The per-frame update kernel of a dynamic scene (the formulas: dynamic.cuh). Elementwise and
+// bandwidth-bound: 40 B read and 16 B written per Gaussian.
+#include "dynamic.cuh"
 
 namespace vis {
 
 __global__ void __launch_bounds__(256)
 dynamic_update_kernel(const float* __restrict__ means0, const float* __restrict__ velocity,
                       const float* __restrict__ logits0, const float* __restrict__ amp,
-                      const float* __restrict__ freq, const float* __restrict__ phase, float t, float two_pi,
-                      int64_t n, float* __restrict__ means_out, float* __restrict__ logits_out) {
+                      const float* __restrict__ freq, const float* __restrict__ phase, float t, int64_t n,
+                      float* __restrict__ means_out, float* __restrict__ logits_out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) means_out[3 * i + k] = __fmaf_rn(t, velocity[3 * i + k], means0[3 * i + k]);
-        const float arg = __fmaf_rn(__fmul_rn(two_pi, freq[i]), t, phase[i]);
-        logits_out[i] = __fmaf_rn(amp[i], sinf(arg), logits0[i]);
+        for (int k = 0; k < 3; ++k) means_out[3 * i + k] = dyn_mean(means0[3 * i + k], velocity[3 * i + k], t);
+        logits_out[i] = dyn_logit(logits0[i], amp[i], freq[i], phase[i], t);
     }
 }
 
@@ -31,9 +25,8 @@ void launch_dynamic_update(const float* means0, const float* velocity, const flo
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (n + 255) / 256, lim = (int64_t)sms * 16;
     const int blocks = (int)(want < lim ? want : lim);
-    const float two_pi = (float)(2.0 * 3.14159265358979323846);
-    dynamic_update_kernel<<<blocks, 256, 0, stream>>>(means0, velocity, logits0, amp, freq, phase, t, two_pi, n,
-                                                      means_out, logits_out);
+    dynamic_update_kernel<<<blocks, 256, 0, stream>>>(means0, velocity, logits0, amp, freq, phase, t, n, means_out,
+                                                      logits_out);
 }
 
 }  // namespace vis

@@ -23,6 +23,7 @@
 
 #include "vis_internal.cuh"
 #include "footprint.cuh"
+#include "dynamic.cuh"
 
 namespace vis {
 
@@ -72,6 +73,7 @@ __device__ __forceinline__ void preprocess_block(const PrepParams& p, int local_
     const int gi = (int)p.index_offset + i;   // slots number at most 2^31 - 1
     __shared__ float s_trim[7][kPrepThreads];
     uint32_t touched = 0;
+    if (p.dyn_flags && local_block == 0 && threadIdx.x == 0) *p.dyn_flags = kFlagNoAdjoint;
     if (i < p.n) {
         // --- camera-space position in float-float: p = R mu + t ---
         float mx, my, mz, opac;
@@ -88,7 +90,14 @@ __device__ __forceinline__ void preprocess_block(const PrepParams& p, int local_
             mx = __ldg(p.means + 3 * i + 0);
             my = __ldg(p.means + 3 * i + 1);
             mz = __ldg(p.means + 3 * i + 2);
-            opac = 1.f / (1.f + __expf(-__ldg(p.logits + i)));
+            float logit = __ldg(p.logits + i);
+            if (p.dyn_velocity) {   // a dynamic frame: frame 0's attributes updated as they are read
+                mx = dyn_mean(mx, __ldg(p.dyn_velocity + 3 * i + 0), p.dyn_t);
+                my = dyn_mean(my, __ldg(p.dyn_velocity + 3 * i + 1), p.dyn_t);
+                mz = dyn_mean(mz, __ldg(p.dyn_velocity + 3 * i + 2), p.dyn_t);
+                logit = dyn_logit(logit, __ldg(p.dyn_amp + i), __ldg(p.dyn_freq + i), __ldg(p.dyn_phase + i), p.dyn_t);
+            }
+            opac = 1.f / (1.f + __expf(-logit));
             // quaternion and log-scales are read after the cull test: start them towards L2
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p.quats + 4 * (size_t)i));
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p.log_scales + 3 * (size_t)i));

@@ -66,6 +66,9 @@ constexpr uint32_t kMaxKeys = (1u << 30) - 1;   // look-back words hold 30-bit c
 // ctrl->error bits
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrNoAdjoint = 4u;   // an adjoint was asked of a render that has none
+// ctrl->flags bits
+constexpr uint32_t kFlagNoAdjoint = 1u;  // a dynamic frame: its attributes were never stored
 
 // Default look-back spin limit, in polls (each poll ~ a few hundred ns with the backoff);
 // far beyond any legitimate wait, it only bounds a wait that can never end. A render's
@@ -126,7 +129,7 @@ struct Ctrl {
     uint32_t error;
     uint32_t part_counter[2 * kMaxPasses];   // partition tickets of up to two sorts per render
     uint32_t num_visible;                    // Gaussians that survive culling (depth-first sort)
-    uint32_t pad0;
+    uint32_t flags;                          // kFlagNoAdjoint: the render was a dynamic frame
     unsigned long long pair_tests;           // compositor statistics (collect_stats only)
     unsigned long long hits;
     uint32_t reserved[40];
@@ -170,6 +173,16 @@ struct PrepParams {
     float shc[12];           // SH polynomial constants, see sh_constants()
     uint32_t batch_image;    // a fused batch: the item's image index (kept in the footprints)
     uint32_t canvas_row0;    // a fused batch: the image's first tile row in its group's canvas
+    // a dynamic frame (vis_render_dynamic): means and logits hold frame 0; the preprocess
+    // applies the update of dynamic.cuh at time dyn_t with these arrays (null otherwise) and
+    // marks the status block (dyn_flags) as a render with no adjoint
+    const float* dyn_velocity;
+    const float* dyn_amp;
+    const float* dyn_freq;
+    const float* dyn_phase;
+    uint32_t* dyn_flags;
+    float dyn_t;
+    uint32_t dyn_pad;
 };
 
 // One image of a fused batch (vis_render_batch with lanes = 0): its (asset, camera) item's
