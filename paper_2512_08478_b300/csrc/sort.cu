@@ -29,7 +29,7 @@ namespace vis {
 // Digit histograms of `passes` digits of DBITS bits (pass p: digit (key >> DBITS p)),
 // hist[p * D + digit]; dynamic shared memory of passes * D words.
 template <typename K, int DBITS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 sort_histogram(const K* __restrict__ keys, const uint32_t* __restrict__ num_keys, int64_t cap, int passes,
                uint32_t* __restrict__ hist, const uint32_t* __restrict__ error) {
     constexpr int D = 1 << DBITS;
@@ -325,9 +325,12 @@ static void sort_generic_impl(const K* keys_in, const uint32_t* vals_in, K* keys
     });
     const int64_t parts = (cap + (int64_t)kSortThreads * KPT - 1) / ((int64_t)kSortThreads * KPT);
     const int grid = pass_grid(parts, SortOcc<K, KPT, DBITS>::value);
-    const int64_t hb = (cap + 255) / 256, hlim = (int64_t)sm_count() * 4;
+    // two CTAs of 1024 threads per SM: each flushes its shared histograms with one global
+    // atomic per non-zero bin, so fewer, larger CTAs halve the atomics on the same words
+    // (against four CTAs of 256: 1M depth sort 0.087 -> 0.083 ms, 6M 0.251 -> 0.238 ms)
+    const int64_t hb = (cap + 1023) / 1024, hlim = (int64_t)sm_count() * 2;
     const int hist_blocks = (int)(hb < hlim ? hb : hlim);
-    launch_k(true, sort_histogram<K, DBITS>, hist_blocks, 256, sizeof(uint32_t) * passes * D, stream, keys_in,
+    launch_k(true, sort_histogram<K, DBITS>, hist_blocks, 1024, sizeof(uint32_t) * passes * D, stream, keys_in,
              (const uint32_t*)num_keys_dev, cap, passes, hist, (const uint32_t*)error);
     if (mark) mark(mark_index, stream);
     const K* src_k = keys_in;
