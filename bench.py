@@ -368,10 +368,14 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     # means + logit read, depth + rect + count written: 40 B; quaternion + log-scales: 28 B for the
     # Gaussians in front; SH (12 B per coefficient) read and 48 B record written per survivor
     bytes_pre = n * 40 + n_ok * 28 + n_vis * (12 * sh_k + 48)
+    pre_note = "40 B per Gaussian + 28 B per Gaussian in front + SH and 48 B record per survivor"
     if packed:   # fp16 planes: pos 8 B for all, cov 12 B in front, colour words per survivor
         bytes_pre = n * 32 + n_ok * 12 + n_vis * (vis.vis_packed_size(1, desc["sh_degree"])[2] + 48)
-    hbm = {"preprocess": (bytes_pre, stage_ms["preprocess"],
-                          "40 B per Gaussian + 28 B per Gaussian in front + SH and 48 B record per survivor")}
+    if dynamic:   # the update's arrays: velocity, amplitude, frequency and phase per Gaussian
+        bytes_pre += n * 24
+        pre_note = "64 B per Gaussian (with the update's 24) + 28 B per Gaussian in front + SH and 48 B record " \
+                   "per survivor"
+    hbm = {"preprocess": (bytes_pre, stage_ms["preprocess"], pre_note)}
     if sort_mode == 1:
         dp = {8: 4, 10: 4, 11: 3}[args.digit_bits]   # digit passes of the depth sort
         # compaction: count + depth read per Gaussian, (depth, index) written per survivor; the
@@ -437,7 +441,9 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
     else:
         h = hbm_stages[dom]
         roof = dict(kernel=dom, bound="hbm", achieved=h["achieved_gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=h["frac"], traffic=_committed_traffic(dom, M, n), peak_source=peaks["source"],
+                    frac=h["frac"],
+                    traffic=_committed_traffic("preprocess_dynamic" if (dom == "preprocess" and dynamic) else dom, M, n),
+                    peak_source=peaks["source"],
                     algorithmic_bytes_per_launch=h["bytes"], launch_ms=h["ms"], bytes_model=h["bytes_model"])
 
     # ---- end to end through the C ABI with host buffers ----
