@@ -175,7 +175,8 @@ typedef struct {
     uint32_t flags;          /* bit 0: the last render was a dynamic frame (it has no adjoint) */
     uint64_t pair_tests;     /* with collect_stats: (pixel, splat) pairs the compositor tested */
     uint64_t hits;           /* with collect_stats: pairs it composited */
-    uint32_t reserved[40];
+    uint32_t internal2[2];   /* block-sum scan tickets */
+    uint32_t reserved[38];
 } vis_ctrl;
 
 /* Borrow a scene (section 3.2: mean, scale, rotation quaternion, opacity, SH colour).

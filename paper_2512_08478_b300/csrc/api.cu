@@ -342,6 +342,8 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
     if (!L.tile_fused) L.off_lookback_tile = L.off_lookback + sizeof(uint32_t) * L.lookback_words_depth;
     L.off_ranges = take(sizeof(uint2) * (size_t)L.ntiles);
     if (L.tile_fused) L.off_tdiff = take(sizeof(int) * (size_t)L.ntiles);
+    L.scan_slot_words = scan_parts(L.prep_blocks);
+    L.off_scan_lb = take(sizeof(unsigned long long) * 2 * (size_t)L.scan_slot_words);
     L.zero_end = off;
     if (L.tile_fused) {
         L.off_order = take(sizeof(uint32_t) * (size_t)L.ntiles);
@@ -353,7 +355,6 @@ Layout make_layout(int64_t n, int W, int H, int tile, int64_t cap, int mode, int
     L.off_touched = take(sizeof(uint32_t) * (size_t)n);
     L.off_bsum = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
     L.off_boff = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
-    L.off_scan_tot = take(sizeof(unsigned long long) * (size_t)kMaxScanChunks);
     if (df) {
         L.off_bsum2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);
         L.off_boff2 = take(sizeof(uint32_t) * (size_t)L.prep_blocks);

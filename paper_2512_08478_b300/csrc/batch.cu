@@ -154,18 +154,20 @@ vis::Layout group_layout(const Fused& F, const Group& g, int area, size_t* scrat
                                      F.digit_bits);
     if (order_ok)
         *order_ok = L.zero_end <= L.off_rec && L.off_order < L.off_rec && L.off_lookback_tile < L.off_rec &&
-                    L.off_boff < L.off_scan_tot &&
+                    L.off_scan_lb < L.zero_end && L.off_boff < L.off_bsum2 &&
                     L.off_vals[1] < L.off_tfinal && L.off_ctrl < L.off_rec;
-    // make_layout takes, in order: the cleared region (status .. tile counts), the tile
-    // order, the per-slot buffers (records .. block offsets), the scratch (scan totals ..
-    // values), then the adjoint and depth-buffer buffers
-    const size_t a_end = L.off_rec, b_begin = L.off_scan_tot, b_end = L.off_tfinal;
+    // make_layout takes, in order: the cleared region (status .. scan look-back words), the
+    // tile order and the tile look-back words, the per-slot buffers (records .. block
+    // offsets), the scratch (second block sums .. values), then the adjoint and depth-buffer
+    // buffers
+    const size_t a_end = L.off_rec, b_begin = L.off_bsum2, b_end = L.off_tfinal;
     const size_t base = F.off_scratch + (size_t)area * F.scratch_stride, shift_b = base + a_end;
     auto mv_a = [&](size_t& o) { o += base; };
     auto mv_b = [&](size_t& o) { o = shift_b + (o - b_begin); };
     mv_a(L.off_ctrl); mv_a(L.off_hist); mv_a(L.off_hist_tile); mv_a(L.off_lookback); mv_a(L.off_ranges);
-    mv_a(L.off_tdiff); mv_a(L.off_order); mv_a(L.off_lookback_tile); mv_a(L.zero_begin); mv_a(L.zero_end);
-    mv_b(L.off_scan_tot); mv_b(L.off_bsum2); mv_b(L.off_boff2);
+    mv_a(L.off_tdiff); mv_a(L.off_order); mv_a(L.off_lookback_tile); mv_a(L.off_scan_lb); mv_a(L.zero_begin);
+    mv_a(L.zero_end);
+    mv_b(L.off_bsum2); mv_b(L.off_boff2);
     for (int k = 0; k < 2; ++k) { mv_b(L.off_dkeys[k]); mv_b(L.off_dvals[k]); mv_b(L.off_keys[k]); mv_b(L.off_vals[k]); }
     L.off_rec = F.off_rec + sizeof(float4) * 3 * (size_t)g.slot_begin;
     L.off_depth = F.off_depth + sizeof(float) * (size_t)g.slot_begin;

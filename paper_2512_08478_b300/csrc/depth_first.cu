@@ -222,8 +222,9 @@ void launch_depth_sort(const Layout& L, char* ws, cudaStream_t stream) {
     uint32_t* lb = reinterpret_cast<uint32_t*>(ws + L.off_lookback);
     // 1. compaction of the surviving splats, in index order (the preprocess wrote the
     //    per-block survivor counts)
-    launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, nullptr, 0,
-                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
+    launch_scan_sums(bvis, bvis_off, L.prep_blocks, &ctrl->num_visible, &ctrl->error, 0,
+                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_lb), &ctrl->scan_ticket[0], L.spin_limit,
+                     stream);
     // the compaction writes buffer 1 when the depth sort has an odd number of passes, so
     // that the passes ping-pong (a pass never writes its own input) and end in buffer 0
     const bool odd = (L.depth_passes & 1) != 0;
@@ -300,7 +301,8 @@ void launch_depth_first(const Layout& L, char* ws, cudaStream_t stream, StageMar
     launch_k(true, depth_touch_sums, (blocks_n + kBlocksPerCta - 1) / kBlocksPerCta, kPrepThreads, 0, stream,
              (const uint32_t*)dv0, touched, L.n, (int64_t)blocks_n, (const Ctrl*)ctrl, bsum2);
     launch_scan_sums(bsum2, boff2, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap,
-                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
+                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_lb) + L.scan_slot_words,
+                     &ctrl->scan_ticket[1], L.spin_limit, stream);
     if (L.tile_fused) {
         // 3'-5'. 16-bit tile keys in depth order; per-tile counts -> histograms and ranges;
         // the passes (tile_sort.cu)

@@ -4,8 +4,8 @@
 // the order (and so the tie order of the sort) run-dependent. Here the offsets are
 // an exclusive prefix sum of the tiles-touched counts in Gaussian-index order, so
 // the key list -- and the sorted result -- is deterministic:
-//   1. scan_block_sums: one CTA scans the per-block sums written by the preprocess
-//      and stores the total key count M in the status block (capacity checked);
+//   1. scan_sums: a single-pass scan of the per-block sums written by the preprocess,
+//      which stores the total key count M in the status block (capacity checked);
 //   2. duplicate_kernel: each block rescans its 256 counts (warp shuffles), then
 //      every warp emits its Gaussians' keys cooperatively, lane j writing key j of
 //      the warp's contiguous output run, so stores are coalesced whatever the
@@ -17,154 +17,113 @@
 
 namespace vis {
 
-// Exclusive scan of per-block sums; the total goes to *total, and if `error` is given
-// a total above `cap` sets kErrCapacity there. One CTA of 1024 threads works through the
-// sums in chunks of kScanChunk: a coalesced load of the chunk into shared memory, a
-// sequential sum of each thread's contiguous run of it, a scan of the 1024 run totals,
-// the run's offsets written back in place, and a coalesced store; a carry links chunks.
-// kScanChunk (8192 sums, 32 KB of static shared memory) is declared in vis_internal.cuh.
+// Exclusive scan of per-block sums in one pass. Each CTA takes the next chunk of kScanPart sums
+// from a ticket, so chunks start in order and a CTA only ever waits on running ones. It scans the
+// chunk (two sums per thread, warp scans, a scan of the 32 warp totals) and publishes the chunk's
+// total. Its first warp then resolves the chunk's offset by decoupled look-back over the
+// preceding chunks' words, 32 per round. A word holds a chunk's total or its inclusive prefix,
+// flagged in its top two bits, and the walk stops at the nearest inclusive prefix. The chunk
+// then writes its offsets. The chunk with the last sum writes the total; a total above `cap`
+// (when cap > 0) sets kErrCapacity. A poll of an unpublished word gives up after spin_limit polls
+// and sets kErrTimeout; the prefix is then wrong but still published, so no successor waits.
+constexpr unsigned long long kScanFlagAgg = 1ull << 62, kScanFlagInc = 2ull << 62;
+constexpr unsigned long long kScanValMask = (1ull << 62) - 1;
 
-__global__ void __launch_bounds__(1024)
-scan_block_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
-                uint32_t* total_out, uint32_t* error, int64_t cap) {
-    pdl_entry();
-    __shared__ uint32_t s[kScanChunk];
-    __shared__ unsigned long long warp_tot[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int per = kScanChunk / 1024;
-    unsigned long long carry = 0;
-    for (int64_t c0 = 0; c0 < nblocks; c0 += kScanChunk) {
-        const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
-        for (int i = threadIdx.x; i < kScanChunk; i += 1024) s[i] = i < n ? bsum[c0 + i] : 0u;
-        __syncthreads();
-        const int r0 = threadIdx.x * per;
-        unsigned long long run = 0;
-#pragma unroll
-        for (int i = 0; i < per; ++i) run += s[r0 + i];
-        unsigned long long incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        unsigned long long excl = carry + incl - run, all = 0;
-        for (int w = 0; w < 32; ++w) {
-            const unsigned long long x = warp_tot[w];
-            if (w < warp) excl += x;
-            all += x;
-        }
-#pragma unroll
-        for (int i = 0; i < per; ++i) {
-            const uint32_t v = s[r0 + i];
-            s[r0 + i] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
-            excl += v;
-        }
-        carry += all;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += 1024) boff[c0 + i] = s[i];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        *total_out = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
-        if (error && carry > (unsigned long long)cap) atomicOr(error, kErrCapacity);
-    }
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-
-// Beyond one chunk the scan runs on one CTA per chunk: scan_chunk_totals sums each chunk
-// into chunk_tot[c]; scan_chunks adds, per CTA, the totals of the chunks before its own to
-// the same in-chunk scan as scan_block_sums, and the last chunk's CTA writes the total.
-__global__ void __launch_bounds__(1024)
-scan_chunk_totals(const uint32_t* __restrict__ bsum, int64_t nblocks, unsigned long long* __restrict__ chunk_tot) {
-    pdl_entry();
-    __shared__ unsigned long long warp_tot[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
-    const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
-    unsigned long long v = 0;
-    for (int i = threadIdx.x; i < n; i += 1024) v += bsum[c0 + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) warp_tot[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < 32; ++w) t += warp_tot[w];
-        chunk_tot[blockIdx.x] = t;
-    }
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 __global__ void __launch_bounds__(1024)
-scan_chunks(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks,
-            const unsigned long long* __restrict__ chunk_tot, uint32_t* total_out, uint32_t* error, int64_t cap) {
+scan_sums(const uint32_t* __restrict__ bsum, uint32_t* __restrict__ boff, int64_t nblocks, uint32_t* total_out,
+          uint32_t* error, int64_t cap, unsigned long long* lb, uint32_t* ticket, uint32_t spin_limit) {
+    static_assert(kScanPart == 2 * 1024, "two sums per thread");
     pdl_entry();
-    __shared__ uint32_t s[kScanChunk];
-    __shared__ unsigned long long warp_tot[32];
-    __shared__ unsigned long long s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int per = kScanChunk / 1024;
-    const int64_t c0 = (int64_t)blockIdx.x * kScanChunk;
-    const int n = (int)min((int64_t)kScanChunk, nblocks - c0);
-    // the totals of the chunks before this one
-    unsigned long long pre = 0;
-    for (int c = threadIdx.x; c < (int)blockIdx.x; c += 1024) pre += chunk_tot[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-    if (lane == 0) warp_tot[warp] = pre;
-    for (int i = threadIdx.x; i < kScanChunk; i += 1024) s[i] = i < n ? bsum[c0 + i] : 0u;
+    __shared__ uint32_t s_part;
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_part = atomicAdd(ticket, 1u);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < 32; ++w) t += warp_tot[w];
-        s_carry = t;
-    }
-    __syncthreads();
-    const unsigned long long carry = s_carry;
-    const int r0 = threadIdx.x * per;
-    unsigned long long run = 0;
-#pragma unroll
-    for (int i = 0; i < per; ++i) run += s[r0 + i];
+    const int64_t part = s_part;
+    const int64_t i0 = part * kScanPart + 2 * tid;
+    const uint32_t v0 = i0 < nblocks ? bsum[i0] : 0u;
+    const uint32_t v1 = i0 + 1 < nblocks ? bsum[i0 + 1] : 0u;
+    const unsigned long long run = (unsigned long long)v0 + v1;
     unsigned long long incl = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    unsigned long long excl = carry + incl - run, all = 0;
-    for (int w = 0; w < 32; ++w) {
-        const unsigned long long x = warp_tot[w];
-        if (w < warp) excl += x;
-        all += x;
-    }
+    if (warp == 0) {
+        const unsigned long long wt = s_warp[lane];
+        unsigned long long wi = wt;
 #pragma unroll
-    for (int i = 0; i < per; ++i) {
-        const uint32_t v = s[r0 + i];
-        s[r0 + i] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
-        excl += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        s_warp[lane] = wi - wt;   // exclusive offset of warp `lane` in the chunk
+        const unsigned long long agg = __shfl_sync(0xffffffffu, wi, 31);
+        if (lane == 0)
+            st_relaxed64(&lb[part], (part == 0 ? kScanFlagInc : kScanFlagAgg) | (agg < kScanValMask ? agg : kScanValMask));
+        unsigned long long prefix = 0;
+        bool to = false;
+        for (int64_t q0 = part - 1; q0 >= 0; q0 -= 32) {
+            const int64_t q = q0 - lane;
+            unsigned long long w = kScanFlagInc;   // before the first chunk: an inclusive prefix of 0
+            if (q >= 0) {
+                w = ld_relaxed64(&lb[q]);
+                uint32_t spins = 0;
+                while ((w >> 62) == 0) {
+                    if (++spins > spin_limit) {
+                        to = true;
+                        w = kScanFlagInc;
+                        break;
+                    }
+                    if (spins > 8) __nanosleep(32);
+                    w = ld_relaxed64(&lb[q]);
+                }
+            }
+            const uint32_t inc = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
+            const int stop = inc ? __ffs(inc) - 1 : 31;   // lanes up to the nearest inclusive prefix count
+            unsigned long long c = lane <= stop ? (w & kScanValMask) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            prefix += c;
+            if (inc) break;
+        }
+        const bool any_to = __any_sync(0xffffffffu, to);
+        if (lane == 0) {
+            const unsigned long long tot = prefix + agg;
+            if (part > 0) st_relaxed64(&lb[part], kScanFlagInc | (tot < kScanValMask ? tot : kScanValMask));
+            s_prefix = prefix;
+            if (any_to && error) atomicOr(error, kErrTimeout);
+            if ((part + 1) * kScanPart >= nblocks) {   // the chunk with the last sum
+                *total_out = (uint32_t)min(tot, (unsigned long long)0xffffffffu);
+                if (cap > 0 && error && tot > (unsigned long long)cap) atomicOr(error, kErrCapacity);
+            }
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += 1024) boff[c0 + i] = s[i];
-    if (threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) {
-        const unsigned long long tot = carry + all;
-        *total_out = (uint32_t)min(tot, (unsigned long long)0xffffffffu);
-        if (error && tot > (unsigned long long)cap) atomicOr(error, kErrCapacity);
-    }
+    const unsigned long long excl = s_prefix + s_warp[warp] + incl - run;
+    if (i0 < nblocks) boff[i0] = (uint32_t)min(excl, (unsigned long long)0xffffffffu);
+    if (i0 + 1 < nblocks) boff[i0 + 1] = (uint32_t)min(excl + v0, (unsigned long long)0xffffffffu);
 }
 
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
-                      int64_t cap, unsigned long long* chunk_tot, cudaStream_t stream) {
-    const int64_t chunks = (nblocks + kScanChunk - 1) / kScanChunk;
-    if (chunks <= 1 || !chunk_tot) {
-        launch_k(true, scan_block_sums, 1, 1024, 0, stream, bsum, boff, nblocks, total, error, cap);
-        return;
-    }
-    launch_k(true, scan_chunk_totals, (int)chunks, 1024, 0, stream, bsum, nblocks, chunk_tot);
-    launch_k(true, scan_chunks, (int)chunks, 1024, 0, stream, bsum, boff, nblocks,
-             (const unsigned long long*)chunk_tot, total, error, cap);
+                      int64_t cap, unsigned long long* lb, uint32_t* ticket, uint32_t spin_limit,
+                      cudaStream_t stream) {
+    const int64_t parts = scan_parts(nblocks);
+    launch_k(true, scan_sums, (int)(parts < 1 ? 1 : parts), 1024, 0, stream, bsum, boff, nblocks, total, error, cap,
+             lb, ticket, spin_limit);
 }
 
 __global__ void __launch_bounds__(kPrepThreads)
@@ -213,7 +172,8 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
     const uint32_t* bsum = reinterpret_cast<const uint32_t*>(ws + L.off_bsum);
     uint32_t* boff = reinterpret_cast<uint32_t*>(ws + L.off_boff);
     launch_scan_sums(bsum, boff, L.prep_blocks, &ctrl->num_keys, &ctrl->error, L.cap,
-                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_tot), stream);
+                     reinterpret_cast<unsigned long long*>(ws + L.off_scan_lb), &ctrl->scan_ticket[0], L.spin_limit,
+                     stream);
     if (n <= 0) return;
     duplicate_kernel<<<(int)L.prep_blocks, kPrepThreads, 0, stream>>>(
         reinterpret_cast<const uint32_t*>(ws + L.off_touched), reinterpret_cast<const uint4*>(ws + L.off_rect),

@@ -95,7 +95,10 @@ struct Layout {
     int64_t sort_parts = 0;
     size_t off_ctrl = 0, off_rec = 0, off_depth = 0, off_rect = 0, off_touched = 0;
     size_t off_bsum = 0, off_boff = 0;
-    size_t off_scan_tot = 0;   // kMaxScanChunks 64-bit chunk totals of the block-sum scans
+    // look-back words of a render's (at most two) block-sum scans: two slots of
+    // scan_parts(prep_blocks) 64-bit words each, in the cleared region
+    size_t off_scan_lb = 0;
+    int64_t scan_slot_words = 0;
     size_t off_keys[2] = {0, 0}, off_vals[2] = {0, 0};
     size_t off_hist = 0, off_lookback = 0, off_ranges = 0;
     // look-back words of the tile sort's passes: after the depth sort's, inside the cleared
@@ -132,7 +135,8 @@ struct Ctrl {
     uint32_t flags;                          // kFlagNoAdjoint: the render was a dynamic frame
     unsigned long long pair_tests;           // compositor statistics (collect_stats only)
     unsigned long long hits;
-    uint32_t reserved[40];
+    uint32_t scan_ticket[2];                 // chunk tickets of the render's block-sum scans
+    uint32_t reserved[38];
 };
 static_assert(sizeof(Ctrl) == 256, "ctrl block is 256 bytes");
 
@@ -320,13 +324,15 @@ void launch_scan_and_duplicate(const Layout& L, char* ws, int64_t n, cudaStream_
 typedef void (*StageMark)(int, cudaStream_t);
 void launch_sort(const Layout& L, char* ws, cudaStream_t stream, StageMark mark = nullptr, int mark_index = 0);
 void launch_ranges(const Layout& L, char* ws, cudaStream_t stream);
-// Exclusive scan of nblocks per-block sums into boff, the total into *total (a total above
-// cap sets kErrCapacity in *error if given). Beyond kScanChunk sums it takes one CTA per chunk
-// and needs chunk_tot (ceil(nblocks / kScanChunk) 64-bit words of scratch).
-constexpr int kScanChunk = 8192;
-constexpr int64_t kMaxScanChunks = 1024;   // 8.4 M blocks of 256: every slot count up to 2^31
+// Exclusive scan of nblocks per-block sums into boff, the total into *total, in one pass over
+// chunks of kScanPart sums (keys.cu). When cap > 0 a total above cap sets kErrCapacity in *error;
+// a look-back that gives up sets kErrTimeout there. lb: scan_parts(nblocks) zeroed 64-bit
+// look-back words; ticket: a zeroed counter (one of each per scan in a render).
+constexpr int kScanPart = 2048;
+inline int64_t scan_parts(int64_t nblocks) { return nblocks <= 0 ? 1 : (nblocks + kScanPart - 1) / kScanPart; }
 void launch_scan_sums(const uint32_t* bsum, uint32_t* boff, int64_t nblocks, uint32_t* total, uint32_t* error,
-                      int64_t cap, unsigned long long* chunk_tot, cudaStream_t stream);
+                      int64_t cap, unsigned long long* lb, uint32_t* ticket, uint32_t spin_limit,
+                      cudaStream_t stream);
 // Depth-first mode: compaction and depth sort (then mark(mark_index)), emission (then
 // mark(mark_index + 1)), tile counts or the tile histogram (then mark(mark_index + 2)), tile
 // passes. Beyond the counts-first grids the 32-bit tile sort runs; ranges for its keys:
