@@ -1,7 +1,8 @@
 // K5 -- tile compositor (section 3.2 Eqs. 2-3, front to back).
 //
-// One CTA per TILE x TILE tile; each thread owns PPT vertically adjacent pixels and
-// each warp an 8 x (4 PPT) pixel block. With PPT = 2 the two pixels are evaluated and
+// One CTA per SUB x SUB square of a TILE x TILE tile (the whole tile up to 16 pixels, a
+// quarter of a 32-pixel tile); each thread owns PPT vertically adjacent pixels and each warp
+// an 8 x (4 PPT) pixel block. With PPT = 2 the two pixels are evaluated and
 // composited together with packed f32x2 arithmetic (one instruction for both pixels' add,
 // multiply or FMA), rounded exactly as the one-pixel code, so the image does not depend on PPT.
 // The tile's range of the sorted (tile, depth, index) list is walked in chunks of
@@ -46,8 +47,8 @@ __device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& 
     P.last = pos1;
 }
 
-template <int TILE, int PPT, bool STATS, bool DEPTH, bool BATCH>
-__global__ void __launch_bounds__(TILE * TILE / PPT)
+template <int TILE, int SUB, int PPT, bool STATS, bool DEPTH, bool BATCH>
+__global__ void __launch_bounds__(SUB * SUB / PPT)
 composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                  const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0, float bg1,
                  float bg2, float alpha_min, float alpha_max, float t_stop, float qcut,
@@ -56,15 +57,19 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                  const float* __restrict__ depth, const float* __restrict__ zlim,
                  const BatchImage* __restrict__ images, int n_images, const uint32_t* __restrict__ order) {
     pdl_entry();
-    constexpr int NT = TILE * TILE / PPT;   // threads
+    // a CTA composites one SUB x SUB square of its TILE x TILE tile (the tile's whole list,
+    // each warp its own block of the square): NSUB CTAs per tile
+    static_assert(TILE % SUB == 0, "the squares tile the tile");
+    constexpr int NSUB = (TILE / SUB) * (TILE / SUB);
+    constexpr int NT = SUB * SUB / PPT;     // threads
     constexpr int NW = NT / 32;             // warps; each owns an 8 x (4 PPT) pixel block
-    constexpr int BX = TILE / 8;            // blocks per tile row
+    constexpr int BX = SUB / 8;             // blocks per row of the square
     constexpr int BH = 4 * PPT;             // block height in pixels
-    // splats staged per chunk: one per thread, up to 256 (512 for the 512 threads of a 32-pixel
-    // tile with two pixels per thread: half the chunk barriers, 3% faster there)
+    // splats staged per chunk: one per thread, up to 256 (512 for a 512-thread square of
+    // two pixels per thread: half the chunk barriers)
     constexpr int CHMAX = PPT == 2 ? 512 : 256;
     constexpr int CH = NT < CHMAX ? NT : CHMAX;
-    static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
+    static_assert(NW == BX * (SUB / BH), "warp blocks tile the square");
     // staged splats, NS float4 slots each: PPT 1 -> (du, dv, f1x, f1y), (f2x, f2y, thr, opacity),
     // (r, g, b, depth); PPT 2 -> the same values laid out as packed pairs for the f32x2
     // instructions (see the pair walk below)
@@ -74,7 +79,9 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     __shared__ uint16_t s_list[NW][CH];
     __shared__ float s_wmax[NW];   // DEPTH: largest depth limit of each warp block's live pixels
     // the tile's index in `ranges`: CTAs take the tiles longest first when an order is given
-    const uint32_t gtile = order ? order[blockIdx.x] : blockIdx.x;
+    const uint32_t gtile = order ? order[blockIdx.x / NSUB] : blockIdx.x / NSUB;
+    const int sub = (int)(blockIdx.x % NSUB);
+    const int sx = (sub % (TILE / SUB)) * SUB, sy = (sub / (TILE / SUB)) * SUB;   // the square in the tile
     int tile = (int)gtile;
     if (BATCH) {
         // a batch group's canvas (tiles_x tiles wide) stacks its images' tile rows: find this
@@ -95,7 +102,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bx = warp % BX, by = warp / BX;
-    const int col = bx * 8 + (lane & 7), row0 = by * BH + (lane >> 3) * PPT;
+    const int col = sx + bx * 8 + (lane & 7), row0 = sy + by * BH + (lane >> 3) * PPT;
     const int px = tx * TILE + col;
     const float half = 0.5f * TILE;
     const float xc = (float)(tx * TILE) + half, yc = (float)(ty * TILE) + half;
@@ -162,7 +169,7 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                 s_st[4][t] = make_float4(-s.c.x, -s.c.x, -s.c.y, -s.c.y);
                 s_st[5][t] = make_float4(-s.c.z, -s.c.z, 0.f, 0.f);
             }
-            uint32_t m = warp_block_mask<NW, BX, BH>(s, half);
+            uint32_t m = warp_block_mask<NW, BX, BH>(s, half, (float)sx, (float)sy);
             if (DEPTH) {
 #pragma unroll
                 for (int w = 0; w < NW; ++w)
@@ -283,6 +290,13 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
     }
 }
 
+// Edge of the square a compositor CTA covers: 16 pixels at most, so that a 32-pixel tile (whose
+// sort lists half the copies of 16-pixel tiles) is composited by four CTAs of four warps, each
+// walking the whole tile's list, instead of one CTA of sixteen warps (which fit two to an SM
+// and wait on each other at every chunk).
+constexpr int kCompositeSub = 16;
+constexpr int sub_of(int tile) { return tile < kCompositeSub ? tile : kCompositeSub; }
+
 void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2, float alpha_min,
                       float alpha_max, float t_stop, int ppt, bool stats, float* out_rgb, float* out_alpha,
                       const float* zlim, cudaStream_t stream) {
@@ -297,10 +311,12 @@ void launch_composite(const Layout& L, char* ws, float bg0, float bg1, float bg2
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
     const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
-#define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                \
-    launch_k(true, composite_kernel<TS, PP, ST, DT, false>, blocks, TS * TS / PP, 0, stream, ranges, vals, rec, L.W, \
-             L.H, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin,    \
-             last, depth, zlim, (const BatchImage*)nullptr, 0, order)
+    // a 32-pixel tile is composited by four CTAs of 16 x 16 pixels (kCompositeSub)
+#define VIS_LAUNCH_COMPOSITE_S(TS, PP, ST, DT)                                                                 \
+    launch_k(true, composite_kernel<TS, sub_of(TS), PP, ST, DT, false>, blocks * (TS / sub_of(TS)) * (TS / sub_of(TS)), \
+             sub_of(TS) * sub_of(TS) / PP, 0, stream, ranges, vals, rec, L.W, L.H, L.tiles_x, bg0, bg1, bg2,       \
+             alpha_min, alpha_max, t_stop, qcut, ctrl, out_rgb, out_alpha, tfin, last, depth, zlim,               \
+             (const BatchImage*)nullptr, 0, order)
 #define VIS_LAUNCH_COMPOSITE(TS, PP)                          \
     do {                                                      \
         if (zlim) VIS_LAUNCH_COMPOSITE_S(TS, PP, false, true);   \
@@ -327,10 +343,11 @@ void launch_composite_batch(const Layout& L, char* ws, const BatchImage* images,
     const float qcut = q_scale().qcut;
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
     const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
-#define VIS_LAUNCH_COMPOSITE_B(TS, PP)                                                                         \
-    launch_k(true, composite_kernel<TS, PP, false, false, true>, blocks, TS * TS / PP, 0, stream, ranges, vals, \
-             rec, 0, 0, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,      \
-             (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images, \
+#define VIS_LAUNCH_COMPOSITE_B(TS, PP)                                                                          \
+    launch_k(true, composite_kernel<TS, sub_of(TS), PP, false, false, true>,                                     \
+             blocks * (TS / sub_of(TS)) * (TS / sub_of(TS)), sub_of(TS) * sub_of(TS) / PP, 0, stream, ranges, vals, \
+             rec, 0, 0, L.tiles_x, bg0, bg1, bg2, alpha_min, alpha_max, t_stop, qcut, ctrl, (float*)nullptr,       \
+             (float*)nullptr, (float*)nullptr, (int32_t*)nullptr, depth, (const float*)nullptr, images, n_images,  \
              order)
     const bool two = ppt == 2;
     if (L.tile == 8) { if (two) VIS_LAUNCH_COMPOSITE_B(8, 2); else VIS_LAUNCH_COMPOSITE_B(8, 1); }

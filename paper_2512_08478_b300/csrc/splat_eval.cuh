@@ -40,10 +40,11 @@ __device__ __forceinline__ StagedSplat stage_splat(const float4* __restrict__ re
 // {d : q'(d) <= thr} and its oriented box, the two slabs |d.f_k| <= sqrt(thr) along the
 // whitening rows (q' = (d.f1)^2 + (d.f2)^2, so every point of the ellipse lies in both).
 // Both tests are padded for float rounding, so no block with such a pixel is dropped.
-// Blocks are 8 px wide and BH px tall, BX per tile row, NW in all; coordinates are
-// relative to the tile centre (half = TILE / 2).
+// Blocks are 8 px wide and BH px tall, BX per row of the CTA's square, NW in all; the square
+// starts at (ox, oy) pixels from the tile's corner (a CTA covering part of its tile);
+// coordinates are relative to the tile centre (half = TILE / 2).
 template <int NW, int BX, int BH>
-__device__ __forceinline__ uint32_t warp_block_mask(const StagedSplat& s, float half) {
+__device__ __forceinline__ uint32_t warp_block_mask(const StagedSplat& s, float half, float ox = 0.f, float oy = 0.f) {
     // half extents sqrt(thr (Q'^-1)_xx), sqrt(thr (Q'^-1)_yy) with Q' = F^T F, F = [f1; f2]
     const float det = fabsf(__fmaf_rn(s.a.z, s.b.y, -__fmul_rn(s.a.w, s.b.x)));
     const float rt = sqrtf(fmaxf(s.b.z, 0.f));
@@ -58,8 +59,8 @@ __device__ __forceinline__ uint32_t warp_block_mask(const StagedSplat& s, float 
     uint32_t m = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-        const float mx = (float)((w % BX) * 8) + 4.f - half;
-        const float my = (float)((w / BX) * BH) + 0.5f * BH - half;
+        const float mx = ox + (float)((w % BX) * 8) + 4.f - half;
+        const float my = oy + (float)((w / BX) * BH) + 0.5f * BH - half;
         const float dx = mx - s.a.x, dy = my - s.a.y;
         const float ox = fabsf(dx) - 3.5f, oy = fabsf(dy) - (0.5f * BH - 0.5f);
         const float p1 = fabsf(__fmaf_rn(dy, s.a.w, __fmul_rn(dx, s.a.z))) - e1;
