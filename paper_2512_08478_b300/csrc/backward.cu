@@ -62,8 +62,8 @@ __device__ __forceinline__ void warp_add_gradients(const float g[9], int lane, f
     if (lane == 1 && t9 != 0.f) atomicAdd(dst + 8, t9);
 }
 
-template <int TILE, int PPT, bool DEPTH>
-__global__ void __launch_bounds__(TILE * TILE / PPT)
+template <int TILE, int SUB, int PPT, bool DEPTH>
+__global__ void __launch_bounds__(SUB * SUB / PPT)
 composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                           const float4* __restrict__ rec, int W, int H, int tiles_x, float bg0,
                           float bg1, float bg2, float alpha_min, float alpha_max, float qcut, float inv_scale,
@@ -77,22 +77,27 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
         return;
     }
     if (ctrl->error) return;   // the forward produced no valid lists: leave the gradients at zero
-    constexpr int NT = TILE * TILE / PPT;     // threads; each owns PPT vertically adjacent pixels
+    // a CTA takes one SUB x SUB square of its tile (the whole tile's list), as the forward does
+    static_assert(TILE % SUB == 0, "the squares tile the tile");
+    constexpr int NSUB = (TILE / SUB) * (TILE / SUB);
+    constexpr int NT = SUB * SUB / PPT;       // threads; each owns PPT vertically adjacent pixels
     constexpr int NW = NT / 32;               // warps; each owns an 8 x (4 PPT) pixel block
-    constexpr int BX = TILE / 8, BH = 4 * PPT;
+    constexpr int BX = SUB / 8, BH = 4 * PPT;
     constexpr int CH = NT < 256 ? NT : 256;   // splats staged per chunk
-    static_assert(NW == BX * (TILE / BH), "warp blocks tile the tile");
+    static_assert(NW == BX * (SUB / BH), "warp blocks tile the square");
     // staged splats, NS float4 slots each: PPT 1 -> (du, dv, f1x, f1y), (f2x, f2y, thr, opacity),
     // (r, g, b, depth); PPT 2 -> packed pairs for the f32x2 instructions (see the pair walk)
     constexpr int NS = PPT == 1 ? 3 : 6;
     __shared__ float4 s_st[NS][CH];
     __shared__ uint32_t s_g[CH], s_mask[CH];
     __shared__ uint16_t s_list[NW][CH];
-    const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;   // longest tiles first if ordered
+    const int tile = order ? (int)order[blockIdx.x / NSUB] : (int)(blockIdx.x / NSUB);   // longest first if ordered
+    const int sub = (int)(blockIdx.x % NSUB);
+    const int sx = (sub % (TILE / SUB)) * SUB, sy = (sub / (TILE / SUB)) * SUB;   // the square in the tile
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int bx = warp % BX, by = warp / BX;
-    const int px = tx * TILE + bx * 8 + (lane & 7);
+    const int px = tx * TILE + sx + bx * 8 + (lane & 7);
     const size_t HW = (size_t)H * W;
     const float half = 0.5f * TILE;
     const float xc = (float)(tx * TILE) + half, yc = (float)(ty * TILE) + half;
@@ -108,7 +113,7 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
     int32_t my_last = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-        const int py = ty * TILE + by * BH + (lane >> 3) * PPT + q;
+        const int py = ty * TILE + sy + by * BH + (lane >> 3) * PPT + q;
         inside[q] = px < W && py < H;
         const size_t pix = (size_t)py * W + px;
         ly[q] = (float)py + 0.5f - yc;
@@ -156,7 +161,7 @@ composite_backward_kernel(const uint2* __restrict__ ranges, const uint32_t* __re
                 s_st[4][t] = make_float4(st.c.x, st.c.x, st.c.y, st.c.y);
                 s_st[5][t] = make_float4(st.c.z, st.c.z, 0.f, 0.f);
             }
-            s_mask[t] = warp_block_mask<NW, BX, BH>(st, half);
+            s_mask[t] = warp_block_mask<NW, BX, BH>(st, half, (float)sx, (float)sy);
         }
         __syncthreads();
         // this warp's list of splats whose 3-sigma box meets its block, in depth order
@@ -524,10 +529,12 @@ void launch_composite_backward(const Layout& L, char* ws, const float bg[3], flo
     const float* depth = reinterpret_cast<const float*>(ws + L.off_depth);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.off_ctrl);
     const uint32_t* order = L.tile_fused ? reinterpret_cast<const uint32_t*>(ws + L.off_order) : nullptr;
-#define VIS_LAUNCH_BWD_D(TS, PP, DT)                                                                       \
-    composite_backward_kernel<TS, PP, DT><<<blocks, TS * TS / PP, 0, stream>>>(                            \
-        ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut,        \
-        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl, order)
+    // 16 x 16 squares at most per CTA, as the forward compositor
+#define VIS_LAUNCH_BWD_D(TS, PP, DT)                                                                           \
+    composite_backward_kernel<TS, (TS < 16 ? TS : 16), PP, DT>                                                 \
+        <<<blocks * (TS / (TS < 16 ? TS : 16)) * (TS / (TS < 16 ? TS : 16)), (TS < 16 ? TS : 16) * (TS < 16 ? TS : 16) / PP, \
+           0, stream>>>(ranges, vals, rec, L.W, L.H, L.tiles_x, bg[0], bg[1], bg[2], alpha_min, alpha_max, qs.qcut, \
+                        qs.inv_scale, tfin, last, d_rgb, d_alpha, g2, depth, zlim, ctrl, order)
 #define VIS_LAUNCH_BWD(TS, PP)                       \
     do {                                             \
         if (zlim) VIS_LAUNCH_BWD_D(TS, PP, true);    \
