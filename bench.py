@@ -454,14 +454,12 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
 
     # kernels per frame: preprocess, (mode 1) block-sum scan, compaction, depth histogram,
     # depth passes, touch sums, scan, emission, tile counts, tile scan, tile look-back clear,
-    # tile passes / (mode 0) scan, duplication, histogram, passes, ranges; the compositor; a
-    # block-sum scan over more than 8192 blocks takes two kernels; the backward adds the
-    # compositor's adjoint and the preprocess adjoint; a depth buffer its per-tile maximum
+    # tile passes / (mode 0) scan, duplication, histogram, passes, ranges; the compositor; the
+    # backward adds the compositor's adjoint and the preprocess adjoint; a depth buffer its
+    # per-tile maximum
     depth_passes = {8: 4, 10: 4, 11: 3}[args.digit_bits]
-    scan_k = 2 if (n + 255) // 256 > 8192 else 1
     fused_tiles = lay.key_bytes == 2
-    launches = {0: 5 + scan_k + passes,
-                1: 6 + 2 * scan_k + depth_passes + passes + (3 if fused_tiles else 2)}[sort_mode] + \
+    launches = {0: 6 + passes, 1: 8 + depth_passes + passes + (3 if fused_tiles else 2)}[sort_mode] + \
         (2 if fwdbwd else 0) + (1 if dbuf is not None else 0)
     line = dict(metric=METRIC, value=round(value, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(t_ms / args.steps, 4), higher_is_better=False,
