@@ -707,7 +707,10 @@ def run_multi(args):
                 merged_scene_ms=round(t_single, 4),
                 merged_note="the same Gaussians as one plain scene, SH zero-padded to degree 3",
                 stage_ms=stage_ms, keys_per_frame=int(keys), gaussians_per_s=round(n_total / t_multi * 1e3, 1),
-                gpu_launches=int(args.steps * (len(scenes) + 9 + 4 + npass.value)), clocks=clk.summary())
+                # per frame: a preprocess per model, then the depth-first frame's kernels (scan,
+                # compaction, histogram, four depth passes, touch sums, scan, emission, tile
+                # counts, tile scan, tile look-back clear, tile passes, compositor)
+                gpu_launches=int(args.steps * (len(scenes) + 10 + 4 + npass.value)), clocks=clk.summary())
     if rank == 0:
         print(json.dumps(line), flush=True)
 
