@@ -106,7 +106,8 @@ typedef struct {
  *              top and bottom rows narrowed to the tiles whose band of pixel centres meets
  *              that region. The image does not depend on it; 1 lists ~40% fewer (tile,
  *              splat) pairs than 0, and 2 ~12% fewer than 1.
- *  spin_limit  how many times a sort partition may poll a predecessor's unpublished
+ *  spin_limit  how many times a sort partition (or a chunk of a block-sum scan, or a group
+ *              of a partition's look-back) may poll a predecessor's unpublished
  *              look-back word before it gives up (0 = the default, 4194304; at most
  *              2^30). A wait that runs out records VIS_ERR_TIMEOUT in the workspace
  *              (returned by vis_check), publishes its own counts so that no other
