@@ -182,15 +182,18 @@ def _kernel_sha(files):
     return h.hexdigest()[:16]
 
 
-def _committed_traffic(stage, M, n):
+def _committed_traffic(stage, M, n, tile=None):
     """DRAM bytes (read + write) per launch of the stage's kernel from a committed ncu capture
-    (profiles/traffic.json), scaled to this launch by keys or Gaussians; None if absent or if
-    the kernel's source changed since the capture (the entry records the sources' hash)."""
+    (profiles/traffic.json), scaled to this launch by keys or Gaussians; None if absent, if
+    the kernel's source changed since the capture (the entry records the sources' hash), or
+    if the capture's tile size (when it records one) is not this launch's."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
         return None
     d = json.loads(p.read_text()).get(stage)
     if not d or "sources" not in d or d.get("source_sha") != _kernel_sha(d["sources"]):
+        return None
+    if tile is not None and d.get("tile") is not None and int(d["tile"]) != int(tile):
         return None
     if "bytes_per_key" in d:
         return int(d["bytes_per_key"] * M)
@@ -428,7 +431,7 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         hb = M * (4 + 48) + W * H * (16 + 8)
         roof = dict(kernel="composite", bound="alu", achieved=round(ach_t, 3), peak=round(peak_t, 2),
                     unit="T FP32 lane-instructions/s", frac=round(ach_t / peak_t, 4),
-                    traffic=_committed_traffic("composite", M, n),
+                    traffic=_committed_traffic("composite", M, n, tile),
                     peak_source=f"{n_sm} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled clock)",
                     algorithmic_instructions_per_launch=int(inst), pair_tests=ctrl["pair_tests"],
                     hits=ctrl["hits"], launch_ms=round(stage_ms["composite"], 4),
@@ -442,7 +445,8 @@ def measure(args, workload, with_e2e=True, with_cpu=True, dist=None):
         h = hbm_stages[dom]
         roof = dict(kernel=dom, bound="hbm", achieved=h["achieved_gbs"], peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=h["frac"],
-                    traffic=_committed_traffic("preprocess_dynamic" if (dom == "preprocess" and dynamic) else dom, M, n),
+                    traffic=_committed_traffic("preprocess_dynamic" if (dom == "preprocess" and dynamic) else dom, M, n,
+                                               tile),
                     peak_source=peaks["source"],
                     algorithmic_bytes_per_launch=h["bytes"], launch_ms=h["ms"], bytes_model=h["bytes_model"])
 
