@@ -31,6 +31,7 @@ cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -127,6 +128,12 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        # The garbage collector is held off while the timed work is enqueued: a full
+        # collection in the middle of the launch loop stalls the host for milliseconds, long
+        # enough for the GPU to run out of queued frames.
+        gc.collect()
+        self.gc_was_enabled = gc.isenabled()
+        gc.disable()
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -142,6 +149,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        if self.gc_was_enabled:
+            gc.enable()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -770,6 +779,9 @@ def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    gc.collect()
+    gc_was_enabled = gc.isenabled()
+    gc.disable()   # no collection pause inside the timed steps (as in the device-timed regions)
     e0.record(stream)
     up.wait_event(e0)
     down.wait_event(e0)
@@ -779,6 +791,8 @@ def run_e2e(args, vis, torch, sc_np, cam_objs, W, H, cap, dist, opts):
     stream.wait_event(read[steps & 1])
     e1.record(stream)
     torch.cuda.synchronize()
+    if gc_was_enabled:
+        gc.enable()
     vis.vis_check(ws.buf)
     t = e0.elapsed_time(e1)
     world = 1

@@ -34,12 +34,14 @@ struct PixAcc {
 };
 
 // Composite one staged splat into one pixel; returns false when the pixel stops.
+// The colour weight alpha T of Eq. 3 is taken as the drop in transmittance, T - T (1 - alpha):
+// the same quantity, and the weights of a pixel then add up to 1 - T to within one rounding each.
 __device__ __forceinline__ void composite_hit(PixAcc& P, float q, const float4& b, const float4& c, float alpha_max,
                                               float t_stop, int32_t pos1) {
     const float alpha = fminf(alpha_max, __fmul_rn(b.w, gauss_of_qs(q)));
     const float Tn = __fmul_rn(P.T, __fsub_rn(1.f, alpha));
     if (Tn < t_stop) { P.done = true; return; }
-    const float w = __fmul_rn(alpha, P.T);
+    const float w = __fsub_rn(P.T, Tn);
     P.C0 = __fmaf_rn(c.x, w, P.C0);
     P.C1 = __fmaf_rn(c.y, w, P.C1);
     P.C2 = __fmaf_rn(c.z, w, P.C2);
@@ -220,6 +222,8 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
             // The update is branch-free: a pixel that does not take the splat gets w = 0 and
             // keeps T. The warp walks its list together and leaves once none of its pixels is live.
             bool live0 = !P[0].done, live1 = !P[PPT - 1].done;
+            int lk0 = -1, lk1 = -1;   // chunk slot of each pixel's last composited splat
+            const float2 mone2 = make_float2(-1.f, -1.f);
             for (int i = 0; i < nlist; ++i) {
                 const int k = s_list[warp][i];
                 const float4 q0 = s_st[0][k], q1 = s_st[1][k], q2 = s_st[2][k], q3 = s_st[3][k];
@@ -239,20 +243,24 @@ composite_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ 
                 const float2 Tn = __fmul2_rn(T2, __fadd2_rn(one2, na));
                 const bool s0 = h0 && Tn.x < t_stop, s1 = h1 && Tn.y < t_stop;   // stops, splat excluded
                 const bool c0 = h0 && !s0, c1 = h1 && !s1;                       // composited
-                const float2 nw = __fmul2_rn(make_float2(c0 ? na.x : 0.f, c1 ? na.y : 0.f), T2);   // -alpha T
+                const float2 T2n = make_float2(c0 ? Tn.x : T2.x, c1 ? Tn.y : T2.y);
+                // -(T - T'): the negated weight of the one-pixel code (one rounding, exact
+                // negation), and +0 for a pixel that keeps T
+                const float2 nw = __ffma2_rn(T2, mone2, T2n);
                 const float4 k0 = s_st[4][k], k1 = s_st[5][k];
                 Cr = __ffma2_rn(make_float2(k0.x, k0.y), nw, Cr);
                 Cg = __ffma2_rn(make_float2(k0.z, k0.w), nw, Cg);
                 Cb = __ffma2_rn(make_float2(k1.x, k1.y), nw, Cb);
-                T2 = make_float2(c0 ? Tn.x : T2.x, c1 ? Tn.y : T2.y);
-                const int32_t pos1 = (int32_t)(base + k + 1);
-                if (c0) P[0].last = pos1;
-                if (c1) P[PPT - 1].last = pos1;
+                T2 = T2n;
+                if (c0) lk0 = k;
+                if (c1) lk1 = k;
                 if (STATS) n_hits += (c0 ? 1 : 0) + (c1 ? 1 : 0);
                 live0 = live0 && !s0;
                 live1 = live1 && !s1;
                 if (!__any_sync(0xffffffffu, live0 || live1)) break;
             }
+            if (lk0 >= 0) P[0].last = (int32_t)(base + lk0 + 1);
+            if (lk1 >= 0) P[PPT - 1].last = (int32_t)(base + lk1 + 1);
             P[0].done = !live0;
             P[PPT - 1].done = !live1;
         }
