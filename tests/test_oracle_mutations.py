@@ -1,0 +1,187 @@
+"""Planted mistakes in the oracle must turn its pins red.
+
+The oracle is trusted because tests pin it to something other than itself: closed forms,
+invariants, brute force on tiny inputs, central differences. This file checks that those
+pins would notice a plausible mistake. Each case copies oracle/oracle.c and plants one
+mistake: a dropped term, a flipped sign, a transposed operand, a comparison made strict at
+equality, or a branch that lets a gradient through. It then compiles the copy and runs the
+oracle's pin suites against it in a child process. ORACLE_LIB points the oracle package at
+the copy. The pins hold when every planted copy fails at least one of them, and the
+unchanged copy passes them all.
+
+The golden fixture is left out of the child runs. It is the oracle's own output, so it is a
+regression check rather than a pin.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+SRC = ROOT / "oracle" / "oracle.c"
+PIN_SUITES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint_fd.py", "tests/test_oracle_multi.py",
+              "tests/test_oracle_prepack.py"]
+
+# name -> (passage the mistake contradicts, [(text in oracle.c, replacement, occurrences)])
+MUTATIONS = {
+    "sh_condon_shortley_phase_dropped": (
+        "section 3.2 colour: real SH with the Condon-Shortley phase",
+        [("double sgn = (am % 2) ? -1.0 : 1.0;", "double sgn = 1.0;", 1)]),
+    "dilation_on_one_axis": (
+        "Eq. 1 with the low-pass dilation S + 0.3 I",
+        [("double s00 = S2[0] + op->dilation, s01 = S2[1], s11 = S2[3] + op->dilation;",
+          "double s00 = S2[0] + op->dilation, s01 = S2[1], s11 = S2[3];", 1)]),
+    "conic_off_diagonal_sign": (
+        "Eq. 2: the conic is the inverse of the 2D covariance",
+        [("out->conic[3 * i + 1] = -s01 / det;", "out->conic[3 * i + 1] = s01 / det;", 1)]),
+    "ewa_jacobian_sign": (
+        "Eq. 1: J is the Jacobian of the perspective projection",
+        [("double J[6] = {cam->fx / z, 0.0, -cam->fx * rx / z,", "double J[6] = {cam->fx / z, 0.0, cam->fx * rx / z,", 2)]),
+    "quaternion_rotation_transposed": (
+        "Algorithm 1, CovFromScaleRot: R from the unit quaternion",
+        [("R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);",
+          "R[1] = 2 * (x * y + w * z);     R[2] = 2 * (x * z - w * y);", 1),
+         ("R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);",
+          "R[3] = 2 * (x * y - w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z + w * x);", 1),
+         ("R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);",
+          "R[6] = 2 * (x * z + w * y);     R[7] = 2 * (y * z - w * x);", 1)]),
+    "camera_centre_sign": (
+        "section 3.2 colour: the view direction from the camera centre -R^T t",
+        [("c[j] = -(cam->R[0 * 3 + j] * cam->t[0]", "c[j] = (cam->R[0 * 3 + j] * cam->t[0]", 1)]),
+    "opacity_sigmoid_sign": (
+        "section 3.2: opacity = sigmoid(logit)",
+        [("return 1.0 / (1.0 + exp(-(double)sc->logits[i]));", "return 1.0 / (1.0 + exp((double)sc->logits[i]));", 1)]),
+    "no_jacobian_guard": (
+        "Eq. 1 with x/z, y/z clamped to 1.3 tan(half FOV)",
+        [("double limx = 1.3 * (cam->W / (2.0 * cam->fx)), limy = 1.3 * (cam->H / (2.0 * cam->fy));",
+          "double limx = 1e300, limy = 1e300;", 2)]),
+    "no_opacity_cull": (
+        "Algorithm 1 culling: opacity below 1/255",
+        [("if (o < op->alpha_min) return;", "", 1)]),
+    "opacity_cull_strict_at_equality": (
+        "Algorithm 1 culling: opacity below 1/255 (equality kept)",
+        [("if (o < op->alpha_min) return;", "if (o <= op->alpha_min) return;", 1)]),
+    "extent_two_sigma": (
+        "Algorithm 1: the 3-sigma screen extent",
+        [("int rad = (int)ceil(3.0 * sqrt(lam));", "int rad = (int)ceil(2.0 * sqrt(lam));", 1)]),
+    "no_alpha_clamp": (
+        "Eq. 3 with alpha = min(0.99, o G)",
+        [("if (alpha > op->alpha_max) alpha = op->alpha_max;", "", 1)]),
+    "alpha_min_strict_at_equality": (
+        "Eq. 3: splats with alpha below 1/255 are skipped (equality kept)",
+        [("if (alpha < op->alpha_min) continue;", "if (alpha <= op->alpha_min) continue;", 1)]),
+    "depth_test_strict_at_equality": (
+        "section 3.4: the depth test against the opaque geometry (equal depth passes)",
+        [("if (z > zlim) continue;", "if (z >= zlim) continue;", 1)]),
+    "stopping_splat_composited": (
+        "Eq. 3 with early termination before T would fall below 1e-4",
+        [("if (Tn < op->t_stop) break;",
+          "if (Tn < op->t_stop) { for (int ch = 0; ch < 3; ++ch) C[ch] += pp->rgb[3 * i + ch] * alpha * T; "
+          "T = Tn; ++n_contrib; last_pos = (int)(j + 1); break; }", 1)]),
+    "depth_tie_break_reversed": (
+        "Algorithm 1's depth sort, equal depths in index order",
+        [("return (x->idx < y->idx) ? -1 : (x->idx > y->idx);", "return (x->idx > y->idx) ? -1 : (x->idx < y->idx);", 1)]),
+    "colour_clamp_dropped": (
+        "section 3.2 colour: max(0, SH sum + 0.5)",
+        [("out->rgb[3 * i + ch] = acc < 0 ? 0.0 : acc;", "out->rgb[3 * i + ch] = acc;", 1),
+         ("if (acc < 0) continue;   /* clamped channel: no gradient */", "", 1)]),
+    "colour_clamp_dropped_in_forward": (
+        "section 3.2 colour: max(0, SH sum + 0.5)",
+        [("out->rgb[3 * i + ch] = acc < 0 ? 0.0 : acc;", "out->rgb[3 * i + ch] = acc;", 1)]),
+    "colour_clamp_dropped_in_adjoint": (
+        "section 3.2 colour: a clamped channel passes no gradient",
+        [("if (acc < 0) continue;   /* clamped channel: no gradient */", "", 1)]),
+    "adjoint_alpha_clamp_passes_gradient": (
+        "Eq. 3: a clamped alpha does not depend on the splat's parameters",
+        [("if (cl[k].clamped) continue;", "", 1)]),
+    "adjoint_jacobian_guard_passes_gradient": (
+        "Eq. 1: a clamped x/z or y/z does not depend on the mean",
+        [("if (!clx) {", "if (1) {", 1), ("if (!cly) {", "if (1) {", 1)]),
+    "world_covariance_not_transposed": (
+        "Algorithm 1, model transforms: Sigma_w = A Sigma A^T",
+        [("Sw[r * 3 + c] = AS[r * 3 + 0] * sc->A[c * 3 + 0] + AS[r * 3 + 1] * sc->A[c * 3 + 1] +\n"
+          "                            AS[r * 3 + 2] * sc->A[c * 3 + 2];",
+          "Sw[r * 3 + c] = AS[r * 3 + 0] * sc->A[0 * 3 + c] + AS[r * 3 + 1] * sc->A[1 * 3 + c] +\n"
+          "                            AS[r * 3 + 2] * sc->A[2 * 3 + c];", 1)]),
+    "sh_ray_in_the_world_frame": (
+        "Algorithm 1, model transforms: the colour is evaluated in the model's own frame",
+        [("    if (!sc->has_model) { d[0] = w[0]; d[1] = w[1]; d[2] = w[2]; return; }",
+          "    if (1) { d[0] = w[0]; d[1] = w[1]; d[2] = w[2]; return; }", 1)]),
+    "conic_cross_term_factor_dropped": (
+        "Eq. 2: q = d^T S^-1 d, whose cross term counts the off-diagonal twice",
+        [("double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;",
+          "double q = a * dx * dx + b * dx * dy + c * dy * dy;", 1)]),
+    "extent_smaller_eigenvalue": (
+        "Algorithm 1: the extent from the larger eigenvalue of the 2D covariance",
+        [("double lam = m + sqrt(disc);", "double lam = m - sqrt(disc);", 1)]),
+    "sh_coefficient_index_mirrored": (
+        "section 3.2 colour: coefficient index l*l+l+m",
+        [("int k = l * l + l + m;", "int k = l * l + l - m;", 1)]),
+    "near_plane_strict_at_equality": (
+        "Algorithm 1 culling: depth at or in front of the near plane",
+        [("if (!(z > cam->near_z)) return;", "if (!(z >= cam->near_z)) return;", 1)]),
+    "transmittance_not_updated": (
+        "Eq. 3: T_i is the product of (1 - alpha_j) over the splats in front",
+        [("        T = Tn;\n        ++n_contrib;", "        ++n_contrib;", 1)]),
+    "background_weight_dropped": (
+        "Eq. 3 over a background: C + T_final bg",
+        [("out->rgb[ch] = C[ch] + T * bg[ch];", "out->rgb[ch] = C[ch] + bg[ch];", 1)]),
+    "adjoint_sigmoid_derivative": (
+        "section 3.2: d sigmoid / d logit = o (1 - o)",
+        [("d_logits[i] = go * o * (1.0 - o);", "d_logits[i] = go * o;", 1)]),
+    "model_adjoint_left_factor_dropped": (
+        "Algorithm 1, model transforms: dL/dSigma = A^T (dL/dSigma_w) A",
+        [("acc += sc->A[r * 3 + a] * gSigw[r * 3 + c] * sc->A[c * 3 + b];",
+          "acc += (double)(r == a) * gSigw[r * 3 + c] * sc->A[c * 3 + b];", 1)]),
+}
+
+
+def _planted(name):
+    """oracle.c with the named mistake planted (None: unchanged)."""
+    src = SRC.read_text()
+    if name is None:
+        return src
+    for old, new, count in MUTATIONS[name][1]:
+        found = src.count(old)
+        assert found == count, f"{name}: {old!r} occurs {found} times in oracle.c, expected {count}"
+        src = src.replace(old, new)
+    return src
+
+
+def _run_pins(name, workdir):
+    """Compile the planted copy and run the pin suites on it; returns (exit code, output tail)."""
+    tag = name or "unchanged"
+    c_file = workdir / f"{tag}.c"
+    lib = workdir / f"lib{tag}.so"
+    c_file.write_text(_planted(name))
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", str(lib), str(c_file), "-lm"],
+                   check=True, capture_output=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_SUITES, "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, (r.stdout + r.stderr)[-600:]
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    names = [None] + list(MUTATIONS)
+    for name in names[1:]:
+        _planted(name)   # each planted text is found where expected before anything runs
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as pool:
+        results = dict(zip(names, pool.map(lambda n: _run_pins(n, tmp_path), names)))
+    code, tail = results.pop(None)
+    assert code == 0, f"the unchanged copy fails its pins:\n{tail}"
+    survivors = {n: t for n, (c, t) in results.items() if c == 0}
+    broken = {n: (c, t) for n, (c, t) in results.items() if c not in (0, 1)}
+    assert not broken, "children that did not run their tests: " + "; ".join(
+        f"{n} (exit {c}): {t[-200:]}" for n, (c, t) in broken.items())
+    assert not survivors, "planted mistakes that no pin catches: " + ", ".join(
+        f"{n} ({MUTATIONS[n][0]})" for n in survivors)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_text_is_in_the_oracle(name):
+    _planted(name)

@@ -374,6 +374,51 @@ def test_ewa_jacobian_matches_numerical_derivative_of_projection():
     np.testing.assert_allclose(prep["S"][0], [expect[0, 0], expect[0, 1], expect[1, 1]], rtol=1e-6)
 
 
+def test_tilted_anisotropic_gaussian_alpha_closed_form():
+    """Eqs. 1-2 for a splat whose screen ellipse is tilted: at every pixel the alpha is
+    min(0.99, o exp(-d^T S^-1 d / 2)), S = J Sigma J^T + dilation I. Here J is the numerical
+    Jacobian of the projection, Sigma = R diag(s^2) R^T with R from scipy's quaternion
+    rotation, and S^-1 comes from numpy, so the conic's off-diagonal term and the factor 2 of
+    its cross term both enter the comparison."""
+    from scipy.spatial.transform import Rotation
+    W, H = 96, 80
+    cam = synth.look_at((0.7, -0.4, 5.0), (0, 0, 0), W, H, 50.0)
+    mu = np.array([0.15, -0.1, 0.2])
+    s = np.array([0.3, 0.06, 0.15])
+    q = np.array([0.8, 0.2, -0.3, 0.4])            # (w, x, y, z)
+    logit = 2.0
+    sc = dict(means=mu[None], log_scales=np.log(s)[None], quats=q[None], opacity_logits=np.array([logit]),
+              sh=np.zeros((1, 1, 3)), sh_degree=0)
+    prep = oracle.preprocess(sc, cam)
+    assert prep["valid"][0] == 1
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    s_eff = np.exp(np.log(s))
+    Sig = R @ np.diag(s_eff ** 2) @ R.T
+    h = 1e-6
+    Jn = np.zeros((2, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        Jn[:, k] = (_project(cam, (mu + e)[None])[0] - _project(cam, (mu - e)[None])[0]) / (2 * h)
+    S = Jn @ Sig @ Jn.T + DIL * np.eye(2)
+    assert abs(S[0, 1]) > 0.2 * math.sqrt(S[0, 0] * S[1, 1])   # the ellipse is tilted
+    Sinv = np.linalg.inv(S)
+    uv = _project(cam, mu[None])[0]
+    ys, xs = np.mgrid[0:H, 0:W]
+    d = np.stack([xs + 0.5 - uv[0], ys + 0.5 - uv[1]], -1)
+    qq = np.einsum("...i,ij,...j->...", d, Sinv, d)
+    o = 1 / (1 + math.exp(-logit))
+    raw = o * np.exp(-0.5 * qq)
+    a = np.minimum(float(np.float32(0.99)), raw)
+    amin = float(np.float32(1 / 255))
+    a = np.where((qq <= 9.0) & (a >= amin), a, 0.0)
+    # decisions within rounding of a threshold are left out (both outcomes are correct there)
+    clear = (np.abs(qq - 9.0) > 1e-6) & (np.abs(raw - amin) > 1e-9)
+    got = oracle.render_bruteforce(prep, W, H)["alpha"]
+    assert (a > 0).sum() > 100
+    np.testing.assert_allclose(got[clear], a[clear], atol=1e-8)
+
+
 # ---------------------------------------------------------------------------------
 # Sort-stage oracles (brute force)
 # ---------------------------------------------------------------------------------
@@ -507,6 +552,25 @@ def test_thresholds_at_equality():
     below = np.nextafter(np.float32(z), np.float32(-np.inf))
     wall, _ = oracle.render(sc2, cam, bg, depth=np.full((H, W), below, np.float32))
     assert np.all(wall["alpha"] == 0.0)
+
+
+def test_near_plane_at_equality():
+    """Reading S6 at equality: a Gaussian whose view depth equals the near plane is culled
+    (z <= near), and one a double-precision step beyond it is kept. The camera looks down the
+    axis from (0, 0, 4) with an exact rotation (entries 0 and +-1), so a mean on the axis at
+    world z = 4 - near has view depth near exactly."""
+    cam = synth.look_at((0, 0, 4.0), (0, 0, 0), 33, 33, 60.0)
+    assert np.array_equal(cam.R[2], [0, 0, -1]) and cam.t[2] == 4.0
+    near = float(np.float32(cam.near))   # the near plane as the library receives it
+    on = 4.0 - near
+    beyond = np.nextafter(on, -np.inf)
+    for zw, depth_ok in ((on, False), (beyond, True)):
+        sc = dict(means=np.array([[0.0, 0.0, zw]]), log_scales=np.log(np.full((1, 3), 0.01)),
+                  quats=np.array([[1.0, 0, 0, 0]]), opacity_logits=np.array([2.0]), sh=np.zeros((1, 1, 3)),
+                  sh_degree=0)
+        prep = oracle.preprocess(sc, cam)
+        assert (prep["z"][0] > near) == depth_ok and (prep["z"][0] == near) != depth_ok
+        assert prep["valid"][0] == (1 if depth_ok else 0)
 
 
 def test_negative_colour_sum_renders_black_closed_form():
