@@ -132,6 +132,19 @@ MUTATIONS = {
     "adjoint_sigmoid_derivative": (
         "section 3.2: d sigmoid / d logit = o (1 - o)",
         [("d_logits[i] = go * o * (1.0 - o);", "d_logits[i] = go * o;", 1)]),
+    "duplicate_tile_id_transposed": (
+        "Algorithm 1's key duplication: row-major tile id ty * tiles_x + tx",
+        [("uint64_t tile = (uint64_t)ty * (uint64_t)tiles_x + (uint64_t)tx;",
+          "uint64_t tile = (uint64_t)tx * (uint64_t)tiles_x + (uint64_t)ty;", 1)]),
+    "duplicate_depth_bits_dropped": (
+        "Algorithm 1's key: the tile id above the depth bits",
+        [("keys[m] = (tile << 32) | (uint64_t)zb;", "keys[m] = (tile << 32);", 1)]),
+    "stable_sort_ties_reversed": (
+        "Algorithm 1's sort: equal keys keep their input order",
+        [("return (x->pos < y->pos) ? -1 : (x->pos > y->pos);", "return (x->pos > y->pos) ? -1 : (x->pos < y->pos);", 1)]),
+    "tile_range_end_inclusive": (
+        "Algorithm 1: a tile's range [start, end) of the sorted keys",
+        [("ranges[2 * t + 1] = (uint32_t)e;", "ranges[2 * t + 1] = (uint32_t)(e - 1);", 1)]),
     "model_adjoint_left_factor_dropped": (
         "Algorithm 1, model transforms: dL/dSigma = A^T (dL/dSigma_w) A",
         [("acc += sc->A[r * 3 + a] * gSigw[r * 3 + c] * sc->A[c * 3 + b];",
