@@ -145,6 +145,18 @@ MUTATIONS = {
     "tile_range_end_inclusive": (
         "Algorithm 1: a tile's range [start, end) of the sorted keys",
         [("ranges[2 * t + 1] = (uint32_t)e;", "ranges[2 * t + 1] = (uint32_t)(e - 1);", 1)]),
+    "ambiguity_flag_of_the_stop_dropped": (
+        "Eq. 3's early stop: a T (1 - alpha) within rounding of 1e-4 is flagged",
+        [("if (fabs(Tn - op->t_stop) <= AMB_T_REL * op->t_stop) amb = 1;", "", 1)]),
+    "ambiguity_flag_of_alpha_min_dropped": (
+        "Eq. 3's alpha_min skip: an alpha within rounding of 1/255 is flagged",
+        [("if (fabs(alpha - op->alpha_min) <= AMB_ALPHA_REL * op->alpha_min) amb = 1;", "", 1)]),
+    "ambiguity_flag_of_the_cut_dropped": (
+        "the 3-sigma cut: a q within rounding of 9 is flagged",
+        [("if (pp->opacity[i] * exp(-0.5 * q) >= op->alpha_min * (1.0 - AMB_ALPHA_REL)) amb = 1;", "", 1)]),
+    "ambiguity_flag_of_the_depth_test_dropped": (
+        "section 3.4's depth test: a depth within rounding of the buffer's is flagged",
+        [("if (isfinite(zlim) && fabs(z - zlim) <= AMB_Z_REL * fabs(zlim)) amb = 1;", "", 1)]),
     "model_adjoint_left_factor_dropped": (
         "Algorithm 1, model transforms: dL/dSigma = A^T (dL/dSigma_w) A",
         [("acc += sc->A[r * 3 + a] * gSigw[r * 3 + c] * sc->A[c * 3 + b];",

@@ -554,6 +554,54 @@ def test_thresholds_at_equality():
     assert np.all(wall["alpha"] == 0.0)
 
 
+def _axis_splats(opacities, depths_world, screen_var, cam):
+    """Pre-packed isotropic splats on the optical axis (world z given), each with the given
+    screen-space variance before dilation (Sigma = var z^2 / fx^2 I at view depth z = 4 - z_w)."""
+    n = len(opacities)
+    cov6 = np.zeros((n, 6))
+    for j, zw in enumerate(depths_world):
+        s2 = screen_var * (4.0 - zw) ** 2 / float(cam.fx) ** 2
+        cov6[j] = [s2, 0, 0, s2, 0, s2]
+    return dict(means=np.array([[0.0, 0.0, zw] for zw in depths_world]), cov6=cov6,
+                opacity=np.asarray(opacities, np.float64), sh=np.zeros((n, 1, 3)), sh_degree=0)
+
+
+def test_ambiguity_flags_mark_decisions_at_their_thresholds():
+    """A pixel is flagged ambiguous when one of its decisions lies within float32 rounding of
+    its threshold: the early stop (T (1 - alpha) against 1e-4), the alpha_min skip, the 3-sigma
+    cut (q against 9, for a splat that would pass alpha_min) and the depth test. Each decision is
+    placed here 1e-6 (relative) from its threshold, where the pixel must be flagged, and then
+    far from it, where it must not be. The camera looks down the axis from (0, 0, 4) onto an
+    odd-sized image, so the centre pixel sees q = 0 and alpha = opacity."""
+    W = H = 33
+    cam = synth.look_at((0, 0, 4.0), (0, 0, 0), W, H, 60.0)
+    f32 = lambda v: float(np.float32(v))
+    t_stop, amin, amax = f32(1e-4), f32(1 / 255), f32(0.99)
+    cx, cy = np.array([W // 2]), np.array([H // 2])
+
+    def flag(scene, px=cx, py=cy, depth=None):
+        prep = oracle.preprocess(scene, cam)
+        assert prep["valid"].all()
+        return int(oracle.render_pixels(prep, px, py, depth=depth)["ambiguous"][0])
+
+    # early stop: alpha 0.99 (clamped), then a2 with 0.01 (1 - a2) = t_stop (1 + e)
+    for e, want in ((1e-6, 1), (0.3, 0)):
+        a2 = 1.0 - t_stop * (1.0 + e) / (1.0 - amax)
+        assert flag(_axis_splats([1.0, a2], [0.5, 0.0], 1.0, cam)) == want, ("stop", e)
+    # alpha_min skip: opacity alpha_min (1 + e) at q = 0
+    for e, want in ((1e-6, 1), (30.0, 0)):
+        assert flag(_axis_splats([amin * (1.0 + e)], [0.0], 1.0, cam)) == want, ("alpha_min", e)
+    # 3-sigma cut: the pixel 3 px right of the centre sees q = 9 / var (dilation added to var)
+    for qv, want in ((9.0 * (1.0 + 1e-6), 1), (4.0, 0)):
+        var = 9.0 / qv - DIL
+        assert flag(_axis_splats([0.9], [0.0], var, cam), px=cx + 3) == want, ("cut", qv)
+    # depth test: a buffer value 1e-7 (relative) beyond the splat's float32 view depth
+    sc = _axis_splats([0.5], [0.0], 1.0, cam)
+    z = float(oracle.preprocess(sc, cam)["zkey"][0])
+    for lim, want in ((z * (1.0 + 1e-7), 1), (z + 1.0, 0)):
+        assert flag(sc, depth=np.array([lim], np.float32)) == want, ("depth", lim)
+
+
 def test_near_plane_at_equality():
     """Reading S6 at equality: a Gaussian whose view depth equals the near plane is culled
     (z <= near), and one a double-precision step beyond it is kept. The camera looks down the
