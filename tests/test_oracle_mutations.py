@@ -157,6 +157,33 @@ MUTATIONS = {
     "ambiguity_flag_of_the_depth_test_dropped": (
         "section 3.4's depth test: a depth within rounding of the buffer's is flagged",
         [("if (isfinite(zlim) && fabs(z - zlim) <= AMB_Z_REL * fabs(zlim)) amb = 1;", "", 1)]),
+    "composite_colour_channel": (
+        "Eq. 3: each channel composites its own colour",
+        [("for (int ch = 0; ch < 3; ++ch) C[ch] += pp->rgb[3 * i + ch] * alpha * T;",
+          "for (int ch = 0; ch < 3; ++ch) C[ch] += pp->rgb[3 * i] * alpha * T;", 1)]),
+    "sh_normalisation_factorials_dropped": (
+        "section 3.2 colour: orthonormal real SH, N = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)",
+        [("double N = sqrt((2.0 * l + 1.0) / (4.0 * PI) * factorial(l - am) / factorial(l + am));",
+          "double N = sqrt((2.0 * l + 1.0) / (4.0 * PI));", 1)]),
+    "sh_sqrt2_dropped": (
+        "section 3.2 colour: the real SH of m != 0 carry sqrt(2)",
+        [("if (m != 0) N *= sqrt(2.0);", "", 1)]),
+    "legendre_recursion": (
+        "section 3.2 colour: Legendre polynomials by Bonnet's recursion",
+        [("double b = (double)l * c[l - 1][k];", "double b = (double)(l + 1) * c[l - 1][k];", 1)]),
+    "principal_point_dropped": (
+        "Eq. 1: x_i = Pi(mu_i), the pinhole projection with its principal point",
+        [("double u = cam->fx * p[0] / z + cam->cx;", "double u = cam->fx * p[0] / z;", 1)]),
+    "view_translation_dropped": (
+        "Eq. 1: the view transform p = R x_w + t",
+        [("p[r] = cam->R[r * 3 + 0] * xw[0] + cam->R[r * 3 + 1] * xw[1] + cam->R[r * 3 + 2] * xw[2] + cam->t[r];\n"
+          "    double z = p[2];",
+          "p[r] = cam->R[r * 3 + 0] * xw[0] + cam->R[r * 3 + 1] * xw[1] + cam->R[r * 3 + 2] * xw[2];\n"
+          "    double z = p[2];", 1)]),
+    "scale_not_squared": (
+        "Algorithm 1, CovFromScaleRot: Sigma = R diag(s)^2 R^T",
+        [("for (int k = 0; k < 3; ++k) { double s = exp((double)log_s[k]); s2[k] = s * s; }",
+          "for (int k = 0; k < 3; ++k) { double s = exp((double)log_s[k]); s2[k] = s; }", 1)]),
     "model_adjoint_left_factor_dropped": (
         "Algorithm 1, model transforms: dL/dSigma = A^T (dL/dSigma_w) A",
         [("acc += sc->A[r * 3 + a] * gSigw[r * 3 + c] * sc->A[c * 3 + b];",
