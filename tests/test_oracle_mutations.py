@@ -2,12 +2,13 @@
 
 The oracle is trusted because tests pin it to something other than itself: closed forms,
 invariants, brute force on tiny inputs, central differences. This file checks that those
-pins would notice a plausible mistake. Each case copies oracle/oracle.c and plants one
-mistake: a dropped term, a flipped sign, a transposed operand, a comparison made strict at
-equality, or a branch that lets a gradient through. It then compiles the copy and runs the
-oracle's pin suites against it in a child process. ORACLE_LIB points the oracle package at
-the copy. The pins hold when every planted copy fails at least one of them, and the
-unchanged copy passes them all.
+pins would notice a plausible mistake. Each case copies oracle/oracle.c (or the oracle's
+Python half, oracle/__init__.py) and plants one mistake: a dropped term, a flipped sign, a
+transposed operand, a comparison made strict at equality, or a branch that lets a gradient
+through. It then builds the copy and runs the oracle's pin suites against it in a child
+process. For oracle.c, ORACLE_LIB points the oracle package at the compiled copy; for the
+Python half, a pytest plugin loads the copy as the module `oracle`. The pins hold when every
+planted copy fails at least one of them, and the unchanged copies pass them all.
 
 The golden fixture is left out of the child runs. It is the oracle's own output, so it is a
 regression check rather than a pin.
@@ -191,49 +192,104 @@ MUTATIONS = {
 }
 
 
+# The same for the oracle's Python half (oracle/__init__.py: the fp16 pre-pack, the dynamic
+# update, the thresholds as the library receives them). A pytest plugin in the child loads the
+# planted copy as the module `oracle` before any test imports it.
+PY_SRC = ROOT / "oracle" / "__init__.py"
+PY_MUTATIONS = {
+    "dynamic_mean_without_time": (
+        "the dynamic workload: mu_t = mu_0 + t v",
+        [("m = _f64(means0) + t * _f64(velocity)", "m = _f64(means0) + _f64(velocity)", 1)]),
+    "dynamic_pulse_without_2pi": (
+        "the dynamic workload: logit_t = logit_0 + A sin(2 pi f t + phi)",
+        [("np.sin(2.0 * np.pi * _f64(freq) * t + _f64(phase))", "np.sin(np.pi * _f64(freq) * t + _f64(phase))", 1)]),
+    "prepack_opacity_sign": (
+        "Algorithm 1's pre-pack: opacity alpha = sigmoid(logit)",
+        [('alpha = 1.0 / (1.0 + np.exp(-_f64(scene["opacity_logits"])))',
+          'alpha = 1.0 / (1.0 + np.exp(_f64(scene["opacity_logits"])))', 1)]),
+    "prepack_covariance_entry_order": (
+        "section 3.4's pre-packed covariance (xx, xy, xz, yy, yz, zz)",
+        [("cov6 = np.stack([sig[:, 0, 0], sig[:, 0, 1], sig[:, 0, 2], sig[:, 1, 1], sig[:, 1, 2], sig[:, 2, 2]], 1)",
+          "cov6 = np.stack([sig[:, 0, 0], sig[:, 0, 2], sig[:, 0, 1], sig[:, 1, 1], sig[:, 1, 2], sig[:, 2, 2]], 1)",
+          1)]),
+    "prepack_means_not_half": (
+        "section 3.4's pre-pack: the means are cast to fp16",
+        [('mu_h = _f64(scene["means"]).astype(np.float16)', 'mu_h = _f64(scene["means"]).astype(np.float32)', 1)]),
+    "thresholds_not_rounded_to_float32": (
+        "the oracle compares against the float32 thresholds the library receives",
+        [("return np.array([float(np.float32(v)) for v in vals], np.float64)",
+          "return np.array([float(v) for v in vals], np.float64)", 1)]),
+}
+
+PY_CONTROL = "python_half_unchanged"   # the plugin route with nothing planted: must pass
+
+PLUGIN = """import importlib.util, sys
+_spec = importlib.util.spec_from_file_location("oracle", {path!r})
+_mod = importlib.util.module_from_spec(_spec)
+sys.modules["oracle"] = _mod
+_spec.loader.exec_module(_mod)
+"""
+
+
 def _planted(name):
-    """oracle.c with the named mistake planted (None: unchanged)."""
-    src = SRC.read_text()
-    if name is None:
+    """oracle.c (or, for a Python mistake, oracle/__init__.py) with the named mistake planted
+    (None: oracle.c unchanged)."""
+    table = PY_MUTATIONS if name in PY_MUTATIONS else MUTATIONS
+    src = (PY_SRC if name in PY_MUTATIONS or name == PY_CONTROL else SRC).read_text()
+    if name is None or name == PY_CONTROL:
         return src
-    for old, new, count in MUTATIONS[name][1]:
+    for old, new, count in table[name][1]:
         found = src.count(old)
-        assert found == count, f"{name}: {old!r} occurs {found} times in oracle.c, expected {count}"
+        assert found == count, f"{name}: {old!r} occurs {found} times in the oracle, expected {count}"
         src = src.replace(old, new)
     return src
 
 
-def _run_pins(name, workdir):
-    """Compile the planted copy and run the pin suites on it; returns (exit code, output tail)."""
+def _run_pins(name, workdir, lib_unchanged=None):
+    """Build the planted copy and run the pin suites on it; returns (exit code, output tail)."""
     tag = name or "unchanged"
-    c_file = workdir / f"{tag}.c"
-    lib = workdir / f"lib{tag}.so"
-    c_file.write_text(_planted(name))
-    subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", str(lib), str(c_file), "-lm"],
-                   check=True, capture_output=True)
-    env = dict(os.environ, ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", *PIN_SUITES, "-x", "-q", "-m", "not gpu",
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    plugin = []
+    if name in PY_MUTATIONS or name == PY_CONTROL:
+        pkg = workdir / f"py_{tag}"
+        pkg.mkdir()
+        (pkg / "planted_oracle.py").write_text(_planted(name))
+        (pkg / f"plant_{tag}.py").write_text(PLUGIN.format(path=str(pkg / "planted_oracle.py")))
+        env["PYTHONPATH"] = os.pathsep.join([str(pkg)] + [p for p in [env.get("PYTHONPATH")] if p])
+        env["ORACLE_LIB"] = str(lib_unchanged)
+        plugin = ["-p", f"plant_{tag}"]
+    else:
+        c_file = workdir / f"{tag}.c"
+        lib = workdir / f"lib{tag}.so"
+        c_file.write_text(_planted(name))
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", str(lib), str(c_file),
+                        "-lm"], check=True, capture_output=True)
+        env["ORACLE_LIB"] = str(lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", *plugin, *PIN_SUITES, "-x", "-q", "-m", "not gpu",
                         "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, (r.stdout + r.stderr)[-600:]
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
-    names = [None] + list(MUTATIONS)
-    for name in names[1:]:
+    import oracle
+    lib_unchanged = oracle.build()
+    names = [None, PY_CONTROL] + list(MUTATIONS) + list(PY_MUTATIONS)
+    for name in names[2:]:
         _planted(name)   # each planted text is found where expected before anything runs
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as pool:
-        results = dict(zip(names, pool.map(lambda n: _run_pins(n, tmp_path), names)))
-    code, tail = results.pop(None)
-    assert code == 0, f"the unchanged copy fails its pins:\n{tail}"
+        results = dict(zip(names, pool.map(lambda n: _run_pins(n, tmp_path, lib_unchanged), names)))
+    for control in (None, PY_CONTROL):
+        code, tail = results.pop(control)
+        assert code == 0, f"the unchanged copy ({control or 'oracle.c'}) fails its pins:\n{tail}"
     survivors = {n: t for n, (c, t) in results.items() if c == 0}
     broken = {n: (c, t) for n, (c, t) in results.items() if c not in (0, 1)}
     assert not broken, "children that did not run their tests: " + "; ".join(
         f"{n} (exit {c}): {t[-200:]}" for n, (c, t) in broken.items())
     assert not survivors, "planted mistakes that no pin catches: " + ", ".join(
-        f"{n} ({MUTATIONS[n][0]})" for n in survivors)
+        f"{n} ({{**MUTATIONS, **PY_MUTATIONS}}[n][0])" for n in survivors)
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(PY_MUTATIONS))
 def test_planted_text_is_in_the_oracle(name):
     _planted(name)
